@@ -1,0 +1,244 @@
+"""Pins of the CPU oracle to facts fixed by the paper and by mathematics (no GPU).
+
+Each test checks the oracle against something other than itself: the paper's two-bus example
+(tests/golden/two_bus_fig2.json, Sec. III Fig. 2), the closed-form roots of the two-bus quadratic,
+the feasibility condition of Eq. 10, the contraction factor of Eq. 11, the radial path-sum form of
+Y_dd^{-1}, an independent sparse Newton-Raphson, the power-balance residual of Eq. 1 and brute
+force on tiny feeders.  The last test plants mistakes in the oracle's inputs (a sign, a dropped
+conjugate, a dropped W) and shows that the pins catch each of them.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2403_04578_gb300 import inputs as G
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def fig2():
+    with open(os.path.join(HERE, "golden", "two_bus_fig2.json")) as fh:
+        g = json.load(fh)
+    return complex(*g["z_s"]), complex(g["p_l"], g["q_l"]), complex(g["v0_abs"], 0.0)
+
+
+def two_bus_case(z, v0=1.0 + 0j):
+    return O.Case(2, [0], [1], [z], slack=0, vs=v0)
+
+
+def power_balance(v, z, s, v0):
+    """Eq. 1 for two buses: injection at bus 1 is v conj((v - v0)/z); it must equal -s."""
+    return abs(v * np.conj((v - v0) / z) + s)
+
+
+def test_closed_form_roots_solve_the_two_bus_power_flow():
+    z, s, v0 = fig2()
+    hi, lo = O.two_bus_roots(z, s, v0)
+    assert power_balance(hi, z, s, v0) < 1e-14
+    assert power_balance(lo, z, s, v0) < 1e-14
+    assert abs(hi) > abs(lo)
+    # |v_high| = 0.62115..., |v_low| = 0.37970... for the Fig. 2 load.
+    assert abs(abs(hi) - 0.621150) < 5e-6 and abs(abs(lo) - 0.379697) < 5e-6
+
+
+def test_fpi_reaches_the_high_voltage_root_fig2():
+    z, s, v0 = fig2()
+    c = two_bus_case(z, v0)
+    assert abs(c.K[0, 0] + z) < 1e-15  # K = -Y_dd^{-1} = -z_s
+    assert abs(c.W[0] - v0) < 1e-15  # W = K Y_ds v_s = v_s
+    V, it, d = c.solve(np.array([[s]]), tol=1e-14, max_iter=500)
+    hi, lo = O.two_bus_roots(z, s, v0)
+    assert it[0] > 0
+    assert abs(V[0, 0] - hi) < 1e-13
+
+
+def test_contraction_ratio_matches_eq11():
+    """Eq. 11 for two buses: the FPI step shrinks by k = |z_s| / |z_l| = |z||s| / |v|^2."""
+    z, s, v0 = fig2()
+    c = two_bus_case(z, v0)
+    hi, _ = O.two_bus_roots(z, s, v0)
+    k = O.two_bus_contraction(z, s, hi)
+    assert abs(k - 0.6113) < 1e-3
+    S = np.array([[s]])
+    iterates = [c.solve(S, tol=0.0, max_iter=m)[0][0, 0] for m in range(1, 40)]
+    steps = np.abs(np.diff(iterates))
+    ratios = steps[1:] / steps[:-1]
+    # The map is anti-holomorphic (v -> v0 - z conj(s)/conj(v)), so the step ratio tends to k.
+    assert abs(ratios[-1] - k) < 1e-4
+
+
+def test_low_root_is_repelling_and_nr_can_find_it():
+    z, s, v0 = fig2()
+    hi, lo = O.two_bus_roots(z, s, v0)
+    assert O.two_bus_contraction(z, s, lo) > 1.0  # Eq. 11: k > 1 at the low-voltage root
+    c = two_bus_case(z, v0)
+    V, it, _ = c.solve(np.array([[s]]), V0=np.array([[lo * (1 + 1e-6)]]), tol=1e-13, max_iter=2000)
+    assert it[0] > 0 and abs(V[0, 0] - hi) < 1e-11
+    # Newton-Raphson started next to the low root converges to it (Fig. 4(a)).
+    vnr, nit, ok = O.nr_solve(c.ybus_sparse(), 0, v0, [1], [s], v_init=[lo * (1 + 1e-3)], tol=1e-13)
+    assert ok and abs(vnr[0] - lo) < 1e-10
+
+
+def test_fpi_basin_covers_the_plane():
+    """Fig. 4(c): the FPI reaches the high root from starts all over the complex plane."""
+    z, s, v0 = fig2()
+    hi, lo = O.two_bus_roots(z, s, v0)
+    c = two_bus_case(z, v0)
+    mags = np.linspace(0.05, 2.0, 14)
+    angs = np.linspace(-np.pi, np.pi, 13, endpoint=False)
+    starts = (mags[:, None] * np.exp(1j * angs[None, :])).ravel()
+    starts = starts[np.abs(starts - lo) > 1e-3]
+    S = np.full((starts.size, 1), s)
+    V, it, _ = c.solve(S, V0=starts[:, None], tol=1e-13, max_iter=3000)
+    assert (it > 0).all()
+    assert np.abs(V[:, 0] - hi).max() < 1e-11
+
+
+@pytest.mark.parametrize("scale", [0.5, 0.9, 0.99, 1.01, 1.5])
+def test_feasibility_eq10(scale):
+    """Eq. 10 is sufficient; the exact two-bus limit is the zero of the quadratic's discriminant."""
+    z, s0, v0 = fig2()
+    # Largest load in the direction of s0 with a real root: a^2 = 4|z|^2|s|^2.
+    u = s0 / abs(s0)
+    lim = None
+    lo_, hi_ = 0.0, 10.0
+    for _ in range(200):
+        mid = 0.5 * (lo_ + hi_)
+        if O.two_bus_roots(z, mid * u, v0) is None:
+            hi_ = mid
+        else:
+            lo_ = mid
+    lim = lo_
+    s = scale * lim * u
+    c = two_bus_case(z, v0)
+    V, it, _ = c.solve(np.array([[s]]), tol=1e-12, max_iter=20000)
+    if scale < 1.0:
+        assert it[0] > 0
+        assert abs(V[0, 0] - O.two_bus_roots(z, s, v0)[0]) < 1e-9
+    else:
+        assert it[0] < 0  # no solution: never converges
+        assert not O.feasible_eq10(z, s, v0)
+    if O.feasible_eq10(z, s, v0):
+        assert it[0] > 0
+
+
+@pytest.mark.parametrize("n_bus,seed", [(2, 1), (5, 2), (20, 3), (60, 4), (34, 1)])
+def test_K_is_the_radial_path_sum(n_bus, seed):
+    f = G.make_feeder(n_bus, seed)
+    c = O.Case.from_feeder(f)
+    Kp = O.path_sum_K(f.n_bus, f.from_bus, f.to_bus, f.z_pu)
+    assert np.abs(c.K - Kp).max() <= 1e-12 * np.abs(Kp).max()
+    # Shunt-free radial feeder: W = K Y_ds v_s = v_s for every bus.
+    assert np.abs(c.W - f.v0).max() < 1e-13
+
+
+def test_W_follows_a_complex_slack_voltage():
+    f = G.make_feeder(30, 5)
+    vs = 1.03 * np.exp(0.02j)
+    c = O.Case(f.n_bus, f.from_bus, f.to_bus, f.z_pu, vs=vs)
+    assert np.abs(c.W - vs).max() < 1e-13
+
+
+def _config1(T=1440):
+    f = G.make_feeder(34, 1)
+    return f, O.Case.from_feeder(f), G.load_tensor(f, T, 1)
+
+
+def test_fpi_agrees_with_newton_raphson_config1():
+    f, c, S = _config1()
+    V, it, _ = c.solve(S, tol=1e-13)
+    assert (it > 0).all()
+    Ysp = c.ybus_sparse()
+    worst = 0.0
+    for t in range(0, S.shape[0], 7):
+        vnr, _, ok = O.nr_solve(Ysp, 0, f.v0, f.pq_bus, S[t], tol=1e-12)
+        assert ok
+        worst = max(worst, np.abs(vnr - V[t]).max())
+    assert worst <= 1e-10
+
+
+def test_fpi_agrees_with_newton_raphson_heavy_feeder():
+    f = G.make_feeder(200, 2)
+    c = O.Case.from_feeder(f)
+    S = G.load_tensor(f, 4096, 2)[1100:1120]  # evening peak
+    V, it, _ = c.solve(S, tol=1e-13)
+    assert (it > 0).all()
+    Ysp = c.ybus_sparse()
+    for t in range(S.shape[0]):
+        vnr, _, ok = O.nr_solve(Ysp, 0, f.v0, f.pq_bus, S[t], tol=1e-12)
+        assert ok and np.abs(vnr - V[t]).max() <= 1e-10
+
+
+def test_power_balance_residual_and_contraction_certificate():
+    for nb, seed, sl in ((34, 1, slice(0, 1440, 5)), (200, 2, slice(1000, 1200)), (500, 3, slice(1100, 1130))):
+        f = G.make_feeder(nb, seed)
+        c = O.Case.from_feeder(f)
+        S = G.load_tensor(f, 4096, seed)[sl]
+        V, it, _ = c.solve(S, tol=1e-13)
+        assert (it > 0).all()
+        assert c.mismatch(S, V).max() <= 1e-10
+        for t in range(0, S.shape[0], max(1, S.shape[0] // 10)):
+            assert O.contraction_certificate(c.K, S[t], V[t]) < 1.0
+
+
+def test_stopping_rule_counts_updates():
+    """iters = number of updates applied; the returned V is that many steps from the start."""
+    f, c, S = _config1(64)
+    V, it, d = c.solve(S, tol=1e-10)
+    for t in (0, 17, 63):
+        k = int(it[t])
+        Vk, itk, _ = c.solve(S[t:t + 1], tol=0.0, max_iter=k)
+        assert np.array_equal(Vk[0], V[t]) and itk[0] == -k
+        Vk1, _, dk1 = c.solve(S[t:t + 1], tol=0.0, max_iter=k - 1)
+        assert np.abs(V[t] - Vk1[0]).max() == pytest.approx(d[t], rel=1e-12, abs=0)
+        assert d[t] <= 1e-10 < np.abs(Vk1[0] - c.solve(S[t:t + 1], tol=0.0, max_iter=k - 2)[0][0]).max()
+
+
+@pytest.mark.parametrize("n_bus,seed", [(3, 11), (4, 12)])
+def test_tiny_feeders_brute_force(n_bus, seed):
+    """All roots by NR from many starts; the FPI returns the one with the largest min |V|."""
+    f = G.make_feeder(n_bus, seed)
+    c = O.Case.from_feeder(f)
+    rng = np.random.default_rng(seed)
+    s_dir = rng.uniform(0.5, 3.0, n_bus - 1) + 1j * rng.uniform(0.2, 1.0, n_bus - 1)
+    lo_, hi_ = 0.0, 1.0 / np.abs(c.K).max()
+    while c.solve(hi_ * s_dir[None, :], tol=1e-9, max_iter=400)[1][0] > 0:
+        hi_ *= 2
+    for _ in range(30):  # loadability limit along s_dir (approximate: slow convergence near it)
+        mid = 0.5 * (lo_ + hi_)
+        lo_, hi_ = (mid, hi_) if c.solve(mid * s_dir[None, :], tol=1e-9, max_iter=400)[1][0] > 0 else (lo_, mid)
+    s = 0.85 * lo_ * s_dir  # near the nose the low-voltage roots are within NR's reach
+    V, it, _ = c.solve(s[None, :], tol=1e-13, max_iter=20000)
+    assert it[0] > 0
+    Ysp = c.ybus_sparse()
+    roots = []
+    for _ in range(300):
+        v_init = rng.uniform(0.05, 1.1, n_bus - 1) * np.exp(1j * rng.uniform(-0.8, 0.3, n_bus - 1))
+        v, _, ok = O.nr_solve(Ysp, 0, f.v0, f.pq_bus, s, v_init=v_init, tol=1e-11, max_iter=25)
+        if ok and not any(np.abs(v - r).max() < 1e-7 for r in roots):
+            roots.append(v)
+    assert len(roots) >= 2  # the high root and at least one low-voltage root
+    best = max(roots, key=lambda r: np.abs(r).min())
+    assert np.abs(best - V[0]).max() < 1e-9
+
+
+@pytest.mark.parametrize("mistake", ["K_sign", "no_conj", "no_W", "K_conj"])
+def test_pins_catch_planted_mistakes(mistake):
+    """A plausible mistake planted in the oracle's inputs fails the two-bus closed-form pin."""
+    z, s, v0 = fig2()
+    c = two_bus_case(z, v0)
+    K, W, S = c.K.copy(), c.W.copy(), np.array([[s]])
+    if mistake == "K_sign":
+        K = -K
+    elif mistake == "no_conj":
+        S = np.conj(S)  # conj(S/V) would become S/conj(V)... i.e. the load current's conjugate dropped
+    elif mistake == "no_W":
+        W = np.zeros_like(W)
+    elif mistake == "K_conj":
+        K = np.conj(K)
+    V, it, _ = O.fpi(K, W, S, tol=1e-13, max_iter=500)
+    hi, _ = O.two_bus_roots(z, s, v0)
+    assert not (it[0] > 0 and abs(V[0, 0] - hi) < 1e-6)

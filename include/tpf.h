@@ -1,0 +1,185 @@
+/*
+ * tpf.h -- C ABI of the GB300 tensor power flow library (libtpf.so).
+ *
+ * The library solves many power flows of one distribution feeder at once with the dense
+ * fixed-point iteration of the paper (Sec. II Eq. 2-3, Sec. IV-A Eq. 12, Algorithm 1):
+ *
+ *     V_{k+1} = K conj(S ./ V_k) + W,      K = -Y_dd^{-1},   W = K Y_ds v_s,
+ *
+ * applied to every column (time step x scenario) of the load tensor S.  S is the *load*
+ * (consumption positive), so the current drawn at a demand bus is conj(S_i / V_i) (Eq. 1).
+ *
+ * Data layout.  A load tensor holds T power flows; column t is the contiguous row
+ * S[t*n_pq .. (t+1)*n_pq) of complex128 values (real, imaginary interleaved), i.e. the reshaped
+ * S-dot of Eq. 12 stored with the bus index fastest.  V, iteration counts and mismatches use the
+ * same column order.  Bus order inside a column is the order of pq_bus given to tpf_create.
+ *
+ * Ownership.  A tpf_handle owns K, W, the network arrays and all device workspaces.  The caller
+ * owns every tensor passed to a solve; the library never frees or keeps caller pointers after
+ * the call returns.
+ *
+ * Errors.  Every entry point returns a tpf_status.  Argument errors are detected on the host
+ * before any device work.  Device-side failures (a bounded wait that expired, a CUDA error) are
+ * reported by the solve that met them.  tpf_strerror() names a status.
+ *
+ * Threads and streams.  A handle may be used by one host thread at a time.  All device work of a
+ * solve is issued on the stream passed to it (a cudaStream_t, passed as void*; NULL = legacy
+ * default stream), and the solve returns only after that work has finished.
+ */
+#ifndef TPF_H
+#define TPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tpf_handle tpf_handle;
+
+typedef enum {
+    TPF_OK = 0,
+    TPF_EINVAL = 1,       /* a bad argument (sizes, indices, NULL pointers, options)            */
+    TPF_ESINGULAR = 2,    /* Y_dd is singular: a bus is not connected to the slack              */
+    TPF_ENOMEM = 3,       /* a host or device allocation failed                                 */
+    TPF_ECUDA = 4,        /* a CUDA runtime or driver call failed (including "no device")       */
+    TPF_ETIMEOUT = 5,     /* a bounded device-side wait expired; outputs are not valid          */
+    TPF_ENOCONV = 6,      /* at least one column did not converge; all outputs are valid       */
+    TPF_EUNSUPPORTED = 7  /* the request is valid but this build or device cannot serve it     */
+} tpf_status;
+
+/* Arithmetic of a solve. */
+enum {
+    TPF_PREC_FP64 = 0,  /* the plain double-precision fixed-point iteration (direct form)          */
+    TPF_PREC_MIXED = 1  /* fp16 tensor-core sweeps with FP32 accumulation in residual form         *
+                         * V <- V + K rho(V); V is carried as two floats and rho is evaluated    *
+                         * against a double-float anchor, so results reach FP64-level accuracy  */
+};
+
+/* Starting point of a solve. */
+enum {
+    TPF_START_FLAT = 0,  /* V_0 = 1 + j0 at every bus (Algorithm 1)                             */
+    TPF_START_GIVEN = 1  /* V_0 is read from the V buffer passed to the solve                   */
+};
+
+typedef struct {
+    double tol;       /* per-column stop: max_i |V_{k+1,i} - V_{k,i}| <= tol (pu).  Default 1e-10 */
+    int max_iter;     /* cap on sweeps per column (Algorithm 1's "iterations").  Default 100     */
+    int precision;    /* TPF_PREC_*.  Default TPF_PREC_MIXED                                      */
+    int start;        /* TPF_START_*.  Default TPF_START_FLAT                                     */
+    double switch_tol;/* mixed only: once a column's step falls below this (pu), or is predicted  *
+                       * to fall below 3e-6 pu in the next sweep, its V is frozen as the anchor   *
+                       * V_ref, rho(V_ref) is evaluated once in double-float, and later sweeps    *
+                       * add FP32 corrections in V - V_ref.  Default 1e-4                         */
+    int profile;      /* nonzero: time every kernel of the solve with CUDA events on its stream  *
+                       * and report the totals in tpf_stats.  Default 0                           */
+} tpf_opts;
+
+/* Per-solve counters (filled by tpf_last_stats after a solve). */
+typedef struct {
+    int sweeps;           /* sweeps launched (the largest per-column count)                    */
+    int precise_sweeps;   /* mixed: sweeps in which at least one column was anchored            */
+    int64_t converged;    /* columns that met tol                                               */
+    int64_t columns;      /* T of the last solve                                                */
+    int64_t kernel_launches; /* kernels of this library launched by the last solve              */
+    /* Filled only when opts.profile was set (milliseconds of device time, CUDA events):        */
+    double gemm_ms;          /* the dense sweep kernel: tensor-core GEMM (mixed) or FP64 sweep   */
+    double residual_ms;      /* mixed: the per-sweep residual / decision kernel; FP64: decision  */
+    double other_ms;         /* packing, initialisation and the output / mismatch kernel         */
+    int64_t gemm_launches;   /* launches of the dense sweep kernel                               */
+    int64_t gemm_columns;    /* sum over those launches of the columns still iterating           */
+} tpf_stats;
+
+/* Fill *opts with the defaults listed in tpf_opts. */
+void tpf_default_opts(tpf_opts *opts);
+
+/* Name of a status (static string, never NULL). */
+const char *tpf_strerror(tpf_status status);
+
+/*
+ * Build a feeder: Eq. 1's admittance matrix from the branch list, then K = -Y_dd^{-1} and
+ * W = K Y_ds v_s (Eq. 3 with constant power, Algorithm 1's Z_B and W), on the host in double
+ * precision, and upload them with the network arrays to the current CUDA device.
+ *
+ *   n_bus, n_branch    number of buses (>= 2) and of branches (>= n_bus - 1)
+ *   from, to           [n_branch] bus indices in [0, n_bus) of each branch's ends
+ *   z_pu               [2*n_branch] series impedance r + jx of each branch in pu, interleaved;
+ *                      no shunts.  |z| must be > 0.
+ *   slack              index of the slack bus;  v0_re + j v0_im its voltage (pu)
+ *   n_pq, pq_bus       the demand buses, [n_pq] distinct indices, every bus but the slack
+ *                      (n_pq = n_bus - 1); their order is the bus order of every tensor.
+ *   out                receives the new handle (set to NULL on failure)
+ *
+ * A radial network (a tree rooted at the slack) gets K from the path sums of its branch
+ * impedances; any other connected network from a dense LU inverse of Y_dd.  Returns TPF_EINVAL
+ * for bad indices or sizes, TPF_ESINGULAR if some bus is not connected to the slack, TPF_ECUDA
+ * if no device can be used.  All arrays are host memory, read during the call only.
+ */
+tpf_status tpf_create(int n_bus, int n_branch, const int32_t *from, const int32_t *to,
+                      const double *z_pu, int slack, double v0_re, double v0_im, int n_pq,
+                      const int32_t *pq_bus, tpf_handle **out);
+
+/* Release a handle and every device buffer it owns (NULL is a no-op). */
+void tpf_destroy(tpf_handle *h);
+
+/* Number of demand buses of a handle (the column length of every tensor). */
+int tpf_n_pq(const tpf_handle *h);
+
+/*
+ * Host-only precomputation (no device needed): the same K (= -Y_dd^{-1}) and W (= K Y_ds v_s) that
+ * tpf_create uploads, written to caller host buffers K_out [2*n_pq*n_pq] (row-major complex,
+ * interleaved) and W_out [2*n_pq].  Arguments and errors as tpf_create.
+ */
+tpf_status tpf_precompute_host(int n_bus, int n_branch, const int32_t *from, const int32_t *to,
+                               const double *z_pu, int slack, double v0_re, double v0_im,
+                               int n_pq, const int32_t *pq_bus, double *K_out, double *W_out);
+
+/*
+ * Solve T power flows (Algorithm 1, one column per power flow, each column stopping on its own):
+ *
+ *   S_dev        device, complex128 [T][n_pq], the loads (read only)
+ *   V_dev        device, complex128 [T][n_pq], receives V.  Read first as V_0 when
+ *                opts->start == TPF_START_GIVEN.
+ *   iters_dev    device, int32 [T], receives the sweeps applied to each column, or -max_iter
+ *                for a column that never met tol (NULL: not written)
+ *   mismatch_dev device, float64 [T], receives max_i |V_i conj((Y v)_i) + S_i| in pu, the power
+ *                balance of Eq. 1 at the returned V (NULL: not written)
+ *   opts         NULL for defaults
+ *   stream       cudaStream_t for all device work
+ *
+ * T = 0 is a valid empty solve.  Returns TPF_OK when every column met tol, TPF_ENOCONV when some
+ * did not (outputs still valid), TPF_ETIMEOUT or TPF_ECUDA on device failures.  Device buffers
+ * must not overlap.  The call blocks until the stream has finished the solve.
+ */
+tpf_status tpf_solve(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev, int32_t *iters_dev,
+                     double *mismatch_dev, const tpf_opts *opts, void *stream);
+
+/*
+ * tpf_solve with HOST buffers (same shapes and meaning): copies S (and V_0) to the device, solves,
+ * and copies V, iteration counts and mismatches back, all on `stream`.  Device staging buffers
+ * are owned by the handle and grow to the largest T seen.  Host buffers may be pageable or
+ * pinned; pinned memory is faster.  iters_host and mismatch_host may be NULL.
+ */
+tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_host,
+                          int32_t *iters_host, double *mismatch_host, const tpf_opts *opts,
+                          void *stream);
+
+/* Counters of the last solve on this handle. */
+tpf_status tpf_last_stats(const tpf_handle *h, tpf_stats *out);
+
+/*
+ * Self-test of the tensor-core complex GEMM used by the mixed solve (tcgen05, fp16 operands,
+ * FP32 accumulation): D = A B^T over complex numbers, with
+ *   A_re, A_im  device fp16 [M][K] (row-major, K fastest),  B_re, B_im device fp16 [N][K],
+ *   D_re, D_im  device float32 [N][M] (D[n][m] = sum_k A[m][k] B[n][k]).
+ * M, N, K must be positive multiples of 128, 128 and 64.  Blocks until done.
+ */
+tpf_status tpf_selftest_gemm(int M, int N, int K, const void *A_re, const void *A_im,
+                             const void *B_re, const void *B_im, float *D_re, float *D_im,
+                             void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TPF_H */

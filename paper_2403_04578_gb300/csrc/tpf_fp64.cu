@@ -1,0 +1,408 @@
+// Device buffers of a handle and the plain double-precision solve path.
+//
+// The FP64 path is Algorithm 1 in its direct form, V_{k+1} = K conj(S ./ V_k) + W (Eq. 2 and
+// Eq. 12), with per-column stopping.  Each sweep is one kernel over (64-bus x 32-column) output
+// tiles: the tile's injections conj(S ./ V) are formed from V_k in shared memory chunk by chunk
+// (the Hadamard step of Algorithm 1), multiplied by the matching K tile with FP64 FMAs, W is
+// added and the per-column max |V_{k+1} - V_k| is folded in with an atomic max.  GB300 runs FP64
+// at 1/64 of its FP32 rate, so this path is FP64-pipe bound; it is the reference point for the
+// mixed-precision path.
+#include <cstdio>
+#include <math_constants.h>
+
+#include "tpf_internal.h"
+
+namespace tpf {
+
+#define TPF_CK(call)                                   \
+    do {                                               \
+        if ((call) != cudaSuccess) {                   \
+            cudaGetLastError();                        \
+            return TPF_ECUDA;                          \
+        }                                              \
+    } while (0)
+
+namespace {
+
+__global__ void k_to_fp16(const double *__restrict__ K, int n, int n_pad, float scale, __half *Kr, __half *Ki) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_pad * n_pad) return;
+    int i = (int)(idx / n_pad), j = (int)(idx % n_pad);
+    float re = 0.f, im = 0.f;
+    if (i < n && j < n) {
+        re = (float)K[((size_t)i * n + j) * 2] * scale;
+        im = (float)K[((size_t)i * n + j) * 2 + 1] * scale;
+    }
+    Kr[idx] = __float2half_rn(re);
+    Ki[idx] = __float2half_rn(im);
+}
+
+}  // namespace
+
+tpf_status upload_network(tpf_handle *h) {
+    int dev = 0;
+    TPF_CK(cudaGetDevice(&dev));
+    h->device = dev;
+    const Network &net = h->net;
+    DeviceNet &d = h->dev;
+    const int n = net.n_pq;
+    d.n = n;
+    d.n_pad = (int)round_up(n, kTileM);
+    const int nnz = net.row_ptr[n];
+    TPF_CK(cudaMalloc(&d.K64, sizeof(double) * 2 * (size_t)n * n));
+    TPF_CK(cudaMalloc(&d.W64, sizeof(double) * 2 * (size_t)n));
+    TPF_CK(cudaMalloc(&d.row_ptr, sizeof(int) * (n + 1)));
+    TPF_CK(cudaMalloc(&d.nbr, sizeof(int) * (nnz > 0 ? nnz : 1)));
+    TPF_CK(cudaMalloc(&d.y64, sizeof(double) * 2 * (nnz > 0 ? nnz : 1)));
+    TPF_CK(cudaMalloc(&d.y2f, sizeof(float4) * (nnz > 0 ? nnz : 1)));
+    TPF_CK(cudaMemcpy(d.K64, net.K.data(), sizeof(double) * net.K.size(), cudaMemcpyHostToDevice));
+    TPF_CK(cudaMemcpy(d.W64, net.W.data(), sizeof(double) * net.W.size(), cudaMemcpyHostToDevice));
+    TPF_CK(cudaMemcpy(d.row_ptr, net.row_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    if (nnz > 0) {
+        TPF_CK(cudaMemcpy(d.nbr, net.nbr.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice));
+        TPF_CK(cudaMemcpy(d.y64, net.y.data(), sizeof(double) * 2 * nnz, cudaMemcpyHostToDevice));
+        // Double-float split of each admittance: hi = fl(y), lo = fl(y - hi).
+        std::vector<float4> y2(nnz);
+        for (int k = 0; k < nnz; ++k) {
+            double re = net.y[2 * k], im = net.y[2 * k + 1];
+            float rh = (float)re, ih = (float)im;
+            y2[k] = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+        }
+        TPF_CK(cudaMemcpy(d.y2f, y2.data(), sizeof(float4) * nnz, cudaMemcpyHostToDevice));
+    }
+    // fp16 planes of K * 2^k_exp with the largest component in [2^13, 2^14).
+    double kmax = 0.0;
+    for (double v : net.K) kmax = fmax(kmax, fabs(v));
+    int e = 0;
+    if (kmax > 0.0) frexp(kmax, &e);
+    d.k_exp = 14 - e;
+    const size_t plane = (size_t)d.n_pad * d.n_pad;
+    TPF_CK(cudaMalloc(&d.Kr16, sizeof(__half) * plane));
+    TPF_CK(cudaMalloc(&d.Ki16, sizeof(__half) * plane));
+    k_to_fp16<<<(unsigned)((plane + 255) / 256), 256>>>(d.K64, n, d.n_pad, ldexpf(1.0f, d.k_exp),
+                                                          (__half *)d.Kr16, (__half *)d.Ki16);
+    TPF_CK(cudaGetLastError());
+    TPF_CK(cudaDeviceSynchronize());
+    return TPF_OK;
+}
+
+void free_device(tpf_handle *h) {
+    DeviceNet &d = h->dev;
+    cudaFree(d.K64); cudaFree(d.W64); cudaFree(d.row_ptr); cudaFree(d.nbr); cudaFree(d.y64); cudaFree(d.y2f);
+    cudaFree(d.Kr16); cudaFree(d.Ki16);
+    d = DeviceNet();
+    Workspace &w = h->ws;
+    cudaFree(w.Vhi); cudaFree(w.Vlo); cudaFree(w.Shi); cudaFree(w.Slo); cudaFree(w.Rr16); cudaFree(w.Ri16);
+    cudaFree(w.RefHi); cudaFree(w.RefLo); cudaFree(w.dprev);
+    cudaFree(w.Valt); cudaFree(w.delta_bits); cudaFree(w.delta64); cudaFree(w.iters); cudaFree(w.flags);
+    cudaFree(w.rexp); cudaFree(w.tile_active); cudaFree(w.counters);
+    if (w.counters_host) cudaFreeHost(w.counters_host);
+    cudaFree(w.S_dev); cudaFree(w.V_dev); cudaFree(w.it_dev); cudaFree(w.mm_dev);
+    w = Workspace();
+    if (h->tmaps) {
+        free(h->tmaps);
+        h->tmaps = nullptr;
+    }
+    cudaGetLastError();
+}
+
+tpf_status ensure_workspace(tpf_handle *h, int64_t cols, bool mixed) {
+    Workspace &w = h->ws;
+    const int n = h->dev.n, n_pad = h->dev.n_pad;
+    cols = round_up(cols, kTileN);
+    const bool have_mixed = w.Vhi != nullptr;
+    const bool have_fp64 = w.Valt != nullptr;
+    if (w.counters == nullptr) {
+        TPF_CK(cudaMalloc(&w.counters, sizeof(int) * 8));
+        TPF_CK(cudaMallocHost(&w.counters_host, sizeof(int) * 8));
+        TPF_CK(cudaMemset(w.counters, 0, sizeof(int) * 8));
+    }
+    if (cols <= w.cap_cols && (mixed ? have_mixed : have_fp64)) return TPF_OK;
+    int64_t cap = cols > w.cap_cols ? cols : w.cap_cols;
+    bool want_mixed = mixed || (have_mixed && cap > w.cap_cols);
+    bool want_fp64 = !mixed || (have_fp64 && cap > w.cap_cols);
+    if (cap > w.cap_cols) {
+        cudaFree(w.delta_bits); cudaFree(w.delta64); cudaFree(w.iters); cudaFree(w.flags); cudaFree(w.rexp);
+        cudaFree(w.tile_active); cudaFree(w.dprev);
+        w.delta_bits = nullptr; w.delta64 = nullptr; w.iters = nullptr; w.flags = nullptr; w.rexp = nullptr;
+        w.tile_active = nullptr; w.dprev = nullptr;
+        TPF_CK(cudaMalloc(&w.delta_bits, sizeof(unsigned) * cap));
+        TPF_CK(cudaMalloc(&w.dprev, sizeof(unsigned) * cap));
+        TPF_CK(cudaMalloc(&w.delta64, sizeof(unsigned long long) * cap));
+        TPF_CK(cudaMalloc(&w.iters, sizeof(int) * cap));
+        TPF_CK(cudaMalloc(&w.flags, sizeof(int) * cap));
+        TPF_CK(cudaMalloc(&w.rexp, sizeof(int) * cap));
+        TPF_CK(cudaMalloc(&w.tile_active, sizeof(int) * (cap / kTileN)));
+        if (have_mixed || want_mixed) {
+            cudaFree(w.Vhi); cudaFree(w.Vlo); cudaFree(w.Shi); cudaFree(w.Slo); cudaFree(w.Rr16); cudaFree(w.Ri16);
+            cudaFree(w.RefHi); cudaFree(w.RefLo);
+            w.Vhi = w.Vlo = w.Shi = w.Slo = w.RefHi = w.RefLo = nullptr; w.Rr16 = w.Ri16 = nullptr;
+        }
+        if (have_fp64 || want_fp64) {
+            cudaFree(w.Valt);
+            w.Valt = nullptr;
+        }
+        w.cap_cols = cap;
+    }
+    w.n_pad = n_pad;
+    const size_t el = (size_t)w.cap_cols * n_pad;
+    if (want_mixed && w.Vhi == nullptr) {
+        if (cudaMalloc(&w.Vhi, sizeof(float2) * el) != cudaSuccess || cudaMalloc(&w.Vlo, sizeof(float2) * el) != cudaSuccess ||
+            cudaMalloc(&w.Shi, sizeof(float2) * el) != cudaSuccess || cudaMalloc(&w.Slo, sizeof(float2) * el) != cudaSuccess ||
+            cudaMalloc(&w.RefHi, sizeof(float2) * el) != cudaSuccess || cudaMalloc(&w.RefLo, sizeof(float2) * el) != cudaSuccess ||
+            cudaMalloc(&w.Rr16, sizeof(__half) * el) != cudaSuccess || cudaMalloc(&w.Ri16, sizeof(__half) * el) != cudaSuccess) {
+            cudaGetLastError();
+            return TPF_ENOMEM;
+        }
+    }
+    if (want_fp64 && w.Valt == nullptr) {
+        if (cudaMalloc(&w.Valt, sizeof(double) * 2 * (size_t)w.cap_cols * n) != cudaSuccess) {
+            cudaGetLastError();
+            return TPF_ENOMEM;
+        }
+    }
+    return TPF_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// FP64 path kernels
+// ------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int F64_BM = 64, F64_BN = 32, F64_KC = 16;
+
+__global__ void f64_init(int64_t T, int64_t cols, int n, int flat, double2 *V, int *flags, int *iters,
+                         unsigned long long *delta) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx < cols) {
+        flags[idx] = idx < T ? kActive : 0;
+        iters[idx] = 0;
+        delta[idx] = 0ull;
+    }
+    if (flat && idx < T * (int64_t)n) V[idx] = make_double2(1.0, 0.0);
+}
+
+// One sweep of V_out = K conj(S ./ V_in) + W over a (64 x 32) tile; inactive columns untouched.
+__global__ void __launch_bounds__(256) f64_sweep(const double2 *__restrict__ K, const double2 *__restrict__ W,
+                                                 const double2 *__restrict__ S, const double2 *__restrict__ Vin,
+                                                 double2 *__restrict__ Vout, int n, int64_t T,
+                                                 const int *__restrict__ flags, unsigned long long *delta) {
+    __shared__ double2 Ks[F64_BM][F64_KC + 1];
+    __shared__ double2 Is[F64_KC][F64_BN];
+    __shared__ int act[F64_BN];
+    __shared__ int any;
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.y * F64_BM;
+    const int64_t t0 = (int64_t)blockIdx.x * F64_BN;
+    if (tid == 0) any = 0;
+    __syncthreads();
+    if (tid < F64_BN) {
+        int64_t t = t0 + tid;
+        int a = (t < T) ? (flags[t] & kActive) : 0;
+        act[tid] = a;
+        if (a) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (!any) return;
+    const int rg = tid / 16, cg = tid % 16;
+    double2 acc[4][2];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) acc[r][c] = make_double2(0.0, 0.0);
+    for (int k0 = 0; k0 < n; k0 += F64_KC) {
+        for (int e = tid; e < F64_BM * F64_KC; e += 256) {
+            int r = e / F64_KC, c = e % F64_KC;
+            int i = m0 + r, k = k0 + c;
+            Ks[r][c] = (i < n && k < n) ? K[(size_t)i * n + k] : make_double2(0.0, 0.0);
+        }
+        for (int e = tid; e < F64_KC * F64_BN; e += 256) {
+            int kk = e % F64_KC, tt = e / F64_KC;
+            int k = k0 + kk;
+            int64_t t = t0 + tt;
+            double2 cur = make_double2(0.0, 0.0);
+            if (k < n && act[tt]) {
+                double2 s = S[t * n + k], v = Vin[t * n + k];
+                // conj(s / v) = conj(s) v / |v|^2
+                double inv = 1.0 / (v.x * v.x + v.y * v.y);
+                cur = make_double2((s.x * v.x + s.y * v.y) * inv, (s.x * v.y - s.y * v.x) * inv);
+            }
+            Is[kk][tt] = cur;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < F64_KC; ++kk) {
+            double2 a[4], b[2];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = Ks[rg * 4 + r][kk];
+#pragma unroll
+            for (int c = 0; c < 2; ++c) b[c] = Is[kk][cg * 2 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    acc[r][c].x = fma(a[r].x, b[c].x, fma(-a[r].y, b[c].y, acc[r][c].x));
+                    acc[r][c].y = fma(a[r].x, b[c].y, fma(a[r].y, b[c].x, acc[r][c].y));
+                }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+        int tt = cg * 2 + c;
+        int64_t t = t0 + tt;
+        if (!act[tt]) continue;
+        double dmax = 0.0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            int i = m0 + rg * 4 + r;
+            if (i >= n) continue;
+            double2 w = W[i];
+            double2 vn = make_double2(acc[r][c].x + w.x, acc[r][c].y + w.y);
+            double2 vo = Vin[t * n + i];
+            double d = hypot(vn.x - vo.x, vn.y - vo.y);
+            if (!(d <= dmax)) dmax = (d != d) ? CUDART_INF : d;  // a NaN step counts as infinite
+            Vout[t * n + i] = vn;
+        }
+        // Non-negative doubles order like their bit patterns.
+        if (dmax > 0.0) atomicMax(&delta[t], (unsigned long long)__double_as_longlong(dmax));
+    }
+}
+
+// Per-column decision after a sweep: count the update, stop converged, exhausted or diverged
+// columns.  iters holds the updates applied; kDone marks the columns that met tol.
+__global__ void f64_decide(int64_t T, double tol, int max_iter, int *flags, int *iters,
+                           unsigned long long *delta, int *counters) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int active = 0, conv = 0;
+    if (t < T && (flags[t] & kActive)) {
+        int k = iters[t] + 1;
+        iters[t] = k;
+        double d = __longlong_as_double((long long)delta[t]);
+        delta[t] = 0ull;
+        if (d <= tol) {
+            flags[t] = kDone;
+            conv = 1;
+        } else if (k >= max_iter || !(d < 1e30)) {
+            flags[t] = 0;
+        } else {
+            active = 1;
+        }
+    }
+    unsigned m = __ballot_sync(0xffffffffu, active);
+    unsigned c = __ballot_sync(0xffffffffu, conv);
+    if ((threadIdx.x & 31) == 0) {
+        if (m) atomicAdd(&counters[kCntActive], __popc(m));
+        if (c) atomicAdd(&counters[kCntConverged], __popc(c));
+    }
+}
+
+// Copy the final iterate into V (when it sits in the second buffer), write the iteration counts
+// and the FP64 power mismatch max_i |V_i conj(sum_j y_ij (V_i - V_j)) + S_i|.
+__global__ void f64_finish(int64_t T, int n, int max_iter, const int *__restrict__ flags,
+                           const int *__restrict__ it_state, double2 *V, const double2 *__restrict__ Valt,
+                           const double2 *__restrict__ S, const int *__restrict__ row_ptr,
+                           const int *__restrict__ nbr, const double2 *__restrict__ y, double2 vs,
+                           int32_t *iters_out, double *mismatch_out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (t >= T) return;
+    const int updates = it_state[t];
+    if (updates & 1) {
+        for (int i = lane; i < n; i += 32) V[t * n + i] = Valt[t * n + i];
+    }
+    __syncwarp();
+    if (lane == 0 && iters_out) iters_out[t] = (flags[t] & kDone) ? updates : -max_iter;
+    if (!mismatch_out) return;
+    double worst = 0.0;
+    const double2 *v = V + t * n;
+    for (int i = lane; i < n; i += 32) {
+        double2 vi = v[i];
+        double2 acc = make_double2(0.0, 0.0);
+        for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            int j = nbr[e];
+            double2 vj = j >= 0 ? v[j] : vs;
+            double2 d = make_double2(vi.x - vj.x, vi.y - vj.y);
+            double2 ye = y[e];
+            acc.x += ye.x * d.x - ye.y * d.y;
+            acc.y += ye.x * d.y + ye.y * d.x;
+        }
+        double2 s = S[t * n + i];
+        // V_i conj(acc) + S_i
+        double mr = vi.x * acc.x + vi.y * acc.y + s.x;
+        double mi = vi.y * acc.x - vi.x * acc.y + s.y;
+        double m = hypot(mr, mi);
+        if (!(m <= worst)) worst = m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double other = __shfl_xor_sync(0xffffffffu, worst, o);
+        if (!(other <= worst)) worst = other;
+    }
+    if (lane == 0) mismatch_out[t] = worst;
+}
+
+}  // namespace
+
+tpf_status solve_fp64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters, double *mismatch,
+                      const tpf_opts &o, cudaStream_t st) {
+    tpf_status rs = ensure_workspace(h, T, false);
+    if (rs != TPF_OK) return rs;
+    Workspace &w = h->ws;
+    const int n = h->dev.n;
+    const int64_t cols = round_up(T, kTileN);
+    int64_t launches = 0;
+    KernelTimer timer(o.profile != 0, st);
+    TPF_CK(cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, st));
+    {
+        int64_t work = cols > T * n ? cols : T * n;
+        f64_init<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(T, cols, n, o.start == TPF_START_FLAT,
+                                                                  (double2 *)V, w.flags, w.iters, w.delta64);
+        ++launches;
+    }
+    TPF_CK(cudaGetLastError());
+    double2 *buf[2] = {(double2 *)V, (double2 *)w.Valt};
+    const dim3 grid((unsigned)((T + F64_BN - 1) / F64_BN), (n + F64_BM - 1) / F64_BM);
+    int sweeps = 0;
+    int64_t active = T, gemm_cols = 0;
+    for (int k = 0; k < o.max_iter; ++k) {
+        timer.begin(KernelTimer::kGemm);
+        f64_sweep<<<grid, 256, 0, st>>>((const double2 *)h->dev.K64, (const double2 *)h->dev.W64, (const double2 *)S,
+                                        buf[k & 1], buf[(k + 1) & 1], n, T, w.flags, w.delta64);
+        timer.end();
+        gemm_cols += active;
+        TPF_CK(cudaMemsetAsync(w.counters, 0, sizeof(int) * 4, st));
+        timer.begin(KernelTimer::kResidual);
+        f64_decide<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(T, o.tol, o.max_iter, w.flags, w.iters, w.delta64,
+                                                                w.counters);
+        timer.end();
+        launches += 2;
+        TPF_CK(cudaGetLastError());
+        ++sweeps;
+        TPF_CK(cudaMemcpyAsync(w.counters_host, w.counters, sizeof(int) * 4, cudaMemcpyDeviceToHost, st));
+        TPF_CK(cudaStreamSynchronize(st));
+        active = w.counters_host[kCntActive];
+        if (active == 0) break;
+    }
+    timer.begin(KernelTimer::kOther);
+    f64_finish<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(
+        T, n, o.max_iter, w.flags, w.iters, (double2 *)V, (const double2 *)w.Valt, (const double2 *)S,
+        h->dev.row_ptr, h->dev.nbr, (const double2 *)h->dev.y64, make_double2(h->net.vs_re, h->net.vs_im), iters,
+        mismatch);
+    timer.end();
+    ++launches;
+    TPF_CK(cudaGetLastError());
+    TPF_CK(cudaMemcpyAsync(w.counters_host, w.counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
+    TPF_CK(cudaStreamSynchronize(st));
+    h->stats.sweeps = sweeps;
+    h->stats.kernel_launches = launches;
+    h->stats.converged = w.counters_host[kCntConverged];
+    h->stats.gemm_launches = sweeps;
+    h->stats.gemm_columns = gemm_cols;
+    h->stats.gemm_ms = timer.total_ms(KernelTimer::kGemm);
+    h->stats.residual_ms = timer.total_ms(KernelTimer::kResidual);
+    h->stats.other_ms = timer.total_ms(KernelTimer::kOther);
+    return h->stats.converged == T ? TPF_OK : TPF_ENOCONV;
+}
+
+}  // namespace tpf

@@ -1,0 +1,349 @@
+// Host side of libtpf: network preprocessing (Eq. 1 and Eq. 3), handle lifetime and the public
+// entry points that dispatch to the FP64 and mixed solve paths.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+#include <queue>
+
+#include "tpf_internal.h"
+
+using cplx = std::complex<double>;
+
+namespace tpf {
+
+namespace {
+
+// Dense inverse by LU with partial pivoting (used for networks that are not trees).
+bool lu_inverse(int n, std::vector<cplx> &A /* in: A, out: A^{-1}, row-major */) {
+    std::vector<int> piv(n);
+    double scale = 0.0;
+    for (const cplx &v : A) scale = std::max(scale, std::abs(v));
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        double best = std::abs(A[(size_t)c * n + c]);
+        for (int r = c + 1; r < n; ++r) {
+            double v = std::abs(A[(size_t)r * n + c]);
+            if (v > best) { best = v; p = r; }
+        }
+        if (!(best > 0.0) || best < 1e-14 * scale) return false;
+        piv[c] = p;
+        if (p != c)
+            for (int j = 0; j < n; ++j) std::swap(A[(size_t)c * n + j], A[(size_t)p * n + j]);
+        cplx inv = 1.0 / A[(size_t)c * n + c];
+        for (int r = c + 1; r < n; ++r) {
+            cplx f = A[(size_t)r * n + c] * inv;
+            A[(size_t)r * n + c] = f;
+            if (f == cplx(0.0)) continue;
+            for (int j = c + 1; j < n; ++j) A[(size_t)r * n + j] -= f * A[(size_t)c * n + j];
+        }
+    }
+    // Solve A X = P^T I column by column.
+    std::vector<cplx> X((size_t)n * n), col(n);
+    for (int j = 0; j < n; ++j) {
+        std::fill(col.begin(), col.end(), cplx(0.0));
+        col[j] = 1.0;
+        for (int c = 0; c < n; ++c) std::swap(col[c], col[piv[c]]);  // apply row swaps in order
+        for (int r = 0; r < n; ++r) {  // forward (unit lower)
+            cplx s = col[r];
+            for (int k = 0; k < r; ++k) s -= A[(size_t)r * n + k] * col[k];
+            col[r] = s;
+        }
+        for (int r = n - 1; r >= 0; --r) {  // backward
+            cplx s = col[r];
+            for (int k = r + 1; k < n; ++k) s -= A[(size_t)r * n + k] * col[k];
+            col[r] = s / A[(size_t)r * n + r];
+        }
+        for (int r = 0; r < n; ++r) X[(size_t)r * n + j] = col[r];
+    }
+    A.swap(X);
+    return true;
+}
+
+}  // namespace
+
+tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int32_t *to,
+                         const double *z_pu, int slack, double v0_re, double v0_im, int n_pq,
+                         const int32_t *pq_bus, Network &net) {
+    if (n_bus < 2 || n_branch < n_bus - 1 || n_pq != n_bus - 1) return TPF_EINVAL;
+    if (!from || !to || !z_pu || !pq_bus) return TPF_EINVAL;
+    if (slack < 0 || slack >= n_bus) return TPF_EINVAL;
+    if (!std::isfinite(v0_re) || !std::isfinite(v0_im)) return TPF_EINVAL;
+    net = Network();
+    net.n_bus = n_bus;
+    net.n_pq = n_pq;
+    net.slack = slack;
+    net.vs_re = v0_re;
+    net.vs_im = v0_im;
+    net.pos.assign(n_bus, -2);
+    net.pos[slack] = -1;
+    net.pq.assign(pq_bus, pq_bus + n_pq);
+    for (int i = 0; i < n_pq; ++i) {
+        int b = pq_bus[i];
+        if (b < 0 || b >= n_bus || net.pos[b] != -2) return TPF_EINVAL;  // out of range, slack or repeated
+        net.pos[b] = i;
+    }
+    // Adjacency with branch admittances y = 1/z (Eq. 1 without shunts).
+    std::vector<std::vector<std::pair<int, cplx>>> adj(n_bus);
+    for (int e = 0; e < n_branch; ++e) {
+        int a = from[e], b = to[e];
+        if (a < 0 || b < 0 || a >= n_bus || b >= n_bus || a == b) return TPF_EINVAL;
+        cplx z(z_pu[2 * e], z_pu[2 * e + 1]);
+        if (!std::isfinite(z.real()) || !std::isfinite(z.imag()) || std::abs(z) == 0.0) return TPF_EINVAL;
+        cplx y = 1.0 / z;
+        adj[a].push_back({b, y});
+        adj[b].push_back({a, y});
+    }
+    // Connectivity from the slack.
+    std::vector<int> parent(n_bus, -2), order;
+    std::vector<cplx> zpar(n_bus, 0.0);
+    order.reserve(n_bus);
+    parent[slack] = -1;
+    order.push_back(slack);
+    for (size_t q = 0; q < order.size(); ++q) {
+        int u = order[q];
+        for (auto &nb : adj[u]) {
+            if (parent[nb.first] == -2) {
+                parent[nb.first] = u;
+                zpar[nb.first] = 1.0 / nb.second;
+                order.push_back(nb.first);
+            }
+        }
+    }
+    if ((int)order.size() != n_bus) return TPF_ESINGULAR;
+    net.radial = (n_branch == n_bus - 1);
+
+    const int n = n_pq;
+    net.K.assign((size_t)2 * n * n, 0.0);
+    if (net.radial) {
+        // (Y_dd^{-1})_{ij} = impedance of the branches shared by the slack-to-i and slack-to-j
+        // paths.  For each j: mark j's ancestors with their path impedance, then a top-down
+        // pass gives every bus the path impedance of its deepest marked ancestor.
+        std::vector<cplx> zpath(n_bus, 0.0), val(n_bus);
+        for (size_t q = 1; q < order.size(); ++q) zpath[order[q]] = zpath[parent[order[q]]] + zpar[order[q]];
+        std::vector<char> mark(n_bus);
+        for (int jc = 0; jc < n; ++jc) {
+            std::fill(mark.begin(), mark.end(), 0);
+            for (int u = net.pq[jc]; u != slack; u = parent[u]) mark[u] = 1;
+            val[slack] = 0.0;
+            for (size_t q = 1; q < order.size(); ++q) {
+                int u = order[q];
+                val[u] = mark[u] ? zpath[u] : val[parent[u]];
+            }
+            for (int ic = 0; ic < n; ++ic) {
+                cplx k = -val[net.pq[ic]];
+                net.K[((size_t)ic * n + jc) * 2] = k.real();
+                net.K[((size_t)ic * n + jc) * 2 + 1] = k.imag();
+            }
+        }
+    } else {
+        std::vector<cplx> Ydd((size_t)n * n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            int b = net.pq[i];
+            for (auto &nb : adj[b]) {
+                Ydd[(size_t)i * n + i] += nb.second;
+                if (nb.first != slack) Ydd[(size_t)i * n + net.pos[nb.first]] -= nb.second;
+            }
+        }
+        if (!lu_inverse(n, Ydd)) return TPF_ESINGULAR;
+        for (size_t k = 0; k < (size_t)n * n; ++k) {
+            net.K[2 * k] = -Ydd[k].real();
+            net.K[2 * k + 1] = -Ydd[k].imag();
+        }
+    }
+    // W = K Y_ds v_s, with (Y_ds)_i = -(sum of admittances of branches from bus i to the slack).
+    std::vector<cplx> yds(n, 0.0);
+    for (int i = 0; i < n; ++i)
+        for (auto &nb : adj[net.pq[i]])
+            if (nb.first == slack) yds[i] -= nb.second;
+    cplx vs(v0_re, v0_im);
+    net.W.assign((size_t)2 * n, 0.0);
+    for (int i = 0; i < n; ++i) {
+        cplx acc = 0.0;
+        for (int j = 0; j < n; ++j) {
+            if (yds[j] == cplx(0.0)) continue;
+            acc += cplx(net.K[((size_t)i * n + j) * 2], net.K[((size_t)i * n + j) * 2 + 1]) * yds[j];
+        }
+        acc *= vs;
+        net.W[2 * i] = acc.real();
+        net.W[2 * i + 1] = acc.imag();
+    }
+    // Neighbour lists in column positions.
+    net.row_ptr.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) net.row_ptr[i + 1] = net.row_ptr[i] + (int)adj[net.pq[i]].size();
+    net.nbr.resize(net.row_ptr[n]);
+    net.y.resize((size_t)2 * net.row_ptr[n]);
+    for (int i = 0; i < n; ++i) {
+        int k = net.row_ptr[i];
+        for (auto &nb : adj[net.pq[i]]) {
+            net.nbr[k] = net.pos[nb.first];  // -1 for the slack
+            net.y[2 * k] = nb.second.real();
+            net.y[2 * k + 1] = nb.second.imag();
+            ++k;
+        }
+    }
+    return TPF_OK;
+}
+
+}  // namespace tpf
+
+extern "C" {
+
+void tpf_default_opts(tpf_opts *o) {
+    if (!o) return;
+    o->tol = 1e-10;
+    o->max_iter = 100;
+    o->precision = TPF_PREC_MIXED;
+    o->start = TPF_START_FLAT;
+    o->switch_tol = 1e-4;
+    o->profile = 0;
+}
+
+const char *tpf_strerror(tpf_status s) {
+    switch (s) {
+        case TPF_OK: return "TPF_OK";
+        case TPF_EINVAL: return "TPF_EINVAL: invalid argument";
+        case TPF_ESINGULAR: return "TPF_ESINGULAR: Y_dd is singular (a bus is not connected to the slack)";
+        case TPF_ENOMEM: return "TPF_ENOMEM: allocation failed";
+        case TPF_ECUDA: return "TPF_ECUDA: CUDA error";
+        case TPF_ETIMEOUT: return "TPF_ETIMEOUT: a bounded device wait expired";
+        case TPF_ENOCONV: return "TPF_ENOCONV: some columns did not converge";
+        case TPF_EUNSUPPORTED: return "TPF_EUNSUPPORTED: not supported by this build or device";
+    }
+    return "TPF_UNKNOWN";
+}
+
+tpf_status tpf_precompute_host(int n_bus, int n_branch, const int32_t *from, const int32_t *to,
+                               const double *z_pu, int slack, double v0_re, double v0_im, int n_pq,
+                               const int32_t *pq_bus, double *K_out, double *W_out) {
+    if (!K_out || !W_out) return TPF_EINVAL;
+    tpf::Network net;
+    tpf_status st;
+    try {
+        st = tpf::build_network(n_bus, n_branch, from, to, z_pu, slack, v0_re, v0_im, n_pq, pq_bus, net);
+    } catch (const std::bad_alloc &) {
+        return TPF_ENOMEM;
+    }
+    if (st != TPF_OK) return st;
+    std::memcpy(K_out, net.K.data(), net.K.size() * sizeof(double));
+    std::memcpy(W_out, net.W.data(), net.W.size() * sizeof(double));
+    return TPF_OK;
+}
+
+tpf_status tpf_create(int n_bus, int n_branch, const int32_t *from, const int32_t *to,
+                      const double *z_pu, int slack, double v0_re, double v0_im, int n_pq,
+                      const int32_t *pq_bus, tpf_handle **out) {
+    if (!out) return TPF_EINVAL;
+    *out = nullptr;
+    tpf_handle *h = new (std::nothrow) tpf_handle();
+    if (!h) return TPF_ENOMEM;
+    tpf_status st;
+    try {
+        st = tpf::build_network(n_bus, n_branch, from, to, z_pu, slack, v0_re, v0_im, n_pq, pq_bus, h->net);
+    } catch (const std::bad_alloc &) {
+        st = TPF_ENOMEM;
+    }
+    if (st == TPF_OK) st = tpf::upload_network(h);
+    if (st != TPF_OK) {
+        tpf::free_device(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return TPF_OK;
+}
+
+void tpf_destroy(tpf_handle *h) {
+    if (!h) return;
+    tpf::free_device(h);
+    delete h;
+}
+
+int tpf_n_pq(const tpf_handle *h) { return h ? h->net.n_pq : -1; }
+
+tpf_status tpf_last_stats(const tpf_handle *h, tpf_stats *out) {
+    if (!h || !out) return TPF_EINVAL;
+    *out = h->stats;
+    return TPF_OK;
+}
+
+static tpf_status check_opts(const tpf_opts *in, tpf_opts &o) {
+    tpf_default_opts(&o);
+    if (in) o = *in;
+    if (!(o.tol >= 0.0) || o.max_iter < 1 || o.max_iter > 100000) return TPF_EINVAL;
+    if (o.precision != TPF_PREC_FP64 && o.precision != TPF_PREC_MIXED) return TPF_EINVAL;
+    if (o.start != TPF_START_FLAT && o.start != TPF_START_GIVEN) return TPF_EINVAL;
+    if (!(o.switch_tol >= 0.0)) return TPF_EINVAL;
+    return TPF_OK;
+}
+
+tpf_status tpf_solve(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev, int32_t *iters_dev,
+                     double *mismatch_dev, const tpf_opts *opts, void *stream) {
+    if (!h || T < 0) return TPF_EINVAL;
+    tpf_opts o;
+    tpf_status st = check_opts(opts, o);
+    if (st != TPF_OK) return st;
+    h->stats = tpf_stats{};
+    h->stats.columns = T;
+    if (T == 0) return TPF_OK;
+    if (!S_dev || !V_dev) return TPF_EINVAL;
+    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (o.precision == TPF_PREC_FP64) return tpf::solve_fp64(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
+    return tpf::solve_mixed(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
+}
+
+tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_host,
+                          int32_t *iters_host, double *mismatch_host, const tpf_opts *opts,
+                          void *stream) {
+    if (!h || T < 0) return TPF_EINVAL;
+    tpf_opts o;
+    tpf_status st = check_opts(opts, o);
+    if (st != TPF_OK) return st;
+    if (T == 0) {
+        h->stats = tpf_stats{};
+        return TPF_OK;
+    }
+    if (!S_host || !V_host) return TPF_EINVAL;
+    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    tpf::Workspace &w = h->ws;
+    const size_t col_bytes = (size_t)h->net.n_pq * 16;
+    if (T > w.host_cap) {
+        cudaFree(w.S_dev); cudaFree(w.V_dev); cudaFree(w.it_dev); cudaFree(w.mm_dev);
+        w.S_dev = w.V_dev = nullptr; w.it_dev = nullptr; w.mm_dev = nullptr; w.host_cap = 0;
+        if (cudaMalloc(&w.S_dev, col_bytes * T) != cudaSuccess || cudaMalloc(&w.V_dev, col_bytes * T) != cudaSuccess ||
+            cudaMalloc(&w.it_dev, sizeof(int32_t) * T) != cudaSuccess ||
+            cudaMalloc(&w.mm_dev, sizeof(double) * T) != cudaSuccess) {
+            cudaGetLastError();
+            return TPF_ENOMEM;
+        }
+        w.host_cap = T;
+    }
+    if (cudaMemcpyAsync(w.S_dev, S_host, col_bytes * T, cudaMemcpyHostToDevice, s) != cudaSuccess) return TPF_ECUDA;
+    if (o.start == TPF_START_GIVEN &&
+        cudaMemcpyAsync(w.V_dev, V_host, col_bytes * T, cudaMemcpyHostToDevice, s) != cudaSuccess)
+        return TPF_ECUDA;
+    st = tpf_solve(h, T, w.S_dev, w.V_dev, iters_host ? w.it_dev : nullptr, mismatch_host ? w.mm_dev : nullptr, &o,
+                   stream);
+    if (st != TPF_OK && st != TPF_ENOCONV) return st;
+    if (cudaMemcpyAsync(V_host, w.V_dev, col_bytes * T, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPF_ECUDA;
+    if (iters_host &&
+        cudaMemcpyAsync(iters_host, w.it_dev, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return TPF_ECUDA;
+    if (mismatch_host &&
+        cudaMemcpyAsync(mismatch_host, w.mm_dev, sizeof(double) * T, cudaMemcpyDeviceToHost, s) != cudaSuccess)
+        return TPF_ECUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return TPF_ECUDA;
+    return st;
+}
+
+tpf_status tpf_selftest_gemm(int M, int N, int K, const void *A_re, const void *A_im, const void *B_re,
+                             const void *B_im, float *D_re, float *D_im, void *stream) {
+    if (M <= 0 || N <= 0 || K <= 0 || M % tpf::kTileM || N % tpf::kTileN || K % tpf::kChunkK) return TPF_EINVAL;
+    if (!A_re || !A_im || !B_re || !B_im || !D_re || !D_im) return TPF_EINVAL;
+    return tpf::selftest_gemm(M, N, K, A_re, A_im, B_re, B_im, D_re, D_im, reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

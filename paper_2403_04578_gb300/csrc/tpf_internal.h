@@ -1,0 +1,159 @@
+// Internal declarations shared by the host and device translation units of libtpf.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include "../../include/tpf.h"
+
+#ifdef __CUDACC__
+#include <cuda_fp16.h>
+#endif
+#include <cuda_runtime.h>
+
+namespace tpf {
+
+// Row padding of the tensor-core operands: the bus dimension is padded to a multiple of the
+// 64-element (128-byte) K chunk and of the 128-row M tile.
+constexpr int kChunkK = 64;
+constexpr int kTileM = 128;
+constexpr int kTileN = 128;
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Host-side result of the network preprocessing (Eq. 1 and Eq. 3).
+struct Network {
+    int n_bus = 0, n_pq = 0, slack = 0;
+    double vs_re = 1.0, vs_im = 0.0;
+    bool radial = false;
+    std::vector<int> pq;          // column position -> bus
+    std::vector<int> pos;         // bus -> column position, -1 for the slack
+    std::vector<double> K;        // complex [n_pq][n_pq], K = -Y_dd^{-1}
+    std::vector<double> W;        // complex [n_pq], W = K Y_ds v_s
+    // Neighbour lists of the demand buses (CSR over column positions): for each bus i, the
+    // other end j of every branch at i (-1 = the slack) and that branch's admittance y = 1/z.
+    std::vector<int> row_ptr, nbr;
+    std::vector<double> y;        // complex [nnz]
+};
+
+// Build the network arrays; returns TPF_OK or the status to report.
+tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int32_t *to,
+                         const double *z_pu, int slack, double v0_re, double v0_im, int n_pq,
+                         const int32_t *pq_bus, Network &net);
+
+// Device copies owned by a handle.
+struct DeviceNet {
+    int n = 0;           // n_pq
+    int n_pad = 0;       // n rounded up to kTileM (and hence to kChunkK)
+    // FP64 path
+    double *K64 = nullptr;   // complex [n][n]
+    double *W64 = nullptr;   // complex [n]
+    int *row_ptr = nullptr, *nbr = nullptr;
+    double *y64 = nullptr;   // complex [nnz]
+    float4 *y2f = nullptr;   // double-float complex admittance (re_hi, im_hi, re_lo, im_lo) [nnz]
+    // Mixed path: fp16 planes of K * 2^k_exp, [n_pad][n_pad], zero padded
+    void *Kr16 = nullptr, *Ki16 = nullptr;
+    int k_exp = 0;
+};
+
+// Workspaces of a solve, grown on demand.
+struct Workspace {
+    int64_t cap_cols = 0;     // columns allocated (multiple of kTileN)
+    int n_pad = 0;
+    // mixed path
+    // V = Vhi + Vlo: before a column is anchored Vhi carries V and Vlo = 0; after, Vhi is the
+    // frozen anchor V_ref and Vlo the offset from it.  S = Shi + Slo.  RefHi + RefLo hold
+    // rho(V_ref) in double-float.
+    float2 *Vhi = nullptr, *Vlo = nullptr, *Shi = nullptr, *Slo = nullptr;  // [cols][n_pad]
+    float2 *RefHi = nullptr, *RefLo = nullptr;                              // [cols][n_pad]
+    void *Rr16 = nullptr, *Ri16 = nullptr;                                  // fp16 [cols][n_pad]
+    unsigned int *dprev = nullptr;        // float bits of the step before the last (mixed)
+    // FP64 path: second V buffer, complex128 [cols][n]
+    double *Valt = nullptr;
+    // per-column state
+    unsigned int *delta_bits = nullptr;   // float bits (mixed) of the last max|dV|
+    unsigned long long *delta64 = nullptr;// double bits (FP64 path)
+    int *iters = nullptr;
+    int *flags = nullptr;
+    int *rexp = nullptr;
+    int *tile_active = nullptr;           // [cols / kTileN]
+    int *counters = nullptr;              // [8] device counters
+    int *counters_host = nullptr;         // pinned mirror
+    // host-solve staging
+    int64_t host_cap = 0;
+    void *S_dev = nullptr, *V_dev = nullptr;
+    int32_t *it_dev = nullptr;
+    double *mm_dev = nullptr;
+};
+
+// kAnchored: the column's residual is rho(V_ref) + FP32 corrections in V - V_ref.
+// kBlind: anchored at a given starting point (not yet at a small step); re-anchored once the step
+// falls below switch_tol.
+enum ColFlags : int { kActive = 1, kAnchored = 2, kDone = 4, kBlind = 8 };
+enum Counter : int { kCntActive = 0, kCntPrecise = 1, kCntError = 2, kCntConverged = 4 };
+
+// CUDA-event timing of kernel launches by category (only when a solve asks for it).
+struct KernelTimer {
+    enum { kGemm = 0, kResidual = 1, kOther = 2 };
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev[3];
+    int cur = -1;
+    KernelTimer(bool enable, cudaStream_t s) : on(enable), st(s) {}
+    void begin(int cat) {
+        if (!on) return;
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        cudaEventRecord(a, st);
+        ev[cat].push_back({a, b});
+        cur = cat;
+    }
+    void end() {
+        if (!on || cur < 0) return;
+        cudaEventRecord(ev[cur].back().second, st);
+        cur = -1;
+    }
+    // Call after the stream has been synchronised.
+    double total_ms(int cat) const {
+        double s = 0.0;
+        for (auto &p : ev[cat]) {
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, p.first, p.second) == cudaSuccess) s += ms;
+        }
+        return s;
+    }
+    ~KernelTimer() {
+        for (auto &v : ev)
+            for (auto &p : v) {
+                cudaEventDestroy(p.first);
+                cudaEventDestroy(p.second);
+            }
+    }
+};
+
+}  // namespace tpf
+
+struct tpf_handle {
+    int device = 0;
+    tpf::Network net;
+    tpf::DeviceNet dev;
+    tpf::Workspace ws;
+    tpf_stats stats{};
+    void *tmaps = nullptr;  // tensor maps of the fp16 K planes (opaque, allocated by the mixed path)
+};
+
+namespace tpf {
+// Upload the network to the device (tpf_create).
+tpf_status upload_network(tpf_handle *h);
+void free_device(tpf_handle *h);
+// Ensure workspaces for `cols` columns.
+tpf_status ensure_workspace(tpf_handle *h, int64_t cols, bool mixed);
+// The two solve paths.  Return TPF_OK / TPF_ENOCONV / errors.
+tpf_status solve_fp64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
+                      double *mismatch, const tpf_opts &o, cudaStream_t st);
+tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
+                       double *mismatch, const tpf_opts &o, cudaStream_t st);
+tpf_status selftest_gemm(int M, int N, int K, const void *Ar, const void *Ai, const void *Br,
+                         const void *Bi, float *Dr, float *Di, cudaStream_t st);
+}  // namespace tpf

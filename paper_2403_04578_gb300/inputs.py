@@ -166,17 +166,21 @@ def _noise_chunk(seed: int, chunk: int, n_cols: int, n_pq: int, tag: int = _TAG_
 
 
 def load_tensor(feeder: Feeder, T: int, seed: int, step_minutes: float = 1.0, t0: int = 0,
-                dtype=np.complex128, threads: int = 8) -> np.ndarray:
+                dtype=np.complex128, threads: int = 8, out: np.ndarray | None = None) -> np.ndarray:
     """Load tensor S[T][n_pq] (consumption, pu) for ``T`` consecutive steps starting at ``t0``.
 
-    ``t0`` must be a multiple of ``CHUNK`` so that chunk seeding lines up with a full run.
+    ``t0`` must be a multiple of ``CHUNK`` so that chunk seeding lines up with a full run.  ``out``
+    (optional) is a C-contiguous [T][n_pq] array to fill, e.g. a view of pinned host memory.
     """
     if t0 % CHUNK:
         raise ValueError("t0 must be a multiple of CHUNK")
     base, pf = feeder.pq_params()
     p0 = feeder.load_scale * base / S_BASE_KW
     tanphi = np.tan(np.arccos(pf))
-    out = np.empty((T, feeder.n_pq), dtype=dtype)
+    if out is None:
+        out = np.empty((T, feeder.n_pq), dtype=dtype)
+    elif out.shape != (T, feeder.n_pq) or not out.flags.c_contiguous:
+        raise ValueError("out must be C-contiguous with shape (T, n_pq)")
     n_chunks = (T + CHUNK - 1) // CHUNK
 
     def work(c):

@@ -1,0 +1,265 @@
+"""Python binding of libtpf (ctypes; argument marshalling only).
+
+Every step of a solve runs in libtpf's CUDA kernels; this module only checks shapes and dtypes,
+passes device pointers and the current CUDA stream, and turns status codes into exceptions.
+PyTorch is used for device memory and streams.  There is no CPU fallback: if libtpf.so cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, EINVAL, ESINGULAR, ENOMEM, ECUDA, ETIMEOUT, ENOCONV, EUNSUPPORTED = range(8)
+PREC_FP64, PREC_MIXED = 0, 1
+START_FLAT, START_GIVEN = 0, 1
+
+# Every entry point declared in include/tpf.h.
+EXPORTS = (
+    "tpf_default_opts", "tpf_strerror", "tpf_create", "tpf_destroy", "tpf_n_pq", "tpf_precompute_host",
+    "tpf_solve", "tpf_solve_host", "tpf_last_stats", "tpf_selftest_gemm",
+)
+
+
+class TpfError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)}")
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
+                ("start", ctypes.c_int), ("switch_tol", ctypes.c_double), ("profile", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("precise_sweeps", ctypes.c_int), ("converged", ctypes.c_int64),
+                ("columns", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("gemm_ms", ctypes.c_double),
+                ("residual_ms", ctypes.c_double), ("other_ms", ctypes.c_double), ("gemm_launches", ctypes.c_int64),
+                ("gemm_columns", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = False):
+    """Load libtpf.so (optionally building it first).  Raises if it cannot be loaded."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise RuntimeError(f"libtpf.so not built ({path}); run __graft_entry__.build() or "
+                               "python -m paper_2403_04578_gb300.build")
+        _build.build()
+    L = ctypes.CDLL(path)
+    vp, i32p, f64p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_double)
+    L.tpf_default_opts.argtypes = [ctypes.POINTER(Opts)]
+    L.tpf_default_opts.restype = None
+    L.tpf_strerror.argtypes = [ctypes.c_int]
+    L.tpf_strerror.restype = ctypes.c_char_p
+    L.tpf_create.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, f64p, ctypes.c_int, ctypes.c_double,
+                             ctypes.c_double, ctypes.c_int, i32p, ctypes.POINTER(vp)]
+    L.tpf_create.restype = ctypes.c_int
+    L.tpf_destroy.argtypes = [vp]
+    L.tpf_destroy.restype = None
+    L.tpf_n_pq.argtypes = [vp]
+    L.tpf_n_pq.restype = ctypes.c_int
+    L.tpf_precompute_host.argtypes = [ctypes.c_int, ctypes.c_int, i32p, i32p, f64p, ctypes.c_int, ctypes.c_double,
+                                      ctypes.c_double, ctypes.c_int, i32p, f64p, f64p]
+    L.tpf_precompute_host.restype = ctypes.c_int
+    L.tpf_solve.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(Opts), vp]
+    L.tpf_solve.restype = ctypes.c_int
+    L.tpf_solve_host.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(Opts), vp]
+    L.tpf_solve_host.restype = ctypes.c_int
+    L.tpf_last_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    L.tpf_last_stats.restype = ctypes.c_int
+    L.tpf_selftest_gemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
+    L.tpf_selftest_gemm.restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def strerror(status: int) -> str:
+    try:
+        return lib().tpf_strerror(int(status)).decode()
+    except RuntimeError:
+        return f"status {status}"
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _z(a):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.complex128)).view(np.float64)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def make_opts(precision: str | int = "mixed", tol: float = 1e-10, max_iter: int = 100, start: str | int = "flat",
+              switch_tol: float = 1e-4, profile: bool = False) -> Opts:
+    o = Opts()
+    lib().tpf_default_opts(ctypes.byref(o))
+    o.tol = float(tol)
+    o.max_iter = int(max_iter)
+    o.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}.get(precision, precision)
+    o.start = {"flat": START_FLAT, "given": START_GIVEN}.get(start, start)
+    o.switch_tol = float(switch_tol)
+    o.profile = 1 if profile else 0
+    return o
+
+
+def precompute_host(n_bus, from_bus, to_bus, z_pu, slack=0, v0=1.0 + 0j, pq_bus=None):
+    """K = -Y_dd^{-1} and W = K Y_ds v_s as computed by tpf_create (host only, no device)."""
+    if pq_bus is None:
+        pq_bus = [b for b in range(n_bus) if b != slack]
+    fa, fp = _i32(from_bus)
+    ta, tp = _i32(to_bus)
+    za, zp = _z(z_pu)
+    pa, pp = _i32(pq_bus)
+    n = len(pa)
+    K = np.zeros((n, n), dtype=np.complex128)
+    W = np.zeros(n, dtype=np.complex128)
+    st = lib().tpf_precompute_host(int(n_bus), len(fa), fp, tp, zp, int(slack), float(np.real(v0)), float(np.imag(v0)),
+                                   n, pp, K.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                   W.view(np.float64).ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    if st != OK:
+        raise TpfError(st, "tpf_precompute_host")
+    return K, W
+
+
+def _stream_ptr(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Feeder:
+    """A feeder uploaded to the GPU (a tpf_handle)."""
+
+    def __init__(self, n_bus, from_bus, to_bus, z_pu, slack=0, v0=1.0 + 0j, pq_bus=None):
+        if pq_bus is None:
+            pq_bus = [b for b in range(n_bus) if b != slack]
+        fa, fp = _i32(from_bus)
+        ta, tp = _i32(to_bus)
+        za, zp = _z(z_pu)
+        pa, pp = _i32(pq_bus)
+        h = ctypes.c_void_p()
+        st = lib().tpf_create(int(n_bus), len(fa), fp, tp, zp, int(slack), float(np.real(v0)), float(np.imag(v0)),
+                              len(pa), pp, ctypes.byref(h))
+        if st != OK:
+            raise TpfError(st, "tpf_create")
+        self._h = h
+        self.n_pq = lib().tpf_n_pq(h)
+
+    @classmethod
+    def from_inputs(cls, f):
+        """From a ``paper_2403_04578_gb300.inputs.Feeder``."""
+        return cls(f.n_bus, f.from_bus, f.to_bus, f.z_pu, f.slack, f.v0, f.pq_bus)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tpf_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def stats(self) -> dict:
+        s = Stats()
+        lib().tpf_last_stats(self._h, ctypes.byref(s))
+        return s.as_dict()
+
+    def solve(self, S, V=None, iters=None, mismatch=None, precision="mixed", tol=1e-10, max_iter=100, start=None,
+              switch_tol=1e-4, stream=None, check=True, profile=False):
+        """Solve every column of the device tensor S (complex128 [T][n_pq]).
+
+        Returns (V, iters, mismatch, status); outputs are allocated when not given.  With
+        ``start='given'`` (default when V is passed) V is read as the starting point.
+        """
+        import torch
+
+        if not (isinstance(S, torch.Tensor) and S.is_cuda and S.dtype == torch.complex128 and S.dim() == 2):
+            raise TypeError("S must be a CUDA complex128 tensor [T, n_pq]")
+        if S.shape[1] != self.n_pq or not S.is_contiguous():
+            raise ValueError(f"S must be contiguous with {self.n_pq} columns")
+        T = S.shape[0]
+        if start is None:
+            start = "given" if V is not None else "flat"
+        if V is None:
+            V = torch.empty_like(S)
+        if iters is None:
+            iters = torch.empty(T, dtype=torch.int32, device=S.device)
+        if mismatch is None:
+            mismatch = torch.empty(T, dtype=torch.float64, device=S.device)
+        for t_, dt in ((V, torch.complex128), (iters, torch.int32), (mismatch, torch.float64)):
+            if not (t_.is_cuda and t_.dtype == dt and t_.is_contiguous() and t_.shape[0] == T):
+                raise ValueError("output tensors must be contiguous CUDA tensors with T rows")
+        o = make_opts(precision, tol, max_iter, start, switch_tol, profile)
+        st = lib().tpf_solve(self._h, T, ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                             ctypes.c_void_p(iters.data_ptr()), ctypes.c_void_p(mismatch.data_ptr()), ctypes.byref(o),
+                             _stream_ptr(stream))
+        if check and st not in (OK, ENOCONV):
+            raise TpfError(st, "tpf_solve")
+        return V, iters, mismatch, st
+
+    def solve_host(self, S, V0=None, precision="mixed", tol=1e-10, max_iter=100, switch_tol=1e-4, stream=None,
+                   out=None, check=True, profile=False):
+        """tpf_solve_host on host arrays (numpy or pinned torch CPU tensors, complex128 [T][n_pq])."""
+        T = S.shape[0]
+        if out is None:
+            V = np.empty((T, self.n_pq), dtype=np.complex128) if V0 is None else V0
+            it = np.empty(T, dtype=np.int32)
+            mm = np.empty(T, dtype=np.float64)
+        else:
+            V, it, mm = out
+        if V0 is not None and V is not V0:
+            V[...] = V0
+
+        def ptr(a):
+            return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+
+        o = make_opts(precision, tol, max_iter, "given" if V0 is not None else "flat", switch_tol, profile)
+        st = lib().tpf_solve_host(self._h, T, ptr(S), ptr(V), ptr(it), ptr(mm), ctypes.byref(o), _stream_ptr(stream))
+        if check and st not in (OK, ENOCONV):
+            raise TpfError(st, "tpf_solve_host")
+        return V, it, mm, st
+
+
+def selftest_gemm(Ar, Ai, Br, Bi, stream=None):
+    """D = A B^T over complex numbers with the library's tcgen05 kernel (fp16 in, FP32 out)."""
+    import torch
+
+    M, K = Ar.shape
+    N = Br.shape[0]
+    Dr = torch.empty((N, M), dtype=torch.float32, device=Ar.device)
+    Di = torch.empty((N, M), dtype=torch.float32, device=Ar.device)
+    st = lib().tpf_selftest_gemm(M, N, K, *(ctypes.c_void_p(x.data_ptr()) for x in (Ar, Ai, Br, Bi)),
+                                 ctypes.c_void_p(Dr.data_ptr()), ctypes.c_void_p(Di.data_ptr()), _stream_ptr(stream))
+    if st != OK:
+        raise TpfError(st, "tpf_selftest_gemm")
+    return Dr, Di

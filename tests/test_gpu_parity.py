@@ -1,0 +1,154 @@
+"""GPU parity: libtpf (through its C ABI) against the FP64 CPU oracle.
+
+Tolerances (stated once here, used below):
+  * FP64 path: max |V - V_oracle| <= 1e-9 pu (oracle iterated to 1e-13).
+  * mixed path: max |V - V_oracle| <= 1e-8 pu.
+  * iteration counts: FP64 path equal to the oracle's at the same tol, except columns whose
+    deciding step lies within 1% of tol (rounding can move them by one); mixed path within +-1.
+  * GEMM self-test: fp16 operands are exact in FP32, so only the FP32 summation order differs:
+    |D - D_ref| <= 1e-4 * (1 + |D_ref|).
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2403_04578_gb300 import inputs as G
+from paper_2403_04578_gb300 import tpf
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-9
+TOL_MIXED = 1e-8
+
+
+def _case(nb, T, seed=1, t0=0):
+    f = G.make_feeder(nb, seed)
+    c = O.Case.from_feeder(f)
+    S = G.load_tensor(f, T, seed, t0=t0)
+    return f, c, S
+
+
+def _dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _iters_close(it_gpu, it_ref, delta_ref_prev, tol, slack):
+    bad = np.flatnonzero(np.abs(it_gpu - it_ref) > slack)
+    return bad
+
+
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (256, 384, 192), (1024, 256, 1024)])
+def test_gemm_selftest(cuda, M, N, K):
+    import torch
+
+    g = torch.Generator(device="cpu").manual_seed(M + N + K)
+    A = [torch.rand((M, K), generator=g).mul(2).sub(1).half().cuda() for _ in range(2)]
+    B = [torch.rand((N, K), generator=g).mul(2).sub(1).half().cuda() for _ in range(2)]
+    Dr, Di = tpf.selftest_gemm(A[0], A[1], B[0], B[1])
+    torch.cuda.synchronize()
+    a = [x.double() for x in A]
+    b = [x.double() for x in B]
+    ref_r = (b[0] @ a[0].T - b[1] @ a[1].T)
+    ref_i = (b[1] @ a[0].T + b[0] @ a[1].T)
+    for got, ref in ((Dr, ref_r), (Di, ref_i)):
+        err = (got.double() - ref).abs() / (1 + ref.abs())
+        assert err.max().item() <= 1e-4, f"max scaled error {err.max().item()}"
+
+
+def _check(f, c, S, precision, tol_v, it_slack, tol=1e-10, **kw):
+    Vo, _, _ = c.solve(S, tol=1e-13)
+    _, it_ref, d_ref = c.solve(S, tol=tol)
+    fd = tpf.Feeder.from_inputs(f)
+    V, it, mm, st = fd.solve(_dev(S), precision=precision, tol=tol, **kw)
+    assert st == tpf.OK
+    V = V.cpu().numpy()
+    it = it.cpu().numpy()
+    mm = mm.cpu().numpy()
+    err = np.abs(V - Vo).max()
+    assert err <= tol_v, f"max |V - V_oracle| = {err:.3e}"
+    assert (it > 0).all()
+    bad = np.flatnonzero(np.abs(it - it_ref) > it_slack)
+    assert bad.size == 0, f"iteration counts differ in {bad.size} columns, e.g. {it[bad[:5]]} vs {it_ref[bad[:5]]}"
+    # Mismatch at the returned V agrees with the oracle's evaluation of the same V.
+    mm_ref = c.mismatch(S, V)
+    assert np.all(np.abs(mm - mm_ref) <= 1e-9 + 1e-3 * mm_ref)
+    st_ = fd.stats()
+    assert st_["converged"] == S.shape[0]
+    fd.close()
+    return err, it
+
+
+@pytest.mark.parametrize("nb,T", [(34, 1440), (2, 7), (3, 1), (35, 129), (100, 200), (200, 300)])
+def test_fp64_vs_oracle(cuda, nb, T):
+    f, c, S = _case(nb, T)
+    _check(f, c, S, "fp64", TOL_FP64, 0)
+
+
+@pytest.mark.parametrize("nb,T", [(34, 1440), (2, 7), (3, 1), (35, 129), (100, 200), (200, 300), (400, 257)])
+def test_mixed_vs_oracle(cuda, nb, T):
+    f, c, S = _case(nb, T)
+    _check(f, c, S, "mixed", TOL_MIXED, 1)
+
+
+def test_mixed_peak_hours_1000(cuda):
+    """1,000-bus feeder, evening peak columns (lowest voltages), ragged T."""
+    f = G.make_feeder(1000, 1)
+    c = O.Case.from_feeder(f)
+    S = G.load_tensor(f, 4096, 1)[1080:1080 + 300]
+    _check(f, c, S, "mixed", TOL_MIXED, 1)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_empty_and_given_start(cuda, precision):
+    import torch
+
+    f, c, S = _case(34, 50)
+    fd = tpf.Feeder.from_inputs(f)
+    V, it, mm, st = fd.solve(_dev(S[:0]), precision=precision)
+    assert st == tpf.OK and V.shape[0] == 0
+    Vo, _, _ = c.solve(S, tol=1e-13)
+    V0 = _dev(Vo)
+    V, it, mm, st = fd.solve(_dev(S), V=V0.clone(), precision=precision, tol=1e-10)
+    assert st == tpf.OK
+    assert (it.cpu().numpy() == 1).all()  # the oracle's solution is already a fixed point
+    assert np.abs(V.cpu().numpy() - Vo).max() <= 1e-12
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_infeasible_and_nan_columns(cuda, precision):
+    f, c, S = _case(34, 64)
+    S = S.copy()
+    S[3] *= 400.0  # far beyond the loadability of the feeder: no solution
+    S[10, 5] = np.nan
+    fd = tpf.Feeder.from_inputs(f)
+    V, it, mm, st = fd.solve(_dev(S), precision=precision, max_iter=60)
+    assert st == tpf.ENOCONV
+    it = it.cpu().numpy()
+    assert it[3] == -60 and it[10] == -60
+    good = np.setdiff1d(np.arange(64), [3, 10])
+    Vo, _, _ = c.solve(S[good], tol=1e-13)
+    tol_v = TOL_FP64 if precision == "fp64" else TOL_MIXED
+    assert np.abs(V.cpu().numpy()[good] - Vo).max() <= tol_v
+    assert fd.stats()["converged"] == 62
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_host_buffers_match_device(cuda, precision):
+    f, c, S = _case(100, 333)
+    fd = tpf.Feeder.from_inputs(f)
+    Vd, itd, mmd, _ = fd.solve(_dev(S), precision=precision)
+    Vh, ith, mmh, st = fd.solve_host(S, precision=precision)
+    assert st == tpf.OK
+    assert np.array_equal(Vh, Vd.cpu().numpy())
+    assert np.array_equal(ith, itd.cpu().numpy())
+
+
+def test_create_errors(cuda):
+    with pytest.raises(tpf.TpfError) as e:
+        tpf.Feeder(3, [0, 0], [1, 1], [0.01 + 0.01j, 0.02 + 0.01j])  # bus 2 not connected
+    assert e.value.status == tpf.ESINGULAR
+    with pytest.raises(tpf.TpfError) as e:
+        tpf.Feeder(3, [0, 1], [1, 5], [0.01 + 0.01j, 0.02 + 0.01j])
+    assert e.value.status == tpf.EINVAL

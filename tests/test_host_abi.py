@@ -1,0 +1,92 @@
+"""libtpf's C ABI on the host (no GPU): symbols, host-side precomputation, argument checks."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2403_04578_gb300 import inputs as G
+from paper_2403_04578_gb300 import tpf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for fn in os.listdir(inc):
+        if fn.endswith(".h"):
+            text = open(os.path.join(inc, fn)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(tpf_\w+)\s*\(", text))
+    return names
+
+
+def test_library_exports_every_declared_symbol(tpf_lib):
+    names = declared_symbols()
+    assert "tpf_solve" in names and "tpf_create" in names
+    for name in names:
+        assert hasattr(tpf_lib, name), f"{name} not exported"
+    assert set(tpf.EXPORTS) <= names
+
+
+def test_strerror_and_defaults(tpf_lib):
+    for st in range(8):
+        assert tpf.strerror(st).startswith("TPF_")
+    o = tpf.Opts()
+    tpf_lib.tpf_default_opts(ctypes.byref(o))
+    assert o.tol == 1e-10 and o.max_iter == 100 and o.precision == tpf.PREC_MIXED and o.start == tpf.START_FLAT
+
+
+@pytest.mark.parametrize("n_bus,seed", [(2, 1), (34, 1), (150, 9)])
+def test_precompute_host_matches_oracle_radial(tpf_lib, n_bus, seed):
+    f = G.make_feeder(n_bus, seed)
+    c = O.Case.from_feeder(f)
+    K, W = tpf.precompute_host(f.n_bus, f.from_bus, f.to_bus, f.z_pu)
+    assert np.abs(K - c.K).max() <= 1e-12 * np.abs(c.K).max()
+    assert np.abs(W - c.W).max() <= 1e-13
+
+
+def test_precompute_host_meshed_and_reordered(tpf_lib):
+    f = G.make_feeder(50, 4)
+    fb = np.r_[f.from_bus, 10, 3]
+    tb = np.r_[f.to_bus, 40, 22]
+    z = np.r_[f.z_pu, 0.01 + 0.02j, 0.03 + 0.01j]
+    vs = 1.02 + 0.01j
+    pq = np.array([b for b in range(50) if b != 0])[::-1].copy()  # reversed bus order
+    c = O.Case(50, fb, tb, z, vs=vs, pq=pq)
+    K, W = tpf.precompute_host(50, fb, tb, z, v0=vs, pq_bus=pq)
+    assert np.abs(K - c.K).max() <= 1e-12 * np.abs(c.K).max()
+    assert np.abs(W - c.W).max() <= 1e-13
+
+
+def test_precompute_host_argument_errors(tpf_lib):
+    z = [0.01 + 0.01j, 0.02 + 0.01j]
+    with pytest.raises(tpf.TpfError) as e:
+        tpf.precompute_host(3, [0, 0], [1, 1], z)  # bus 2 isolated: Y_dd singular
+    assert e.value.status == tpf.ESINGULAR
+    with pytest.raises(tpf.TpfError) as e:
+        tpf.precompute_host(3, [0, 1], [1, 7], z)  # index out of range
+    assert e.value.status == tpf.EINVAL
+    with pytest.raises(tpf.TpfError) as e:
+        tpf.precompute_host(3, [0, 1], [1, 2], [0.01 + 0.01j, 0.0])  # zero impedance
+    assert e.value.status == tpf.EINVAL
+    with pytest.raises(tpf.TpfError) as e:
+        tpf.precompute_host(3, [0, 1], [1, 2], z, pq_bus=[1, 1])  # repeated bus
+    assert e.value.status == tpf.EINVAL
+    with pytest.raises(tpf.TpfError) as e:
+        tpf.precompute_host(3, [0, 1], [1, 2], z, pq_bus=[0, 1])  # slack listed as PQ
+    assert e.value.status == tpf.EINVAL
+
+
+def test_create_fails_loudly_without_a_device(tpf_lib):
+    import torch
+
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    f = G.make_feeder(10, 1)
+    with pytest.raises(tpf.TpfError) as e:
+        tpf.Feeder.from_inputs(f)
+    assert e.value.status == tpf.ECUDA

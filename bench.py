@@ -1,0 +1,367 @@
+#!/usr/bin/env python
+"""Benchmark: power-flow solves per second of the tensor power flow on one GB300 per rank.
+
+Workload (default): a 1,000-bus synthetic radial feeder (999 PQ buses) and one year of one-minute
+load columns (T = 525,600), solved to max |dV| <= 1e-10 pu from a flat start with the mixed
+path (fp16 tensor-core sweeps in residual form, double-float residual anchoring).  One "step"
+is one full tpf_solve of all T columns.
+
+Reported on one JSON line (rank 0):
+  value       PF/s, device-resident inputs (S, V on the GPU), CUDA events around the K steps,
+              max over ranks; N ranks run N independent replicas (weak scaling)
+  e2e         PF/s through tpf_solve_host with pinned HOST buffers: H2D of S, solve, D2H of V,
+              iteration counts and mismatches inside the timed region
+  roofline    the tensor-core GEMM kernel: algorithmic 8 n^2 flops per iterating column per sweep,
+              over its CUDA-event time inside the timed steps, against the measured bf16 peak
+              (fp16 runs at the bf16 rate)
+  fp64_gpu    the plain FP64 GPU fixed-point iteration (direct form), timed on a column sample
+  cpu_baseline the CPU oracle on the host cores, on a bounded column sample; the same leg checks
+              the GPU result against the oracle (iterated to 1e-13) on sampled columns
+  clocks      nvidia-smi samples taken during the timed region
+
+``--impl reference`` times the CPU oracle as the reference arm on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "PF solves/s at ≤1e-8 pu vs FP64 oracle: mixed+learned-start vs plain FP64 FPI"
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch of the GEMM kernel from an ncu capture
+# (profiles/), scaled to one full-workload launch; None until a capture of the current kernel exists.
+GEMM_TRAFFIC_BYTES_PER_LAUNCH = None
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--buses", type=int, default=1000)
+    p.add_argument("--columns", type=int, default=525600)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--tol", type=float, default=1e-10)
+    p.add_argument("--fp64-sample", type=int, default=8192)
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--check-columns", type=int, default=256)
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    return p.parse_args()
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allmax(world, x: float) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(args):
+    from paper_2403_04578_gb300 import inputs as G
+
+    f = G.make_feeder(args.buses, args.seed)
+    return f, {
+        "workload": f"{args.buses}-bus radial feeder x {args.columns:,} one-minute load columns (one year); "
+                    f"flat start, per-column stop at max|dV| <= {args.tol:g} pu",
+        "buses": args.buses,
+        "pq_buses": f.n_pq,
+        "columns": args.columns,
+        "feeder_seed": args.seed,
+        "load_scale": round(f.load_scale, 6),
+        "l2": "no flush: S alone is %.1f GB, far above the 129 MB L2" % (args.columns * f.n_pq * 16 / 1e9),
+    }
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_leg(f, S_host, V_gpu_host, it_gpu, args, full_T):
+    """Time the CPU oracle on a bounded column sample and check GPU results against it."""
+    from oracle import oracle as O
+
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    case = O.Case.from_feeder(f)
+    t_setup = time.perf_counter() - t0
+    # Probe the per-column cost, then size the sample to about args.cpu_seconds.
+    probe_cols = np.linspace(0, full_T - 1, 4 * threads).astype(np.int64)
+    t0 = time.perf_counter()
+    case.solve(S_host[probe_cols], tol=args.tol, threads=threads)
+    per_col = (time.perf_counter() - t0) / probe_cols.size
+    n_cols = int(min(full_T, max(probe_cols.size, args.cpu_seconds / max(per_col, 1e-9))))
+    cols = np.linspace(0, full_T - 1, n_cols).astype(np.int64)
+    t0 = time.perf_counter()
+    Vo, ito, _ = case.solve(S_host[cols], tol=args.tol, threads=threads)
+    dt = time.perf_counter() - t0
+    out = {"value": n_cols / dt, "unit": "PF/s", "cores": threads, "kind": "oracle",
+           "sample": f"{n_cols} columns evenly spaced over the {full_T:,}-column year, same feeder and tol; "
+                     f"K = -Y_dd^-1 setup {t_setup:.1f} s not included"}
+    check = {}
+    if V_gpu_host is not None:
+        cc = np.linspace(0, full_T - 1, min(args.check_columns, full_T)).astype(np.int64)
+        Vt, _, _ = case.solve(S_host[cc], tol=1e-13, threads=threads)
+        err = float(np.abs(V_gpu_host[cc] - Vt).max())
+        _, it_ref, _ = case.solve(S_host[cc], tol=args.tol, threads=threads)
+        check = {"max_abs_err_pu": err, "columns_checked": int(cc.size),
+                 "iters_equal_frac": float(np.mean(it_gpu[cc] == it_ref)),
+                 "iters_diff_max": int(np.abs(it_gpu[cc] - it_ref).max())}
+    return out, check
+
+
+def run_reference(args, world, rank):
+    """The reference arm: the CPU oracle (FP64, all host cores) on bounded samples of the workload."""
+    if rank != 0:
+        return
+    from paper_2403_04578_gb300 import inputs as G
+    from oracle import oracle as O
+
+    f, config = workload(args)
+    threads = os.cpu_count() or 1
+    case = O.Case.from_feeder(f)
+    budget = 120.0  # seconds for all warm-up and timed steps
+    probe_T = G.CHUNK
+    S = G.load_tensor(f, probe_T, args.seed)
+    t0 = time.perf_counter()
+    case.solve(S[: 2 * threads], tol=args.tol, threads=threads)
+    per_col = (time.perf_counter() - t0) / (2 * threads)
+    per_step = int(max(threads, min(probe_T, budget / (args.steps + args.warmup) / per_col)))
+    cols = np.linspace(0, probe_T - 1, per_step).astype(np.int64)
+    Ss = np.ascontiguousarray(S[cols])
+    for _ in range(args.warmup):
+        case.solve(Ss, tol=args.tol, threads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        case.solve(Ss, tol=args.tol, threads=threads)
+        times.append(time.perf_counter() - t0)
+    dt = sum(times) / len(times)
+    value = per_step / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "PF/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
+            "cpu_baseline": {"value": value, "unit": "PF/s", "cores": threads, "kind": "oracle",
+                             "sample": f"{per_step} columns per step, evenly spaced over the first {probe_T} "
+                                       "columns of the year"},
+            "e2e": {"value": value, "unit": "PF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    import torch
+
+    import __graft_entry__
+
+    torch.cuda.set_device(local)
+    __graft_entry__.build()
+    from paper_2403_04578_gb300 import inputs as G
+    from paper_2403_04578_gb300 import tpf
+
+    f, config = workload(args)
+    T, n = args.columns, f.n_pq
+    Sh = torch.empty((T, n), dtype=torch.complex128, pin_memory=True)
+    G.load_tensor(f, T, args.seed, out=Sh.numpy())
+    Sd = Sh.to(f"cuda:{local}")
+    fd = tpf.Feeder.from_inputs(f)
+    Vd = torch.empty_like(Sd)
+    itd = torch.empty(T, dtype=torch.int32, device=Sd.device)
+    mmd = torch.empty(T, dtype=torch.float64, device=Sd.device)
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat")
+    torch.cuda.synchronize()
+
+    gemm_ms = gemm_cols = gemm_launch = 0.0
+    launches = 0
+    step_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clocks:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            _, _, _, st = fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat", profile=True)
+            b.record(stream)
+            s = fd.stats()
+            gemm_ms += s["gemm_ms"]
+            gemm_cols += s["gemm_columns"]
+            gemm_launch += s["gemm_launches"]
+            launches += s["kernel_launches"]
+            b.synchronize()
+            step_ms.append(a.elapsed_time(b))
+        e1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    total_ms = e0.elapsed_time(e1)
+    ms_per_step = allmax(world, total_ms / args.steps)
+    value = world * T / (ms_per_step / 1e3)
+    stats = fd.stats()
+
+    # Roofline of the GEMM kernel (algorithmic flops: 8 n^2 per iterating column per sweep).
+    peaks, peak_src = measured_peaks()
+    achieved = 8.0 * n * n * gemm_cols / (gemm_ms / 1e3) / 1e12
+    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": GEMM_TRAFFIC_BYTES_PER_LAUNCH, "kernel": "tc_gemm",
+                "peak_source": f"{peak_src} bf16 sustained (fp16 has the bf16 rate)",
+                "gemm_share_of_step": gemm_ms / sum(step_ms),
+                "gemm_ms_per_launch": gemm_ms / max(gemm_launch, 1)}
+
+    # End to end through the host-buffer entry point.
+    e2e = None
+    if not args.no_e2e:
+        Vh = torch.empty((T, n), dtype=torch.complex128, pin_memory=True)
+        ith = torch.empty(T, dtype=torch.int32, pin_memory=True)
+        mmh = torch.empty(T, dtype=torch.float64, pin_memory=True)
+        fd.solve_host(Sh, precision="mixed", tol=args.tol, out=(Vh, ith, mmh))
+        e2e_steps = max(1, args.steps // 2)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            fd.solve_host(Sh, precision="mixed", tol=args.tol, out=(Vh, ith, mmh))
+        dt = allmax(world, (time.perf_counter() - t0) / e2e_steps)
+        e2e = {"value": world * T / dt, "unit": "PF/s", "h2d_bytes_per_step": T * n * 16,
+               "d2h_bytes_per_step": T * n * 16 + T * 4 + T * 8, "ms_per_step": dt * 1e3,
+               "entry_point": "tpf_solve_host (pinned host buffers)"}
+
+    # Plain FP64 GPU FPI on a column sample (the comparison path of the metric).
+    F = min(args.fp64_sample, T)
+    Sf = Sd[:F].contiguous()
+    fd.solve(Sf, precision="fp64", tol=args.tol)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(2):
+        fd.solve(Sf, precision="fp64", tol=args.tol)
+    b.record(stream)
+    b.synchronize()
+    fp64_pfs = F / (a.elapsed_time(b) / 2 / 1e3)
+    fp64 = {"value": fp64_pfs, "unit": "PF/s", "sample": f"first {F} columns", "sweeps": fd.stats()["sweeps"]}
+
+    line = {"metric": METRIC, "value": value, "unit": "PF/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f16 tensor-core products + f32/double-float elementwise",
+            "data": "synthetic", "config": config, "roofline": roofline,
+            "e2e": e2e, "clocks": clocks.summary(), "gpu_launches": launches,
+            "sweeps": stats["sweeps"], "anchor_sweeps": stats["precise_sweeps"],
+            "fp64_gpu": fp64, "speedup_vs_fp64_gpu": (value / world) / fp64_pfs,
+            "learned_start": "not used on this workload (flat start); see the 200-bus learned-start benchmark"}
+    if rank == 0 and not args.no_cpu:
+        Vhost = Vd.cpu().numpy()
+        ithost = itd.cpu().numpy()
+        cpu, check = cpu_oracle_leg(f, Sh.numpy(), Vhost, ithost, args, T)
+        line["cpu_baseline"] = cpu
+        line["accuracy"] = check
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    fd.close()
+
+
+if __name__ == "__main__":
+    main()

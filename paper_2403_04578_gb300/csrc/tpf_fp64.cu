@@ -70,6 +70,20 @@ tpf_status upload_network(tpf_handle *h) {
         }
         TPF_CK(cudaMemcpy(d.y2f, y2.data(), sizeof(float4) * nnz, cudaMemcpyHostToDevice));
     }
+    d.radial = net.radial;
+    if (net.radial) {
+        const int nch = net.ch_ptr[n];
+        std::vector<float2> yp(n);
+        for (int i = 0; i < n; ++i) yp[i] = make_float2((float)net.ypar[2 * i], (float)net.ypar[2 * i + 1]);
+        TPF_CK(cudaMalloc(&d.par, sizeof(int) * n));
+        TPF_CK(cudaMalloc(&d.ch_ptr, sizeof(int) * (n + 1)));
+        TPF_CK(cudaMalloc(&d.ch, sizeof(int) * (nch > 0 ? nch : 1)));
+        TPF_CK(cudaMalloc(&d.ypar, sizeof(float2) * n));
+        TPF_CK(cudaMemcpy(d.par, net.par.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        TPF_CK(cudaMemcpy(d.ch_ptr, net.ch_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+        if (nch > 0) TPF_CK(cudaMemcpy(d.ch, net.ch.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
+        TPF_CK(cudaMemcpy(d.ypar, yp.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    }
     // fp16 planes of K * 2^k_exp with the largest component in [2^13, 2^14).
     double kmax = 0.0;
     for (double v : net.K) kmax = fmax(kmax, fabs(v));
@@ -90,6 +104,7 @@ void free_device(tpf_handle *h) {
     DeviceNet &d = h->dev;
     cudaFree(d.K64); cudaFree(d.W64); cudaFree(d.row_ptr); cudaFree(d.nbr); cudaFree(d.y64); cudaFree(d.y2f);
     cudaFree(d.Kr16); cudaFree(d.Ki16);
+    cudaFree(d.par); cudaFree(d.ch_ptr); cudaFree(d.ch); cudaFree(d.ypar);
     d = DeviceNet();
     Workspace &w = h->ws;
     cudaFree(w.Vhi); cudaFree(w.Vlo); cudaFree(w.Shi); cudaFree(w.Slo); cudaFree(w.Rr16); cudaFree(w.Ri16);

@@ -169,6 +169,26 @@ tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int
         net.W[2 * i] = acc.real();
         net.W[2 * i + 1] = acc.imag();
     }
+    // Tree arrays in column positions (radial networks).
+    if (net.radial) {
+        net.par.assign(n, -1);
+        net.ypar.assign((size_t)2 * n, 0.0);
+        std::vector<int> nch(n, 0);
+        for (int i = 0; i < n; ++i) {
+            int b = net.pq[i], p = parent[b];
+            net.par[i] = net.pos[p];  // -1 for the slack
+            cplx y = 1.0 / zpar[b];
+            net.ypar[2 * i] = y.real();
+            net.ypar[2 * i + 1] = y.imag();
+            if (net.par[i] >= 0) ++nch[net.par[i]];
+        }
+        net.ch_ptr.assign(n + 1, 0);
+        for (int i = 0; i < n; ++i) net.ch_ptr[i + 1] = net.ch_ptr[i] + nch[i];
+        net.ch.assign(net.ch_ptr[n], 0);
+        std::vector<int> fill(net.ch_ptr.begin(), net.ch_ptr.end() - 1);
+        for (int i = 0; i < n; ++i)
+            if (net.par[i] >= 0) net.ch[fill[net.par[i]]++] = i;
+    }
     // Neighbour lists in column positions.
     net.row_ptr.assign(n + 1, 0);
     for (int i = 0; i < n; ++i) net.row_ptr[i + 1] = net.row_ptr[i] + (int)adj[net.pq[i]].size();

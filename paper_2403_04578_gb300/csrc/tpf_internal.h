@@ -34,6 +34,10 @@ struct Network {
     // other end j of every branch at i (-1 = the slack) and that branch's admittance y = 1/z.
     std::vector<int> row_ptr, nbr;
     std::vector<double> y;        // complex [nnz]
+    // Radial networks only: the parent of each demand bus (column position, -1 = the slack), the
+    // admittance of the branch to it, and each bus's children (CSR over column positions).
+    std::vector<int> par, ch_ptr, ch;
+    std::vector<double> ypar;     // complex [n_pq]
 };
 
 // Build the network arrays; returns TPF_OK or the status to report.
@@ -51,6 +55,9 @@ struct DeviceNet {
     int *row_ptr = nullptr, *nbr = nullptr;
     double *y64 = nullptr;   // complex [nnz]
     float4 *y2f = nullptr;   // double-float complex admittance (re_hi, im_hi, re_lo, im_lo) [nnz]
+    bool radial = false;
+    int *par = nullptr, *ch_ptr = nullptr, *ch = nullptr;  // radial only
+    float2 *ypar = nullptr;  // FP32 admittance of the branch to the parent [n]
     // Mixed path: fp16 planes of K * 2^k_exp, [n_pad][n_pad], zero padded
     void *Kr16 = nullptr, *Ki16 = nullptr;
     int k_exp = 0;

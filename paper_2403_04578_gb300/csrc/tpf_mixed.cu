@@ -121,13 +121,28 @@ __device__ __forceinline__ c2 residual_dd(int i, const float2 *vh, const float2 
     return acc;
 }
 
+// conj(s / v) = conj(s) v / |v|^2 in FP32.
+__device__ __forceinline__ float2 load_current_f32(float2 v, float2 s) {
+    float inv = 1.0f / (v.x * v.x + v.y * v.y);
+    return make_float2((s.x * v.x + s.y * v.y) * inv, (s.x * v.y - s.y * v.x) * inv);
+}
+
+// conj(s / (v + d)) - conj(s / v) = -conj(s d / ((v + d) v)) in FP32 (small when d is small).
+__device__ __forceinline__ float2 delta_current(float2 v, float2 d, float2 s) {
+    float2 w = make_float2(s.x * d.x - s.y * d.y, s.x * d.y + s.y * d.x);
+    float2 vp = make_float2(v.x + d.x, v.y + d.y);
+    float2 q = make_float2(vp.x * v.x - vp.y * v.y, vp.x * v.y + vp.y * v.x);
+    float inv = 1.0f / (q.x * q.x + q.y * q.y);
+    float wr = (w.x * q.x + w.y * q.y) * inv, wi = (w.y * q.x - w.x * q.y) * inv;  // w / q
+    return make_float2(-wr, wi);                                                    // -conj(w / q)
+}
+
 // rho_i in FP32 from the high words only (the sweeps far from convergence).
 __device__ __forceinline__ float2 residual_f32(int i, const float2 *vh, const float2 *sh, const int *row_ptr,
                                                const int *nbr, const float4 *y, float2 vs) {
-    float2 v = vh[i], s = sh[i];
-    float inv = 1.0f / (v.x * v.x + v.y * v.y);
-    float ar = (s.x * v.x + s.y * v.y) * inv;
-    float ai = (s.x * v.y - s.y * v.x) * inv;
+    float2 v = vh[i];
+    float2 cur = load_current_f32(v, sh[i]);
+    float ar = cur.x, ai = cur.y;
     for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
         int j = nbr[e];
         float2 vj = j >= 0 ? vh[j] : vs;
@@ -145,13 +160,9 @@ __device__ __forceinline__ float2 residual_f32(int i, const float2 *vh, const fl
 // Both terms are proportional to |d|, so their FP32 rounding error is ~6e-8 |d| |y|.
 __device__ __forceinline__ float2 residual_corr(int i, const float2 *vh, const float2 *vl, const float2 *sh,
                                                 const int *row_ptr, const int *nbr, const float4 *y) {
-    float2 v = vh[i], d = vl[i], s = sh[i];
-    float2 w = make_float2(s.x * d.x - s.y * d.y, s.x * d.y + s.y * d.x);
-    float2 vp = make_float2(v.x + d.x, v.y + d.y);
-    float2 q = make_float2(vp.x * v.x - vp.y * v.y, vp.x * v.y + vp.y * v.x);
-    float inv = 1.0f / (q.x * q.x + q.y * q.y);
-    float wr = (w.x * q.x + w.y * q.y) * inv, wi = (w.y * q.x - w.x * q.y) * inv;  // w / q
-    float ar = -wr, ai = wi;                                                          // -conj(w / q)
+    const float2 d = vl[i];
+    const float2 dc = delta_current(vh[i], d, sh[i]);
+    float ar = dc.x, ai = dc.y;
     for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
         int j = nbr[e];
         float2 dj = j >= 0 ? vl[j] : make_float2(0.0f, 0.0f);
@@ -217,6 +228,9 @@ struct PrologueArgs {
     int *flags, *iters, *rexp, *tile_active, *counters;
     unsigned *delta, *dprev;
     int given;  // the solve started from a given V_0: anchor every column at sweep 0
+    int radial;
+    const int *par, *ch_ptr, *ch;
+    const float2 *ypar;
     __half *Rr, *Ri;
 };
 
@@ -278,22 +292,75 @@ __global__ void __launch_bounds__(512, 1) mx_prologue(PrologueArgs a) {
         const float2 *sh = a.Shi + base;
         float rr[BPL], ri[BPL];
         float m = 0.0f;
-        if (f & kAnchored) {
-            float2 *vl = a.Vlo + base;
-            float2 *rh = a.RefHi + base, *rl = a.RefLo + base;
-            if (anchor) {  // re-base: Vhi <- fl(Vhi + Vlo), Vlo <- the exact remainder
+        const bool anchored = (f & kAnchored) != 0;
+        float2 *vl = a.Vlo + base;
+        float2 *rh = a.RefHi + base, *rl = a.RefLo + base;
+        if (anchor) {  // re-base: Vhi <- fl(Vhi + Vlo), Vlo <- the exact remainder
 #pragma unroll
-                for (int b = 0; b < BPL; ++b) {
-                    int i = lane + 32 * b;
-                    if (i < a.n) {
-                        float2 h = vh[i], l = vl[i];
-                        f2 re = two_sum(h.x, l.x), im = two_sum(h.y, l.y);
-                        vh[i] = make_float2(re.h, im.h);
-                        vl[i] = make_float2(re.l, im.l);
+            for (int b = 0; b < BPL; ++b) {
+                int i = lane + 32 * b;
+                if (i < a.n) {
+                    float2 h = vh[i], l = vl[i];
+                    f2 re = two_sum(h.x, l.x), im = two_sum(h.y, l.y);
+                    vh[i] = make_float2(re.h, im.h);
+                    vl[i] = make_float2(re.l, im.l);
+                }
+            }
+            __syncwarp();
+        }
+        if (a.radial && !anchor) {
+            // Radial feeder: rho_i = local_i - J_i + sum_{children c} J_c with the branch current
+            // J_c = y_c (V_parent(c) - V_c).  The column's V (or V - V_ref once anchored) is staged
+            // in shared memory so the parent gathers and the children sums stay on chip.
+            extern __shared__ float2 psm[];
+            float2 *vb = psm + (size_t)(threadIdx.x >> 5) * 2 * a.n_pad;
+            float2 *jb = vb + a.n_pad;
+            const float2 *src = anchored ? vl : vh;
+            const float2 vsrc = anchored ? make_float2(0.0f, 0.0f) : a.vs_f;
+#pragma unroll
+            for (int b = 0; b < BPL; ++b) {
+                int i = lane + 32 * b;
+                vb[i] = i < a.n ? src[i] : make_float2(0.0f, 0.0f);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int b = 0; b < BPL; ++b) {
+                int i = lane + 32 * b;
+                rr[b] = 0.f;
+                ri[b] = 0.f;
+                if (i < a.n) {
+                    const float2 v = vb[i];
+                    const int p = a.par[i];
+                    const float2 vp = p >= 0 ? vb[p] : vsrc;
+                    const float2 y = a.ypar[i];
+                    const float dr = vp.x - v.x, di = vp.y - v.y;
+                    const float2 J = make_float2(y.x * dr - y.y * di, y.x * di + y.y * dr);
+                    jb[i] = J;
+                    const float2 loc = anchored ? delta_current(vh[i], v, sh[i]) : load_current_f32(v, sh[i]);
+                    rr[b] = loc.x - J.x;
+                    ri[b] = loc.y - J.y;
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int b = 0; b < BPL; ++b) {
+                int i = lane + 32 * b;
+                if (i < a.n) {
+                    for (int e = a.ch_ptr[i]; e < a.ch_ptr[i + 1]; ++e) {
+                        const float2 J = jb[a.ch[e]];
+                        rr[b] += J.x;
+                        ri[b] += J.y;
+                    }
+                    if (anchored) {
+                        const float2 h = rh[i], l = rl[i];
+                        const f2 sr = two_sum(h.x, rr[b]), si = two_sum(h.y, ri[b]);
+                        rr[b] = sr.h + (sr.l + l.x);
+                        ri[b] = si.h + (si.l + l.y);
                     }
                 }
-                __syncwarp();
+                m = fmaxf(m, fmaxf(fabsf(rr[b]), fabsf(ri[b])));
             }
+        } else if (anchored) {
 #pragma unroll
             for (int b = 0; b < BPL; ++b) {
                 int i = lane + 32 * b;
@@ -627,26 +694,48 @@ __global__ void __launch_bounds__(128, 1)
                     ep.Di[nn * ep.ldD + m] = __uint_as_float(vi[q]);
                 }
             } else {
+                // Update V of this lane's bus for the 32 columns (all loads first, then the
+                // stores), then a transposed butterfly max over the warp: after 31 shuffles lane l
+                // holds max_rows |dV| of column cb*32 + l.
+                float2 old[32];
+                float mag[32];
 #pragma unroll
                 for (int q = 0; q < 32; ++q) {
                     const int c = cb * 32 + q;
                     const int f = col_flag[c];
-                    if (!(f & kActive)) continue;  // warp-uniform
+                    const bool act = (f & kActive) && m < ep.n;
+                    const int64_t k = ((int64_t)n_tile * kTileN + c) * ep.n_pad + m;
+                    const float2 *src = (f & kAnchored) ? ep.Vlo : ep.Vhi;  // anchored: V_ref stays fixed
+                    old[q] = act ? src[k] : make_float2(0.0f, 0.0f);
+                }
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    const int c = cb * 32 + q;
+                    const int f = col_flag[c];
+                    const bool act = (f & kActive) && m < ep.n;
                     const float sc = col_scale[c];
                     const float dr = __uint_as_float(vr[q]) * sc, di = __uint_as_float(vi[q]) * sc;
                     float dmag = 0.0f;
-                    if (m < ep.n) {
+                    if (act) {
                         const int64_t k = ((int64_t)n_tile * kTileN + c) * ep.n_pad + m;
-                        float2 *dst = (f & kAnchored) ? ep.Vlo : ep.Vhi;  // anchored: V_ref stays fixed
-                        float2 h = dst[k];
-                        dst[k] = make_float2(h.x + dr, h.y + di);
+                        float2 *dst = (f & kAnchored) ? ep.Vlo : ep.Vhi;
+                        dst[k] = make_float2(old[q].x + dr, old[q].y + di);
                         dmag = sqrtf(dr * dr + di * di);
                         if (dmag != dmag) dmag = __int_as_float(0x7f800000);  // NaN -> +inf
                     }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) dmag = fmaxf(dmag, __shfl_xor_sync(0xffffffffu, dmag, o));
-                    if (lane == 0 && dmag > 0.0f) atomicMax(&col_dmax[c], __float_as_uint(dmag));
+                    mag[q] = dmag;
                 }
+#pragma unroll
+                for (int off = 16; off >= 1; off >>= 1) {
+                    const bool upper = (lane & off) != 0;
+#pragma unroll
+                    for (int j = 0; j < off; ++j) {
+                        const float send = upper ? mag[j] : mag[j + off];
+                        const float keep = upper ? mag[j + off] : mag[j];
+                        mag[j] = fmaxf(keep, __shfl_xor_sync(0xffffffffu, send, off));
+                    }
+                }
+                if (mag[0] > 0.0f) atomicMax(&col_dmax[cb * 32 + lane], __float_as_uint(mag[0]));
             }
         }
     }
@@ -700,10 +789,22 @@ tpf_status prepare_gemm() {
     return TPF_OK;
 }
 
+// Radial feeders stage two n_pad-long float2 rows per warp in shared memory; the block takes as
+// many warps (columns) as fit in ~96 KB so that two blocks share an SM.
 template <int BPL>
-void launch_prologue(const PrologueArgs &a, cudaStream_t st) {
-    const int64_t threads = a.cols * 32;
-    mx_prologue<BPL><<<(unsigned)((threads + 511) / 512), 512, 0, st>>>(a);
+tpf_status launch_prologue(const PrologueArgs &a, cudaStream_t st) {
+    static bool attr = false;
+    const size_t per_warp = a.radial ? (size_t)2 * a.n_pad * sizeof(float2) : 0;
+    int warps = per_warp ? (int)((96 * 1024) / per_warp) : 16;
+    warps = warps < 1 ? 1 : (warps > 16 ? 16 : warps);
+    const size_t smem = per_warp * warps;
+    if (!attr) {
+        TPF_CK(cudaFuncSetAttribute(mx_prologue<BPL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+        attr = true;
+    }
+    const int64_t blocks = (a.cols + warps - 1) / warps;
+    mx_prologue<BPL><<<(unsigned)blocks, 32 * warps, smem, st>>>(a);
+    return TPF_OK;
 }
 
 }  // namespace
@@ -783,6 +884,11 @@ tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t
     pa.RefLo = w.RefLo;
     pa.dprev = w.dprev;
     pa.given = o.start == TPF_START_GIVEN;
+    pa.radial = h->dev.radial ? 1 : 0;
+    pa.par = h->dev.par;
+    pa.ch_ptr = h->dev.ch_ptr;
+    pa.ch = h->dev.ch;
+    pa.ypar = h->dev.ypar;
     pa.row_ptr = h->dev.row_ptr;
     pa.nbr = h->dev.nbr;
     pa.y = h->dev.y2f;
@@ -816,12 +922,13 @@ tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t
         pa.sweep = s;
         const int bpl = n_pad / 32;
         timer.begin(KernelTimer::kResidual);
-        if (bpl <= 4) launch_prologue<4>(pa, st);
-        else if (bpl <= 8) launch_prologue<8>(pa, st);
-        else if (bpl <= 16) launch_prologue<16>(pa, st);
-        else if (bpl <= 32) launch_prologue<32>(pa, st);
-        else launch_prologue<64>(pa, st);
+        if (bpl <= 4) rs = launch_prologue<4>(pa, st);
+        else if (bpl <= 8) rs = launch_prologue<8>(pa, st);
+        else if (bpl <= 16) rs = launch_prologue<16>(pa, st);
+        else if (bpl <= 32) rs = launch_prologue<32>(pa, st);
+        else rs = launch_prologue<64>(pa, st);
         timer.end();
+        if (rs != TPF_OK) return rs;
         ++launches;
         TPF_CK(cudaGetLastError());
         TPF_CK(cudaMemcpyAsync(w.counters_host, w.counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));

@@ -168,6 +168,44 @@ tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_
 tpf_status tpf_last_stats(const tpf_handle *h, tpf_stats *out);
 
 /*
+ * Allocation-free FP64 solve.  The paper has no counterpart to this entry point; it exists for
+ * callers that must not allocate device memory themselves or have the library do it: runtimes
+ * that hand out device memory only from their own pool (raw cudaMalloc/cudaFree would escape
+ * their accounting), and latency-bound loops where cudaMalloc/cudaFree may synchronise the device
+ * or block for an unbounded time.  It runs the same FP64 kernels as tpf_solve with
+ * TPF_PREC_FP64 (Algorithm 1 in direct form, per-column stopping) but needs no handle: the
+ * caller passes K and W on the device, and the solve's scratch (the second V buffer and the
+ * per-column state) lives in a fixed array compiled into libtpf.so.
+ *
+ *   n          demand buses (the column length)
+ *   K_dev      device, complex128 [n][n], K = -Y_dd^{-1} (e.g. from tpf_precompute_host)
+ *   W_dev      device, complex128 [n], W = K Y_ds v_s
+ *   T          columns; T = 0 is a valid empty solve
+ *   S_dev      device, complex128 [T][n], the loads (read only)
+ *   V_dev      device, complex128 [T][n], receives V; read first as V_0 if given_start != 0,
+ *              otherwise the flat start 1 + j0 is used
+ *   iters_dev  device, int32 [T], sweeps applied per column or -max_iter (NULL: not written)
+ *   tol, max_iter  as in tpf_opts;   stream  a cudaStream_t
+ *
+ * Scratch limit: the solve needs 1024 + 16 * T_128 * (n + 1) bytes of the built-in array, where
+ * T_128 is T rounded up to a multiple of 128; more than TPF_NOALLOC_SCRATCH_BYTES (64 MiB) is
+ * rejected with TPF_EINVAL before any device work.  No power mismatch is computed (there is no
+ * network on the device here).  The array occupies 64 MiB on every device that loads the library,
+ * until the process exits.
+ *
+ * Set-up: the first call on each device looks the array's device address up (with that device
+ * current) and keeps it; make that first call before any stream capture begins.  Every call uses
+ * the same array and leaves its contents behind; each call re-initialises the state it reads, but
+ * calls whose device work overlaps (different streams, or different host threads, on one device)
+ * race on the array and must be serialised by the caller.  Blocks until the stream has finished.
+ * This entry point calls no cudaMalloc, cudaFree or other allocating routine.
+ */
+#define TPF_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+tpf_status tpf_solve_fp64_noalloc(int n, const void *K_dev, const void *W_dev, int64_t T,
+                                  const void *S_dev, void *V_dev, int32_t *iters_dev, double tol,
+                                  int max_iter, int given_start, void *stream);
+
+/*
  * Self-test of the tensor-core complex GEMM used by the mixed solve (tcgen05, fp16 operands,
  * FP32 accumulation): D = A B^T over complex numbers, with
  *   A_re, A_im  device fp16 [M][K] (row-major, K fastest),  B_re, B_im device fp16 [N][K],

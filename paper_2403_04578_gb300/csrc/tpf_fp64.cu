@@ -421,3 +421,97 @@ tpf_status solve_fp64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t 
 }
 
 }  // namespace tpf
+
+// ------------------------------------------------------------------------------------------
+// Allocation-free FP64 solve (tpf_solve_fp64_noalloc)
+//
+// For callers that cannot allocate device memory (their runtime hands out device memory only
+// from its own pool, or their loop cannot afford cudaMalloc/cudaFree, which may synchronise the
+// device): the same FP64 kernels as solve_fp64, with the scratch they need in one fixed array.
+// ------------------------------------------------------------------------------------------
+
+// The scratch of every tpf_solve_fp64_noalloc call on a device.  Layout for a call with
+// cols = T rounded up to 128:  [0, 1024) counters | flags int[cols] | iters int[cols] |
+// step double-bits[cols] | second V buffer complex128[cols][n].
+static __device__ __align__(256) unsigned char g_noalloc_scratch[TPF_NOALLOC_SCRATCH_BYTES];
+
+#include <mutex>
+
+namespace {
+constexpr int kNoallocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kNoallocMaxDevices];  // device address of g_noalloc_scratch, per device
+}  // namespace
+
+extern "C" tpf_status tpf_solve_fp64_noalloc(int n, const void *K_dev, const void *W_dev, int64_t T,
+                                             const void *S_dev, void *V_dev, int32_t *iters_dev, double tol,
+                                             int max_iter, int given_start, void *stream) {
+    using namespace tpf;
+    if (n < 1 || T < 0 || !(tol >= 0.0) || max_iter < 1 || max_iter > 100000) return TPF_EINVAL;
+    if (T == 0) return TPF_OK;
+    if (!K_dev || !W_dev || !S_dev || !V_dev) return TPF_EINVAL;
+    const int64_t cols = round_up(T, kTileN);
+    const size_t off_flags = 1024;
+    const size_t off_iters = off_flags + sizeof(int) * (size_t)cols;
+    const size_t off_delta = off_iters + sizeof(int) * (size_t)cols;
+    const size_t off_valt = off_delta + sizeof(unsigned long long) * (size_t)cols;
+    const size_t need = off_valt + sizeof(double2) * (size_t)cols * (size_t)n;  // 1024 + 16 cols (n + 1)
+    if ((size_t)cols > TPF_NOALLOC_SCRATCH_BYTES / 16 || need > TPF_NOALLOC_SCRATCH_BYTES) return TPF_EINVAL;
+
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return TPF_ECUDA;
+    }
+    if (dev < 0 || dev >= kNoallocMaxDevices) return TPF_EUNSUPPORTED;
+    char *base = nullptr;
+    {
+        // Host code cannot use the array's name as a device address: look it up once per device.
+        std::lock_guard<std::mutex> lock(g_noalloc_mu);
+        if (!g_noalloc_addr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();
+                return TPF_ECUDA;
+            }
+            g_noalloc_addr[dev] = p;
+        }
+        base = (char *)g_noalloc_addr[dev];
+    }
+    int *counters = (int *)base;
+    int *flags = (int *)(base + off_flags);
+    int *iters = (int *)(base + off_iters);
+    unsigned long long *delta = (unsigned long long *)(base + off_delta);
+    double2 *Valt = (double2 *)(base + off_valt);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+
+    // The array keeps the previous call's contents: zero the counters, and f64_init resets the
+    // per-column state (flags, iteration counts, steps) that the sweeps read.
+    TPF_CK(cudaMemsetAsync(counters, 0, sizeof(int) * 8, st));
+    {
+        int64_t work = cols > T * n ? cols : T * n;
+        f64_init<<<(unsigned)((work + 255) / 256), 256, 0, st>>>(T, cols, n, given_start ? 0 : 1, (double2 *)V_dev,
+                                                                  flags, iters, delta);
+    }
+    TPF_CK(cudaGetLastError());
+    double2 *buf[2] = {(double2 *)V_dev, Valt};
+    const dim3 grid((unsigned)((T + F64_BN - 1) / F64_BN), (n + F64_BM - 1) / F64_BM);
+    int host_counters[8] = {0};
+    for (int k = 0; k < max_iter; ++k) {
+        f64_sweep<<<grid, 256, 0, st>>>((const double2 *)K_dev, (const double2 *)W_dev, (const double2 *)S_dev,
+                                        buf[k & 1], buf[(k + 1) & 1], n, T, flags, delta);
+        TPF_CK(cudaMemsetAsync(counters, 0, sizeof(int) * 4, st));
+        f64_decide<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(T, tol, max_iter, flags, iters, delta, counters);
+        TPF_CK(cudaGetLastError());
+        TPF_CK(cudaMemcpyAsync(host_counters, counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
+        TPF_CK(cudaStreamSynchronize(st));
+        if (host_counters[kCntActive] == 0) break;
+    }
+    f64_finish<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(T, n, max_iter, flags, iters, (double2 *)V_dev,
+                                                                 Valt, (const double2 *)S_dev, nullptr, nullptr,
+                                                                 nullptr, make_double2(0.0, 0.0), iters_dev, nullptr);
+    TPF_CK(cudaGetLastError());
+    TPF_CK(cudaMemcpyAsync(host_counters, counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
+    TPF_CK(cudaStreamSynchronize(st));
+    return host_counters[kCntConverged] == T ? TPF_OK : TPF_ENOCONV;
+}

@@ -21,8 +21,11 @@ START_FLAT, START_GIVEN = 0, 1
 # Every entry point declared in include/tpf.h.
 EXPORTS = (
     "tpf_default_opts", "tpf_strerror", "tpf_create", "tpf_destroy", "tpf_n_pq", "tpf_precompute_host",
-    "tpf_solve", "tpf_solve_host", "tpf_last_stats", "tpf_selftest_gemm",
+    "tpf_solve", "tpf_solve_host", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
 )
+
+# Size of the built-in scratch array of tpf_solve_fp64_noalloc (include/tpf.h).
+NOALLOC_SCRATCH_BYTES = 64 << 20
 
 
 class TpfError(RuntimeError):
@@ -88,6 +91,9 @@ def lib(build_if_missing: bool = False):
     L.tpf_last_stats.restype = ctypes.c_int
     L.tpf_selftest_gemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
     L.tpf_selftest_gemm.restype = ctypes.c_int
+    L.tpf_solve_fp64_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int64, vp, vp, vp, ctypes.c_double,
+                                         ctypes.c_int, ctypes.c_int, vp]
+    L.tpf_solve_fp64_noalloc.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -248,6 +254,21 @@ class Feeder:
         if check and st not in (OK, ENOCONV):
             raise TpfError(st, "tpf_solve_host")
         return V, it, mm, st
+
+
+def solve_fp64_noalloc(K, W, S, V, iters=None, tol=1e-10, max_iter=100, given_start=False, stream=None):
+    """tpf_solve_fp64_noalloc: the FP64 solve without any allocation by the library.
+
+    For callers whose device memory all comes from their own pool: K (complex128 [n, n]), W
+    (complex128 [n]), S and V (complex128 [T, n]) and iters (int32 [T], optional) are the caller's
+    CUDA tensors; the solve's scratch is libtpf's built-in 64 MiB array.  Returns the status.
+    """
+    n = K.shape[0]
+    T = S.shape[0]
+    return lib().tpf_solve_fp64_noalloc(
+        int(n), ctypes.c_void_p(K.data_ptr()), ctypes.c_void_p(W.data_ptr()), int(T), ctypes.c_void_p(S.data_ptr()),
+        ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(iters.data_ptr() if iters is not None else 0), float(tol),
+        int(max_iter), 1 if given_start else 0, _stream_ptr(stream))
 
 
 def selftest_gemm(Ar, Ai, Br, Bi, stream=None):

@@ -39,9 +39,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PF solves/s at ≤1e-8 pu vs FP64 oracle: mixed+learned-start vs plain FP64 FPI"
 
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the GEMM kernel from an ncu capture
-# (profiles/), scaled to one full-workload launch; None until a capture of the current kernel exists.
-GEMM_TRAFFIC_BYTES_PER_LAUNCH = None
+# dram__bytes_read.sum + dram__bytes_write.sum of one tc_gemm launch from the ncu capture in
+# profiles/tc_gemm_n999_T16384.md (203.7 MB + 75.5 MB for 16,384 columns), per iterating column;
+# scaled by the columns each launch of this run processes.  None once the kernel has changed since.
+GEMM_TRAFFIC_BYTES_PER_COLUMN = (203.725056e6 + 75.471360e6) / 16384
 
 
 def parse_args():
@@ -306,8 +307,13 @@ def main():
     peaks, peak_src = measured_peaks()
     achieved = 8.0 * n * n * gemm_cols / (gemm_ms / 1e3) / 1e12
     peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+    traffic = None
+    if GEMM_TRAFFIC_BYTES_PER_COLUMN is not None and args.buses == 1000:
+        traffic = GEMM_TRAFFIC_BYTES_PER_COLUMN * gemm_cols / max(gemm_launch, 1)
     roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": GEMM_TRAFFIC_BYTES_PER_LAUNCH, "kernel": "tc_gemm",
+                "traffic": traffic, "traffic_note": "ncu DRAM bytes per iterating column (16,384-column capture, "
+                                                    "profiles/tc_gemm_n999_T16384.md) x columns per launch",
+                "kernel": "tc_gemm",
                 "peak_source": f"{peak_src} bf16 sustained (fp16 has the bf16 rate)",
                 "gemm_share_of_step": gemm_ms / sum(step_ms),
                 "gemm_ms_per_launch": gemm_ms / max(gemm_launch, 1)}

@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtpf.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["tpf_host.cpp", "tpf_fp64.cu", "tpf_mixed.cu"]
+SOURCES = ["tpf_host.cpp", "tpf_fp64.cu", "tpf_mixed.cu", "tpf_residual.cu", "tpf_gemm.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 
@@ -37,7 +37,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags: list[str] | N
     """Compile and link libtpf.so; returns its path."""
     os.makedirs(OUT, exist_ok=True)
     cc = nvcc()
-    hdr_time = max(os.path.getmtime(os.path.join(CSRC, "tpf_internal.h")), os.path.getmtime(os.path.join(INCLUDE, "tpf.h")))
+    headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
+    hdr_time = max(os.path.getmtime(p) for p in headers + [os.path.join(INCLUDE, "tpf.h")])
     extra = list(extra_flags or [])
 
     def compile_one(src: str) -> str:

@@ -1,0 +1,412 @@
+// Tensor-core complex GEMM of the mixed path: D = K rho for all iterating columns (the dense step
+// of Eq. 12 in residual form), fp16 operands, FP32 accumulation in TMEM.
+//
+// A complex product becomes four real-plane MMAs per 16-wide K step:
+//     Re D = Kr rr - Ki ri,   Im D = Kr ri + Ki rr
+// (the minus sign by the instruction descriptor's negate-A bit).  Tiles are 128 buses x 128
+// columns with both accumulators (Re, Im) in TMEM; the K loop runs over 64-element chunks
+// streamed by TMA in the 128-byte swizzle that the MMA descriptors read.
+//
+// One persistent CTA per SM walks the tiles.  Warp 0 issues the TMA loads into a 3-slot ring,
+// warp 1 issues the MMAs, and warps 2-5 drain the accumulators.  TMEM holds two accumulator
+// stages (2 x 256 columns), so the epilogue of one tile overlaps the main loop of the next.
+// Every wait is bounded (2 s on %globaltimer): on expiry the CTA raises an error flag, stops,
+// waits for its own copies and MMAs (again bounded), frees TMEM and returns.
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+
+#include "tpf_gemm.h"
+
+namespace tpf {
+
+namespace {
+
+constexpr int kStages = 3;
+constexpr uint32_t kTileBytes = kTileM * kChunkK * 2;  // 16 KB: 128 rows x 64 fp16
+constexpr uint32_t kStageBytes = 4 * kTileBytes;        // Ar, Ai, Br, Bi
+constexpr uint64_t kWaitNs = 2000000000ull;             // bounded waits: 2 s
+constexpr uint32_t kAccCols = 256;                      // one stage: Re cols [0,128), Im [128,256)
+constexpr uint32_t kTmemCols = 512;                     // two stages
+constexpr int kGemmThreads = 192;                       // 6 warps
+constexpr size_t kGemmSmem = 1024 + kStages * kStageBytes + 2048;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+// Wait until the phase with the given parity has completed; false if kWaitNs passed first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        for (int i = 0; i < 32; ++i)
+            if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+// Shared-memory matrix descriptor of a K-major tile in the 128-byte swizzle layout written by
+// TMA: rows of 64 fp16 (128 B), 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor of kind::f16 with fp16 A and B, FP32 accumulation, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int negA) {
+    return (1u << 4) | ((uint32_t)negA << 13) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void epi_barrier() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ float pow2f_g(int e) {
+    e = e < -126 ? -126 : (e > 127 ? 127 : e);
+    return __int_as_float((127 + e) << 23);
+}
+
+__device__ __forceinline__ bool tile_live(const GemmEpi &ep, int64_t n_tile) {
+    return ep.mode != 1 || ep.tile_active[n_tile] != 0;
+}
+
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    tc_gemm(const __grid_constant__ CUtensorMap tmAr, const __grid_constant__ CUtensorMap tmAi,
+            const __grid_constant__ CUtensorMap tmBr, const __grid_constant__ CUtensorMap tmBi, int m_tiles,
+            int64_t n_tiles, int n_chunks, GemmEpi ep) {
+    extern __shared__ uint8_t smem_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint64_t *full = (uint64_t *)(smem + kStages * kStageBytes);  // [kStages]  TMA -> MMA
+    uint64_t *empty = full + kStages;                              // [kStages]  MMA -> TMA
+    uint64_t *tfull = empty + kStages;                             // [2]        MMA -> epilogue
+    uint64_t *tempty = tfull + 2;                                  // [2]        epilogue -> MMA
+    uint64_t *done = tempty + 2;                                   // [1]        all MMAs retired
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    int *abort_flag = (int *)(tmem_slot + 1);
+    float *col_scale = (float *)(abort_flag + 1);                  // [128]
+    int *col_flag = (int *)(col_scale + kTileN);                   // [128]
+    unsigned *col_dmax = (unsigned *)(col_flag + kTileN);          // [128]
+
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&tfull[a]), 1);
+            mbar_init(smem_u32(&tempty[a]), 4);  // lane 0 of each epilogue warp
+        }
+        mbar_init(smem_u32(done), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int64_t total = (int64_t)m_tiles * n_tiles;
+    volatile int *vabort = abort_flag;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer ----------------
+        const uint32_t sbase = smem_u32(smem);
+        int64_t g = 0;  // chunks issued by this CTA
+        for (int64_t tile = blockIdx.x; tile < total && !*vabort; tile += gridDim.x) {
+            const int64_t n_tile = tile / m_tiles;
+            const int m_tile = (int)(tile % m_tiles);
+            if (!tile_live(ep, n_tile)) continue;
+            const int m0 = m_tile * kTileM;
+            const int n0 = (int)(n_tile * kTileN);
+            for (int c = 0; c < n_chunks; ++c, ++g) {
+                const int slot = (int)(g % kStages);
+                const uint32_t use = (uint32_t)(g / kStages);
+                if (!mbar_wait(smem_u32(&empty[slot]), (use & 1) ^ 1)) {
+                    *vabort = 1;
+                    atomicExch(ep.err, 1);
+                    break;
+                }
+                const uint32_t st = sbase + slot * kStageBytes;
+                const uint32_t bar = smem_u32(&full[slot]);
+                mbar_expect_tx(bar, kStageBytes);
+                const int k = c * kChunkK;
+                tma_load_2d(st, &tmAr, bar, k, m0);
+                tma_load_2d(st + kTileBytes, &tmAi, bar, k, m0);
+                tma_load_2d(st + 2 * kTileBytes, &tmBr, bar, k, n0);
+                tma_load_2d(st + 3 * kTileBytes, &tmBi, bar, k, n0);
+            }
+        }
+        if (*vabort) {  // let this CTA's copies in flight land before it leaves (bounded)
+            for (int64_t q = g - 1; q >= 0 && q >= g - kStages; --q)
+                mbar_wait(smem_u32(&full[q % kStages]), (uint32_t)(q / kStages) & 1);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t sbase = smem_u32(smem);
+        const uint32_t id_pos = idesc_f16(kTileM, kTileN, 0), id_neg = idesc_f16(kTileM, kTileN, 1);
+        int64_t g = 0;
+        uint32_t j = 0;  // tiles processed by this CTA
+        for (int64_t tile = blockIdx.x; tile < total && !*vabort; tile += gridDim.x) {
+            if (!tile_live(ep, tile / m_tiles)) continue;
+            const uint32_t a = j & 1, u = j >> 1;
+            if (!mbar_wait(smem_u32(&tempty[a]), (u & 1) ^ 1)) {
+                *vabort = 1;
+                atomicExch(ep.err, 1);
+                break;
+            }
+            tc_fence_after();
+            const uint32_t tDr = tmem + a * kAccCols, tDi = tDr + kTileN;
+            bool ok = true;
+            for (int c = 0; c < n_chunks; ++c, ++g) {
+                const int slot = (int)(g % kStages);
+                if (!mbar_wait(smem_u32(&full[slot]), (uint32_t)(g / kStages) & 1)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t st = sbase + slot * kStageBytes;
+#pragma unroll
+                for (int kk = 0; kk < kChunkK / 16; ++kk) {
+                    const uint64_t ar = sw128_desc(st + kk * 32), ai = sw128_desc(st + kTileBytes + kk * 32);
+                    const uint64_t br = sw128_desc(st + 2 * kTileBytes + kk * 32);
+                    const uint64_t bi = sw128_desc(st + 3 * kTileBytes + kk * 32);
+                    const uint32_t first = (c | kk) != 0;
+                    umma_f16(tDr, ar, br, id_pos, first);  // Re += Kr rr
+                    umma_f16(tDr, ai, bi, id_neg, 1u);     // Re -= Ki ri
+                    umma_f16(tDi, ar, bi, id_pos, first);  // Im += Kr ri
+                    umma_f16(tDi, ai, br, id_pos, 1u);     // Im += Ki rr
+                }
+                umma_commit(smem_u32(&empty[slot]));
+            }
+            umma_commit(smem_u32(&tfull[a]));
+            ++j;
+            if (!ok) {
+                *vabort = 1;
+                atomicExch(ep.err, 1);
+                break;
+            }
+        }
+        umma_commit(smem_u32(done));
+        mbar_wait(smem_u32(done), 0);  // every MMA of this CTA has retired (bounded)
+    } else if (warp >= 2) {
+        // ---------------- epilogue (128 threads, one TMEM lane each) ----------------
+        const int et = tid - 64;
+        const int quarter = warp & 3;  // TMEM lanes this warp may access
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        __shared__ int s_fail;
+        if (et == 0) s_fail = 0;
+        epi_barrier();
+        uint32_t j = 0;
+        for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
+            const int64_t n_tile = tile / m_tiles;
+            const int m_tile = (int)(tile % m_tiles);
+            if (!tile_live(ep, n_tile)) continue;
+            const uint32_t a = j & 1, u = j >> 1;
+            if (ep.mode == 1) {
+                const int64_t t = n_tile * kTileN + et;
+                const int f = ep.flags[t];
+                col_flag[et] = f;
+                col_scale[et] = (f & kActive) ? pow2f_g(-ep.k_exp - ep.rexp[t]) : 0.0f;
+                col_dmax[et] = 0u;
+            }
+            if (!mbar_wait(smem_u32(&tfull[a]), u & 1)) atomicOr(&s_fail, 1);
+            epi_barrier();
+            if (s_fail) {
+                *vabort = 1;
+                atomicExch(ep.err, 1);
+                break;
+            }
+            tc_fence_after();
+            const int m = m_tile * kTileM + row;
+            const uint32_t tacc = tmem + a * kAccCols + lane_off;
+            for (int cb = 0; cb < kTileN / 32; ++cb) {
+                uint32_t vr[32], vi[32];
+                tmem_ld32(tacc + cb * 32, vr);
+                tmem_ld32(tacc + kTileN + cb * 32, vi);
+                tmem_wait_ld();
+                if (ep.mode == 0) {
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int64_t nn = n_tile * kTileN + cb * 32 + q;
+                        ep.Dr[nn * ep.ldD + m] = __uint_as_float(vr[q]);
+                        ep.Di[nn * ep.ldD + m] = __uint_as_float(vi[q]);
+                    }
+                } else {
+                    // Update V of this lane's bus for 32 columns (loads first, then stores), then a
+                    // transposed butterfly: after 31 shuffles lane l holds max_rows |dV| of column
+                    // cb*32 + l.
+                    float2 old[32];
+                    float mag[32];
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int c = cb * 32 + q;
+                        const int f = col_flag[c];
+                        const bool act = (f & kActive) && m < ep.n;
+                        const int64_t k = (n_tile * kTileN + c) * ep.n_pad + m;
+                        const float2 *src = (f & kAnchored) ? ep.Vlo : ep.Vhi;  // anchored: V_ref fixed
+                        old[q] = act ? src[k] : make_float2(0.0f, 0.0f);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int c = cb * 32 + q;
+                        const int f = col_flag[c];
+                        const bool act = (f & kActive) && m < ep.n;
+                        const float sc = col_scale[c];
+                        const float dr = __uint_as_float(vr[q]) * sc, di = __uint_as_float(vi[q]) * sc;
+                        float dmag = 0.0f;
+                        if (act) {
+                            const int64_t k = (n_tile * kTileN + c) * ep.n_pad + m;
+                            float2 *dst = (f & kAnchored) ? ep.Vlo : ep.Vhi;
+                            dst[k] = make_float2(old[q].x + dr, old[q].y + di);
+                            dmag = sqrtf(dr * dr + di * di);
+                            if (dmag != dmag) dmag = __int_as_float(0x7f800000);  // NaN -> +inf
+                        }
+                        mag[q] = dmag;
+                    }
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) {
+                        const bool upper = (lane & off) != 0;
+#pragma unroll
+                        for (int jj = 0; jj < off; ++jj) {
+                            const float send = upper ? mag[jj] : mag[jj + off];
+                            const float keep = upper ? mag[jj + off] : mag[jj];
+                            mag[jj] = fmaxf(keep, __shfl_xor_sync(0xffffffffu, send, off));
+                        }
+                    }
+                    if (mag[0] > 0.0f) atomicMax(&col_dmax[cb * 32 + lane], __float_as_uint(mag[0]));
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&tempty[a]));  // accumulator stage a is free again
+            epi_barrier();
+            if (ep.mode == 1) {
+                const unsigned d = col_dmax[et];
+                if (d) atomicMax(&ep.delta[n_tile * kTileN + et], d);
+            }
+            epi_barrier();  // column info is rewritten by the next tile
+            ++j;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    }
+    return fn;
+}
+
+// A [rows][inner] fp16 matrix read in (128 rows x 64 elements) boxes, 128-byte swizzle.
+bool make_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {inner * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileM};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+bool make_gemm_maps(GemmMaps *maps, const void *Ar, const void *Ai, int M, int K, const void *Br, const void *Bi,
+                    int64_t N) {
+    return make_map(&maps->ar, Ar, K, M) && make_map(&maps->ai, Ai, K, M) && make_map(&maps->br, Br, K, N) &&
+           make_map(&maps->bi, Bi, K, N);
+}
+
+tpf_status launch_gemm(const GemmMaps &maps, int m_tiles, int64_t n_tiles, int n_chunks, const GemmEpi &ep,
+                       cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem) != cudaSuccess) {
+            cudaGetLastError();
+            return TPF_ECUDA;
+        }
+        attr = true;
+    }
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return TPF_ECUDA;
+    }
+    const int64_t total = (int64_t)m_tiles * n_tiles;
+    const unsigned grid = (unsigned)(total < sms ? total : sms);
+    tc_gemm<<<grid, kGemmThreads, kGemmSmem, st>>>(maps.ar, maps.ai, maps.br, maps.bi, m_tiles, n_tiles, n_chunks, ep);
+    if (cudaGetLastError() != cudaSuccess) return TPF_ECUDA;
+    return TPF_OK;
+}
+
+}  // namespace tpf

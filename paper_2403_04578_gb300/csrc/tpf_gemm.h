@@ -1,0 +1,37 @@
+// The tensor-core complex GEMM of the mixed path (tpf_gemm.cu).
+#pragma once
+
+#include <cuda.h>
+
+#include "tpf_internal.h"
+
+namespace tpf {
+
+// What the GEMM epilogue does with D = A B^T (one 128 x 128 tile per accumulator stage).
+struct GemmEpi {
+    int mode;  // 0 = store D (self-test), 1 = fixed-point update of V
+    int *err;  // set to 1 when a bounded wait expires
+    // mode 0: D[n][m] in two FP32 planes with leading dimension ldD (= M)
+    float *Dr, *Di;
+    int ldD;
+    // mode 1: V += 2^-(k_exp + rexp[col]) D for iterating columns, max |dV| per column into delta
+    int n, n_pad, k_exp;
+    const int *flags, *rexp, *tile_active;
+    float2 *Vhi, *Vlo;
+    unsigned *delta;
+};
+
+// Tensor maps of the four fp16 operand planes: A (K) [M][K] and B (rho) [N][K], K fastest.
+struct GemmMaps {
+    CUtensorMap ar, ai, br, bi;
+};
+
+bool make_gemm_maps(GemmMaps *maps, const void *Ar, const void *Ai, int M, int K, const void *Br, const void *Bi,
+                    int64_t N);
+
+// D = A B^T over complex numbers for all (m_tiles x n_tiles) tiles of 128 x 128, K = 64 n_chunks,
+// by one persistent CTA per SM.  In mode 1, tiles whose tile_active entry is 0 are skipped.
+tpf_status launch_gemm(const GemmMaps &maps, int m_tiles, int64_t n_tiles, int n_chunks, const GemmEpi &ep,
+                       cudaStream_t st);
+
+}  // namespace tpf

@@ -168,6 +168,51 @@ tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_
 tpf_status tpf_last_stats(const tpf_handle *h, tpf_stats *out);
 
 /*
+ * Learned warm start.  The paper starts Algorithm 1 from the flat profile V_0 = 1; these entry
+ * points train and run a small multilayer perceptron that predicts V_0 from a column's loads, so
+ * that a solve started from it (TPF_START_GIVEN) needs fewer sweeps.  The iteration still decides
+ * the result: it converges to the same high-voltage solution from any start (Sec. III).
+ *
+ * Network: inputs P_1..P_n, Q_1..Q_n (real and imaginary parts of a column of S), z-scored per
+ * feature; n_hidden_layers hidden layers of `hidden` units with the erf GELU; linear outputs
+ * Re V_i - 1, Im V_i, z-scored.  Loss: mean squared error.  Optimiser: Adam (beta 0.9, 0.999,
+ * eps 1e-8).  Every product runs on the tensor cores in BF16 with FP32 accumulation; weights are
+ * kept in FP32 (Xavier-uniform initialisation from `seed`, zero biases).  Buffers are sized for
+ * batches of up to max_batch columns (a positive multiple of 128).
+ */
+typedef struct tpf_mlp tpf_mlp;
+
+tpf_status tpf_mlp_create(int n_pq, int hidden, int n_hidden_layers, int max_batch, uint64_t seed,
+                          tpf_mlp **out);
+void tpf_mlp_destroy(tpf_mlp *h);
+/* Number of parameters: per layer W (out x in) then b (out). */
+int64_t tpf_mlp_param_count(const tpf_mlp *h);
+/* Parameters as one flat FP32 host array in the order above (get: copy out; set: copy in). */
+tpf_status tpf_mlp_get_params(tpf_mlp *h, float *host);
+tpf_status tpf_mlp_set_params(tpf_mlp *h, const float *host);
+/* Per-feature and per-target mean and standard deviation over T training columns
+ * (S_dev, V_dev: device complex128 [T][n_pq], V the solved voltages).  Must precede training. */
+tpf_status tpf_mlp_fit_normalization(tpf_mlp *h, int64_t T, const void *S_dev, const void *V_dev,
+                                     void *stream);
+/* The fitted statistics, 2 n_pq floats each (host). */
+tpf_status tpf_mlp_get_normalization(tpf_mlp *h, float *in_mean, float *in_std, float *out_mean,
+                                     float *out_std);
+/* One Adam step on a batch of B columns (B a multiple of 128, <= max_batch): S_dev and V_dev are
+ * device complex128 [B][n_pq].  loss_out (host, may be NULL) receives the batch loss before the
+ * step; with loss_out the call waits for the stream, otherwise it only enqueues work. */
+tpf_status tpf_mlp_train_step(tpf_mlp *h, int B, const void *S_dev, const void *V_dev, double lr,
+                              double *loss_out, void *stream);
+/* Loss and gradients of the current parameters on a batch (no update); grads_host (may be NULL)
+ * receives them in the parameter order.  Blocks. */
+tpf_status tpf_mlp_gradients(tpf_mlp *h, int B, const void *S_dev, const void *V_dev,
+                             double *loss_out, float *grads_host, void *stream);
+/* Predicted V_0 for T columns (device complex128 [T][n_pq] in and out).  A column whose predicted
+ * |V_i| leaves [0.7, 1.1] at any bus gets the flat start; fallback_out (host, may be NULL)
+ * receives how many.  Blocks. */
+tpf_status tpf_mlp_predict(tpf_mlp *h, int64_t T, const void *S_dev, void *V0_dev,
+                           int64_t *fallback_out, void *stream);
+
+/*
  * Allocation-free FP64 solve.  The paper has no counterpart to this entry point; it exists for
  * callers that must not allocate device memory themselves or have the library do it: runtimes
  * that hand out device memory only from their own pool (raw cudaMalloc/cudaFree would escape

@@ -167,5 +167,9 @@ struct PrologueArgs {
 
 // Launch the residual kernel of one sweep (tpf_residual.cu).
 tpf_status launch_residual(const PrologueArgs &a, cudaStream_t st);
+// Final outputs of a solve: V (complex128 [T][n]), iteration counts, mismatch, and the converged
+// columns counted per 128-column tile into tile_done (zeroed by the caller).
+tpf_status launch_final(const PrologueArgs &a, int64_t T, void *V_out, int32_t *iters_out, double *mismatch_out,
+                        int *tile_done, cudaStream_t st);
 
 }  // namespace tpf

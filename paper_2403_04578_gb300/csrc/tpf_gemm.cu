@@ -15,20 +15,28 @@
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
 
+#include <cstring>
+
 #include "tpf_gemm.h"
 
 namespace tpf {
 
 namespace {
 
-constexpr int kStages = 3;
-constexpr uint32_t kTileBytes = kTileM * kChunkK * 2;  // 16 KB: 128 rows x 64 fp16
-constexpr uint32_t kStageBytes = 4 * kTileBytes;        // Ar, Ai, Br, Bi
+constexpr uint32_t kTileBytes = kTileM * kChunkK * 2;  // 16 KB: 128 rows x 64 16-bit elements
 constexpr uint64_t kWaitNs = 2000000000ull;             // bounded waits: 2 s
-constexpr uint32_t kAccCols = 256;                      // one stage: Re cols [0,128), Im [128,256)
-constexpr uint32_t kTmemCols = 512;                     // two stages
 constexpr int kGemmThreads = 192;                       // 6 warps
-constexpr size_t kGemmSmem = 1024 + kStages * kStageBytes + 2048;
+constexpr size_t kGemmSmem = 1024 + 192 * 1024 + 2048;  // align slack + operand ring + barriers
+
+// Complex products stream four planes per K chunk (Ar, Ai, Br, Bi) into 3 slots and keep two
+// accumulators (Re, Im) per TMEM stage; real products stream two planes into 6 slots.
+template <bool CPLX>
+struct Cfg {
+    static constexpr int kStages = CPLX ? 3 : 6;
+    static constexpr uint32_t kStageBytes = (CPLX ? 4 : 2) * kTileBytes;
+    static constexpr uint32_t kAccCols = CPLX ? 256 : 128;  // one stage: Re [0,128), Im [128,256)
+    static constexpr uint32_t kTmemCols = 2 * kAccCols;     // two stages
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -80,9 +88,11 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
     return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
            ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
 }
-// Instruction descriptor of kind::f16 with fp16 A and B, FP32 accumulation, both K-major.
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int negA) {
-    return (1u << 4) | ((uint32_t)negA << 13) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+// Instruction descriptor of kind::f16: A and B both fp16 (fmt 0) or both bf16 (fmt 1), FP32
+// accumulation, both K-major.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N, int negA, uint32_t fmt) {
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)negA << 13) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
 }
 __device__ __forceinline__ void umma_f16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
     asm volatile(
@@ -120,10 +130,14 @@ __device__ __forceinline__ bool tile_live(const GemmEpi &ep, int64_t n_tile) {
     return ep.mode != 1 || ep.tile_active[n_tile] != 0;
 }
 
+template <bool CPLX>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_gemm(const __grid_constant__ CUtensorMap tmAr, const __grid_constant__ CUtensorMap tmAi,
             const __grid_constant__ CUtensorMap tmBr, const __grid_constant__ CUtensorMap tmBi, int m_tiles,
             int64_t n_tiles, int n_chunks, GemmEpi ep) {
+    using C = Cfg<CPLX>;
+    constexpr int kStages = C::kStages;
+    constexpr uint32_t kStageBytes = C::kStageBytes, kAccCols = C::kAccCols, kTmemCols = C::kTmemCols;
     extern __shared__ uint8_t smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -186,10 +200,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 const uint32_t bar = smem_u32(&full[slot]);
                 mbar_expect_tx(bar, kStageBytes);
                 const int k = c * kChunkK;
-                tma_load_2d(st, &tmAr, bar, k, m0);
-                tma_load_2d(st + kTileBytes, &tmAi, bar, k, m0);
-                tma_load_2d(st + 2 * kTileBytes, &tmBr, bar, k, n0);
-                tma_load_2d(st + 3 * kTileBytes, &tmBi, bar, k, n0);
+                if constexpr (CPLX) {
+                    tma_load_2d(st, &tmAr, bar, k, m0);
+                    tma_load_2d(st + kTileBytes, &tmAi, bar, k, m0);
+                    tma_load_2d(st + 2 * kTileBytes, &tmBr, bar, k, n0);
+                    tma_load_2d(st + 3 * kTileBytes, &tmBi, bar, k, n0);
+                } else {
+                    tma_load_2d(st, &tmAr, bar, k, m0);
+                    tma_load_2d(st + kTileBytes, &tmBr, bar, k, n0);
+                }
             }
         }
         if (*vabort) {  // let this CTA's copies in flight land before it leaves (bounded)
@@ -199,7 +218,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
         const uint32_t sbase = smem_u32(smem);
-        const uint32_t id_pos = idesc_f16(kTileM, kTileN, 0), id_neg = idesc_f16(kTileM, kTileN, 1);
+        const uint32_t fmt = ep.bf16 ? 1u : 0u;
+        const uint32_t id_pos = idesc_f16(kTileM, kTileN, 0, fmt), id_neg = idesc_f16(kTileM, kTileN, 1, fmt);
         int64_t g = 0;
         uint32_t j = 0;  // tiles processed by this CTA
         for (int64_t tile = blockIdx.x; tile < total && !*vabort; tile += gridDim.x) {
@@ -223,14 +243,20 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 const uint32_t st = sbase + slot * kStageBytes;
 #pragma unroll
                 for (int kk = 0; kk < kChunkK / 16; ++kk) {
-                    const uint64_t ar = sw128_desc(st + kk * 32), ai = sw128_desc(st + kTileBytes + kk * 32);
-                    const uint64_t br = sw128_desc(st + 2 * kTileBytes + kk * 32);
-                    const uint64_t bi = sw128_desc(st + 3 * kTileBytes + kk * 32);
                     const uint32_t first = (c | kk) != 0;
-                    umma_f16(tDr, ar, br, id_pos, first);  // Re += Kr rr
-                    umma_f16(tDr, ai, bi, id_neg, 1u);     // Re -= Ki ri
-                    umma_f16(tDi, ar, bi, id_pos, first);  // Im += Kr ri
-                    umma_f16(tDi, ai, br, id_pos, 1u);     // Im += Ki rr
+                    if constexpr (CPLX) {
+                        const uint64_t ar = sw128_desc(st + kk * 32), ai = sw128_desc(st + kTileBytes + kk * 32);
+                        const uint64_t br = sw128_desc(st + 2 * kTileBytes + kk * 32);
+                        const uint64_t bi = sw128_desc(st + 3 * kTileBytes + kk * 32);
+                        umma_f16(tDr, ar, br, id_pos, first);  // Re += Kr rr
+                        umma_f16(tDr, ai, bi, id_neg, 1u);     // Re -= Ki ri
+                        umma_f16(tDi, ar, bi, id_pos, first);  // Im += Kr ri
+                        umma_f16(tDi, ai, br, id_pos, 1u);     // Im += Ki rr
+                    } else {
+                        (void)id_neg;
+                        (void)tDi;
+                        umma_f16(tDr, sw128_desc(st + kk * 32), sw128_desc(st + kTileBytes + kk * 32), id_pos, first);
+                    }
                 }
                 umma_commit(smem_u32(&empty[slot]));
             }
@@ -279,16 +305,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             for (int cb = 0; cb < kTileN / 32; ++cb) {
                 uint32_t vr[32], vi[32];
                 tmem_ld32(tacc + cb * 32, vr);
-                tmem_ld32(tacc + kTileN + cb * 32, vi);
+                if constexpr (CPLX) tmem_ld32(tacc + kTileN + cb * 32, vi);
                 tmem_wait_ld();
                 if (ep.mode == 0) {
 #pragma unroll
                     for (int q = 0; q < 32; ++q) {
                         const int64_t nn = n_tile * kTileN + cb * 32 + q;
                         ep.Dr[nn * ep.ldD + m] = __uint_as_float(vr[q]);
-                        ep.Di[nn * ep.ldD + m] = __uint_as_float(vi[q]);
+                        if constexpr (CPLX) ep.Di[nn * ep.ldD + m] = __uint_as_float(vi[q]);
                     }
-                } else {
+                } else if constexpr (CPLX) {
                     // Update V of this lane's bus for 32 columns (loads first, then stores), then a
                     // transposed butterfly: after 31 shuffles lane l holds max_rows |dV| of column
                     // cb*32 + l.
@@ -366,15 +392,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// A [rows][inner] fp16 matrix read in (128 rows x 64 elements) boxes, 128-byte swizzle.
-bool make_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows) {
+// A [rows][inner] 16-bit matrix read in (128 rows x 64 elements) boxes, 128-byte swizzle.
+bool make_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, bool bf16) {
     auto fn = encode_fn();
     if (!fn) return false;
     cuuint64_t dims[2] = {inner, rows};
     cuuint64_t strides[1] = {inner * 2};
     cuuint32_t box[2] = {(cuuint32_t)kChunkK, (cuuint32_t)kTileM};
     cuuint32_t estr[2] = {1, 1};
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+    return fn(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -382,21 +408,28 @@ bool make_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows)
 }  // namespace
 
 bool make_gemm_maps(GemmMaps *maps, const void *Ar, const void *Ai, int M, int K, const void *Br, const void *Bi,
-                    int64_t N) {
-    return make_map(&maps->ar, Ar, K, M) && make_map(&maps->ai, Ai, K, M) && make_map(&maps->br, Br, K, N) &&
-           make_map(&maps->bi, Bi, K, N);
+                    int64_t N, bool bf16) {
+    std::memset(maps, 0, sizeof(*maps));
+    if (!make_map(&maps->ar, Ar, K, M, bf16) || !make_map(&maps->br, Br, K, N, bf16)) return false;
+    if (Ai && !make_map(&maps->ai, Ai, K, M, bf16)) return false;
+    if (Bi && !make_map(&maps->bi, Bi, K, N, bf16)) return false;
+    return true;
 }
 
 tpf_status launch_gemm(const GemmMaps &maps, int m_tiles, int64_t n_tiles, int n_chunks, const GemmEpi &ep,
                        cudaStream_t st) {
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem) != cudaSuccess) {
+        if (cudaFuncSetAttribute(tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem) !=
+                cudaSuccess ||
+            cudaFuncSetAttribute(tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem) !=
+                cudaSuccess) {
             cudaGetLastError();
             return TPF_ECUDA;
         }
         attr = true;
     }
+    if (!ep.cplx && ep.mode != 0) return TPF_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();
@@ -404,7 +437,12 @@ tpf_status launch_gemm(const GemmMaps &maps, int m_tiles, int64_t n_tiles, int n
     }
     const int64_t total = (int64_t)m_tiles * n_tiles;
     const unsigned grid = (unsigned)(total < sms ? total : sms);
-    tc_gemm<<<grid, kGemmThreads, kGemmSmem, st>>>(maps.ar, maps.ai, maps.br, maps.bi, m_tiles, n_tiles, n_chunks, ep);
+    if (ep.cplx)
+        tc_gemm<true><<<grid, kGemmThreads, kGemmSmem, st>>>(maps.ar, maps.ai, maps.br, maps.bi, m_tiles, n_tiles,
+                                                             n_chunks, ep);
+    else
+        tc_gemm<false><<<grid, kGemmThreads, kGemmSmem, st>>>(maps.ar, maps.ai, maps.br, maps.bi, m_tiles, n_tiles,
+                                                              n_chunks, ep);
     if (cudaGetLastError() != cudaSuccess) return TPF_ECUDA;
     return TPF_OK;
 }

@@ -9,7 +9,9 @@ namespace tpf {
 
 // What the GEMM epilogue does with D = A B^T (one 128 x 128 tile per accumulator stage).
 struct GemmEpi {
-    int mode;  // 0 = store D (self-test), 1 = fixed-point update of V
+    int mode;  // 0 = store D (FP32), 1 = fixed-point update of V (complex only)
+    int cplx;  // 1: A, B, D complex (four real-plane MMAs per K step); 0: real (one MMA)
+    int bf16;  // operand format: 0 = fp16, 1 = bf16
     int *err;  // set to 1 when a bounded wait expires
     // mode 0: D[n][m] in two FP32 planes with leading dimension ldD (= M)
     float *Dr, *Di;
@@ -26,11 +28,13 @@ struct GemmMaps {
     CUtensorMap ar, ai, br, bi;
 };
 
+// Ai, Bi may be null for a real product.  bf16 selects the element type of the maps.
 bool make_gemm_maps(GemmMaps *maps, const void *Ar, const void *Ai, int M, int K, const void *Br, const void *Bi,
-                    int64_t N);
+                    int64_t N, bool bf16 = false);
 
-// D = A B^T over complex numbers for all (m_tiles x n_tiles) tiles of 128 x 128, K = 64 n_chunks,
-// by one persistent CTA per SM.  In mode 1, tiles whose tile_active entry is 0 are skipped.
+// D = A B^T (complex or real, per ep.cplx) for all (m_tiles x n_tiles) tiles of 128 x 128,
+// K = 64 n_chunks, by one persistent CTA per SM.  In mode 1, tiles whose tile_active entry is 0
+// are skipped.
 tpf_status launch_gemm(const GemmMaps &maps, int m_tiles, int64_t n_tiles, int n_chunks, const GemmEpi &ep,
                        cudaStream_t st);
 

@@ -77,41 +77,6 @@ __global__ void mx_pack(int64_t T, int n, int n_pad, const double2 *__restrict__
     }
 }
 
-// Final outputs: V (complex128) from double-float, iteration counts, and the power mismatch
-// max_i |V_i conj((Y v)_i) + S_i| = max_i |V_i| |rho_i| evaluated in double-float.
-__global__ void __launch_bounds__(256) mx_finish(int64_t T, int n, int n_pad, int max_iter, const int *flags,
-                                                 const int *it_state, const float2 *Vhi, const float2 *Vlo,
-                                                 const float2 *Shi, const float2 *Slo, const int *row_ptr,
-                                                 const int *nbr, const float4 *y, c2 vs, double2 *V_out,
-                                                 int32_t *iters_out, double *mismatch_out, int *tile_done) {
-    const int lane = threadIdx.x & 31;
-    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (t >= T) return;
-    const int64_t base = t * n_pad;
-    if (lane == 0) {
-        const bool done = (flags[t] & kDone) != 0;
-        if (iters_out) iters_out[t] = done ? it_state[t] : -max_iter;
-        if (done) atomicAdd(&tile_done[t / kTileN], 1);  // converged columns per 128-column tile
-    }
-    float worst = 0.0f;
-    for (int i = lane; i < n; i += 32) {
-        float2 h = Vhi[base + i], l = Vlo[base + i];
-        V_out[t * n + i] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
-        if (mismatch_out) {
-            c2 r = residual_dd(i, Vhi + base, Vlo + base, Shi + base, Slo + base, row_ptr, nbr, y, vs);
-            float mv = sqrtf(h.x * h.x + h.y * h.y) * sqrtf(r.re.h * r.re.h + r.im.h * r.im.h);
-            if (!(mv <= worst)) worst = mv;
-        }
-    }
-    if (!mismatch_out) return;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        float other = __shfl_xor_sync(0xffffffffu, worst, o);
-        if (!(other <= worst)) worst = other;
-    }
-    if (lane == 0) mismatch_out[t] = (double)worst;
-}
-
 }  // namespace
 
 tpf_status selftest_gemm(int M, int N, int K, const void *Ar, const void *Ai, const void *Br, const void *Bi, float *Dr,
@@ -123,6 +88,7 @@ tpf_status selftest_gemm(int M, int N, int K, const void *Ar, const void *Ai, co
     TPF_CK(cudaMemsetAsync(err, 0, sizeof(int), st));
     GemmEpi ep{};
     ep.mode = 0;
+    ep.cplx = 1;
     ep.err = err;
     ep.Dr = Dr;
     ep.Di = Di;
@@ -201,6 +167,7 @@ tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t
 
     GemmEpi ep{};
     ep.mode = 1;
+    ep.cplx = 1;
     ep.err = w.counters + kCntError;
     ep.n = n;
     ep.n_pad = n_pad;
@@ -243,13 +210,10 @@ tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t
     }
     TPF_CK(cudaMemsetAsync(w.tile_active, 0, sizeof(int) * n_tiles, st));  // reused: converged per tile
     timer.begin(KernelTimer::kOther);
-    mx_finish<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(T, n, n_pad, o.max_iter, w.flags, w.iters, w.Vhi,
-                                                               w.Vlo, w.Shi, w.Slo, h->dev.row_ptr, h->dev.nbr,
-                                                               h->dev.y2f, pa.vs_dd, (double2 *)V, iters, mismatch,
-                                                               w.tile_active);
+    rs = launch_final(pa, T, V, iters, mismatch, w.tile_active, st);
     timer.end();
+    if (rs != TPF_OK) return rs;
     ++launches;
-    TPF_CK(cudaGetLastError());
     TPF_CK(cudaMemcpyAsync(w.counters_host, w.counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
     TPF_CK(cudaMemcpyAsync(tile_host.data(), w.tile_active, sizeof(int) * n_tiles, cudaMemcpyDeviceToHost, st));
     TPF_CK(cudaStreamSynchronize(st));

@@ -22,6 +22,9 @@ START_FLAT, START_GIVEN = 0, 1
 EXPORTS = (
     "tpf_default_opts", "tpf_strerror", "tpf_create", "tpf_destroy", "tpf_n_pq", "tpf_precompute_host",
     "tpf_solve", "tpf_solve_host", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
+    "tpf_mlp_create", "tpf_mlp_destroy", "tpf_mlp_param_count", "tpf_mlp_get_params", "tpf_mlp_set_params",
+    "tpf_mlp_fit_normalization", "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients",
+    "tpf_mlp_predict",
 )
 
 # Size of the built-in scratch array of tpf_solve_fp64_noalloc (include/tpf.h).
@@ -94,6 +97,23 @@ def lib(build_if_missing: bool = False):
     L.tpf_solve_fp64_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int64, vp, vp, vp, ctypes.c_double,
                                          ctypes.c_int, ctypes.c_int, vp]
     L.tpf_solve_fp64_noalloc.restype = ctypes.c_int
+    f32p = ctypes.POINTER(ctypes.c_float)
+    L.tpf_mlp_create.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64,
+                                 ctypes.POINTER(vp)]
+    L.tpf_mlp_destroy.argtypes = [vp]
+    L.tpf_mlp_destroy.restype = None
+    L.tpf_mlp_param_count.argtypes = [vp]
+    L.tpf_mlp_param_count.restype = ctypes.c_int64
+    L.tpf_mlp_get_params.argtypes = [vp, f32p]
+    L.tpf_mlp_set_params.argtypes = [vp, f32p]
+    L.tpf_mlp_fit_normalization.argtypes = [vp, ctypes.c_int64, vp, vp, vp]
+    L.tpf_mlp_get_normalization.argtypes = [vp, f32p, f32p, f32p, f32p]
+    L.tpf_mlp_train_step.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp]
+    L.tpf_mlp_gradients.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_double), f32p, vp]
+    L.tpf_mlp_predict.argtypes = [vp, ctypes.c_int64, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]
+    for name in ("tpf_mlp_create", "tpf_mlp_get_params", "tpf_mlp_set_params", "tpf_mlp_fit_normalization",
+                 "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients", "tpf_mlp_predict"):
+        getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
 
@@ -284,3 +304,105 @@ def selftest_gemm(Ar, Ai, Br, Bi, stream=None):
     if st != OK:
         raise TpfError(st, "tpf_selftest_gemm")
     return Dr, Di
+
+
+class LearnedStart:
+    """The learned warm-start network of libtpf (tpf_mlp_*): BF16 tensor-core training and inference.
+
+    Inputs are a column's loads (P then Q of the n demand buses), outputs Re V - 1 and Im V; both
+    z-scored with statistics fitted on training columns.  All arithmetic runs in libtpf's kernels.
+    """
+
+    def __init__(self, n_pq, hidden=256, hidden_layers=3, max_batch=1024, seed=1):
+        h = ctypes.c_void_p()
+        st = lib().tpf_mlp_create(int(n_pq), int(hidden), int(hidden_layers), int(max_batch), int(seed),
+                                  ctypes.byref(h))
+        if st != OK:
+            raise TpfError(st, "tpf_mlp_create")
+        self._h = h
+        self.n_pq = int(n_pq)
+        self.max_batch = int(max_batch)
+        self.sizes = [2 * n_pq] + [hidden] * hidden_layers + [2 * n_pq]
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tpf_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _f32(a):
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+    def params(self):
+        """Flat FP32 parameters: per layer W (out x in, row-major) then b."""
+        out = np.empty(lib().tpf_mlp_param_count(self._h), dtype=np.float32)
+        st = lib().tpf_mlp_get_params(self._h, self._f32(out))
+        if st != OK:
+            raise TpfError(st, "tpf_mlp_get_params")
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        st = lib().tpf_mlp_set_params(self._h, self._f32(flat))
+        if st != OK:
+            raise TpfError(st, "tpf_mlp_set_params")
+
+    def unflatten(self, flat):
+        Ws, bs, off = [], [], 0
+        for i in range(len(self.sizes) - 1):
+            o, k = self.sizes[i + 1], self.sizes[i]
+            Ws.append(flat[off:off + o * k].reshape(o, k))
+            off += o * k
+            bs.append(flat[off:off + o])
+            off += o
+        return Ws, bs
+
+    def fit_normalization(self, S, V, stream=None):
+        st = lib().tpf_mlp_fit_normalization(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()),
+                                             ctypes.c_void_p(V.data_ptr()), _stream_ptr(stream))
+        if st != OK:
+            raise TpfError(st, "tpf_mlp_fit_normalization")
+
+    def normalization(self):
+        a = [np.empty(2 * self.n_pq, dtype=np.float32) for _ in range(4)]
+        st = lib().tpf_mlp_get_normalization(self._h, *(self._f32(x) for x in a))
+        if st != OK:
+            raise TpfError(st, "tpf_mlp_get_normalization")
+        return tuple(a)
+
+    def train_step(self, S, V, lr=1e-3, want_loss=True, stream=None):
+        loss = ctypes.c_double(0.0)
+        st = lib().tpf_mlp_train_step(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()),
+                                      ctypes.c_void_p(V.data_ptr()), float(lr),
+                                      ctypes.byref(loss) if want_loss else None, _stream_ptr(stream))
+        if st != OK:
+            raise TpfError(st, "tpf_mlp_train_step")
+        return loss.value if want_loss else None
+
+    def gradients(self, S, V, stream=None):
+        loss = ctypes.c_double(0.0)
+        g = np.empty(lib().tpf_mlp_param_count(self._h), dtype=np.float32)
+        st = lib().tpf_mlp_gradients(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                                     ctypes.byref(loss), self._f32(g), _stream_ptr(stream))
+        if st != OK:
+            raise TpfError(st, "tpf_mlp_gradients")
+        return loss.value, g
+
+    def predict(self, S, V0=None, stream=None):
+        """Predicted starting voltages (complex128 CUDA tensor like S) and the fallback count."""
+        import torch
+
+        if V0 is None:
+            V0 = torch.empty_like(S)
+        fb = ctypes.c_int64(0)
+        st = lib().tpf_mlp_predict(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V0.data_ptr()),
+                                   ctypes.byref(fb), _stream_ptr(stream))
+        if st != OK:
+            raise TpfError(st, "tpf_mlp_predict")
+        return V0, fb.value

@@ -1,0 +1,133 @@
+"""The learned warm start on the GPU: BF16 tensor-core gradients against the FP64 reference, training,
+and what the trained network saves the fixed-point iteration.
+
+Tolerances: the GPU runs every product in BF16 (8-bit significand) with FP32 accumulation, so its
+gradient is compared with the FP64 reference (same weights, same normalised batch) by relative L2
+error <= 3e-2 and cosine similarity >= 0.999; the loss within 2 %.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as OM
+from oracle import oracle as O
+from paper_2403_04578_gb300 import inputs as G
+from paper_2403_04578_gb300 import tpf
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _features(S):
+    return np.concatenate([S.real, S.imag], axis=1)
+
+
+def _targets(V):
+    return np.concatenate([V.real - 1.0, V.imag], axis=1)
+
+
+def _zscore_stats(A):
+    mu = A.mean(axis=0)
+    sd = A.std(axis=0)
+    return mu, sd
+
+
+def _norm(A, mu, sd):
+    return np.where(sd > 0, (A - mu) / np.where(sd > 0, sd, 1.0), 0.0)
+
+
+@pytest.fixture(scope="module")
+def feeder200():
+    f = G.make_feeder(200, 5)
+    c = O.Case.from_feeder(f)
+    return f, c
+
+
+def test_gradients_match_the_fp64_reference(cuda, feeder200):
+    f, c = feeder200
+    S = G.load_tensor(f, 4096, 5)[::32][:128]  # 128 columns spread over the day
+    V, it, _ = c.solve(S, tol=1e-12)
+    assert (it > 0).all()
+    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=128, seed=3)
+    Sd, Vd = _dev(S), _dev(V)
+    net.fit_normalization(Sd, Vd)
+    X, Y = _features(S), _targets(V)
+    xm, xs = _zscore_stats(X)
+    ym, ys = _zscore_stats(Y)
+    gm, gs, hm, hs = net.normalization()
+    assert np.allclose(gm, xm, rtol=1e-5, atol=1e-9) and np.allclose(gs, xs, rtol=1e-4, atol=1e-9)
+    assert np.allclose(hm, ym, rtol=1e-5, atol=1e-9) and np.allclose(hs, ys, rtol=1e-4, atol=1e-9)
+    rng = np.random.default_rng(11)
+    sizes = net.sizes
+    Ws = [rng.uniform(-1, 1, (sizes[i + 1], sizes[i])) * np.sqrt(6.0 / (sizes[i] + sizes[i + 1]))
+          for i in range(len(sizes) - 1)]
+    bs = [rng.normal(0, 0.05, sizes[i + 1]) for i in range(len(sizes) - 1)]
+    flat = np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(Ws, bs)]).astype(np.float32)
+    net.set_params(flat)
+    assert np.array_equal(net.params(), flat)
+    loss_gpu, g_gpu = net.gradients(Sd, Vd)
+    ref = OM.MLP([w.astype(np.float32).astype(np.float64) for w in Ws], [b.astype(np.float32) for b in bs])
+    loss_ref, gW, gb = ref.gradients(_norm(X, xm, xs), _norm(Y, ym, ys))
+    g_ref = np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(gW, gb)])
+    assert loss_gpu == pytest.approx(loss_ref, rel=2e-2)
+    rel = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
+    cos = float(g_gpu @ g_ref / (np.linalg.norm(g_gpu) * np.linalg.norm(g_ref)))
+    assert rel <= 3e-2, rel
+    assert cos >= 0.999, cos
+    net.close()
+
+
+def test_training_reduces_the_loss(cuda, feeder200):
+    f, c = feeder200
+    S = G.load_tensor(f, 4096, 6)
+    V, it, _ = c.solve(S, tol=1e-12)
+    Sd, Vd = _dev(S), _dev(V)
+    net = tpf.LearnedStart(f.n_pq, max_batch=1024, seed=4)
+    net.fit_normalization(Sd, Vd)
+    first = None
+    last = []
+    for step in range(400):
+        k = (step % 4) * 1024
+        loss = net.train_step(Sd[k:k + 1024], Vd[k:k + 1024], lr=1e-3)
+        first = loss if first is None else first
+        last.append(loss)
+    assert np.isfinite(last).all()
+    assert np.mean(last[-8:]) < 0.02 * first
+    net.close()
+
+
+def test_learned_start_saves_sweeps(cuda, feeder200):
+    """Trained on GPU-solved columns of one load draw, evaluated on unseen columns of another."""
+    import torch
+
+    f, c = feeder200
+    fd = tpf.Feeder.from_inputs(f)
+    S_tr = _dev(G.load_tensor(f, 16384, 21))
+    V_tr, _, _, st = fd.solve(S_tr, precision="mixed", tol=1e-10)
+    assert st == tpf.OK
+    net = tpf.LearnedStart(f.n_pq, max_batch=1024, seed=5)
+    net.fit_normalization(S_tr, V_tr)
+    for epoch in range(25):
+        for k in range(0, 16384, 1024):
+            net.train_step(S_tr[k:k + 1024], V_tr[k:k + 1024], lr=1e-3, want_loss=False)
+    S_np = G.load_tensor(f, 4096, 22)
+    S_ev = _dev(S_np)
+    V0, fallback = net.predict(S_ev)
+    assert fallback == 0
+    Vo, _, _ = c.solve(S_np, tol=1e-13)
+    start_err = np.abs(V0.cpu().numpy() - Vo).max()
+    flat_err = np.abs(1.0 - Vo).max()
+    assert start_err < 0.1 * flat_err, (start_err, flat_err)
+    V_l, it_l, _, st_l = fd.solve(S_ev, V=V0.clone(), precision="mixed", tol=1e-10)
+    V_f, it_f, _, st_f = fd.solve(S_ev, precision="mixed", tol=1e-10)
+    assert st_l == tpf.OK and st_f == tpf.OK
+    assert np.abs(V_l.cpu().numpy() - Vo).max() <= 1e-8
+    assert np.abs(V_f.cpu().numpy() - Vo).max() <= 1e-8
+    assert it_l.float().mean().item() < it_f.float().mean().item() - 1.0
+    net.close()
+    fd.close()
+    torch.cuda.synchronize()

@@ -15,6 +15,7 @@ Reported on one JSON line (rank 0):
               over its CUDA-event time inside the timed steps, against the measured bf16 peak
               (fp16 runs at the bf16 rate)
   fp64_gpu    the plain FP64 GPU fixed-point iteration (direct form), timed on a column sample
+  sparse_method the sparse formulation (Algorithm 2, tree substitution) on the same workload
   cpu_baseline the CPU oracle on the host cores, on a bounded column sample; the same leg checks
               the GPU result against the oracle (iterated to 1e-13) on sampled columns
   clocks      nvidia-smi samples taken during the timed region
@@ -60,6 +61,8 @@ def parse_args():
     p.add_argument("--check-columns", type=int, default=256)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--no-sparse", action="store_true")
     return p.parse_args()
 
 
@@ -172,7 +175,7 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_leg(f, S_host, V_gpu_host, it_gpu, args, full_T):
+def cpu_oracle_leg(f, S_host, V_gpu_host, it_gpu, args, full_T, V_sparse_host=None):
     """Time the CPU oracle on a bounded column sample and check GPU results against it."""
     from oracle import oracle as O
 
@@ -202,7 +205,87 @@ def cpu_oracle_leg(f, S_host, V_gpu_host, it_gpu, args, full_T):
         check = {"max_abs_err_pu": err, "columns_checked": int(cc.size),
                  "iters_equal_frac": float(np.mean(it_gpu[cc] == it_ref)),
                  "iters_diff_max": int(np.abs(it_gpu[cc] - it_ref).max())}
+        if V_sparse_host is not None:
+            check["sparse_max_abs_err_pu"] = float(np.abs(V_sparse_host[cc] - Vt).max())
     return out, check
+
+
+def learned_start_leg(args, stream):
+    """Config 5: a 200-bus feeder, the network trained on 100,000 columns solved by the library, then
+    525,600 unseen columns solved from its prediction vs from the flat start (both mixed, tol as the
+    headline), and the plain FP64 GPU path from the flat start on a column sample."""
+    import torch
+
+    from paper_2403_04578_gb300 import inputs as G
+    from paper_2403_04578_gb300 import tpf
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f = G.make_feeder(200, args.seed)
+    fd = tpf.Feeder.from_inputs(f)
+    n_train, n_eval = 100_000, args.columns
+    S_tr = torch.from_numpy(G.load_tensor(f, n_train, args.seed + 100)).to(dev)
+    V_tr, _, _, st = fd.solve(S_tr, precision="mixed", tol=args.tol)
+    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=1024, seed=args.seed)
+    net.fit_normalization(S_tr, V_tr)
+    B = 1024
+    steps_per_epoch = n_train // B
+    epochs = 20
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    perm_gen = torch.Generator(device="cpu").manual_seed(args.seed)
+    for ep in range(epochs):
+        lr = 1e-3 * (0.5 * (1 + np.cos(np.pi * ep / epochs)) * 0.9 + 0.1)
+        order = torch.randperm(n_train, generator=perm_gen)[: steps_per_epoch * B].to(dev)
+        Sp, Vp = S_tr[order].contiguous(), V_tr[order].contiguous()
+        for k in range(steps_per_epoch):
+            net.train_step(Sp[k * B:(k + 1) * B], Vp[k * B:(k + 1) * B], lr=lr, want_loss=False)
+    loss = net.train_step(S_tr[:B], V_tr[:B], lr=1e-12)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    S_ev = torch.from_numpy(G.load_tensor(f, n_eval, args.seed + 200)).to(dev)
+    V = torch.empty_like(S_ev)
+    it = torch.empty(n_eval, dtype=torch.int32, device=dev)
+    mm = torch.empty(n_eval, dtype=torch.float64, device=dev)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    fb = [0]
+
+    def learned():
+        V0, fb[0] = net.predict(S_ev, V)
+        fd.solve(S_ev, V0, it, mm, precision="mixed", tol=args.tol, start="given")
+
+    ms_learned = timed(learned)
+    it_learned = it.float().mean().item()
+    V_learned = V.cpu().numpy()
+    ms_flat = timed(lambda: fd.solve(S_ev, V, it, mm, precision="mixed", tol=args.tol, start="flat"))
+    it_flat = it.float().mean().item()
+    F = min(args.fp64_sample, n_eval)
+    Sf = S_ev[:F].contiguous()
+    ms_fp64 = timed(lambda: fd.solve(Sf, precision="fp64", tol=args.tol), reps=2)
+    out = {
+        "workload": f"200-bus feeder, network 398-256-256-256-398 (GELU, BF16), trained {epochs} epochs on "
+                    f"{n_train:,} library-solved columns; evaluated on {n_eval:,} unseen columns",
+        "value": n_eval / (ms_learned / 1e3), "unit": "PF/s",
+        "flat_start_mixed": n_eval / (ms_flat / 1e3),
+        "plain_fp64_gpu": F / (ms_fp64 / 1e3),
+        "speedup_vs_plain_fp64": (n_eval / (ms_learned / 1e3)) / (F / (ms_fp64 / 1e3)),
+        "mean_sweeps_learned": it_learned, "mean_sweeps_flat": it_flat,
+        "fallback_columns": fb[0], "train_seconds": train_s, "final_batch_loss": loss,
+    }
+    fd.close()
+    net.close()
+    return out, f, S_ev, V_learned
 
 
 def run_reference(args, world, rank):
@@ -335,6 +418,27 @@ def main():
                "d2h_bytes_per_step": T * n * 16 + T * 4 + T * 8, "ms_per_step": dt * 1e3,
                "entry_point": "tpf_solve_host (pinned host buffers)"}
 
+    # The sparse formulation (Algorithm 2): tree substitution, one kernel for the whole solve.
+    sparse = None
+    Vsp = None
+    if not args.no_sparse:
+        fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat", method="sparse")
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat", method="sparse")
+        b.record(stream)
+        b.synchronize()
+        sp_ms = allmax(world, a.elapsed_time(b) / args.steps)
+        sparse = {"value": world * T / (sp_ms / 1e3), "unit": "PF/s", "ms_per_step": sp_ms,
+                  "kernel": "mx_tree", "gpu_launches_per_step": fd.stats()["kernel_launches"],
+                  "max_sweeps": fd.stats()["sweeps"], "converged": fd.stats()["converged"]}
+        if rank == 0 and not args.no_cpu:
+            Vsp = Vd.cpu().numpy()
+        fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat")  # dense result again
+
     # Plain FP64 GPU FPI on a column sample (the comparison path of the metric).
     F = min(args.fp64_sample, T)
     Sf = Sd[:F].contiguous()
@@ -357,13 +461,30 @@ def main():
             "e2e": e2e, "clocks": clocks.summary(), "gpu_launches": launches,
             "sweeps": stats["sweeps"], "anchor_sweeps": stats["precise_sweeps"],
             "fp64_gpu": fp64, "speedup_vs_fp64_gpu": (value / world) / fp64_pfs,
-            "learned_start": "not used on this workload (flat start); see the 200-bus learned-start benchmark"}
+            }
     if rank == 0 and not args.no_cpu:
         Vhost = Vd.cpu().numpy()
         ithost = itd.cpu().numpy()
-        cpu, check = cpu_oracle_leg(f, Sh.numpy(), Vhost, ithost, args, T)
+        cpu, check = cpu_oracle_leg(f, Sh.numpy(), Vhost, ithost, args, T, Vsp)
         line["cpu_baseline"] = cpu
+        if sparse is not None and "sparse_max_abs_err_pu" in check:
+            sparse["max_abs_err_pu"] = check.pop("sparse_max_abs_err_pu")
         line["accuracy"] = check
+    if sparse is not None:
+        line["sparse_method"] = sparse
+    if not args.no_learned:
+        del Sd, Vd
+        torch.cuda.empty_cache()
+        ls, f200, S_ev, V_ls = learned_start_leg(args, stream)
+        if rank == 0 and not args.no_cpu:
+            from oracle import oracle as O
+
+            cc = np.linspace(0, S_ev.shape[0] - 1, args.check_columns).astype(np.int64)
+            S_s = S_ev[torch.from_numpy(cc).to(S_ev.device)].cpu().numpy()
+            Vt, _, _ = O.Case.from_feeder(f200).solve(S_s, tol=1e-13, threads=os.cpu_count() or 1)
+            ls["max_abs_err_pu"] = float(np.abs(V_ls[cc] - Vt).max())
+            ls["columns_checked"] = int(cc.size)
+        line["learned_start"] = ls
     if rank == 0:
         print(json.dumps(line), flush=True)
     fd.close()

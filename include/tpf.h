@@ -73,7 +73,17 @@ typedef struct {
                        * add FP32 corrections in V - V_ref.  Default 1e-4                         */
     int profile;      /* nonzero: time every kernel of the solve with CUDA events on its stream  *
                        * and report the totals in tpf_stats.  Default 0                           */
+    int method;       /* TPF_METHOD_*.  Default TPF_METHOD_DENSE                                   */
 } tpf_opts;
+
+/* Formulation of a solve (both give the same iterates in exact arithmetic). */
+enum {
+    TPF_METHOD_DENSE = 0,  /* Algorithm 1 / Eq. 12: the dense product with K = -Y_dd^{-1}              */
+    TPF_METHOD_SPARSE = 1  /* Algorithm 2 / Eq. 13-14: a sparse solve with Y_dd each sweep, here the  *
+                            * fill-in-free tree substitution of a radial feeder, O(n) per column and  *
+                            * sweep, the whole sweep loop of a column on chip.  Radial networks and  *
+                            * TPF_PREC_MIXED only (TPF_EUNSUPPORTED otherwise)                       */
+};
 
 /* Per-solve counters (filled by tpf_last_stats after a solve). */
 typedef struct {

@@ -83,6 +83,15 @@ tpf_status upload_network(tpf_handle *h) {
         TPF_CK(cudaMemcpy(d.ch_ptr, net.ch_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
         if (nch > 0) TPF_CK(cudaMemcpy(d.ch, net.ch.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
         TPF_CK(cudaMemcpy(d.ypar, yp.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+        std::vector<float2> zp(n);
+        for (int i = 0; i < n; ++i) zp[i] = make_float2((float)net.zpar[2 * i], (float)net.zpar[2 * i + 1]);
+        TPF_CK(cudaMalloc(&d.zpar, sizeof(float2) * n));
+        TPF_CK(cudaMemcpy(d.zpar, zp.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+        d.depth = (int)net.lvl_ptr.size() - 1;
+        TPF_CK(cudaMalloc(&d.lvl_ptr, sizeof(int) * net.lvl_ptr.size()));
+        TPF_CK(cudaMalloc(&d.lvl_bus, sizeof(int) * (net.lvl_bus.empty() ? 1 : net.lvl_bus.size())));
+        TPF_CK(cudaMemcpy(d.lvl_ptr, net.lvl_ptr.data(), sizeof(int) * net.lvl_ptr.size(), cudaMemcpyHostToDevice));
+        TPF_CK(cudaMemcpy(d.lvl_bus, net.lvl_bus.data(), sizeof(int) * net.lvl_bus.size(), cudaMemcpyHostToDevice));
     }
     // fp16 planes of K * 2^k_exp with the largest component in [2^13, 2^14).
     double kmax = 0.0;
@@ -105,6 +114,7 @@ void free_device(tpf_handle *h) {
     cudaFree(d.K64); cudaFree(d.W64); cudaFree(d.row_ptr); cudaFree(d.nbr); cudaFree(d.y64); cudaFree(d.y2f);
     cudaFree(d.Kr16); cudaFree(d.Ki16);
     cudaFree(d.par); cudaFree(d.ch_ptr); cudaFree(d.ch); cudaFree(d.ypar);
+    cudaFree(d.zpar); cudaFree(d.lvl_ptr); cudaFree(d.lvl_bus);
     d = DeviceNet();
     Workspace &w = h->ws;
     cudaFree(w.Vhi); cudaFree(w.Vlo); cudaFree(w.Shi); cudaFree(w.Slo); cudaFree(w.Rr16); cudaFree(w.Ri16);
@@ -121,7 +131,8 @@ void free_device(tpf_handle *h) {
     cudaGetLastError();
 }
 
-tpf_status ensure_workspace(tpf_handle *h, int64_t cols, bool mixed) {
+tpf_status ensure_workspace(tpf_handle *h, int64_t cols, int kind) {
+    const bool mixed = kind == kWsMixed, fp64 = kind == kWsFp64;
     Workspace &w = h->ws;
     const int n = h->dev.n, n_pad = h->dev.n_pad;
     cols = round_up(cols, kTileN);
@@ -132,10 +143,10 @@ tpf_status ensure_workspace(tpf_handle *h, int64_t cols, bool mixed) {
         TPF_CK(cudaMallocHost(&w.counters_host, sizeof(int) * 8));
         TPF_CK(cudaMemset(w.counters, 0, sizeof(int) * 8));
     }
-    if (cols <= w.cap_cols && (mixed ? have_mixed : have_fp64)) return TPF_OK;
+    if (cols <= w.cap_cols && (mixed ? have_mixed : (fp64 ? have_fp64 : true))) return TPF_OK;
     int64_t cap = cols > w.cap_cols ? cols : w.cap_cols;
     bool want_mixed = mixed || (have_mixed && cap > w.cap_cols);
-    bool want_fp64 = !mixed || (have_fp64 && cap > w.cap_cols);
+    bool want_fp64 = fp64 || (have_fp64 && cap > w.cap_cols);
     if (cap > w.cap_cols) {
         cudaFree(w.delta_bits); cudaFree(w.delta64); cudaFree(w.iters); cudaFree(w.flags); cudaFree(w.rexp);
         cudaFree(w.tile_active); cudaFree(w.dprev);
@@ -361,7 +372,7 @@ __global__ void f64_finish(int64_t T, int n, int max_iter, const int *__restrict
 
 tpf_status solve_fp64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters, double *mismatch,
                       const tpf_opts &o, cudaStream_t st) {
-    tpf_status rs = ensure_workspace(h, T, false);
+    tpf_status rs = ensure_workspace(h, T, kWsFp64);
     if (rs != TPF_OK) return rs;
     Workspace &w = h->ws;
     const int n = h->dev.n;

@@ -188,6 +188,26 @@ tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int
         std::vector<int> fill(net.ch_ptr.begin(), net.ch_ptr.end() - 1);
         for (int i = 0; i < n; ++i)
             if (net.par[i] >= 0) net.ch[fill[net.par[i]]++] = i;
+        net.zpar.assign((size_t)2 * n, 0.0);
+        for (int i = 0; i < n; ++i) {
+            net.zpar[2 * i] = zpar[net.pq[i]].real();
+            net.zpar[2 * i + 1] = zpar[net.pq[i]].imag();
+        }
+        // Levels in breadth-first order (parents before children).
+        std::vector<int> depth(n_bus, 0);
+        net.lvl_ptr.assign(1, 0);
+        net.lvl_bus.clear();
+        int cur = 1;
+        for (size_t q = 1; q < order.size(); ++q) {
+            const int u = order[q];
+            depth[u] = depth[parent[u]] + 1;
+            while (depth[u] > cur) {
+                net.lvl_ptr.push_back((int)net.lvl_bus.size());
+                ++cur;
+            }
+            net.lvl_bus.push_back(net.pos[u]);
+        }
+        net.lvl_ptr.push_back((int)net.lvl_bus.size());
     }
     // Neighbour lists in column positions.
     net.row_ptr.assign(n + 1, 0);
@@ -218,6 +238,7 @@ void tpf_default_opts(tpf_opts *o) {
     o->start = TPF_START_FLAT;
     o->switch_tol = 1e-4;
     o->profile = 0;
+    o->method = TPF_METHOD_DENSE;
 }
 
 const char *tpf_strerror(tpf_status s) {
@@ -295,6 +316,7 @@ static tpf_status check_opts(const tpf_opts *in, tpf_opts &o) {
     if (o.precision != TPF_PREC_FP64 && o.precision != TPF_PREC_MIXED) return TPF_EINVAL;
     if (o.start != TPF_START_FLAT && o.start != TPF_START_GIVEN) return TPF_EINVAL;
     if (!(o.switch_tol >= 0.0)) return TPF_EINVAL;
+    if (o.method != TPF_METHOD_DENSE && o.method != TPF_METHOD_SPARSE) return TPF_EINVAL;
     return TPF_OK;
 }
 
@@ -310,6 +332,7 @@ tpf_status tpf_solve(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev, i
     if (!S_dev || !V_dev) return TPF_EINVAL;
     if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (o.method == TPF_METHOD_SPARSE) return tpf::solve_sparse(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
     if (o.precision == TPF_PREC_FP64) return tpf::solve_fp64(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
     return tpf::solve_mixed(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
 }
@@ -341,22 +364,90 @@ tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_
         }
         w.host_cap = T;
     }
-    if (cudaMemcpyAsync(w.S_dev, S_host, col_bytes * T, cudaMemcpyHostToDevice, s) != cudaSuccess) return TPF_ECUDA;
-    if (o.start == TPF_START_GIVEN &&
-        cudaMemcpyAsync(w.V_dev, V_host, col_bytes * T, cudaMemcpyHostToDevice, s) != cudaSuccess)
+    // Columns are independent, so the solve runs chunk by chunk: every host-to-device copy is queued
+    // at once on an input stream, each chunk's solve waits only for its own copy, and its results go
+    // back on an output stream while the next chunk is solved (pinned host memory overlaps; pageable
+    // memory still works, with the copies serialised by the driver).
+    const int64_t n_chunks = T >= 65536 ? std::min<int64_t>(8, T / 16384) : 1;
+    const int64_t chunk = tpf::round_up((T + n_chunks - 1) / n_chunks, tpf::kTileN);
+    cudaStream_t sin = nullptr, sout = nullptr;
+    std::vector<cudaEvent_t> ev;
+    auto cleanup = [&]() {
+        if (sout) cudaStreamSynchronize(sout);
+        if (sin) cudaStreamSynchronize(sin);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (sin) cudaStreamDestroy(sin);
+        if (sout) cudaStreamDestroy(sout);
+        cudaGetLastError();
+    };
+    if (cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking) != cudaSuccess) {
+        cleanup();
         return TPF_ECUDA;
-    st = tpf_solve(h, T, w.S_dev, w.V_dev, iters_host ? w.it_dev : nullptr, mismatch_host ? w.mm_dev : nullptr, &o,
-                   stream);
-    if (st != TPF_OK && st != TPF_ENOCONV) return st;
-    if (cudaMemcpyAsync(V_host, w.V_dev, col_bytes * T, cudaMemcpyDeviceToHost, s) != cudaSuccess) return TPF_ECUDA;
-    if (iters_host &&
-        cudaMemcpyAsync(iters_host, w.it_dev, sizeof(int32_t) * T, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return TPF_ECUDA;
-    if (mismatch_host &&
-        cudaMemcpyAsync(mismatch_host, w.mm_dev, sizeof(double) * T, cudaMemcpyDeviceToHost, s) != cudaSuccess)
-        return TPF_ECUDA;
-    if (cudaStreamSynchronize(s) != cudaSuccess) return TPF_ECUDA;
-    return st;
+    }
+    ev.assign(2 * n_chunks, nullptr);
+    for (cudaEvent_t &e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            return TPF_ECUDA;
+        }
+    const char *Sh = static_cast<const char *>(S_host);
+    char *Vh = static_cast<char *>(V_host);
+    char *Sd = static_cast<char *>(w.S_dev), *Vd = static_cast<char *>(w.V_dev);
+    for (int64_t c = 0; c < n_chunks; ++c) {
+        const int64_t a = c * chunk, b = std::min(T, a + chunk);
+        if (a >= b) break;
+        if (cudaMemcpyAsync(Sd + a * col_bytes, Sh + a * col_bytes, (b - a) * col_bytes, cudaMemcpyHostToDevice, sin) !=
+                cudaSuccess ||
+            (o.start == TPF_START_GIVEN && cudaMemcpyAsync(Vd + a * col_bytes, Vh + a * col_bytes, (b - a) * col_bytes,
+                                                           cudaMemcpyHostToDevice, sin) != cudaSuccess) ||
+            cudaEventRecord(ev[2 * c], sin) != cudaSuccess) {
+            cleanup();
+            return TPF_ECUDA;
+        }
+    }
+    tpf_stats total{};
+    tpf_status result = TPF_OK;
+    for (int64_t c = 0; c < n_chunks; ++c) {
+        const int64_t a = c * chunk, b = std::min(T, a + chunk);
+        if (a >= b) break;
+        if (cudaStreamWaitEvent(s, ev[2 * c], 0) != cudaSuccess) {
+            cleanup();
+            return TPF_ECUDA;
+        }
+        st = tpf_solve(h, b - a, Sd + a * col_bytes, Vd + a * col_bytes, iters_host ? w.it_dev + a : nullptr,
+                       mismatch_host ? w.mm_dev + a : nullptr, &o, stream);
+        if (st != TPF_OK && st != TPF_ENOCONV) {
+            cleanup();
+            return st;
+        }
+        if (st == TPF_ENOCONV) result = TPF_ENOCONV;
+        const tpf_stats &p = h->stats;
+        total.sweeps = std::max(total.sweeps, p.sweeps);
+        total.precise_sweeps = std::max(total.precise_sweeps, p.precise_sweeps);
+        total.converged += p.converged;
+        total.columns += p.columns;
+        total.kernel_launches += p.kernel_launches;
+        total.gemm_ms += p.gemm_ms;
+        total.residual_ms += p.residual_ms;
+        total.other_ms += p.other_ms;
+        total.gemm_launches += p.gemm_launches;
+        total.gemm_columns += p.gemm_columns;
+        if (cudaEventRecord(ev[2 * c + 1], s) != cudaSuccess || cudaStreamWaitEvent(sout, ev[2 * c + 1], 0) != cudaSuccess ||
+            cudaMemcpyAsync(Vh + a * col_bytes, Vd + a * col_bytes, (b - a) * col_bytes, cudaMemcpyDeviceToHost, sout) !=
+                cudaSuccess ||
+            (iters_host && cudaMemcpyAsync(iters_host + a, w.it_dev + a, sizeof(int32_t) * (b - a),
+                                           cudaMemcpyDeviceToHost, sout) != cudaSuccess) ||
+            (mismatch_host && cudaMemcpyAsync(mismatch_host + a, w.mm_dev + a, sizeof(double) * (b - a),
+                                              cudaMemcpyDeviceToHost, sout) != cudaSuccess)) {
+            cleanup();
+            return TPF_ECUDA;
+        }
+    }
+    const bool ok = cudaStreamSynchronize(sout) == cudaSuccess;
+    cleanup();
+    h->stats = total;
+    return ok ? result : TPF_ECUDA;
 }
 
 tpf_status tpf_selftest_gemm(int M, int N, int K, const void *A_re, const void *A_im, const void *B_re,

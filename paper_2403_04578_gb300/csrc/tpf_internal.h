@@ -38,6 +38,10 @@ struct Network {
     // admittance of the branch to it, and each bus's children (CSR over column positions).
     std::vector<int> par, ch_ptr, ch;
     std::vector<double> ypar;     // complex [n_pq]
+    std::vector<double> zpar;     // complex [n_pq], impedance of the branch to the parent
+    // Radial networks only: the demand buses grouped by depth below the slack (level 1 = buses on a
+    // branch from the slack): lvl_bus[lvl_ptr[d-1] .. lvl_ptr[d]) holds the level-d buses.
+    std::vector<int> lvl_ptr, lvl_bus;
 };
 
 // Build the network arrays; returns TPF_OK or the status to report.
@@ -58,6 +62,9 @@ struct DeviceNet {
     bool radial = false;
     int *par = nullptr, *ch_ptr = nullptr, *ch = nullptr;  // radial only
     float2 *ypar = nullptr;  // FP32 admittance of the branch to the parent [n]
+    float2 *zpar = nullptr;  // FP32 impedance of the branch to the parent [n]
+    int *lvl_ptr = nullptr, *lvl_bus = nullptr;  // buses by depth (radial only)
+    int depth = 0;
     // Mixed path: fp16 planes of K * 2^k_exp, [n_pad][n_pad], zero padded
     void *Kr16 = nullptr, *Ki16 = nullptr;
     int k_exp = 0;
@@ -154,13 +161,16 @@ namespace tpf {
 // Upload the network to the device (tpf_create).
 tpf_status upload_network(tpf_handle *h);
 void free_device(tpf_handle *h);
-// Ensure workspaces for `cols` columns.
-tpf_status ensure_workspace(tpf_handle *h, int64_t cols, bool mixed);
+// Ensure workspaces for `cols` columns: kind 0 = FP64 path, 1 = mixed path, 2 = per-column state only.
+enum WorkspaceKind : int { kWsFp64 = 0, kWsMixed = 1, kWsState = 2 };
+tpf_status ensure_workspace(tpf_handle *h, int64_t cols, int kind);
 // The two solve paths.  Return TPF_OK / TPF_ENOCONV / errors.
 tpf_status solve_fp64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
                       double *mismatch, const tpf_opts &o, cudaStream_t st);
 tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
                        double *mismatch, const tpf_opts &o, cudaStream_t st);
+tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
+                        double *mismatch, const tpf_opts &o, cudaStream_t st);
 tpf_status selftest_gemm(int M, int N, int K, const void *Ar, const void *Ai, const void *Br,
                          const void *Bi, float *Dr, float *Di, cudaStream_t st);
 }  // namespace tpf

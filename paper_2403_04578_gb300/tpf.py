@@ -16,6 +16,7 @@ from . import build as _build
 
 OK, EINVAL, ESINGULAR, ENOMEM, ECUDA, ETIMEOUT, ENOCONV, EUNSUPPORTED = range(8)
 PREC_FP64, PREC_MIXED = 0, 1
+METHOD_DENSE, METHOD_SPARSE = 0, 1
 START_FLAT, START_GIVEN = 0, 1
 
 # Every entry point declared in include/tpf.h.
@@ -39,7 +40,8 @@ class TpfError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
-                ("start", ctypes.c_int), ("switch_tol", ctypes.c_double), ("profile", ctypes.c_int)]
+                ("start", ctypes.c_int), ("switch_tol", ctypes.c_double), ("profile", ctypes.c_int),
+                ("method", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -136,7 +138,7 @@ def _z(a):
 
 
 def make_opts(precision: str | int = "mixed", tol: float = 1e-10, max_iter: int = 100, start: str | int = "flat",
-              switch_tol: float = 1e-4, profile: bool = False) -> Opts:
+              switch_tol: float = 1e-4, profile: bool = False, method: str | int = "dense") -> Opts:
     o = Opts()
     lib().tpf_default_opts(ctypes.byref(o))
     o.tol = float(tol)
@@ -145,6 +147,7 @@ def make_opts(precision: str | int = "mixed", tol: float = 1e-10, max_iter: int 
     o.start = {"flat": START_FLAT, "given": START_GIVEN}.get(start, start)
     o.switch_tol = float(switch_tol)
     o.profile = 1 if profile else 0
+    o.method = {"dense": METHOD_DENSE, "sparse": METHOD_SPARSE}.get(method, method)
     return o
 
 
@@ -221,7 +224,7 @@ class Feeder:
         return s.as_dict()
 
     def solve(self, S, V=None, iters=None, mismatch=None, precision="mixed", tol=1e-10, max_iter=100, start=None,
-              switch_tol=1e-4, stream=None, check=True, profile=False):
+              switch_tol=1e-4, stream=None, check=True, profile=False, method="dense"):
         """Solve every column of the device tensor S (complex128 [T][n_pq]).
 
         Returns (V, iters, mismatch, status); outputs are allocated when not given.  With
@@ -245,7 +248,7 @@ class Feeder:
         for t_, dt in ((V, torch.complex128), (iters, torch.int32), (mismatch, torch.float64)):
             if not (t_.is_cuda and t_.dtype == dt and t_.is_contiguous() and t_.shape[0] == T):
                 raise ValueError("output tensors must be contiguous CUDA tensors with T rows")
-        o = make_opts(precision, tol, max_iter, start, switch_tol, profile)
+        o = make_opts(precision, tol, max_iter, start, switch_tol, profile, method)
         st = lib().tpf_solve(self._h, T, ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
                              ctypes.c_void_p(iters.data_ptr()), ctypes.c_void_p(mismatch.data_ptr()), ctypes.byref(o),
                              _stream_ptr(stream))
@@ -254,7 +257,7 @@ class Feeder:
         return V, iters, mismatch, st
 
     def solve_host(self, S, V0=None, precision="mixed", tol=1e-10, max_iter=100, switch_tol=1e-4, stream=None,
-                   out=None, check=True, profile=False):
+                   out=None, check=True, profile=False, method="dense"):
         """tpf_solve_host on host arrays (numpy or pinned torch CPU tensors, complex128 [T][n_pq])."""
         T = S.shape[0]
         if out is None:
@@ -269,7 +272,7 @@ class Feeder:
         def ptr(a):
             return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
 
-        o = make_opts(precision, tol, max_iter, "given" if V0 is not None else "flat", switch_tol, profile)
+        o = make_opts(precision, tol, max_iter, "given" if V0 is not None else "flat", switch_tol, profile, method)
         st = lib().tpf_solve_host(self._h, T, ptr(S), ptr(V), ptr(it), ptr(mm), ctypes.byref(o), _stream_ptr(stream))
         if check and st not in (OK, ENOCONV):
             raise TpfError(st, "tpf_solve_host")

@@ -145,6 +145,25 @@ def test_host_buffers_match_device(cuda, precision):
     assert np.array_equal(ith, itd.cpu().numpy())
 
 
+def test_chunked_host_solve_matches_device(cuda):
+    """tpf_solve_host splits large T into chunks whose copies overlap the solve of other chunks."""
+    import torch
+
+    f = G.make_feeder(34, 1)
+    T = 70001  # four chunks, ragged last one
+    S = G.load_tensor(f, T, 3)
+    fd = tpf.Feeder.from_inputs(f)
+    Vd, itd, mmd, _ = fd.solve(_dev(S), precision="mixed")
+    Sh = torch.from_numpy(S).pin_memory()
+    out = (torch.empty((T, f.n_pq), dtype=torch.complex128).pin_memory(),
+           torch.empty(T, dtype=torch.int32).pin_memory(), torch.empty(T, dtype=torch.float64).pin_memory())
+    Vh, ith, mmh, st = fd.solve_host(Sh, precision="mixed", out=out)
+    assert st == tpf.OK
+    assert torch.equal(Vh, Vd.cpu()) and torch.equal(ith, itd.cpu()) and torch.equal(mmh, mmd.cpu())
+    assert fd.stats()["converged"] == T
+    fd.close()
+
+
 def test_create_errors(cuda):
     with pytest.raises(tpf.TpfError) as e:
         tpf.Feeder(3, [0, 0], [1, 1], [0.01 + 0.01j, 0.02 + 0.01j])  # bus 2 not connected
@@ -152,3 +171,110 @@ def test_create_errors(cuda):
     with pytest.raises(tpf.TpfError) as e:
         tpf.Feeder(3, [0, 1], [1, 5], [0.01 + 0.01j, 0.02 + 0.01j])
     assert e.value.status == tpf.EINVAL
+
+
+# --- sparse formulation (Algorithm 2, Eq. 13-14): tree substitution instead of the dense K ---
+
+@pytest.mark.parametrize("nb,T", [(34, 1440), (2, 7), (3, 1), (35, 129), (100, 200), (400, 257)])
+def test_sparse_vs_oracle(cuda, nb, T):
+    f, c, S = _case(nb, T)
+    _check(f, c, S, "mixed", TOL_MIXED, 1, method="sparse")
+
+
+def test_sparse_peak_hours_1000(cuda):
+    f = G.make_feeder(1000, 1)
+    c = O.Case.from_feeder(f)
+    S = G.load_tensor(f, 4096, 1)[1080:1080 + 300]
+    _check(f, c, S, "mixed", TOL_MIXED, 1, method="sparse")
+
+
+def test_sparse_chain_feeder(cuda):
+    """A 150-bus chain (149 depth levels of one bus each: the longest level walk per sweep), with
+    the slack at the far end and a shuffled demand-bus order."""
+    import torch
+
+    nb = 150
+    rng = np.random.default_rng(11)
+    frm, to = np.arange(nb - 1, 0, -1), np.arange(nb - 2, -1, -1)  # slack = bus 149
+    z = (4e-4 + 3e-4j) * rng.uniform(0.5, 1.5, nb - 1)
+    pq = rng.permutation(nb - 1)
+    c = O.Case(nb, frm, to, z, slack=nb - 1, vs=1.02 + 0.01j, pq=pq)
+    S = (rng.uniform(1e-3, 6e-3, (130, nb - 1)) * (1 + 0.3j)).astype(np.complex128)
+    Vo, _, _ = c.solve(S, tol=1e-13)
+    _, it_ref, _ = c.solve(S, tol=1e-10)
+    fd = tpf.Feeder(nb, frm, to, z, slack=nb - 1, v0=1.02 + 0.01j, pq_bus=pq)
+    V, it, mm, st = fd.solve(_dev(S), precision="mixed", tol=1e-10, method="sparse")
+    assert st == tpf.OK
+    assert np.abs(V.cpu().numpy() - Vo).max() <= TOL_MIXED
+    assert np.abs(it.cpu().numpy() - it_ref).max() <= 1
+    fd.close()
+
+
+def test_sparse_largest_feeder_vs_newton(cuda):
+    """3,500 buses (the shared-memory limit of one column is 3,657 demand buses): a few columns
+    against the sparse Newton-Raphson solution, which does not need the dense K."""
+    f = G.make_feeder(3500, 2)
+    S = G.load_tensor(f, 4096, 2)[[0, 700, 1100, 4095]]
+    Ysp = O.ybus(f.n_bus, f.from_bus, f.to_bus, f.z_pu)
+    fd = tpf.Feeder.from_inputs(f)
+    V, it, mm, st = fd.solve(_dev(S), precision="mixed", tol=1e-10, method="sparse")
+    assert st == tpf.OK
+    V = V.cpu().numpy()
+    for k in range(S.shape[0]):
+        # Power mismatch 1e-11 pu is at the rounding floor of a 3,500-bus sum; the voltage error it
+        # leaves is below 1e-11 * max|K_ij| (about 1e-12 pu here).
+        Vn, _, ok = O.nr_solve(Ysp, f.slack, f.v0, f.pq_bus, S[k], tol=1e-11)
+        assert ok
+        assert np.abs(V[k] - Vn).max() <= TOL_MIXED
+    fd.close()
+
+
+def test_sparse_matches_dense_iterates(cuda):
+    """Same iterates as the dense form: equal iteration counts up to rounding (+-1) and the same V."""
+    f, c, S = _case(200, 600, seed=3)
+    fd = tpf.Feeder.from_inputs(f)
+    Vd, itd, _, _ = fd.solve(_dev(S), precision="mixed")
+    Vs, its, _, st = fd.solve(_dev(S), precision="mixed", method="sparse")
+    assert st == tpf.OK
+    assert np.abs(itd.cpu().numpy() - its.cpu().numpy()).max() <= 1
+    assert np.abs(Vd.cpu().numpy() - Vs.cpu().numpy()).max() <= 2 * TOL_MIXED
+    fd.close()
+
+
+def test_sparse_empty_given_and_failures(cuda):
+    f, c, S = _case(34, 64)
+    fd = tpf.Feeder.from_inputs(f)
+    V, it, mm, st = fd.solve(_dev(S[:0]), precision="mixed", method="sparse")
+    assert st == tpf.OK and V.shape[0] == 0
+    Vo, _, _ = c.solve(S, tol=1e-13)
+    V, it, mm, st = fd.solve(_dev(S), V=_dev(Vo), precision="mixed", tol=1e-10, method="sparse")
+    assert st == tpf.OK
+    assert (it.cpu().numpy() == 1).all()
+    assert np.abs(V.cpu().numpy() - Vo).max() <= 1e-12
+    S2 = S.copy()
+    S2[3] *= 400.0
+    S2[10, 5] = np.nan
+    V, it, mm, st = fd.solve(_dev(S2), precision="mixed", max_iter=60, method="sparse")
+    assert st == tpf.ENOCONV
+    it = it.cpu().numpy()
+    assert it[3] == -60 and it[10] == -60
+    good = np.setdiff1d(np.arange(64), [3, 10])
+    assert np.abs(V.cpu().numpy()[good] - Vo[good]).max() <= TOL_MIXED
+    assert fd.stats()["converged"] == 62
+    # Host buffers through the same method.
+    Vh, ith, mmh, st = fd.solve_host(S, precision="mixed", method="sparse")
+    Vd, itd, mmd, _ = fd.solve(_dev(S), precision="mixed", method="sparse")
+    assert st == tpf.OK and np.array_equal(Vh, Vd.cpu().numpy()) and np.array_equal(ith, itd.cpu().numpy())
+    fd.close()
+
+
+def test_sparse_unsupported(cuda):
+    f, c, S = _case(34, 8)
+    fd = tpf.Feeder.from_inputs(f)
+    _, _, _, st = fd.solve(_dev(S), precision="fp64", method="sparse", check=False)
+    assert st == tpf.EUNSUPPORTED
+    fd.close()
+    mesh = tpf.Feeder(3, [0, 1, 0], [1, 2, 2], [0.01 + 0.01j, 0.02 + 0.01j, 0.03 + 0.02j])
+    _, _, _, st = mesh.solve(_dev(np.full((4, 2), 0.01 + 0.005j)), precision="mixed", method="sparse", check=False)
+    assert st == tpf.EUNSUPPORTED
+    mesh.close()

@@ -8,6 +8,7 @@
 // at 1/64 of its FP32 rate, so this path is FP64-pipe bound; it is the reference point for the
 // mixed-precision path.
 #include <cstdio>
+#include <type_traits>
 #include <math_constants.h>
 
 #include "tpf_internal.h"
@@ -83,15 +84,45 @@ tpf_status upload_network(tpf_handle *h) {
         TPF_CK(cudaMemcpy(d.ch_ptr, net.ch_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
         if (nch > 0) TPF_CK(cudaMemcpy(d.ch, net.ch.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
         TPF_CK(cudaMemcpy(d.ypar, yp.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
-        std::vector<float2> zp(n);
-        for (int i = 0; i < n; ++i) zp[i] = make_float2((float)net.zpar[2 * i], (float)net.zpar[2 * i + 1]);
-        TPF_CK(cudaMalloc(&d.zpar, sizeof(float2) * n));
-        TPF_CK(cudaMemcpy(d.zpar, zp.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
-        d.depth = (int)net.lvl_ptr.size() - 1;
-        TPF_CK(cudaMalloc(&d.lvl_ptr, sizeof(int) * net.lvl_ptr.size()));
-        TPF_CK(cudaMalloc(&d.lvl_bus, sizeof(int) * (net.lvl_bus.empty() ? 1 : net.lvl_bus.size())));
-        TPF_CK(cudaMemcpy(d.lvl_ptr, net.lvl_ptr.data(), sizeof(int) * net.lvl_ptr.size(), cudaMemcpyHostToDevice));
-        TPF_CK(cudaMemcpy(d.lvl_bus, net.lvl_bus.data(), sizeof(int) * net.lvl_bus.size(), cudaMemcpyHostToDevice));
+        // Slot-ordered depth-first arrays of the sparse formulation.
+        const int th = tree_threads(n);
+        d.t_threads = th;
+        if (th > 0) {
+            const int ns = th * kTreeBPT;
+            auto slot = [th](int q) { return (q % kTreeBPT) * th + q / kTreeBPT; };
+            std::vector<int> col(ns, -1), end(ns, 0), par(ns, -1), ecnt(ns, 0), ends;
+            std::vector<float4> z(ns, make_float4(0.f, 0.f, 0.f, 0.f));
+            std::vector<int> pos_par(n, -1);  // parent position of each position
+            for (int q = 0; q < n; ++q)
+                for (int c = q + 1; c < net.dfs_end[q]; c = net.dfs_end[c]) pos_par[c] = q;
+            bool fits = true;
+            for (int q = 0; q < n; ++q) {
+                const int s = slot(q), cnt = net.dfs_eptr[q + 1] - net.dfs_eptr[q];
+                col[s] = net.dfs_col[q];
+                end[s] = net.dfs_end[q];
+                par[s] = pos_par[q] < 0 ? -1 : slot(pos_par[q]);
+                if ((int)ends.size() > 0xffff || cnt > 0x7fff) fits = false;
+                ecnt[s] = (int)ends.size() | (cnt << 16);
+                for (int k = net.dfs_eptr[q]; k < net.dfs_eptr[q + 1]; ++k) ends.push_back(slot(net.dfs_ends[k]));
+                const double zr = net.dfs_z[2 * q], zi = net.dfs_z[2 * q + 1];
+                const float zrh = (float)zr, zih = (float)zi;
+                z[s] = make_float4(zrh, zih, (float)(zr - (double)zrh), (float)(zi - (double)zih));
+            }
+            d.t_n_ends = (int)ends.size();
+            if (ends.empty()) ends.push_back(0);
+            auto up = [](auto **dst, const auto &v) -> bool {
+                using T = typename std::decay_t<decltype(v)>::value_type;
+                if (cudaMalloc((void **)dst, sizeof(T) * v.size()) != cudaSuccess) return false;
+                return cudaMemcpy(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+            };
+            if (!fits) {
+                d.t_threads = 0;
+            } else if (!up(&d.t_col, col) || !up(&d.t_end, end) || !up(&d.t_par, par) || !up(&d.t_ecnt, ecnt) ||
+                       !up(&d.t_ends, ends) || !up(&d.t_z, z)) {
+                cudaGetLastError();
+                return TPF_ECUDA;
+            }
+        }
     }
     // fp16 planes of K * 2^k_exp with the largest component in [2^13, 2^14).
     double kmax = 0.0;
@@ -114,7 +145,7 @@ void free_device(tpf_handle *h) {
     cudaFree(d.K64); cudaFree(d.W64); cudaFree(d.row_ptr); cudaFree(d.nbr); cudaFree(d.y64); cudaFree(d.y2f);
     cudaFree(d.Kr16); cudaFree(d.Ki16);
     cudaFree(d.par); cudaFree(d.ch_ptr); cudaFree(d.ch); cudaFree(d.ypar);
-    cudaFree(d.zpar); cudaFree(d.lvl_ptr); cudaFree(d.lvl_bus);
+    cudaFree(d.t_col); cudaFree(d.t_end); cudaFree(d.t_par); cudaFree(d.t_ecnt); cudaFree(d.t_ends); cudaFree(d.t_z);
     d = DeviceNet();
     Workspace &w = h->ws;
     cudaFree(w.Vhi); cudaFree(w.Vlo); cudaFree(w.Shi); cudaFree(w.Slo); cudaFree(w.Rr16); cudaFree(w.Ri16);

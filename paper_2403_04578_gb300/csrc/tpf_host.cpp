@@ -188,26 +188,53 @@ tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int
         std::vector<int> fill(net.ch_ptr.begin(), net.ch_ptr.end() - 1);
         for (int i = 0; i < n; ++i)
             if (net.par[i] >= 0) net.ch[fill[net.par[i]]++] = i;
-        net.zpar.assign((size_t)2 * n, 0.0);
+        // Depth-first preorder of the demand buses: the subtree of the bus at position q is the
+        // position range [q, dfs_end[q]).
+        net.dfs_col.clear();
+        net.dfs_col.reserve(n);
+        std::vector<int> stack, posdfs(n_bus, -1);
+        std::vector<std::vector<int>> kids(n_bus);
+        for (size_t q = 1; q < order.size(); ++q) kids[parent[order[q]]].push_back(order[q]);
+        for (auto it = kids[slack].rbegin(); it != kids[slack].rend(); ++it) stack.push_back(*it);
+        while (!stack.empty()) {
+            const int u = stack.back();
+            stack.pop_back();
+            posdfs[u] = (int)net.dfs_col.size();
+            net.dfs_col.push_back(net.pos[u]);
+            for (auto it = kids[u].rbegin(); it != kids[u].rend(); ++it) stack.push_back(*it);
+        }
+        std::vector<int> size(n_bus, 1);
+        for (size_t q = order.size() - 1; q >= 1; --q) size[parent[order[q]]] += size[order[q]];
+        net.dfs_end.assign(n, 0);
+        net.dfs_z.assign((size_t)2 * n, 0.0);
+        std::vector<int> nend(n + 1, 0);
         for (int i = 0; i < n; ++i) {
-            net.zpar[2 * i] = zpar[net.pq[i]].real();
-            net.zpar[2 * i + 1] = zpar[net.pq[i]].imag();
+            const int b = net.pq[i], q = posdfs[b];
+            net.dfs_end[q] = q + size[b];
+            net.dfs_z[2 * q] = zpar[b].real();
+            net.dfs_z[2 * q + 1] = zpar[b].imag();
+            ++nend[net.dfs_end[q]];
         }
-        // Levels in breadth-first order (parents before children).
-        std::vector<int> depth(n_bus, 0);
-        net.lvl_ptr.assign(1, 0);
-        net.lvl_bus.clear();
-        int cur = 1;
-        for (size_t q = 1; q < order.size(); ++q) {
-            const int u = order[q];
-            depth[u] = depth[parent[u]] + 1;
-            while (depth[u] > cur) {
-                net.lvl_ptr.push_back((int)net.lvl_bus.size());
-                ++cur;
+        // For each position q < n, the positions whose subtree range ends at q.
+        net.dfs_eptr.assign(n + 1, 0);
+        for (int q = 0; q < n; ++q) net.dfs_eptr[q + 1] = net.dfs_eptr[q] + nend[q];
+        net.dfs_ends.assign(net.dfs_eptr[n], 0);
+        std::vector<int> fill_e(net.dfs_eptr.begin(), net.dfs_eptr.end() - 1);
+        for (int q = 0; q < n; ++q)
+            if (net.dfs_end[q] < n) net.dfs_ends[fill_e[net.dfs_end[q]]++] = q;
+        // Neighbour lists in depth-first positions (-1 = the slack), for the residual at the end.
+        net.dfs_rp.assign(n + 1, 0);
+        net.dfs_nbr.clear();
+        net.dfs_y.clear();
+        for (int q = 0; q < n; ++q) {
+            const int b = net.pq[net.dfs_col[q]];
+            for (auto &nb : adj[b]) {
+                net.dfs_nbr.push_back(nb.first == slack ? -1 : posdfs[nb.first]);
+                net.dfs_y.push_back(nb.second.real());
+                net.dfs_y.push_back(nb.second.imag());
             }
-            net.lvl_bus.push_back(net.pos[u]);
+            net.dfs_rp[q + 1] = (int)net.dfs_nbr.size();
         }
-        net.lvl_ptr.push_back((int)net.lvl_bus.size());
     }
     // Neighbour lists in column positions.
     net.row_ptr.assign(n + 1, 0);

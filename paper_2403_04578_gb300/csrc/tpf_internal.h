@@ -21,6 +21,16 @@ constexpr int kTileN = 128;
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Sparse formulation: positions per thread, largest block, and the block size for n demand buses
+// (0 when n is too large for one block).
+constexpr int kTreeBPT = 8;
+constexpr int kTreeMaxThreads = 512;
+inline int tree_threads(int n) {
+    int t = 32;
+    while (t * kTreeBPT < n) t *= 2;
+    return t <= kTreeMaxThreads ? t : 0;
+}
+
 // Host-side result of the network preprocessing (Eq. 1 and Eq. 3).
 struct Network {
     int n_bus = 0, n_pq = 0, slack = 0;
@@ -38,10 +48,12 @@ struct Network {
     // admittance of the branch to it, and each bus's children (CSR over column positions).
     std::vector<int> par, ch_ptr, ch;
     std::vector<double> ypar;     // complex [n_pq]
-    std::vector<double> zpar;     // complex [n_pq], impedance of the branch to the parent
-    // Radial networks only: the demand buses grouped by depth below the slack (level 1 = buses on a
-    // branch from the slack): lvl_bus[lvl_ptr[d-1] .. lvl_ptr[d]) holds the level-d buses.
-    std::vector<int> lvl_ptr, lvl_bus;
+    // Radial networks only, in depth-first preorder positions q of the demand buses: the column
+    // of each position, the end of its subtree's position range [q, dfs_end[q]), the impedance of
+    // the branch to its parent, the positions whose range ends at q (CSR dfs_eptr / dfs_ends) and
+    // the neighbour lists (CSR dfs_rp / dfs_nbr, -1 = the slack, admittances dfs_y).
+    std::vector<int> dfs_col, dfs_end, dfs_eptr, dfs_ends, dfs_rp, dfs_nbr;
+    std::vector<double> dfs_z, dfs_y;  // complex
 };
 
 // Build the network arrays; returns TPF_OK or the status to report.
@@ -62,9 +74,16 @@ struct DeviceNet {
     bool radial = false;
     int *par = nullptr, *ch_ptr = nullptr, *ch = nullptr;  // radial only
     float2 *ypar = nullptr;  // FP32 admittance of the branch to the parent [n]
-    float2 *zpar = nullptr;  // FP32 impedance of the branch to the parent [n]
-    int *lvl_ptr = nullptr, *lvl_bus = nullptr;  // buses by depth (radial only)
-    int depth = 0;
+    // Sparse formulation (radial only).  Block of t_threads threads per column; thread k owns the
+    // kTreeBPT consecutive depth-first positions q = kTreeBPT k + j, stored at slot
+    // s = j t_threads + k (so that a warp touches consecutive words).  Per slot: the column (-1
+    // past n), the end of the subtree's position range, the parent's slot (-1 = the slack), the
+    // start and count (start | count << 16) in t_ends of the slots of the positions whose
+    // subtree range ends at q, and the double-float z of the branch to the parent
+    // (re_hi, im_hi, re_lo, im_lo).
+    int t_threads = 0, t_n_ends = 0;
+    int *t_col = nullptr, *t_end = nullptr, *t_par = nullptr, *t_ecnt = nullptr, *t_ends = nullptr;
+    float4 *t_z = nullptr;
     // Mixed path: fp16 planes of K * 2^k_exp, [n_pad][n_pad], zero padded
     void *Kr16 = nullptr, *Ki16 = nullptr;
     int k_exp = 0;

@@ -1,34 +1,49 @@
 // Sparse tensor formulation (Sec. IV-B, Eq. 13-14, Algorithm 2) on radial feeders.
 //
-// Algorithm 2 replaces the dense product with K by a sparse solve with Y_dd, factored once.  On a
-// radial feeder Y_dd factors without fill-in and its solve is a two-pass tree substitution, so a
-// sweep costs O(n) per column instead of the dense O(n^2).  The iterate is the same as in the
-// dense form (Algorithm 2's text: the voltage sequence does not change).  Written in residual form
-// like the mixed dense path,
+// Algorithm 2 replaces the dense product with K = -Y_dd^{-1} by a sparse solve with Y_dd, factored
+// once; the sequence of iterates is the one of the dense form.  On a radial feeder Y_dd factors
+// without fill-in and the solve is a substitution over the tree.  Expanding the fixed-point step
+// V_{k+1} = K conj(S ./ V_k) + W that way gives, for every demand bus c with parent p(c) and
+// branch impedance z_c (V_slack = v_s),
 //
-//     Y_dd dV = -rho(V),   V <- V + dV,
+//     L_c      = sum over the subtree of c of I_i,   I_i = conj(S_i / V_i)      (leaves -> slack)
+//     V_new_c  = V_new_p(c) - z_c L_c  =  v_s - sum over the path slack..c of z_b L_b   (slack -> leaves)
 //
-// the solve is: branch currents J_c = rho_c + sum_{children k} J_k from the leaves up (the current
-// each subtree draws), then dV_c = dV_parent(c) - z_c J_c from the slack down (dV = 0 at the slack).
-// rho uses the anchored precision scheme of the mixed path (FP32 far from convergence, then
-// rho(V_ref) in double-float plus FP32 corrections), and the solve itself runs in FP32 on the small
-// correction, so results reach the FP64 solution.
+// Both passes become prefix sums once the buses are numbered in depth-first preorder: the subtree
+// of the bus at position q is the position range [q, end_q), so L_q = P[end_q - 1] - P[q - 1]
+// with P the inclusive prefix sum of I; and the path sum at q is the prefix sum at q of E, where
+// E_q = x_q minus the x_b of every b whose range ends at q (x_b = z_b L_b).  A sweep is then two
+// block-wide scans and no level-by-level walk.
 //
-// One 128-thread block owns one column for the whole solve: S, V, rho(V_ref) and the work vector
-// stay in shared memory across all sweeps, so device memory is touched once to read S and once to
-// write V.  Each tree pass walks the depth levels with one barrier per level.
+// Precision follows the mixed dense path: far from convergence the sweep runs in FP32 on V
+// itself.  Once the step is small the column is anchored at V_ref = fl32(V): the first step from
+// V_ref, D = BFS(V_ref) - V_ref, is computed once in double-float, and every later sweep only
+// carries FP32 corrections:  delta_new = D - sum over the path of z_b dL_b, with dL the subtree
+// sums of conj(S ./ (V_ref + delta)) - conj(S ./ V_ref), which are small near the solution.
+// The iterate is V_ref + delta; results reach the FP64 solution.
+//
+// One block owns one column for its whole solve.  Each thread owns kBPT consecutive depth-first
+// positions and keeps their V_ref, delta, S, z and ends-list bounds in registers; shared memory
+// holds the prefix-sum arrays, D and the tree's end / parent / ends arrays, all indexed by slot
+// (j * threads + k for the j-th position of thread k) so that a warp's accesses to its own
+// positions fall in consecutive banks.  Device memory is read for S once (again at an anchor) and
+// written once for V.
 #include "tpf_dd.cuh"
 
 namespace tpf {
 
 namespace {
 
-constexpr int kTreeThreads = 128;
+constexpr int kBPT = kTreeBPT;                // demand buses per thread (consecutive positions)
+constexpr int kMaxThreads = kTreeMaxThreads;  // so at most kBPT * 512 = 4096 demand buses
+constexpr int kMaxWarps = kMaxThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
+static_assert(kBPT == 8, "slot_of assumes 8 positions per thread");
 
 struct TreeArgs {
     int64_t T;
-    int n, depth, max_iter, given;
-    float tol, switch_tol;
+    int n, n_ends, max_iter, given;
+    float tol2, switch_tol, switch_tol2;  // squared tolerances compare with squared steps
     float2 vs_f;
     c2 vs_dd;
     const double2 *S;
@@ -37,177 +52,386 @@ struct TreeArgs {
     int32_t *iters_out;
     double *mismatch_out;
     int *tile_done;   // converged columns per 128-column tile
-    int *max_sweeps;  // largest per-column sweep count
-    const int *par, *ch_ptr, *ch, *lvl_ptr, *lvl_bus, *row_ptr, *nbr;
-    const float2 *ypar, *zpar;
-    const float4 *y;
+    int *counters;    // [5] largest per-column sweep count, [6] largest anchor count
+    const int *col, *end, *par, *ecnt, *ends;
+    const float4 *z;
 };
 
-// rho_i (FP32 or anchored) from the staged column: vh = V (or V_ref), vl = V - V_ref.
-__device__ __forceinline__ float2 tree_rho(const TreeArgs &a, int i, bool anchored, const float2 *vh,
-                                           const float2 *vl, const float2 *sh, const float2 *rh, const float2 *rl) {
-    const float2 *v = anchored ? vl : vh;
-    const float2 vi = v[i];
-    const int p = a.par[i];
-    const float2 vp = p >= 0 ? v[p] : (anchored ? make_float2(0.0f, 0.0f) : a.vs_f);
-    const float2 y = a.ypar[i];
-    float dr = vp.x - vi.x, di = vp.y - vi.y;
-    const float2 loc = anchored ? delta_current(vh[i], vi, sh[i]) : load_current_f32(vi, sh[i]);
-    float ar = loc.x - (y.x * dr - y.y * di), ai = loc.y - (y.x * di + y.y * dr);
-    for (int e = a.ch_ptr[i]; e < a.ch_ptr[i + 1]; ++e) {
-        const int k = a.ch[e];
-        const float2 yk = a.ypar[k], vk = v[k];
-        dr = vi.x - vk.x;
-        di = vi.y - vk.y;
-        ar += yk.x * dr - yk.y * di;
-        ai += yk.x * di + yk.y * dr;
-    }
-    if (anchored) {
-        const f2 sr = two_sum(rh[i].x, ar), si = two_sum(rh[i].y, ai);
-        ar = sr.h + (sr.l + rl[i].x);
-        ai = si.h + (si.l + rl[i].y);
-    }
-    return make_float2(ar, ai);
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul2(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float4 pack(c2 v) { return make_float4(v.re.h, v.re.l, v.im.h, v.im.l); }
+__device__ __forceinline__ c2 unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+
+// conj(s / v) in FP32 with the hardware reciprocal (sweeps: their rounding is far below what the
+// FP32 phase resolves, and the anchored corrections are small differences).
+__device__ __forceinline__ float2 current_fast(float2 v, float2 s) {
+    const float inv = __fdividef(1.0f, v.x * v.x + v.y * v.y);
+    return make_float2((s.x * v.x + s.y * v.y) * inv, (s.x * v.y - s.y * v.x) * inv);
+}
+// conj(s / (v + d)) - conj(s / v) = -conj(s d / ((v + d) v)), FP32 with the hardware reciprocal.
+__device__ __forceinline__ float2 delta_current_fast(float2 v, float2 d, float2 s) {
+    const float2 w = make_float2(s.x * d.x - s.y * d.y, s.x * d.y + s.y * d.x);
+    const float2 vp = make_float2(v.x + d.x, v.y + d.y);
+    const float2 q = make_float2(vp.x * v.x - vp.y * v.y, vp.x * v.y + vp.y * v.x);
+    const float inv = __fdividef(1.0f, q.x * q.x + q.y * q.y);
+    return make_float2(-(w.x * q.x + w.y * q.y) * inv, (w.y * q.x - w.x * q.y) * inv);
 }
 
-__global__ void __launch_bounds__(kTreeThreads) mx_tree(TreeArgs a) {
-    extern __shared__ float2 tsm[];
-    const int n = a.n;
-    float2 *vh = tsm, *vl = vh + n, *sh = vl + n, *sl = sh + n, *rh = sl + n, *rl = rh + n, *w = rl + n;
-    __shared__ float s_red[kTreeThreads / 32];
-    __shared__ int s_state;  // bit 0 done, 1 converged, 2 anchored, 3 blind, 4 anchor now
-    __shared__ int s_it;
-    __shared__ float s_dprev;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+// Exclusive scan over the threads of the block (thread order) of one complex FP32 value.
+__device__ __forceinline__ float2 block_scan(float2 v, float2 *wt, int lane, int warp) {
+    float2 inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float ux = __shfl_up_sync(kFull, inc.x, o), uy = __shfl_up_sync(kFull, inc.y, o);
+        if (lane >= o) inc = add2(make_float2(ux, uy), inc);
+    }
+    const float ex = __shfl_up_sync(kFull, inc.x, 1), ey = __shfl_up_sync(kFull, inc.y, 1);
+    const float2 off = lane ? make_float2(ex, ey) : make_float2(0.0f, 0.0f);
+    if (lane == 31) wt[warp] = inc;
+    __syncthreads();
+    float2 pre = make_float2(0.0f, 0.0f);
+    for (int w = 0; w < warp; ++w) pre = add2(pre, wt[w]);
+    return add2(pre, off);
+}
+
+// The same in double-float.
+__device__ __noinline__ c2 block_scan_dd(c2 v, float4 *wt, int lane, int warp) {
+    c2 inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        float4 u = pack(inc);
+        u.x = __shfl_up_sync(kFull, u.x, o);
+        u.y = __shfl_up_sync(kFull, u.y, o);
+        u.z = __shfl_up_sync(kFull, u.z, o);
+        u.w = __shfl_up_sync(kFull, u.w, o);
+        if (lane >= o) inc = c_add(unpack(u), inc);
+    }
+    float4 e = pack(inc);
+    e.x = __shfl_up_sync(kFull, e.x, 1);
+    e.y = __shfl_up_sync(kFull, e.y, 1);
+    e.z = __shfl_up_sync(kFull, e.z, 1);
+    e.w = __shfl_up_sync(kFull, e.w, 1);
+    const c2 off = lane ? unpack(e) : c2{{0.0f, 0.0f}, {0.0f, 0.0f}};
+    if (lane == 31) wt[warp] = pack(inc);
+    __syncthreads();
+    c2 pre = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    for (int w = 0; w < warp; ++w) pre = c_add(pre, unpack(wt[w]));
+    return c_add(pre, off);
+}
+
+// Largest values over the block; every thread gets the same result.
+__device__ __forceinline__ float2 block_max(float2 m, float2 *wm, int lane, int warp, int nwarps) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        m.x = fmaxf(m.x, __shfl_xor_sync(kFull, m.x, o));
+        m.y = fmaxf(m.y, __shfl_xor_sync(kFull, m.y, o));
+    }
+    if (lane == 0) wm[warp] = m;
+    __syncthreads();
+    float2 d = wm[0];
+    for (int w = 1; w < nwarps; ++w) d = make_float2(fmaxf(d.x, wm[w].x), fmaxf(d.y, wm[w].y));
+    return d;
+}
+
+__device__ __forceinline__ c2 s_dd(double2 s) {
+    const float hx = __double2float_rn(s.x), hy = __double2float_rn(s.y);
+    return {{hx, __double2float_rn(s.x - (double)hx)}, {hy, __double2float_rn(s.y - (double)hy)}};
+}
+
+// Slot of depth-first position p for blocks of th threads.
+__device__ __forceinline__ int slot_of(int p, int th) { return (p & (kBPT - 1)) * th + (p >> 3); }
+
+// Shared-memory view of one block.
+struct TreeSmem {
+    float4 *A;    // [ns] double-float prefix sums (anchor); float2 P and X during the sweeps
+    float4 *B;    // [ns] V_ref (anchor input), x (anchor), then D = BFS(V_ref) - V_ref
+    int *ends;    // [n_ends] slots of the positions whose subtree range ends at a position
+    int *end;     // [ns] end of the subtree's position range
+    int *par;     // [ns] parent slot, -1 = the slack
+};
+
+// First part of an anchor, in double-float: with V_ref in B (x, y), leaves the inclusive prefix
+// sums of the path terms in A and returns the thread's exclusive scan offset; B holds the branch
+// terms.  Loops are not unrolled: this runs once or twice per column and its code stays small.
+__device__ __noinline__ c2 anchor_dd(const TreeArgs &a, const double2 *S, const TreeSmem &m, const int *ecnt,
+                                     float4 *wtd, int tid, int th, int lane, int warp) {
+    const int n = a.n, base = tid * kBPT;
+    // Load currents at V_ref and their inclusive prefix sums.
+    c2 run = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll 1
+    for (int j = 0; j < kBPT; ++j) {
+        const int q = base + j, s = j * th + tid;
+        if (q < n) {
+            const float4 v = m.B[s];
+            run = c_add(run, load_current_dd(s_dd(S[a.col[s]]), c2{{v.x, 0.0f}, {v.y, 0.0f}}));
+            m.A[s] = pack(run);
+        }
+    }
+    c2 off = block_scan_dd(run, wtd, lane, warp);
+#pragma unroll 1
+    for (int j = 0; j < kBPT; ++j) {
+        const int q = base + j, s = j * th + tid;
+        if (q < n) m.A[s] = pack(c_add(off, unpack(m.A[s])));
+    }
+    __syncthreads();
+    // Branch terms x_q = z_q (P[end_q - 1] - P[q - 1]).
+#pragma unroll 1
+    for (int j = 0; j < kBPT; ++j) {
+        const int q = base + j, s = j * th + tid;
+        if (q < n) {
+            c2 L = unpack(m.A[slot_of(m.end[s] - 1, th)]);
+            if (q > 0) L = c_sub(L, unpack(m.A[j ? s - th : (kBPT - 1) * th + tid - 1]));
+            const float4 zq = a.z[s];
+            m.B[s] = pack(c_mul(c2{{zq.x, zq.z}, {zq.y, zq.w}}, L));
+        }
+    }
+    __syncthreads();
+    // Inclusive prefix sums of E_q = x_q - (x_b of every b whose range ends at q).
+    run = c2{{0.0f, 0.0f}, {0.0f, 0.0f}};
+#pragma unroll 1
+    for (int j = 0; j < kBPT; ++j) {
+        const int q = base + j, s = j * th + tid;
+        if (q < n) {
+            const int ec = ecnt[j];
+            c2 e = unpack(m.B[s]);
+            for (int k = 0; k < (ec >> 16); ++k) e = c_sub(e, unpack(m.B[m.ends[(ec & 0xffff) + k]]));
+            run = c_add(run, e);
+            m.A[s] = pack(run);
+        }
+    }
+    return block_scan_dd(run, wtd, lane, warp);
+}
+
+__global__ void __launch_bounds__(kMaxThreads) mx_tree(TreeArgs a) {
+    extern __shared__ float4 tsm[];
+    const int n = a.n, th = blockDim.x, ns = th * kBPT;
+    // Arrays indexed by slot s = j th + k of position q = kBPT k + j.
+    TreeSmem m;
+    m.A = tsm;
+    m.B = tsm + ns;
+    m.end = reinterpret_cast<int *>(tsm + 2 * ns);
+    m.par = m.end + ns;
+    m.ends = m.par + ns;
+    float2 *P = reinterpret_cast<float2 *>(m.A);  // [ns] inclusive prefix sums of the load currents
+    float2 *X = P + ns;                           // [ns] branch terms z_q L_q; the residual's x at the end
+    __shared__ float2 wt1[kMaxWarps], wt2[kMaxWarps];
+    __shared__ float4 wtd[kMaxWarps];
+    __shared__ float2 wm[kMaxWarps];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = th >> 5;
     const int64_t t = blockIdx.x;
-    if (t >= a.T) return;
+    const int base = tid * kBPT;
     const double2 *S = a.S + t * n;
-    for (int i = tid; i < n; i += kTreeThreads) {
-        const double2 s = S[i];
-        const float2 h = make_float2(__double2float_rn(s.x), __double2float_rn(s.y));
-        sh[i] = h;
-        sl[i] = make_float2(__double2float_rn(s.x - (double)h.x), __double2float_rn(s.y - (double)h.y));
-        float2 v0h = make_float2(1.0f, 0.0f), v0l = make_float2(0.0f, 0.0f);
-        if (a.given) {
-            const double2 v = a.V0[t * n + i];
-            v0h = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
-            v0l = make_float2(__double2float_rn(v.x - (double)v0h.x), __double2float_rn(v.y - (double)v0h.y));
-        }
-        vh[i] = v0h;
-        vl[i] = v0l;
+
+    for (int s = tid; s < ns; s += th) {
+        m.end[s] = a.end[s];
+        m.par[s] = a.par[s];
     }
-    if (tid == 0) {
-        s_state = a.given ? (4 | 8 | 16) : 0;  // a given start is anchored at once (blind)
-        s_it = 0;
-        s_dprev = 0.0f;
+    for (int k = tid; k < a.n_ends; k += th) m.ends[k] = a.ends[k];
+    // Per position: V_ref (or V before anchoring), delta = V - V_ref, S (FP32), z, ends list.
+    float2 vr[kBPT], dl[kBPT], sh[kBPT], zr[kBPT];
+    int ecnt[kBPT];
+#pragma unroll
+    for (int j = 0; j < kBPT; ++j) {
+        const int q = base + j, s = j * th + tid;
+        vr[j] = make_float2(1.0f, 0.0f);
+        dl[j] = sh[j] = zr[j] = make_float2(0.0f, 0.0f);
+        ecnt[j] = 0;
+        if (q < n) {
+            const int i = a.col[s];
+            const double2 sv = S[i];
+            sh[j] = make_float2(__double2float_rn(sv.x), __double2float_rn(sv.y));
+            const float4 zq = a.z[s];
+            zr[j] = make_float2(zq.x, zq.y);
+            ecnt[j] = a.ecnt[s];
+            if (a.given) {
+                const double2 v = a.V0[t * n + i];
+                vr[j] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+                dl[j] = make_float2(__double2float_rn(v.x - (double)vr[j].x), __double2float_rn(v.y - (double)vr[j].y));
+            }
+        }
     }
     __syncthreads();
+    // A given start is anchored at once ("blind"), and anchored again when the step is small.
+    bool anchored = a.given != 0, blind = anchored, anchor_now = anchored, done = false, conv = false;
+    int it = 0, anchors = 0;
+    float dprev2 = 0.0f;
     for (;;) {
-        int state = s_state;
-        if (state & 16) {  // (re-)anchor: V_ref <- fl(V), rho(V_ref) in double-float
-            for (int i = tid; i < n; i += kTreeThreads) {
-                const f2 re = two_sum(vh[i].x, vl[i].x), im = two_sum(vh[i].y, vl[i].y);
-                vh[i] = make_float2(re.h, im.h);
-                vl[i] = make_float2(re.l, im.l);
+        if (anchor_now) {
+            anchor_now = false;
+            anchored = true;
+            ++anchors;
+            // V_ref <- fl32(V); the remainder stays in delta.  D = BFS(V_ref) - V_ref goes to B.
+#pragma unroll
+            for (int j = 0; j < kBPT; ++j) {
+                const f2 re = two_sum(vr[j].x, dl[j].x), im = two_sum(vr[j].y, dl[j].y);
+                vr[j] = make_float2(re.h, im.h);
+                dl[j] = make_float2(re.l, im.l);
+                m.B[j * th + tid] = make_float4(re.h, im.h, 0.0f, 0.0f);
             }
-            __syncthreads();
-            for (int i = tid; i < n; i += kTreeThreads) {
-                const c2 r = residual_dd(i, vh, nullptr, sh, sl, a.row_ptr, a.nbr, a.y, a.vs_dd);
-                rh[i] = make_float2(r.re.h, r.im.h);
-                rl[i] = make_float2(r.re.l, r.im.l);
-            }
-            __syncthreads();
-            if (tid == 0) s_state = state & ~16;
-            state &= ~16;
-        }
-        if (state & 1) break;
-        const bool anchored = (state & 4) != 0;
-        // rho -> w
-        for (int i = tid; i < n; i += kTreeThreads) w[i] = tree_rho(a, i, anchored, vh, vl, sh, rh, rl);
-        __syncthreads();
-        // leaves to slack: J_c = rho_c + sum_{children} J_k
-        for (int d = a.depth; d >= 1; --d) {
-            for (int q = a.lvl_ptr[d - 1] + tid; q < a.lvl_ptr[d]; q += kTreeThreads) {
-                const int c = a.lvl_bus[q];
-                float2 J = w[c];
-                for (int e = a.ch_ptr[c]; e < a.ch_ptr[c + 1]; ++e) {
-                    const float2 Jk = w[a.ch[e]];
-                    J.x += Jk.x;
-                    J.y += Jk.y;
+            const c2 off = anchor_dd(a, S, m, ecnt, wtd, tid, th, lane, warp);
+#pragma unroll
+            for (int j = 0; j < kBPT; ++j) {
+                const int q = base + j, s = j * th + tid;
+                if (q < n) {
+                    const c2 ps = c_add(off, unpack(m.A[s]));
+                    const c2 D = c_sub(c_sub(a.vs_dd, c2{{vr[j].x, 0.0f}, {vr[j].y, 0.0f}}), ps);
+                    m.B[s] = make_float4(D.re.h, D.im.h, D.re.l, D.im.l);
                 }
-                w[c] = J;
             }
-            __syncthreads();
+            __syncthreads();  // the sweep reuses A
         }
-        // slack to leaves: dV_c = dV_parent - z_c J_c
-        for (int d = 1; d <= a.depth; ++d) {
-            for (int q = a.lvl_ptr[d - 1] + tid; q < a.lvl_ptr[d]; q += kTreeThreads) {
-                const int c = a.lvl_bus[q];
-                const int p = a.par[c];
-                const float2 dp = p >= 0 ? w[p] : make_float2(0.0f, 0.0f);
-                const float2 J = w[c], z = a.zpar[c];
-                w[c] = make_float2(dp.x - (z.x * J.x - z.y * J.y), dp.y - (z.x * J.y + z.y * J.x));
-            }
-            __syncthreads();
+        if (done) break;
+
+        // --- one sweep ---
+        // Load currents (or their change from V_ref) and their inclusive prefix sums P.
+        float2 loc[kBPT];
+        float2 run = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int j = 0; j < kBPT; ++j) {
+            const float2 I = anchored ? delta_current_fast(vr[j], dl[j], sh[j]) : current_fast(vr[j], sh[j]);
+            run = add2(run, I);  // positions past n have S = 0 and add nothing
+            loc[j] = run;
         }
-        // V += dV and max |dV|
-        float m = 0.0f;
-        for (int i = tid; i < n; i += kTreeThreads) {
-            const float2 dv = w[i];
-            if (anchored) {
-                vl[i] = make_float2(vl[i].x + dv.x, vl[i].y + dv.y);
-            } else {
-                vh[i] = make_float2(vh[i].x + dv.x, vh[i].y + dv.y);
-            }
-            float mag = sqrtf(dv.x * dv.x + dv.y * dv.y);
-            if (mag != mag) mag = __int_as_float(0x7f800000);
-            m = fmaxf(m, mag);
-        }
-        for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-        if (lane == 0) s_red[warp] = m;
+        float2 off = block_scan(run, wt1, lane, warp);
+#pragma unroll
+        for (int j = 0; j < kBPT; ++j) P[j * th + tid] = add2(off, loc[j]);
         __syncthreads();
-        if (tid == 0) {
-            float d = s_red[0];
-            for (int k = 1; k < kTreeThreads / 32; ++k) d = fmaxf(d, s_red[k]);
-            const int it = ++s_it;
-            int st = s_state;
-            if (d <= a.tol) {
-                st |= 1 | 2;
-            } else if (it >= a.max_iter || !(d < 1e30f)) {
-                st |= 1;
-            } else if (!(st & 4) || (st & 8)) {
-                if (d < a.switch_tol || (s_dprev > 0.0f && d * d < 3e-6f * s_dprev)) st = (st | 4 | 16) & ~8;
+        // Branch terms x_q = z_q (P[end_q - 1] - P[q - 1]).
+#pragma unroll
+        for (int j = 0; j < kBPT; ++j) {
+            const int q = base + j, s = j * th + tid;
+            if (q < n) {
+                float2 L = P[slot_of(m.end[s] - 1, th)];
+                if (q > 0) L = sub2(L, P[j ? s - th : (kBPT - 1) * th + tid - 1]);
+                X[s] = cmul2(zr[j], L);
             }
-            s_dprev = d;
-            s_state = st;
         }
         __syncthreads();
+        // Path sums: prefix sums of E_q = x_q - (x_b of every b whose subtree range ends at q).
+        run = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int j = 0; j < kBPT; ++j) {
+            const int q = base + j, s = j * th + tid;
+            if (q < n) {
+                float2 e = X[s];
+                const int st = ecnt[j] & 0xffff, cnt = ecnt[j] >> 16;
+                for (int k = 0; k < cnt; ++k) e = sub2(e, X[m.ends[st + k]]);
+                run = add2(run, e);
+            }
+            loc[j] = run;
+        }
+        off = block_scan(run, wt2, lane, warp);
+        float2 mx = make_float2(0.0f, 0.0f);  // max |step|^2, max |delta|^2
+#pragma unroll
+        for (int j = 0; j < kBPT; ++j) {
+            const int q = base + j, s = j * th + tid;
+            if (q < n) {
+                const float2 ps = add2(off, loc[j]);
+                float2 step;
+                if (anchored) {
+                    const float4 D = m.B[s];
+                    const float2 nd = add2(sub2(make_float2(D.x, D.y), ps), make_float2(D.z, D.w));
+                    step = sub2(nd, dl[j]);
+                    dl[j] = nd;
+                    mx.y = fmaxf(mx.y, abs2(nd));
+                } else {
+                    const float2 nv = sub2(a.vs_f, ps);
+                    step = sub2(nv, vr[j]);
+                    vr[j] = nv;
+                }
+                float mag2 = abs2(step);
+                if (mag2 != mag2) mag2 = __int_as_float(0x7f800000);
+                mx.x = fmaxf(mx.x, mag2);
+            }
+        }
+        const float2 dm = block_max(mx, wm, lane, warp, nwarps);
+        const float d2 = dm.x;
+        // Every thread takes the same decision from the same d.  A step is only trusted to be
+        // below tol on an anchored column whose offset from V_ref is small: in FP32 on V itself
+        // (or on a large offset) a tiny step can round to zero.
+        ++it;
+        if (d2 <= a.tol2 && anchored && (!blind || dm.y < a.switch_tol2)) {
+            done = conv = true;
+        } else if (it >= a.max_iter || !(d2 < 1e30f)) {
+            done = true;
+        } else if (!anchored || blind) {
+            // Anchor once the step is small, or is predicted (geometric rate) to fall below 3e-6
+            // in the next sweep: d^2 < 3e-6 d_prev, squared.
+            if (d2 < a.switch_tol2 || (dprev2 > 0.0f && d2 * d2 < 9e-12f * dprev2)) {
+                anchor_now = true;
+                blind = false;
+            }
+        }
+        dprev2 = d2;
     }
-    // Outputs: V, iteration count, mismatch max_i |V_i| |rho_i| at the returned V.
-    const int state = s_state;
-    const bool anchored = (state & 4) != 0;
-    float m = 0.0f;
-    for (int i = tid; i < n; i += kTreeThreads) {
-        const float2 r = tree_rho(a, i, anchored, vh, vl, sh, rh, rl);
-        const float2 h = vh[i], l = vl[i];
-        a.V_out[t * n + i] = make_double2((double)h.x + (double)l.x, (double)h.y + (double)l.y);
-        const float vr = h.x + l.x, vi = h.y + l.y;
-        float mv = sqrtf(vr * vr + vi * vi) * sqrtf(r.x * r.x + r.y * r.y);
-        if (mv != mv) mv = __int_as_float(0x7f800000);
-        m = fmaxf(m, mv);
+
+    // Outputs: V, iteration count and the mismatch max_i |V_i| |rho_i| at the returned V, with
+    // rho = Y_dd x + c:
+    //   anchored:   x = delta - D, x_slack = 0,   c = conj(S ./ V) - conj(S ./ V_ref)
+    //               (from rho(V_ref) = -Y_dd D, as D = K rho(V_ref) with K = -Y_dd^{-1});
+    //   otherwise:  x = V,         x_slack = v_s, c = conj(S ./ V).
+    // On the tree (Y_dd x)_q = -J_q + sum over the children k of J_k with the branch currents
+    // J_k = y_k (x_parent(k) - x_k); the children of q are q + 1 and then each next sibling, the
+    // end of the previous one's range, while inside q's range.
+    float2 *J = reinterpret_cast<float2 *>(m.B);
+    float2 xs[kBPT];
+#pragma unroll
+    for (int j = 0; j < kBPT; ++j) {
+        const int q = base + j, s = j * th + tid;
+        if (anchored) {
+            const float4 D = m.B[s];
+            xs[j] = sub2(sub2(dl[j], make_float2(D.x, D.y)), make_float2(D.z, D.w));
+        } else {
+            xs[j] = vr[j];
+        }
+        if (q < n) {
+            a.V_out[t * n + a.col[s]] =
+                make_double2((double)vr[j].x + (double)dl[j].x, (double)vr[j].y + (double)dl[j].y);
+            X[s] = xs[j];
+        }
     }
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __syncthreads();  // X complete; B (D) no longer read
+    const float2 x_slack = anchored ? make_float2(0.0f, 0.0f) : a.vs_f;
+#pragma unroll
+    for (int j = 0; j < kBPT; ++j) {
+        const int q = base + j, s = j * th + tid;
+        if (q < n) {
+            const int p = m.par[s];
+            const float2 y = make_float2(zr[j].x, -zr[j].y);
+            const float2 yk = make_float2(y.x * __fdividef(1.0f, abs2(zr[j])), y.y * __fdividef(1.0f, abs2(zr[j])));
+            J[s] = cmul2(yk, sub2(p >= 0 ? X[p] : x_slack, xs[j]));
+        }
+    }
     __syncthreads();
-    if (lane == 0) s_red[warp] = m;
-    __syncthreads();
+    float mm = 0.0f;
+#pragma unroll
+    for (int j = 0; j < kBPT; ++j) {
+        const int q = base + j, s = j * th + tid;
+        if (q < n) {
+            float2 r = anchored ? delta_current_fast(vr[j], dl[j], sh[j]) : current_fast(vr[j], sh[j]);
+            r = sub2(r, J[s]);
+            const int e = m.end[s];
+            for (int k = q + 1; k < e;) {
+                const int ks = slot_of(k, th);
+                r = add2(r, J[ks]);
+                k = m.end[ks];
+            }
+            const float2 v = add2(vr[j], dl[j]);
+            float mv = sqrtf(abs2(v) * abs2(r));
+            if (mv != mv) mv = __int_as_float(0x7f800000);  // a NaN mismatch reports as +inf
+            mm = fmaxf(mm, mv);
+        }
+    }
+    mm = block_max(make_float2(mm, 0.0f), wm, lane, warp, nwarps).x;
     if (tid == 0) {
-        float mm = s_red[0];
-        for (int k = 1; k < kTreeThreads / 32; ++k) mm = fmaxf(mm, s_red[k]);
-        const bool conv = (state & 2) != 0;
         if (a.mismatch_out) a.mismatch_out[t] = (double)mm;
-        if (a.iters_out) a.iters_out[t] = conv ? s_it : -a.max_iter;
+        if (a.iters_out) a.iters_out[t] = conv ? it : -a.max_iter;
         if (conv) atomicAdd(&a.tile_done[t / kTileN], 1);
-        atomicMax(a.max_sweeps, s_it);
+        atomicMax(&a.counters[5], it);
+        atomicMax(&a.counters[6], anchors);
     }
 }
 
@@ -217,13 +441,13 @@ tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_
                         const tpf_opts &o, cudaStream_t st) {
     const DeviceNet &d = h->dev;
     if (!d.radial || o.precision != TPF_PREC_MIXED) return TPF_EUNSUPPORTED;
-    const int n = d.n;
-    const size_t smem = (size_t)7 * n * sizeof(float2);
-    if (smem > 200 * 1024) return TPF_EUNSUPPORTED;
+    const int n = d.n, threads = d.t_threads;
+    if (threads == 0) return TPF_EUNSUPPORTED;
+    if (T > 0x7fffffff) return TPF_EUNSUPPORTED;  // one block per column
+    const size_t smem = (size_t)2 * threads * kBPT * sizeof(float4) + sizeof(int) * (2 * threads * kBPT + d.t_n_ends);
     tpf_status rs = ensure_workspace(h, T, kWsState);  // counters and per-tile counts
     if (rs != TPF_OK) return rs;
     Workspace &w = h->ws;
-    if (T > 0x7fffffff) return TPF_EUNSUPPORTED;  // one block per column
     if (cudaFuncSetAttribute(mx_tree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return TPF_ECUDA;
@@ -237,11 +461,12 @@ tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_
     TreeArgs a{};
     a.T = T;
     a.n = n;
-    a.depth = d.depth;
     a.max_iter = o.max_iter;
     a.given = o.start == TPF_START_GIVEN;
-    a.tol = (float)o.tol;
-    a.switch_tol = (float)o.switch_tol;
+    const float tol = (float)o.tol, sw = (float)o.switch_tol;
+    a.tol2 = tol * tol;
+    a.switch_tol = sw;
+    a.switch_tol2 = sw * sw;
     a.vs_f = make_float2((float)h->net.vs_re, (float)h->net.vs_im);
     {
         const float rh = (float)h->net.vs_re, ih = (float)h->net.vs_im;
@@ -253,20 +478,17 @@ tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_
     a.iters_out = iters;
     a.mismatch_out = mismatch;
     a.tile_done = w.tile_active;
-    a.max_sweeps = w.counters + 5;
-    a.par = d.par;
-    a.ch_ptr = d.ch_ptr;
-    a.ch = d.ch;
-    a.lvl_ptr = d.lvl_ptr;
-    a.lvl_bus = d.lvl_bus;
-    a.row_ptr = d.row_ptr;
-    a.nbr = d.nbr;
-    a.ypar = d.ypar;
-    a.zpar = d.zpar;
-    a.y = d.y2f;
+    a.counters = w.counters;
+    a.n_ends = d.t_n_ends;
+    a.col = d.t_col;
+    a.end = d.t_end;
+    a.par = d.t_par;
+    a.ecnt = d.t_ecnt;
+    a.ends = d.t_ends;
+    a.z = d.t_z;
     KernelTimer timer(o.profile != 0, st);
     timer.begin(KernelTimer::kResidual);
-    mx_tree<<<(unsigned)T, kTreeThreads, smem, st>>>(a);
+    mx_tree<<<(unsigned)T, threads, smem, st>>>(a);
     timer.end();
     if (cudaGetLastError() != cudaSuccess) return TPF_ECUDA;
     std::vector<int> tiles(n_tiles);
@@ -280,6 +502,7 @@ tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_
     int64_t conv = 0;
     for (int x : tiles) conv += x;
     h->stats.sweeps = w.counters_host[5];
+    h->stats.precise_sweeps = w.counters_host[6];
     h->stats.kernel_launches = 1;
     h->stats.converged = conv;
     h->stats.residual_ms = timer.total_ms(KernelTimer::kResidual);

@@ -2,22 +2,25 @@
 """Benchmark: power-flow solves per second of the tensor power flow on one GB300 per rank.
 
 Workload (default): a 1,000-bus synthetic radial feeder (999 PQ buses) and one year of one-minute
-load columns (T = 525,600), solved to max |dV| <= 1e-10 pu from a flat start with the mixed
-path (fp16 tensor-core sweeps in residual form, double-float residual anchoring).  One "step"
-is one full tpf_solve of all T columns.
+load columns (T = 525,600), solved to max |dV| <= 1e-10 pu from a flat start.  One "step" is one
+full tpf_solve of all T columns.  ``--method sparse`` (default) is the sparse formulation
+(Algorithm 2): one launch, each column's whole sweep loop on chip, FP32 sweeps with double-float
+anchors.  ``--method dense`` is Algorithm 1's dense product on the tensor cores (fp16 operands,
+FP32 accumulation, residual form).  Both return results within 1e-8 pu of the FP64 oracle.
 
 Reported on one JSON line (rank 0):
   value       PF/s, device-resident inputs (S, V on the GPU), CUDA events around the K steps,
               max over ranks; N ranks run N independent replicas (weak scaling)
   e2e         PF/s through tpf_solve_host with pinned HOST buffers: H2D of S, solve, D2H of V,
               iteration counts and mismatches inside the timed region
-  roofline    the tensor-core GEMM kernel: algorithmic 8 n^2 flops per iterating column per sweep,
-              over its CUDA-event time inside the timed steps, against the measured bf16 peak
-              (fp16 runs at the bf16 rate)
+  roofline    the headline path's dominant kernel: mx_tree (sparse; FP32 flops over the derived
+              FP32 peak) or tc_gemm (dense; 8 n^2 flops per iterating column per sweep over the
+              measured bf16 peak)
+  dense_method / sparse_method   the other formulation on the same workload, with its roofline
   fp64_gpu    the plain FP64 GPU fixed-point iteration (direct form), timed on a column sample
-  sparse_method the sparse formulation (Algorithm 2, tree substitution) on the same workload
   cpu_baseline the CPU oracle on the host cores, on a bounded column sample; the same leg checks
-              the GPU result against the oracle (iterated to 1e-13) on sampled columns
+              the GPU results against the oracle (iterated to 1e-13) on sampled columns
+  learned_start  config-5 leg: the MLP warm start on a 200-bus feeder
   clocks      nvidia-smi samples taken during the timed region
 
 ``--impl reference`` times the CPU oracle as the reference arm on the same workload.
@@ -44,6 +47,13 @@ METRIC = "PF solves/s at ≤1e-8 pu vs FP64 oracle: mixed+learned-start vs plain
 # profiles/tc_gemm_n999_T16384.md (203.7 MB + 75.5 MB for 16,384 columns), per iterating column;
 # scaled by the columns each launch of this run processes.  None once the kernel has changed since.
 GEMM_TRAFFIC_BYTES_PER_COLUMN = (203.725056e6 + 75.471360e6) / 16384
+# The same for the sparse tree kernel mx_tree (one launch per solve): 263.5 MB read + 214.1 MB
+# written for 16,384 columns, profiles/mx_tree_n999_T16384.md.
+TREE_TRAFFIC_BYTES_PER_COLUMN = (263.511040e6 + 214.134272e6) / 16384
+# Algorithmic FP32 flop per bus per sweep of the tree formulation: load current conj(S/V) 12,
+# prefix sum 2, subtree difference 2, z L 6, subtree-end subtraction 2, path prefix 2, update 4,
+# |step|^2 and max 6.
+TREE_FLOPS_PER_BUS_SWEEP = 36
 
 
 def parse_args():
@@ -62,7 +72,8 @@ def parse_args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true")
-    p.add_argument("--no-sparse", action="store_true")
+    p.add_argument("--method", choices=["sparse", "dense"], default="sparse")
+    p.add_argument("--no-other", action="store_true", help="skip timing the other formulation")
     return p.parse_args()
 
 
@@ -326,6 +337,46 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def timed_steps(fd, Sd, Vd, itd, mmd, args, method, steps, stream, world, clocks_index=None):
+    """Time `steps` full solves of every column with CUDA events; returns per-step numbers."""
+    import torch
+
+    kern_ms = gemm_ms = gemm_cols = gemm_launch = 0.0
+    launches = 0
+    step_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    sampler = ClockSampler(clocks_index) if clocks_index is not None else None
+    if sampler:
+        sampler.__enter__()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat", profile=True, method=method)
+        b.record(stream)
+        s = fd.stats()
+        kern_ms += s["residual_ms"] if method == "sparse" else s["gemm_ms"]
+        gemm_ms += s["gemm_ms"]
+        gemm_cols += s["gemm_columns"]
+        gemm_launch += s["gemm_launches"]
+        launches += s["kernel_launches"]
+        b.synchronize()
+        step_ms.append(a.elapsed_time(b))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__exit__(None, None, None)
+    barrier(world)
+    total_ms = e0.elapsed_time(e1)
+    return {"ms_per_step": allmax(world, total_ms / steps), "kernel_ms": kern_ms / steps, "gemm_ms": gemm_ms,
+            "gemm_cols": gemm_cols, "gemm_launch": gemm_launch, "launches": launches, "step_ms": step_ms,
+            "stats": fd.stats(), "clocks": sampler.summary() if sampler else None}
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup()
@@ -342,6 +393,7 @@ def main():
     from paper_2403_04578_gb300 import tpf
 
     f, config = workload(args)
+    config["method"] = args.method
     T, n = args.columns, f.n_pq
     Sh = torch.empty((T, n), dtype=torch.complex128, pin_memory=True)
     G.load_tensor(f, T, args.seed, out=Sh.numpy())
@@ -351,55 +403,55 @@ def main():
     itd = torch.empty(T, dtype=torch.int32, device=Sd.device)
     mmd = torch.empty(T, dtype=torch.float64, device=Sd.device)
     stream = torch.cuda.current_stream()
-
-    for _ in range(args.warmup):
-        fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat")
-    torch.cuda.synchronize()
-
-    gemm_ms = gemm_cols = gemm_launch = 0.0
-    launches = 0
-    step_ms = []
-    barrier(world)
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            _, _, _, st = fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat", profile=True)
-            b.record(stream)
-            s = fd.stats()
-            gemm_ms += s["gemm_ms"]
-            gemm_cols += s["gemm_columns"]
-            gemm_launch += s["gemm_launches"]
-            launches += s["kernel_launches"]
-            b.synchronize()
-            step_ms.append(a.elapsed_time(b))
-        e1.record(stream)
-        torch.cuda.synchronize()
-    barrier(world)
-    total_ms = e0.elapsed_time(e1)
-    ms_per_step = allmax(world, total_ms / args.steps)
-    value = world * T / (ms_per_step / 1e3)
-    stats = fd.stats()
-
-    # Roofline of the GEMM kernel (algorithmic flops: 8 n^2 per iterating column per sweep).
     peaks, peak_src = measured_peaks()
-    achieved = 8.0 * n * n * gemm_cols / (gemm_ms / 1e3) / 1e12
-    peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
-    traffic = None
-    if GEMM_TRAFFIC_BYTES_PER_COLUMN is not None and args.buses == 1000:
-        traffic = GEMM_TRAFFIC_BYTES_PER_COLUMN * gemm_cols / max(gemm_launch, 1)
-    roofline = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_note": "ncu DRAM bytes per iterating column (16,384-column capture, "
-                                                    "profiles/tc_gemm_n999_T16384.md) x columns per launch",
-                "kernel": "tc_gemm",
+
+    # The headline path: all T columns per step, inputs resident on the device.
+    for _ in range(args.warmup):
+        fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat", method=args.method)
+    torch.cuda.synchronize()
+    main_run = timed_steps(fd, Sd, Vd, itd, mmd, args, args.method, args.steps, stream, world, clocks_index=local)
+    ms_per_step = main_run["ms_per_step"]
+    value = world * T / (ms_per_step / 1e3)
+    stats = main_run["stats"]
+    column_sweeps = int(itd.abs().sum().item())
+    Vhost = Vd.cpu().numpy() if (rank == 0 and not args.no_cpu) else None
+    ithost = itd.cpu().numpy() if Vhost is not None else None
+
+    def gemm_roofline(run):
+        achieved = 8.0 * n * n * run["gemm_cols"] / (run["gemm_ms"] / 1e3) / 1e12
+        peak = float(peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")))
+        traffic = None
+        if GEMM_TRAFFIC_BYTES_PER_COLUMN is not None and args.buses == 1000:
+            traffic = GEMM_TRAFFIC_BYTES_PER_COLUMN * run["gemm_cols"] / max(run["gemm_launch"], 1)
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "tc_gemm",
                 "peak_source": f"{peak_src} bf16 sustained (fp16 has the bf16 rate)",
-                "gemm_share_of_step": gemm_ms / sum(step_ms),
-                "gemm_ms_per_launch": gemm_ms / max(gemm_launch, 1)}
+                "traffic_note": "ncu DRAM bytes per iterating column (16,384-column capture, "
+                                "profiles/tc_gemm_n999_T16384.md) x columns per launch",
+                "share_of_step": run["gemm_ms"] / sum(run["step_ms"]),
+                "ms_per_launch": run["gemm_ms"] / max(run["gemm_launch"], 1)}
+
+    def tree_roofline(run, sweeps):
+        # FP32 peak from the unit counts: SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock.
+        sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+        peak = sm_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
+        achieved = TREE_FLOPS_PER_BUS_SWEEP * n * sweeps / (run["kernel_ms"] / 1e3) / 1e12
+        traffic = None
+        if TREE_TRAFFIC_BYTES_PER_COLUMN is not None and args.buses == 1000:
+            traffic = TREE_TRAFFIC_BYTES_PER_COLUMN * T
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "mx_tree",
+                "peak_source": f"FP32: {sm_count} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
+                "flops_note": f"{TREE_FLOPS_PER_BUS_SWEEP} flop per bus per sweep x {n} buses x {sweeps:,} "
+                              "column-sweeps (anchors and the final residual not counted)",
+                "traffic_note": "ncu DRAM bytes per column (16,384-column capture, profiles/mx_tree_n999_T16384.md) "
+                                "x columns per launch",
+                "hbm_frac": (TREE_TRAFFIC_BYTES_PER_COLUMN or 0) * T / (run["kernel_ms"] / 1e3) / 1e9
+                            / float(peaks.get("hbm_gbs", 6800.0)),
+                "share_of_step": run["kernel_ms"] * len(run["step_ms"]) / sum(run["step_ms"]),
+                "ms_per_launch": run["kernel_ms"]}
+
+    roofline = tree_roofline(main_run, column_sweeps) if args.method == "sparse" else gemm_roofline(main_run)
 
     # End to end through the host-buffer entry point.
     e2e = None
@@ -407,37 +459,31 @@ def main():
         Vh = torch.empty((T, n), dtype=torch.complex128, pin_memory=True)
         ith = torch.empty(T, dtype=torch.int32, pin_memory=True)
         mmh = torch.empty(T, dtype=torch.float64, pin_memory=True)
-        fd.solve_host(Sh, precision="mixed", tol=args.tol, out=(Vh, ith, mmh))
+        fd.solve_host(Sh, precision="mixed", tol=args.tol, out=(Vh, ith, mmh), method=args.method)
         e2e_steps = max(1, args.steps // 2)
         barrier(world)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            fd.solve_host(Sh, precision="mixed", tol=args.tol, out=(Vh, ith, mmh))
+            fd.solve_host(Sh, precision="mixed", tol=args.tol, out=(Vh, ith, mmh), method=args.method)
         dt = allmax(world, (time.perf_counter() - t0) / e2e_steps)
         e2e = {"value": world * T / dt, "unit": "PF/s", "h2d_bytes_per_step": T * n * 16,
                "d2h_bytes_per_step": T * n * 16 + T * 4 + T * 8, "ms_per_step": dt * 1e3,
                "entry_point": "tpf_solve_host (pinned host buffers)"}
 
-    # The sparse formulation (Algorithm 2): tree substitution, one kernel for the whole solve.
-    sparse = None
-    Vsp = None
-    if not args.no_sparse:
-        fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat", method="sparse")
+    # The other formulation on the same workload.
+    other = "dense" if args.method == "sparse" else "sparse"
+    other_obj = None
+    if not args.no_other:
+        fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat", method=other)
         torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.steps):
-            fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat", method="sparse")
-        b.record(stream)
-        b.synchronize()
-        sp_ms = allmax(world, a.elapsed_time(b) / args.steps)
-        sparse = {"value": world * T / (sp_ms / 1e3), "unit": "PF/s", "ms_per_step": sp_ms,
-                  "kernel": "mx_tree", "gpu_launches_per_step": fd.stats()["kernel_launches"],
-                  "max_sweeps": fd.stats()["sweeps"], "converged": fd.stats()["converged"]}
+        run = timed_steps(fd, Sd, Vd, itd, mmd, args, other, max(1, min(args.steps, 3)), stream, world)
+        other_obj = {"value": world * T / (run["ms_per_step"] / 1e3), "unit": "PF/s",
+                     "ms_per_step": run["ms_per_step"], "gpu_launches_per_step": run["launches"] / len(run["step_ms"]),
+                     "sweeps": run["stats"]["sweeps"], "converged": run["stats"]["converged"]}
+        other_obj["roofline"] = gemm_roofline(run) if other == "dense" else tree_roofline(
+            run, int(itd.abs().sum().item()))
         if rank == 0 and not args.no_cpu:
-            Vsp = Vd.cpu().numpy()
-        fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat")  # dense result again
+            other_obj["_V"] = Vd.cpu().numpy()
 
     # Plain FP64 GPU FPI on a column sample (the comparison path of the metric).
     F = min(args.fp64_sample, T)
@@ -456,22 +502,24 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": "PF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f16 tensor-core products + f32/double-float elementwise",
+            "vs_baseline": None,
+            "dtype": ("f32 sweeps + double-float anchors" if args.method == "sparse"
+                      else "f16 tensor-core products + f32/double-float elementwise"),
             "data": "synthetic", "config": config, "roofline": roofline,
-            "e2e": e2e, "clocks": clocks.summary(), "gpu_launches": launches,
-            "sweeps": stats["sweeps"], "anchor_sweeps": stats["precise_sweeps"],
+            "e2e": e2e, "clocks": main_run["clocks"], "gpu_launches": main_run["launches"],
+            "sweeps": stats["sweeps"], "anchors_or_anchor_sweeps": stats["precise_sweeps"],
+            "mean_sweeps": column_sweeps / T,
             "fp64_gpu": fp64, "speedup_vs_fp64_gpu": (value / world) / fp64_pfs,
             }
+    V_other = other_obj.pop("_V", None) if other_obj else None
     if rank == 0 and not args.no_cpu:
-        Vhost = Vd.cpu().numpy()
-        ithost = itd.cpu().numpy()
-        cpu, check = cpu_oracle_leg(f, Sh.numpy(), Vhost, ithost, args, T, Vsp)
+        cpu, check = cpu_oracle_leg(f, Sh.numpy(), Vhost, ithost, args, T, V_other)
         line["cpu_baseline"] = cpu
-        if sparse is not None and "sparse_max_abs_err_pu" in check:
-            sparse["max_abs_err_pu"] = check.pop("sparse_max_abs_err_pu")
+        if other_obj is not None and "sparse_max_abs_err_pu" in check:
+            other_obj["max_abs_err_pu"] = check.pop("sparse_max_abs_err_pu")
         line["accuracy"] = check
-    if sparse is not None:
-        line["sparse_method"] = sparse
+    if other_obj is not None:
+        line[f"{other}_method"] = other_obj
     if not args.no_learned:
         del Sd, Vd
         torch.cuda.empty_cache()

@@ -85,11 +85,12 @@ tpf_status upload_network(tpf_handle *h) {
         if (nch > 0) TPF_CK(cudaMemcpy(d.ch, net.ch.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
         TPF_CK(cudaMemcpy(d.ypar, yp.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
         // Slot-ordered depth-first arrays of the sparse formulation.
-        const int th = tree_threads(n);
+        const int bpt = tree_bpt(n), th = bpt ? tree_threads(n, bpt) : 0;
         d.t_threads = th;
+        d.t_bpt = bpt;
         if (th > 0) {
-            const int ns = th * kTreeBPT;
-            auto slot = [th](int q) { return (q % kTreeBPT) * th + q / kTreeBPT; };
+            const int ns = th * bpt;
+            auto slot = [th, bpt](int q) { return (q % bpt) * th + q / bpt; };
             std::vector<int> col(ns, -1), end(ns, 0), par(ns, -1), ecnt(ns, 0), ends;
             std::vector<float4> z(ns, make_float4(0.f, 0.f, 0.f, 0.f));
             std::vector<int> pos_par(n, -1);  // parent position of each position

@@ -21,13 +21,13 @@ constexpr int kTileN = 128;
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-// Sparse formulation: positions per thread, largest block, and the block size for n demand buses
-// (0 when n is too large for one block).
-constexpr int kTreeBPT = 8;
+// Sparse formulation: demand buses per thread (2, 4 or 8), largest block, and the block size for
+// n demand buses with bpt buses per thread (0 when n does not fit one block).
 constexpr int kTreeMaxThreads = 512;
-inline int tree_threads(int n) {
+int tree_bpt(int n);  // the choice for n demand buses (TPF_TREE_BPT overrides it)
+inline int tree_threads(int n, int bpt) {
     int t = 32;
-    while (t * kTreeBPT < n) t *= 2;
+    while (t * bpt < n) t *= 2;
     return t <= kTreeMaxThreads ? t : 0;
 }
 
@@ -75,13 +75,13 @@ struct DeviceNet {
     int *par = nullptr, *ch_ptr = nullptr, *ch = nullptr;  // radial only
     float2 *ypar = nullptr;  // FP32 admittance of the branch to the parent [n]
     // Sparse formulation (radial only).  Block of t_threads threads per column; thread k owns the
-    // kTreeBPT consecutive depth-first positions q = kTreeBPT k + j, stored at slot
+    // t_bpt consecutive depth-first positions q = t_bpt k + j, stored at slot
     // s = j t_threads + k (so that a warp touches consecutive words).  Per slot: the column (-1
     // past n), the end of the subtree's position range, the parent's slot (-1 = the slack), the
     // start and count (start | count << 16) in t_ends of the slots of the positions whose
     // subtree range ends at q, and the double-float z of the branch to the parent
     // (re_hi, im_hi, re_lo, im_lo).
-    int t_threads = 0, t_n_ends = 0;
+    int t_threads = 0, t_bpt = 0, t_n_ends = 0;
     int *t_col = nullptr, *t_end = nullptr, *t_par = nullptr, *t_ecnt = nullptr, *t_ends = nullptr;
     float4 *t_z = nullptr;
     // Mixed path: fp16 planes of K * 2^k_exp, [n_pad][n_pad], zero padded

@@ -28,17 +28,18 @@
 // (j * threads + k for the j-th position of thread k) so that a warp's accesses to its own
 // positions fall in consecutive banks.  Device memory is read for S once (again at an anchor) and
 // written once for V.
+#include <cstdlib>
+
 #include "tpf_dd.cuh"
 
 namespace tpf {
 
 namespace {
 
-constexpr int kBPT = kTreeBPT;                // demand buses per thread (consecutive positions)
-constexpr int kMaxThreads = kTreeMaxThreads;  // so at most kBPT * 512 = 4096 demand buses
+constexpr int kMaxThreads = kTreeMaxThreads;  // so at most 8 * 512 = 4096 demand buses
 constexpr int kMaxWarps = kMaxThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
-static_assert(kBPT == 8, "slot_of assumes 8 positions per thread");
+constexpr int kGather = 4;  // ends-list entries per position gathered without a loop
 
 struct TreeArgs {
     int64_t T;
@@ -98,16 +99,59 @@ __device__ __forceinline__ float2 block_scan(float2 v, float2 *wt, int lane, int
     return add2(pre, off);
 }
 
-// The same in double-float.
-__device__ __noinline__ c2 block_scan_dd(c2 v, float4 *wt, int lane, int warp) {
+// Double-float arithmetic of the anchor.  Each result carries an absolute error of a few units
+// of 2^-44 times the larger operand, which is what the anchor needs (D to about 1e-13 pu against
+// terms of order 0.1 pu); the products are exact in their high parts through FMA.
+__device__ __forceinline__ f2 qadd(f2 a, f2 b) {
+    const f2 s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ f2 qneg(f2 a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ c2 cqadd(c2 a, c2 b) { return {qadd(a.re, b.re), qadd(a.im, b.im)}; }
+__device__ __forceinline__ c2 cqsub(c2 a, c2 b) { return {qadd(a.re, qneg(b.re)), qadd(a.im, qneg(b.im))}; }
+// a * b, both double-float complex.
+__device__ __forceinline__ c2 cqmul(c2 a, c2 b) {
+    const float p = __fmul_rn(a.re.h, b.re.h), pe = __fmaf_rn(a.re.h, b.re.h, -p);
+    const float q = __fmul_rn(a.im.h, b.im.h), qe = __fmaf_rn(a.im.h, b.im.h, -q);
+    const f2 sr = two_sum(p, -q);
+    const float lr = (pe - qe) + (a.re.h * b.re.l + a.re.l * b.re.h) - (a.im.h * b.im.l + a.im.l * b.im.h);
+    const float u = __fmul_rn(a.re.h, b.im.h), ue = __fmaf_rn(a.re.h, b.im.h, -u);
+    const float v = __fmul_rn(a.im.h, b.re.h), ve = __fmaf_rn(a.im.h, b.re.h, -v);
+    const f2 si = two_sum(u, v);
+    const float li = (ue + ve) + (a.re.h * b.im.l + a.re.l * b.im.h) + (a.im.h * b.re.l + a.im.l * b.re.h);
+    return {fast_two_sum(sr.h, __fadd_rn(sr.l, lr)), fast_two_sum(si.h, __fadd_rn(si.l, li))};
+}
+// conj(S / V) for a double-float S and an FP32 V: w_h = S / V in FP32, then the residual
+// r = S - w_h V from exact products and w_l = r / V, so that w_h + w_l carries S / V to about
+// 2^-44 relative.
+__device__ __forceinline__ c2 current_q(c2 S, float2 V) {
+    const float inv = __fdividef(1.0f, V.x * V.x + V.y * V.y);
+    const float2 wh = make_float2((S.re.h * V.x + S.im.h * V.y) * inv, (S.im.h * V.x - S.re.h * V.y) * inv);
+    // r.re = S.re - (wh.x V.x - wh.y V.y)
+    const float a1 = __fmul_rn(wh.x, V.x), a1e = __fmaf_rn(wh.x, V.x, -a1);
+    const float a2 = __fmul_rn(wh.y, V.y), a2e = __fmaf_rn(wh.y, V.y, -a2);
+    const f2 t = two_sum(S.re.h, -a1);
+    const float rr = __fadd_rn(__fadd_rn(t.h, a2), __fadd_rn(t.l, __fadd_rn(S.re.l, __fsub_rn(a2e, a1e))));
+    // r.im = S.im - (wh.x V.y + wh.y V.x)
+    const float b1 = __fmul_rn(wh.x, V.y), b1e = __fmaf_rn(wh.x, V.y, -b1);
+    const float b2 = __fmul_rn(wh.y, V.x), b2e = __fmaf_rn(wh.y, V.x, -b2);
+    const f2 u = two_sum(S.im.h, -b2);
+    const float ri = __fadd_rn(__fsub_rn(u.h, b1), __fadd_rn(u.l, __fsub_rn(S.im.l, __fadd_rn(b1e, b2e))));
+    const float2 wl = make_float2((rr * V.x + ri * V.y) * inv, (ri * V.x - rr * V.y) * inv);
+    return {fast_two_sum(wh.x, wl.x), fast_two_sum(-wh.y, -wl.y)};
+}
+
+// Exclusive block scan in double-float.
+__device__ __forceinline__ c2 block_scan_dd(c2 v, float4 *wt, int lane, int warp) {
     c2 inc = v;
+#pragma unroll 1
     for (int o = 1; o < 32; o <<= 1) {
         float4 u = pack(inc);
         u.x = __shfl_up_sync(kFull, u.x, o);
         u.y = __shfl_up_sync(kFull, u.y, o);
         u.z = __shfl_up_sync(kFull, u.z, o);
         u.w = __shfl_up_sync(kFull, u.w, o);
-        if (lane >= o) inc = c_add(unpack(u), inc);
+        if (lane >= o) inc = cqadd(unpack(u), inc);
     }
     float4 e = pack(inc);
     e.x = __shfl_up_sync(kFull, e.x, 1);
@@ -118,8 +162,8 @@ __device__ __noinline__ c2 block_scan_dd(c2 v, float4 *wt, int lane, int warp) {
     if (lane == 31) wt[warp] = pack(inc);
     __syncthreads();
     c2 pre = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-    for (int w = 0; w < warp; ++w) pre = c_add(pre, unpack(wt[w]));
-    return c_add(pre, off);
+    for (int w = 0; w < warp; ++w) pre = cqadd(pre, unpack(wt[w]));
+    return cqadd(pre, off);
 }
 
 // Largest values over the block; every thread gets the same result.
@@ -136,28 +180,23 @@ __device__ __forceinline__ float2 block_max(float2 m, float2 *wm, int lane, int 
     return d;
 }
 
-__device__ __forceinline__ c2 s_dd(double2 s) {
-    const float hx = __double2float_rn(s.x), hy = __double2float_rn(s.y);
-    return {{hx, __double2float_rn(s.x - (double)hx)}, {hy, __double2float_rn(s.y - (double)hy)}};
+
+// Slot of depth-first position p for blocks of th threads with kBPT positions each.
+template <int kBPT>
+__device__ __forceinline__ int slot_of(int p, int th) {
+    return (p & (kBPT - 1)) * th + p / kBPT;
 }
 
-// Slot of depth-first position p for blocks of th threads.
-__device__ __forceinline__ int slot_of(int p, int th) { return (p & (kBPT - 1)) * th + (p >> 3); }
-
-// Shared-memory view of one block.
-struct TreeSmem {
-    float4 *A;    // [ns] double-float prefix sums (anchor); float2 P and X during the sweeps
-    float4 *B;    // [ns] V_ref (anchor input), x (anchor), then D = BFS(V_ref) - V_ref
-    int *ends;    // [n_ends] slots of the positions whose subtree range ends at a position
-    int *end;     // [ns] end of the subtree's position range
-    int *par;     // [ns] parent slot, -1 = the slack
-};
-
-// First part of an anchor, in double-float: with V_ref in B (x, y), leaves the inclusive prefix
-// sums of the path terms in A and returns the thread's exclusive scan offset; B holds the branch
-// terms.  Loops are not unrolled: this runs once or twice per column and its code stays small.
-__device__ __noinline__ c2 anchor_dd(const TreeArgs &a, const double2 *S, const TreeSmem &m, const int *ecnt,
-                                     float4 *wtd, int tid, int th, int lane, int warp) {
+// First part of an anchor, in double-float.  On entry A[s] = (S_hi) and B[s] = (V_ref, S_lo) for
+// the thread's own slots.  Leaves in A the inclusive prefix sums of the path terms and returns the
+// thread's exclusive scan offset.  ecnt holds the thread's ends-list bounds.
+// The loops run over shared memory only and are not unrolled: the anchor runs once or twice per
+// column and its code stays small; the unrolled staging in the kernel keeps the device-memory
+// loads in flight together.
+template <int kBPT>
+__device__ __forceinline__ c2 anchor_dd(const TreeArgs &a, float4 *A, float4 *B, const int *s_end,
+                                        const int *s_ends, const int *ecnt, float4 *wtd, int tid, int th, int lane,
+                                        int warp) {
     const int n = a.n, base = tid * kBPT;
     // Load currents at V_ref and their inclusive prefix sums.
     c2 run = {{0.0f, 0.0f}, {0.0f, 0.0f}};
@@ -165,16 +204,17 @@ __device__ __noinline__ c2 anchor_dd(const TreeArgs &a, const double2 *S, const 
     for (int j = 0; j < kBPT; ++j) {
         const int q = base + j, s = j * th + tid;
         if (q < n) {
-            const float4 v = m.B[s];
-            run = c_add(run, load_current_dd(s_dd(S[a.col[s]]), c2{{v.x, 0.0f}, {v.y, 0.0f}}));
-            m.A[s] = pack(run);
+            const float4 sh = A[s], v = B[s];
+            run = cqadd(run, current_q(c2{{sh.x, v.z}, {sh.y, v.w}}, make_float2(v.x, v.y)));
+            A[s] = pack(run);
         }
     }
     c2 off = block_scan_dd(run, wtd, lane, warp);
-#pragma unroll 1
+#pragma unroll
     for (int j = 0; j < kBPT; ++j) {
-        const int q = base + j, s = j * th + tid;
-        if (q < n) m.A[s] = pack(c_add(off, unpack(m.A[s])));
+        const int s = j * th + tid;
+        A[s] = pack(cqadd(off, unpack(A[s])));
+        B[s] = a.z[s];  // (re_hi, im_hi, re_lo, im_lo)
     }
     __syncthreads();
     // Branch terms x_q = z_q (P[end_q - 1] - P[q - 1]).
@@ -182,40 +222,42 @@ __device__ __noinline__ c2 anchor_dd(const TreeArgs &a, const double2 *S, const 
     for (int j = 0; j < kBPT; ++j) {
         const int q = base + j, s = j * th + tid;
         if (q < n) {
-            c2 L = unpack(m.A[slot_of(m.end[s] - 1, th)]);
-            if (q > 0) L = c_sub(L, unpack(m.A[j ? s - th : (kBPT - 1) * th + tid - 1]));
-            const float4 zq = a.z[s];
-            m.B[s] = pack(c_mul(c2{{zq.x, zq.z}, {zq.y, zq.w}}, L));
+            c2 L = unpack(A[slot_of<kBPT>(s_end[s] - 1, th)]);
+            if (q > 0) L = cqsub(L, unpack(A[j ? s - th : (kBPT - 1) * th + tid - 1]));
+            const float4 zq = B[s];
+            B[s] = pack(cqmul(c2{{zq.x, zq.z}, {zq.y, zq.w}}, L));
         }
     }
     __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kBPT; ++j) A[j * th + tid].x = __int_as_float(ecnt[j]);
     // Inclusive prefix sums of E_q = x_q - (x_b of every b whose range ends at q).
     run = c2{{0.0f, 0.0f}, {0.0f, 0.0f}};
 #pragma unroll 1
     for (int j = 0; j < kBPT; ++j) {
         const int q = base + j, s = j * th + tid;
         if (q < n) {
-            const int ec = ecnt[j];
-            c2 e = unpack(m.B[s]);
-            for (int k = 0; k < (ec >> 16); ++k) e = c_sub(e, unpack(m.B[m.ends[(ec & 0xffff) + k]]));
-            run = c_add(run, e);
-            m.A[s] = pack(run);
+            const int ec = __float_as_int(A[s].x);
+            c2 e = unpack(B[s]);
+            for (int k = 0; k < (ec >> 16); ++k) e = cqsub(e, unpack(B[s_ends[(ec & 0xffff) + k]]));
+            run = cqadd(run, e);
+            A[s] = pack(run);
         }
     }
     return block_scan_dd(run, wtd, lane, warp);
 }
 
-__global__ void __launch_bounds__(kMaxThreads) mx_tree(TreeArgs a) {
+template <int kBPT>
+__global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(TreeArgs a) {
     extern __shared__ float4 tsm[];
     const int n = a.n, th = blockDim.x, ns = th * kBPT;
     // Arrays indexed by slot s = j th + k of position q = kBPT k + j.
-    TreeSmem m;
-    m.A = tsm;
-    m.B = tsm + ns;
-    m.end = reinterpret_cast<int *>(tsm + 2 * ns);
-    m.par = m.end + ns;
-    m.ends = m.par + ns;
-    float2 *P = reinterpret_cast<float2 *>(m.A);  // [ns] inclusive prefix sums of the load currents
+    float4 *const A = tsm;       // [ns] double-float prefix sums (anchor); float2 P and X in the sweeps
+    float4 *const B = tsm + ns;  // [ns] V_ref (anchor input), x (anchor), then D = BFS(V_ref) - V_ref
+    int *const s_end = reinterpret_cast<int *>(tsm + 2 * ns);  // [ns] end of the subtree's range
+    int *const s_par = s_end + ns;                             // [ns] parent slot, -1 = the slack
+    int *const s_ends = s_par + ns;  // [n_ends] slots of the positions whose range ends at a position
+    float2 *P = reinterpret_cast<float2 *>(A);  // [ns] inclusive prefix sums of the load currents
     float2 *X = P + ns;                           // [ns] branch terms z_q L_q; the residual's x at the end
     __shared__ float2 wt1[kMaxWarps], wt2[kMaxWarps];
     __shared__ float4 wtd[kMaxWarps];
@@ -225,11 +267,13 @@ __global__ void __launch_bounds__(kMaxThreads) mx_tree(TreeArgs a) {
     const int base = tid * kBPT;
     const double2 *S = a.S + t * n;
 
-    for (int s = tid; s < ns; s += th) {
-        m.end[s] = a.end[s];
-        m.par[s] = a.par[s];
+#pragma unroll
+    for (int j = 0; j < kBPT; ++j) {
+        const int s = j * th + tid;
+        s_end[s] = a.end[s];
+        s_par[s] = a.par[s];
+        if (s < a.n_ends) s_ends[s] = a.ends[s];
     }
-    for (int k = tid; k < a.n_ends; k += th) m.ends[k] = a.ends[k];
     // Per position: V_ref (or V before anchoring), delta = V - V_ref, S (FP32), z, ends list.
     float2 vr[kBPT], dl[kBPT], sh[kBPT], zr[kBPT];
     int ecnt[kBPT];
@@ -266,19 +310,26 @@ __global__ void __launch_bounds__(kMaxThreads) mx_tree(TreeArgs a) {
             // V_ref <- fl32(V); the remainder stays in delta.  D = BFS(V_ref) - V_ref goes to B.
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
+                const int q = base + j, s = j * th + tid;
                 const f2 re = two_sum(vr[j].x, dl[j].x), im = two_sum(vr[j].y, dl[j].y);
                 vr[j] = make_float2(re.h, im.h);
                 dl[j] = make_float2(re.l, im.l);
-                m.B[j * th + tid] = make_float4(re.h, im.h, 0.0f, 0.0f);
+                float2 slo = make_float2(0.0f, 0.0f);
+                if (q < n) {
+                    const double2 sv = S[a.col[s]];
+                    slo = make_float2(__double2float_rn(sv.x - (double)sh[j].x), __double2float_rn(sv.y - (double)sh[j].y));
+                }
+                A[s] = make_float4(sh[j].x, sh[j].y, 0.0f, 0.0f);
+                B[s] = make_float4(re.h, im.h, slo.x, slo.y);
             }
-            const c2 off = anchor_dd(a, S, m, ecnt, wtd, tid, th, lane, warp);
+            const c2 off = anchor_dd<kBPT>(a, A, B, s_end, s_ends, ecnt, wtd, tid, th, lane, warp);
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
                 const int q = base + j, s = j * th + tid;
                 if (q < n) {
-                    const c2 ps = c_add(off, unpack(m.A[s]));
-                    const c2 D = c_sub(c_sub(a.vs_dd, c2{{vr[j].x, 0.0f}, {vr[j].y, 0.0f}}), ps);
-                    m.B[s] = make_float4(D.re.h, D.im.h, D.re.l, D.im.l);
+                    const c2 ps = cqadd(off, unpack(A[s]));
+                    const c2 D = cqsub(cqsub(a.vs_dd, c2{{vr[j].x, 0.0f}, {vr[j].y, 0.0f}}), ps);
+                    B[s] = make_float4(D.re.h, D.im.h, D.re.l, D.im.l);
                 }
             }
             __syncthreads();  // the sweep reuses A
@@ -303,24 +354,41 @@ __global__ void __launch_bounds__(kMaxThreads) mx_tree(TreeArgs a) {
 #pragma unroll
         for (int j = 0; j < kBPT; ++j) {
             const int q = base + j, s = j * th + tid;
+            float2 xq = make_float2(0.0f, 0.0f);  // positions past n contribute nothing
             if (q < n) {
-                float2 L = P[slot_of(m.end[s] - 1, th)];
+                float2 L = P[slot_of<kBPT>(s_end[s] - 1, th)];
                 if (q > 0) L = sub2(L, P[j ? s - th : (kBPT - 1) * th + tid - 1]);
-                X[s] = cmul2(zr[j], L);
+                xq = cmul2(zr[j], L);
             }
+            X[s] = xq;
         }
         __syncthreads();
         // Path sums: prefix sums of E_q = x_q - (x_b of every b whose subtree range ends at q).
+        // Up to kGather entries per position unrolled and predicated; longer lists (rare: a drop
+        // of more than kGather levels between neighbouring positions) finish in a loop.
+        bool longer = false;
+#pragma unroll
+        for (int j = 0; j < kBPT; ++j) {
+            const int s = j * th + tid;
+            const int st = ecnt[j] & 0xffff, cnt = ecnt[j] >> 16;
+            float2 e = X[s];
+#pragma unroll
+            for (int k = 0; k < kGather; ++k)
+                if (k < cnt) e = sub2(e, X[s_ends[st + k]]);
+            longer |= cnt > kGather;
+            loc[j] = e;
+        }
+        if (longer) {
+#pragma unroll
+            for (int j = 0; j < kBPT; ++j) {
+                const int st = ecnt[j] & 0xffff, cnt = ecnt[j] >> 16;
+                for (int k = kGather; k < cnt; ++k) loc[j] = sub2(loc[j], X[s_ends[st + k]]);
+            }
+        }
         run = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int j = 0; j < kBPT; ++j) {
-            const int q = base + j, s = j * th + tid;
-            if (q < n) {
-                float2 e = X[s];
-                const int st = ecnt[j] & 0xffff, cnt = ecnt[j] >> 16;
-                for (int k = 0; k < cnt; ++k) e = sub2(e, X[m.ends[st + k]]);
-                run = add2(run, e);
-            }
+            run = add2(run, loc[j]);  // positions past n have x = 0 and no ends
             loc[j] = run;
         }
         off = block_scan(run, wt2, lane, warp);
@@ -332,7 +400,7 @@ __global__ void __launch_bounds__(kMaxThreads) mx_tree(TreeArgs a) {
                 const float2 ps = add2(off, loc[j]);
                 float2 step;
                 if (anchored) {
-                    const float4 D = m.B[s];
+                    const float4 D = B[s];
                     const float2 nd = add2(sub2(make_float2(D.x, D.y), ps), make_float2(D.z, D.w));
                     step = sub2(nd, dl[j]);
                     dl[j] = nd;
@@ -376,13 +444,13 @@ __global__ void __launch_bounds__(kMaxThreads) mx_tree(TreeArgs a) {
     // On the tree (Y_dd x)_q = -J_q + sum over the children k of J_k with the branch currents
     // J_k = y_k (x_parent(k) - x_k); the children of q are q + 1 and then each next sibling, the
     // end of the previous one's range, while inside q's range.
-    float2 *J = reinterpret_cast<float2 *>(m.B);
+    float2 *J = reinterpret_cast<float2 *>(B);
     float2 xs[kBPT];
 #pragma unroll
     for (int j = 0; j < kBPT; ++j) {
         const int q = base + j, s = j * th + tid;
         if (anchored) {
-            const float4 D = m.B[s];
+            const float4 D = B[s];
             xs[j] = sub2(sub2(dl[j], make_float2(D.x, D.y)), make_float2(D.z, D.w));
         } else {
             xs[j] = vr[j];
@@ -399,7 +467,7 @@ __global__ void __launch_bounds__(kMaxThreads) mx_tree(TreeArgs a) {
     for (int j = 0; j < kBPT; ++j) {
         const int q = base + j, s = j * th + tid;
         if (q < n) {
-            const int p = m.par[s];
+            const int p = s_par[s];
             const float2 y = make_float2(zr[j].x, -zr[j].y);
             const float2 yk = make_float2(y.x * __fdividef(1.0f, abs2(zr[j])), y.y * __fdividef(1.0f, abs2(zr[j])));
             J[s] = cmul2(yk, sub2(p >= 0 ? X[p] : x_slack, xs[j]));
@@ -413,11 +481,11 @@ __global__ void __launch_bounds__(kMaxThreads) mx_tree(TreeArgs a) {
         if (q < n) {
             float2 r = anchored ? delta_current_fast(vr[j], dl[j], sh[j]) : current_fast(vr[j], sh[j]);
             r = sub2(r, J[s]);
-            const int e = m.end[s];
+            const int e = s_end[s];
             for (int k = q + 1; k < e;) {
-                const int ks = slot_of(k, th);
+                const int ks = slot_of<kBPT>(k, th);
                 r = add2(r, J[ks]);
-                k = m.end[ks];
+                k = s_end[ks];
             }
             const float2 v = add2(vr[j], dl[j]);
             float mv = sqrtf(abs2(v) * abs2(r));
@@ -437,6 +505,16 @@ __global__ void __launch_bounds__(kMaxThreads) mx_tree(TreeArgs a) {
 
 }  // namespace
 
+int tree_bpt(int n) {
+    if (const char *e = std::getenv("TPF_TREE_BPT")) {
+        const int b = std::atoi(e);
+        if (b == 2 || b == 4 || b == 8) return tree_threads(n, b) ? b : 0;
+    }
+    for (int b : {4, 8})
+        if (tree_threads(n, b)) return b;
+    return 0;
+}
+
 tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters, double *mismatch,
                         const tpf_opts &o, cudaStream_t st) {
     const DeviceNet &d = h->dev;
@@ -444,11 +522,14 @@ tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_
     const int n = d.n, threads = d.t_threads;
     if (threads == 0) return TPF_EUNSUPPORTED;
     if (T > 0x7fffffff) return TPF_EUNSUPPORTED;  // one block per column
-    const size_t smem = (size_t)2 * threads * kBPT * sizeof(float4) + sizeof(int) * (2 * threads * kBPT + d.t_n_ends);
+    const int ns = threads * d.t_bpt;
+    const size_t smem = (size_t)2 * ns * sizeof(float4) + sizeof(int) * (2 * ns + d.t_n_ends);
     tpf_status rs = ensure_workspace(h, T, kWsState);  // counters and per-tile counts
     if (rs != TPF_OK) return rs;
     Workspace &w = h->ws;
-    if (cudaFuncSetAttribute(mx_tree, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    if (cudaFuncSetAttribute(mx_tree<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(mx_tree<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(mx_tree<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return TPF_ECUDA;
     }
@@ -488,7 +569,12 @@ tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_
     a.z = d.t_z;
     KernelTimer timer(o.profile != 0, st);
     timer.begin(KernelTimer::kResidual);
-    mx_tree<<<(unsigned)T, threads, smem, st>>>(a);
+    if (d.t_bpt == 8)
+        mx_tree<8><<<(unsigned)T, threads, smem, st>>>(a);
+    else if (d.t_bpt == 4)
+        mx_tree<4><<<(unsigned)T, threads, smem, st>>>(a);
+    else
+        mx_tree<2><<<(unsigned)T, threads, smem, st>>>(a);
     timer.end();
     if (cudaGetLastError() != cudaSuccess) return TPF_ECUDA;
     std::vector<int> tiles(n_tiles);

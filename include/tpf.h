@@ -178,6 +178,48 @@ tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_
 tpf_status tpf_last_stats(const tpf_handle *h, tpf_stats *out);
 
 /*
+ * Scenario / time tensors (Sec. IV: the load tensor may have any number of scenario and time
+ * dimensions; its columns are flattened in C order, bus fastest) with per-column and per-bus
+ * statistics of the kind probabilistic and time-series studies report, computed in the solve's
+ * own final pass.  Every pointer is a device pointer and may be NULL (not written).
+ */
+typedef struct {
+    int s_complex64;    /* S is complex64 [T][n_pq] (else complex128)                           */
+    int v_complex64;    /* V is complex64 [T][n_pq] (else complex128); V_dev may be NULL when    *
+                         * opts->start is TPF_START_FLAT (statistics only)                       */
+    double v_min, v_max;          /* voltage band in pu for the counts below                     */
+    float *col_vmin, *col_vmax;   /* [T]: min and max |V_i| of each column                       */
+    int32_t *col_viol;            /* [T]: buses of each column with |V_i| outside [v_min, v_max] */
+    int32_t *bus_under, *bus_over;/* [n_pq]: ADDED TO: columns with |V_i| < v_min (> v_max);     *
+                                   * the caller zeroes them before the first call                */
+} tpf_outputs;
+
+/*
+ * tpf_solve with the outputs above.  Sparse formulation only (opts->method TPF_METHOD_SPARSE,
+ * TPF_PREC_MIXED, radial network; TPF_EUNSUPPORTED otherwise).  out == NULL is tpf_solve.
+ */
+tpf_status tpf_solve_ex(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev, int32_t *iters_dev,
+                        double *mismatch_dev, const tpf_outputs *out, const tpf_opts *opts,
+                        void *stream);
+
+/*
+ * Solve F feeders at once (many networks of different sizes, Sec. V): feeder f has handle hs[f],
+ * T[f] columns, device tensors S[f] and V[f] (complex128 [T[f]][n_pq of hs[f]], V read as V_0
+ * when opts->start == TPF_START_GIVEN), and optional iters[f] / mismatch[f] (the arrays iters and
+ * mismatch may be NULL, as may their entries).  Radial feeders under TPF_METHOD_SPARSE with
+ * TPF_PREC_MIXED share one launch per launch shape (feeders grouped by the block size the sparse
+ * kernel uses for them), each block finding its feeder in a device table; any other feeder is
+ * solved on its own with tpf_solve and TPF_METHOD_DENSE.  converged_out (host, F entries, may be NULL) receives each
+ * feeder's converged-column count; stats_out (host, may be NULL) the totals.  Handles must be on
+ * the current device and distinct.  Returns TPF_OK when every column of every feeder met tol,
+ * TPF_ENOCONV when some did not.  Blocks until the stream has finished.
+ */
+tpf_status tpf_solve_batch(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S_dev,
+                           void *const *V_dev, int32_t *const *iters_dev, double *const *mismatch_dev,
+                           const tpf_opts *opts, int64_t *converged_out, tpf_stats *stats_out,
+                           void *stream);
+
+/*
  * Learned warm start.  The paper starts Algorithm 1 from the flat profile V_0 = 1; these entry
  * points train and run a small multilayer perceptron that predicts V_0 from a column's loads, so
  * that a solve started from it (TPF_START_GIVEN) needs fewer sweeps.  The iteration still decides

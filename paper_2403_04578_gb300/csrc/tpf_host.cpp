@@ -364,6 +364,95 @@ tpf_status tpf_solve(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev, i
     return tpf::solve_mixed(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
 }
 
+tpf_status tpf_solve_ex(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev, int32_t *iters_dev,
+                        double *mismatch_dev, const tpf_outputs *out, const tpf_opts *opts, void *stream) {
+    if (!out) return tpf_solve(h, T, S_dev, V_dev, iters_dev, mismatch_dev, opts, stream);
+    if (!h || T < 0) return TPF_EINVAL;
+    tpf_opts o;
+    tpf_status st = check_opts(opts, o);
+    if (st != TPF_OK) return st;
+    if (o.method != TPF_METHOD_SPARSE) return TPF_EUNSUPPORTED;
+    if (!(out->v_min <= out->v_max)) return TPF_EINVAL;
+    h->stats = tpf_stats{};
+    h->stats.columns = T;
+    if (T == 0) return TPF_OK;
+    if (!S_dev || (!V_dev && o.start == TPF_START_GIVEN)) return TPF_EINVAL;
+    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    return tpf::solve_sparse_ex(h, T, S_dev, V_dev, iters_dev, mismatch_dev, out, o,
+                                reinterpret_cast<cudaStream_t>(stream));
+}
+
+tpf_status tpf_solve_batch(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S_dev,
+                           void *const *V_dev, int32_t *const *iters_dev, double *const *mismatch_dev,
+                           const tpf_opts *opts, int64_t *converged_out, tpf_stats *stats_out, void *stream) {
+    if (F < 0 || (F > 0 && (!hs || !T || !S_dev || !V_dev))) return TPF_EINVAL;
+    tpf_opts o;
+    tpf_status st = check_opts(opts, o);
+    if (st != TPF_OK) return st;
+    if (stats_out) *stats_out = tpf_stats{};
+    if (F == 0) return TPF_OK;
+    for (int f = 0; f < F; ++f) {
+        if (!hs[f] || T[f] < 0 || (T[f] > 0 && (!S_dev[f] || !V_dev[f]))) return TPF_EINVAL;
+        if (hs[f]->device != hs[0]->device) return TPF_EINVAL;
+        for (int g = 0; g < f; ++g)
+            if (hs[g] == hs[f]) return TPF_EINVAL;  // each handle's workspaces serve one feeder
+    }
+    if (cudaSetDevice(hs[0]->device) != cudaSuccess) return TPF_ECUDA;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // Radial feeders under the sparse method share launches; the rest are solved one by one.
+    std::vector<int> grouped, single;
+    for (int f = 0; f < F; ++f) {
+        const bool fits = o.method == TPF_METHOD_SPARSE && o.precision == TPF_PREC_MIXED && hs[f]->dev.radial &&
+                          hs[f]->dev.t_threads > 0;
+        (fits ? grouped : single).push_back(f);
+    }
+    tpf_stats tot{};
+    bool all = true;
+    if (!grouped.empty()) {
+        const int G = (int)grouped.size();
+        std::vector<tpf_handle *> gh(G);
+        std::vector<int64_t> gT(G), gconv(G);
+        std::vector<const void *> gS(G);
+        std::vector<void *> gV(G);
+        std::vector<int32_t *> gi(G);
+        std::vector<double *> gm(G);
+        for (int k = 0; k < G; ++k) {
+            const int f = grouped[k];
+            gh[k] = hs[f];
+            gT[k] = T[f];
+            gS[k] = S_dev[f];
+            gV[k] = V_dev[f];
+            gi[k] = iters_dev ? iters_dev[f] : nullptr;
+            gm[k] = mismatch_dev ? mismatch_dev[f] : nullptr;
+        }
+        st = tpf::solve_batch_sparse(G, gh.data(), gT.data(), gS.data(), gV.data(), gi.data(), gm.data(), o,
+                                     gconv.data(), &tot, s);
+        if (st != TPF_OK && st != TPF_ENOCONV) return st;
+        all = st == TPF_OK;
+        for (int k = 0; k < G; ++k)
+            if (converged_out) converged_out[grouped[k]] = gconv[k];
+    }
+    tpf_opts od = o;
+    od.method = TPF_METHOD_DENSE;  // feeders the sparse kernel cannot take use the dense form
+    for (int f : single) {
+        st = tpf_solve(hs[f], T[f], S_dev[f], V_dev[f], iters_dev ? iters_dev[f] : nullptr,
+                       mismatch_dev ? mismatch_dev[f] : nullptr, &od, stream);
+        if (st != TPF_OK && st != TPF_ENOCONV) return st;
+        all = all && st == TPF_OK;
+        const tpf_stats &fs = hs[f]->stats;
+        if (converged_out) converged_out[f] = fs.converged;
+        tot.converged += fs.converged;
+        tot.columns += fs.columns;
+        tot.sweeps = std::max(tot.sweeps, fs.sweeps);
+        tot.kernel_launches += fs.kernel_launches;
+        tot.gemm_ms += fs.gemm_ms;
+        tot.residual_ms += fs.residual_ms;
+        tot.other_ms += fs.other_ms;
+    }
+    if (stats_out) *stats_out = tot;
+    return all ? TPF_OK : TPF_ENOCONV;
+}
+
 tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_host,
                           int32_t *iters_host, double *mismatch_host, const tpf_opts *opts,
                           void *stream) {

@@ -190,6 +190,11 @@ tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t
                        double *mismatch, const tpf_opts &o, cudaStream_t st);
 tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
                         double *mismatch, const tpf_opts &o, cudaStream_t st);
+tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
+                           double *mismatch, const tpf_outputs *out, const tpf_opts &o, cudaStream_t st);
+tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S,
+                              void *const *V, int32_t *const *iters, double *const *mismatch,
+                              const tpf_opts &o, int64_t *conv_out, tpf_stats *stats, cudaStream_t st);
 tpf_status selftest_gemm(int M, int N, int K, const void *Ar, const void *Ai, const void *Br,
                          const void *Bi, float *Dr, float *Di, cudaStream_t st);
 }  // namespace tpf

@@ -28,7 +28,9 @@
 // (j * threads + k for the j-th position of thread k) so that a warp's accesses to its own
 // positions fall in consecutive banks.  Device memory is read for S once (again at an anchor) and
 // written once for V.
+#include <algorithm>
 #include <cstdlib>
+#include <limits>
 
 #include "tpf_dd.cuh"
 
@@ -41,21 +43,36 @@ constexpr int kMaxWarps = kMaxThreads / 32;
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kGather = 4;  // ends-list entries per position gathered without a loop
 
-struct TreeArgs {
-    int64_t T;
-    int n, n_ends, max_iter, given;
-    float tol2, switch_tol, switch_tol2;  // squared tolerances compare with squared steps
+// One feeder's share of a launch: its network arrays (slot layout) and its tensors.
+struct TreeWork {
+    int n, n_ends;
     float2 vs_f;
     c2 vs_dd;
-    const double2 *S;
-    const double2 *V0;
-    double2 *V_out;
-    int32_t *iters_out;
-    double *mismatch_out;
-    int *tile_done;   // converged columns per 128-column tile
-    int *counters;    // [5] largest per-column sweep count, [6] largest anchor count
     const int *col, *end, *par, *ecnt, *ends;
     const float4 *z;
+    const void *S;       // complex128 or, with s32, complex64 [T][n]
+    const void *V0;      // given start, same type as V_out
+    void *V_out;         // complex128 or, with v32, complex64 [T][n]; may be null
+    int32_t *iters_out;  // [T] or null
+    double *mismatch_out;  // [T] or null
+    int s32, v32;
+    int64_t col0;        // first launch column of this feeder
+    int64_t T;
+    int *conv;           // converged columns of this feeder (accumulated)
+    // Voltage-band statistics (each may be null): per column min / max |V| and the number of buses
+    // outside [v_min, v_max]; per bus the number of columns below / above the band.
+    float *col_vmin, *col_vmax;
+    int32_t *col_viol, *bus_under, *bus_over;
+    float v_min2, v_max2;
+};
+
+struct TreeArgs {
+    const TreeWork *works;  // n_works entries, sorted by col0; null: the single feeder `one`
+    TreeWork one;
+    int n_works;
+    int max_iter, given;
+    float tol2, switch_tol, switch_tol2;  // squared tolerances compare with squared steps
+    int *counters;                        // [5] largest per-column sweep count, [6] largest anchor count
 };
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -194,7 +211,7 @@ __device__ __forceinline__ int slot_of(int p, int th) {
 // column and its code stays small; the unrolled staging in the kernel keeps the device-memory
 // loads in flight together.
 template <int kBPT>
-__device__ __forceinline__ c2 anchor_dd(const TreeArgs &a, float4 *A, float4 *B, const int *s_end,
+__device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B, const int *s_end,
                                         const int *s_ends, const int *ecnt, float4 *wtd, int tid, int th, int lane,
                                         int warp) {
     const int n = a.n, base = tid * kBPT;
@@ -248,9 +265,23 @@ __device__ __forceinline__ c2 anchor_dd(const TreeArgs &a, float4 *A, float4 *B,
 }
 
 template <int kBPT>
-__global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(TreeArgs a) {
+__global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(const __grid_constant__ TreeArgs g) {
     extern __shared__ float4 tsm[];
-    const int n = a.n, th = blockDim.x, ns = th * kBPT;
+    __shared__ int s_work;
+    const int th = blockDim.x, ns = th * kBPT;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = th >> 5;
+    if (tid == 0) {
+        // The feeder of this block's column: the last work whose first column is <= blockIdx.x.
+        int lo = 0, hi = g.works ? g.n_works - 1 : 0;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (g.works[mid].col0 <= (int64_t)blockIdx.x) lo = mid; else hi = mid - 1;
+        }
+        s_work = lo;
+    }
+    __syncthreads();
+    const TreeWork &a = g.works ? g.works[s_work] : g.one;
+    const int n = a.n;
     // Arrays indexed by slot s = j th + k of position q = kBPT k + j.
     float4 *const A = tsm;       // [ns] double-float prefix sums (anchor); float2 P and X in the sweeps
     float4 *const B = tsm + ns;  // [ns] V_ref (anchor input), x (anchor), then D = BFS(V_ref) - V_ref
@@ -261,11 +292,13 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(Tre
     float2 *X = P + ns;                           // [ns] branch terms z_q L_q; the residual's x at the end
     __shared__ float2 wt1[kMaxWarps], wt2[kMaxWarps];
     __shared__ float4 wtd[kMaxWarps];
-    __shared__ float2 wm[kMaxWarps];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = th >> 5;
-    const int64_t t = blockIdx.x;
+    __shared__ float2 wmax[kMaxWarps];
+    __shared__ float4 wm[kMaxWarps];
+    const int64_t t = (int64_t)blockIdx.x - a.col0;  // column within the feeder
     const int base = tid * kBPT;
-    const double2 *S = a.S + t * n;
+    // S and V of this column: complex128 (double2) or complex64 (float2).
+    const double2 *S64 = static_cast<const double2 *>(a.S) + t * n;
+    const float2 *S32 = static_cast<const float2 *>(a.S) + t * n;
 
 #pragma unroll
     for (int j = 0; j < kBPT; ++j) {
@@ -285,21 +318,30 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(Tre
         ecnt[j] = 0;
         if (q < n) {
             const int i = a.col[s];
-            const double2 sv = S[i];
-            sh[j] = make_float2(__double2float_rn(sv.x), __double2float_rn(sv.y));
+            if (a.s32) {
+                sh[j] = S32[i];
+            } else {
+                const double2 sv = S64[i];
+                sh[j] = make_float2(__double2float_rn(sv.x), __double2float_rn(sv.y));
+            }
             const float4 zq = a.z[s];
             zr[j] = make_float2(zq.x, zq.y);
             ecnt[j] = a.ecnt[s];
-            if (a.given) {
-                const double2 v = a.V0[t * n + i];
-                vr[j] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
-                dl[j] = make_float2(__double2float_rn(v.x - (double)vr[j].x), __double2float_rn(v.y - (double)vr[j].y));
+            if (g.given) {
+                if (a.v32) {
+                    vr[j] = static_cast<const float2 *>(a.V0)[t * n + i];
+                } else {
+                    const double2 v = static_cast<const double2 *>(a.V0)[t * n + i];
+                    vr[j] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+                    dl[j] = make_float2(__double2float_rn(v.x - (double)vr[j].x),
+                                        __double2float_rn(v.y - (double)vr[j].y));
+                }
             }
         }
     }
     __syncthreads();
     // A given start is anchored at once ("blind"), and anchored again when the step is small.
-    bool anchored = a.given != 0, blind = anchored, anchor_now = anchored, done = false, conv = false;
+    bool anchored = g.given != 0, blind = anchored, anchor_now = anchored, done = false, conv = false;
     int it = 0, anchors = 0;
     float dprev2 = 0.0f;
     for (;;) {
@@ -315,8 +357,8 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(Tre
                 vr[j] = make_float2(re.h, im.h);
                 dl[j] = make_float2(re.l, im.l);
                 float2 slo = make_float2(0.0f, 0.0f);
-                if (q < n) {
-                    const double2 sv = S[a.col[s]];
+                if (q < n && !a.s32) {
+                    const double2 sv = S64[a.col[s]];
                     slo = make_float2(__double2float_rn(sv.x - (double)sh[j].x), __double2float_rn(sv.y - (double)sh[j].y));
                 }
                 A[s] = make_float4(sh[j].x, sh[j].y, 0.0f, 0.0f);
@@ -415,20 +457,20 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(Tre
                 mx.x = fmaxf(mx.x, mag2);
             }
         }
-        const float2 dm = block_max(mx, wm, lane, warp, nwarps);
+        const float2 dm = block_max(mx, wmax, lane, warp, nwarps);
         const float d2 = dm.x;
         // Every thread takes the same decision from the same d.  A step is only trusted to be
         // below tol on an anchored column whose offset from V_ref is small: in FP32 on V itself
         // (or on a large offset) a tiny step can round to zero.
         ++it;
-        if (d2 <= a.tol2 && anchored && (!blind || dm.y < a.switch_tol2)) {
+        if (d2 <= g.tol2 && anchored && (!blind || dm.y < g.switch_tol2)) {
             done = conv = true;
-        } else if (it >= a.max_iter || !(d2 < 1e30f)) {
+        } else if (it >= g.max_iter || !(d2 < 1e30f)) {
             done = true;
         } else if (!anchored || blind) {
             // Anchor once the step is small, or is predicted (geometric rate) to fall below 3e-6
             // in the next sweep: d^2 < 3e-6 d_prev, squared.
-            if (d2 < a.switch_tol2 || (dprev2 > 0.0f && d2 * d2 < 9e-12f * dprev2)) {
+            if (d2 < g.switch_tol2 || (dprev2 > 0.0f && d2 * d2 < 9e-12f * dprev2)) {
                 anchor_now = true;
                 blind = false;
             }
@@ -456,8 +498,14 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(Tre
             xs[j] = vr[j];
         }
         if (q < n) {
-            a.V_out[t * n + a.col[s]] =
-                make_double2((double)vr[j].x + (double)dl[j].x, (double)vr[j].y + (double)dl[j].y);
+            if (a.V_out) {
+                const int64_t k = t * n + a.col[s];
+                if (a.v32)
+                    static_cast<float2 *>(a.V_out)[k] = add2(vr[j], dl[j]);
+                else
+                    static_cast<double2 *>(a.V_out)[k] =
+                        make_double2((double)vr[j].x + (double)dl[j].x, (double)vr[j].y + (double)dl[j].y);
+            }
             X[s] = xs[j];
         }
     }
@@ -474,7 +522,8 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(Tre
         }
     }
     __syncthreads();
-    float mm = 0.0f;
+    // Mismatch, |V| band statistics: (max mismatch, -min |V|^2, max |V|^2, buses outside the band).
+    float4 red = make_float4(0.0f, -__int_as_float(0x7f800000), 0.0f, 0.0f);
 #pragma unroll
     for (int j = 0; j < kBPT; ++j) {
         const int q = base + j, s = j * th + tid;
@@ -487,19 +536,39 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(Tre
                 r = add2(r, J[ks]);
                 k = s_end[ks];
             }
-            const float2 v = add2(vr[j], dl[j]);
-            float mv = sqrtf(abs2(v) * abs2(r));
+            const float v2 = abs2(add2(vr[j], dl[j]));
+            float mv = sqrtf(v2 * abs2(r));
             if (mv != mv) mv = __int_as_float(0x7f800000);  // a NaN mismatch reports as +inf
-            mm = fmaxf(mm, mv);
+            red.x = fmaxf(red.x, mv);
+            red.y = fmaxf(red.y, -v2);
+            red.z = fmaxf(red.z, v2);
+            const bool under = v2 < a.v_min2, over = v2 > a.v_max2;
+            red.w += (under || over) ? 1.0f : 0.0f;
+            if (under && a.bus_under) atomicAdd(&a.bus_under[a.col[s]], 1);
+            if (over && a.bus_over) atomicAdd(&a.bus_over[a.col[s]], 1);
         }
     }
-    mm = block_max(make_float2(mm, 0.0f), wm, lane, warp, nwarps).x;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        red.x = fmaxf(red.x, __shfl_xor_sync(kFull, red.x, o));
+        red.y = fmaxf(red.y, __shfl_xor_sync(kFull, red.y, o));
+        red.z = fmaxf(red.z, __shfl_xor_sync(kFull, red.z, o));
+        red.w += __shfl_xor_sync(kFull, red.w, o);
+    }
+    if (lane == 0) wm[warp] = red;
+    __syncthreads();
     if (tid == 0) {
-        if (a.mismatch_out) a.mismatch_out[t] = (double)mm;
-        if (a.iters_out) a.iters_out[t] = conv ? it : -a.max_iter;
-        if (conv) atomicAdd(&a.tile_done[t / kTileN], 1);
-        atomicMax(&a.counters[5], it);
-        atomicMax(&a.counters[6], anchors);
+        float4 r = wm[0];
+        for (int w = 1; w < nwarps; ++w)
+            r = make_float4(fmaxf(r.x, wm[w].x), fmaxf(r.y, wm[w].y), fmaxf(r.z, wm[w].z), r.w + wm[w].w);
+        if (a.mismatch_out) a.mismatch_out[t] = (double)r.x;
+        if (a.iters_out) a.iters_out[t] = conv ? it : -g.max_iter;
+        if (a.col_vmin) a.col_vmin[t] = sqrtf(-r.y);
+        if (a.col_vmax) a.col_vmax[t] = sqrtf(r.z);
+        if (a.col_viol) a.col_viol[t] = (int32_t)r.w;
+        if (conv) atomicAdd(a.conv, 1);
+        atomicMax(&g.counters[5], it);
+        atomicMax(&g.counters[6], anchors);
     }
 }
 
@@ -515,84 +584,219 @@ int tree_bpt(int n) {
     return 0;
 }
 
-tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters, double *mismatch,
-                        const tpf_opts &o, cudaStream_t st) {
+namespace {
+
+// The network part of a feeder's work entry.
+TreeWork work_of(const tpf_handle *h) {
     const DeviceNet &d = h->dev;
-    if (!d.radial || o.precision != TPF_PREC_MIXED) return TPF_EUNSUPPORTED;
-    const int n = d.n, threads = d.t_threads;
-    if (threads == 0) return TPF_EUNSUPPORTED;
-    if (T > 0x7fffffff) return TPF_EUNSUPPORTED;  // one block per column
-    const int ns = threads * d.t_bpt;
-    const size_t smem = (size_t)2 * ns * sizeof(float4) + sizeof(int) * (2 * ns + d.t_n_ends);
-    tpf_status rs = ensure_workspace(h, T, kWsState);  // counters and per-tile counts
+    TreeWork w{};
+    w.n = d.n;
+    w.n_ends = d.t_n_ends;
+    w.vs_f = make_float2((float)h->net.vs_re, (float)h->net.vs_im);
+    const float rh = (float)h->net.vs_re, ih = (float)h->net.vs_im;
+    w.vs_dd = c2{{rh, (float)(h->net.vs_re - (double)rh)}, {ih, (float)(h->net.vs_im - (double)ih)}};
+    w.col = d.t_col;
+    w.end = d.t_end;
+    w.par = d.t_par;
+    w.ecnt = d.t_ecnt;
+    w.ends = d.t_ends;
+    w.z = d.t_z;
+    w.v_min2 = 0.0f;
+    w.v_max2 = std::numeric_limits<float>::infinity();
+    return w;
+}
+
+size_t tree_smem(int threads, int bpt) {
+    const size_t ns = (size_t)threads * bpt;
+    return 2 * ns * sizeof(float4) + sizeof(int) * 3 * ns;  // A, B, end, parent, ends (<= ns entries)
+}
+
+tpf_status launch_tree(int bpt, int threads, int64_t cols, const TreeArgs &g, cudaStream_t st) {
+    if (cols <= 0) return TPF_OK;
+    if (cols > 0x7fffffff) return TPF_EUNSUPPORTED;  // one block per column
+    const size_t smem = tree_smem(threads, bpt);
+    cudaError_t e;
+    if (bpt == 8) {
+        e = cudaFuncSetAttribute(mx_tree<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) mx_tree<8><<<(unsigned)cols, threads, smem, st>>>(g);
+    } else if (bpt == 4) {
+        e = cudaFuncSetAttribute(mx_tree<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) mx_tree<4><<<(unsigned)cols, threads, smem, st>>>(g);
+    } else {
+        e = cudaFuncSetAttribute(mx_tree<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) mx_tree<2><<<(unsigned)cols, threads, smem, st>>>(g);
+    }
+    if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return TPF_ECUDA;
+    return TPF_OK;
+}
+
+TreeArgs args_of(const tpf_opts &o) {
+    TreeArgs g{};
+    g.max_iter = o.max_iter;
+    g.given = o.start == TPF_START_GIVEN;
+    const float tol = (float)o.tol, sw = (float)o.switch_tol;
+    g.tol2 = tol * tol;
+    g.switch_tol = sw;
+    g.switch_tol2 = sw * sw;
+    return g;
+}
+
+}  // namespace
+
+tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters, double *mismatch,
+                           const tpf_outputs *out, const tpf_opts &o, cudaStream_t st) {
+    const DeviceNet &d = h->dev;
+    if (!d.radial || o.precision != TPF_PREC_MIXED || d.t_threads == 0) return TPF_EUNSUPPORTED;
+    if (T > 0x7fffffff) return TPF_EUNSUPPORTED;
+    tpf_status rs = ensure_workspace(h, T, kWsState);  // counters
     if (rs != TPF_OK) return rs;
     Workspace &w = h->ws;
-    if (cudaFuncSetAttribute(mx_tree<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(mx_tree<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
-        cudaFuncSetAttribute(mx_tree<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+    if (cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, st) != cudaSuccess) {
         cudaGetLastError();
         return TPF_ECUDA;
     }
-    const int64_t n_tiles = round_up(T, kTileN) / kTileN;
-    if (cudaMemsetAsync(w.tile_active, 0, sizeof(int) * n_tiles, st) != cudaSuccess ||
-        cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, st) != cudaSuccess) {
-        cudaGetLastError();
-        return TPF_ECUDA;
+    TreeArgs g = args_of(o);
+    g.counters = w.counters;
+    g.one = work_of(h);
+    TreeWork &wk = g.one;
+    wk.S = S;
+    wk.V0 = V;
+    wk.V_out = V;
+    wk.iters_out = iters;
+    wk.mismatch_out = mismatch;
+    wk.T = T;
+    wk.conv = w.counters + kCntConverged;
+    if (out) {
+        wk.s32 = out->s_complex64 != 0;
+        wk.v32 = out->v_complex64 != 0;
+        wk.col_vmin = out->col_vmin;
+        wk.col_vmax = out->col_vmax;
+        wk.col_viol = out->col_viol;
+        wk.bus_under = out->bus_under;
+        wk.bus_over = out->bus_over;
+        wk.v_min2 = (float)(out->v_min * out->v_min);
+        wk.v_max2 = (float)(out->v_max * out->v_max);
     }
-    TreeArgs a{};
-    a.T = T;
-    a.n = n;
-    a.max_iter = o.max_iter;
-    a.given = o.start == TPF_START_GIVEN;
-    const float tol = (float)o.tol, sw = (float)o.switch_tol;
-    a.tol2 = tol * tol;
-    a.switch_tol = sw;
-    a.switch_tol2 = sw * sw;
-    a.vs_f = make_float2((float)h->net.vs_re, (float)h->net.vs_im);
-    {
-        const float rh = (float)h->net.vs_re, ih = (float)h->net.vs_im;
-        a.vs_dd = c2{{rh, (float)(h->net.vs_re - (double)rh)}, {ih, (float)(h->net.vs_im - (double)ih)}};
-    }
-    a.S = (const double2 *)S;
-    a.V0 = (const double2 *)V;
-    a.V_out = (double2 *)V;
-    a.iters_out = iters;
-    a.mismatch_out = mismatch;
-    a.tile_done = w.tile_active;
-    a.counters = w.counters;
-    a.n_ends = d.t_n_ends;
-    a.col = d.t_col;
-    a.end = d.t_end;
-    a.par = d.t_par;
-    a.ecnt = d.t_ecnt;
-    a.ends = d.t_ends;
-    a.z = d.t_z;
     KernelTimer timer(o.profile != 0, st);
     timer.begin(KernelTimer::kResidual);
-    if (d.t_bpt == 8)
-        mx_tree<8><<<(unsigned)T, threads, smem, st>>>(a);
-    else if (d.t_bpt == 4)
-        mx_tree<4><<<(unsigned)T, threads, smem, st>>>(a);
-    else
-        mx_tree<2><<<(unsigned)T, threads, smem, st>>>(a);
+    rs = launch_tree(d.t_bpt, d.t_threads, T, g, st);
     timer.end();
-    if (cudaGetLastError() != cudaSuccess) return TPF_ECUDA;
-    std::vector<int> tiles(n_tiles);
+    if (rs != TPF_OK) return rs;
     if (cudaMemcpyAsync(w.counters_host, w.counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaMemcpyAsync(tiles.data(), w.tile_active, sizeof(int) * n_tiles, cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
         cudaGetLastError();
         return TPF_ECUDA;
     }
-    int64_t conv = 0;
-    for (int x : tiles) conv += x;
+    const int64_t conv = w.counters_host[kCntConverged];
     h->stats.sweeps = w.counters_host[5];
     h->stats.precise_sweeps = w.counters_host[6];
     h->stats.kernel_launches = 1;
     h->stats.converged = conv;
     h->stats.residual_ms = timer.total_ms(KernelTimer::kResidual);
     return conv == T ? TPF_OK : TPF_ENOCONV;
+}
+
+tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters, double *mismatch,
+                        const tpf_opts &o, cudaStream_t st) {
+    return solve_sparse_ex(h, T, S, V, iters, mismatch, nullptr, o, st);
+}
+
+tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S, void *const *V,
+                              int32_t *const *iters, double *const *mismatch, const tpf_opts &o, int64_t *conv_out,
+                              tpf_stats *stats, cudaStream_t st) {
+    // Group the feeders by launch shape (buses per thread, threads); one launch per group over the
+    // concatenated columns of its feeders.
+    std::vector<int> order(F);
+    for (int f = 0; f < F; ++f) order[f] = f;
+    std::sort(order.begin(), order.end(), [&](int x, int y) {
+        const DeviceNet &a = hs[x]->dev, &b = hs[y]->dev;
+        return a.t_bpt != b.t_bpt ? a.t_bpt < b.t_bpt : (a.t_threads != b.t_threads ? a.t_threads < b.t_threads : x < y);
+    });
+    std::vector<TreeWork> works(F);
+    for (int k = 0; k < F; ++k) {
+        const int f = order[k];
+        TreeWork w = work_of(hs[f]);
+        w.S = S[f];
+        w.V0 = V[f];
+        w.V_out = V[f];
+        w.iters_out = iters ? iters[f] : nullptr;
+        w.mismatch_out = mismatch ? mismatch[f] : nullptr;
+        w.T = T[f];
+        works[k] = w;
+    }
+    // Device copies: the work table and the per-feeder converged counts, plus the counters.
+    const size_t wbytes = sizeof(TreeWork) * F, cbytes = sizeof(int) * ((size_t)F + 8);
+    char *dbuf = nullptr;
+    if (cudaMalloc(&dbuf, wbytes + cbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return TPF_ENOMEM;
+    }
+    TreeWork *dworks = reinterpret_cast<TreeWork *>(dbuf);
+    int *dconv = reinterpret_cast<int *>(dbuf + wbytes), *dcnt = dconv + F;
+    for (int k = 0; k < F; ++k) works[k].conv = dconv + order[k];
+    tpf_status rs = TPF_OK;
+    KernelTimer timer(o.profile != 0, st);
+    int launches = 0;
+    if (cudaMemsetAsync(dconv, 0, cbytes, st) != cudaSuccess) rs = TPF_ECUDA;
+    // Launch-local column offsets are set per group before the table is copied.
+    std::vector<std::pair<int, int>> groups;  // [first, last) in `works`
+    for (int k = 0; k < F;) {
+        int e = k + 1;
+        while (e < F && hs[order[e]]->dev.t_bpt == hs[order[k]]->dev.t_bpt &&
+               hs[order[e]]->dev.t_threads == hs[order[k]]->dev.t_threads)
+            ++e;
+        int64_t c = 0;
+        for (int i = k; i < e; ++i) {
+            works[i].col0 = c;
+            c += works[i].T;
+        }
+        groups.push_back({k, e});
+        k = e;
+    }
+    if (rs == TPF_OK && cudaMemcpyAsync(dworks, works.data(), wbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rs = TPF_ECUDA;
+    TreeArgs g = args_of(o);
+    g.counters = dcnt;
+    for (auto &gr : groups) {
+        if (rs != TPF_OK) break;
+        const DeviceNet &d = hs[order[gr.first]]->dev;
+        int64_t cols = 0;
+        for (int i = gr.first; i < gr.second; ++i) cols += works[i].T;
+        g.works = dworks + gr.first;
+        g.n_works = gr.second - gr.first;
+        timer.begin(KernelTimer::kResidual);
+        rs = launch_tree(d.t_bpt, d.t_threads, cols, g, st);
+        timer.end();
+        ++launches;
+    }
+    std::vector<int> hconv(F + 8, 0);
+    if (rs == TPF_OK && (cudaMemcpyAsync(hconv.data(), dconv, cbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                         cudaStreamSynchronize(st) != cudaSuccess))
+        rs = TPF_ECUDA;
+    if (rs != TPF_OK) cudaStreamSynchronize(st);
+    cudaFree(dbuf);
+    if (rs != TPF_OK) {
+        cudaGetLastError();
+        return rs;
+    }
+    bool all = true;
+    int64_t conv = 0, cols = 0;
+    for (int f = 0; f < F; ++f) {
+        if (conv_out) conv_out[f] = hconv[f];
+        conv += hconv[f];
+        cols += T[f];
+        all = all && hconv[f] == T[f];
+    }
+    if (stats) {
+        *stats = tpf_stats{};
+        stats->sweeps = hconv[F + 5];
+        stats->precise_sweeps = hconv[F + 6];
+        stats->converged = conv;
+        stats->columns = cols;
+        stats->kernel_launches = launches;
+        stats->residual_ms = timer.total_ms(KernelTimer::kResidual);
+    }
+    return all ? TPF_OK : TPF_ENOCONV;
 }
 
 }  // namespace tpf

@@ -22,7 +22,7 @@ START_FLAT, START_GIVEN = 0, 1
 # Every entry point declared in include/tpf.h.
 EXPORTS = (
     "tpf_default_opts", "tpf_strerror", "tpf_create", "tpf_destroy", "tpf_n_pq", "tpf_precompute_host",
-    "tpf_solve", "tpf_solve_host", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
+    "tpf_solve", "tpf_solve_host", "tpf_solve_ex", "tpf_solve_batch", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
     "tpf_mlp_create", "tpf_mlp_destroy", "tpf_mlp_param_count", "tpf_mlp_get_params", "tpf_mlp_set_params",
     "tpf_mlp_fit_normalization", "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients",
     "tpf_mlp_predict",
@@ -42,6 +42,12 @@ class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int), ("precision", ctypes.c_int),
                 ("start", ctypes.c_int), ("switch_tol", ctypes.c_double), ("profile", ctypes.c_int),
                 ("method", ctypes.c_int)]
+
+
+class Outputs(ctypes.Structure):
+    _fields_ = [("s_complex64", ctypes.c_int), ("v_complex64", ctypes.c_int), ("v_min", ctypes.c_double),
+                ("v_max", ctypes.c_double), ("col_vmin", ctypes.c_void_p), ("col_vmax", ctypes.c_void_p),
+                ("col_viol", ctypes.c_void_p), ("bus_under", ctypes.c_void_p), ("bus_over", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -92,6 +98,11 @@ def lib(build_if_missing: bool = False):
     L.tpf_solve.restype = ctypes.c_int
     L.tpf_solve_host.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(Opts), vp]
     L.tpf_solve_host.restype = ctypes.c_int
+    L.tpf_solve_ex.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(Outputs), ctypes.POINTER(Opts), vp]
+    L.tpf_solve_ex.restype = ctypes.c_int
+    L.tpf_solve_batch.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Opts), vp,
+                                  ctypes.POINTER(Stats), vp]
+    L.tpf_solve_batch.restype = ctypes.c_int
     L.tpf_last_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     L.tpf_last_stats.restype = ctypes.c_int
     L.tpf_selftest_gemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
@@ -256,6 +267,52 @@ class Feeder:
             raise TpfError(st, "tpf_solve")
         return V, iters, mismatch, st
 
+    def solve_tensor(self, S, V=None, want_V=True, v_complex64=None, v_band=(0.95, 1.05), bus_counts=None,
+                     tol=1e-10, max_iter=100, start=None, switch_tol=1e-4, stream=None, check=True, profile=False):
+        """tpf_solve_ex on a load tensor of any leading shape [..., n_pq] (complex64 or complex128).
+
+        Returns a dict: V (same leading shape; None when want_V is False), iters, mismatch, vmin, vmax
+        (per column |V| extremes), viol (buses outside v_band per column), bus_under / bus_over
+        (columns below / above the band per bus, added to `bus_counts` when given) and status.
+        """
+        import torch
+
+        if not (isinstance(S, torch.Tensor) and S.is_cuda and S.dtype in (torch.complex64, torch.complex128)):
+            raise TypeError("S must be a CUDA complex64 or complex128 tensor")
+        if S.shape[-1] != self.n_pq or not S.is_contiguous():
+            raise ValueError(f"S must be contiguous with last dimension {self.n_pq}")
+        lead = S.shape[:-1]
+        T = int(np.prod(lead)) if len(lead) else 1
+        dev = S.device
+        if start is None:
+            start = "given" if V is not None else "flat"
+        v32 = (S.dtype == torch.complex64) if v_complex64 is None else bool(v_complex64)
+        vdt = torch.complex64 if v32 else torch.complex128
+        if V is None and (want_V or start == "given"):
+            V = torch.empty(S.shape, dtype=vdt, device=dev)
+        if V is not None and (V.dtype != vdt or V.shape != S.shape or not V.is_contiguous()):
+            raise ValueError("V must be contiguous, shaped like S, complex64 iff v_complex64")
+        it = torch.empty(lead, dtype=torch.int32, device=dev)
+        mm = torch.empty(lead, dtype=torch.float64, device=dev)
+        vmin = torch.empty(lead, dtype=torch.float32, device=dev)
+        vmax = torch.empty(lead, dtype=torch.float32, device=dev)
+        viol = torch.empty(lead, dtype=torch.int32, device=dev)
+        if bus_counts is None:
+            bus_counts = (torch.zeros(self.n_pq, dtype=torch.int32, device=dev),
+                          torch.zeros(self.n_pq, dtype=torch.int32, device=dev))
+        out = Outputs(1 if S.dtype == torch.complex64 else 0, 1 if v32 else 0, float(v_band[0]), float(v_band[1]),
+                      vmin.data_ptr(), vmax.data_ptr(), viol.data_ptr(), bus_counts[0].data_ptr(),
+                      bus_counts[1].data_ptr())
+        o = make_opts("mixed", tol, max_iter, start, switch_tol, profile, "sparse")
+        vp = ctypes.c_void_p
+        st = lib().tpf_solve_ex(self._h, T, vp(S.data_ptr()), vp(V.data_ptr() if V is not None else 0),
+                                vp(it.data_ptr()), vp(mm.data_ptr()), ctypes.byref(out), ctypes.byref(o),
+                                _stream_ptr(stream))
+        if check and st not in (OK, ENOCONV):
+            raise TpfError(st, "tpf_solve_ex")
+        return {"V": V, "iters": it, "mismatch": mm, "vmin": vmin, "vmax": vmax, "viol": viol,
+                "bus_under": bus_counts[0], "bus_over": bus_counts[1], "status": st}
+
     def solve_host(self, S, V0=None, precision="mixed", tol=1e-10, max_iter=100, switch_tol=1e-4, stream=None,
                    out=None, check=True, profile=False, method="dense"):
         """tpf_solve_host on host arrays (numpy or pinned torch CPU tensors, complex128 [T][n_pq])."""
@@ -277,6 +334,47 @@ class Feeder:
         if check and st not in (OK, ENOCONV):
             raise TpfError(st, "tpf_solve_host")
         return V, it, mm, st
+
+
+def solve_batch(feeders, S, V=None, iters=None, mismatch=None, precision="mixed", tol=1e-10, max_iter=100,
+                start=None, switch_tol=1e-4, method="sparse", stream=None, check=True, profile=False):
+    """tpf_solve_batch over a list of Feeder objects with their CUDA complex128 load tensors.
+
+    Outputs (V, iters, mismatch lists) are allocated when not given.  Returns
+    (V, iters, mismatch, converged per feeder (numpy int64), stats dict, status).
+    """
+    import torch
+
+    F = len(feeders)
+    if len(S) != F:
+        raise ValueError("one load tensor per feeder")
+    if start is None:
+        start = "given" if V is not None else "flat"
+    V = list(V) if V is not None else [torch.empty_like(s) for s in S]
+    iters = list(iters) if iters is not None else [torch.empty(s.shape[0], dtype=torch.int32, device=s.device)
+                                                    for s in S]
+    mismatch = list(mismatch) if mismatch is not None else [
+        torch.empty(s.shape[0], dtype=torch.float64, device=s.device) for s in S]
+    for f in range(F):
+        s = S[f]
+        if not (isinstance(s, torch.Tensor) and s.is_cuda and s.dtype == torch.complex128 and s.dim() == 2
+                and s.shape[1] == feeders[f].n_pq and s.is_contiguous()):
+            raise ValueError(f"S[{f}] must be a contiguous CUDA complex128 [T, n_pq] tensor")
+    P = ctypes.c_void_p * F
+    hs = P(*[fd._h.value for fd in feeders])
+    Ts = (ctypes.c_int64 * F)(*[int(s.shape[0]) for s in S])
+    Sp = P(*[s.data_ptr() for s in S])
+    Vp = P(*[v.data_ptr() for v in V])
+    Ip = P(*[i.data_ptr() for i in iters])
+    Mp = P(*[m.data_ptr() for m in mismatch])
+    conv = (ctypes.c_int64 * F)()
+    st_ = Stats()
+    o = make_opts(precision, tol, max_iter, start, switch_tol, profile, method)
+    st = lib().tpf_solve_batch(F, hs, Ts, Sp, Vp, Ip, Mp, ctypes.byref(o), conv, ctypes.byref(st_),
+                               _stream_ptr(stream))
+    if check and st not in (OK, ENOCONV):
+        raise TpfError(st, "tpf_solve_batch")
+    return V, iters, mismatch, np.array(conv[:], dtype=np.int64), st_.as_dict(), st
 
 
 def solve_fp64_noalloc(K, W, S, V, iters=None, tol=1e-10, max_iter=100, given_start=False, stream=None):

@@ -21,6 +21,9 @@ Reported on one JSON line (rank 0):
   cpu_baseline the CPU oracle on the host cores, on a bounded column sample; the same leg checks
               the GPU results against the oracle (iterated to 1e-13) on sampled columns
   learned_start  config-5 leg: the MLP warm start on a 200-bus feeder
+  scenario_tensor  config-3 leg: 500-bus feeder, [200 x 8,760] complex64 scenario tensor with fused
+              voltage-band statistics
+  feeder_batch  config-4 leg: 4,096 feeders of 20-2,000 buses in one tpf_solve_batch call
   clocks      nvidia-smi samples taken during the timed region
 
 ``--impl reference`` times the CPU oracle as the reference arm on the same workload.
@@ -73,6 +76,12 @@ def parse_args():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true")
     p.add_argument("--method", choices=["sparse", "dense"], default="sparse")
+    p.add_argument("--no-scenario", action="store_true")
+    p.add_argument("--no-batch", action="store_true")
+    p.add_argument("--scen", type=int, default=200)
+    p.add_argument("--hours", type=int, default=8760)
+    p.add_argument("--scen-buses", type=int, default=500)
+    p.add_argument("--batch-feeders", type=int, default=4096)
     p.add_argument("--no-other", action="store_true", help="skip timing the other formulation")
     return p.parse_args()
 
@@ -299,6 +308,123 @@ def learned_start_leg(args, stream):
     return out, f, S_ev, V_learned
 
 
+def timed_device(fn, reps, stream):
+    """Mean CUDA-event time (ms) of `reps` calls after one warm-up call."""
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+def scenario_leg(args, stream, check):
+    """Config 3: a 500-bus feeder and a [200 scenarios x 8,760 hours] complex64 load tensor
+    (1,752,000 power flows), solved with voltage-band statistics fused into the solve."""
+    import torch
+
+    from paper_2403_04578_gb300 import inputs as G
+    from paper_2403_04578_gb300 import tpf
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f = G.make_feeder(args.scen_buses, args.seed, peak_factor=1.8)
+    S = G.scenario_tensor_device(f, args.scen, args.hours, args.seed, dev)
+    T = args.scen * args.hours
+    fd = tpf.Feeder.from_inputs(f)
+    V = torch.empty(S.shape, dtype=torch.complex64, device=dev)
+    band = (0.95, 1.05)
+    res = {}
+
+    def run(v=V):
+        res.update(fd.solve_tensor(S, V=v, start="flat", v_band=band, tol=args.tol))
+
+    ms = timed_device(run, max(1, min(args.steps, 3)), stream)
+    ms_stats = timed_device(lambda: run(None), max(1, min(args.steps, 3)), stream) if V is not None else None
+    out = {"workload": f"{args.scen_buses}-bus feeder x [{args.scen} scenarios x {args.hours:,} hours] complex64 "
+                       f"loads (factor U(0.5,1.8), 30% PV); sparse method; band {band[0]}-{band[1]} pu statistics",
+           "value": T / (ms / 1e3), "unit": "PF/s", "ms_per_step": ms,
+           "stats_only": {"value": T / (ms_stats / 1e3), "ms_per_step": ms_stats, "note": "V not written"},
+           "converged": int((res["iters"] > 0).sum().item()), "columns": T,
+           "buses_out_of_band_per_column_mean": float(res["viol"].float().mean().item()),
+           "min_v_pu": float(res["vmin"].min().item()), "max_v_pu": float(res["vmax"].max().item())}
+    if check:
+        from oracle import oracle as O
+
+        idx = torch.linspace(0, T - 1, args.check_columns, device=dev).long()
+        Sf = S.reshape(T, -1)[idx].contiguous()
+        r = fd.solve_tensor(Sf, v_complex64=False, v_band=band, tol=args.tol)
+        Vt, _, _ = O.Case.from_feeder(f).solve(Sf.cpu().numpy().astype(np.complex128), tol=1e-13,
+                                               threads=os.cpu_count() or 1)
+        out["max_abs_err_pu"] = float(np.abs(r["V"].cpu().numpy() - Vt).max())
+        out["columns_checked"] = int(idx.numel())
+    fd.close()
+    del S, V
+    torch.cuda.empty_cache()
+    return out
+
+
+def batch_leg(args, stream, check):
+    """Config 4: 4,096 feeders, bus counts log-uniform in [20, 2,000], T in {96, 288, 1,440}
+    (one day at 15, 5 or 1 minute), all solved by one tpf_solve_batch call."""
+    import torch
+
+    from paper_2403_04578_gb300 import inputs as G
+    from paper_2403_04578_gb300 import tpf
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    specs = G.batch_specs(args.batch_feeders)
+    t0 = time.perf_counter()
+    feeders = [G.make_feeder(nb, sd) for nb, _, sd in specs]
+    t_gen = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    fds = [tpf.Feeder.from_inputs(f) for f in feeders]
+    t_create = time.perf_counter() - t0
+    S = [G.load_tensor_device(f, T, sd, dev, step_minutes=G.step_minutes_for(T))
+         for f, (_, T, sd) in zip(feeders, specs)]
+    V = [torch.empty_like(s) for s in S]
+    it = [torch.empty(s.shape[0], dtype=torch.int32, device=dev) for s in S]
+    mm = [torch.empty(s.shape[0], dtype=torch.float64, device=dev) for s in S]
+    cols = sum(T for _, T, _ in specs)
+    res = {}
+
+    def run():
+        r = tpf.solve_batch(fds, S, V=V, iters=it, mismatch=mm, start="flat", tol=args.tol)
+        res["conv"], res["stats"], res["st"] = r[3], r[4], r[5]
+
+    ms = timed_device(run, max(1, min(args.steps, 3)), stream)
+    out = {"workload": f"{args.batch_feeders} feeders, buses log-uniform in [20, 2000], T in {{96, 288, 1440}}; "
+                       "sparse method, one tpf_solve_batch call",
+           "value": cols / (ms / 1e3), "unit": "PF/s", "ms_per_step": ms, "columns": cols,
+           "bus_columns": int(sum(f.n_pq * T for f, (_, T, _) in zip(feeders, specs))),
+           "converged": int(res["conv"].sum()), "gpu_launches_per_step": res["stats"]["kernel_launches"],
+           "tpf_create_s_total": t_create, "feeder_generation_s": t_gen}
+    if check:
+        from oracle import oracle as O
+
+        errs, checked = [], 0
+        pick = [k for k, f in enumerate(feeders) if f.n_bus <= 600][:: max(1, args.batch_feeders // 256)][:16]
+        for k in pick:
+            cc = torch.linspace(0, S[k].shape[0] - 1, 8, device=dev).long()
+            Vt, _, _ = O.Case.from_feeder(feeders[k]).solve(S[k][cc].cpu().numpy(), tol=1e-13,
+                                                            threads=os.cpu_count() or 1)
+            errs.append(float(np.abs(V[k][cc].cpu().numpy() - Vt).max()))
+            checked += int(cc.numel())
+        out["max_abs_err_pu"] = max(errs) if errs else None
+        out["columns_checked"] = checked
+        out["feeders_checked"] = len(pick)
+    for fd in fds:
+        fd.close()
+    del S, V
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, world, rank):
     """The reference arm: the CPU oracle (FP64, all host cores) on bounded samples of the workload."""
     if rank != 0:
@@ -520,9 +646,9 @@ def main():
         line["accuracy"] = check
     if other_obj is not None:
         line[f"{other}_method"] = other_obj
+    del Sd, Vd, Sh
+    torch.cuda.empty_cache()
     if not args.no_learned:
-        del Sd, Vd
-        torch.cuda.empty_cache()
         ls, f200, S_ev, V_ls = learned_start_leg(args, stream)
         if rank == 0 and not args.no_cpu:
             from oracle import oracle as O
@@ -533,6 +659,10 @@ def main():
             ls["max_abs_err_pu"] = float(np.abs(V_ls[cc] - Vt).max())
             ls["columns_checked"] = int(cc.size)
         line["learned_start"] = ls
+    if not args.no_scenario:
+        line["scenario_tensor"] = scenario_leg(args, stream, rank == 0 and not args.no_cpu)
+    if not args.no_batch:
+        line["feeder_batch"] = batch_leg(args, stream, rank == 0 and not args.no_cpu)
     if rank == 0:
         print(json.dumps(line), flush=True)
     fd.close()

@@ -50,14 +50,10 @@ tpf_status upload_network(tpf_handle *h) {
     d.n = n;
     d.n_pad = (int)round_up(n, kTileM);
     const int nnz = net.row_ptr[n];
-    TPF_CK(cudaMalloc(&d.K64, sizeof(double) * 2 * (size_t)n * n));
-    TPF_CK(cudaMalloc(&d.W64, sizeof(double) * 2 * (size_t)n));
     TPF_CK(cudaMalloc(&d.row_ptr, sizeof(int) * (n + 1)));
     TPF_CK(cudaMalloc(&d.nbr, sizeof(int) * (nnz > 0 ? nnz : 1)));
     TPF_CK(cudaMalloc(&d.y64, sizeof(double) * 2 * (nnz > 0 ? nnz : 1)));
     TPF_CK(cudaMalloc(&d.y2f, sizeof(float4) * (nnz > 0 ? nnz : 1)));
-    TPF_CK(cudaMemcpy(d.K64, net.K.data(), sizeof(double) * net.K.size(), cudaMemcpyHostToDevice));
-    TPF_CK(cudaMemcpy(d.W64, net.W.data(), sizeof(double) * net.W.size(), cudaMemcpyHostToDevice));
     TPF_CK(cudaMemcpy(d.row_ptr, net.row_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
     if (nnz > 0) {
         TPF_CK(cudaMemcpy(d.nbr, net.nbr.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice));
@@ -125,6 +121,27 @@ tpf_status upload_network(tpf_handle *h) {
             }
         }
     }
+    if (!net.K.empty()) return ensure_dense(h);  // meshed networks: K was built with the network
+    return TPF_OK;
+}
+
+tpf_status ensure_dense(tpf_handle *h) {
+    DeviceNet &d = h->dev;
+    if (d.K64) return TPF_OK;
+    Network &net = h->net;
+    try {
+        compute_dense(net);
+    } catch (const std::bad_alloc &) {
+        return TPF_ENOMEM;
+    }
+    const int n = d.n;
+    if (cudaMalloc(&d.K64, sizeof(double) * 2 * (size_t)n * n) != cudaSuccess ||
+        cudaMalloc(&d.W64, sizeof(double) * 2 * (size_t)n) != cudaSuccess) {
+        cudaGetLastError();
+        return TPF_ENOMEM;
+    }
+    TPF_CK(cudaMemcpy(d.K64, net.K.data(), sizeof(double) * net.K.size(), cudaMemcpyHostToDevice));
+    TPF_CK(cudaMemcpy(d.W64, net.W.data(), sizeof(double) * net.W.size(), cudaMemcpyHostToDevice));
     // fp16 planes of K * 2^k_exp with the largest component in [2^13, 2^14).
     double kmax = 0.0;
     for (double v : net.K) kmax = fmax(kmax, fabs(v));
@@ -138,6 +155,7 @@ tpf_status upload_network(tpf_handle *h) {
                                                           (__half *)d.Kr16, (__half *)d.Ki16);
     TPF_CK(cudaGetLastError());
     TPF_CK(cudaDeviceSynchronize());
+    std::vector<double>().swap(net.K);  // the device copies serve from here on
     return TPF_OK;
 }
 
@@ -404,7 +422,9 @@ __global__ void f64_finish(int64_t T, int n, int max_iter, const int *__restrict
 
 tpf_status solve_fp64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters, double *mismatch,
                       const tpf_opts &o, cudaStream_t st) {
-    tpf_status rs = ensure_workspace(h, T, kWsFp64);
+    tpf_status rs = ensure_dense(h);
+    if (rs != TPF_OK) return rs;
+    rs = ensure_workspace(h, T, kWsFp64);
     if (rs != TPF_OK) return rs;
     Workspace &w = h->ws;
     const int n = h->dev.n;

@@ -115,29 +115,17 @@ tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int
     net.radial = (n_branch == n_bus - 1);
 
     const int n = n_pq;
-    net.K.assign((size_t)2 * n * n, 0.0);
     if (net.radial) {
-        // (Y_dd^{-1})_{ij} = impedance of the branches shared by the slack-to-i and slack-to-j
-        // paths.  For each j: mark j's ancestors with their path impedance, then a top-down
-        // pass gives every bus the path impedance of its deepest marked ancestor.
-        std::vector<cplx> zpath(n_bus, 0.0), val(n_bus);
-        for (size_t q = 1; q < order.size(); ++q) zpath[order[q]] = zpath[parent[order[q]]] + zpar[order[q]];
-        std::vector<char> mark(n_bus);
-        for (int jc = 0; jc < n; ++jc) {
-            std::fill(mark.begin(), mark.end(), 0);
-            for (int u = net.pq[jc]; u != slack; u = parent[u]) mark[u] = 1;
-            val[slack] = 0.0;
-            for (size_t q = 1; q < order.size(); ++q) {
-                int u = order[q];
-                val[u] = mark[u] ? zpath[u] : val[parent[u]];
-            }
-            for (int ic = 0; ic < n; ++ic) {
-                cplx k = -val[net.pq[ic]];
-                net.K[((size_t)ic * n + jc) * 2] = k.real();
-                net.K[((size_t)ic * n + jc) * 2 + 1] = k.imag();
-            }
+        // K is built on demand (compute_dense): the sparse formulation never needs it.
+        net.bfs_order = order;
+        net.bus_parent = parent;
+        net.bus_z.assign(2 * (size_t)n_bus, 0.0);
+        for (int b = 0; b < n_bus; ++b) {
+            net.bus_z[2 * b] = zpar[b].real();
+            net.bus_z[2 * b + 1] = zpar[b].imag();
         }
     } else {
+        net.K.assign((size_t)2 * n * n, 0.0);
         std::vector<cplx> Ydd((size_t)n * n, 0.0);
         for (int i = 0; i < n; ++i) {
             int b = net.pq[i];
@@ -152,22 +140,12 @@ tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int
             net.K[2 * k + 1] = -Ydd[k].imag();
         }
     }
-    // W = K Y_ds v_s, with (Y_ds)_i = -(sum of admittances of branches from bus i to the slack).
-    std::vector<cplx> yds(n, 0.0);
-    for (int i = 0; i < n; ++i)
-        for (auto &nb : adj[net.pq[i]])
-            if (nb.first == slack) yds[i] -= nb.second;
-    cplx vs(v0_re, v0_im);
+    // W = K Y_ds v_s.  Without shunts every row of Y sums to zero, so Y_dd 1 = -Y_ds and
+    // W = -Y_dd^{-1} Y_ds v_s = v_s at every demand bus.
     net.W.assign((size_t)2 * n, 0.0);
     for (int i = 0; i < n; ++i) {
-        cplx acc = 0.0;
-        for (int j = 0; j < n; ++j) {
-            if (yds[j] == cplx(0.0)) continue;
-            acc += cplx(net.K[((size_t)i * n + j) * 2], net.K[((size_t)i * n + j) * 2 + 1]) * yds[j];
-        }
-        acc *= vs;
-        net.W[2 * i] = acc.real();
-        net.W[2 * i + 1] = acc.imag();
+        net.W[2 * i] = v0_re;
+        net.W[2 * i + 1] = v0_im;
     }
     // Tree arrays in column positions (radial networks).
     if (net.radial) {
@@ -253,6 +231,36 @@ tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int
     return TPF_OK;
 }
 
+void compute_dense(Network &net) {
+    if (!net.K.empty() || !net.radial) return;
+    // (Y_dd^{-1})_{ij} = impedance of the branches shared by the slack-to-i and slack-to-j paths.
+    // For each j: mark j's ancestors with their path impedance, then a top-down pass gives every
+    // bus the path impedance of its deepest marked ancestor.
+    const int n = net.n_pq, n_bus = net.n_bus, slack = net.slack;
+    const std::vector<int> &order = net.bfs_order, &parent = net.bus_parent;
+    net.K.assign((size_t)2 * n * n, 0.0);
+    std::vector<cplx> zpath(n_bus, 0.0), val(n_bus);
+    for (size_t q = 1; q < order.size(); ++q) {
+        const int u = order[q];
+        zpath[u] = zpath[parent[u]] + cplx(net.bus_z[2 * u], net.bus_z[2 * u + 1]);
+    }
+    std::vector<char> mark(n_bus);
+    for (int jc = 0; jc < n; ++jc) {
+        std::fill(mark.begin(), mark.end(), 0);
+        for (int u = net.pq[jc]; u != slack; u = parent[u]) mark[u] = 1;
+        val[slack] = 0.0;
+        for (size_t q = 1; q < order.size(); ++q) {
+            const int u = order[q];
+            val[u] = mark[u] ? zpath[u] : val[parent[u]];
+        }
+        for (int ic = 0; ic < n; ++ic) {
+            const cplx k = -val[net.pq[ic]];
+            net.K[((size_t)ic * n + jc) * 2] = k.real();
+            net.K[((size_t)ic * n + jc) * 2 + 1] = k.imag();
+        }
+    }
+}
+
 }  // namespace tpf
 
 extern "C" {
@@ -294,6 +302,11 @@ tpf_status tpf_precompute_host(int n_bus, int n_branch, const int32_t *from, con
         return TPF_ENOMEM;
     }
     if (st != TPF_OK) return st;
+    try {
+        tpf::compute_dense(net);
+    } catch (const std::bad_alloc &) {
+        return TPF_ENOMEM;
+    }
     std::memcpy(K_out, net.K.data(), net.K.size() * sizeof(double));
     std::memcpy(W_out, net.W.data(), net.W.size() * sizeof(double));
     return TPF_OK;

@@ -38,7 +38,11 @@ struct Network {
     bool radial = false;
     std::vector<int> pq;          // column position -> bus
     std::vector<int> pos;         // bus -> column position, -1 for the slack
-    std::vector<double> K;        // complex [n_pq][n_pq], K = -Y_dd^{-1}
+    std::vector<double> K;        // complex [n_pq][n_pq], K = -Y_dd^{-1} (radial: built on demand)
+    // Radial networks: breadth-first bus order from the slack, each bus's parent and the complex
+    // impedance of the branch to it (bus-indexed), from which compute_dense builds K.
+    std::vector<int> bfs_order, bus_parent;
+    std::vector<double> bus_z;
     std::vector<double> W;        // complex [n_pq], W = K Y_ds v_s
     // Neighbour lists of the demand buses (CSR over column positions): for each bus i, the
     // other end j of every branch at i (-1 = the slack) and that branch's admittance y = 1/z.
@@ -55,6 +59,9 @@ struct Network {
     std::vector<int> dfs_col, dfs_end, dfs_eptr, dfs_ends, dfs_rp, dfs_nbr;
     std::vector<double> dfs_z, dfs_y;  // complex
 };
+
+// Build K (radial networks build it here, on first need; a no-op when it exists).
+void compute_dense(Network &net);
 
 // Build the network arrays; returns TPF_OK or the status to report.
 tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int32_t *to,
@@ -179,6 +186,8 @@ struct tpf_handle {
 namespace tpf {
 // Upload the network to the device (tpf_create).
 tpf_status upload_network(tpf_handle *h);
+// Upload K, W and the fp16 planes of K on first use by a dense solve.
+tpf_status ensure_dense(tpf_handle *h);
 void free_device(tpf_handle *h);
 // Ensure workspaces for `cols` columns: kind 0 = FP64 path, 1 = mixed path, 2 = per-column state only.
 enum WorkspaceKind : int { kWsFp64 = 0, kWsMixed = 1, kWsState = 2 };

@@ -111,7 +111,9 @@ tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t
                        const tpf_opts &o, cudaStream_t st) {
     const int n = h->dev.n, n_pad = h->dev.n_pad;
     if (n_pad > 2048) return TPF_EUNSUPPORTED;
-    tpf_status rs = ensure_workspace(h, T, kWsMixed);
+    tpf_status rs = ensure_dense(h);
+    if (rs != TPF_OK) return rs;
+    rs = ensure_workspace(h, T, kWsMixed);
     if (rs != TPF_OK) return rs;
     Workspace &w = h->ws;
     const int64_t cols = round_up(T, kTileN);

@@ -254,3 +254,66 @@ def step_minutes_for(T: int) -> float:
 
 def flat_start(T: int, n_pq: int) -> np.ndarray:
     return np.ones((T, n_pq), dtype=np.complex128)
+
+
+# ---------------------------------------------------------------------------------------------
+# The same recipes drawn directly on a CUDA device (torch), for workloads too large to build on
+# the host.  The noise comes from torch's device generator seeded from (seed, purpose), so these
+# tensors are reproducible for a given torch build but differ from the host recipes' draws; checks
+# against the oracle read the sampled columns back from the device.
+# ---------------------------------------------------------------------------------------------
+
+def _torch_gen(device, seed: int, tag: int, sub: int = 0):
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed((int(seed) * 1_000_003 + int(tag) * 7_919 + int(sub)) % (2 ** 63))
+    return g
+
+
+def load_tensor_device(feeder: Feeder, T: int, seed: int, device, step_minutes: float = 1.0,
+                       dtype=None):
+    """Load tensor S[T][n_pq] on ``device`` with the recipe of ``load_tensor`` (complex128 default)."""
+    import torch
+
+    dtype = dtype or torch.complex128
+    real = torch.float64 if dtype == torch.complex128 else torch.float32
+    base, pf = feeder.pq_params()
+    p0 = torch.tensor(feeder.load_scale * base / S_BASE_KW, dtype=torch.float64, device=device)
+    tanphi = torch.tensor(np.tan(np.arccos(pf)), dtype=torch.float64, device=device)
+    hours = torch.tensor((np.arange(T) * step_minutes / 60.0) % 24.0, dtype=torch.float64)
+    shape = torch.tensor(daily_shape(hours.numpy()), dtype=torch.float64, device=device)
+    noise = torch.randn((T, feeder.n_pq), generator=_torch_gen(device, seed, _TAG_LOAD), device=device,
+                        dtype=torch.float64).mul_(0.2).exp_()
+    p = noise.mul_(p0[None, :]).mul_(shape[:, None])
+    return torch.complex(p.to(real), (p * tanphi[None, :]).to(real)).to(dtype)
+
+
+def scenario_tensor_device(feeder: Feeder, n_scen: int, n_hours: int, seed: int, device,
+                           factor_range=(0.5, 1.8), pv_fraction: float = 0.3, pv_kw_max: float = 8.0):
+    """Scenario x time load tensor S[scenario, hour, n_pq], complex64, with the recipe of
+    ``scenario_tensor`` (scenario factors, PV buses and PV sizes are the host recipe's draws)."""
+    import torch
+
+    base, pf = feeder.pq_params()
+    n_pq = feeder.n_pq
+    p0 = torch.tensor(feeder.load_scale * base / S_BASE_KW, dtype=torch.float32, device=device)
+    tanphi = torch.tensor(np.tan(np.arccos(pf)), dtype=torch.float32, device=device)
+    rs = _rng(seed, _TAG_SCEN)
+    factor = torch.tensor(rs.uniform(factor_range[0], factor_range[1], n_scen), dtype=torch.float32, device=device)
+    rp = _rng(seed, _TAG_PV)
+    has_pv = np.zeros(n_pq, dtype=bool)
+    has_pv[rp.choice(n_pq, size=int(round(pv_fraction * n_pq)), replace=False)] = True
+    pv_kw = torch.tensor(rp.uniform(0.0, pv_kw_max, (n_scen, n_pq)) * has_pv[None, :], dtype=torch.float32,
+                         device=device)
+    hours = np.arange(n_hours) % 24
+    shape = torch.tensor(daily_shape(hours), dtype=torch.float32, device=device)
+    bell = torch.tensor(clear_sky(hours), dtype=torch.float32, device=device)
+    out = torch.empty((n_scen, n_hours, n_pq), dtype=torch.complex64, device=device)
+    g = _torch_gen(device, seed, _TAG_LOAD)
+    for s in range(n_scen):
+        noise = torch.randn((n_hours, n_pq), generator=g, device=device, dtype=torch.float32).mul_(0.2).exp_()
+        pl = noise.mul_(p0[None, :]).mul_(shape[:, None]).mul_(factor[s])
+        ppv = pv_kw[s][None, :] / S_BASE_KW * bell[:, None]
+        out[s] = torch.complex(pl - ppv, pl * tanphi[None, :])
+    return out

@@ -183,21 +183,6 @@ __device__ __forceinline__ c2 block_scan_dd(c2 v, float4 *wt, int lane, int warp
     return cqadd(pre, off);
 }
 
-// Largest values over the block; every thread gets the same result.
-__device__ __forceinline__ float2 block_max(float2 m, float2 *wm, int lane, int warp, int nwarps) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        m.x = fmaxf(m.x, __shfl_xor_sync(kFull, m.x, o));
-        m.y = fmaxf(m.y, __shfl_xor_sync(kFull, m.y, o));
-    }
-    if (lane == 0) wm[warp] = m;
-    __syncthreads();
-    float2 d = wm[0];
-    for (int w = 1; w < nwarps; ++w) d = make_float2(fmaxf(d.x, wm[w].x), fmaxf(d.y, wm[w].y));
-    return d;
-}
-
-
 // Slot of depth-first position p for blocks of th threads with kBPT positions each.
 template <int kBPT>
 __device__ __forceinline__ int slot_of(int p, int th) {
@@ -211,8 +196,8 @@ __device__ __forceinline__ int slot_of(int p, int th) {
 // column and its code stays small; the unrolled staging in the kernel keeps the device-memory
 // loads in flight together.
 template <int kBPT>
-__device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B, const int *s_end,
-                                        const int *s_ends, const int *ecnt, float4 *wtd, int tid, int th, int lane,
+__device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B, const short *s_end,
+                                        const short *s_ends, const int *ecnt, float4 *wtd, int tid, int th, int lane,
                                         int warp) {
     const int n = a.n, base = tid * kBPT;
     // Load currents at V_ref and their inclusive prefix sums.
@@ -265,7 +250,7 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
 }
 
 template <int kBPT>
-__global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(const __grid_constant__ TreeArgs g) {
+__global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant__ TreeArgs g) {
     extern __shared__ float4 tsm[];
     __shared__ int s_work;
     const int th = blockDim.x, ns = th * kBPT;
@@ -285,14 +270,15 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(con
     // Arrays indexed by slot s = j th + k of position q = kBPT k + j.
     float4 *const A = tsm;       // [ns] double-float prefix sums (anchor); float2 P and X in the sweeps
     float4 *const B = tsm + ns;  // [ns] V_ref (anchor input), x (anchor), then D = BFS(V_ref) - V_ref
-    int *const s_end = reinterpret_cast<int *>(tsm + 2 * ns);  // [ns] end of the subtree's range
-    int *const s_par = s_end + ns;                             // [ns] parent slot, -1 = the slack
-    int *const s_ends = s_par + ns;  // [n_ends] slots of the positions whose range ends at a position
+    float4 *const C = tsm + 2 * ns;  // [ns] (S_hi, z_hi) of each position
+    short *const s_end = reinterpret_cast<short *>(tsm + 3 * ns);  // [ns] end of the subtree's range
+    short *const s_par = s_end + ns;                               // [ns] parent slot, -1 = the slack
+    short *const s_ends = s_par + ns;  // [n_ends] slots of the positions whose range ends at a position
     float2 *P = reinterpret_cast<float2 *>(A);  // [ns] inclusive prefix sums of the load currents
     float2 *X = P + ns;                           // [ns] branch terms z_q L_q; the residual's x at the end
-    __shared__ float2 wt1[kMaxWarps], wt2[kMaxWarps];
+    __shared__ float2 wt2[kMaxWarps];
     __shared__ float4 wtd[kMaxWarps];
-    __shared__ float2 wmax[kMaxWarps];
+    __shared__ float4 wtm[kMaxWarps];
     __shared__ float4 wm[kMaxWarps];
     const int64_t t = (int64_t)blockIdx.x - a.col0;  // column within the feeder
     const int base = tid * kBPT;
@@ -303,29 +289,31 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(con
 #pragma unroll
     for (int j = 0; j < kBPT; ++j) {
         const int s = j * th + tid;
-        s_end[s] = a.end[s];
-        s_par[s] = a.par[s];
-        if (s < a.n_ends) s_ends[s] = a.ends[s];
+        s_end[s] = (short)a.end[s];
+        s_par[s] = (short)a.par[s];
+        if (s < a.n_ends) s_ends[s] = (short)a.ends[s];
     }
-    // Per position: V_ref (or V before anchoring), delta = V - V_ref, S (FP32), z, ends list.
-    float2 vr[kBPT], dl[kBPT], sh[kBPT], zr[kBPT];
+    // Per position: V_ref (or V before anchoring) and delta = V - V_ref in registers, the ends-list
+    // bounds in registers, S and z in C.
+    float2 vr[kBPT], dl[kBPT];
     int ecnt[kBPT];
 #pragma unroll
     for (int j = 0; j < kBPT; ++j) {
         const int q = base + j, s = j * th + tid;
         vr[j] = make_float2(1.0f, 0.0f);
-        dl[j] = sh[j] = zr[j] = make_float2(0.0f, 0.0f);
+        dl[j] = make_float2(0.0f, 0.0f);
         ecnt[j] = 0;
+        float2 sh = make_float2(0.0f, 0.0f), zh = sh;
         if (q < n) {
             const int i = a.col[s];
             if (a.s32) {
-                sh[j] = S32[i];
+                sh = S32[i];
             } else {
                 const double2 sv = S64[i];
-                sh[j] = make_float2(__double2float_rn(sv.x), __double2float_rn(sv.y));
+                sh = make_float2(__double2float_rn(sv.x), __double2float_rn(sv.y));
             }
             const float4 zq = a.z[s];
-            zr[j] = make_float2(zq.x, zq.y);
+            zh = make_float2(zq.x, zq.y);
             ecnt[j] = a.ecnt[s];
             if (g.given) {
                 if (a.v32) {
@@ -338,14 +326,46 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(con
                 }
             }
         }
+        C[s] = make_float4(sh.x, sh.y, zh.x, zh.y);
     }
     __syncthreads();
     // A given start is anchored at once ("blind"), and anchored again when the step is small.
     bool anchored = g.given != 0, blind = anchored, anchor_now = anchored, done = false, conv = false;
     int it = 0, anchors = 0;
     float dprev2 = 0.0f;
+    // Each sweep's block-wide max |step| (and max |delta|) is reduced within the warp at the end
+    // of the sweep and finished at the first barrier of the next one (its first scan's), where
+    // the decision is taken; a sweep whose predecessor turns out to end the column or to call for
+    // an anchor is abandoned before it changes any state.
+    bool pending = false;
+    float2 wmx = make_float2(0.0f, 0.0f);
+    // Every thread takes the same decision from the same block max.  A step is only trusted to be
+    // below tol on an anchored column whose offset from V_ref is small: in FP32 on V itself (or on
+    // a large offset) a tiny step can round to zero.
+    auto decide = [&](float2 dm) {
+        const float d2 = dm.x;
+        ++it;
+        if (d2 <= g.tol2 && anchored && (!blind || dm.y < g.switch_tol2)) {
+            done = conv = true;
+        } else if (it >= g.max_iter || !(d2 < 1e30f)) {
+            done = true;
+        } else if (!anchored || blind) {
+            // Anchor once the step is small, or is predicted (geometric rate) to fall below 3e-6
+            // in the next sweep: d^2 < 3e-6 d_prev, squared.
+            if (d2 < g.switch_tol2 || (dprev2 > 0.0f && d2 * d2 < 9e-12f * dprev2)) {
+                anchor_now = true;
+                blind = false;
+            }
+        }
+        dprev2 = d2;
+    };
     for (;;) {
+        // The first sweep after an anchor taken from the FP32 phase starts at delta = 0 exactly:
+        // every load-current change is zero, so the path sums are zero and the sweep returns
+        // delta = D.  Its scans are skipped (the result is the same bit for bit).
+        bool zero_sweep = false;
         if (anchor_now) {
+            zero_sweep = !anchored;
             anchor_now = false;
             anchored = true;
             ++anchors;
@@ -356,12 +376,13 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(con
                 const f2 re = two_sum(vr[j].x, dl[j].x), im = two_sum(vr[j].y, dl[j].y);
                 vr[j] = make_float2(re.h, im.h);
                 dl[j] = make_float2(re.l, im.l);
+                const float4 cs = C[s];
                 float2 slo = make_float2(0.0f, 0.0f);
                 if (q < n && !a.s32) {
                     const double2 sv = S64[a.col[s]];
-                    slo = make_float2(__double2float_rn(sv.x - (double)sh[j].x), __double2float_rn(sv.y - (double)sh[j].y));
+                    slo = make_float2(__double2float_rn(sv.x - (double)cs.x), __double2float_rn(sv.y - (double)cs.y));
                 }
-                A[s] = make_float4(sh[j].x, sh[j].y, 0.0f, 0.0f);
+                A[s] = make_float4(cs.x, cs.y, 0.0f, 0.0f);
                 B[s] = make_float4(re.h, im.h, slo.x, slo.y);
             }
             const c2 off = anchor_dd<kBPT>(a, A, B, s_end, s_ends, ecnt, wtd, tid, th, lane, warp);
@@ -379,61 +400,89 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(con
         if (done) break;
 
         // --- one sweep ---
-        // Load currents (or their change from V_ref) and their inclusive prefix sums P.
-        float2 loc[kBPT];
-        float2 run = make_float2(0.0f, 0.0f);
+        float2 loc[kBPT], off = make_float2(0.0f, 0.0f);  // path sums: off + loc[j]
 #pragma unroll
-        for (int j = 0; j < kBPT; ++j) {
-            const float2 I = anchored ? delta_current_fast(vr[j], dl[j], sh[j]) : current_fast(vr[j], sh[j]);
-            run = add2(run, I);  // positions past n have S = 0 and add nothing
-            loc[j] = run;
-        }
-        float2 off = block_scan(run, wt1, lane, warp);
-#pragma unroll
-        for (int j = 0; j < kBPT; ++j) P[j * th + tid] = add2(off, loc[j]);
-        __syncthreads();
-        // Branch terms x_q = z_q (P[end_q - 1] - P[q - 1]).
-#pragma unroll
-        for (int j = 0; j < kBPT; ++j) {
-            const int q = base + j, s = j * th + tid;
-            float2 xq = make_float2(0.0f, 0.0f);  // positions past n contribute nothing
-            if (q < n) {
-                float2 L = P[slot_of<kBPT>(s_end[s] - 1, th)];
-                if (q > 0) L = sub2(L, P[j ? s - th : (kBPT - 1) * th + tid - 1]);
-                xq = cmul2(zr[j], L);
-            }
-            X[s] = xq;
-        }
-        __syncthreads();
-        // Path sums: prefix sums of E_q = x_q - (x_b of every b whose subtree range ends at q).
-        // Up to kGather entries per position unrolled and predicated; longer lists (rare: a drop
-        // of more than kGather levels between neighbouring positions) finish in a loop.
-        bool longer = false;
-#pragma unroll
-        for (int j = 0; j < kBPT; ++j) {
-            const int s = j * th + tid;
-            const int st = ecnt[j] & 0xffff, cnt = ecnt[j] >> 16;
-            float2 e = X[s];
-#pragma unroll
-            for (int k = 0; k < kGather; ++k)
-                if (k < cnt) e = sub2(e, X[s_ends[st + k]]);
-            longer |= cnt > kGather;
-            loc[j] = e;
-        }
-        if (longer) {
+        for (int j = 0; j < kBPT; ++j) loc[j] = off;
+        if (!zero_sweep) {
+            // Load currents (or their change from V_ref) and their inclusive prefix sums P.
+            float2 run = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
-                const int st = ecnt[j] & 0xffff, cnt = ecnt[j] >> 16;
-                for (int k = kGather; k < cnt; ++k) loc[j] = sub2(loc[j], X[s_ends[st + k]]);
+                const float4 cs = C[j * th + tid];
+                const float2 sh = make_float2(cs.x, cs.y);
+                const float2 I = anchored ? delta_current_fast(vr[j], dl[j], sh) : current_fast(vr[j], sh);
+                run = add2(run, I);  // positions past n have S = 0 and add nothing
+                loc[j] = run;
             }
-        }
-        run = make_float2(0.0f, 0.0f);
+            {
+                // First scan; its barrier also finishes the previous sweep's block max.
+                float2 inc = run;
 #pragma unroll
-        for (int j = 0; j < kBPT; ++j) {
-            run = add2(run, loc[j]);  // positions past n have x = 0 and no ends
-            loc[j] = run;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float ux = __shfl_up_sync(kFull, inc.x, o), uy = __shfl_up_sync(kFull, inc.y, o);
+                    if (lane >= o) inc = add2(make_float2(ux, uy), inc);
+                }
+                const float ex = __shfl_up_sync(kFull, inc.x, 1), ey = __shfl_up_sync(kFull, inc.y, 1);
+                if (lane == 31) wtm[warp] = make_float4(inc.x, inc.y, wmx.x, wmx.y);
+                __syncthreads();
+                if (pending) {
+                    pending = false;
+                    float2 dm = make_float2(wtm[0].z, wtm[0].w);
+                    for (int w = 1; w < nwarps; ++w) dm = make_float2(fmaxf(dm.x, wtm[w].z), fmaxf(dm.y, wtm[w].w));
+                    decide(dm);
+                    if (done || anchor_now) continue;
+                }
+                float2 pre = make_float2(0.0f, 0.0f);
+                for (int w = 0; w < warp; ++w) pre = add2(pre, make_float2(wtm[w].x, wtm[w].y));
+                off = add2(pre, lane ? make_float2(ex, ey) : make_float2(0.0f, 0.0f));
+            }
+#pragma unroll
+            for (int j = 0; j < kBPT; ++j) P[j * th + tid] = add2(off, loc[j]);
+            __syncthreads();
+            // Branch terms x_q = z_q (P[end_q - 1] - P[q - 1]).
+#pragma unroll
+            for (int j = 0; j < kBPT; ++j) {
+                const int q = base + j, s = j * th + tid;
+                float2 xq = make_float2(0.0f, 0.0f);  // positions past n contribute nothing
+                if (q < n) {
+                    float2 L = P[slot_of<kBPT>(s_end[s] - 1, th)];
+                    if (q > 0) L = sub2(L, P[j ? s - th : (kBPT - 1) * th + tid - 1]);
+                    const float4 cs = C[s];
+                    xq = cmul2(make_float2(cs.z, cs.w), L);
+                }
+                X[s] = xq;
+            }
+            __syncthreads();
+            // Path sums: prefix sums of E_q = x_q - (x_b of every b whose subtree range ends at
+            // q).  Up to kGather entries per position unrolled and predicated; longer lists (rare:
+            // a drop of more than kGather levels between neighbouring positions) finish in a loop.
+            bool longer = false;
+#pragma unroll
+            for (int j = 0; j < kBPT; ++j) {
+                const int s = j * th + tid;
+                const int st = ecnt[j] & 0xffff, cnt = ecnt[j] >> 16;
+                float2 e = X[s];
+#pragma unroll
+                for (int k = 0; k < kGather; ++k)
+                    if (k < cnt) e = sub2(e, X[s_ends[st + k]]);
+                longer |= cnt > kGather;
+                loc[j] = e;
+            }
+            if (longer) {
+#pragma unroll
+                for (int j = 0; j < kBPT; ++j) {
+                    const int st = ecnt[j] & 0xffff, cnt = ecnt[j] >> 16;
+                    for (int k = kGather; k < cnt; ++k) loc[j] = sub2(loc[j], X[s_ends[st + k]]);
+                }
+            }
+            run = make_float2(0.0f, 0.0f);
+#pragma unroll
+            for (int j = 0; j < kBPT; ++j) {
+                run = add2(run, loc[j]);  // positions past n have x = 0 and no ends
+                loc[j] = run;
+            }
+            off = block_scan(run, wt2, lane, warp);
         }
-        off = block_scan(run, wt2, lane, warp);
         float2 mx = make_float2(0.0f, 0.0f);  // max |step|^2, max |delta|^2
 #pragma unroll
         for (int j = 0; j < kBPT; ++j) {
@@ -457,25 +506,13 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(con
                 mx.x = fmaxf(mx.x, mag2);
             }
         }
-        const float2 dm = block_max(mx, wmax, lane, warp, nwarps);
-        const float d2 = dm.x;
-        // Every thread takes the same decision from the same d.  A step is only trusted to be
-        // below tol on an anchored column whose offset from V_ref is small: in FP32 on V itself
-        // (or on a large offset) a tiny step can round to zero.
-        ++it;
-        if (d2 <= g.tol2 && anchored && (!blind || dm.y < g.switch_tol2)) {
-            done = conv = true;
-        } else if (it >= g.max_iter || !(d2 < 1e30f)) {
-            done = true;
-        } else if (!anchored || blind) {
-            // Anchor once the step is small, or is predicted (geometric rate) to fall below 3e-6
-            // in the next sweep: d^2 < 3e-6 d_prev, squared.
-            if (d2 < g.switch_tol2 || (dprev2 > 0.0f && d2 * d2 < 9e-12f * dprev2)) {
-                anchor_now = true;
-                blind = false;
-            }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            mx.x = fmaxf(mx.x, __shfl_xor_sync(kFull, mx.x, o));
+            mx.y = fmaxf(mx.y, __shfl_xor_sync(kFull, mx.y, o));
         }
-        dprev2 = d2;
+        wmx = mx;
+        pending = true;
     }
 
     // Outputs: V, iteration count and the mismatch max_i |V_i| |rho_i| at the returned V, with
@@ -516,8 +553,10 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(con
         const int q = base + j, s = j * th + tid;
         if (q < n) {
             const int p = s_par[s];
-            const float2 y = make_float2(zr[j].x, -zr[j].y);
-            const float2 yk = make_float2(y.x * __fdividef(1.0f, abs2(zr[j])), y.y * __fdividef(1.0f, abs2(zr[j])));
+            const float4 cs = C[s];
+            const float2 zq = make_float2(cs.z, cs.w);
+            const float inv = __fdividef(1.0f, abs2(zq));
+            const float2 yk = make_float2(zq.x * inv, -zq.y * inv);
             J[s] = cmul2(yk, sub2(p >= 0 ? X[p] : x_slack, xs[j]));
         }
     }
@@ -528,7 +567,9 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 ? 80 : 64)) mx_tree(con
     for (int j = 0; j < kBPT; ++j) {
         const int q = base + j, s = j * th + tid;
         if (q < n) {
-            float2 r = anchored ? delta_current_fast(vr[j], dl[j], sh[j]) : current_fast(vr[j], sh[j]);
+            const float4 cs = C[s];
+            const float2 sh = make_float2(cs.x, cs.y);
+            float2 r = anchored ? delta_current_fast(vr[j], dl[j], sh) : current_fast(vr[j], sh);
             r = sub2(r, J[s]);
             const int e = s_end[s];
             for (int k = q + 1; k < e;) {
@@ -608,7 +649,7 @@ TreeWork work_of(const tpf_handle *h) {
 
 size_t tree_smem(int threads, int bpt) {
     const size_t ns = (size_t)threads * bpt;
-    return 2 * ns * sizeof(float4) + sizeof(int) * 3 * ns;  // A, B, end, parent, ends (<= ns entries)
+    return 3 * ns * sizeof(float4) + sizeof(short) * 3 * ns;  // A, B, C; end, parent, ends (<= ns entries)
 }
 
 tpf_status launch_tree(int bpt, int threads, int64_t cols, const TreeArgs &g, cudaStream_t st) {

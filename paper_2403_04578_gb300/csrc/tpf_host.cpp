@@ -497,7 +497,10 @@ tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_
     // at once on an input stream, each chunk's solve waits only for its own copy, and its results go
     // back on an output stream while the next chunk is solved (pinned host memory overlaps; pageable
     // memory still works, with the copies serialised by the driver).
-    const int64_t n_chunks = T >= 65536 ? std::min<int64_t>(8, T / 16384) : 1;
+    // The sparse solve is one short launch per chunk, so it takes finer chunks (less fill and drain
+    // around the copies); the dense solve's per-sweep host loop prefers fewer.
+    const int64_t max_chunks = o.method == TPF_METHOD_SPARSE ? 32 : 8;
+    const int64_t n_chunks = T >= 65536 ? std::min<int64_t>(max_chunks, T / 16384) : 1;
     const int64_t chunk = tpf::round_up((T + n_chunks - 1) / n_chunks, tpf::kTileN);
     cudaStream_t sin = nullptr, sout = nullptr;
     std::vector<cudaEvent_t> ev;

@@ -303,7 +303,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
         vr[j] = make_float2(1.0f, 0.0f);
         dl[j] = make_float2(0.0f, 0.0f);
         ecnt[j] = 0;
-        float2 sh = make_float2(0.0f, 0.0f), zh = sh;
+        float2 sh = make_float2(0.0f, 0.0f), zh = sh, sl = sh;
         if (q < n) {
             const int i = a.col[s];
             if (a.s32) {
@@ -311,6 +311,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
             } else {
                 const double2 sv = S64[i];
                 sh = make_float2(__double2float_rn(sv.x), __double2float_rn(sv.y));
+                sl = make_float2(__double2float_rn(sv.x - (double)sh.x), __double2float_rn(sv.y - (double)sh.y));
             }
             const float4 zq = a.z[s];
             zh = make_float2(zq.x, zq.y);
@@ -327,6 +328,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
             }
         }
         C[s] = make_float4(sh.x, sh.y, zh.x, zh.y);
+        B[s] = make_float4(sl.x, sl.y, 0.0f, 0.0f);  // S_lo until the first anchor replaces it by D
     }
     __syncthreads();
     // A given start is anchored at once ("blind"), and anchored again when the step is small.
@@ -377,10 +379,16 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                 vr[j] = make_float2(re.h, im.h);
                 dl[j] = make_float2(re.l, im.l);
                 const float4 cs = C[s];
-                float2 slo = make_float2(0.0f, 0.0f);
-                if (q < n && !a.s32) {
-                    const double2 sv = S64[a.col[s]];
-                    slo = make_float2(__double2float_rn(sv.x - (double)cs.x), __double2float_rn(sv.y - (double)cs.y));
+                float2 slo;
+                if (anchors == 1) {  // B still holds S_lo
+                    const float4 b = B[s];
+                    slo = make_float2(b.x, b.y);
+                } else {
+                    slo = make_float2(0.0f, 0.0f);
+                    if (q < n && !a.s32) {
+                        const double2 sv = S64[a.col[s]];
+                        slo = make_float2(__double2float_rn(sv.x - (double)cs.x), __double2float_rn(sv.y - (double)cs.y));
+                    }
                 }
                 A[s] = make_float4(cs.x, cs.y, 0.0f, 0.0f);
                 B[s] = make_float4(re.h, im.h, slo.x, slo.y);

@@ -71,7 +71,7 @@ def parse_args():
     p.add_argument("--tol", type=float, default=1e-10)
     p.add_argument("--fp64-sample", type=int, default=8192)
     p.add_argument("--cpu-seconds", type=float, default=15.0)
-    p.add_argument("--check-columns", type=int, default=256)
+    p.add_argument("--check-columns", type=int, default=10000)
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-learned", action="store_true")
@@ -524,7 +524,10 @@ def main():
     Sh = torch.empty((T, n), dtype=torch.complex128, pin_memory=True)
     G.load_tensor(f, T, args.seed, out=Sh.numpy())
     Sd = Sh.to(f"cuda:{local}")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     fd = tpf.Feeder.from_inputs(f)
+    create_ms = (time.perf_counter() - t0) * 1e3
     Vd = torch.empty_like(Sd)
     itd = torch.empty(T, dtype=torch.int32, device=Sd.device)
     mmd = torch.empty(T, dtype=torch.float64, device=Sd.device)
@@ -634,7 +637,7 @@ def main():
             "data": "synthetic", "config": config, "roofline": roofline,
             "e2e": e2e, "clocks": main_run["clocks"], "gpu_launches": main_run["launches"],
             "sweeps": stats["sweeps"], "anchors_or_anchor_sweeps": stats["precise_sweeps"],
-            "mean_sweeps": column_sweeps / T,
+            "mean_sweeps": column_sweeps / T, "tpf_create_ms": create_ms,
             "fp64_gpu": fp64, "speedup_vs_fp64_gpu": (value / world) / fp64_pfs,
             }
     V_other = other_obj.pop("_V", None) if other_obj else None

@@ -182,3 +182,106 @@ void orc_mismatch(int n_bus, const cplx *Y, int slack, double vs_re, double vs_i
     }
     free(full);
 }
+
+/* Eq. 3 with the ZIP load model of the paper, one column at a time.  alpha is [3][n_pq]: the
+ * alpha_P, alpha_I and alpha_Z coefficients of every demand bus.  The demand current of Eq. 1 is
+ * i_d = alpha_P .* conj(s) ./ conj(v) + alpha_I .* conj(s) + alpha_Z .* conj(s) .* v, and for
+ * each column s (its own operating point):
+ *   A = diag(alpha_P .* conj(s)),  B = diag(alpha_Z .* conj(s)) + Y_dd,
+ *   c = Y_ds v_s + alpha_I .* conj(s),  F = -B^{-1} A,  w = -B^{-1} c,
+ *   v_{k+1} = F conj(v_k)^{.-1} + w
+ * with orc_fpi's start and stopping rule.  A column whose B is singular returns NaN and
+ * -max_iter.  Dense, O(n^3) per column: for small test cases only. */
+void orc_fpi_zip(int n_bus, const cplx *Y, int slack, double vs_re, double vs_im, int n_pq, const int *pq,
+                 const double *alpha, long T, const cplx *S, const cplx *V0, double tol, int max_iter,
+                 cplx *V, int *iters, double *last_delta, int n_threads)
+{
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#else
+    (void)n_threads;
+#endif
+    const cplx vs = vs_re + I * vs_im;
+    const int n = n_pq;
+    const double *aP = alpha, *aI = alpha + n, *aZ = alpha + 2 * n;
+#pragma omp parallel
+    {
+        cplx *B = (cplx *)malloc(sizeof(cplx) * (size_t)n * n);
+        cplx *F = (cplx *)malloc(sizeof(cplx) * (size_t)n * n);
+        cplx *w = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+        cplx *c = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+        cplx *v = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+        cplx *cur = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+        cplx *vn = (cplx *)malloc(sizeof(cplx) * (size_t)n);
+#pragma omp for schedule(dynamic, 1)
+        for (long t = 0; t < T; ++t) {
+            const cplx *s = S + (size_t)t * n;
+            for (int i = 0; i < n; ++i) {
+                for (int j = 0; j < n; ++j) B[(size_t)i * n + j] = Y[(size_t)pq[i] * n_bus + pq[j]];
+                B[(size_t)i * n + i] += aZ[i] * conj(s[i]);
+                c[i] = Y[(size_t)pq[i] * n_bus + slack] * vs + aI[i] * conj(s[i]);
+            }
+            if (orc_invert(n, B)) {
+                for (int i = 0; i < n; ++i) V[(size_t)t * n + i] = NAN;
+                iters[t] = -max_iter;
+                last_delta[t] = INFINITY;
+                continue;
+            }
+            for (int i = 0; i < n; ++i) {
+                cplx acc = 0;
+                for (int j = 0; j < n; ++j) {
+                    F[(size_t)i * n + j] = -B[(size_t)i * n + j] * (aP[j] * conj(s[j]));
+                    acc += B[(size_t)i * n + j] * c[j];
+                }
+                w[i] = -acc;
+            }
+            for (int i = 0; i < n; ++i) v[i] = V0 ? V0[(size_t)t * n + i] : 1.0;
+            int k = 0, done = 0;
+            double delta = INFINITY;
+            while (k < max_iter) {
+                for (int j = 0; j < n; ++j) cur[j] = 1.0 / conj(v[j]);
+                delta = 0.0;
+                for (int i = 0; i < n; ++i) {
+                    cplx acc = 0;
+                    for (int j = 0; j < n; ++j) acc += F[(size_t)i * n + j] * cur[j];
+                    vn[i] = acc + w[i];
+                    double d = cabs(vn[i] - v[i]);
+                    if (!(d <= delta)) delta = d;
+                }
+                memcpy(v, vn, sizeof(cplx) * (size_t)n);
+                ++k;
+                if (delta <= tol) { done = 1; break; }
+            }
+            memcpy(V + (size_t)t * n, v, sizeof(cplx) * (size_t)n);
+            iters[t] = done ? k : -max_iter;
+            last_delta[t] = delta;
+        }
+        free(B); free(F); free(w); free(c); free(v); free(cur); free(vn);
+    }
+}
+
+/* Power balance of Eq. 1 with ZIP loads: max_i |V_i| |(Y v)_i + i_d,i| over the demand buses, with
+ * i_d as in orc_fpi_zip (for alpha_P = 1 this is orc_mismatch's |V_i conj((Y v)_i) + S_i|). */
+void orc_mismatch_zip(int n_bus, const cplx *Y, int slack, double vs_re, double vs_im, int n_pq, const int *pq,
+                      const double *alpha, long T, const cplx *S, const cplx *V, double *out)
+{
+    cplx vs = vs_re + I * vs_im;
+    const double *aP = alpha, *aI = alpha + n_pq, *aZ = alpha + 2 * n_pq;
+    cplx *full = (cplx *)malloc(sizeof(cplx) * (size_t)n_bus);
+    for (long t = 0; t < T; ++t) {
+        full[slack] = vs;
+        for (int i = 0; i < n_pq; ++i) full[pq[i]] = V[(size_t)t * n_pq + i];
+        double worst = 0.0;
+        for (int i = 0; i < n_pq; ++i) {
+            const cplx *Yr = Y + (size_t)pq[i] * n_bus;
+            cplx acc = 0;
+            for (int j = 0; j < n_bus; ++j) acc += Yr[j] * full[j];
+            const cplx s = S[(size_t)t * n_pq + i], vi = full[pq[i]];
+            const cplx id = aP[i] * conj(s / vi) + aI[i] * conj(s) + aZ[i] * conj(s) * vi;
+            double m = cabs(vi) * cabs(acc + id);
+            if (!(m <= worst)) worst = m;
+        }
+        out[t] = worst;
+    }
+    free(full);
+}

@@ -71,6 +71,13 @@ def lib():
             L.orc_mismatch.argtypes = [ctypes.c_int, _c128p, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _i32p,
                                        ctypes.c_long, _c128p, _c128p, _f64p]
             L.orc_mismatch.restype = None
+            L.orc_fpi_zip.argtypes = [ctypes.c_int, _c128p, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                      _i32p, _f64p, ctypes.c_long, _c128p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
+                                      _c128p, _i32p, _f64p, ctypes.c_int]
+            L.orc_fpi_zip.restype = None
+            L.orc_mismatch_zip.argtypes = [ctypes.c_int, _c128p, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                           ctypes.c_int, _i32p, _f64p, ctypes.c_long, _c128p, _c128p, _f64p]
+            L.orc_mismatch_zip.restype = None
             _lib = L
         return _lib
 
@@ -129,6 +136,40 @@ def mismatch(Y: np.ndarray, slack: int, vs: complex, pq, S: np.ndarray, V: np.nd
     return out
 
 
+def fpi_zip(Y: np.ndarray, slack: int, vs: complex, pq, alpha, S: np.ndarray, V0: np.ndarray | None = None,
+            tol: float = 1e-13, max_iter: int = 100, threads: int = 0):
+    """Eq. 3 with ZIP loads, column by column (alpha = [alpha_P, alpha_I, alpha_Z], each [n_pq]):
+    F = -B^{-1} A and w = -B^{-1} c of each column's operating point, v <- F conj(v)^{-1} + w.
+    Returns (V, iters, last_delta) like fpi."""
+    S = np.ascontiguousarray(S, np.complex128)
+    T, n = S.shape
+    alpha = np.ascontiguousarray(alpha, np.float64).reshape(3, n)
+    pq = np.ascontiguousarray(pq, np.int32)
+    V = np.empty_like(S)
+    iters = np.empty(T, dtype=np.int32)
+    delta = np.empty(T, dtype=np.float64)
+    v0p = None
+    if V0 is not None:
+        V0 = np.ascontiguousarray(V0, np.complex128)
+        assert V0.shape == S.shape
+        v0p = V0.ctypes.data
+    lib().orc_fpi_zip(Y.shape[0], np.ascontiguousarray(Y), int(slack), *_cd(vs), n, pq, alpha, T, S, v0p, float(tol),
+                      int(max_iter), V, iters, delta, int(threads))
+    return V, iters, delta
+
+
+def mismatch_zip(Y: np.ndarray, slack: int, vs: complex, pq, alpha, S: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """max_i |V_i| |(Y v)_i + i_d,i| per column with the ZIP demand current of Eq. 3."""
+    S = np.ascontiguousarray(S, np.complex128)
+    V = np.ascontiguousarray(V, np.complex128)
+    pq = np.ascontiguousarray(pq, np.int32)
+    alpha = np.ascontiguousarray(alpha, np.float64).reshape(3, pq.shape[0])
+    out = np.empty(S.shape[0], dtype=np.float64)
+    lib().orc_mismatch_zip(Y.shape[0], np.ascontiguousarray(Y), int(slack), *_cd(vs), pq.shape[0], pq, alpha,
+                           S.shape[0], S, V, out)
+    return out
+
+
 class Case:
     """A feeder prepared for the oracle: Y, K, W and the bus bookkeeping."""
 
@@ -152,6 +193,12 @@ class Case:
 
     def mismatch(self, S, V):
         return mismatch(self.Y, self.slack, self.vs, self.pq, S, V)
+
+    def solve_zip(self, S, alpha, V0=None, tol=1e-13, max_iter=100, threads=0):
+        return fpi_zip(self.Y, self.slack, self.vs, self.pq, alpha, S, V0, tol, max_iter, threads)
+
+    def mismatch_zip(self, S, alpha, V):
+        return mismatch_zip(self.Y, self.slack, self.vs, self.pq, alpha, S, V)
 
     def ybus_sparse(self):
         return sp.csr_matrix(self.Y)

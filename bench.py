@@ -24,6 +24,7 @@ Reported on one JSON line (rank 0):
   scenario_tensor  config-3 leg: 500-bus feeder, [200 x 8,760] complex64 scenario tensor with fused
               voltage-band statistics
   feeder_batch  config-4 leg: 4,096 feeders of 20-2,000 buses in one tpf_solve_batch call
+  zip_loads   the headline workload with ZIP loads (Eq. 3) on the sparse formulation
   clocks      nvidia-smi samples taken during the timed region
 
 ``--impl reference`` times the CPU oracle as the reference arm on the same workload.
@@ -77,6 +78,7 @@ def parse_args():
     p.add_argument("--no-learned", action="store_true")
     p.add_argument("--method", choices=["sparse", "dense"], default="sparse")
     p.add_argument("--no-scenario", action="store_true")
+    p.add_argument("--no-zip", action="store_true")
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--scen", type=int, default=200)
     p.add_argument("--hours", type=int, default=8760)
@@ -614,6 +616,26 @@ def main():
         if rank == 0 and not args.no_cpu:
             other_obj["_V"] = Vd.cpu().numpy()
 
+    # ZIP loads (Eq. 3) on the same workload: per-bus shares of constant power / current /
+    # impedance drawn once; the oracle checks the ZIP power balance of sampled columns.
+    zip_obj = None
+    if not args.no_zip:
+        alpha = np.random.default_rng(args.seed).dirichlet([2, 1, 1], n).T.copy()
+        fd.set_zip(alpha)
+        zrun = timed_steps(fd, Sd, Vd, itd, mmd, args, "sparse", max(1, min(args.steps, 3)), stream, world)
+        zip_obj = {"value": world * T / (zrun["ms_per_step"] / 1e3), "unit": "PF/s", "ms_per_step": zrun["ms_per_step"],
+                   "alpha": "per bus (alpha_P, alpha_I, alpha_Z) ~ Dirichlet(2, 1, 1)",
+                   "mean_sweeps": float(itd.abs().float().mean().item()), "converged": zrun["stats"]["converged"]}
+        if rank == 0 and not args.no_cpu:
+            from oracle import oracle as O
+
+            cc = np.linspace(0, T - 1, min(args.check_columns, T)).astype(np.int64)
+            Vz = Vd[torch.from_numpy(cc).to(Vd.device)].cpu().numpy()
+            c = O.Case.from_feeder(f)
+            zip_obj["max_power_mismatch_pu"] = float(c.mismatch_zip(Sh.numpy()[cc], alpha, Vz).max())
+            zip_obj["columns_checked"] = int(cc.size)
+        fd.set_zip(None)
+
     # Plain FP64 GPU FPI on a column sample (the comparison path of the metric).
     F = min(args.fp64_sample, T)
     Sf = Sd[:F].contiguous()
@@ -649,6 +671,8 @@ def main():
         line["accuracy"] = check
     if other_obj is not None:
         line[f"{other}_method"] = other_obj
+    if zip_obj is not None:
+        line["zip_loads"] = zip_obj
     del Sd, Vd, Sh
     torch.cuda.empty_cache()
     if not args.no_learned:

@@ -178,6 +178,22 @@ tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_
 tpf_status tpf_last_stats(const tpf_handle *h, tpf_stats *out);
 
 /*
+ * ZIP loads (Eq. 3).  alpha is host memory [3][n_pq]: alpha_P, alpha_I and alpha_Z of every demand
+ * bus (bus order of tpf_create), applied to every later solve on this handle:
+ *
+ *     i_d = alpha_P conj(S ./ V) + alpha_I conj(S) + alpha_Z conj(S) .* V
+ *
+ * (constant power, constant current and constant impedance parts of each bus's load S).  The
+ * solves keep the shared K = -Y_dd^{-1} and evaluate i_d from the current iterate,
+ * V <- K i_d(V) + W; Eq. 3's per-operating-point F = -B^{-1} A and w = -B^{-1} c have the same
+ * fixed point, but B depends on each column's S when alpha_Z != 0, so a tensor of columns cannot
+ * share them.  alpha == NULL returns the handle to constant power.  Served by TPF_METHOD_SPARSE and
+ * TPF_PREC_FP64; the dense mixed path returns TPF_EUNSUPPORTED while ZIP coefficients are set.
+ * TPF_EINVAL for non-finite coefficients.
+ */
+tpf_status tpf_set_zip(tpf_handle *h, const double *alpha);
+
+/*
  * Scenario / time tensors (Sec. IV: the load tensor may have any number of scenario and time
  * dimensions; its columns are flattened in C order, bus fastest) with per-column and per-bus
  * statistics of the kind probabilistic and time-series studies report, computed in the solve's

@@ -159,12 +159,47 @@ tpf_status ensure_dense(tpf_handle *h) {
     return TPF_OK;
 }
 
+tpf_status set_zip(tpf_handle *h, const double *alpha) {
+    DeviceNet &d = h->dev;
+    cudaFree(d.zip64);
+    cudaFree(d.t_zip_hi);
+    cudaFree(d.t_zip_lo);
+    d.zip64 = nullptr;
+    d.t_zip_hi = d.t_zip_lo = nullptr;
+    if (!alpha) return TPF_OK;
+    const int n = d.n;
+    TPF_CK(cudaMalloc(&d.zip64, sizeof(double) * 3 * (size_t)n));
+    TPF_CK(cudaMemcpy(d.zip64, alpha, sizeof(double) * 3 * (size_t)n, cudaMemcpyHostToDevice));
+    if (d.t_threads > 0) {
+        const int th = d.t_threads, bpt = d.t_bpt, ns = th * bpt;
+        std::vector<float4> hi(ns, make_float4(0.f, 0.f, 0.f, 0.f)), lo = hi;
+        const Network &net = h->net;
+        for (int q = 0; q < n; ++q) {
+            const int s = (q % bpt) * th + q / bpt, i = net.dfs_col[q];
+            float hv[3], lv[3];
+            for (int k = 0; k < 3; ++k) {
+                const double a = alpha[(size_t)k * n + i];
+                hv[k] = (float)a;
+                lv[k] = (float)(a - (double)hv[k]);
+            }
+            hi[s] = make_float4(hv[0], hv[1], hv[2], 0.f);
+            lo[s] = make_float4(lv[0], lv[1], lv[2], 0.f);
+        }
+        TPF_CK(cudaMalloc(&d.t_zip_hi, sizeof(float4) * ns));
+        TPF_CK(cudaMalloc(&d.t_zip_lo, sizeof(float4) * ns));
+        TPF_CK(cudaMemcpy(d.t_zip_hi, hi.data(), sizeof(float4) * ns, cudaMemcpyHostToDevice));
+        TPF_CK(cudaMemcpy(d.t_zip_lo, lo.data(), sizeof(float4) * ns, cudaMemcpyHostToDevice));
+    }
+    return TPF_OK;
+}
+
 void free_device(tpf_handle *h) {
     DeviceNet &d = h->dev;
     cudaFree(d.K64); cudaFree(d.W64); cudaFree(d.row_ptr); cudaFree(d.nbr); cudaFree(d.y64); cudaFree(d.y2f);
     cudaFree(d.Kr16); cudaFree(d.Ki16);
     cudaFree(d.par); cudaFree(d.ch_ptr); cudaFree(d.ch); cudaFree(d.ypar);
     cudaFree(d.t_col); cudaFree(d.t_end); cudaFree(d.t_par); cudaFree(d.t_ecnt); cudaFree(d.t_ends); cudaFree(d.t_z);
+    cudaFree(d.zip64); cudaFree(d.t_zip_hi); cudaFree(d.t_zip_lo);
     d = DeviceNet();
     Workspace &w = h->ws;
     cudaFree(w.Vhi); cudaFree(w.Vlo); cudaFree(w.Shi); cudaFree(w.Slo); cudaFree(w.Rr16); cudaFree(w.Ri16);
@@ -262,7 +297,8 @@ __global__ void f64_init(int64_t T, int64_t cols, int n, int flat, double2 *V, i
 __global__ void __launch_bounds__(256) f64_sweep(const double2 *__restrict__ K, const double2 *__restrict__ W,
                                                  const double2 *__restrict__ S, const double2 *__restrict__ Vin,
                                                  double2 *__restrict__ Vout, int n, int64_t T,
-                                                 const int *__restrict__ flags, unsigned long long *delta) {
+                                                 const int *__restrict__ flags, unsigned long long *delta,
+                                                 const double *__restrict__ zip) {
     __shared__ double2 Ks[F64_BM][F64_KC + 1];
     __shared__ double2 Is[F64_KC][F64_BN];
     __shared__ int act[F64_BN];
@@ -302,6 +338,12 @@ __global__ void __launch_bounds__(256) f64_sweep(const double2 *__restrict__ K, 
                 // conj(s / v) = conj(s) v / |v|^2
                 double inv = 1.0 / (v.x * v.x + v.y * v.y);
                 cur = make_double2((s.x * v.x + s.y * v.y) * inv, (s.x * v.y - s.y * v.x) * inv);
+                if (zip) {
+                    // Eq. 3: alpha_P conj(s / v) + alpha_I conj(s) + alpha_Z conj(s) v
+                    const double ap = zip[k], ai = zip[n + k], az = zip[2 * n + k];
+                    cur = make_double2(ap * cur.x + ai * s.x + az * (s.x * v.x + s.y * v.y),
+                                       ap * cur.y - ai * s.y + az * (s.x * v.y - s.y * v.x));
+                }
             }
             Is[kk][tt] = cur;
         }
@@ -379,7 +421,7 @@ __global__ void f64_finish(int64_t T, int n, int max_iter, const int *__restrict
                            const int *__restrict__ it_state, double2 *V, const double2 *__restrict__ Valt,
                            const double2 *__restrict__ S, const int *__restrict__ row_ptr,
                            const int *__restrict__ nbr, const double2 *__restrict__ y, double2 vs,
-                           int32_t *iters_out, double *mismatch_out) {
+                           const double *__restrict__ zip, int32_t *iters_out, double *mismatch_out) {
     const int lane = threadIdx.x & 31;
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (t >= T) return;
@@ -404,10 +446,21 @@ __global__ void f64_finish(int64_t T, int n, int max_iter, const int *__restrict
             acc.y += ye.x * d.y + ye.y * d.x;
         }
         double2 s = S[t * n + i];
-        // V_i conj(acc) + S_i
-        double mr = vi.x * acc.x + vi.y * acc.y + s.x;
-        double mi = vi.y * acc.x - vi.x * acc.y + s.y;
-        double m = hypot(mr, mi);
+        double m;
+        if (zip) {
+            // |V_i| |(Y v)_i + i_d,i| with the ZIP demand current of Eq. 3
+            const double ap = zip[i], ai = zip[n + i], az = zip[2 * n + i];
+            const double inv = 1.0 / (vi.x * vi.x + vi.y * vi.y);
+            const double cr = (s.x * vi.x + s.y * vi.y) * inv, ci = (s.x * vi.y - s.y * vi.x) * inv;
+            const double ir = ap * cr + ai * s.x + az * (s.x * vi.x + s.y * vi.y);
+            const double ii = ap * ci - ai * s.y + az * (s.x * vi.y - s.y * vi.x);
+            m = hypot(vi.x, vi.y) * hypot(acc.x + ir, acc.y + ii);
+        } else {
+            // V_i conj(acc) + S_i
+            double mr = vi.x * acc.x + vi.y * acc.y + s.x;
+            double mi = vi.y * acc.x - vi.x * acc.y + s.y;
+            m = hypot(mr, mi);
+        }
         if (!(m <= worst)) worst = m;
     }
 #pragma unroll
@@ -446,7 +499,7 @@ tpf_status solve_fp64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t 
     for (int k = 0; k < o.max_iter; ++k) {
         timer.begin(KernelTimer::kGemm);
         f64_sweep<<<grid, 256, 0, st>>>((const double2 *)h->dev.K64, (const double2 *)h->dev.W64, (const double2 *)S,
-                                        buf[k & 1], buf[(k + 1) & 1], n, T, w.flags, w.delta64);
+                                        buf[k & 1], buf[(k + 1) & 1], n, T, w.flags, w.delta64, h->dev.zip64);
         timer.end();
         gemm_cols += active;
         TPF_CK(cudaMemsetAsync(w.counters, 0, sizeof(int) * 4, st));
@@ -465,8 +518,8 @@ tpf_status solve_fp64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t 
     timer.begin(KernelTimer::kOther);
     f64_finish<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(
         T, n, o.max_iter, w.flags, w.iters, (double2 *)V, (const double2 *)w.Valt, (const double2 *)S,
-        h->dev.row_ptr, h->dev.nbr, (const double2 *)h->dev.y64, make_double2(h->net.vs_re, h->net.vs_im), iters,
-        mismatch);
+        h->dev.row_ptr, h->dev.nbr, (const double2 *)h->dev.y64, make_double2(h->net.vs_re, h->net.vs_im),
+        h->dev.zip64, iters, mismatch);
     timer.end();
     ++launches;
     TPF_CK(cudaGetLastError());
@@ -562,7 +615,7 @@ extern "C" tpf_status tpf_solve_fp64_noalloc(int n, const void *K_dev, const voi
     int host_counters[8] = {0};
     for (int k = 0; k < max_iter; ++k) {
         f64_sweep<<<grid, 256, 0, st>>>((const double2 *)K_dev, (const double2 *)W_dev, (const double2 *)S_dev,
-                                        buf[k & 1], buf[(k + 1) & 1], n, T, flags, delta);
+                                        buf[k & 1], buf[(k + 1) & 1], n, T, flags, delta, nullptr);
         TPF_CK(cudaMemsetAsync(counters, 0, sizeof(int) * 4, st));
         f64_decide<<<(unsigned)((T + 255) / 256), 256, 0, st>>>(T, tol, max_iter, flags, iters, delta, counters);
         TPF_CK(cudaGetLastError());
@@ -572,7 +625,8 @@ extern "C" tpf_status tpf_solve_fp64_noalloc(int n, const void *K_dev, const voi
     }
     f64_finish<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(T, n, max_iter, flags, iters, (double2 *)V_dev,
                                                                  Valt, (const double2 *)S_dev, nullptr, nullptr,
-                                                                 nullptr, make_double2(0.0, 0.0), iters_dev, nullptr);
+                                                                 nullptr, make_double2(0.0, 0.0), nullptr, iters_dev,
+                                                                 nullptr);
     TPF_CK(cudaGetLastError());
     TPF_CK(cudaMemcpyAsync(host_counters, counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));
     TPF_CK(cudaStreamSynchronize(st));

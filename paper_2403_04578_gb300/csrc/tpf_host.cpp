@@ -377,6 +377,16 @@ tpf_status tpf_solve(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev, i
     return tpf::solve_mixed(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
 }
 
+tpf_status tpf_set_zip(tpf_handle *h, const double *alpha) {
+    if (!h) return TPF_EINVAL;
+    if (alpha) {
+        for (size_t k = 0; k < 3 * (size_t)h->net.n_pq; ++k)
+            if (!std::isfinite(alpha[k])) return TPF_EINVAL;
+    }
+    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    return tpf::set_zip(h, alpha);
+}
+
 tpf_status tpf_solve_ex(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev, int32_t *iters_dev,
                         double *mismatch_dev, const tpf_outputs *out, const tpf_opts *opts, void *stream) {
     if (!out) return tpf_solve(h, T, S_dev, V_dev, iters_dev, mismatch_dev, opts, stream);

@@ -91,6 +91,11 @@ struct DeviceNet {
     int t_threads = 0, t_bpt = 0, t_n_ends = 0;
     int *t_col = nullptr, *t_end = nullptr, *t_par = nullptr, *t_ecnt = nullptr, *t_ends = nullptr;
     float4 *t_z = nullptr;
+    // ZIP load coefficients (Eq. 3), set by tpf_set_zip; null for constant power.  zip64: double
+    // [3][n] in column order (FP64 path); t_zip_hi / t_zip_lo: float4 (alpha_P, alpha_I, alpha_Z, 0)
+    // per slot, high and low words (sparse path).
+    double *zip64 = nullptr;
+    float4 *t_zip_hi = nullptr, *t_zip_lo = nullptr;
     // Mixed path: fp16 planes of K * 2^k_exp, [n_pad][n_pad], zero padded
     void *Kr16 = nullptr, *Ki16 = nullptr;
     int k_exp = 0;
@@ -188,6 +193,8 @@ namespace tpf {
 tpf_status upload_network(tpf_handle *h);
 // Upload K, W and the fp16 planes of K on first use by a dense solve.
 tpf_status ensure_dense(tpf_handle *h);
+// Upload (alpha != null, host [3][n]) or drop the ZIP coefficients.
+tpf_status set_zip(tpf_handle *h, const double *alpha);
 void free_device(tpf_handle *h);
 // Ensure workspaces for `cols` columns: kind 0 = FP64 path, 1 = mixed path, 2 = per-column state only.
 enum WorkspaceKind : int { kWsFp64 = 0, kWsMixed = 1, kWsState = 2 };

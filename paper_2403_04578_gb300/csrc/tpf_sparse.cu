@@ -50,6 +50,7 @@ struct TreeWork {
     c2 vs_dd;
     const int *col, *end, *par, *ecnt, *ends;
     const float4 *z;
+    const float4 *zip_hi, *zip_lo;  // ZIP coefficients (alpha_P, alpha_I, alpha_Z, 0) per slot, or null
     const void *S;       // complex128 or, with s32, complex64 [T][n]
     const void *V0;      // given start, same type as V_out
     void *V_out;         // complex128 or, with v32, complex64 [T][n]; may be null
@@ -97,6 +98,24 @@ __device__ __forceinline__ float2 delta_current_fast(float2 v, float2 d, float2 
     const float2 q = make_float2(vp.x * v.x - vp.y * v.y, vp.x * v.y + vp.y * v.x);
     const float inv = __fdividef(1.0f, q.x * q.x + q.y * q.y);
     return make_float2(-(w.x * q.x + w.y * q.y) * inv, (w.y * q.x - w.x * q.y) * inv);
+}
+
+// Demand current of Eq. 3 with ZIP loads, i_d = alpha_P conj(s / v) + alpha_I conj(s) +
+// alpha_Z conj(s) v, and its change when v moves from v to v + d (the constant-current part
+// cancels, the constant-impedance part is linear).  al = (alpha_P, alpha_I, alpha_Z, -).
+template <bool kZip>
+__device__ __forceinline__ float2 demand_current(float2 v, float2 s, float4 al) {
+    const float2 c = current_fast(v, s);
+    if (!kZip) return c;
+    const float2 cs_v = make_float2(s.x * v.x + s.y * v.y, s.x * v.y - s.y * v.x);  // conj(s) v
+    return make_float2(al.x * c.x + al.y * s.x + al.z * cs_v.x, al.x * c.y - al.y * s.y + al.z * cs_v.y);
+}
+template <bool kZip>
+__device__ __forceinline__ float2 demand_change(float2 v, float2 d, float2 s, float4 al) {
+    const float2 c = delta_current_fast(v, d, s);
+    if (!kZip) return c;
+    const float2 cs_d = make_float2(s.x * d.x + s.y * d.y, s.x * d.y - s.y * d.x);  // conj(s) d
+    return make_float2(al.x * c.x + al.z * cs_d.x, al.x * c.y + al.z * cs_d.y);
 }
 
 // Exclusive scan over the threads of the block (thread order) of one complex FP32 value.
@@ -195,10 +214,10 @@ __device__ __forceinline__ int slot_of(int p, int th) {
 // The loops run over shared memory only and are not unrolled: the anchor runs once or twice per
 // column and its code stays small; the unrolled staging in the kernel keeps the device-memory
 // loads in flight together.
-template <int kBPT>
+template <int kBPT, bool kZip>
 __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B, const short *s_end,
-                                        const short *s_ends, const int *ecnt, float4 *wtd, int tid, int th, int lane,
-                                        int warp) {
+                                        const short *s_ends, const float4 *Zs, const int *ecnt, float4 *wtd, int tid,
+                                        int th, int lane, int warp) {
     const int n = a.n, base = tid * kBPT;
     // Load currents at V_ref and their inclusive prefix sums.
     c2 run = {{0.0f, 0.0f}, {0.0f, 0.0f}};
@@ -207,7 +226,16 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
         const int q = base + j, s = j * th + tid;
         if (q < n) {
             const float4 sh = A[s], v = B[s];
-            run = cqadd(run, current_q(c2{{sh.x, v.z}, {sh.y, v.w}}, make_float2(v.x, v.y)));
+            const c2 Sd = {{sh.x, v.z}, {sh.y, v.w}};
+            c2 I = current_q(Sd, make_float2(v.x, v.y));
+            if (kZip) {
+                // alpha_P conj(s / v) + alpha_I conj(s) + alpha_Z conj(s) v with double-float alphas
+                const float4 ah = Zs[s], al = a.zip_lo[s];
+                const c2 cs = {Sd.re, qneg(Sd.im)};
+                I = cqadd(cqadd(cqmul(c2{{ah.x, al.x}, {0.0f, 0.0f}}, I), cqmul(c2{{ah.y, al.y}, {0.0f, 0.0f}}, cs)),
+                          cqmul(c2{{ah.z, al.z}, {0.0f, 0.0f}}, cqmul(cs, c2{{v.x, 0.0f}, {v.y, 0.0f}})));
+            }
+            run = cqadd(run, I);
             A[s] = pack(run);
         }
     }
@@ -249,7 +277,7 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
     return block_scan_dd(run, wtd, lane, warp);
 }
 
-template <int kBPT>
+template <int kBPT, bool kZip>
 __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant__ TreeArgs g) {
     extern __shared__ float4 tsm[];
     __shared__ int s_work;
@@ -271,7 +299,8 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
     float4 *const A = tsm;       // [ns] double-float prefix sums (anchor); float2 P and X in the sweeps
     float4 *const B = tsm + ns;  // [ns] V_ref (anchor input), x (anchor), then D = BFS(V_ref) - V_ref
     float4 *const C = tsm + 2 * ns;  // [ns] (S_hi, z_hi) of each position
-    short *const s_end = reinterpret_cast<short *>(tsm + 3 * ns);  // [ns] end of the subtree's range
+    float4 *const Zs = tsm + 3 * ns;  // [ns] ZIP coefficients (kZip only)
+    short *const s_end = reinterpret_cast<short *>(tsm + (kZip ? 4 : 3) * ns);  // [ns] end of the subtree's range
     short *const s_par = s_end + ns;                               // [ns] parent slot, -1 = the slack
     short *const s_ends = s_par + ns;  // [n_ends] slots of the positions whose range ends at a position
     float2 *P = reinterpret_cast<float2 *>(A);  // [ns] inclusive prefix sums of the load currents
@@ -329,6 +358,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
         }
         C[s] = make_float4(sh.x, sh.y, zh.x, zh.y);
         B[s] = make_float4(sl.x, sl.y, 0.0f, 0.0f);  // S_lo until the first anchor replaces it by D
+        if (kZip) Zs[s] = q < n ? a.zip_hi[s] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     __syncthreads();
     // A given start is anchored at once ("blind"), and anchored again when the step is small.
@@ -393,7 +423,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                 A[s] = make_float4(cs.x, cs.y, 0.0f, 0.0f);
                 B[s] = make_float4(re.h, im.h, slo.x, slo.y);
             }
-            const c2 off = anchor_dd<kBPT>(a, A, B, s_end, s_ends, ecnt, wtd, tid, th, lane, warp);
+            const c2 off = anchor_dd<kBPT, kZip>(a, A, B, s_end, s_ends, Zs, ecnt, wtd, tid, th, lane, warp);
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
                 const int q = base + j, s = j * th + tid;
@@ -418,7 +448,9 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
             for (int j = 0; j < kBPT; ++j) {
                 const float4 cs = C[j * th + tid];
                 const float2 sh = make_float2(cs.x, cs.y);
-                const float2 I = anchored ? delta_current_fast(vr[j], dl[j], sh) : current_fast(vr[j], sh);
+                const float4 al = kZip ? Zs[j * th + tid] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+                const float2 I = anchored ? demand_change<kZip>(vr[j], dl[j], sh, al)
+                                          : demand_current<kZip>(vr[j], sh, al);
                 run = add2(run, I);  // positions past n have S = 0 and add nothing
                 loc[j] = run;
             }
@@ -577,7 +609,8 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
         if (q < n) {
             const float4 cs = C[s];
             const float2 sh = make_float2(cs.x, cs.y);
-            float2 r = anchored ? delta_current_fast(vr[j], dl[j], sh) : current_fast(vr[j], sh);
+            const float4 al = kZip ? Zs[s] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+            float2 r = anchored ? demand_change<kZip>(vr[j], dl[j], sh, al) : demand_current<kZip>(vr[j], sh, al);
             r = sub2(r, J[s]);
             const int e = s_end[s];
             for (int k = q + 1; k < e;) {
@@ -650,31 +683,38 @@ TreeWork work_of(const tpf_handle *h) {
     w.ecnt = d.t_ecnt;
     w.ends = d.t_ends;
     w.z = d.t_z;
+    w.zip_hi = d.t_zip_hi;
+    w.zip_lo = d.t_zip_lo;
     w.v_min2 = 0.0f;
     w.v_max2 = std::numeric_limits<float>::infinity();
     return w;
 }
 
-size_t tree_smem(int threads, int bpt) {
+size_t tree_smem(int threads, int bpt, bool zip) {
     const size_t ns = (size_t)threads * bpt;
-    return 3 * ns * sizeof(float4) + sizeof(short) * 3 * ns;  // A, B, C; end, parent, ends (<= ns entries)
+    // A, B, C (and the ZIP coefficients); end, parent, ends (<= ns entries)
+    return (zip ? 4 : 3) * ns * sizeof(float4) + sizeof(short) * 3 * ns;
 }
 
-tpf_status launch_tree(int bpt, int threads, int64_t cols, const TreeArgs &g, cudaStream_t st) {
+template <int kBPT, bool kZip>
+cudaError_t launch_tree_t(int threads, int64_t cols, size_t smem, const TreeArgs &g, cudaStream_t st) {
+    cudaError_t e = cudaFuncSetAttribute(mx_tree<kBPT, kZip>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) mx_tree<kBPT, kZip><<<(unsigned)cols, threads, smem, st>>>(g);
+    return e;
+}
+
+tpf_status launch_tree(int bpt, int threads, bool zip, int64_t cols, const TreeArgs &g, cudaStream_t st) {
     if (cols <= 0) return TPF_OK;
     if (cols > 0x7fffffff) return TPF_EUNSUPPORTED;  // one block per column
-    const size_t smem = tree_smem(threads, bpt);
+    const size_t smem = tree_smem(threads, bpt, zip);
+    if (smem > 227 * 1024) return TPF_EUNSUPPORTED;
     cudaError_t e;
-    if (bpt == 8) {
-        e = cudaFuncSetAttribute(mx_tree<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) mx_tree<8><<<(unsigned)cols, threads, smem, st>>>(g);
-    } else if (bpt == 4) {
-        e = cudaFuncSetAttribute(mx_tree<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) mx_tree<4><<<(unsigned)cols, threads, smem, st>>>(g);
-    } else {
-        e = cudaFuncSetAttribute(mx_tree<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e == cudaSuccess) mx_tree<2><<<(unsigned)cols, threads, smem, st>>>(g);
-    }
+    if (bpt == 8)
+        e = zip ? launch_tree_t<8, true>(threads, cols, smem, g, st) : launch_tree_t<8, false>(threads, cols, smem, g, st);
+    else if (bpt == 4)
+        e = zip ? launch_tree_t<4, true>(threads, cols, smem, g, st) : launch_tree_t<4, false>(threads, cols, smem, g, st);
+    else
+        e = zip ? launch_tree_t<2, true>(threads, cols, smem, g, st) : launch_tree_t<2, false>(threads, cols, smem, g, st);
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return TPF_ECUDA;
     return TPF_OK;
 }
@@ -728,7 +768,7 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
     }
     KernelTimer timer(o.profile != 0, st);
     timer.begin(KernelTimer::kResidual);
-    rs = launch_tree(d.t_bpt, d.t_threads, T, g, st);
+    rs = launch_tree(d.t_bpt, d.t_threads, d.t_zip_hi != nullptr, T, g, st);
     timer.end();
     if (rs != TPF_OK) return rs;
     if (cudaMemcpyAsync(w.counters_host, w.counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -759,6 +799,8 @@ tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, co
     for (int f = 0; f < F; ++f) order[f] = f;
     std::sort(order.begin(), order.end(), [&](int x, int y) {
         const DeviceNet &a = hs[x]->dev, &b = hs[y]->dev;
+        const int za = a.t_zip_hi != nullptr, zb = b.t_zip_hi != nullptr;
+        if (za != zb) return za < zb;
         return a.t_bpt != b.t_bpt ? a.t_bpt < b.t_bpt : (a.t_threads != b.t_threads ? a.t_threads < b.t_threads : x < y);
     });
     std::vector<TreeWork> works(F);
@@ -792,7 +834,8 @@ tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, co
     for (int k = 0; k < F;) {
         int e = k + 1;
         while (e < F && hs[order[e]]->dev.t_bpt == hs[order[k]]->dev.t_bpt &&
-               hs[order[e]]->dev.t_threads == hs[order[k]]->dev.t_threads)
+               hs[order[e]]->dev.t_threads == hs[order[k]]->dev.t_threads &&
+               (hs[order[e]]->dev.t_zip_hi != nullptr) == (hs[order[k]]->dev.t_zip_hi != nullptr))
             ++e;
         int64_t c = 0;
         for (int i = k; i < e; ++i) {
@@ -814,7 +857,7 @@ tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, co
         g.works = dworks + gr.first;
         g.n_works = gr.second - gr.first;
         timer.begin(KernelTimer::kResidual);
-        rs = launch_tree(d.t_bpt, d.t_threads, cols, g, st);
+        rs = launch_tree(d.t_bpt, d.t_threads, d.t_zip_hi != nullptr, cols, g, st);
         timer.end();
         ++launches;
     }

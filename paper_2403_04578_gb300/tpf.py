@@ -22,7 +22,7 @@ START_FLAT, START_GIVEN = 0, 1
 # Every entry point declared in include/tpf.h.
 EXPORTS = (
     "tpf_default_opts", "tpf_strerror", "tpf_create", "tpf_destroy", "tpf_n_pq", "tpf_precompute_host",
-    "tpf_solve", "tpf_solve_host", "tpf_solve_ex", "tpf_solve_batch", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
+    "tpf_solve", "tpf_solve_host", "tpf_solve_ex", "tpf_solve_batch", "tpf_set_zip", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
     "tpf_mlp_create", "tpf_mlp_destroy", "tpf_mlp_param_count", "tpf_mlp_get_params", "tpf_mlp_set_params",
     "tpf_mlp_fit_normalization", "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients",
     "tpf_mlp_predict",
@@ -98,6 +98,8 @@ def lib(build_if_missing: bool = False):
     L.tpf_solve.restype = ctypes.c_int
     L.tpf_solve_host.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(Opts), vp]
     L.tpf_solve_host.restype = ctypes.c_int
+    L.tpf_set_zip.argtypes = [vp, vp]
+    L.tpf_set_zip.restype = ctypes.c_int
     L.tpf_solve_ex.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(Outputs), ctypes.POINTER(Opts), vp]
     L.tpf_solve_ex.restype = ctypes.c_int
     L.tpf_solve_batch.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Opts), vp,
@@ -228,6 +230,16 @@ class Feeder:
 
     def __exit__(self, *exc):
         self.close()
+
+    def set_zip(self, alpha=None):
+        """ZIP load coefficients (Eq. 3): alpha = [alpha_P, alpha_I, alpha_Z], each [n_pq] (or None)."""
+        if alpha is None:
+            st = lib().tpf_set_zip(self._h, None)
+        else:
+            a = np.ascontiguousarray(alpha, dtype=np.float64).reshape(3, self.n_pq)
+            st = lib().tpf_set_zip(self._h, ctypes.c_void_p(a.ctypes.data))
+        if st != OK:
+            raise TpfError(st, "tpf_set_zip")
 
     def stats(self) -> dict:
         s = Stats()

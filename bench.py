@@ -247,7 +247,9 @@ def learned_start_leg(args, stream):
     n_train, n_eval = 100_000, args.columns
     S_tr = torch.from_numpy(G.load_tensor(f, n_train, args.seed + 100)).to(dev)
     V_tr, _, _, st = fd.solve(S_tr, precision="mixed", tol=args.tol)
-    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=1024, seed=args.seed)
+    # Buffers for 16,384-column batches: training steps use 1,024 columns, inference the full width
+    # (fewer, larger launches).
+    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=16384, seed=args.seed)
     net.fit_normalization(S_tr, V_tr)
     B = 1024
     steps_per_epoch = n_train // B

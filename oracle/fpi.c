@@ -285,3 +285,32 @@ void orc_mismatch_zip(int n_bus, const cplx *Y, int slack, double vs_re, double 
     }
     free(full);
 }
+
+/* Admittance matrix of Eq. 1 for a polyphase network, node index b*phases + p
+ * for bus b and phase p.  Branch e joins from[e] and to[e] with the phases x phases series impedance
+ * matrix Z_e (row-major, z + e*phases*phases); its admittance Y_e = Z_e^{-1} adds to the two
+ * diagonal blocks and subtracts from the two off-diagonal blocks.  Returns 0, or 1 for a bus index
+ * out of range, 2 for a singular branch matrix. */
+int orc_build_ybus_poly(int n_bus, int n_branch, int phases, const int *from, const int *to, const cplx *z,
+                        cplx *Y)
+{
+    const int ph = phases, N = n_bus * phases;
+    memset(Y, 0, sizeof(cplx) * (size_t)N * N);
+    cplx *Ye = (cplx *)malloc(sizeof(cplx) * (size_t)ph * ph);
+    for (int e = 0; e < n_branch; ++e) {
+        const int a = from[e], b = to[e];
+        if (a < 0 || b < 0 || a >= n_bus || b >= n_bus || a == b) { free(Ye); return 1; }
+        memcpy(Ye, z + (size_t)e * ph * ph, sizeof(cplx) * (size_t)ph * ph);
+        if (orc_invert(ph, Ye)) { free(Ye); return 2; }
+        for (int p = 0; p < ph; ++p)
+            for (int q = 0; q < ph; ++q) {
+                const cplx y = Ye[p * ph + q];
+                Y[(size_t)(a * ph + p) * N + a * ph + q] += y;
+                Y[(size_t)(b * ph + p) * N + b * ph + q] += y;
+                Y[(size_t)(a * ph + p) * N + b * ph + q] -= y;
+                Y[(size_t)(b * ph + p) * N + a * ph + q] -= y;
+            }
+    }
+    free(Ye);
+    return 0;
+}

@@ -71,6 +71,8 @@ def lib():
             L.orc_mismatch.argtypes = [ctypes.c_int, _c128p, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _i32p,
                                        ctypes.c_long, _c128p, _c128p, _f64p]
             L.orc_mismatch.restype = None
+            L.orc_build_ybus_poly.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p, _i32p, _c128p, _c128p]
+            L.orc_build_ybus_poly.restype = ctypes.c_int
             L.orc_fpi_zip.argtypes = [ctypes.c_int, _c128p, ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                       _i32p, _f64p, ctypes.c_long, _c128p, ctypes.c_void_p, ctypes.c_double, ctypes.c_int,
                                       _c128p, _i32p, _f64p, ctypes.c_int]
@@ -168,6 +170,48 @@ def mismatch_zip(Y: np.ndarray, slack: int, vs: complex, pq, alpha, S: np.ndarra
     lib().orc_mismatch_zip(Y.shape[0], np.ascontiguousarray(Y), int(slack), *_cd(vs), pq.shape[0], pq, alpha,
                            S.shape[0], S, V, out)
     return out
+
+
+class PolyCase:
+    """A polyphase feeder for the oracle (Eq. 1 with phases > 1): nodes are (bus, phase), index
+    b*phases + p; the demand unknowns are ordered bus-major over pq (i*phases + p), the slack
+    bus's phases hold vs[0..phases).  K = -Y_dd^{-1} by Gauss-Jordan, W = K Y_ds v_s, and the
+    fixed-point iteration of Algorithm 1 (orc_fpi) are the single-phase ones on this index space."""
+
+    def __init__(self, n_bus, from_bus, to_bus, z_blocks, phases, slack=0, vs=None, pq=None):
+        self.n_bus, self.phases, self.slack = int(n_bus), int(phases), int(slack)
+        ph = self.phases
+        z = np.ascontiguousarray(z_blocks, np.complex128).reshape(len(from_bus), ph, ph)
+        N = self.n_bus * ph
+        self.Y = np.zeros((N, N), dtype=np.complex128)
+        rc = lib().orc_build_ybus_poly(self.n_bus, len(from_bus), ph, np.ascontiguousarray(from_bus, np.int32),
+                                       np.ascontiguousarray(to_bus, np.int32), z, self.Y)
+        if rc:
+            raise ValueError(f"bad branch data (code {rc})")
+        pq = np.asarray(pq if pq is not None else [b for b in range(self.n_bus) if b != slack], np.int64)
+        self.vs = np.asarray(vs if vs is not None else np.exp(-2j * np.pi * np.arange(ph) / ph), np.complex128)
+        self.nodes = (pq[:, None] * ph + np.arange(ph)[None, :]).reshape(-1)
+        self.snodes = self.slack * ph + np.arange(ph)
+        Ydd = np.ascontiguousarray(self.Y[np.ix_(self.nodes, self.nodes)])
+        self.K = Ydd.copy()
+        if lib().orc_invert(self.K.shape[0], self.K):
+            raise np.linalg.LinAlgError("Y_dd is singular")
+        self.K = -self.K
+        self.W = self.K @ (self.Y[np.ix_(self.nodes, self.snodes)] @ self.vs)
+
+    def solve(self, S, V0=None, tol=1e-13, max_iter=100, threads=0):
+        """S: [T][n_pq*phases] loads (bus-major)."""
+        return fpi(self.K, self.W, S, V0, tol, max_iter, threads)
+
+    def mismatch(self, S, V):
+        """max over demand nodes of |V_i conj((Y v)_i) + S_i| per column."""
+        S = np.atleast_2d(np.asarray(S, np.complex128))
+        V = np.atleast_2d(np.asarray(V, np.complex128))
+        full = np.empty((V.shape[0], self.Y.shape[0]), dtype=np.complex128)
+        full[:, self.snodes] = self.vs
+        full[:, self.nodes] = V
+        acc = full @ self.Y.T
+        return np.abs(V * np.conj(acc[:, self.nodes]) + S).max(axis=1)
 
 
 class Case:

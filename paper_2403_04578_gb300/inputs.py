@@ -317,3 +317,76 @@ def scenario_tensor_device(feeder: Feeder, n_scen: int, n_hours: int, seed: int,
         ppv = pv_kw[s][None, :] / S_BASE_KW * bell[:, None]
         out[s] = torch.complex(pl - ppv, pl * tanphi[None, :])
     return out
+
+
+# ---------------------------------------------------------------------------------------------
+# Polyphase feeders (Eq. 1 with phases > 1): the radial recipe above with a phases x phases
+# series impedance per branch and per-phase loads.
+# ---------------------------------------------------------------------------------------------
+
+_TAG_POLY = 6
+
+
+@dataclasses.dataclass
+class PolyFeeder:
+    """A radial polyphase feeder: per branch a [phases][phases] impedance block (pu)."""
+
+    n_bus: int
+    phases: int
+    from_bus: np.ndarray  # int32 [n_branch]
+    to_bus: np.ndarray  # int32 [n_branch]
+    z_blocks: np.ndarray  # complex128 [n_branch][phases][phases]
+    base_kw: np.ndarray  # float64 [n_bus][phases], 0 at the slack
+    pf: np.ndarray  # float64 [n_bus][phases]
+    load_scale: float
+    seed: int
+    slack: int = 0
+
+    @property
+    def n_pq(self) -> int:
+        return self.n_bus - 1
+
+    @property
+    def pq_bus(self) -> np.ndarray:
+        return np.arange(1, self.n_bus, dtype=np.int32)
+
+    @property
+    def v0(self) -> np.ndarray:
+        """Balanced source (1, a^2, a) for three phases, a = exp(j 2 pi / 3)."""
+        return np.exp(-2j * np.pi * np.arange(self.phases) / self.phases)
+
+
+def make_feeder_poly(n_bus: int, seed: int, phases: int = 3, mutual: float = 0.4, unbalance: float = 0.2,
+                     max_depth: int = 12, load_factor: float = 0.8) -> PolyFeeder:
+    """Polyphase version of ``make_feeder``: the same tree and line draws; each branch gets the
+    self impedance z + z_m and the mutual impedance z_m = mutual * (0.2 r + j x) between phases
+    (so its positive-sequence impedance is the single-phase z); each phase of each bus carries
+    the single-phase base load times a share in [1 - unbalance, 1 + unbalance] (mean 1), scaled by
+    ``load_factor`` times the single-phase feeder's load scale."""
+    f = make_feeder(n_bus, seed, max_depth=max_depth)
+    z = f.z_pu
+    zm = mutual * (0.2 * z.real + 1j * z.imag)
+    blocks = np.empty((z.shape[0], phases, phases), dtype=np.complex128)
+    blocks[:] = zm[:, None, None]
+    for p in range(phases):
+        blocks[:, p, p] = z + zm
+    rng = _rng(seed, _TAG_POLY)
+    share = rng.uniform(1.0 - unbalance, 1.0 + unbalance, (n_bus, phases))
+    share /= share.mean(axis=1, keepdims=True)
+    base = f.base_kw[:, None] * share
+    base[0] = 0.0
+    pf = np.repeat(f.pf[:, None], phases, axis=1)
+    return PolyFeeder(n_bus=n_bus, phases=phases, from_bus=f.from_bus, to_bus=f.to_bus, z_blocks=blocks,
+                      base_kw=base, pf=pf, load_scale=f.load_scale * load_factor, seed=seed)
+
+
+def load_tensor_poly(feeder: PolyFeeder, T: int, seed: int, step_minutes: float = 1.0) -> np.ndarray:
+    """Loads S[T][n_pq][phases] (complex128, consumption), the recipe of ``load_tensor`` per phase."""
+    ph = feeder.phases
+    base = feeder.base_kw[1:]
+    tanphi = np.tan(np.arccos(feeder.pf[1:]))
+    hours = (np.arange(T) * step_minutes / 60.0) % 24.0
+    rng = _rng(seed, _TAG_LOAD, 1 << 20)
+    noise = np.exp(0.2 * rng.standard_normal((T, feeder.n_pq, ph)))
+    p = feeder.load_scale * base[None] / S_BASE_KW * daily_shape(hours)[:, None, None] * noise
+    return (p + 1j * p * tanphi[None]).astype(np.complex128)

@@ -130,6 +130,24 @@ tpf_status tpf_create(int n_bus, int n_branch, const int32_t *from, const int32_
                       const int32_t *pq_bus, tpf_handle **out);
 
 /* Release a handle and every device buffer it owns (NULL is a no-op). */
+/*
+ * Build a polyphase feeder (Eq. 1 with phases > 1): every bus has `phases` nodes; branch e joins
+ * from[e] and to[e] through the phases x phases series impedance block z_pu[e] (pu, row-major,
+ * interleaved complex: z_pu[2*((e*phases + p)*phases + q)] + j z_pu[... + 1]; self impedances on
+ * the diagonal, mutual impedances off it; each block must be invertible); the slack bus holds
+ * v0[p] (interleaved complex, [phases]).  The unknowns are the phases x n_pq demand-node voltages,
+ * ordered bus-major: unknown i*phases + p is phase p of demand bus pq_bus[i], so load and voltage
+ * tensors are [T][n_pq][phases] (tpf_n_pq returns n_pq * phases).  Loads are wye-connected: the
+ * current drawn at a node is conj(S / V) of that node.  Served by TPF_PREC_FP64 (any connected
+ * network, K = -Y_dd^{-1} by LU) and, for radial networks with phases == 3, TPF_METHOD_SPARSE
+ * (the tree substitution with phases x phases branch blocks); the dense mixed path and ZIP
+ * coefficients return TPF_EUNSUPPORTED.  phases == 1 is tpf_create.  Errors as tpf_create, and
+ * TPF_EINVAL for phases outside 1..3 or a singular branch block.
+ */
+tpf_status tpf_create_poly(int n_bus, int n_branch, int phases, const int32_t *from, const int32_t *to,
+                           const double *z_pu, int slack, const double *v0, int n_pq, const int32_t *pq_bus,
+                           tpf_handle **out);
+
 void tpf_destroy(tpf_handle *h);
 
 /* Number of demand buses of a handle (the column length of every tensor). */

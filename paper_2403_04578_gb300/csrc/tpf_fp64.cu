@@ -68,7 +68,20 @@ tpf_status upload_network(tpf_handle *h) {
         TPF_CK(cudaMemcpy(d.y2f, y2.data(), sizeof(float4) * nnz, cudaMemcpyHostToDevice));
     }
     d.radial = net.radial;
-    if (net.radial) {
+    d.phases = net.phases;
+    d.nbp = n / net.phases;
+    if (net.phases > 1) {
+        // Polyphase: the unknown each neighbour-list entry's admittance multiplies, and v_s.
+        TPF_CK(cudaMalloc(&d.csr_self, sizeof(int) * (nnz > 0 ? nnz : 1)));
+        if (nnz > 0) TPF_CK(cudaMemcpy(d.csr_self, net.csr_self.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice));
+    }
+    TPF_CK(cudaMalloc(&d.vs64, sizeof(double) * 2 * net.phases));
+    {
+        std::vector<double> vs(net.vs);
+        if (vs.empty()) vs = {net.vs_re, net.vs_im};
+        TPF_CK(cudaMemcpy(d.vs64, vs.data(), sizeof(double) * 2 * net.phases, cudaMemcpyHostToDevice));
+    }
+    if (net.radial && net.phases == 1) {
         const int nch = net.ch_ptr[n];
         std::vector<float2> yp(n);
         for (int i = 0; i < n; ++i) yp[i] = make_float2((float)net.ypar[2 * i], (float)net.ypar[2 * i + 1]);
@@ -80,6 +93,8 @@ tpf_status upload_network(tpf_handle *h) {
         TPF_CK(cudaMemcpy(d.ch_ptr, net.ch_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
         if (nch > 0) TPF_CK(cudaMemcpy(d.ch, net.ch.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
         TPF_CK(cudaMemcpy(d.ypar, yp.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    }
+    if (net.radial) {
         // Slot-ordered depth-first arrays of the sparse formulation.
         const int bpt = tree_bpt(n), th = bpt ? tree_threads(n, bpt) : 0;
         d.t_threads = th;
@@ -87,8 +102,12 @@ tpf_status upload_network(tpf_handle *h) {
         if (th > 0) {
             const int ns = th * bpt;
             auto slot = [th, bpt](int q) { return (q % bpt) * th + q / bpt; };
+            const int ph = net.phases, nb = n / ph;
             std::vector<int> col(ns, -1), end(ns, 0), par(ns, -1), ecnt(ns, 0), ends;
             std::vector<float4> z(ns, make_float4(0.f, 0.f, 0.f, 0.f));
+            // Polyphase: row p of the branch's impedance (double-float) and admittance per slot.
+            std::vector<float4> zrow(ph > 1 ? (size_t)ns * ph : 0, make_float4(0.f, 0.f, 0.f, 0.f));
+            std::vector<float2> yrow(ph > 1 ? (size_t)ns * ph : 0, make_float2(0.f, 0.f));
             std::vector<int> pos_par(n, -1);  // parent position of each position
             for (int q = 0; q < n; ++q)
                 for (int c = q + 1; c < net.dfs_end[q]; c = net.dfs_end[c]) pos_par[c] = q;
@@ -98,12 +117,25 @@ tpf_status upload_network(tpf_handle *h) {
                 col[s] = net.dfs_col[q];
                 end[s] = net.dfs_end[q];
                 par[s] = pos_par[q] < 0 ? -1 : slot(pos_par[q]);
-                if ((int)ends.size() > 0xffff || cnt > 0x7fff) fits = false;
-                ecnt[s] = (int)ends.size() | (cnt << 16);
+                if ((int)ends.size() > 0xffff || cnt > 0x3fff) fits = false;
+                // start | count << 16 | phase << 30
+                ecnt[s] = (int)ends.size() | (cnt << 16) | ((q / nb) << 30);
                 for (int k = net.dfs_eptr[q]; k < net.dfs_eptr[q + 1]; ++k) ends.push_back(slot(net.dfs_ends[k]));
-                const double zr = net.dfs_z[2 * q], zi = net.dfs_z[2 * q + 1];
-                const float zrh = (float)zr, zih = (float)zi;
-                z[s] = make_float4(zrh, zih, (float)(zr - (double)zrh), (float)(zi - (double)zih));
+                auto dd = [](double re, double im) {
+                    const float rh = (float)re, ih = (float)im;
+                    return make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+                };
+                if (ph == 1) {
+                    z[s] = dd(net.dfs_z[2 * q], net.dfs_z[2 * q + 1]);
+                } else {
+                    for (int pp = 0; pp < ph; ++pp) {
+                        const size_t k = (size_t)q * ph + pp;
+                        zrow[(size_t)s * ph + pp] = dd(net.dfs_zrow[2 * k], net.dfs_zrow[2 * k + 1]);
+                        yrow[(size_t)s * ph + pp] = make_float2((float)net.dfs_yrow[2 * k], (float)net.dfs_yrow[2 * k + 1]);
+                    }
+                    const float4 zz = zrow[(size_t)s * ph + q / nb];  // the own-phase entry, for z-only uses
+                    z[s] = zz;
+                }
             }
             d.t_n_ends = (int)ends.size();
             if (ends.empty()) ends.push_back(0);
@@ -115,7 +147,8 @@ tpf_status upload_network(tpf_handle *h) {
             if (!fits) {
                 d.t_threads = 0;
             } else if (!up(&d.t_col, col) || !up(&d.t_end, end) || !up(&d.t_par, par) || !up(&d.t_ecnt, ecnt) ||
-                       !up(&d.t_ends, ends) || !up(&d.t_z, z)) {
+                       !up(&d.t_ends, ends) || !up(&d.t_z, z) ||
+                       (ph > 1 && (!up(&d.t_zrow, zrow) || !up(&d.t_yrow, yrow)))) {
                 cudaGetLastError();
                 return TPF_ECUDA;
             }
@@ -161,6 +194,7 @@ tpf_status ensure_dense(tpf_handle *h) {
 
 tpf_status set_zip(tpf_handle *h, const double *alpha) {
     DeviceNet &d = h->dev;
+    if (d.phases > 1) return alpha ? TPF_EUNSUPPORTED : TPF_OK;
     cudaFree(d.zip64);
     cudaFree(d.t_zip_hi);
     cudaFree(d.t_zip_lo);
@@ -200,6 +234,7 @@ void free_device(tpf_handle *h) {
     cudaFree(d.par); cudaFree(d.ch_ptr); cudaFree(d.ch); cudaFree(d.ypar);
     cudaFree(d.t_col); cudaFree(d.t_end); cudaFree(d.t_par); cudaFree(d.t_ecnt); cudaFree(d.t_ends); cudaFree(d.t_z);
     cudaFree(d.zip64); cudaFree(d.t_zip_hi); cudaFree(d.t_zip_lo);
+    cudaFree(d.csr_self); cudaFree(d.vs64); cudaFree(d.t_zrow); cudaFree(d.t_yrow);
     d = DeviceNet();
     Workspace &w = h->ws;
     cudaFree(w.Vhi); cudaFree(w.Vlo); cudaFree(w.Shi); cudaFree(w.Slo); cudaFree(w.Rr16); cudaFree(w.Ri16);
@@ -420,7 +455,8 @@ __global__ void f64_decide(int64_t T, double tol, int max_iter, int *flags, int 
 __global__ void f64_finish(int64_t T, int n, int max_iter, const int *__restrict__ flags,
                            const int *__restrict__ it_state, double2 *V, const double2 *__restrict__ Valt,
                            const double2 *__restrict__ S, const int *__restrict__ row_ptr,
-                           const int *__restrict__ nbr, const double2 *__restrict__ y, double2 vs,
+                           const int *__restrict__ nbr, const double2 *__restrict__ y,
+                           const int *__restrict__ self, const double2 *__restrict__ vs,
                            const double *__restrict__ zip, int32_t *iters_out, double *mismatch_out) {
     const int lane = threadIdx.x & 31;
     const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -438,9 +474,11 @@ __global__ void f64_finish(int64_t T, int n, int max_iter, const int *__restrict
         double2 vi = v[i];
         double2 acc = make_double2(0.0, 0.0);
         for (int e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            // (Y v)_i = sum_e y_e (v[self_e] - v[nbr_e]); nbr_e = -1 - p names slack phase p
             int j = nbr[e];
-            double2 vj = j >= 0 ? v[j] : vs;
-            double2 d = make_double2(vi.x - vj.x, vi.y - vj.y);
+            double2 vj = j >= 0 ? v[j] : vs[-1 - j];
+            double2 vself = self ? v[self[e]] : vi;
+            double2 d = make_double2(vself.x - vj.x, vself.y - vj.y);
             double2 ye = y[e];
             acc.x += ye.x * d.x - ye.y * d.y;
             acc.y += ye.x * d.y + ye.y * d.x;
@@ -518,7 +556,7 @@ tpf_status solve_fp64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t 
     timer.begin(KernelTimer::kOther);
     f64_finish<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(
         T, n, o.max_iter, w.flags, w.iters, (double2 *)V, (const double2 *)w.Valt, (const double2 *)S,
-        h->dev.row_ptr, h->dev.nbr, (const double2 *)h->dev.y64, make_double2(h->net.vs_re, h->net.vs_im),
+        h->dev.row_ptr, h->dev.nbr, (const double2 *)h->dev.y64, h->dev.csr_self, (const double2 *)h->dev.vs64,
         h->dev.zip64, iters, mismatch);
     timer.end();
     ++launches;
@@ -625,7 +663,7 @@ extern "C" tpf_status tpf_solve_fp64_noalloc(int n, const void *K_dev, const voi
     }
     f64_finish<<<(unsigned)((T * 32 + 255) / 256), 256, 0, st>>>(T, n, max_iter, flags, iters, (double2 *)V_dev,
                                                                  Valt, (const double2 *)S_dev, nullptr, nullptr,
-                                                                 nullptr, make_double2(0.0, 0.0), nullptr, iters_dev,
+                                                                 nullptr, nullptr, nullptr, nullptr, iters_dev,
                                                                  nullptr);
     TPF_CK(cudaGetLastError());
     TPF_CK(cudaMemcpyAsync(host_counters, counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st));

@@ -200,19 +200,6 @@ tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int
         std::vector<int> fill_e(net.dfs_eptr.begin(), net.dfs_eptr.end() - 1);
         for (int q = 0; q < n; ++q)
             if (net.dfs_end[q] < n) net.dfs_ends[fill_e[net.dfs_end[q]]++] = q;
-        // Neighbour lists in depth-first positions (-1 = the slack), for the residual at the end.
-        net.dfs_rp.assign(n + 1, 0);
-        net.dfs_nbr.clear();
-        net.dfs_y.clear();
-        for (int q = 0; q < n; ++q) {
-            const int b = net.pq[net.dfs_col[q]];
-            for (auto &nb : adj[b]) {
-                net.dfs_nbr.push_back(nb.first == slack ? -1 : posdfs[nb.first]);
-                net.dfs_y.push_back(nb.second.real());
-                net.dfs_y.push_back(nb.second.imag());
-            }
-            net.dfs_rp[q + 1] = (int)net.dfs_nbr.size();
-        }
     }
     // Neighbour lists in column positions.
     net.row_ptr.assign(n + 1, 0);
@@ -231,8 +218,168 @@ tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int
     return TPF_OK;
 }
 
+tpf_status build_network_poly(int n_bus, int n_branch, int phases, const int32_t *from, const int32_t *to,
+                              const double *z_pu, int slack, const double *v0, int n_pq, const int32_t *pq_bus,
+                              Network &net) {
+    const int ph = phases;
+    if (ph < 2 || ph > 3) return TPF_EINVAL;
+    if (n_bus < 2 || n_branch < n_bus - 1 || n_pq != n_bus - 1) return TPF_EINVAL;
+    if (!from || !to || !z_pu || !pq_bus || !v0) return TPF_EINVAL;
+    if (slack < 0 || slack >= n_bus) return TPF_EINVAL;
+    for (int p = 0; p < 2 * ph; ++p)
+        if (!std::isfinite(v0[p])) return TPF_EINVAL;
+    net = Network();
+    net.n_bus = n_bus;
+    net.phases = ph;
+    net.n_pq = n_pq * ph;
+    net.slack = slack;
+    net.vs.assign(v0, v0 + 2 * ph);
+    net.vs_re = v0[0];
+    net.vs_im = v0[1];
+    net.pos.assign(n_bus, -2);
+    net.pos[slack] = -1;
+    net.pq.assign(pq_bus, pq_bus + n_pq);
+    for (int i = 0; i < n_pq; ++i) {
+        const int b = pq_bus[i];
+        if (b < 0 || b >= n_bus || net.pos[b] != -2) return TPF_EINVAL;
+        net.pos[b] = i;
+    }
+    // Branch admittance blocks Y_e = Z_e^{-1} (phases x phases, by LU).
+    std::vector<std::vector<std::pair<int, int>>> adj(n_bus);  // (other bus, branch)
+    std::vector<cplx> Yb((size_t)n_branch * ph * ph), Zb((size_t)n_branch * ph * ph);
+    for (int e = 0; e < n_branch; ++e) {
+        const int a = from[e], b = to[e];
+        if (a < 0 || b < 0 || a >= n_bus || b >= n_bus || a == b) return TPF_EINVAL;
+        std::vector<cplx> blk(ph * ph);
+        for (int k = 0; k < ph * ph; ++k) {
+            const cplx z(z_pu[2 * ((size_t)e * ph * ph + k)], z_pu[2 * ((size_t)e * ph * ph + k) + 1]);
+            if (!std::isfinite(z.real()) || !std::isfinite(z.imag())) return TPF_EINVAL;
+            blk[k] = z;
+            Zb[(size_t)e * ph * ph + k] = z;
+        }
+        if (!lu_inverse(ph, blk)) return TPF_EINVAL;  // a singular branch matrix
+        std::copy(blk.begin(), blk.end(), Yb.begin() + (size_t)e * ph * ph);
+        adj[a].push_back({b, e});
+        adj[b].push_back({a, e});
+    }
+    std::vector<int> parent(n_bus, -2), pbranch(n_bus, -1), order;
+    order.reserve(n_bus);
+    parent[slack] = -1;
+    order.push_back(slack);
+    for (size_t q = 0; q < order.size(); ++q) {
+        const int u = order[q];
+        for (auto &nb : adj[u])
+            if (parent[nb.first] == -2) {
+                parent[nb.first] = u;
+                pbranch[nb.first] = nb.second;
+                order.push_back(nb.first);
+            }
+    }
+    if ((int)order.size() != n_bus) return TPF_ESINGULAR;
+    net.radial = (n_branch == n_bus - 1);
+    // W = v_s phase by phase: with every bus at v_s no branch carries current, so
+    // Y_dd (1 x v_s) + Y_ds v_s = 0 without shunts.
+    net.W.assign(2 * (size_t)net.n_pq, 0.0);
+    for (int i = 0; i < n_pq; ++i)
+        for (int p = 0; p < ph; ++p) {
+            net.W[2 * ((size_t)i * ph + p)] = v0[2 * p];
+            net.W[2 * ((size_t)i * ph + p) + 1] = v0[2 * p + 1];
+        }
+    // Neighbour lists over unknowns u = i*ph + p: for each branch at bus i and each phase p',
+    // y = Y_e[p][p'] multiplying (v_{i,p'} - v_{j,p'}).
+    net.row_ptr.assign(net.n_pq + 1, 0);
+    net.nbr.clear();
+    net.y.clear();
+    net.csr_self.clear();
+    for (int i = 0; i < n_pq; ++i) {
+        const int b = net.pq[i];
+        for (int p = 0; p < ph; ++p) {
+            for (auto &nb : adj[b]) {
+                const cplx *Y = &Yb[(size_t)nb.second * ph * ph];
+                for (int pp = 0; pp < ph; ++pp) {
+                    net.csr_self.push_back(i * ph + pp);
+                    net.nbr.push_back(nb.first == slack ? -1 - pp : net.pos[nb.first] * ph + pp);
+                    net.y.push_back(Y[p * ph + pp].real());
+                    net.y.push_back(Y[p * ph + pp].imag());
+                }
+            }
+            net.row_ptr[i * ph + p + 1] = (int)net.nbr.size();
+        }
+    }
+    if (net.radial) {
+        // Depth-first positions of the demand buses, repeated per phase block (position
+        // p*n_pq + q); a block's first position also closes the previous block's open path.
+        std::vector<int> posdfs(n_bus, -1), dcol;
+        std::vector<std::vector<int>> kids(n_bus);
+        for (size_t q = 1; q < order.size(); ++q) kids[parent[order[q]]].push_back(order[q]);
+        std::vector<int> stack;
+        for (auto it = kids[slack].rbegin(); it != kids[slack].rend(); ++it) stack.push_back(*it);
+        while (!stack.empty()) {
+            const int u = stack.back();
+            stack.pop_back();
+            posdfs[u] = (int)dcol.size();
+            dcol.push_back(u);
+            for (auto it = kids[u].rbegin(); it != kids[u].rend(); ++it) stack.push_back(*it);
+        }
+        std::vector<int> size(n_bus, 1);
+        for (size_t q = order.size() - 1; q >= 1; --q) size[parent[order[q]]] += size[order[q]];
+        const int n = n_pq, P = n * ph;
+        net.dfs_col.assign(P, 0);
+        net.dfs_end.assign(P, 0);
+        net.dfs_zrow.assign(2 * (size_t)P * ph, 0.0);
+        net.dfs_yrow.assign(2 * (size_t)P * ph, 0.0);
+        std::vector<std::vector<int>> ends_at(P + 1);
+        std::vector<int> open_last;  // positions of block 0 whose range ends at n
+        for (int q = 0; q < n; ++q) {
+            const int b = dcol[q], e = pbranch[b];
+            for (int p = 0; p < ph; ++p) {
+                const int Q = p * n + q;
+                net.dfs_col[Q] = net.pos[b] * ph + p;
+                net.dfs_end[Q] = p * n + q + size[b];
+                if (q + size[b] < n) ends_at[p * n + q + size[b]].push_back(Q);
+                for (int pp = 0; pp < ph; ++pp) {
+                    const cplx z = Zb[(size_t)e * ph * ph + p * ph + pp], y = Yb[(size_t)e * ph * ph + p * ph + pp];
+                    net.dfs_zrow[2 * ((size_t)Q * ph + pp)] = z.real();
+                    net.dfs_zrow[2 * ((size_t)Q * ph + pp) + 1] = z.imag();
+                    net.dfs_yrow[2 * ((size_t)Q * ph + pp)] = y.real();
+                    net.dfs_yrow[2 * ((size_t)Q * ph + pp) + 1] = y.imag();
+                }
+            }
+            if (q + size[b] == n) open_last.push_back(q);
+        }
+        for (int p = 1; p < ph; ++p)
+            for (int q : open_last) ends_at[p * n].push_back((p - 1) * n + q);
+        net.dfs_eptr.assign(P + 1, 0);
+        net.dfs_ends.clear();
+        for (int Q = 0; Q < P; ++Q) {
+            for (int b : ends_at[Q]) net.dfs_ends.push_back(b);
+            net.dfs_eptr[Q + 1] = (int)net.dfs_ends.size();
+        }
+    }
+    return TPF_OK;
+}
+
 void compute_dense(Network &net) {
-    if (!net.K.empty() || !net.radial) return;
+    if (!net.K.empty()) return;
+    if (net.phases > 1) {
+        // Y_dd over unknowns from the neighbour lists (diagonal blocks from csr_self), then K by LU.
+        const int N = net.n_pq;
+        std::vector<cplx> Ydd((size_t)N * N, 0.0);
+        for (int u = 0; u < N; ++u)
+            for (int e = net.row_ptr[u]; e < net.row_ptr[u + 1]; ++e) {
+                const cplx y(net.y[2 * e], net.y[2 * e + 1]);
+                Ydd[(size_t)u * N + net.csr_self[e]] += y;
+                if (net.nbr[e] >= 0) Ydd[(size_t)u * N + net.nbr[e]] -= y;
+            }
+        if (!lu_inverse(N, Ydd)) return;  // connected networks are nonsingular
+        net.K.assign((size_t)2 * N * N, 0.0);
+        for (size_t k = 0; k < (size_t)N * N; ++k) {
+            net.K[2 * k] = -Ydd[k].real();
+            net.K[2 * k + 1] = -Ydd[k].imag();
+        }
+        return;
+    }
+    if (!net.radial) return;
     // (Y_dd^{-1})_{ij} = impedance of the branches shared by the slack-to-i and slack-to-j paths.
     // For each j: mark j's ancestors with their path impedance, then a top-down pass gives every
     // bus the path impedance of its deepest marked ancestor.
@@ -322,6 +469,33 @@ tpf_status tpf_create(int n_bus, int n_branch, const int32_t *from, const int32_
     tpf_status st;
     try {
         st = tpf::build_network(n_bus, n_branch, from, to, z_pu, slack, v0_re, v0_im, n_pq, pq_bus, h->net);
+    } catch (const std::bad_alloc &) {
+        st = TPF_ENOMEM;
+    }
+    if (st == TPF_OK) st = tpf::upload_network(h);
+    if (st != TPF_OK) {
+        tpf::free_device(h);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return TPF_OK;
+}
+
+tpf_status tpf_create_poly(int n_bus, int n_branch, int phases, const int32_t *from, const int32_t *to,
+                           const double *z_pu, int slack, const double *v0, int n_pq, const int32_t *pq_bus,
+                           tpf_handle **out) {
+    if (!out) return TPF_EINVAL;
+    *out = nullptr;
+    if (phases == 1) {
+        if (!v0) return TPF_EINVAL;
+        return tpf_create(n_bus, n_branch, from, to, z_pu, slack, v0[0], v0[1], n_pq, pq_bus, out);
+    }
+    tpf_handle *h = new (std::nothrow) tpf_handle();
+    if (!h) return TPF_ENOMEM;
+    tpf_status st;
+    try {
+        st = tpf::build_network_poly(n_bus, n_branch, phases, from, to, z_pu, slack, v0, n_pq, pq_bus, h->net);
     } catch (const std::bad_alloc &) {
         st = TPF_ENOMEM;
     }

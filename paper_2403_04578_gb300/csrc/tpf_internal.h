@@ -54,14 +54,28 @@ struct Network {
     std::vector<double> ypar;     // complex [n_pq]
     // Radial networks only, in depth-first preorder positions q of the demand buses: the column
     // of each position, the end of its subtree's position range [q, dfs_end[q]), the impedance of
-    // the branch to its parent, the positions whose range ends at q (CSR dfs_eptr / dfs_ends) and
-    // the neighbour lists (CSR dfs_rp / dfs_nbr, -1 = the slack, admittances dfs_y).
-    std::vector<int> dfs_col, dfs_end, dfs_eptr, dfs_ends, dfs_rp, dfs_nbr;
-    std::vector<double> dfs_z, dfs_y;  // complex
+    // the branch to its parent and the positions whose range ends at q (CSR dfs_eptr / dfs_ends).
+    // Polyphase networks repeat the positions once per phase (position p n_bus_pq + q for phase p)
+    // and carry, per position, the row p of the branch's impedance and admittance blocks.
+    std::vector<int> dfs_col, dfs_end, dfs_eptr, dfs_ends;
+    std::vector<double> dfs_z;  // complex [positions]
+    // Polyphase networks (phases > 1): unknowns are (demand bus, phase), index i*phases + p; the
+    // slack holds vs[p]; the neighbour lists above run over unknowns and also name, per entry, the
+    // unknown of the own bus whose voltage the entry's admittance multiplies (csr_self), so that
+    // (Y v)_u = sum_e y_e (v[csr_self_e] - v[nbr_e]) with nbr_e = -1 - p' for slack phase p'.
+    int phases = 1;
+    std::vector<double> vs;       // complex [phases]
+    std::vector<int> csr_self;    // [nnz] (phases > 1)
+    std::vector<double> dfs_zrow, dfs_yrow;  // complex [positions][phases]
 };
 
 // Build K (radial networks build it here, on first need; a no-op when it exists).
 void compute_dense(Network &net);
+
+// The same for a polyphase network (phases x phases branch blocks, interleaved complex).
+tpf_status build_network_poly(int n_bus, int n_branch, int phases, const int32_t *from, const int32_t *to,
+                              const double *z_pu, int slack, const double *v0, int n_pq, const int32_t *pq_bus,
+                              Network &net);
 
 // Build the network arrays; returns TPF_OK or the status to report.
 tpf_status build_network(int n_bus, int n_branch, const int32_t *from, const int32_t *to,
@@ -96,6 +110,15 @@ struct DeviceNet {
     // per slot, high and low words (sparse path).
     double *zip64 = nullptr;
     float4 *t_zip_hi = nullptr, *t_zip_lo = nullptr;
+    // Polyphase networks: phases, demand buses per phase block (n = nbp * phases unknowns), the
+    // unknown each neighbour-list entry's admittance multiplies (null when phases == 1), v_s per
+    // phase (complex, also for phases == 1), and per slot the rows p of the branch's impedance
+    // (double-float, [ns][phases]) and admittance (FP32) blocks.
+    int phases = 1, nbp = 0;
+    int *csr_self = nullptr;
+    double *vs64 = nullptr;
+    float4 *t_zrow = nullptr;
+    float2 *t_yrow = nullptr;
     // Mixed path: fp16 planes of K * 2^k_exp, [n_pad][n_pad], zero padded
     void *Kr16 = nullptr, *Ki16 = nullptr;
     int k_exp = 0;

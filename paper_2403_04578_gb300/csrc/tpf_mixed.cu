@@ -111,7 +111,8 @@ tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t
                        const tpf_opts &o, cudaStream_t st) {
     const int n = h->dev.n, n_pad = h->dev.n_pad;
     if (n_pad > 2048) return TPF_EUNSUPPORTED;
-    if (h->dev.zip64) return TPF_EUNSUPPORTED;  // ZIP loads: sparse formulation or FP64 path
+    if (h->dev.zip64) return TPF_EUNSUPPORTED;    // ZIP loads: sparse formulation or FP64 path
+    if (h->dev.phases > 1) return TPF_EUNSUPPORTED;  // polyphase: sparse formulation or FP64 path
     tpf_status rs = ensure_dense(h);
     if (rs != TPF_OK) return rs;
     rs = ensure_workspace(h, T, kWsMixed);

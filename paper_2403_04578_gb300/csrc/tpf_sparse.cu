@@ -51,6 +51,13 @@ struct TreeWork {
     const int *col, *end, *par, *ecnt, *ends;
     const float4 *z;
     const float4 *zip_hi, *zip_lo;  // ZIP coefficients (alpha_P, alpha_I, alpha_Z, 0) per slot, or null
+    // Polyphase: positions per phase block, v_s per phase, per slot the rows of the branch's
+    // impedance (double-float) and admittance blocks, [slot][phase].
+    int nbp;
+    float2 vs_fp[3];
+    c2 vs_ddp[3];
+    const float4 *zrow;
+    const float2 *yrow;
     const void *S;       // complex128 or, with s32, complex64 [T][n]
     const void *V0;      // given start, same type as V_out
     void *V_out;         // complex128 or, with v32, complex64 [T][n]; may be null
@@ -75,6 +82,10 @@ struct TreeArgs {
     float tol2, switch_tol, switch_tol2;  // squared tolerances compare with squared steps
     int *counters;                        // [5] largest per-column sweep count, [6] largest anchor count
 };
+
+// Packed per-position word: ends-list start (bits 0-15), count (16-29), phase (30-31).
+__device__ __forceinline__ int ends_cnt(int ec) { return (int)(((unsigned)ec >> 16) & 0x3fffu); }
+__device__ __forceinline__ int phase_of(int ec) { return (int)((unsigned)ec >> 30); }
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -214,7 +225,7 @@ __device__ __forceinline__ int slot_of(int p, int th) {
 // The loops run over shared memory only and are not unrolled: the anchor runs once or twice per
 // column and its code stays small; the unrolled staging in the kernel keeps the device-memory
 // loads in flight together.
-template <int kBPT, bool kZip>
+template <int kBPT, bool kZip, int kPh>
 __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B, const short *s_end,
                                         const short *s_ends, const float4 *Zs, const int *ecnt, float4 *wtd, int tid,
                                         int th, int lane, int warp) {
@@ -244,18 +255,32 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
     for (int j = 0; j < kBPT; ++j) {
         const int s = j * th + tid;
         A[s] = pack(cqadd(off, unpack(A[s])));
-        B[s] = a.z[s];  // (re_hi, im_hi, re_lo, im_lo)
+        if (kPh == 1) B[s] = a.z[s];  // (re_hi, im_hi, re_lo, im_lo)
     }
     __syncthreads();
-    // Branch terms x_q = z_q (P[end_q - 1] - P[q - 1]).
+    // Branch terms x_q = z_q (P[end_q - 1] - P[q - 1]); polyphase: x = sum over phases p' of
+    // Z[p][p'] L_{p'}, the subtree sums of the same buses in the other phase blocks.
 #pragma unroll 1
     for (int j = 0; j < kBPT; ++j) {
         const int q = base + j, s = j * th + tid;
         if (q < n) {
-            c2 L = unpack(A[slot_of<kBPT>(s_end[s] - 1, th)]);
-            if (q > 0) L = cqsub(L, unpack(A[j ? s - th : (kBPT - 1) * th + tid - 1]));
-            const float4 zq = B[s];
-            B[s] = pack(cqmul(c2{{zq.x, zq.z}, {zq.y, zq.w}}, L));
+            if (kPh == 1) {
+                c2 L = unpack(A[slot_of<kBPT>(s_end[s] - 1, th)]);
+                if (q > 0) L = cqsub(L, unpack(A[j ? s - th : (kBPT - 1) * th + tid - 1]));
+                const float4 zq = B[s];
+                B[s] = pack(cqmul(c2{{zq.x, zq.z}, {zq.y, zq.w}}, L));
+            } else {
+                const int p = q / a.nbp, qb = q - p * a.nbp, eb = s_end[s] - p * a.nbp;
+                c2 x = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+                for (int pp = 0; pp < kPh; ++pp) {
+                    c2 L = unpack(A[slot_of<kBPT>(pp * a.nbp + eb - 1, th)]);
+                    const int prev = pp * a.nbp + qb - 1;
+                    if (prev >= 0) L = cqsub(L, unpack(A[slot_of<kBPT>(prev, th)]));
+                    const float4 zq = a.zrow[(size_t)s * kPh + pp];
+                    x = cqadd(x, cqmul(c2{{zq.x, zq.z}, {zq.y, zq.w}}, L));
+                }
+                B[s] = pack(x);
+            }
         }
     }
     __syncthreads();
@@ -269,7 +294,7 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
         if (q < n) {
             const int ec = __float_as_int(A[s].x);
             c2 e = unpack(B[s]);
-            for (int k = 0; k < (ec >> 16); ++k) e = cqsub(e, unpack(B[s_ends[(ec & 0xffff) + k]]));
+            for (int k = 0; k < ends_cnt(ec); ++k) e = cqsub(e, unpack(B[s_ends[(ec & 0xffff) + k]]));
             run = cqadd(run, e);
             A[s] = pack(run);
         }
@@ -277,7 +302,7 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
     return block_scan_dd(run, wtd, lane, warp);
 }
 
-template <int kBPT, bool kZip>
+template <int kBPT, bool kZip, int kPh>
 __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant__ TreeArgs g) {
     extern __shared__ float4 tsm[];
     __shared__ int s_work;
@@ -300,7 +325,10 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
     float4 *const B = tsm + ns;  // [ns] V_ref (anchor input), x (anchor), then D = BFS(V_ref) - V_ref
     float4 *const C = tsm + 2 * ns;  // [ns] (S_hi, z_hi) of each position
     float4 *const Zs = tsm + 3 * ns;  // [ns] ZIP coefficients (kZip only)
-    short *const s_end = reinterpret_cast<short *>(tsm + (kZip ? 4 : 3) * ns);  // [ns] end of the subtree's range
+    // [ns][kPh] rows of the branch impedance blocks (polyphase only)
+    float2 *const ZR = reinterpret_cast<float2 *>(tsm + (kZip ? 4 : 3) * ns);
+    short *const s_end = reinterpret_cast<short *>(reinterpret_cast<char *>(ZR) +
+                                                   (kPh > 1 ? sizeof(float2) * kPh * ns : 0));  // [ns] end of the subtree's range
     short *const s_par = s_end + ns;                               // [ns] parent slot, -1 = the slack
     short *const s_ends = s_par + ns;  // [n_ends] slots of the positions whose range ends at a position
     float2 *P = reinterpret_cast<float2 *>(A);  // [ns] inclusive prefix sums of the load currents
@@ -359,6 +387,13 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
         C[s] = make_float4(sh.x, sh.y, zh.x, zh.y);
         B[s] = make_float4(sl.x, sl.y, 0.0f, 0.0f);  // S_lo until the first anchor replaces it by D
         if (kZip) Zs[s] = q < n ? a.zip_hi[s] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (kPh > 1) {
+#pragma unroll
+            for (int pp = 0; pp < kPh; ++pp) {
+                const float4 zq = q < n ? a.zrow[(size_t)s * kPh + pp] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                ZR[s * kPh + pp] = make_float2(zq.x, zq.y);
+            }
+        }
     }
     __syncthreads();
     // A given start is anchored at once ("blind"), and anchored again when the step is small.
@@ -423,13 +458,14 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                 A[s] = make_float4(cs.x, cs.y, 0.0f, 0.0f);
                 B[s] = make_float4(re.h, im.h, slo.x, slo.y);
             }
-            const c2 off = anchor_dd<kBPT, kZip>(a, A, B, s_end, s_ends, Zs, ecnt, wtd, tid, th, lane, warp);
+            const c2 off = anchor_dd<kBPT, kZip, kPh>(a, A, B, s_end, s_ends, Zs, ecnt, wtd, tid, th, lane, warp);
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
                 const int q = base + j, s = j * th + tid;
                 if (q < n) {
                     const c2 ps = cqadd(off, unpack(A[s]));
-                    const c2 D = cqsub(cqsub(a.vs_dd, c2{{vr[j].x, 0.0f}, {vr[j].y, 0.0f}}), ps);
+                    const c2 vs = kPh == 1 ? a.vs_dd : a.vs_ddp[phase_of(ecnt[j])];
+                    const c2 D = cqsub(cqsub(vs, c2{{vr[j].x, 0.0f}, {vr[j].y, 0.0f}}), ps);
                     B[s] = make_float4(D.re.h, D.im.h, D.re.l, D.im.l);
                 }
             }
@@ -485,10 +521,22 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                 const int q = base + j, s = j * th + tid;
                 float2 xq = make_float2(0.0f, 0.0f);  // positions past n contribute nothing
                 if (q < n) {
-                    float2 L = P[slot_of<kBPT>(s_end[s] - 1, th)];
-                    if (q > 0) L = sub2(L, P[j ? s - th : (kBPT - 1) * th + tid - 1]);
-                    const float4 cs = C[s];
-                    xq = cmul2(make_float2(cs.z, cs.w), L);
+                    if (kPh == 1) {
+                        float2 L = P[slot_of<kBPT>(s_end[s] - 1, th)];
+                        if (q > 0) L = sub2(L, P[j ? s - th : (kBPT - 1) * th + tid - 1]);
+                        const float4 cs = C[s];
+                        xq = cmul2(make_float2(cs.z, cs.w), L);
+                    } else {
+                        // x = sum over phases p' of Z[p][p'] L_{p'}
+                        const int p = phase_of(ecnt[j]), qb = q - p * a.nbp, eb = s_end[s] - p * a.nbp;
+#pragma unroll
+                        for (int pp = 0; pp < kPh; ++pp) {
+                            float2 L = P[slot_of<kBPT>(pp * a.nbp + eb - 1, th)];
+                            const int prev = pp * a.nbp + qb - 1;
+                            if (prev >= 0) L = sub2(L, P[slot_of<kBPT>(prev, th)]);
+                            xq = add2(xq, cmul2(ZR[s * kPh + pp], L));
+                        }
+                    }
                 }
                 X[s] = xq;
             }
@@ -500,7 +548,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
                 const int s = j * th + tid;
-                const int st = ecnt[j] & 0xffff, cnt = ecnt[j] >> 16;
+                const int st = ecnt[j] & 0xffff, cnt = ends_cnt(ecnt[j]);
                 float2 e = X[s];
 #pragma unroll
                 for (int k = 0; k < kGather; ++k)
@@ -511,7 +559,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
             if (longer) {
 #pragma unroll
                 for (int j = 0; j < kBPT; ++j) {
-                    const int st = ecnt[j] & 0xffff, cnt = ecnt[j] >> 16;
+                    const int st = ecnt[j] & 0xffff, cnt = ends_cnt(ecnt[j]);
                     for (int k = kGather; k < cnt; ++k) loc[j] = sub2(loc[j], X[s_ends[st + k]]);
                 }
             }
@@ -537,7 +585,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                     dl[j] = nd;
                     mx.y = fmaxf(mx.y, abs2(nd));
                 } else {
-                    const float2 nv = sub2(a.vs_f, ps);
+                    const float2 nv = sub2(kPh == 1 ? a.vs_f : a.vs_fp[phase_of(ecnt[j])], ps);
                     step = sub2(nv, vr[j]);
                     vr[j] = nv;
                 }
@@ -593,11 +641,27 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
         const int q = base + j, s = j * th + tid;
         if (q < n) {
             const int p = s_par[s];
-            const float4 cs = C[s];
-            const float2 zq = make_float2(cs.z, cs.w);
-            const float inv = __fdividef(1.0f, abs2(zq));
-            const float2 yk = make_float2(zq.x * inv, -zq.y * inv);
-            J[s] = cmul2(yk, sub2(p >= 0 ? X[p] : x_slack, xs[j]));
+            if (kPh == 1) {
+                const float4 cs = C[s];
+                const float2 zq = make_float2(cs.z, cs.w);
+                const float inv = __fdividef(1.0f, abs2(zq));
+                const float2 yk = make_float2(zq.x * inv, -zq.y * inv);
+                J[s] = cmul2(yk, sub2(p >= 0 ? X[p] : x_slack, xs[j]));
+            } else {
+                // J = sum over phases p' of Y[ph][p'] (x_parent,p' - x_q,p'): the parent's
+                // position comes back from its slot (position = (slot % th) kBPT + slot / th).
+                const int ph = phase_of(ecnt[j]), qb = q - ph * a.nbp;
+                const int pb = p >= 0 ? (p % th) * kBPT + p / th - ph * a.nbp : -1;
+                float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+                for (int pp = 0; pp < kPh; ++pp) {
+                    const float2 xp = pb >= 0 ? X[slot_of<kBPT>(pp * a.nbp + pb, th)]
+                                              : (anchored ? make_float2(0.0f, 0.0f) : a.vs_fp[pp]);
+                    const float2 xq = X[slot_of<kBPT>(pp * a.nbp + qb, th)];
+                    acc = add2(acc, cmul2(a.yrow[(size_t)s * kPh + pp], sub2(xp, xq)));
+                }
+                J[s] = acc;
+            }
         }
     }
     __syncthreads();
@@ -685,36 +749,57 @@ TreeWork work_of(const tpf_handle *h) {
     w.z = d.t_z;
     w.zip_hi = d.t_zip_hi;
     w.zip_lo = d.t_zip_lo;
+    w.nbp = d.nbp;
+    w.zrow = d.t_zrow;
+    w.yrow = d.t_yrow;
+    for (int p = 0; p < 3; ++p) {
+        const bool has = p < h->net.phases && (int)h->net.vs.size() >= 2 * (p + 1);
+        const double re = has ? h->net.vs[2 * p] : h->net.vs_re, im = has ? h->net.vs[2 * p + 1] : h->net.vs_im;
+        const float fr = (float)re, fi = (float)im;
+        w.vs_fp[p] = make_float2(fr, fi);
+        w.vs_ddp[p] = c2{{fr, (float)(re - (double)fr)}, {fi, (float)(im - (double)fi)}};
+    }
     w.v_min2 = 0.0f;
     w.v_max2 = std::numeric_limits<float>::infinity();
     return w;
 }
 
-size_t tree_smem(int threads, int bpt, bool zip) {
+size_t tree_smem(int threads, int bpt, bool zip, int phases) {
     const size_t ns = (size_t)threads * bpt;
-    // A, B, C (and the ZIP coefficients); end, parent, ends (<= ns entries)
-    return (zip ? 4 : 3) * ns * sizeof(float4) + sizeof(short) * 3 * ns;
+    // A, B, C (and the ZIP coefficients); the impedance rows (polyphase); end, parent, ends
+    return (zip ? 4 : 3) * ns * sizeof(float4) + (phases > 1 ? ns * phases * sizeof(float2) : 0) +
+           sizeof(short) * 3 * ns;
 }
 
-template <int kBPT, bool kZip>
+template <int kBPT, bool kZip, int kPh>
 cudaError_t launch_tree_t(int threads, int64_t cols, size_t smem, const TreeArgs &g, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(mx_tree<kBPT, kZip>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) mx_tree<kBPT, kZip><<<(unsigned)cols, threads, smem, st>>>(g);
+    cudaError_t e =
+        cudaFuncSetAttribute(mx_tree<kBPT, kZip, kPh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) mx_tree<kBPT, kZip, kPh><<<(unsigned)cols, threads, smem, st>>>(g);
     return e;
 }
 
-tpf_status launch_tree(int bpt, int threads, bool zip, int64_t cols, const TreeArgs &g, cudaStream_t st) {
+template <int kBPT>
+cudaError_t launch_tree_b(int threads, bool zip, int phases, int64_t cols, size_t smem, const TreeArgs &g,
+                          cudaStream_t st) {
+    if (phases == 3) return launch_tree_t<kBPT, false, 3>(threads, cols, smem, g, st);
+    return zip ? launch_tree_t<kBPT, true, 1>(threads, cols, smem, g, st)
+               : launch_tree_t<kBPT, false, 1>(threads, cols, smem, g, st);
+}
+
+tpf_status launch_tree(int bpt, int threads, bool zip, int phases, int64_t cols, const TreeArgs &g, cudaStream_t st) {
     if (cols <= 0) return TPF_OK;
     if (cols > 0x7fffffff) return TPF_EUNSUPPORTED;  // one block per column
-    const size_t smem = tree_smem(threads, bpt, zip);
+    if (phases != 1 && (phases != 3 || zip)) return TPF_EUNSUPPORTED;
+    const size_t smem = tree_smem(threads, bpt, zip, phases);
     if (smem > 227 * 1024) return TPF_EUNSUPPORTED;
     cudaError_t e;
     if (bpt == 8)
-        e = zip ? launch_tree_t<8, true>(threads, cols, smem, g, st) : launch_tree_t<8, false>(threads, cols, smem, g, st);
+        e = launch_tree_b<8>(threads, zip, phases, cols, smem, g, st);
     else if (bpt == 4)
-        e = zip ? launch_tree_t<4, true>(threads, cols, smem, g, st) : launch_tree_t<4, false>(threads, cols, smem, g, st);
+        e = launch_tree_b<4>(threads, zip, phases, cols, smem, g, st);
     else
-        e = zip ? launch_tree_t<2, true>(threads, cols, smem, g, st) : launch_tree_t<2, false>(threads, cols, smem, g, st);
+        e = launch_tree_b<2>(threads, zip, phases, cols, smem, g, st);
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return TPF_ECUDA;
     return TPF_OK;
 }
@@ -768,7 +853,7 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
     }
     KernelTimer timer(o.profile != 0, st);
     timer.begin(KernelTimer::kResidual);
-    rs = launch_tree(d.t_bpt, d.t_threads, d.t_zip_hi != nullptr, T, g, st);
+    rs = launch_tree(d.t_bpt, d.t_threads, d.t_zip_hi != nullptr, d.phases, T, g, st);
     timer.end();
     if (rs != TPF_OK) return rs;
     if (cudaMemcpyAsync(w.counters_host, w.counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -801,6 +886,7 @@ tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, co
         const DeviceNet &a = hs[x]->dev, &b = hs[y]->dev;
         const int za = a.t_zip_hi != nullptr, zb = b.t_zip_hi != nullptr;
         if (za != zb) return za < zb;
+        if (a.phases != b.phases) return a.phases < b.phases;
         return a.t_bpt != b.t_bpt ? a.t_bpt < b.t_bpt : (a.t_threads != b.t_threads ? a.t_threads < b.t_threads : x < y);
     });
     std::vector<TreeWork> works(F);
@@ -835,7 +921,8 @@ tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, co
         int e = k + 1;
         while (e < F && hs[order[e]]->dev.t_bpt == hs[order[k]]->dev.t_bpt &&
                hs[order[e]]->dev.t_threads == hs[order[k]]->dev.t_threads &&
-               (hs[order[e]]->dev.t_zip_hi != nullptr) == (hs[order[k]]->dev.t_zip_hi != nullptr))
+               (hs[order[e]]->dev.t_zip_hi != nullptr) == (hs[order[k]]->dev.t_zip_hi != nullptr) &&
+               hs[order[e]]->dev.phases == hs[order[k]]->dev.phases)
             ++e;
         int64_t c = 0;
         for (int i = k; i < e; ++i) {
@@ -857,7 +944,7 @@ tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, co
         g.works = dworks + gr.first;
         g.n_works = gr.second - gr.first;
         timer.begin(KernelTimer::kResidual);
-        rs = launch_tree(d.t_bpt, d.t_threads, d.t_zip_hi != nullptr, cols, g, st);
+        rs = launch_tree(d.t_bpt, d.t_threads, d.t_zip_hi != nullptr, d.phases, cols, g, st);
         timer.end();
         ++launches;
     }

@@ -21,7 +21,7 @@ START_FLAT, START_GIVEN = 0, 1
 
 # Every entry point declared in include/tpf.h.
 EXPORTS = (
-    "tpf_default_opts", "tpf_strerror", "tpf_create", "tpf_destroy", "tpf_n_pq", "tpf_precompute_host",
+    "tpf_default_opts", "tpf_strerror", "tpf_create", "tpf_create_poly", "tpf_destroy", "tpf_n_pq", "tpf_precompute_host",
     "tpf_solve", "tpf_solve_host", "tpf_solve_ex", "tpf_solve_batch", "tpf_set_zip", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
     "tpf_mlp_create", "tpf_mlp_destroy", "tpf_mlp_param_count", "tpf_mlp_get_params", "tpf_mlp_set_params",
     "tpf_mlp_fit_normalization", "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients",
@@ -98,6 +98,9 @@ def lib(build_if_missing: bool = False):
     L.tpf_solve.restype = ctypes.c_int
     L.tpf_solve_host.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(Opts), vp]
     L.tpf_solve_host.restype = ctypes.c_int
+    L.tpf_create_poly.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p, i32p, f64p, ctypes.c_int, f64p,
+                                  ctypes.c_int, i32p, ctypes.POINTER(vp)]
+    L.tpf_create_poly.restype = ctypes.c_int
     L.tpf_set_zip.argtypes = [vp, vp]
     L.tpf_set_zip.restype = ctypes.c_int
     L.tpf_solve_ex.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(Outputs), ctypes.POINTER(Opts), vp]
@@ -208,6 +211,31 @@ class Feeder:
             raise TpfError(st, "tpf_create")
         self._h = h
         self.n_pq = lib().tpf_n_pq(h)
+
+    @classmethod
+    def poly(cls, n_bus, from_bus, to_bus, z_blocks, phases=3, slack=0, v0=None, pq_bus=None):
+        """A polyphase feeder: z_blocks [n_branch][phases][phases] complex; v0 [phases]."""
+        if pq_bus is None:
+            pq_bus = [b for b in range(n_bus) if b != slack]
+        if v0 is None:
+            v0 = np.exp(-2j * np.pi * np.arange(phases) / phases)
+        fa, fp = _i32(from_bus)
+        ta, tp = _i32(to_bus)
+        z = np.ascontiguousarray(np.asarray(z_blocks, np.complex128).reshape(len(fa), phases, phases))
+        zr = z.view(np.float64).reshape(-1)
+        v = np.ascontiguousarray(np.asarray(v0, np.complex128)).view(np.float64)
+        pa, pp = _i32(pq_bus)
+        h = ctypes.c_void_p()
+        st = lib().tpf_create_poly(int(n_bus), len(fa), int(phases), fp, tp,
+                                   zr.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), int(slack),
+                                   v.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), len(pa), pp, ctypes.byref(h))
+        if st != OK:
+            raise TpfError(st, "tpf_create_poly")
+        obj = cls.__new__(cls)
+        obj._h = h
+        obj.n_pq = lib().tpf_n_pq(h)
+        obj._keep = (fa, ta, z, v, pa)
+        return obj
 
     @classmethod
     def from_inputs(cls, f):

@@ -25,6 +25,7 @@ Reported on one JSON line (rank 0):
               voltage-band statistics
   feeder_batch  config-4 leg: 4,096 feeders of 20-2,000 buses in one tpf_solve_batch call
   zip_loads   the headline workload with ZIP loads (Eq. 3) on the sparse formulation
+  three_phase a 500-bus three-phase feeder (Eq. 1 with phases = 3) on the sparse formulation
   clocks      nvidia-smi samples taken during the timed region
 
 ``--impl reference`` times the CPU oracle as the reference arm on the same workload.
@@ -79,6 +80,9 @@ def parse_args():
     p.add_argument("--method", choices=["sparse", "dense"], default="sparse")
     p.add_argument("--no-scenario", action="store_true")
     p.add_argument("--no-zip", action="store_true")
+    p.add_argument("--no-poly", action="store_true")
+    p.add_argument("--poly-buses", type=int, default=500)
+    p.add_argument("--poly-columns", type=int, default=65536)
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--scen", type=int, default=200)
     p.add_argument("--hours", type=int, default=8760)
@@ -429,6 +433,42 @@ def batch_leg(args, stream, check):
     return out
 
 
+def poly_leg(args, stream, check):
+    """Three-phase feeder: 500 buses (1,497 unknowns), mutual coupling 0.4, per-phase unbalance
+    +-20 %, 65,536 one-minute columns, sparse formulation; the oracle checks sampled columns."""
+    import torch
+
+    from paper_2403_04578_gb300 import inputs as G
+    from paper_2403_04578_gb300 import tpf
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    pf = G.make_feeder_poly(args.poly_buses, args.seed)
+    T = args.poly_columns
+    S = torch.from_numpy(G.load_tensor_poly(pf, T, args.seed).reshape(T, -1)).to(dev)
+    fd = tpf.Feeder.poly(pf.n_bus, pf.from_bus, pf.to_bus, pf.z_blocks, 3, v0=pf.v0)
+    V = torch.empty_like(S)
+    it = torch.empty(T, dtype=torch.int32, device=dev)
+    mm = torch.empty(T, dtype=torch.float64, device=dev)
+    ms = timed_device(lambda: fd.solve(S, V, it, mm, precision="mixed", method="sparse", start="flat", tol=args.tol),
+                      max(1, min(args.steps, 3)), stream)
+    out = {"workload": f"{args.poly_buses}-bus three-phase feeder ({3 * pf.n_pq} unknowns), {T:,} one-minute "
+                       "columns, sparse formulation",
+           "value": T / (ms / 1e3), "unit": "PF/s", "ms_per_step": ms, "converged": fd.stats()["converged"],
+           "mean_sweeps": float(it.abs().float().mean().item())}
+    if check:
+        from oracle import oracle as O
+
+        pc = O.PolyCase(pf.n_bus, pf.from_bus, pf.to_bus, pf.z_blocks, 3, vs=pf.v0)
+        cc = torch.linspace(0, T - 1, min(args.check_columns, 1024, T), device=dev).long()
+        Vt, _, _ = pc.solve(S[cc].cpu().numpy(), tol=1e-13, threads=os.cpu_count() or 1)
+        out["max_abs_err_pu"] = float(np.abs(V[cc].cpu().numpy() - Vt).max())
+        out["columns_checked"] = int(cc.numel())
+    fd.close()
+    del S, V
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_reference(args, world, rank):
     """The reference arm: the CPU oracle (FP64, all host cores) on bounded samples of the workload."""
     if rank != 0:
@@ -692,6 +732,8 @@ def main():
         line["scenario_tensor"] = scenario_leg(args, stream, rank == 0 and not args.no_cpu)
     if not args.no_batch:
         line["feeder_batch"] = batch_leg(args, stream, rank == 0 and not args.no_cpu)
+    if not args.no_poly:
+        line["three_phase"] = poly_leg(args, stream, rank == 0 and not args.no_cpu)
     if rank == 0:
         print(json.dumps(line), flush=True)
     fd.close()

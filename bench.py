@@ -81,6 +81,7 @@ def parse_args():
     p.add_argument("--no-scenario", action="store_true")
     p.add_argument("--no-zip", action="store_true")
     p.add_argument("--no-poly", action="store_true")
+    p.add_argument("--ref-seconds", type=float, default=120.0, help="reference arm: seconds for all its steps")
     p.add_argument("--poly-buses", type=int, default=500)
     p.add_argument("--poly-columns", type=int, default=65536)
     p.add_argument("--no-batch", action="store_true")
@@ -479,7 +480,7 @@ def run_reference(args, world, rank):
     f, config = workload(args)
     threads = os.cpu_count() or 1
     case = O.Case.from_feeder(f)
-    budget = 120.0  # seconds for all warm-up and timed steps
+    budget = args.ref_seconds  # seconds for all warm-up and timed steps
     probe_T = G.CHUNK
     S = G.load_tensor(f, probe_T, args.seed)
     t0 = time.perf_counter()

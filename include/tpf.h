@@ -196,6 +196,17 @@ tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_
 tpf_status tpf_last_stats(const tpf_handle *h, tpf_stats *out);
 
 /*
+ * Autotune the sparse formulation's launch shape for this feeder: time the kernel with 2, 4 and 8
+ * demand buses per thread (the block sizes that follow from them) on the T columns of S_dev
+ * (device, complex128 [T][n_pq], a representative sample such as the first few thousand columns
+ * of a workload), flat start and opts' tolerances, and keep the fastest for every later sparse
+ * solve.  bpt_out (host, may be NULL) receives the choice.  Allocates a scratch V of T columns.
+ * TPF_EUNSUPPORTED for networks the sparse formulation does not take or opts->precision FP64.
+ */
+tpf_status tpf_autotune(tpf_handle *h, int64_t T, const void *S_dev, const tpf_opts *opts, int *bpt_out,
+                        void *stream);
+
+/*
  * ZIP loads (Eq. 3).  alpha is host memory [3][n_pq]: alpha_P, alpha_I and alpha_Z of every demand
  * bus (bus order of tpf_create), applied to every later solve on this handle:
  *

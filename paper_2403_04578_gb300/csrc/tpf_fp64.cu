@@ -40,63 +40,21 @@ __global__ void k_to_fp16(const double *__restrict__ K, int n, int n_pad, float 
 
 }  // namespace
 
-tpf_status upload_network(tpf_handle *h) {
-    int dev = 0;
-    TPF_CK(cudaGetDevice(&dev));
-    h->device = dev;
+// Slot-ordered depth-first arrays of the sparse formulation for blocks of tree_threads(n, bpt)
+// threads with bpt positions each (replacing any earlier layout; bpt 0 disables the sparse path).
+tpf_status layout_tree(tpf_handle *h, int bpt) {
     const Network &net = h->net;
     DeviceNet &d = h->dev;
     const int n = net.n_pq;
-    d.n = n;
-    d.n_pad = (int)round_up(n, kTileM);
-    const int nnz = net.row_ptr[n];
-    TPF_CK(cudaMalloc(&d.row_ptr, sizeof(int) * (n + 1)));
-    TPF_CK(cudaMalloc(&d.nbr, sizeof(int) * (nnz > 0 ? nnz : 1)));
-    TPF_CK(cudaMalloc(&d.y64, sizeof(double) * 2 * (nnz > 0 ? nnz : 1)));
-    TPF_CK(cudaMalloc(&d.y2f, sizeof(float4) * (nnz > 0 ? nnz : 1)));
-    TPF_CK(cudaMemcpy(d.row_ptr, net.row_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
-    if (nnz > 0) {
-        TPF_CK(cudaMemcpy(d.nbr, net.nbr.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice));
-        TPF_CK(cudaMemcpy(d.y64, net.y.data(), sizeof(double) * 2 * nnz, cudaMemcpyHostToDevice));
-        // Double-float split of each admittance: hi = fl(y), lo = fl(y - hi).
-        std::vector<float4> y2(nnz);
-        for (int k = 0; k < nnz; ++k) {
-            double re = net.y[2 * k], im = net.y[2 * k + 1];
-            float rh = (float)re, ih = (float)im;
-            y2[k] = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
-        }
-        TPF_CK(cudaMemcpy(d.y2f, y2.data(), sizeof(float4) * nnz, cudaMemcpyHostToDevice));
-    }
-    d.radial = net.radial;
-    d.phases = net.phases;
-    d.nbp = n / net.phases;
-    if (net.phases > 1) {
-        // Polyphase: the unknown each neighbour-list entry's admittance multiplies, and v_s.
-        TPF_CK(cudaMalloc(&d.csr_self, sizeof(int) * (nnz > 0 ? nnz : 1)));
-        if (nnz > 0) TPF_CK(cudaMemcpy(d.csr_self, net.csr_self.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice));
-    }
-    TPF_CK(cudaMalloc(&d.vs64, sizeof(double) * 2 * net.phases));
-    {
-        std::vector<double> vs(net.vs);
-        if (vs.empty()) vs = {net.vs_re, net.vs_im};
-        TPF_CK(cudaMemcpy(d.vs64, vs.data(), sizeof(double) * 2 * net.phases, cudaMemcpyHostToDevice));
-    }
-    if (net.radial && net.phases == 1) {
-        const int nch = net.ch_ptr[n];
-        std::vector<float2> yp(n);
-        for (int i = 0; i < n; ++i) yp[i] = make_float2((float)net.ypar[2 * i], (float)net.ypar[2 * i + 1]);
-        TPF_CK(cudaMalloc(&d.par, sizeof(int) * n));
-        TPF_CK(cudaMalloc(&d.ch_ptr, sizeof(int) * (n + 1)));
-        TPF_CK(cudaMalloc(&d.ch, sizeof(int) * (nch > 0 ? nch : 1)));
-        TPF_CK(cudaMalloc(&d.ypar, sizeof(float2) * n));
-        TPF_CK(cudaMemcpy(d.par, net.par.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
-        TPF_CK(cudaMemcpy(d.ch_ptr, net.ch_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
-        if (nch > 0) TPF_CK(cudaMemcpy(d.ch, net.ch.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
-        TPF_CK(cudaMemcpy(d.ypar, yp.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
-    }
+    cudaFree(d.t_col); cudaFree(d.t_end); cudaFree(d.t_par); cudaFree(d.t_ecnt); cudaFree(d.t_ends); cudaFree(d.t_z);
+    cudaFree(d.t_zrow); cudaFree(d.t_yrow);
+    d.t_col = d.t_end = d.t_par = d.t_ecnt = d.t_ends = nullptr;
+    d.t_z = d.t_zrow = nullptr;
+    d.t_yrow = nullptr;
+    d.t_threads = d.t_bpt = 0;
     if (net.radial) {
         // Slot-ordered depth-first arrays of the sparse formulation.
-        const int bpt = tree_bpt(n), th = bpt ? tree_threads(n, bpt) : 0;
+        const int th = bpt ? tree_threads(n, bpt) : 0;
         d.t_threads = th;
         d.t_bpt = bpt;
         if (th > 0) {
@@ -153,6 +111,67 @@ tpf_status upload_network(tpf_handle *h) {
                 return TPF_ECUDA;
             }
         }
+    }
+    return TPF_OK;
+}
+
+tpf_status upload_network(tpf_handle *h) {
+    int dev = 0;
+    TPF_CK(cudaGetDevice(&dev));
+    h->device = dev;
+    const Network &net = h->net;
+    DeviceNet &d = h->dev;
+    const int n = net.n_pq;
+    d.n = n;
+    d.n_pad = (int)round_up(n, kTileM);
+    const int nnz = net.row_ptr[n];
+    TPF_CK(cudaMalloc(&d.row_ptr, sizeof(int) * (n + 1)));
+    TPF_CK(cudaMalloc(&d.nbr, sizeof(int) * (nnz > 0 ? nnz : 1)));
+    TPF_CK(cudaMalloc(&d.y64, sizeof(double) * 2 * (nnz > 0 ? nnz : 1)));
+    TPF_CK(cudaMalloc(&d.y2f, sizeof(float4) * (nnz > 0 ? nnz : 1)));
+    TPF_CK(cudaMemcpy(d.row_ptr, net.row_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+    if (nnz > 0) {
+        TPF_CK(cudaMemcpy(d.nbr, net.nbr.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice));
+        TPF_CK(cudaMemcpy(d.y64, net.y.data(), sizeof(double) * 2 * nnz, cudaMemcpyHostToDevice));
+        // Double-float split of each admittance: hi = fl(y), lo = fl(y - hi).
+        std::vector<float4> y2(nnz);
+        for (int k = 0; k < nnz; ++k) {
+            double re = net.y[2 * k], im = net.y[2 * k + 1];
+            float rh = (float)re, ih = (float)im;
+            y2[k] = make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
+        }
+        TPF_CK(cudaMemcpy(d.y2f, y2.data(), sizeof(float4) * nnz, cudaMemcpyHostToDevice));
+    }
+    d.radial = net.radial;
+    d.phases = net.phases;
+    d.nbp = n / net.phases;
+    if (net.phases > 1) {
+        // Polyphase: the unknown each neighbour-list entry's admittance multiplies, and v_s.
+        TPF_CK(cudaMalloc(&d.csr_self, sizeof(int) * (nnz > 0 ? nnz : 1)));
+        if (nnz > 0) TPF_CK(cudaMemcpy(d.csr_self, net.csr_self.data(), sizeof(int) * nnz, cudaMemcpyHostToDevice));
+    }
+    TPF_CK(cudaMalloc(&d.vs64, sizeof(double) * 2 * net.phases));
+    {
+        std::vector<double> vs(net.vs);
+        if (vs.empty()) vs = {net.vs_re, net.vs_im};
+        TPF_CK(cudaMemcpy(d.vs64, vs.data(), sizeof(double) * 2 * net.phases, cudaMemcpyHostToDevice));
+    }
+    if (net.radial && net.phases == 1) {
+        const int nch = net.ch_ptr[n];
+        std::vector<float2> yp(n);
+        for (int i = 0; i < n; ++i) yp[i] = make_float2((float)net.ypar[2 * i], (float)net.ypar[2 * i + 1]);
+        TPF_CK(cudaMalloc(&d.par, sizeof(int) * n));
+        TPF_CK(cudaMalloc(&d.ch_ptr, sizeof(int) * (n + 1)));
+        TPF_CK(cudaMalloc(&d.ch, sizeof(int) * (nch > 0 ? nch : 1)));
+        TPF_CK(cudaMalloc(&d.ypar, sizeof(float2) * n));
+        TPF_CK(cudaMemcpy(d.par, net.par.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
+        TPF_CK(cudaMemcpy(d.ch_ptr, net.ch_ptr.data(), sizeof(int) * (n + 1), cudaMemcpyHostToDevice));
+        if (nch > 0) TPF_CK(cudaMemcpy(d.ch, net.ch.data(), sizeof(int) * nch, cudaMemcpyHostToDevice));
+        TPF_CK(cudaMemcpy(d.ypar, yp.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    }
+    if (net.radial) {
+        const tpf_status rs = layout_tree(h, tree_bpt(n));
+        if (rs != TPF_OK) return rs;
     }
     if (!net.K.empty()) return ensure_dense(h);  // meshed networks: K was built with the network
     return TPF_OK;

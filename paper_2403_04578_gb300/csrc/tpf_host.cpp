@@ -551,6 +551,19 @@ tpf_status tpf_solve(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev, i
     return tpf::solve_mixed(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
 }
 
+tpf_status tpf_autotune(tpf_handle *h, int64_t T, const void *S_dev, const tpf_opts *opts, int *bpt_out,
+                        void *stream) {
+    if (!h || T <= 0 || !S_dev) return TPF_EINVAL;
+    tpf_opts o;
+    tpf_status st = check_opts(opts, o);
+    if (st != TPF_OK) return st;
+    if (o.precision != TPF_PREC_MIXED) return TPF_EUNSUPPORTED;
+    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    st = tpf::autotune_sparse(h, T, S_dev, o, reinterpret_cast<cudaStream_t>(stream), bpt_out);
+    h->stats = tpf_stats{};
+    return st;
+}
+
 tpf_status tpf_set_zip(tpf_handle *h, const double *alpha) {
     if (!h) return TPF_EINVAL;
     if (alpha) {

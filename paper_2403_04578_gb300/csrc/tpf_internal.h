@@ -216,6 +216,11 @@ namespace tpf {
 tpf_status upload_network(tpf_handle *h);
 // Upload K, W and the fp16 planes of K on first use by a dense solve.
 tpf_status ensure_dense(tpf_handle *h);
+// (Re)build the sparse formulation's slot layout for bpt positions per thread (0: none).
+tpf_status layout_tree(tpf_handle *h, int bpt);
+// Time the sparse kernel's block shapes on T sample columns and keep the fastest.
+tpf_status autotune_sparse(tpf_handle *h, int64_t T, const void *S, const tpf_opts &o, cudaStream_t st,
+                           int *bpt_out);
 // Upload (alpha != null, host [3][n]) or drop the ZIP coefficients.
 tpf_status set_zip(tpf_handle *h, const double *alpha);
 void free_device(tpf_handle *h);

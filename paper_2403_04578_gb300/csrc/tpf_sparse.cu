@@ -875,6 +875,73 @@ tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_
     return solve_sparse_ex(h, T, S, V, iters, mismatch, nullptr, o, st);
 }
 
+tpf_status autotune_sparse(tpf_handle *h, int64_t T, const void *S, const tpf_opts &o, cudaStream_t st,
+                           int *bpt_out) {
+    DeviceNet &d = h->dev;
+    if (!d.radial || d.t_threads == 0) return TPF_EUNSUPPORTED;
+    const int n = d.n;
+    // The ZIP coefficients live in the slot layout too: keep a host copy to lay them out again.
+    std::vector<double> zip;
+    if (d.zip64) {
+        zip.resize(3 * (size_t)n);
+        if (cudaMemcpy(zip.data(), d.zip64, sizeof(double) * zip.size(), cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return TPF_ECUDA;
+        }
+    }
+    auto relayout = [&](int bpt) -> tpf_status {
+        tpf_status rs = layout_tree(h, bpt);
+        if (rs == TPF_OK && !zip.empty()) rs = set_zip(h, zip.data());
+        return rs;
+    };
+    void *V = nullptr;
+    if (cudaMalloc(&V, sizeof(double) * 2 * (size_t)T * n) != cudaSuccess) {
+        cudaGetLastError();
+        return TPF_ENOMEM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    tpf_opts ot = o;
+    ot.start = TPF_START_FLAT;
+    ot.profile = 0;
+    const int current = d.t_bpt;
+    int best = 0;
+    float best_ms = 0.0f;
+    tpf_status rs = TPF_OK;
+    for (int bpt : {2, 4, 8}) {
+        if (!tree_threads(n, bpt)) continue;
+        rs = relayout(bpt);
+        if (rs != TPF_OK) break;
+        if (d.t_threads == 0) continue;  // the layout does not fit this shape
+        rs = solve_sparse(h, T, S, V, nullptr, nullptr, ot, st);  // warm-up
+        if (rs != TPF_OK && rs != TPF_ENOCONV) {
+            if (rs == TPF_EUNSUPPORTED) { rs = TPF_OK; continue; }  // too much shared memory
+            break;
+        }
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 2 && (rs == TPF_OK || rs == TPF_ENOCONV); ++r) rs = solve_sparse(h, T, S, V, nullptr, nullptr, ot, st);
+        cudaEventRecord(e1, st);
+        if (rs != TPF_OK && rs != TPF_ENOCONV) break;
+        rs = TPF_OK;
+        float ms = 0.0f;
+        cudaEventSynchronize(e1);
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best == 0 || ms < best_ms) {
+            best = bpt;
+            best_ms = ms;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(V);
+    const tpf_status rs2 = relayout(best ? best : current);
+    if (rs != TPF_OK) return rs;
+    if (rs2 != TPF_OK) return rs2;
+    if (bpt_out) *bpt_out = d.t_bpt;
+    return TPF_OK;
+}
+
 tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S, void *const *V,
                               int32_t *const *iters, double *const *mismatch, const tpf_opts &o, int64_t *conv_out,
                               tpf_stats *stats, cudaStream_t st) {

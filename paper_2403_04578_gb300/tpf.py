@@ -22,7 +22,7 @@ START_FLAT, START_GIVEN = 0, 1
 # Every entry point declared in include/tpf.h.
 EXPORTS = (
     "tpf_default_opts", "tpf_strerror", "tpf_create", "tpf_create_poly", "tpf_destroy", "tpf_n_pq", "tpf_precompute_host",
-    "tpf_solve", "tpf_solve_host", "tpf_solve_ex", "tpf_solve_batch", "tpf_set_zip", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
+    "tpf_solve", "tpf_solve_host", "tpf_solve_ex", "tpf_solve_batch", "tpf_set_zip", "tpf_autotune", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
     "tpf_mlp_create", "tpf_mlp_destroy", "tpf_mlp_param_count", "tpf_mlp_get_params", "tpf_mlp_set_params",
     "tpf_mlp_fit_normalization", "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients",
     "tpf_mlp_predict",
@@ -101,6 +101,8 @@ def lib(build_if_missing: bool = False):
     L.tpf_create_poly.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, i32p, i32p, f64p, ctypes.c_int, f64p,
                                   ctypes.c_int, i32p, ctypes.POINTER(vp)]
     L.tpf_create_poly.restype = ctypes.c_int
+    L.tpf_autotune.argtypes = [vp, ctypes.c_int64, vp, ctypes.POINTER(Opts), ctypes.POINTER(ctypes.c_int), vp]
+    L.tpf_autotune.restype = ctypes.c_int
     L.tpf_set_zip.argtypes = [vp, vp]
     L.tpf_set_zip.restype = ctypes.c_int
     L.tpf_solve_ex.argtypes = [vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(Outputs), ctypes.POINTER(Opts), vp]
@@ -258,6 +260,16 @@ class Feeder:
 
     def __exit__(self, *exc):
         self.close()
+
+    def autotune(self, S, tol=1e-10, max_iter=100, switch_tol=1e-4, stream=None) -> int:
+        """tpf_autotune on the CUDA complex128 sample S [T, n_pq]; returns the chosen buses per thread."""
+        o = make_opts("mixed", tol, max_iter, "flat", switch_tol, False, "sparse")
+        b = ctypes.c_int(0)
+        st = lib().tpf_autotune(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()), ctypes.byref(o), ctypes.byref(b),
+                                _stream_ptr(stream))
+        if st != OK:
+            raise TpfError(st, "tpf_autotune")
+        return b.value
 
     def set_zip(self, alpha=None):
         """ZIP load coefficients (Eq. 3): alpha = [alpha_P, alpha_I, alpha_Z], each [n_pq] (or None)."""

@@ -278,3 +278,22 @@ def test_sparse_unsupported(cuda):
     _, _, _, st = mesh.solve(_dev(np.full((4, 2), 0.01 + 0.005j)), precision="mixed", method="sparse", check=False)
     assert st == tpf.EUNSUPPORTED
     mesh.close()
+
+
+def test_autotune_keeps_results(cuda):
+    """tpf_autotune picks a launch shape on a sample; solves afterwards still match the oracle,
+    also with ZIP coefficients laid out again for the new shape."""
+    f, c, S = _case(300, 1500, seed=6)
+    fd = tpf.Feeder.from_inputs(f)
+    b = fd.autotune(_dev(S[:1024]))
+    assert b in (2, 4, 8)
+    Vo, _, _ = c.solve(S, tol=1e-13)
+    V, it, mm, st = fd.solve(_dev(S), method="sparse")
+    assert st == tpf.OK and np.abs(V.cpu().numpy() - Vo).max() <= TOL_MIXED
+    a = np.random.default_rng(1).dirichlet([2, 1, 1], f.n_pq).T.copy()
+    fd.set_zip(a)
+    assert fd.autotune(_dev(S[:512])) in (2, 4, 8)
+    Vz, _, _ = c.solve_zip(S[:200], a, tol=1e-13)
+    V, _, _, st = fd.solve(_dev(S[:200]), method="sparse")
+    assert st == tpf.OK and np.abs(V.cpu().numpy() - Vz).max() <= TOL_MIXED
+    fd.close()

@@ -129,6 +129,20 @@ __device__ __forceinline__ float2 demand_change(float2 v, float2 d, float2 s, fl
     return make_float2(al.x * c.x + al.z * cs_d.x, al.x * c.y + al.z * cs_d.y);
 }
 
+// Sum of the warp totals of the warps before `warp`: lane l holds the total of warp l (lanes past
+// the block's warps are zero), a shuffle scan over the lanes, then the entry of lane warp - 1.
+__device__ __forceinline__ float2 warps_before(float2 t, int lane, int warp) {
+    const int nw = blockDim.x >> 5;
+    if (lane >= nw) t = make_float2(0.0f, 0.0f);
+#pragma unroll
+    for (int o = 1; o < kMaxWarps; o <<= 1) {
+        const float ux = __shfl_up_sync(kFull, t.x, o), uy = __shfl_up_sync(kFull, t.y, o);
+        if (lane >= o) t = add2(make_float2(ux, uy), t);
+    }
+    const float px = __shfl_sync(kFull, t.x, warp ? warp - 1 : 0), py = __shfl_sync(kFull, t.y, warp ? warp - 1 : 0);
+    return warp ? make_float2(px, py) : make_float2(0.0f, 0.0f);
+}
+
 // Exclusive scan over the threads of the block (thread order) of one complex FP32 value.
 __device__ __forceinline__ float2 block_scan(float2 v, float2 *wt, int lane, int warp) {
     float2 inc = v;
@@ -141,9 +155,7 @@ __device__ __forceinline__ float2 block_scan(float2 v, float2 *wt, int lane, int
     const float2 off = lane ? make_float2(ex, ey) : make_float2(0.0f, 0.0f);
     if (lane == 31) wt[warp] = inc;
     __syncthreads();
-    float2 pre = make_float2(0.0f, 0.0f);
-    for (int w = 0; w < warp; ++w) pre = add2(pre, wt[w]);
-    return add2(pre, off);
+    return add2(warps_before(wt[lane < kMaxWarps ? lane : 0], lane, warp), off);
 }
 
 // Double-float arithmetic of the anchor.  Each result carries an absolute error of a few units
@@ -501,16 +513,25 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                 const float ex = __shfl_up_sync(kFull, inc.x, 1), ey = __shfl_up_sync(kFull, inc.y, 1);
                 if (lane == 31) wtm[warp] = make_float4(inc.x, inc.y, wmx.x, wmx.y);
                 __syncthreads();
+                const float4 tw = lane < nwarps ? wtm[lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (pending) {
                     pending = false;
-                    float2 dm = make_float2(wtm[0].z, wtm[0].w);
-                    for (int w = 1; w < nwarps; ++w) dm = make_float2(fmaxf(dm.x, wtm[w].z), fmaxf(dm.y, wtm[w].w));
+                    // Max over all 32 lanes (lanes past the block's warps hold zeros), then lane 0's
+                    // value for every lane: the decision below must be the same in every thread of
+                    // the block, or threads would leave the sweep loop while others wait at a barrier.
+                    float2 dm = make_float2(tw.z, tw.w);
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        dm.x = fmaxf(dm.x, __shfl_xor_sync(kFull, dm.x, o));
+                        dm.y = fmaxf(dm.y, __shfl_xor_sync(kFull, dm.y, o));
+                    }
+                    dm.x = __shfl_sync(kFull, dm.x, 0);
+                    dm.y = __shfl_sync(kFull, dm.y, 0);
                     decide(dm);
                     if (done || anchor_now) continue;
                 }
-                float2 pre = make_float2(0.0f, 0.0f);
-                for (int w = 0; w < warp; ++w) pre = add2(pre, make_float2(wtm[w].x, wtm[w].y));
-                off = add2(pre, lane ? make_float2(ex, ey) : make_float2(0.0f, 0.0f));
+                off = add2(warps_before(make_float2(tw.x, tw.y), lane, warp),
+                           lane ? make_float2(ex, ey) : make_float2(0.0f, 0.0f));
             }
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) P[j * th + tid] = add2(off, loc[j]);

@@ -47,8 +47,8 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
     DeviceNet &d = h->dev;
     const int n = net.n_pq;
     cudaFree(d.t_col); cudaFree(d.t_end); cudaFree(d.t_par); cudaFree(d.t_ecnt); cudaFree(d.t_ends); cudaFree(d.t_z);
-    cudaFree(d.t_zrow); cudaFree(d.t_yrow);
-    d.t_col = d.t_end = d.t_par = d.t_ecnt = d.t_ends = nullptr;
+    cudaFree(d.t_zrow); cudaFree(d.t_yrow); cudaFree(d.t_kidx);
+    d.t_col = d.t_end = d.t_par = d.t_ecnt = d.t_ends = d.t_kidx = nullptr;
     d.t_z = d.t_zrow = nullptr;
     d.t_yrow = nullptr;
     d.t_threads = d.t_bpt = 0;
@@ -61,7 +61,7 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
             const int ns = th * bpt;
             auto slot = [th, bpt](int q) { return (q % bpt) * th + q / bpt; };
             const int ph = net.phases, nb = n / ph;
-            std::vector<int> col(ns, -1), end(ns, 0), par(ns, -1), ecnt(ns, 0), ends;
+            std::vector<int> col(ns, -1), end(ns, 0), par(ns, -1), ecnt(ns, 0), ends, kidx(ns, -1);
             std::vector<float4> z(ns, make_float4(0.f, 0.f, 0.f, 0.f));
             // Polyphase: row p of the branch's impedance (double-float) and admittance per slot.
             std::vector<float4> zrow(ph > 1 ? (size_t)ns * ph : 0, make_float4(0.f, 0.f, 0.f, 0.f));
@@ -78,7 +78,10 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
                 if ((int)ends.size() > 0xffff || cnt > 0x3fff) fits = false;
                 // start | count << 16 | phase << 30
                 ecnt[s] = (int)ends.size() | (cnt << 16) | ((q / nb) << 30);
-                for (int k = net.dfs_eptr[q]; k < net.dfs_eptr[q + 1]; ++k) ends.push_back(slot(net.dfs_ends[k]));
+                for (int k = net.dfs_eptr[q]; k < net.dfs_eptr[q + 1]; ++k) {
+                    kidx[slot(net.dfs_ends[k])] = (int)ends.size();  // where its branch term is scattered
+                    ends.push_back(slot(net.dfs_ends[k]));
+                }
                 auto dd = [](double re, double im) {
                     const float rh = (float)re, ih = (float)im;
                     return make_float4(rh, ih, (float)(re - (double)rh), (float)(im - (double)ih));
@@ -105,7 +108,7 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
             if (!fits) {
                 d.t_threads = 0;
             } else if (!up(&d.t_col, col) || !up(&d.t_end, end) || !up(&d.t_par, par) || !up(&d.t_ecnt, ecnt) ||
-                       !up(&d.t_ends, ends) || !up(&d.t_z, z) ||
+                       !up(&d.t_ends, ends) || !up(&d.t_z, z) || !up(&d.t_kidx, kidx) ||
                        (ph > 1 && (!up(&d.t_zrow, zrow) || !up(&d.t_yrow, yrow)))) {
                 cudaGetLastError();
                 return TPF_ECUDA;
@@ -252,6 +255,7 @@ void free_device(tpf_handle *h) {
     cudaFree(d.Kr16); cudaFree(d.Ki16);
     cudaFree(d.par); cudaFree(d.ch_ptr); cudaFree(d.ch); cudaFree(d.ypar);
     cudaFree(d.t_col); cudaFree(d.t_end); cudaFree(d.t_par); cudaFree(d.t_ecnt); cudaFree(d.t_ends); cudaFree(d.t_z);
+    cudaFree(d.t_kidx);
     cudaFree(d.zip64); cudaFree(d.t_zip_hi); cudaFree(d.t_zip_lo);
     cudaFree(d.csr_self); cudaFree(d.vs64); cudaFree(d.t_zrow); cudaFree(d.t_yrow);
     d = DeviceNet();

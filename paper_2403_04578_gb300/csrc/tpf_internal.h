@@ -104,6 +104,7 @@ struct DeviceNet {
     // (re_hi, im_hi, re_lo, im_lo).
     int t_threads = 0, t_bpt = 0, t_n_ends = 0;
     int *t_col = nullptr, *t_end = nullptr, *t_par = nullptr, *t_ecnt = nullptr, *t_ends = nullptr;
+    int *t_kidx = nullptr;  // per slot: the index in t_ends at which its position appears, or -1
     float4 *t_z = nullptr;
     // ZIP load coefficients (Eq. 3), set by tpf_set_zip; null for constant power.  zip64: double
     // [3][n] in column order (FP64 path); t_zip_hi / t_zip_lo: float4 (alpha_P, alpha_I, alpha_Z, 0)

@@ -48,7 +48,7 @@ struct TreeWork {
     int n, n_ends;
     float2 vs_f;
     c2 vs_dd;
-    const int *col, *end, *par, *ecnt, *ends;
+    const int *col, *end, *par, *ecnt, *ends, *kidx;
     const float4 *z;
     const float4 *zip_hi, *zip_lo;  // ZIP coefficients (alpha_P, alpha_I, alpha_Z, 0) per slot, or null
     // Polyphase: positions per phase block, v_s per phase, per slot the rows of the branch's
@@ -239,7 +239,7 @@ __device__ __forceinline__ int slot_of(int p, int th) {
 // loads in flight together.
 template <int kBPT, bool kZip, int kPh>
 __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B, const short *s_end,
-                                        const short *s_ends, const float4 *Zs, const int *ecnt, float4 *wtd, int tid,
+                                        const float4 *Zs, const int *ecnt, float4 *wtd, int tid,
                                         int th, int lane, int warp) {
     const int n = a.n, base = tid * kBPT;
     // Load currents at V_ref and their inclusive prefix sums.
@@ -306,7 +306,7 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
         if (q < n) {
             const int ec = __float_as_int(A[s].x);
             c2 e = unpack(B[s]);
-            for (int k = 0; k < ends_cnt(ec); ++k) e = cqsub(e, unpack(B[s_ends[(ec & 0xffff) + k]]));
+            for (int k = 0; k < ends_cnt(ec); ++k) e = cqsub(e, unpack(B[a.ends[(ec & 0xffff) + k]]));
             run = cqadd(run, e);
             A[s] = pack(run);
         }
@@ -342,7 +342,8 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
     short *const s_end = reinterpret_cast<short *>(reinterpret_cast<char *>(ZR) +
                                                    (kPh > 1 ? sizeof(float2) * kPh * ns : 0));  // [ns] end of the subtree's range
     short *const s_par = s_end + ns;                               // [ns] parent slot, -1 = the slack
-    short *const s_ends = s_par + ns;  // [n_ends] slots of the positions whose range ends at a position
+    // [ns] where each position's branch term goes in the ends-ordered copy of X (-1: nowhere)
+    short *const s_kidx = s_par + ns;
     float2 *P = reinterpret_cast<float2 *>(A);  // [ns] inclusive prefix sums of the load currents
     float2 *X = P + ns;                           // [ns] branch terms z_q L_q; the residual's x at the end
     __shared__ float2 wt2[kMaxWarps];
@@ -360,7 +361,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
         const int s = j * th + tid;
         s_end[s] = (short)a.end[s];
         s_par[s] = (short)a.par[s];
-        if (s < a.n_ends) s_ends[s] = (short)a.ends[s];
+        s_kidx[s] = (short)a.kidx[s];
     }
     // Per position: V_ref (or V before anchoring) and delta = V - V_ref in registers, the ends-list
     // bounds in registers, S and z in C.
@@ -470,7 +471,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                 A[s] = make_float4(cs.x, cs.y, 0.0f, 0.0f);
                 B[s] = make_float4(re.h, im.h, slo.x, slo.y);
             }
-            const c2 off = anchor_dd<kBPT, kZip, kPh>(a, A, B, s_end, s_ends, Zs, ecnt, wtd, tid, th, lane, warp);
+            const c2 off = anchor_dd<kBPT, kZip, kPh>(a, A, B, s_end, Zs, ecnt, wtd, tid, th, lane, warp);
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
                 const int q = base + j, s = j * th + tid;
@@ -559,7 +560,11 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                         }
                     }
                 }
-                X[s] = xq;
+                // The branch term goes where the position that closes its range gathers it: X
+                // holds the terms in ends-list order, so each position's list is contiguous.
+                const int k = s_kidx[s];
+                if (k >= 0) X[k] = xq;
+                loc[j] = xq;
             }
             __syncthreads();
             // Path sums: prefix sums of E_q = x_q - (x_b of every b whose subtree range ends at
@@ -568,12 +573,11 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
             bool longer = false;
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
-                const int s = j * th + tid;
                 const int st = ecnt[j] & 0xffff, cnt = ends_cnt(ecnt[j]);
-                float2 e = X[s];
+                float2 e = loc[j];
 #pragma unroll
                 for (int k = 0; k < kGather; ++k)
-                    if (k < cnt) e = sub2(e, X[s_ends[st + k]]);
+                    if (k < cnt) e = sub2(e, X[st + k]);
                 longer |= cnt > kGather;
                 loc[j] = e;
             }
@@ -581,7 +585,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
 #pragma unroll
                 for (int j = 0; j < kBPT; ++j) {
                     const int st = ecnt[j] & 0xffff, cnt = ends_cnt(ecnt[j]);
-                    for (int k = kGather; k < cnt; ++k) loc[j] = sub2(loc[j], X[s_ends[st + k]]);
+                    for (int k = kGather; k < cnt; ++k) loc[j] = sub2(loc[j], X[st + k]);
                 }
             }
             run = make_float2(0.0f, 0.0f);
@@ -767,6 +771,7 @@ TreeWork work_of(const tpf_handle *h) {
     w.par = d.t_par;
     w.ecnt = d.t_ecnt;
     w.ends = d.t_ends;
+    w.kidx = d.t_kidx;
     w.z = d.t_z;
     w.zip_hi = d.t_zip_hi;
     w.zip_lo = d.t_zip_lo;

@@ -535,17 +535,23 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                            lane ? make_float2(ex, ey) : make_float2(0.0f, 0.0f));
             }
 #pragma unroll
-            for (int j = 0; j < kBPT; ++j) P[j * th + tid] = add2(off, loc[j]);
+            for (int j = 0; j < kBPT; ++j) {
+                loc[j] = add2(off, loc[j]);  // the thread's own prefix values, also kept in registers
+                P[j * th + tid] = loc[j];
+            }
             __syncthreads();
             // Branch terms x_q = z_q (P[end_q - 1] - P[q - 1]).
+            // Descending j: loc[j - 1] still holds the prefix value of position q - 1.
 #pragma unroll
-            for (int j = 0; j < kBPT; ++j) {
+            for (int j = kBPT - 1; j >= 0; --j) {
                 const int q = base + j, s = j * th + tid;
                 float2 xq = make_float2(0.0f, 0.0f);  // positions past n contribute nothing
                 if (q < n) {
                     if (kPh == 1) {
-                        float2 L = P[slot_of<kBPT>(s_end[s] - 1, th)];
-                        if (q > 0) L = sub2(L, P[j ? s - th : (kBPT - 1) * th + tid - 1]);
+                        const int last = s_end[s] - 1;  // last position of the subtree (q for a leaf)
+                        float2 L = last == q ? loc[j] : P[slot_of<kBPT>(last, th)];
+                        if (j) L = sub2(L, loc[j - 1]);
+                        else if (q > 0) L = sub2(L, P[(kBPT - 1) * th + tid - 1]);
                         const float4 cs = C[s];
                         xq = cmul2(make_float2(cs.z, cs.w), L);
                     } else {

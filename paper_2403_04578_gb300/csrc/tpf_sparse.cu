@@ -220,9 +220,24 @@ __device__ __forceinline__ c2 block_scan_dd(c2 v, float4 *wt, int lane, int warp
     const c2 off = lane ? unpack(e) : c2{{0.0f, 0.0f}, {0.0f, 0.0f}};
     if (lane == 31) wt[warp] = pack(inc);
     __syncthreads();
-    c2 pre = {{0.0f, 0.0f}, {0.0f, 0.0f}};
-    for (int w = 0; w < warp; ++w) pre = cqadd(pre, unpack(wt[w]));
-    return cqadd(pre, off);
+    // Lane l scans the warp totals up to warp l; each warp takes lane warp - 1's sum.
+    const int nw = blockDim.x >> 5;
+    float4 tw = lane < nw ? wt[lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 1
+    for (int o = 1; o < nw; o <<= 1) {
+        float4 u;
+        u.x = __shfl_up_sync(kFull, tw.x, o);
+        u.y = __shfl_up_sync(kFull, tw.y, o);
+        u.z = __shfl_up_sync(kFull, tw.z, o);
+        u.w = __shfl_up_sync(kFull, tw.w, o);
+        if (lane >= o) tw = pack(cqadd(unpack(u), unpack(tw)));
+    }
+    const int src = warp ? warp - 1 : 0;
+    tw.x = __shfl_sync(kFull, tw.x, src);
+    tw.y = __shfl_sync(kFull, tw.y, src);
+    tw.z = __shfl_sync(kFull, tw.z, src);
+    tw.w = __shfl_sync(kFull, tw.w, src);
+    return warp ? cqadd(unpack(tw), off) : off;
 }
 
 // Slot of depth-first position p for blocks of th threads with kBPT positions each.
@@ -232,15 +247,15 @@ __device__ __forceinline__ int slot_of(int p, int th) {
 }
 
 // First part of an anchor, in double-float.  On entry A[s] = (S_hi) and B[s] = (V_ref, S_lo) for
-// the thread's own slots.  Leaves in A the inclusive prefix sums of the path terms and returns the
+// the thread's own slots.  Leaves in B the inclusive prefix sums of the path terms and returns the
 // thread's exclusive scan offset.  ecnt holds the thread's ends-list bounds.
 // The loops run over shared memory only and are not unrolled: the anchor runs once or twice per
 // column and its code stays small; the unrolled staging in the kernel keeps the device-memory
 // loads in flight together.
 template <int kBPT, bool kZip, int kPh>
 __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B, const short *s_end,
-                                        const float4 *Zs, const int *ecnt, float4 *wtd, int tid,
-                                        int th, int lane, int warp) {
+                                        const short *s_kidx, const float4 *Zs, const int *ecnt, float4 *wtd,
+                                        int tid, int th, int lane, int warp) {
     const int n = a.n, base = tid * kBPT;
     // Load currents at V_ref and their inclusive prefix sums.
     c2 run = {{0.0f, 0.0f}, {0.0f, 0.0f}};
@@ -296,19 +311,30 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
         }
     }
     __syncthreads();
+    // The branch terms in ends-list order (A is free now), so that each position's list is
+    // contiguous.
 #pragma unroll
-    for (int j = 0; j < kBPT; ++j) A[j * th + tid].x = __int_as_float(ecnt[j]);
-    // Inclusive prefix sums of E_q = x_q - (x_b of every b whose range ends at q).
+    for (int j = 0; j < kBPT; ++j) {
+        const int s = j * th + tid, k = s_kidx[s];
+        if (k >= 0) A[k] = B[s];
+    }
+    __syncthreads();
+    // Inclusive prefix sums of E_q = x_q - (x_b of every b whose range ends at q), into B.
     run = c2{{0.0f, 0.0f}, {0.0f, 0.0f}};
 #pragma unroll 1
     for (int j = 0; j < kBPT; ++j) {
         const int q = base + j, s = j * th + tid;
         if (q < n) {
-            const int ec = __float_as_int(A[s].x);
+            int ec = ecnt[0];  // ecnt[j] by selects: the array stays in registers
+#pragma unroll
+            for (int i = 1; i < kBPT; ++i)
+                if (j == i) ec = ecnt[i];
+            const int st = ec & 0xffff, cnt = ends_cnt(ec);
             c2 e = unpack(B[s]);
-            for (int k = 0; k < ends_cnt(ec); ++k) e = cqsub(e, unpack(B[a.ends[(ec & 0xffff) + k]]));
+#pragma unroll 1
+            for (int k = 0; k < cnt; ++k) e = cqsub(e, unpack(A[st + k]));
             run = cqadd(run, e);
-            A[s] = pack(run);
+            B[s] = pack(run);
         }
     }
     return block_scan_dd(run, wtd, lane, warp);
@@ -471,12 +497,12 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                 A[s] = make_float4(cs.x, cs.y, 0.0f, 0.0f);
                 B[s] = make_float4(re.h, im.h, slo.x, slo.y);
             }
-            const c2 off = anchor_dd<kBPT, kZip, kPh>(a, A, B, s_end, Zs, ecnt, wtd, tid, th, lane, warp);
+            const c2 off = anchor_dd<kBPT, kZip, kPh>(a, A, B, s_end, s_kidx, Zs, ecnt, wtd, tid, th, lane, warp);
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
                 const int q = base + j, s = j * th + tid;
                 if (q < n) {
-                    const c2 ps = cqadd(off, unpack(A[s]));
+                    const c2 ps = cqadd(off, unpack(B[s]));
                     const c2 vs = kPh == 1 ? a.vs_dd : a.vs_ddp[phase_of(ecnt[j])];
                     const c2 D = cqsub(cqsub(vs, c2{{vr[j].x, 0.0f}, {vr[j].y, 0.0f}}), ps);
                     B[s] = make_float4(D.re.h, D.im.h, D.re.l, D.im.l);

@@ -185,7 +185,11 @@ def test_sparse_peak_hours_1000(cuda):
     f = G.make_feeder(1000, 1)
     c = O.Case.from_feeder(f)
     S = G.load_tensor(f, 4096, 1)[1080:1080 + 300]
-    _check(f, c, S, "mixed", TOL_MIXED, 1, method="sparse")
+    err, _ = _check(f, c, S, "mixed", TOL_MIXED, 1, method="sparse")
+    # The anchored sweeps reach the FP64 fixed point to about 1e-11 pu.  Losing the low word of S
+    # or V in the FP64 <-> FP32-pair conversions leaves errors near 1e-9..1e-8 pu, inside the bar
+    # above: this bound catches that.
+    assert err <= 1e-10, f"max |V - V_oracle| = {err:.3e}"
 
 
 def test_sparse_chain_feeder(cuda):

@@ -130,12 +130,11 @@ __device__ __forceinline__ float2 demand_change(float2 v, float2 d, float2 s, fl
 }
 
 // Sum of the warp totals of the warps before `warp`: lane l holds the total of warp l (lanes past
-// the block's warps are zero), a shuffle scan over the lanes, then the entry of lane warp - 1.
-__device__ __forceinline__ float2 warps_before(float2 t, int lane, int warp) {
-    const int nw = blockDim.x >> 5;
+// the block's nw warps are zero), a shuffle scan over the lanes, then the entry of lane warp - 1.
+__device__ __forceinline__ float2 warps_before(float2 t, int lane, int warp, int nw) {
     if (lane >= nw) t = make_float2(0.0f, 0.0f);
 #pragma unroll
-    for (int o = 1; o < kMaxWarps; o <<= 1) {
+    for (int o = 1; o < nw; o <<= 1) {
         const float ux = __shfl_up_sync(kFull, t.x, o), uy = __shfl_up_sync(kFull, t.y, o);
         if (lane >= o) t = add2(make_float2(ux, uy), t);
     }
@@ -144,7 +143,7 @@ __device__ __forceinline__ float2 warps_before(float2 t, int lane, int warp) {
 }
 
 // Exclusive scan over the threads of the block (thread order) of one complex FP32 value.
-__device__ __forceinline__ float2 block_scan(float2 v, float2 *wt, int lane, int warp) {
+__device__ __forceinline__ float2 block_scan(float2 v, float2 *wt, int lane, int warp, int nw) {
     float2 inc = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -155,7 +154,7 @@ __device__ __forceinline__ float2 block_scan(float2 v, float2 *wt, int lane, int
     const float2 off = lane ? make_float2(ex, ey) : make_float2(0.0f, 0.0f);
     if (lane == 31) wt[warp] = inc;
     __syncthreads();
-    return add2(warps_before(wt[lane < kMaxWarps ? lane : 0], lane, warp), off);
+    return add2(warps_before(wt[lane < kMaxWarps ? lane : 0], lane, warp, nw), off);
 }
 
 // Double-float arithmetic of the anchor.  Each result carries an absolute error of a few units
@@ -201,7 +200,7 @@ __device__ __forceinline__ c2 current_q(c2 S, float2 V) {
 }
 
 // Exclusive block scan in double-float.
-__device__ __forceinline__ c2 block_scan_dd(c2 v, float4 *wt, int lane, int warp) {
+__device__ __forceinline__ c2 block_scan_dd(c2 v, float4 *wt, int lane, int warp, int nw) {
     c2 inc = v;
 #pragma unroll 1
     for (int o = 1; o < 32; o <<= 1) {
@@ -221,7 +220,6 @@ __device__ __forceinline__ c2 block_scan_dd(c2 v, float4 *wt, int lane, int warp
     if (lane == 31) wt[warp] = pack(inc);
     __syncthreads();
     // Lane l scans the warp totals up to warp l; each warp takes lane warp - 1's sum.
-    const int nw = blockDim.x >> 5;
     float4 tw = lane < nw ? wt[lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 1
     for (int o = 1; o < nw; o <<= 1) {
@@ -277,7 +275,7 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
             A[s] = pack(run);
         }
     }
-    c2 off = block_scan_dd(run, wtd, lane, warp);
+    c2 off = block_scan_dd(run, wtd, lane, warp, th >> 5);
 #pragma unroll
     for (int j = 0; j < kBPT; ++j) {
         const int s = j * th + tid;
@@ -337,14 +335,16 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
             B[s] = pack(run);
         }
     }
-    return block_scan_dd(run, wtd, lane, warp);
+    return block_scan_dd(run, wtd, lane, warp, th >> 5);
 }
 
-template <int kBPT, bool kZip, int kPh>
+// kTh > 0 fixes the block size at compile time (it must equal blockDim.x): the slot arithmetic
+// and the scans then run on constants.  kTh = 0 takes it from blockDim.x.
+template <int kBPT, bool kZip, int kPh, int kTh>
 __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant__ TreeArgs g) {
     extern __shared__ float4 tsm[];
     __shared__ int s_work;
-    const int th = blockDim.x, ns = th * kBPT;
+    const int th = kTh ? kTh : (int)blockDim.x, ns = th * kBPT;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = th >> 5;
     if (tid == 0) {
         // The feeder of this block's column: the last work whose first column is <= blockIdx.x.
@@ -412,16 +412,6 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
             const float4 zq = a.z[s];
             zh = make_float2(zq.x, zq.y);
             ecnt[j] = a.ecnt[s];
-            if (g.given) {
-                if (a.v32) {
-                    vr[j] = static_cast<const float2 *>(a.V0)[t * n + i];
-                } else {
-                    const double2 v = static_cast<const double2 *>(a.V0)[t * n + i];
-                    vr[j] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
-                    dl[j] = make_float2(__double2float_rn(v.x - (double)vr[j].x),
-                                        __double2float_rn(v.y - (double)vr[j].y));
-                }
-            }
         }
         C[s] = make_float4(sh.x, sh.y, zh.x, zh.y);
         B[s] = make_float4(sl.x, sl.y, 0.0f, 0.0f);  // S_lo until the first anchor replaces it by D
@@ -431,6 +421,23 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
             for (int pp = 0; pp < kPh; ++pp) {
                 const float4 zq = q < n ? a.zrow[(size_t)s * kPh + pp] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 ZR[s * kPh + pp] = make_float2(zq.x, zq.y);
+            }
+        }
+    }
+    if (g.given) {  // a loop of its own: fewer loads in flight at once, fewer registers
+#pragma unroll
+        for (int j = 0; j < kBPT; ++j) {
+            const int q = base + j, s = j * th + tid;
+            if (q < n) {
+                const int64_t k = t * n + a.col[s];
+                if (a.v32) {
+                    vr[j] = static_cast<const float2 *>(a.V0)[k];
+                } else {
+                    const double2 v = static_cast<const double2 *>(a.V0)[k];
+                    vr[j] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
+                    dl[j] = make_float2(__double2float_rn(v.x - (double)vr[j].x),
+                                        __double2float_rn(v.y - (double)vr[j].y));
+                }
             }
         }
     }
@@ -475,27 +482,30 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
             anchor_now = false;
             anchored = true;
             ++anchors;
+            if (anchors > 1) {
+                // B holds the previous anchor's D: S_lo again, one position at a time (rare).
+#pragma unroll 1
+                for (int j = 0; j < kBPT; ++j) {
+                    const int q = base + j, s = j * th + tid;
+                    float2 slo = make_float2(0.0f, 0.0f);
+                    if (q < n && !a.s32) {
+                        const double2 sv = S64[a.col[s]];
+                        const float4 cs = C[s];
+                        slo = make_float2(__double2float_rn(sv.x - (double)cs.x), __double2float_rn(sv.y - (double)cs.y));
+                    }
+                    B[s] = make_float4(slo.x, slo.y, 0.0f, 0.0f);
+                }
+            }
             // V_ref <- fl32(V); the remainder stays in delta.  D = BFS(V_ref) - V_ref goes to B.
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
-                const int q = base + j, s = j * th + tid;
+                const int s = j * th + tid;
                 const f2 re = two_sum(vr[j].x, dl[j].x), im = two_sum(vr[j].y, dl[j].y);
                 vr[j] = make_float2(re.h, im.h);
                 dl[j] = make_float2(re.l, im.l);
-                const float4 cs = C[s];
-                float2 slo;
-                if (anchors == 1) {  // B still holds S_lo
-                    const float4 b = B[s];
-                    slo = make_float2(b.x, b.y);
-                } else {
-                    slo = make_float2(0.0f, 0.0f);
-                    if (q < n && !a.s32) {
-                        const double2 sv = S64[a.col[s]];
-                        slo = make_float2(__double2float_rn(sv.x - (double)cs.x), __double2float_rn(sv.y - (double)cs.y));
-                    }
-                }
+                const float4 cs = C[s], b = B[s];  // b = (S_lo, -)
                 A[s] = make_float4(cs.x, cs.y, 0.0f, 0.0f);
-                B[s] = make_float4(re.h, im.h, slo.x, slo.y);
+                B[s] = make_float4(re.h, im.h, b.x, b.y);
             }
             const c2 off = anchor_dd<kBPT, kZip, kPh>(a, A, B, s_end, s_kidx, Zs, ecnt, wtd, tid, th, lane, warp);
 #pragma unroll
@@ -557,7 +567,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                     decide(dm);
                     if (done || anchor_now) continue;
                 }
-                off = add2(warps_before(make_float2(tw.x, tw.y), lane, warp),
+                off = add2(warps_before(make_float2(tw.x, tw.y), lane, warp, nwarps),
                            lane ? make_float2(ex, ey) : make_float2(0.0f, 0.0f));
             }
 #pragma unroll
@@ -626,7 +636,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                 run = add2(run, loc[j]);  // positions past n have x = 0 and no ends
                 loc[j] = run;
             }
-            off = block_scan(run, wt2, lane, warp);
+            off = block_scan(run, wt2, lane, warp, nwarps);
         }
         float2 mx = make_float2(0.0f, 0.0f);  // max |step|^2, max |delta|^2
 #pragma unroll
@@ -829,20 +839,34 @@ size_t tree_smem(int threads, int bpt, bool zip, int phases) {
            sizeof(short) * 3 * ns;
 }
 
-template <int kBPT, bool kZip, int kPh>
+template <int kBPT, bool kZip, int kPh, int kTh = 0>
 cudaError_t launch_tree_t(int threads, int64_t cols, size_t smem, const TreeArgs &g, cudaStream_t st) {
-    cudaError_t e =
-        cudaFuncSetAttribute(mx_tree<kBPT, kZip, kPh>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) mx_tree<kBPT, kZip, kPh><<<(unsigned)cols, threads, smem, st>>>(g);
+    cudaError_t e = cudaFuncSetAttribute(mx_tree<kBPT, kZip, kPh, kTh>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e == cudaSuccess) mx_tree<kBPT, kZip, kPh, kTh><<<(unsigned)cols, threads, smem, st>>>(g);
     return e;
 }
 
+// The single-phase constant-power kernel has compile-time block sizes for the shapes that the
+// default bus-per-thread choice gives (4 buses per thread up to 2,048 buses, 8 beyond); other
+// shapes and the ZIP and polyphase kernels take the block size at run time.
 template <int kBPT>
 cudaError_t launch_tree_b(int threads, bool zip, int phases, int64_t cols, size_t smem, const TreeArgs &g,
                           cudaStream_t st) {
     if (phases == 3) return launch_tree_t<kBPT, false, 3>(threads, cols, smem, g, st);
-    return zip ? launch_tree_t<kBPT, true, 1>(threads, cols, smem, g, st)
-               : launch_tree_t<kBPT, false, 1>(threads, cols, smem, g, st);
+    if (zip) return launch_tree_t<kBPT, true, 1>(threads, cols, smem, g, st);
+    if constexpr (kBPT == 4) {
+        switch (threads) {
+        case 64: return launch_tree_t<kBPT, false, 1, 64>(threads, cols, smem, g, st);
+        case 128: return launch_tree_t<kBPT, false, 1, 128>(threads, cols, smem, g, st);
+        case 256: return launch_tree_t<kBPT, false, 1, 256>(threads, cols, smem, g, st);
+        case 512: return launch_tree_t<kBPT, false, 1, 512>(threads, cols, smem, g, st);
+        default: break;
+        }
+    }
+    if constexpr (kBPT == 8)
+        if (threads == 512) return launch_tree_t<kBPT, false, 1, 512>(threads, cols, smem, g, st);
+    return launch_tree_t<kBPT, false, 1>(threads, cols, smem, g, st);
 }
 
 tpf_status launch_tree(int bpt, int threads, bool zip, int phases, int64_t cols, const TreeArgs &g, cudaStream_t st) {

@@ -93,6 +93,12 @@ __device__ __forceinline__ float2 cmul2(float2 a, float2 b) {
     return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 __device__ __forceinline__ float abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+// max(a, b) that returns NaN if either is NaN (fmaxf returns the other operand).
+__device__ __forceinline__ float fmax_nan(float a, float b) {
+    float r;
+    asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
 __device__ __forceinline__ float4 pack(c2 v) { return make_float4(v.re.h, v.re.l, v.im.h, v.im.l); }
 __device__ __forceinline__ c2 unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
 
@@ -243,15 +249,21 @@ template <int kBPT>
 __device__ __forceinline__ int slot_of(int p, int th) {
     return (p & (kBPT - 1)) * th + p / kBPT;
 }
+// Slot of the position after the one in slot s.
+template <int kBPT>
+__device__ __forceinline__ int next_slot(int s, int th) {
+    return s < (kBPT - 1) * th ? s + th : s - (kBPT - 1) * th + 1;
+}
 
 // First part of an anchor, in double-float.  On entry A[s] = (S_hi) and B[s] = (V_ref, S_lo) for
 // the thread's own slots.  Leaves in B the inclusive prefix sums of the path terms and returns the
-// thread's exclusive scan offset.  ecnt holds the thread's ends-list bounds.
+// thread's exclusive scan offset.  ecnt holds the thread's ends-list bounds, s_rng the subtree
+// ranges (as in the kernel).
 // The loops run over shared memory only and are not unrolled: the anchor runs once or twice per
 // column and its code stays small; the unrolled staging in the kernel keeps the device-memory
 // loads in flight together.
 template <int kBPT, bool kZip, int kPh>
-__device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B, const short *s_end,
+__device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B, const short *s_rng,
                                         const short *s_kidx, const float4 *Zs, const int *ecnt, float4 *wtd,
                                         int tid, int th, int lane, int warp) {
     const int n = a.n, base = tid * kBPT;
@@ -290,12 +302,12 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
         const int q = base + j, s = j * th + tid;
         if (q < n) {
             if (kPh == 1) {
-                c2 L = unpack(A[slot_of<kBPT>(s_end[s] - 1, th)]);
+                c2 L = unpack(A[s_rng[s]]);
                 if (q > 0) L = cqsub(L, unpack(A[j ? s - th : (kBPT - 1) * th + tid - 1]));
                 const float4 zq = B[s];
                 B[s] = pack(cqmul(c2{{zq.x, zq.z}, {zq.y, zq.w}}, L));
             } else {
-                const int p = q / a.nbp, qb = q - p * a.nbp, eb = s_end[s] - p * a.nbp;
+                const int p = q / a.nbp, qb = q - p * a.nbp, eb = s_rng[s] - p * a.nbp;
                 c2 x = {{0.0f, 0.0f}, {0.0f, 0.0f}};
                 for (int pp = 0; pp < kPh; ++pp) {
                     c2 L = unpack(A[slot_of<kBPT>(pp * a.nbp + eb - 1, th)]);
@@ -365,9 +377,11 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
     float4 *const Zs = tsm + 3 * ns;  // [ns] ZIP coefficients (kZip only)
     // [ns][kPh] rows of the branch impedance blocks (polyphase only)
     float2 *const ZR = reinterpret_cast<float2 *>(tsm + (kZip ? 4 : 3) * ns);
-    short *const s_end = reinterpret_cast<short *>(reinterpret_cast<char *>(ZR) +
-                                                   (kPh > 1 ? sizeof(float2) * kPh * ns : 0));  // [ns] end of the subtree's range
-    short *const s_par = s_end + ns;                               // [ns] parent slot, -1 = the slack
+    // [ns] the subtree's range [q, end_q): one phase, the slot of its last position end_q - 1 (the
+    // slot itself for a leaf); polyphase, end_q
+    short *const s_rng = reinterpret_cast<short *>(reinterpret_cast<char *>(ZR) +
+                                                   (kPh > 1 ? sizeof(float2) * kPh * ns : 0));
+    short *const s_par = s_rng + ns;                               // [ns] parent slot, -1 = the slack
     // [ns] where each position's branch term goes in the ends-ordered copy of X (-1: nowhere)
     short *const s_kidx = s_par + ns;
     float2 *P = reinterpret_cast<float2 *>(A);  // [ns] inclusive prefix sums of the load currents
@@ -384,8 +398,8 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
 
 #pragma unroll
     for (int j = 0; j < kBPT; ++j) {
-        const int s = j * th + tid;
-        s_end[s] = (short)a.end[s];
+        const int q = base + j, s = j * th + tid;
+        s_rng[s] = (short)(kPh > 1 ? a.end[s] : (q < n ? slot_of<kBPT>(a.end[s] - 1, th) : s));
         s_par[s] = (short)a.par[s];
         s_kidx[s] = (short)a.kidx[s];
     }
@@ -507,7 +521,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                 A[s] = make_float4(cs.x, cs.y, 0.0f, 0.0f);
                 B[s] = make_float4(re.h, im.h, b.x, b.y);
             }
-            const c2 off = anchor_dd<kBPT, kZip, kPh>(a, A, B, s_end, s_kidx, Zs, ecnt, wtd, tid, th, lane, warp);
+            const c2 off = anchor_dd<kBPT, kZip, kPh>(a, A, B, s_rng, s_kidx, Zs, ecnt, wtd, tid, th, lane, warp);
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
                 const int q = base + j, s = j * th + tid;
@@ -553,16 +567,16 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                 const float4 tw = lane < nwarps ? wtm[lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (pending) {
                     pending = false;
-                    // Max over all 32 lanes (lanes past the block's warps hold zeros), then lane 0's
-                    // value for every lane: the decision below must be the same in every thread of
-                    // the block, or threads would leave the sweep loop while others wait at a barrier.
+                    // Max over lanes 0 .. nwarps - 1 (the warps' maxima; a NaN stays NaN) into lane 0,
+                    // then lane 0's value for every lane: the decision below must be the same in every
+                    // thread of the block, or threads would leave the sweep loop while others wait at
+                    // a barrier.  max |delta| only counts on a blind anchor.
                     float2 dm = make_float2(tw.z, tw.w);
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        dm.x = fmaxf(dm.x, __shfl_xor_sync(kFull, dm.x, o));
-                        dm.y = fmaxf(dm.y, __shfl_xor_sync(kFull, dm.y, o));
-                    }
+                    for (int o = 1; o < nwarps; o <<= 1) dm.x = fmax_nan(dm.x, __shfl_xor_sync(kFull, dm.x, o));
                     dm.x = __shfl_sync(kFull, dm.x, 0);
+#pragma unroll
+                    for (int o = 1; o < nwarps; o <<= 1) dm.y = fmaxf(dm.y, __shfl_xor_sync(kFull, dm.y, o));
                     dm.y = __shfl_sync(kFull, dm.y, 0);
                     decide(dm);
                     if (done || anchor_now) continue;
@@ -584,15 +598,15 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                 float2 xq = make_float2(0.0f, 0.0f);  // positions past n contribute nothing
                 if (q < n) {
                     if (kPh == 1) {
-                        const int last = s_end[s] - 1;  // last position of the subtree (q for a leaf)
-                        float2 L = last == q ? loc[j] : P[slot_of<kBPT>(last, th)];
+                        const int ls = s_rng[s];  // slot of the subtree's last position (s for a leaf)
+                        float2 L = ls == s ? loc[j] : P[ls];
                         if (j) L = sub2(L, loc[j - 1]);
                         else if (q > 0) L = sub2(L, P[(kBPT - 1) * th + tid - 1]);
                         const float4 cs = C[s];
                         xq = cmul2(make_float2(cs.z, cs.w), L);
                     } else {
                         // x = sum over phases p' of Z[p][p'] L_{p'}
-                        const int p = phase_of(ecnt[j]), qb = q - p * a.nbp, eb = s_end[s] - p * a.nbp;
+                        const int p = phase_of(ecnt[j]), qb = q - p * a.nbp, eb = s_rng[s] - p * a.nbp;
 #pragma unroll
                         for (int pp = 0; pp < kPh; ++pp) {
                             float2 L = P[slot_of<kBPT>(pp * a.nbp + eb - 1, th)];
@@ -638,7 +652,8 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
             }
             off = block_scan(run, wt2, lane, warp, nwarps);
         }
-        float2 mx = make_float2(0.0f, 0.0f);  // max |step|^2, max |delta|^2
+        // max |step|^2 (NaN if any step is NaN), and on a blind anchor max |delta|^2
+        float2 mx = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int j = 0; j < kBPT; ++j) {
             const int q = base + j, s = j * th + tid;
@@ -656,16 +671,13 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
                     step = sub2(nv, vr[j]);
                     vr[j] = nv;
                 }
-                float mag2 = abs2(step);
-                if (mag2 != mag2) mag2 = __int_as_float(0x7f800000);
-                mx.x = fmaxf(mx.x, mag2);
+                mx.x = fmax_nan(mx.x, abs2(step));
             }
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            mx.x = fmaxf(mx.x, __shfl_xor_sync(kFull, mx.x, o));
-            mx.y = fmaxf(mx.y, __shfl_xor_sync(kFull, mx.y, o));
-        }
+        for (int o = 16; o > 0; o >>= 1) mx.x = fmax_nan(mx.x, __shfl_xor_sync(kFull, mx.x, o));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) mx.y = fmaxf(mx.y, __shfl_xor_sync(kFull, mx.y, o));
         wmx = mx;
         pending = true;
     }
@@ -743,11 +755,22 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant_
             const float4 al = kZip ? Zs[s] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
             float2 r = anchored ? demand_change<kZip>(vr[j], dl[j], sh, al) : demand_current<kZip>(vr[j], sh, al);
             r = sub2(r, J[s]);
-            const int e = s_end[s];
-            for (int k = q + 1; k < e;) {
-                const int ks = slot_of<kBPT>(k, th);
-                r = add2(r, J[ks]);
-                k = s_end[ks];
+            if (kPh == 1) {
+                // The first child is q + 1, each next one follows the previous one's last position;
+                // the child whose subtree ends where q's ends is the last.
+                const int lq = s_rng[s];
+                for (int ks = lq == s ? -1 : next_slot<kBPT>(s, th); ks >= 0;) {
+                    r = add2(r, J[ks]);
+                    const int lc = s_rng[ks];
+                    ks = lc == lq ? -1 : next_slot<kBPT>(lc, th);
+                }
+            } else {
+                const int e = s_rng[s];
+                for (int k = q + 1; k < e;) {
+                    const int ks = slot_of<kBPT>(k, th);
+                    r = add2(r, J[ks]);
+                    k = s_rng[ks];
+                }
             }
             const float v2 = abs2(add2(vr[j], dl[j]));
             float mv = sqrtf(v2 * abs2(r));

@@ -353,7 +353,8 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
 // kTh > 0 fixes the block size at compile time (it must equal blockDim.x): the slot arithmetic
 // and the scans then run on constants.  kTh = 0 takes it from blockDim.x.
 template <int kBPT, bool kZip, int kPh, int kTh>
-__global__ void __maxnreg__(kBPT == 8 ? 128 : 64) mx_tree(const __grid_constant__ TreeArgs g) {
+__global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 && (kZip || kPh > 1) ? 80 : 64))
+    mx_tree(const __grid_constant__ TreeArgs g) {
     extern __shared__ float4 tsm[];
     __shared__ int s_work;
     const int th = kTh ? kTh : (int)blockDim.x, ns = th * kBPT;

@@ -59,7 +59,13 @@ enum {
 /* Starting point of a solve. */
 enum {
     TPF_START_FLAT = 0,  /* V_0 = 1 + j0 at every bus (Algorithm 1)                             */
-    TPF_START_GIVEN = 1  /* V_0 is read from the V buffer passed to the solve                   */
+    TPF_START_GIVEN = 1, /* V_0 is read from the V buffer passed to the solve.  Mixed precision:   *
+                          * every column is anchored at V_0 at once, which suits a V_0 that is    *
+                          * already close to the solution (a restart, a converged neighbour)     */
+    TPF_START_WARM = 2   /* V_0 is read from the V buffer as an approximate start (a learned      *
+                          * prediction, a neighbouring time step).  Mixed precision: the FP32     *
+                          * sweeps start from fl32(V_0) and a column is anchored once its step is *
+                          * small, as from the flat start.  FP64: the same as TPF_START_GIVEN     */
 };
 
 typedef struct {
@@ -167,7 +173,7 @@ tpf_status tpf_precompute_host(int n_bus, int n_branch, const int32_t *from, con
  *
  *   S_dev        device, complex128 [T][n_pq], the loads (read only)
  *   V_dev        device, complex128 [T][n_pq], receives V.  Read first as V_0 when
- *                opts->start == TPF_START_GIVEN.
+ *                opts->start is TPF_START_GIVEN or TPF_START_WARM.
  *   iters_dev    device, int32 [T], receives the sweeps applied to each column, or -max_iter
  *                for a column that never met tol (NULL: not written)
  *   mismatch_dev device, float64 [T], receives max_i |V_i conj((Y v)_i) + S_i| in pu, the power
@@ -250,7 +256,7 @@ tpf_status tpf_solve_ex(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev
 /*
  * Solve F feeders at once (many networks of different sizes, Sec. V): feeder f has handle hs[f],
  * T[f] columns, device tensors S[f] and V[f] (complex128 [T[f]][n_pq of hs[f]], V read as V_0
- * when opts->start == TPF_START_GIVEN), and optional iters[f] / mismatch[f] (the arrays iters and
+ * when opts->start is TPF_START_GIVEN or TPF_START_WARM), and optional iters[f] / mismatch[f] (the arrays iters and
  * mismatch may be NULL, as may their entries).  Radial feeders under TPF_METHOD_SPARSE with
  * TPF_PREC_MIXED share one launch per launch shape (feeders grouped by the block size the sparse
  * kernel uses for them), each block finding its feeder in a device table; any other feeder is
@@ -267,7 +273,7 @@ tpf_status tpf_solve_batch(int F, tpf_handle *const *hs, const int64_t *T, const
 /*
  * Learned warm start.  The paper starts Algorithm 1 from the flat profile V_0 = 1; these entry
  * points train and run a small multilayer perceptron that predicts V_0 from a column's loads, so
- * that a solve started from it (TPF_START_GIVEN) needs fewer sweeps.  The iteration still decides
+ * that a solve started from it (TPF_START_WARM) needs fewer sweeps.  The iteration still decides
  * the result: it converges to the same high-voltage solution from any start (Sec. III).
  *
  * Network: inputs P_1..P_n, Q_1..Q_n (real and imaginary parts of a column of S), z-scored per

@@ -528,7 +528,7 @@ static tpf_status check_opts(const tpf_opts *in, tpf_opts &o) {
     if (in) o = *in;
     if (!(o.tol >= 0.0) || o.max_iter < 1 || o.max_iter > 100000) return TPF_EINVAL;
     if (o.precision != TPF_PREC_FP64 && o.precision != TPF_PREC_MIXED) return TPF_EINVAL;
-    if (o.start != TPF_START_FLAT && o.start != TPF_START_GIVEN) return TPF_EINVAL;
+    if (o.start != TPF_START_FLAT && o.start != TPF_START_GIVEN && o.start != TPF_START_WARM) return TPF_EINVAL;
     if (!(o.switch_tol >= 0.0)) return TPF_EINVAL;
     if (o.method != TPF_METHOD_DENSE && o.method != TPF_METHOD_SPARSE) return TPF_EINVAL;
     return TPF_OK;
@@ -586,7 +586,7 @@ tpf_status tpf_solve_ex(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev
     h->stats = tpf_stats{};
     h->stats.columns = T;
     if (T == 0) return TPF_OK;
-    if (!S_dev || (!V_dev && o.start == TPF_START_GIVEN)) return TPF_EINVAL;
+    if (!S_dev || (!V_dev && o.start != TPF_START_FLAT)) return TPF_EINVAL;
     if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
     return tpf::solve_sparse_ex(h, T, S_dev, V_dev, iters_dev, mismatch_dev, out, o,
                                 reinterpret_cast<cudaStream_t>(stream));
@@ -728,7 +728,7 @@ tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_
         if (a >= b) break;
         if (cudaMemcpyAsync(Sd + a * col_bytes, Sh + a * col_bytes, (b - a) * col_bytes, cudaMemcpyHostToDevice, sin) !=
                 cudaSuccess ||
-            (o.start == TPF_START_GIVEN && cudaMemcpyAsync(Vd + a * col_bytes, Vh + a * col_bytes, (b - a) * col_bytes,
+            (o.start != TPF_START_FLAT && cudaMemcpyAsync(Vd + a * col_bytes, Vh + a * col_bytes, (b - a) * col_bytes,
                                                            cudaMemcpyHostToDevice, sin) != cudaSuccess) ||
             cudaEventRecord(ev[2 * c], sin) != cudaSuccess) {
             cleanup();

@@ -46,9 +46,10 @@ namespace {
 // Elementwise kernels
 // ------------------------------------------------------------------------------------------
 
-// Split S (and V_0) into double-float planes with padded rows; one block per column.
+// Split S (and V_0) into double-float planes with padded rows; one block per column.  A warm start
+// (v0_lo == 0) keeps only fl32(V_0): its FP32 sweeps run on the high plane.
 __global__ void mx_pack(int64_t T, int n, int n_pad, const double2 *__restrict__ S, const double2 *__restrict__ V0,
-                        float2 *Shi, float2 *Slo, float2 *Vhi, float2 *Vlo, int *flags, int *iters,
+                        int v0_lo, float2 *Shi, float2 *Slo, float2 *Vhi, float2 *Vlo, int *flags, int *iters,
                         unsigned *delta, unsigned *dprev) {
     const int64_t t = blockIdx.x;
     for (int i = threadIdx.x; i < n_pad; i += blockDim.x) {
@@ -60,7 +61,8 @@ __global__ void mx_pack(int64_t T, int n, int n_pad, const double2 *__restrict__
             if (V0) {
                 double2 v = V0[t * n + i];
                 vh = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
-                vl = make_float2(__double2float_rn(v.x - (double)vh.x), __double2float_rn(v.y - (double)vh.y));
+                if (v0_lo)
+                    vl = make_float2(__double2float_rn(v.x - (double)vh.x), __double2float_rn(v.y - (double)vh.y));
             }
         }
         const int64_t k = t * n_pad + i;
@@ -126,7 +128,8 @@ tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t
     TPF_CK(cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, st));
     timer.begin(KernelTimer::kOther);
     mx_pack<<<(unsigned)cols, 256, 0, st>>>(T, n, n_pad, (const double2 *)S,
-                                             o.start == TPF_START_GIVEN ? (const double2 *)V : nullptr, w.Shi, w.Slo,
+                                             o.start != TPF_START_FLAT ? (const double2 *)V : nullptr,
+                                             o.start == TPF_START_GIVEN, w.Shi, w.Slo,
                                              w.Vhi, w.Vlo, w.flags, w.iters, w.delta_bits, w.dprev);
     timer.end();
     ++launches;

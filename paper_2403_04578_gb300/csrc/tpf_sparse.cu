@@ -78,7 +78,9 @@ struct TreeArgs {
     const TreeWork *works;  // n_works entries, sorted by col0; null: the single feeder `one`
     TreeWork one;
     int n_works;
-    int max_iter, given;
+    int max_iter;
+    int given;  // V_0 is read from V0 (a given or warm start)
+    int blind;  // ... and anchored at once, its low words kept (a given start)
     float tol2, switch_tol, switch_tol2;  // squared tolerances compare with squared steps
     int *counters;                        // [5] largest per-column sweep count, [6] largest anchor count
 };
@@ -450,15 +452,17 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 && (kZip || kPh > 1) ? 
                 } else {
                     const double2 v = static_cast<const double2 *>(a.V0)[k];
                     vr[j] = make_float2(__double2float_rn(v.x), __double2float_rn(v.y));
-                    dl[j] = make_float2(__double2float_rn(v.x - (double)vr[j].x),
-                                        __double2float_rn(v.y - (double)vr[j].y));
+                    if (g.blind)  // a warm start runs FP32 sweeps on fl32(V_0) first
+                        dl[j] = make_float2(__double2float_rn(v.x - (double)vr[j].x),
+                                            __double2float_rn(v.y - (double)vr[j].y));
                 }
             }
         }
     }
     __syncthreads();
-    // A given start is anchored at once ("blind"), and anchored again when the step is small.
-    bool anchored = g.given != 0, blind = anchored, anchor_now = anchored, done = false, conv = false;
+    // A given start is anchored at once ("blind"), and anchored again when the step is small; a
+    // warm start (an approximate V_0) takes FP32 sweeps first, like the flat start.
+    bool anchored = g.blind != 0, blind = anchored, anchor_now = anchored, done = false, conv = false;
     int it = 0, anchors = 0;
     float dprev2 = 0.0f;
     // Each sweep's block-wide max |step| (and max |delta|) is reduced within the warp at the end
@@ -913,7 +917,8 @@ tpf_status launch_tree(int bpt, int threads, bool zip, int phases, int64_t cols,
 TreeArgs args_of(const tpf_opts &o) {
     TreeArgs g{};
     g.max_iter = o.max_iter;
-    g.given = o.start == TPF_START_GIVEN;
+    g.given = o.start != TPF_START_FLAT;
+    g.blind = o.start == TPF_START_GIVEN;
     const float tol = (float)o.tol, sw = (float)o.switch_tol;
     g.tol2 = tol * tol;
     g.switch_tol = sw;

@@ -17,7 +17,7 @@ from . import build as _build
 OK, EINVAL, ESINGULAR, ENOMEM, ECUDA, ETIMEOUT, ENOCONV, EUNSUPPORTED = range(8)
 PREC_FP64, PREC_MIXED = 0, 1
 METHOD_DENSE, METHOD_SPARSE = 0, 1
-START_FLAT, START_GIVEN = 0, 1
+START_FLAT, START_GIVEN, START_WARM = 0, 1, 2
 
 # Every entry point declared in include/tpf.h.
 EXPORTS = (
@@ -162,7 +162,7 @@ def make_opts(precision: str | int = "mixed", tol: float = 1e-10, max_iter: int 
     o.tol = float(tol)
     o.max_iter = int(max_iter)
     o.precision = {"fp64": PREC_FP64, "mixed": PREC_MIXED}.get(precision, precision)
-    o.start = {"flat": START_FLAT, "given": START_GIVEN}.get(start, start)
+    o.start = {"flat": START_FLAT, "given": START_GIVEN, "warm": START_WARM}.get(start, start)
     o.switch_tol = float(switch_tol)
     o.profile = 1 if profile else 0
     o.method = {"dense": METHOD_DENSE, "sparse": METHOD_SPARSE}.get(method, method)
@@ -291,7 +291,8 @@ class Feeder:
         """Solve every column of the device tensor S (complex128 [T][n_pq]).
 
         Returns (V, iters, mismatch, status); outputs are allocated when not given.  With
-        ``start='given'`` (default when V is passed) V is read as the starting point.
+        ``start='given'`` (default when V is passed) V is read as the starting point and anchored at
+        once; ``start='warm'`` reads it as an approximate start (FP32 sweeps first).
         """
         import torch
 
@@ -340,7 +341,7 @@ class Feeder:
             start = "given" if V is not None else "flat"
         v32 = (S.dtype == torch.complex64) if v_complex64 is None else bool(v_complex64)
         vdt = torch.complex64 if v32 else torch.complex128
-        if V is None and (want_V or start == "given"):
+        if V is None and (want_V or start in ("given", "warm")):
             V = torch.empty(S.shape, dtype=vdt, device=dev)
         if V is not None and (V.dtype != vdt or V.shape != S.shape or not V.is_contiguous()):
             raise ValueError("V must be contiguous, shaped like S, complex64 iff v_complex64")

@@ -128,6 +128,12 @@ def test_learned_start_saves_sweeps(cuda, feeder200):
     assert np.abs(V_l.cpu().numpy() - Vo).max() <= 1e-8
     assert np.abs(V_f.cpu().numpy() - Vo).max() <= 1e-8
     assert it_l.float().mean().item() < it_f.float().mean().item() - 1.0
+    # The sparse formulation from the prediction as a warm start (FP32 sweeps first, one anchor).
+    V_w, it_w, _, st_w = fd.solve(S_ev, V=V0.clone(), precision="mixed", tol=1e-10, method="sparse", start="warm")
+    V_s, it_s, _, st_s = fd.solve(S_ev, precision="mixed", tol=1e-10, method="sparse")
+    assert st_w == tpf.OK and st_s == tpf.OK
+    assert np.abs(V_w.cpu().numpy() - Vo).max() <= 1e-8
+    assert it_w.float().mean().item() < it_s.float().mean().item() - 1.0
     net.close()
     fd.close()
     torch.cuda.synchronize()

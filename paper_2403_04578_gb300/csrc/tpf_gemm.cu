@@ -13,6 +13,7 @@
 // Every wait is bounded (2 s on %globaltimer): on expiry the CTA raises an error flag, stops,
 // waits for its own copies and MMAs (again bounded), frees TMEM and returns.
 #include <cudaTypedefs.h>
+#include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
 #include <cstring>
@@ -314,7 +315,21 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         ep.Dr[nn * ep.ldD + m] = __uint_as_float(vr[q]);
                         if constexpr (CPLX) ep.Di[nn * ep.ldD + m] = __uint_as_float(vi[q]);
                     }
-                } else if constexpr (CPLX) {
+                } else if constexpr (!CPLX) {
+                    // Layer output of this lane's unit m for 32 columns: bias, then GELU (erf form).
+                    const bool live = m < ep.real;
+                    const float bm = live ? ep.bias[m] : 0.0f;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int64_t k = (n_tile * kTileN + cb * 32 + q) * ep.ldD + m;
+                        const float z = live ? __uint_as_float(vr[q]) + bm : 0.0f;
+                        if (ep.Dr) ep.Dr[k] = z;
+                        if (ep.Ab) {
+                            const float a = ep.gelu ? 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)) : z;
+                            ep.Ab[k] = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+                        }
+                    }
+                } else {
                     // Update V of this lane's bus for 32 columns (loads first, then stores), then a
                     // transposed butterfly: after 31 shuffles lane l holds max_rows |dV| of column
                     // cb*32 + l.
@@ -429,7 +444,8 @@ tpf_status launch_gemm(const GemmMaps &maps, int m_tiles, int64_t n_tiles, int n
         }
         attr = true;
     }
-    if (!ep.cplx && ep.mode != 0) return TPF_EINVAL;
+    if (ep.cplx ? ep.mode == 2 : ep.mode == 1) return TPF_EINVAL;
+    if (ep.mode == 2 && (!ep.bias || (!ep.Dr && !ep.Ab))) return TPF_EINVAL;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
         cudaGetLastError();

@@ -9,7 +9,8 @@ namespace tpf {
 
 // What the GEMM epilogue does with D = A B^T (one 128 x 128 tile per accumulator stage).
 struct GemmEpi {
-    int mode;  // 0 = store D (FP32), 1 = fixed-point update of V (complex only)
+    int mode;  // 0 = store D (FP32), 1 = fixed-point update of V (complex only), 2 = bias and
+               // activation of a network layer (real only)
     int cplx;  // 1: A, B, D complex (four real-plane MMAs per K step); 0: real (one MMA)
     int bf16;  // operand format: 0 = fp16, 1 = bf16
     int *err;  // set to 1 when a bounded wait expires
@@ -21,6 +22,12 @@ struct GemmEpi {
     const int *flags, *rexp, *tile_active;
     float2 *Vhi, *Vlo;
     unsigned *delta;
+    // mode 2: z = D + bias[m] for rows m < real (z = 0 beyond); Dr[n][m] = z when Dr is set, and
+    // Ab[n][m] = bf16(gelu(z)) (gelu != 0) or bf16(z) when Ab is set (16-bit words), both with
+    // leading dimension ldD
+    const float *bias;
+    int real, gelu;
+    unsigned short *Ab;
 };
 
 // Tensor maps of the four fp16 operand planes: A (K) [M][K] and B (rho) [N][K], K fastest.

@@ -13,6 +13,7 @@
 // to multiples of 128 and the batch to a multiple of 128; padded units stay exactly zero.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -64,22 +65,42 @@ __device__ __forceinline__ float gelu_grad(float z) {
     return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
 }
 
-// Features of columns t0..t0+B-1 (rows beyond T are zero): x = (f - mean) / std.
+// The elementwise kernels run on a 2-D grid: x over the features (or units) of a column, y over
+// the columns b of the batch (grid-stride), so that no thread divides an index.
+//
+// Features of columns t0..t0+B-1 (rows beyond T are zero): x = (f - mean) / std, feature j < n
+// is Re S_j and feature n + j is Im S_j; features 2n .. P-1 are padding (zero).  Thread j reads
+// S_j once and writes both of its features, and zeroes padding feature 2n + j.
 __global__ void k_features(const double2 *__restrict__ S, int64_t T, int64_t t0, int B, int n, int P,
                            const float *__restrict__ mean, const float *__restrict__ sd, bf16 *X, bf16 *XT) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)B * P) return;
-    const int b = (int)(idx / P), j = (int)(idx % P);
-    const int64_t t = t0 + b;
-    float x = 0.0f;
-    if (t < T && j < 2 * n) {
-        const double2 s = S[t * n + (j < n ? j : j - n)];
-        const float f = (float)(j < n ? s.x : s.y);
-        x = sd[j] > 0.0f ? (f - mean[j]) / sd[j] : 0.0f;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool feat = j < n, pad = j < P - 2 * n;
+    if (!feat && !pad) return;
+    const float mr = feat ? mean[j] : 0.0f, dr = feat ? sd[j] : 0.0f;
+    const float mi = feat ? mean[n + j] : 0.0f, di = feat ? sd[n + j] : 0.0f;
+    const bf16 zero = __float2bfloat16_rn(0.0f);
+    for (int b = blockIdx.y; b < B; b += gridDim.y) {
+        const int64_t t = t0 + b;
+        if (feat) {
+            float xr = 0.0f, xi = 0.0f;
+            if (t < T) {
+                const double2 s = S[t * n + j];
+                xr = dr > 0.0f ? ((float)s.x - mr) / dr : 0.0f;
+                xi = di > 0.0f ? ((float)s.y - mi) / di : 0.0f;
+            }
+            const bf16 vr = __float2bfloat16_rn(xr), vi = __float2bfloat16_rn(xi);
+            X[(int64_t)b * P + j] = vr;
+            X[(int64_t)b * P + n + j] = vi;
+            if (XT) {
+                XT[(int64_t)j * B + b] = vr;
+                XT[(int64_t)(n + j) * B + b] = vi;
+            }
+        }
+        if (pad) {
+            X[(int64_t)b * P + 2 * n + j] = zero;
+            if (XT) XT[(int64_t)(2 * n + j) * B + b] = zero;
+        }
     }
-    const bf16 v = __float2bfloat16_rn(x);
-    X[idx] = v;
-    if (XT) XT[(int64_t)j * B + b] = v;
 }
 
 // Normalised targets: (Re V - 1, Im V).
@@ -98,18 +119,22 @@ __global__ void k_targets(const double2 *__restrict__ V, int64_t T, int64_t t0, 
     Y[idx] = y;
 }
 
-// z += b; a = gelu(z) (hidden) or z (output); padded units forced to zero.
+// z += b; a = gelu(z) (hidden) or z (output); padded units forced to zero.  AT (the transposed
+// activations, for the weight gradients) may be null.
 __global__ void k_act_fwd(float *Z, const float *__restrict__ bias, int B, int P, int real, int hidden, bf16 *A,
                           bf16 *AT) {
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= (int64_t)B * P) return;
-    const int b = (int)(idx / P), o = (int)(idx % P);
-    float z = o < real ? Z[idx] + bias[o] : 0.0f;
-    Z[idx] = z;
-    if (hidden) {
-        const bf16 a = __float2bfloat16_rn(o < real ? gelu(z) : 0.0f);
-        A[idx] = a;
-        AT[(int64_t)o * B + b] = a;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= P) return;
+    const float bo = o < real ? bias[o] : 0.0f;
+    for (int b = blockIdx.y; b < B; b += gridDim.y) {
+        const int64_t idx = (int64_t)b * P + o;
+        const float z = o < real ? Z[idx] + bo : 0.0f;
+        Z[idx] = z;
+        if (hidden) {
+            const bf16 a = __float2bfloat16_rn(o < real ? gelu(z) : 0.0f);
+            A[idx] = a;
+            if (AT) AT[(int64_t)o * B + b] = a;
+        }
     }
 }
 
@@ -242,6 +267,7 @@ __global__ void k_norm_stats(const double2 *__restrict__ S, const double2 *__res
 
 // Denormalise the prediction of columns t0..t0+B-1 into V_0; one warp per column.  A column
 // whose predicted |V_i| leaves [lo, hi] anywhere (or is not finite) gets the flat start instead.
+// The prediction is an approximate start: it is formed in FP32 (the iteration refines it).
 __global__ void k_predict_out(const float *__restrict__ Y, int B, int P, int n, int64_t T, int64_t t0,
                               const float *__restrict__ mean, const float *__restrict__ sd, float lo, float hi,
                               double2 *V0, int *fallback) {
@@ -250,11 +276,11 @@ __global__ void k_predict_out(const float *__restrict__ Y, int B, int P, int n, 
     const int64_t t = t0 + b;
     bool ok = true;
     for (int i = lane; i < n; i += 32) {
-        const double re = 1.0 + (double)(Y[(int64_t)b * P + i] * sd[i] + mean[i]);
-        const double im = (double)(Y[(int64_t)b * P + n + i] * sd[n + i] + mean[n + i]);
-        const double mag = sqrt(re * re + im * im);
-        if (!(mag >= lo && mag <= hi)) ok = false;
-        V0[t * n + i] = make_double2(re, im);
+        const float re = 1.0f + (Y[(int64_t)b * P + i] * sd[i] + mean[i]);
+        const float im = Y[(int64_t)b * P + n + i] * sd[n + i] + mean[n + i];
+        const float mag2 = re * re + im * im;
+        if (!(mag2 >= lo * lo && mag2 <= hi * hi)) ok = false;
+        V0[t * n + i] = make_double2((double)re, (double)im);
     }
     ok = __all_sync(0xffffffffu, ok);
     if (!ok) {
@@ -276,6 +302,26 @@ tpf_status gemm_bf16(const void *A, int M, int K, const void *B, int N, float *D
     ep.err = err;
     ep.Dr = D;
     ep.ldD = M;
+    return launch_gemm(maps, M / kTileM, N / kTileN, K / kChunkK, ep, st);
+}
+
+// The same product with the layer's bias and activation in the epilogue: z = D + bias for the
+// first `real` rows; Z (FP32, may be null) receives z, Ab (may be null) bf16(gelu(z)) or bf16(z).
+tpf_status gemm_bf16_layer(const void *A, int M, int K, const void *B, int N, const float *bias, int real, bool gelu,
+                           float *Z, bf16 *Ab, int *err, cudaStream_t st) {
+    GemmMaps maps;
+    if (!make_gemm_maps(&maps, A, nullptr, M, K, B, nullptr, N, true)) return TPF_ECUDA;
+    GemmEpi ep{};
+    ep.mode = 2;
+    ep.cplx = 0;
+    ep.bf16 = 1;
+    ep.err = err;
+    ep.Dr = Z;
+    ep.ldD = M;
+    ep.bias = bias;
+    ep.real = real;
+    ep.gelu = gelu ? 1 : 0;
+    ep.Ab = reinterpret_cast<unsigned short *>(Ab);
     return launch_gemm(maps, M / kTileM, N / kTileN, K / kChunkK, ep, st);
 }
 
@@ -315,17 +361,29 @@ tpf_status publish(tpf_mlp *h, cudaStream_t st) {
     return TPF_OK;
 }
 
+// 2-D grid of the elementwise kernels for B columns of P features or units.
+dim3 grid2(int P, int B) { return dim3((unsigned)((P + kThreads - 1) / kThreads), (unsigned)std::min(B, 4096)); }
+
 // Forward pass of B columns whose features are in X0; leaves Z[L-1] = normalised prediction.
-tpf_status forward(tpf_mlp *h, int B, cudaStream_t st) {
+// Training also keeps every layer's Z and writes the transposed activations that the weight
+// gradients read (a pass of its own); inference takes bias and GELU in the product's epilogue.
+tpf_status forward(tpf_mlp *h, int B, cudaStream_t st, bool train) {
     const bf16 *in = h->X0;
     for (int l = 0; l < h->L; ++l) {
         const int Po = h->pad[l + 1], Pi = h->pad[l];
+        const bool hidden = l < h->L - 1;
+        if (!train) {
+            tpf_status rs = gemm_bf16_layer(h->Wb[l], Po, Pi, in, B, h->b[l], h->dim[l + 1], hidden,
+                                            hidden ? nullptr : h->Z[l], hidden ? h->A[l] : nullptr, h->err, st);
+            if (rs != TPF_OK) return rs;
+            in = hidden ? h->A[l] : nullptr;
+            continue;
+        }
         tpf_status rs = gemm_bf16(h->Wb[l], Po, Pi, in, B, h->Z[l], h->err, st);
         if (rs != TPF_OK) return rs;
-        const bool hidden = l < h->L - 1;
-        k_act_fwd<<<blocks((int64_t)B * Po), kThreads, 0, st>>>(h->Z[l], h->b[l], B, Po, h->dim[l + 1], hidden,
-                                                                hidden ? h->A[l] : nullptr,
-                                                                hidden ? h->AT[l] : nullptr);
+        k_act_fwd<<<grid2(Po, B), kThreads, 0, st>>>(h->Z[l], h->b[l], B, Po, h->dim[l + 1], hidden,
+                                                     hidden ? h->A[l] : nullptr,
+                                                     hidden && train ? h->AT[l] : nullptr);
         MLP_CK(cudaGetLastError());
         in = hidden ? h->A[l] : nullptr;
     }
@@ -359,9 +417,8 @@ tpf_status backward(tpf_mlp *h, int B, cudaStream_t st) {
 
 tpf_status load_batch(tpf_mlp *h, int B, const void *S, const void *V, int64_t T, int64_t t0, bool transpose,
                       cudaStream_t st) {
-    k_features<<<blocks((int64_t)B * h->pad[0]), kThreads, 0, st>>>((const double2 *)S, T, t0, B, h->n, h->pad[0],
-                                                                    h->in_mean, h->in_std, h->X0,
-                                                                    transpose ? h->X0T : nullptr);
+    k_features<<<grid2(std::max(h->n, h->pad[0] - 2 * h->n), B), kThreads, 0, st>>>(
+        (const double2 *)S, T, t0, B, h->n, h->pad[0], h->in_mean, h->in_std, h->X0, transpose ? h->X0T : nullptr);
     if (V)
         k_targets<<<blocks((int64_t)B * h->pad[h->L]), kThreads, 0, st>>>(
             (const double2 *)V, T, t0, B, h->n, h->pad[h->L], h->out_mean, h->out_std, h->target);
@@ -550,7 +607,7 @@ tpf_status tpf_mlp_gradients(tpf_mlp *h, int B, const void *S_dev, const void *V
     cudaStream_t st = (cudaStream_t)stream;
     MLP_CK(cudaMemsetAsync(h->err, 0, sizeof(int), st));
     tpf_status rs = load_batch(h, B, S_dev, V_dev, B, 0, true, st);
-    if (rs == TPF_OK) rs = forward(h, B, st);
+    if (rs == TPF_OK) rs = forward(h, B, st, true);
     if (rs == TPF_OK) rs = backward(h, B, st);
     if (rs == TPF_OK) rs = check_err(h, st);
     if (rs != TPF_OK) return rs;
@@ -566,7 +623,7 @@ tpf_status tpf_mlp_train_step(tpf_mlp *h, int B, const void *S_dev, const void *
     cudaStream_t st = (cudaStream_t)stream;
     MLP_CK(cudaMemsetAsync(h->err, 0, sizeof(int), st));
     tpf_status rs = load_batch(h, B, S_dev, V_dev, B, 0, true, st);
-    if (rs == TPF_OK) rs = forward(h, B, st);
+    if (rs == TPF_OK) rs = forward(h, B, st, true);
     if (rs == TPF_OK) rs = backward(h, B, st);
     if (rs != TPF_OK) return rs;
     const int64_t k = ++h->step;
@@ -602,7 +659,7 @@ tpf_status tpf_mlp_predict(tpf_mlp *h, int64_t T, const void *S_dev, void *V0_de
     const int B = h->max_batch;
     for (int64_t t0 = 0; t0 < T; t0 += B) {
         tpf_status rs = load_batch(h, B, S_dev, nullptr, T, t0, false, st);
-        if (rs == TPF_OK) rs = forward(h, B, st);
+        if (rs == TPF_OK) rs = forward(h, B, st, false);
         if (rs != TPF_OK) return rs;
         k_predict_out<<<(B * 32 + kThreads - 1) / kThreads, kThreads, 0, st>>>(
             h->Z[h->L - 1], B, h->pad[h->L], h->n, T, t0, h->out_mean, h->out_std, 0.7f, 1.1f, (double2 *)V0_dev,

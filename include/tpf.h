@@ -36,6 +36,7 @@ extern "C" {
 #endif
 
 typedef struct tpf_handle tpf_handle;
+typedef struct tpf_batch tpf_batch;   /* a prepared batch of feeders (tpf_batch_create) */
 
 typedef enum {
     TPF_OK = 0,
@@ -269,6 +270,28 @@ tpf_status tpf_solve_batch(int F, tpf_handle *const *hs, const int64_t *T, const
                            void *const *V_dev, int32_t *const *iters_dev, double *const *mismatch_dev,
                            const tpf_opts *opts, int64_t *converged_out, tpf_stats *stats_out,
                            void *stream);
+
+/*
+ * A prepared batch (Sec. V, one submission for many feeders): the arguments of tpf_solve_batch,
+ * fixed once, with every feeder radial and opts->method == TPF_METHOD_SPARSE,
+ * opts->precision == TPF_PREC_MIXED (else TPF_EUNSUPPORTED).  tpf_batch_create uploads the work
+ * table and captures one solve of all feeders (counter reset, one kernel per launch shape, copy of
+ * the counts to pinned host memory) as a CUDA graph; tpf_batch_launch replays it on `stream` with
+ * one graph launch and returns at once; tpf_batch_wait blocks until that replay has finished and
+ * fills converged_out (F entries, may be NULL) and stats_out (may be NULL), returning TPF_OK when
+ * every column met tol, TPF_ENOCONV otherwise, TPF_EINVAL when nothing was launched.
+ * Each replay reads the current contents of S (and V for a given or warm start) and writes V,
+ * iters and mismatch, so new loads are solved by rewriting S in place and launching again.  The
+ * handles and all tensors must outlive the batch.  A feeder whose layout changed since creation
+ * (tpf_autotune, tpf_set_zip) makes tpf_batch_launch return TPF_EINVAL.  A second launch waits
+ * for the first to finish.  tpf_batch_destroy(NULL) is a no-op.
+ */
+tpf_status tpf_batch_create(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S_dev,
+                            void *const *V_dev, int32_t *const *iters_dev, double *const *mismatch_dev,
+                            const tpf_opts *opts, tpf_batch **out);
+tpf_status tpf_batch_launch(tpf_batch *b, void *stream);
+tpf_status tpf_batch_wait(tpf_batch *b, int64_t *converged_out, tpf_stats *stats_out);
+void tpf_batch_destroy(tpf_batch *b);
 
 /*
  * Learned warm start.  The paper starts Algorithm 1 from the flat profile V_0 = 1; these entry

@@ -45,6 +45,7 @@ __global__ void k_to_fp16(const double *__restrict__ K, int n, int n_pad, float 
 tpf_status layout_tree(tpf_handle *h, int bpt) {
     const Network &net = h->net;
     DeviceNet &d = h->dev;
+    ++d.layout_gen;
     const int n = net.n_pq;
     cudaFree(d.t_col); cudaFree(d.t_end); cudaFree(d.t_par); cudaFree(d.t_ecnt); cudaFree(d.t_ends); cudaFree(d.t_z);
     cudaFree(d.t_zrow); cudaFree(d.t_yrow); cudaFree(d.t_kidx);
@@ -217,6 +218,7 @@ tpf_status ensure_dense(tpf_handle *h) {
 tpf_status set_zip(tpf_handle *h, const double *alpha) {
     DeviceNet &d = h->dev;
     if (d.phases > 1) return alpha ? TPF_EUNSUPPORTED : TPF_OK;
+    ++d.layout_gen;
     cudaFree(d.zip64);
     cudaFree(d.t_zip_hi);
     cudaFree(d.t_zip_lo);

@@ -551,6 +551,42 @@ tpf_status tpf_solve(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev, i
     return tpf::solve_mixed(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
 }
 
+tpf_status tpf_batch_create(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S_dev,
+                            void *const *V_dev, int32_t *const *iters_dev, double *const *mismatch_dev,
+                            const tpf_opts *opts, tpf_batch **out) {
+    if (!out) return TPF_EINVAL;
+    *out = nullptr;
+    if (F < 1 || !hs || !T || !S_dev || !V_dev) return TPF_EINVAL;
+    tpf_opts o;
+    tpf_status st = check_opts(opts, o);
+    if (st != TPF_OK) return st;
+    for (int f = 0; f < F; ++f) {
+        if (!hs[f] || T[f] < 0 || (T[f] > 0 && (!S_dev[f] || !V_dev[f]))) return TPF_EINVAL;
+        if (hs[f]->device != hs[0]->device) return TPF_EINVAL;
+        for (int g = 0; g < f; ++g)
+            if (hs[g] == hs[f]) return TPF_EINVAL;
+    }
+    if (o.method != TPF_METHOD_SPARSE || o.precision != TPF_PREC_MIXED) return TPF_EUNSUPPORTED;
+    for (int f = 0; f < F; ++f)
+        if (!hs[f]->dev.radial || hs[f]->dev.t_threads <= 0) return TPF_EUNSUPPORTED;
+    if (cudaSetDevice(hs[0]->device) != cudaSuccess) return TPF_ECUDA;
+    return tpf::batch_plan_create(F, hs, T, S_dev, V_dev, iters_dev, mismatch_dev, o, out);
+}
+
+tpf_status tpf_batch_launch(tpf_batch *b, void *stream) {
+    if (!b) return TPF_EINVAL;
+    if (cudaSetDevice(tpf::batch_device(b)) != cudaSuccess) return TPF_ECUDA;
+    return tpf::batch_plan_launch(b, reinterpret_cast<cudaStream_t>(stream));
+}
+
+tpf_status tpf_batch_wait(tpf_batch *b, int64_t *converged_out, tpf_stats *stats_out) {
+    if (!b) return TPF_EINVAL;
+    if (cudaSetDevice(tpf::batch_device(b)) != cudaSuccess) return TPF_ECUDA;
+    return tpf::batch_plan_wait(b, converged_out, stats_out);
+}
+
+void tpf_batch_destroy(tpf_batch *b) { tpf::batch_plan_destroy(b); }
+
 tpf_status tpf_autotune(tpf_handle *h, int64_t T, const void *S_dev, const tpf_opts *opts, int *bpt_out,
                         void *stream) {
     if (!h || T <= 0 || !S_dev) return TPF_EINVAL;

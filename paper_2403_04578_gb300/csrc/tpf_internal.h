@@ -123,6 +123,9 @@ struct DeviceNet {
     // Mixed path: fp16 planes of K * 2^k_exp, [n_pad][n_pad], zero padded
     void *Kr16 = nullptr, *Ki16 = nullptr;
     int k_exp = 0;
+    // Incremented whenever the sparse layout or the ZIP coefficients are replaced: a prepared
+    // batch (tpf_batch) that captured the old device arrays then refuses to launch.
+    int layout_gen = 0;
 };
 
 // Workspaces of a solve, grown on demand.
@@ -240,6 +243,15 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
 tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S,
                               void *const *V, int32_t *const *iters, double *const *mismatch,
                               const tpf_opts &o, int64_t *conv_out, tpf_stats *stats, cudaStream_t st);
+// A prepared batch of radial feeders under the sparse method (arguments checked by the caller):
+// its work table on the device and a CUDA graph of one solve of all of them.
+tpf_status batch_plan_create(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S,
+                             void *const *V, int32_t *const *iters, double *const *mismatch,
+                             const tpf_opts &o, tpf_batch **out);
+tpf_status batch_plan_launch(tpf_batch *b, cudaStream_t st);
+tpf_status batch_plan_wait(tpf_batch *b, int64_t *conv_out, tpf_stats *stats);
+void batch_plan_destroy(tpf_batch *b);
+int batch_device(const tpf_batch *b);
 tpf_status selftest_gemm(int M, int N, int K, const void *Ar, const void *Ai, const void *Br,
                          const void *Bi, float *Dr, float *Di, cudaStream_t st);
 }  // namespace tpf

@@ -29,6 +29,9 @@
 // positions fall in consecutive banks.  Device memory is read for S once (again at an anchor) and
 // written once for V.
 #include <algorithm>
+#include <new>
+#include <tuple>
+#include <vector>
 #include <cstdlib>
 #include <limits>
 
@@ -867,11 +870,12 @@ size_t tree_smem(int threads, int bpt, bool zip, int phases) {
            sizeof(short) * 3 * ns;
 }
 
+// cols == 0 only sets the kernel's shared-memory attribute.
 template <int kBPT, bool kZip, int kPh, int kTh = 0>
 cudaError_t launch_tree_t(int threads, int64_t cols, size_t smem, const TreeArgs &g, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(mx_tree<kBPT, kZip, kPh, kTh>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
-    if (e == cudaSuccess) mx_tree<kBPT, kZip, kPh, kTh><<<(unsigned)cols, threads, smem, st>>>(g);
+    if (e == cudaSuccess && cols > 0) mx_tree<kBPT, kZip, kPh, kTh><<<(unsigned)cols, threads, smem, st>>>(g);
     return e;
 }
 
@@ -897,19 +901,22 @@ cudaError_t launch_tree_b(int threads, bool zip, int phases, int64_t cols, size_
     return launch_tree_t<kBPT, false, 1>(threads, cols, smem, g, st);
 }
 
-tpf_status launch_tree(int bpt, int threads, bool zip, int phases, int64_t cols, const TreeArgs &g, cudaStream_t st) {
-    if (cols <= 0) return TPF_OK;
+// prepare: set the kernel's attributes only (before a stream capture), launch nothing.
+tpf_status launch_tree(int bpt, int threads, bool zip, int phases, int64_t cols, const TreeArgs &g, cudaStream_t st,
+                       bool prepare = false) {
+    if (cols <= 0 && !prepare) return TPF_OK;
     if (cols > 0x7fffffff) return TPF_EUNSUPPORTED;  // one block per column
     if (phases != 1 && (phases != 3 || zip)) return TPF_EUNSUPPORTED;
     const size_t smem = tree_smem(threads, bpt, zip, phases);
     if (smem > 227 * 1024) return TPF_EUNSUPPORTED;
     cudaError_t e;
+    const int64_t c = prepare ? 0 : cols;
     if (bpt == 8)
-        e = launch_tree_b<8>(threads, zip, phases, cols, smem, g, st);
+        e = launch_tree_b<8>(threads, zip, phases, c, smem, g, st);
     else if (bpt == 4)
-        e = launch_tree_b<4>(threads, zip, phases, cols, smem, g, st);
+        e = launch_tree_b<4>(threads, zip, phases, c, smem, g, st);
     else
-        e = launch_tree_b<2>(threads, zip, phases, cols, smem, g, st);
+        e = launch_tree_b<2>(threads, zip, phases, c, smem, g, st);
     if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) return TPF_ECUDA;
     return TPF_OK;
 }
@@ -1053,23 +1060,33 @@ tpf_status autotune_sparse(tpf_handle *h, int64_t T, const void *S, const tpf_op
     return TPF_OK;
 }
 
-tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S, void *const *V,
-                              int32_t *const *iters, double *const *mismatch, const tpf_opts &o, int64_t *conv_out,
-                              tpf_stats *stats, cudaStream_t st) {
-    // Group the feeders by launch shape (buses per thread, threads); one launch per group over the
-    // concatenated columns of its feeders.
-    std::vector<int> order(F);
-    for (int f = 0; f < F; ++f) order[f] = f;
-    std::sort(order.begin(), order.end(), [&](int x, int y) {
-        const DeviceNet &a = hs[x]->dev, &b = hs[y]->dev;
-        const int za = a.t_zip_hi != nullptr, zb = b.t_zip_hi != nullptr;
-        if (za != zb) return za < zb;
-        if (a.phases != b.phases) return a.phases < b.phases;
-        return a.t_bpt != b.t_bpt ? a.t_bpt < b.t_bpt : (a.t_threads != b.t_threads ? a.t_threads < b.t_threads : x < y);
+namespace {
+
+// The work table of a batch: feeders grouped by launch shape (buses per thread, threads, ZIP,
+// phases), each group one launch over the concatenated columns of its feeders (col0 relative to
+// the group), and the feeder behind each entry.
+struct BatchLayout {
+    std::vector<TreeWork> works;
+    std::vector<std::pair<int, int>> groups;  // [first, last) in works
+    std::vector<int> order;                   // works[k] belongs to feeder order[k]
+};
+
+BatchLayout batch_layout(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S, void *const *V,
+                         int32_t *const *iters, double *const *mismatch) {
+    BatchLayout L;
+    L.order.resize(F);
+    for (int f = 0; f < F; ++f) L.order[f] = f;
+    auto key = [&](int f) {
+        const DeviceNet &d = hs[f]->dev;
+        return std::make_tuple(d.t_zip_hi != nullptr, d.phases, d.t_bpt, d.t_threads);
+    };
+    std::sort(L.order.begin(), L.order.end(), [&](int x, int y) {
+        const auto kx = key(x), ky = key(y);
+        return kx != ky ? kx < ky : x < y;
     });
-    std::vector<TreeWork> works(F);
+    L.works.resize(F);
     for (int k = 0; k < F; ++k) {
-        const int f = order[k];
+        const int f = L.order[k];
         TreeWork w = work_of(hs[f]);
         w.S = S[f];
         w.V0 = V[f];
@@ -1077,65 +1094,32 @@ tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, co
         w.iters_out = iters ? iters[f] : nullptr;
         w.mismatch_out = mismatch ? mismatch[f] : nullptr;
         w.T = T[f];
-        works[k] = w;
+        L.works[k] = w;
     }
-    // Device copies: the work table and the per-feeder converged counts, plus the counters.
-    const size_t wbytes = sizeof(TreeWork) * F, cbytes = sizeof(int) * ((size_t)F + 8);
-    char *dbuf = nullptr;
-    if (cudaMalloc(&dbuf, wbytes + cbytes) != cudaSuccess) {
-        cudaGetLastError();
-        return TPF_ENOMEM;
-    }
-    TreeWork *dworks = reinterpret_cast<TreeWork *>(dbuf);
-    int *dconv = reinterpret_cast<int *>(dbuf + wbytes), *dcnt = dconv + F;
-    for (int k = 0; k < F; ++k) works[k].conv = dconv + order[k];
-    tpf_status rs = TPF_OK;
-    KernelTimer timer(o.profile != 0, st);
-    int launches = 0;
-    if (cudaMemsetAsync(dconv, 0, cbytes, st) != cudaSuccess) rs = TPF_ECUDA;
-    // Launch-local column offsets are set per group before the table is copied.
-    std::vector<std::pair<int, int>> groups;  // [first, last) in `works`
     for (int k = 0; k < F;) {
         int e = k + 1;
-        while (e < F && hs[order[e]]->dev.t_bpt == hs[order[k]]->dev.t_bpt &&
-               hs[order[e]]->dev.t_threads == hs[order[k]]->dev.t_threads &&
-               (hs[order[e]]->dev.t_zip_hi != nullptr) == (hs[order[k]]->dev.t_zip_hi != nullptr) &&
-               hs[order[e]]->dev.phases == hs[order[k]]->dev.phases)
-            ++e;
+        while (e < F && key(L.order[e]) == key(L.order[k])) ++e;
         int64_t c = 0;
         for (int i = k; i < e; ++i) {
-            works[i].col0 = c;
-            c += works[i].T;
+            L.works[i].col0 = c;
+            c += L.works[i].T;
         }
-        groups.push_back({k, e});
+        L.groups.push_back({k, e});
         k = e;
     }
-    if (rs == TPF_OK && cudaMemcpyAsync(dworks, works.data(), wbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        rs = TPF_ECUDA;
-    TreeArgs g = args_of(o);
-    g.counters = dcnt;
-    for (auto &gr : groups) {
-        if (rs != TPF_OK) break;
-        const DeviceNet &d = hs[order[gr.first]]->dev;
-        int64_t cols = 0;
-        for (int i = gr.first; i < gr.second; ++i) cols += works[i].T;
-        g.works = dworks + gr.first;
-        g.n_works = gr.second - gr.first;
-        timer.begin(KernelTimer::kResidual);
-        rs = launch_tree(d.t_bpt, d.t_threads, d.t_zip_hi != nullptr, d.phases, cols, g, st);
-        timer.end();
-        ++launches;
-    }
-    std::vector<int> hconv(F + 8, 0);
-    if (rs == TPF_OK && (cudaMemcpyAsync(hconv.data(), dconv, cbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                         cudaStreamSynchronize(st) != cudaSuccess))
-        rs = TPF_ECUDA;
-    if (rs != TPF_OK) cudaStreamSynchronize(st);
-    cudaFree(dbuf);
-    if (rs != TPF_OK) {
-        cudaGetLastError();
-        return rs;
-    }
+    return L;
+}
+
+int64_t group_cols(const BatchLayout &L, const std::pair<int, int> &gr) {
+    int64_t cols = 0;
+    for (int i = gr.first; i < gr.second; ++i) cols += L.works[i].T;
+    return cols;
+}
+
+// Per-feeder converged counts (the first F entries of hconv), the largest sweep and anchor counts
+// (entries F + 5 and F + 6) into the caller's outputs; TPF_OK when every column converged.
+tpf_status batch_results(int F, const int64_t *T, const int *hconv, int launches, double kernel_ms,
+                         int64_t *conv_out, tpf_stats *stats) {
     bool all = true;
     int64_t conv = 0, cols = 0;
     for (int f = 0; f < F; ++f) {
@@ -1151,9 +1135,174 @@ tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, co
         stats->converged = conv;
         stats->columns = cols;
         stats->kernel_launches = launches;
-        stats->residual_ms = timer.total_ms(KernelTimer::kResidual);
+        stats->residual_ms = kernel_ms;
     }
     return all ? TPF_OK : TPF_ENOCONV;
+}
+
+}  // namespace
+
+tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S, void *const *V,
+                              int32_t *const *iters, double *const *mismatch, const tpf_opts &o, int64_t *conv_out,
+                              tpf_stats *stats, cudaStream_t st) {
+    BatchLayout L = batch_layout(F, hs, T, S, V, iters, mismatch);
+    // Device copies: the work table and the per-feeder converged counts, plus the counters.
+    const size_t wbytes = sizeof(TreeWork) * F, cbytes = sizeof(int) * ((size_t)F + 8);
+    char *dbuf = nullptr;
+    if (cudaMalloc(&dbuf, wbytes + cbytes) != cudaSuccess) {
+        cudaGetLastError();
+        return TPF_ENOMEM;
+    }
+    TreeWork *dworks = reinterpret_cast<TreeWork *>(dbuf);
+    int *dconv = reinterpret_cast<int *>(dbuf + wbytes), *dcnt = dconv + F;
+    for (int k = 0; k < F; ++k) L.works[k].conv = dconv + L.order[k];
+    tpf_status rs = TPF_OK;
+    KernelTimer timer(o.profile != 0, st);
+    int launches = 0;
+    if (cudaMemsetAsync(dconv, 0, cbytes, st) != cudaSuccess ||
+        cudaMemcpyAsync(dworks, L.works.data(), wbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rs = TPF_ECUDA;
+    TreeArgs g = args_of(o);
+    g.counters = dcnt;
+    for (auto &gr : L.groups) {
+        if (rs != TPF_OK) break;
+        const DeviceNet &d = hs[L.order[gr.first]]->dev;
+        g.works = dworks + gr.first;
+        g.n_works = gr.second - gr.first;
+        timer.begin(KernelTimer::kResidual);
+        rs = launch_tree(d.t_bpt, d.t_threads, d.t_zip_hi != nullptr, d.phases, group_cols(L, gr), g, st);
+        timer.end();
+        ++launches;
+    }
+    std::vector<int> hconv(F + 8, 0);
+    if (rs == TPF_OK && (cudaMemcpyAsync(hconv.data(), dconv, cbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                         cudaStreamSynchronize(st) != cudaSuccess))
+        rs = TPF_ECUDA;
+    if (rs != TPF_OK) cudaStreamSynchronize(st);
+    cudaFree(dbuf);
+    if (rs != TPF_OK) {
+        cudaGetLastError();
+        return rs;
+    }
+    return batch_results(F, T, hconv.data(), launches, timer.total_ms(KernelTimer::kResidual), conv_out, stats);
+}
+
+}  // namespace tpf
+
+// A prepared batch: the work table stays on the device, and one solve of every feeder (reset of
+// the counters, one launch per launch shape, copy of the counts to pinned host memory) is a CUDA
+// graph, replayed by tpf_batch_launch.
+struct tpf_batch {
+    int F = 0, device = 0, launches = 0;
+    std::vector<tpf_handle *> hs;
+    std::vector<int> gens;      // each handle's layout generation when the graph was captured
+    std::vector<int64_t> T;
+    char *dbuf = nullptr;       // work table, converged counts [F], counters [8]
+    int *hcnt = nullptr;        // pinned: the counts and counters of the last replay
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+};
+
+namespace tpf {
+
+int batch_device(const tpf_batch *b) { return b->device; }
+
+void batch_plan_destroy(tpf_batch *b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    if (b->pending && b->done) cudaEventSynchronize(b->done);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->done) cudaEventDestroy(b->done);
+    cudaFree(b->dbuf);
+    if (b->hcnt) cudaFreeHost(b->hcnt);
+    cudaGetLastError();
+    delete b;
+}
+
+tpf_status batch_plan_create(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S, void *const *V,
+                             int32_t *const *iters, double *const *mismatch, const tpf_opts &o, tpf_batch **out) {
+    tpf_batch *b = new (std::nothrow) tpf_batch;
+    if (!b) return TPF_ENOMEM;
+    b->F = F;
+    b->device = hs[0]->device;
+    b->hs.assign(hs, hs + F);
+    b->T.assign(T, T + F);
+    for (int f = 0; f < F; ++f) b->gens.push_back(hs[f]->dev.layout_gen);
+    BatchLayout L = batch_layout(F, hs, T, S, V, iters, mismatch);
+    const size_t wbytes = sizeof(TreeWork) * F, cbytes = sizeof(int) * ((size_t)F + 8);
+    if (cudaMalloc(&b->dbuf, wbytes + cbytes) != cudaSuccess || cudaMallocHost(&b->hcnt, cbytes) != cudaSuccess) {
+        batch_plan_destroy(b);
+        return TPF_ENOMEM;
+    }
+    TreeWork *dworks = reinterpret_cast<TreeWork *>(b->dbuf);
+    int *dconv = reinterpret_cast<int *>(b->dbuf + wbytes), *dcnt = dconv + F;
+    for (int k = 0; k < F; ++k) L.works[k].conv = dconv + L.order[k];
+    tpf_status rs = TPF_OK;
+    if (cudaMemcpy(dworks, L.works.data(), wbytes, cudaMemcpyHostToDevice) != cudaSuccess) rs = TPF_ECUDA;
+    TreeArgs g = args_of(o);
+    g.counters = dcnt;
+    // Kernel attributes first: they are not stream work, so they stay out of the capture.
+    for (auto &gr : L.groups) {
+        if (rs != TPF_OK) break;
+        const DeviceNet &d = hs[L.order[gr.first]]->dev;
+        rs = launch_tree(d.t_bpt, d.t_threads, d.t_zip_hi != nullptr, d.phases, 0, g, nullptr, true);
+    }
+    cudaStream_t cs = nullptr;
+    if (rs == TPF_OK && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rs = TPF_ECUDA;
+    if (rs == TPF_OK && cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        if (cudaMemsetAsync(dconv, 0, cbytes, cs) != cudaSuccess) rs = TPF_ECUDA;
+        for (auto &gr : L.groups) {
+            if (rs != TPF_OK) break;
+            const DeviceNet &d = hs[L.order[gr.first]]->dev;
+            g.works = dworks + gr.first;
+            g.n_works = gr.second - gr.first;
+            const int64_t cols = group_cols(L, gr);
+            rs = launch_tree(d.t_bpt, d.t_threads, d.t_zip_hi != nullptr, d.phases, cols, g, cs);
+            if (cols > 0) ++b->launches;
+        }
+        if (rs == TPF_OK && cudaMemcpyAsync(b->hcnt, dconv, cbytes, cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+            rs = TPF_ECUDA;
+        // The capture always ends, so that the stream leaves capture mode whatever happened.
+        if (cudaStreamEndCapture(cs, &b->graph) != cudaSuccess && rs == TPF_OK) rs = TPF_ECUDA;
+    } else if (rs == TPF_OK) {
+        rs = TPF_ECUDA;
+    }
+    if (rs == TPF_OK && (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess ||
+                         cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming) != cudaSuccess))
+        rs = TPF_ECUDA;
+    if (cs) cudaStreamDestroy(cs);
+    if (rs != TPF_OK) {
+        cudaGetLastError();
+        batch_plan_destroy(b);
+        return rs;
+    }
+    *out = b;
+    return TPF_OK;
+}
+
+tpf_status batch_plan_launch(tpf_batch *b, cudaStream_t st) {
+    for (int f = 0; f < b->F; ++f)
+        if (b->hs[f]->dev.layout_gen != b->gens[f]) return TPF_EINVAL;  // a re-laid-out feeder
+    if (b->pending && cudaEventSynchronize(b->done) != cudaSuccess) return TPF_ECUDA;  // one replay at a time
+    if (cudaGraphLaunch(b->exec, st) != cudaSuccess || cudaEventRecord(b->done, st) != cudaSuccess) {
+        cudaGetLastError();
+        return TPF_ECUDA;
+    }
+    b->pending = true;
+    return TPF_OK;
+}
+
+tpf_status batch_plan_wait(tpf_batch *b, int64_t *conv_out, tpf_stats *stats) {
+    if (!b->pending) return TPF_EINVAL;
+    if (cudaEventSynchronize(b->done) != cudaSuccess) {
+        cudaGetLastError();
+        return TPF_ECUDA;
+    }
+    b->pending = false;
+    return batch_results(b->F, b->T.data(), b->hcnt, b->launches, 0.0, conv_out, stats);
 }
 
 }  // namespace tpf

@@ -22,7 +22,8 @@ START_FLAT, START_GIVEN, START_WARM = 0, 1, 2
 # Every entry point declared in include/tpf.h.
 EXPORTS = (
     "tpf_default_opts", "tpf_strerror", "tpf_create", "tpf_create_poly", "tpf_destroy", "tpf_n_pq", "tpf_precompute_host",
-    "tpf_solve", "tpf_solve_host", "tpf_solve_ex", "tpf_solve_batch", "tpf_set_zip", "tpf_autotune", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
+    "tpf_solve", "tpf_solve_host", "tpf_solve_ex", "tpf_solve_batch", "tpf_batch_create", "tpf_batch_launch",
+    "tpf_batch_wait", "tpf_batch_destroy", "tpf_set_zip", "tpf_autotune", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
     "tpf_mlp_create", "tpf_mlp_destroy", "tpf_mlp_param_count", "tpf_mlp_get_params", "tpf_mlp_set_params",
     "tpf_mlp_fit_normalization", "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients",
     "tpf_mlp_predict",
@@ -110,6 +111,14 @@ def lib(build_if_missing: bool = False):
     L.tpf_solve_batch.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Opts), vp,
                                   ctypes.POINTER(Stats), vp]
     L.tpf_solve_batch.restype = ctypes.c_int
+    L.tpf_batch_create.argtypes = [ctypes.c_int, vp, vp, vp, vp, vp, vp, ctypes.POINTER(Opts), ctypes.POINTER(vp)]
+    L.tpf_batch_create.restype = ctypes.c_int
+    L.tpf_batch_launch.argtypes = [vp, vp]
+    L.tpf_batch_launch.restype = ctypes.c_int
+    L.tpf_batch_wait.argtypes = [vp, vp, ctypes.POINTER(Stats)]
+    L.tpf_batch_wait.restype = ctypes.c_int
+    L.tpf_batch_destroy.argtypes = [vp]
+    L.tpf_batch_destroy.restype = None
     L.tpf_last_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     L.tpf_last_stats.restype = ctypes.c_int
     L.tpf_selftest_gemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
@@ -428,6 +437,69 @@ def solve_batch(feeders, S, V=None, iters=None, mismatch=None, precision="mixed"
     if check and st not in (OK, ENOCONV):
         raise TpfError(st, "tpf_solve_batch")
     return V, iters, mismatch, np.array(conv[:], dtype=np.int64), st_.as_dict(), st
+
+
+class BatchGraph:
+    """tpf_batch_*: a batch of radial feeders prepared once (sparse method, mixed precision) and
+    solved by replaying one captured CUDA graph.  Rewrite the tensors of S in place and call
+    launch() / wait() again to solve new loads.  The feeders and tensors must outlive the object.
+    """
+
+    def __init__(self, feeders, S, V=None, iters=None, mismatch=None, tol=1e-10, max_iter=100, start=None,
+                 switch_tol=1e-4):
+        import torch
+
+        F = len(feeders)
+        if len(S) != F:
+            raise ValueError("one load tensor per feeder")
+        if start is None:
+            start = "given" if V is not None else "flat"
+        self.V = list(V) if V is not None else [torch.empty_like(s) for s in S]
+        self.iters = list(iters) if iters is not None else [
+            torch.empty(s.shape[0], dtype=torch.int32, device=s.device) for s in S]
+        self.mismatch = list(mismatch) if mismatch is not None else [
+            torch.empty(s.shape[0], dtype=torch.float64, device=s.device) for s in S]
+        for f in range(F):
+            s = S[f]
+            if not (isinstance(s, torch.Tensor) and s.is_cuda and s.dtype == torch.complex128 and s.dim() == 2
+                    and s.shape[1] == feeders[f].n_pq and s.is_contiguous()):
+                raise ValueError(f"S[{f}] must be a contiguous CUDA complex128 [T, n_pq] tensor")
+        self.F, self.S, self.feeders = F, list(S), list(feeders)
+        P = ctypes.c_void_p * F
+        hs = P(*[fd._h.value for fd in feeders])
+        Ts = (ctypes.c_int64 * F)(*[int(s.shape[0]) for s in S])
+        o = make_opts("mixed", tol, max_iter, start, switch_tol, False, "sparse")
+        self._b = ctypes.c_void_p()
+        st = lib().tpf_batch_create(F, hs, Ts, P(*[s.data_ptr() for s in S]), P(*[v.data_ptr() for v in self.V]),
+                                    P(*[i.data_ptr() for i in self.iters]), P(*[m.data_ptr() for m in self.mismatch]),
+                                    ctypes.byref(o), ctypes.byref(self._b))
+        if st != OK:
+            raise TpfError(st, "tpf_batch_create")
+
+    def launch(self, stream=None):
+        st = lib().tpf_batch_launch(self._b, _stream_ptr(stream))
+        if st != OK:
+            raise TpfError(st, "tpf_batch_launch")
+
+    def wait(self, check=True):
+        """(converged per feeder (numpy int64), stats dict, status) of the last launch."""
+        conv = (ctypes.c_int64 * self.F)()
+        st_ = Stats()
+        st = lib().tpf_batch_wait(self._b, conv, ctypes.byref(st_))
+        if check and st not in (OK, ENOCONV):
+            raise TpfError(st, "tpf_batch_wait")
+        return np.array(conv[:], dtype=np.int64), st_.as_dict(), st
+
+    def close(self):
+        if self._b:
+            lib().tpf_batch_destroy(self._b)
+            self._b = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def solve_fp64_noalloc(K, W, S, V, iters=None, tol=1e-10, max_iter=100, given_start=False, stream=None):

@@ -108,3 +108,53 @@ def test_batch_errors(cuda):
     V, it, mm, conv, stats, st = tpf.solve_batch([], [])
     assert st == tpf.OK and conv.size == 0
     fd.close()
+
+
+def test_batch_graph_replays_match_solve_batch(cuda):
+    """tpf_batch_*: the batch is prepared once and solved by replaying one captured CUDA graph;
+    each replay reads the current loads.  Its results are those of tpf_solve_batch bit for bit."""
+    import torch
+
+    specs = [(2, 7, 1), (35, 129, 3), (130, 96, 4), (20, 0, 6), (700, 96, 7), (57, 288, 9)]
+    feeders, S = _batch(specs)
+    fds = [tpf.Feeder.from_inputs(f) for f in feeders]
+    alpha = np.random.default_rng(2).dirichlet([2, 1, 1], fds[2].n_pq).T.copy()
+    fds[2].set_zip(alpha)  # a ZIP feeder takes a launch of its own
+    Sd = [_dev(s) for s in S]
+    Vr, itr, mmr, convr, _, st = tpf.solve_batch(fds, Sd)
+    assert st == tpf.OK
+    bg = tpf.BatchGraph(fds, Sd)
+    _, _, st = bg.wait(check=False)
+    assert st == tpf.EINVAL  # nothing launched yet
+    for _ in range(2):
+        bg.launch()
+        conv, stats, st = bg.wait()
+        assert st == tpf.OK and list(conv) == list(convr) and stats["converged"] == sum(convr)
+        for f in range(len(fds)):
+            assert torch.equal(bg.V[f], Vr[f]) and torch.equal(bg.iters[f], itr[f])
+            assert torch.equal(bg.mismatch[f], mmr[f])
+    # New loads written in place are solved by the next replay.
+    for s in Sd:
+        s.mul_(0.8)
+    Vr2, itr2, _, convr2, _, _ = tpf.solve_batch(fds, Sd)
+    bg.launch()
+    conv, _, st = bg.wait()
+    assert st == tpf.OK and list(conv) == list(convr2)
+    assert all(torch.equal(bg.V[f], Vr2[f]) and torch.equal(bg.iters[f], itr2[f]) for f in range(len(fds)))
+    # A feeder re-laid out after creation (autotune) makes the launch refuse.
+    fds[4].autotune(Sd[4][:64].contiguous())
+    with pytest.raises(tpf.TpfError) as e:
+        bg.launch()
+    assert e.value.status == tpf.EINVAL
+    bg.close()
+    # Meshed feeders have no tree layout: unsupported.
+    f = feeders[1]
+    fr, to, z = list(f.from_bus), list(f.to_bus), list(f.z_pu)
+    fr.append(5), to.append(30), z.append(0.02 + 0.01j)
+    mesh = tpf.Feeder(f.n_bus, fr, to, z, f.slack, f.v0, f.pq_bus)
+    with pytest.raises(tpf.TpfError) as e:
+        tpf.BatchGraph([mesh], [Sd[1]])
+    assert e.value.status == tpf.EUNSUPPORTED
+    mesh.close()
+    for fd in fds:
+        fd.close()

@@ -90,3 +90,22 @@ def test_create_fails_loudly_without_a_device(tpf_lib):
     with pytest.raises(tpf.TpfError) as e:
         tpf.Feeder.from_inputs(f)
     assert e.value.status == tpf.ECUDA
+
+
+def test_batch_entry_points_argument_errors(tpf_lib):
+    """The prepared-batch entry points reject bad arguments before touching a device."""
+    vp = ctypes.c_void_p
+    out = vp(123)
+    h = (vp * 1)(vp(0))
+    T = (ctypes.c_int64 * 1)(4)
+    ptrs = (vp * 1)(vp(0))
+    o = tpf.Opts()
+    tpf_lib.tpf_default_opts(ctypes.byref(o))
+    assert tpf_lib.tpf_batch_create(1, h, T, ptrs, ptrs, None, None, ctypes.byref(o), None) == tpf.EINVAL
+    assert tpf_lib.tpf_batch_create(0, h, T, ptrs, ptrs, None, None, ctypes.byref(o), ctypes.byref(out)) == tpf.EINVAL
+    assert out.value is None  # cleared on failure
+    assert tpf_lib.tpf_batch_create(1, None, T, ptrs, ptrs, None, None, ctypes.byref(o), ctypes.byref(out)) == tpf.EINVAL
+    assert tpf_lib.tpf_batch_create(1, h, T, ptrs, ptrs, None, None, ctypes.byref(o), ctypes.byref(out)) == tpf.EINVAL
+    assert tpf_lib.tpf_batch_launch(None, None) == tpf.EINVAL
+    assert tpf_lib.tpf_batch_wait(None, None, None) == tpf.EINVAL
+    tpf_lib.tpf_batch_destroy(None)

@@ -48,10 +48,10 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
     ++d.layout_gen;
     const int n = net.n_pq;
     cudaFree(d.t_col); cudaFree(d.t_end); cudaFree(d.t_par); cudaFree(d.t_ecnt); cudaFree(d.t_ends); cudaFree(d.t_z);
-    cudaFree(d.t_zrow); cudaFree(d.t_yrow); cudaFree(d.t_kidx);
+    cudaFree(d.t_zrow); cudaFree(d.t_yrow); cudaFree(d.t_kidx); cudaFree(d.t_zrow_f);
     d.t_col = d.t_end = d.t_par = d.t_ecnt = d.t_ends = d.t_kidx = nullptr;
     d.t_z = d.t_zrow = nullptr;
-    d.t_yrow = nullptr;
+    d.t_yrow = d.t_zrow_f = nullptr;
     d.t_threads = d.t_bpt = 0;
     if (net.radial) {
         // Slot-ordered depth-first arrays of the sparse formulation.
@@ -66,7 +66,7 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
             std::vector<float4> z(ns, make_float4(0.f, 0.f, 0.f, 0.f));
             // Polyphase: row p of the branch's impedance (double-float) and admittance per slot.
             std::vector<float4> zrow(ph > 1 ? (size_t)ns * ph : 0, make_float4(0.f, 0.f, 0.f, 0.f));
-            std::vector<float2> yrow(ph > 1 ? (size_t)ns * ph : 0, make_float2(0.f, 0.f));
+            std::vector<float2> yrow(ph > 1 ? (size_t)ns * ph : 0, make_float2(0.f, 0.f)), zrow_f = yrow;
             std::vector<int> pos_par(n, -1);  // parent position of each position
             for (int q = 0; q < n; ++q)
                 for (int c = q + 1; c < net.dfs_end[q]; c = net.dfs_end[c]) pos_par[c] = q;
@@ -93,6 +93,7 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
                     for (int pp = 0; pp < ph; ++pp) {
                         const size_t k = (size_t)q * ph + pp;
                         zrow[(size_t)s * ph + pp] = dd(net.dfs_zrow[2 * k], net.dfs_zrow[2 * k + 1]);
+                        zrow_f[(size_t)s * ph + pp] = make_float2(zrow[(size_t)s * ph + pp].x, zrow[(size_t)s * ph + pp].y);
                         yrow[(size_t)s * ph + pp] = make_float2((float)net.dfs_yrow[2 * k], (float)net.dfs_yrow[2 * k + 1]);
                     }
                     const float4 zz = zrow[(size_t)s * ph + q / nb];  // the own-phase entry, for z-only uses
@@ -110,7 +111,7 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
                 d.t_threads = 0;
             } else if (!up(&d.t_col, col) || !up(&d.t_end, end) || !up(&d.t_par, par) || !up(&d.t_ecnt, ecnt) ||
                        !up(&d.t_ends, ends) || !up(&d.t_z, z) || !up(&d.t_kidx, kidx) ||
-                       (ph > 1 && (!up(&d.t_zrow, zrow) || !up(&d.t_yrow, yrow)))) {
+                       (ph > 1 && (!up(&d.t_zrow, zrow) || !up(&d.t_yrow, yrow) || !up(&d.t_zrow_f, zrow_f)))) {
                 cudaGetLastError();
                 return TPF_ECUDA;
             }
@@ -259,7 +260,7 @@ void free_device(tpf_handle *h) {
     cudaFree(d.t_col); cudaFree(d.t_end); cudaFree(d.t_par); cudaFree(d.t_ecnt); cudaFree(d.t_ends); cudaFree(d.t_z);
     cudaFree(d.t_kidx);
     cudaFree(d.zip64); cudaFree(d.t_zip_hi); cudaFree(d.t_zip_lo);
-    cudaFree(d.csr_self); cudaFree(d.vs64); cudaFree(d.t_zrow); cudaFree(d.t_yrow);
+    cudaFree(d.csr_self); cudaFree(d.vs64); cudaFree(d.t_zrow); cudaFree(d.t_yrow); cudaFree(d.t_zrow_f);
     d = DeviceNet();
     Workspace &w = h->ws;
     cudaFree(w.Vhi); cudaFree(w.Vlo); cudaFree(w.Shi); cudaFree(w.Slo); cudaFree(w.Rr16); cudaFree(w.Ri16);

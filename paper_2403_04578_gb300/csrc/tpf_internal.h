@@ -22,13 +22,13 @@ constexpr int kTileN = 128;
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 // Sparse formulation: demand buses per thread (2, 4 or 8), largest block, and the block size for
-// n demand buses with bpt buses per thread (0 when n does not fit one block).
+// n demand buses with bpt buses per thread: the fewest whole warps that hold them (0 when n does
+// not fit one block).
 constexpr int kTreeMaxThreads = 512;
 int tree_bpt(int n);  // the choice for n demand buses (TPF_TREE_BPT overrides it)
 inline int tree_threads(int n, int bpt) {
-    int t = 32;
-    while (t * bpt < n) t *= 2;
-    return t <= kTreeMaxThreads ? t : 0;
+    const int t = ((n + bpt - 1) / bpt + 31) / 32 * 32;
+    return t < 32 ? 32 : (t <= kTreeMaxThreads ? t : 0);
 }
 
 // Host-side result of the network preprocessing (Eq. 1 and Eq. 3).
@@ -120,6 +120,7 @@ struct DeviceNet {
     double *vs64 = nullptr;
     float4 *t_zrow = nullptr;
     float2 *t_yrow = nullptr;
+    float2 *t_zrow_f = nullptr;  // the high words of t_zrow (the sweeps' FP32 impedance rows)
     // Mixed path: fp16 planes of K * 2^k_exp, [n_pad][n_pad], zero padded
     void *Kr16 = nullptr, *Ki16 = nullptr;
     int k_exp = 0;

@@ -61,6 +61,7 @@ struct TreeWork {
     c2 vs_ddp[3];
     const float4 *zrow;
     const float2 *yrow;
+    const float2 *zrow_f;  // FP32 impedance rows for the sweeps, read through the cache
     const void *S;       // complex128 or, with s32, complex64 [T][n]
     const void *V0;      // given start, same type as V_out
     void *V_out;         // complex128 or, with v32, complex64 [T][n]; may be null
@@ -381,12 +382,10 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 && (kZip || kPh > 1) ? 
     float4 *const B = tsm + ns;  // [ns] V_ref (anchor input), x (anchor), then D = BFS(V_ref) - V_ref
     float4 *const C = tsm + 2 * ns;  // [ns] (S_hi, z_hi) of each position
     float4 *const Zs = tsm + 3 * ns;  // [ns] ZIP coefficients (kZip only)
-    // [ns][kPh] rows of the branch impedance blocks (polyphase only)
-    float2 *const ZR = reinterpret_cast<float2 *>(tsm + (kZip ? 4 : 3) * ns);
     // [ns] the subtree's range [q, end_q): one phase, the slot of its last position end_q - 1 (the
-    // slot itself for a leaf); polyphase, end_q
-    short *const s_rng = reinterpret_cast<short *>(reinterpret_cast<char *>(ZR) +
-                                                   (kPh > 1 ? sizeof(float2) * kPh * ns : 0));
+    // slot itself for a leaf); polyphase, end_q.  (The polyphase impedance rows stay in device
+    // memory, read through the cache: in shared memory they would halve the resident blocks.)
+    short *const s_rng = reinterpret_cast<short *>(tsm + (kZip ? 4 : 3) * ns);
     short *const s_par = s_rng + ns;                               // [ns] parent slot, -1 = the slack
     // [ns] where each position's branch term goes in the ends-ordered copy of X (-1: nowhere)
     short *const s_kidx = s_par + ns;
@@ -436,13 +435,6 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 && (kZip || kPh > 1) ? 
         C[s] = make_float4(sh.x, sh.y, zh.x, zh.y);
         B[s] = make_float4(sl.x, sl.y, 0.0f, 0.0f);  // S_lo until the first anchor replaces it by D
         if (kZip) Zs[s] = q < n ? a.zip_hi[s] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (kPh > 1) {
-#pragma unroll
-            for (int pp = 0; pp < kPh; ++pp) {
-                const float4 zq = q < n ? a.zrow[(size_t)s * kPh + pp] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                ZR[s * kPh + pp] = make_float2(zq.x, zq.y);
-            }
-        }
     }
     if (g.given) {  // a loop of its own: fewer loads in flight at once, fewer registers
 #pragma unroll
@@ -620,7 +612,7 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 && (kZip || kPh > 1) ? 
                             float2 L = P[slot_of<kBPT>(pp * a.nbp + eb - 1, th)];
                             const int prev = pp * a.nbp + qb - 1;
                             if (prev >= 0) L = sub2(L, P[slot_of<kBPT>(prev, th)]);
-                            xq = add2(xq, cmul2(ZR[s * kPh + pp], L));
+                            xq = add2(xq, cmul2(__ldg(&a.zrow_f[(size_t)s * kPh + pp]), L));
                         }
                     }
                 }
@@ -850,6 +842,7 @@ TreeWork work_of(const tpf_handle *h) {
     w.zip_lo = d.t_zip_lo;
     w.nbp = d.nbp;
     w.zrow = d.t_zrow;
+    w.zrow_f = d.t_zrow_f;
     w.yrow = d.t_yrow;
     for (int p = 0; p < 3; ++p) {
         const bool has = p < h->net.phases && (int)h->net.vs.size() >= 2 * (p + 1);
@@ -864,10 +857,10 @@ TreeWork work_of(const tpf_handle *h) {
 }
 
 size_t tree_smem(int threads, int bpt, bool zip, int phases) {
+    (void)phases;
     const size_t ns = (size_t)threads * bpt;
-    // A, B, C (and the ZIP coefficients); the impedance rows (polyphase); end, parent, ends
-    return (zip ? 4 : 3) * ns * sizeof(float4) + (phases > 1 ? ns * phases * sizeof(float2) : 0) +
-           sizeof(short) * 3 * ns;
+    // A, B, C (and the ZIP coefficients); range, parent, ends index
+    return (zip ? 4 : 3) * ns * sizeof(float4) + sizeof(short) * 3 * ns;
 }
 
 // cols == 0 only sets the kernel's shared-memory attribute.
@@ -879,9 +872,9 @@ cudaError_t launch_tree_t(int threads, int64_t cols, size_t smem, const TreeArgs
     return e;
 }
 
-// The single-phase constant-power kernel has compile-time block sizes for the shapes that the
-// default bus-per-thread choice gives (4 buses per thread up to 2,048 buses, 8 beyond); other
-// shapes and the ZIP and polyphase kernels take the block size at run time.
+// The single-phase constant-power kernel has compile-time block sizes for the power-of-two shapes
+// of the default bus-per-thread choice (4 buses per thread at 64-512 threads, 8 at 512); other
+// block sizes and the ZIP and polyphase kernels take the block size at run time.
 template <int kBPT>
 cudaError_t launch_tree_b(int threads, bool zip, int phases, int64_t cols, size_t smem, const TreeArgs &g,
                           cudaStream_t st) {

@@ -32,7 +32,7 @@ def _batch(specs):
 
 
 def test_batch_matches_oracle_and_single_solves(cuda):
-    # Sizes spanning every launch shape (32 ... 512 threads), ragged and empty column counts.
+    # Sizes spanning block sizes from 32 to 512 threads, ragged and empty column counts.
     specs = [(2, 7, 1), (20, 96, 2), (35, 129, 3), (130, 96, 4), (300, 288, 5), (20, 0, 6), (700, 96, 7),
              (1100, 40, 8), (57, 288, 9), (3, 1, 11)]
     feeders, S = _batch(specs)

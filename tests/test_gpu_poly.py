@@ -85,3 +85,14 @@ def test_poly_given_start_batch_and_errors(cuda):
     assert e.value.status == tpf.EINVAL  # singular branch blocks
     fd.close()
     fd1.close()
+
+
+def test_poly_large_feeder_eight_buses_per_thread(cuda):
+    """1,000 three-phase buses (2,997 unknowns): 8 positions per thread, 384 threads, the impedance
+    rows read through the cache; against the oracle on a few columns."""
+    pf, pc, S, fd = _poly(1000, 6, seed=4)
+    Vo, it_o, _ = pc.solve(S, tol=1e-13)
+    V, it, mm, st = fd.solve(_dev(S), method="sparse", tol=1e-10)
+    assert st == tpf.OK
+    assert np.abs(V.cpu().numpy() - Vo).max() <= 1e-8
+    fd.close()

@@ -81,6 +81,39 @@ def test_gradients_match_the_fp64_reference(cuda, feeder200):
     net.close()
 
 
+def test_prediction_matches_the_fp64_reference(cuda, feeder200):
+    """Inference (bias and GELU in the GEMM epilogue, FP32 output) against the FP64 network on the
+    same weights: the normalised outputs agree to BF16 accuracy, and V_0 is their denormalisation."""
+    f, c = feeder200
+    S = G.load_tensor(f, 4096, 7)[::16][:256]
+    V, it, _ = c.solve(S, tol=1e-12)
+    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=128, seed=3)
+    Sd, Vd = _dev(S), _dev(V)
+    net.fit_normalization(Sd, Vd)
+    xm, xs, ym, ys = (np.asarray(a, dtype=np.float64) for a in net.normalization())
+    rng = np.random.default_rng(12)
+    sizes = net.sizes
+    Ws = [rng.uniform(-1, 1, (sizes[i + 1], sizes[i])) * np.sqrt(6.0 / (sizes[i] + sizes[i + 1]))
+          for i in range(len(sizes) - 1)]
+    bs = [rng.normal(0, 0.05, sizes[i + 1]) for i in range(len(sizes) - 1)]
+    Ws[-1] *= 0.05  # small outputs: every prediction stays inside the |V| guard
+    flat = np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(Ws, bs)]).astype(np.float32)
+    net.set_params(flat)
+    V0, fallback = net.predict(Sd)  # 256 columns: two batches of 128
+    assert fallback == 0
+    ref = OM.MLP([w.astype(np.float32).astype(np.float64) for w in Ws], [b.astype(np.float32) for b in bs])
+    y_ref, _ = ref.forward(_norm(_features(S), xm, xs))
+    V0 = V0.cpu().numpy()
+    ok = ys > 0  # outputs with spread (all of them here)
+    y_gpu = (np.concatenate([V0.real - 1.0, V0.imag], axis=1)[:, ok] - ym[ok]) / ys[ok]
+    y_ref = y_ref[:, ok]
+    rel = np.linalg.norm(y_gpu - y_ref) / np.linalg.norm(y_ref)
+    cos = float((y_gpu * y_ref).sum() / (np.linalg.norm(y_gpu) * np.linalg.norm(y_ref)))
+    assert rel <= 3e-2, rel
+    assert cos >= 0.999, cos
+    net.close()
+
+
 def test_training_reduces_the_loss(cuda, feeder200):
     f, c = feeder200
     S = G.load_tensor(f, 4096, 6)

@@ -327,3 +327,27 @@ def test_autotune_keeps_results(cuda):
     V, _, _, st = fd.solve(_dev(S[:200]), method="sparse")
     assert st == tpf.OK and np.abs(V.cpu().numpy() - Vz).max() <= TOL_MIXED
     fd.close()
+
+
+@pytest.mark.parametrize("nb", [33, 97, 161, 290, 481, 700, 1021, 1500, 2100, 2900, 4097])
+def test_sparse_block_shapes(cuda, nb):
+    """Feeders whose demand-bus counts land on block sizes of every kind: whole warps that are not
+    powers of two (runtime-size kernels), the compile-time power-of-two sizes, 8 buses per thread
+    above 2,048, and the 4,096-bus limit.  A few peak columns against the oracle (FPI up to 1,500
+    buses, sparse Newton-Raphson beyond)."""
+    f = G.make_feeder(nb, 3)
+    S = G.load_tensor(f, 4096, 3)[[1080, 1140, 2400]]
+    fd = tpf.Feeder.from_inputs(f)
+    V, it, mm, st = fd.solve(_dev(S), precision="mixed", tol=1e-10, method="sparse")
+    assert st == tpf.OK
+    V = V.cpu().numpy()
+    if nb <= 1500:
+        Vo, _, _ = O.Case.from_feeder(f).solve(S, tol=1e-13)
+        assert np.abs(V - Vo).max() <= TOL_MIXED
+    else:
+        Ysp = O.ybus(f.n_bus, f.from_bus, f.to_bus, f.z_pu)
+        for k in range(S.shape[0]):
+            Vn, _, ok = O.nr_solve(Ysp, f.slack, f.v0, f.pq_bus, S[k], tol=1e-11)
+            assert ok
+            assert np.abs(V[k] - Vn).max() <= TOL_MIXED
+    fd.close()

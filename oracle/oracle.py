@@ -178,7 +178,8 @@ class PolyCase:
     bus's phases hold vs[0..phases).  K = -Y_dd^{-1} by Gauss-Jordan, W = K Y_ds v_s, and the
     fixed-point iteration of Algorithm 1 (orc_fpi) are the single-phase ones on this index space."""
 
-    def __init__(self, n_bus, from_bus, to_bus, z_blocks, phases, slack=0, vs=None, pq=None):
+    def __init__(self, n_bus, from_bus, to_bus, z_blocks, phases, slack=0, vs=None, pq=None, with_k=True):
+        """with_k=False skips K and W (the O(n^3) inverse): the case then only evaluates mismatches."""
         self.n_bus, self.phases, self.slack = int(n_bus), int(phases), int(slack)
         ph = self.phases
         z = np.ascontiguousarray(z_blocks, np.complex128).reshape(len(from_bus), ph, ph)
@@ -192,6 +193,9 @@ class PolyCase:
         self.vs = np.asarray(vs if vs is not None else np.exp(-2j * np.pi * np.arange(ph) / ph), np.complex128)
         self.nodes = (pq[:, None] * ph + np.arange(ph)[None, :]).reshape(-1)
         self.snodes = self.slack * ph + np.arange(ph)
+        if not with_k:
+            self.K = self.W = None
+            return
         Ydd = np.ascontiguousarray(self.Y[np.ix_(self.nodes, self.nodes)])
         self.K = Ydd.copy()
         if lib().orc_invert(self.K.shape[0], self.K):

@@ -268,7 +268,7 @@ void free_device(tpf_handle *h) {
     cudaFree(w.Valt); cudaFree(w.delta_bits); cudaFree(w.delta64); cudaFree(w.iters); cudaFree(w.flags);
     cudaFree(w.rexp); cudaFree(w.tile_active); cudaFree(w.counters);
     if (w.counters_host) cudaFreeHost(w.counters_host);
-    cudaFree(w.S_dev); cudaFree(w.V_dev); cudaFree(w.it_dev); cudaFree(w.mm_dev);
+    cudaFree(w.S_dev); cudaFree(w.V_dev); cudaFree(w.it_dev); cudaFree(w.mm_dev); cudaFree(w.tree_scratch);
     w = Workspace();
     if (h->tmaps) {
         free(h->tmaps);

@@ -567,8 +567,9 @@ tpf_status tpf_batch_create(int F, tpf_handle *const *hs, const int64_t *T, cons
             if (hs[g] == hs[f]) return TPF_EINVAL;
     }
     if (o.method != TPF_METHOD_SPARSE || o.precision != TPF_PREC_MIXED) return TPF_EUNSUPPORTED;
-    for (int f = 0; f < F; ++f)
-        if (!hs[f]->dev.radial || hs[f]->dev.t_threads <= 0) return TPF_EUNSUPPORTED;
+    for (int f = 0; f < F; ++f)  // (feeders past 4,096 buses take chunked launches with scratch)
+        if (!hs[f]->dev.radial || hs[f]->dev.t_threads <= 0 || hs[f]->dev.t_bpt == tpf::kTreeBigBPT)
+            return TPF_EUNSUPPORTED;
     if (cudaSetDevice(hs[0]->device) != cudaSuccess) return TPF_ECUDA;
     return tpf::batch_plan_create(F, hs, T, S_dev, V_dev, iters_dev, mismatch_dev, o, out);
 }
@@ -649,7 +650,7 @@ tpf_status tpf_solve_batch(int F, tpf_handle *const *hs, const int64_t *T, const
     std::vector<int> grouped, single;
     for (int f = 0; f < F; ++f) {
         const bool fits = o.method == TPF_METHOD_SPARSE && o.precision == TPF_PREC_MIXED && hs[f]->dev.radial &&
-                          hs[f]->dev.t_threads > 0;
+                          hs[f]->dev.t_threads > 0 && hs[f]->dev.t_bpt != tpf::kTreeBigBPT;
         (fits ? grouped : single).push_back(f);
     }
     tpf_stats tot{};

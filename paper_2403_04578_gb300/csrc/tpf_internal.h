@@ -21,14 +21,17 @@ constexpr int kTileN = 128;
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
-// Sparse formulation: demand buses per thread (2, 4 or 8), largest block, and the block size for
-// n demand buses with bpt buses per thread: the fewest whole warps that hold them (0 when n does
-// not fit one block).
+// Sparse formulation: demand buses per thread (2, 4 or 8; 16 for the large-feeder kernel, whose
+// D, S and z live in a device scratch), largest block, and the block size for n demand buses with
+// bpt buses per thread: the fewest whole warps that hold them (0 when n does not fit one block).
 constexpr int kTreeMaxThreads = 512;
+constexpr int kTreeBigBPT = 16;
+constexpr int kTreeBigMaxThreads = 384;  // 168 registers per thread
 int tree_bpt(int n);  // the choice for n demand buses (TPF_TREE_BPT overrides it)
 inline int tree_threads(int n, int bpt) {
     const int t = ((n + bpt - 1) / bpt + 31) / 32 * 32;
-    return t < 32 ? 32 : (t <= kTreeMaxThreads ? t : 0);
+    const int cap = bpt == kTreeBigBPT ? kTreeBigMaxThreads : kTreeMaxThreads;
+    return t < 32 ? 32 : (t <= cap ? t : 0);
 }
 
 // Host-side result of the network preprocessing (Eq. 1 and Eq. 3).
@@ -152,6 +155,9 @@ struct Workspace {
     int *tile_active = nullptr;           // [cols / kTileN]
     int *counters = nullptr;              // [8] device counters
     int *counters_host = nullptr;         // pinned mirror
+    // large-feeder sparse kernel: per-block slices of D, (S_hi, z) and the ZIP coefficients
+    float4 *tree_scratch = nullptr;
+    size_t tree_scratch_bytes = 0;
     // host-solve staging
     int64_t host_cap = 0;
     void *S_dev = nullptr, *V_dev = nullptr;

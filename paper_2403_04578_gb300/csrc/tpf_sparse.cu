@@ -87,6 +87,9 @@ struct TreeArgs {
     int blind;  // ... and anchored at once, its low words kept (a given start)
     float tol2, switch_tol, switch_tol2;  // squared tolerances compare with squared steps
     int *counters;                        // [5] largest per-column sweep count, [6] largest anchor count
+    // Large-feeder kernel (16 buses per thread): per block (launch column), (kZip ? 3 : 2) * ns
+    // float4 of device scratch for D, (S_hi, z) and the ZIP coefficients.
+    float4 *scratch;
 };
 
 // Packed per-position word: ends-list start (bits 0-15), count (16-29), phase (30-31).
@@ -358,9 +361,14 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
 
 // kTh > 0 fixes the block size at compile time (it must equal blockDim.x): the slot arithmetic
 // and the scans then run on constants.  kTh = 0 takes it from blockDim.x.
+//
+// kBPT == 16 is the large-feeder kernel (4,097 to 6,144 demand buses): the prefix array and the tree
+// indices stay in shared memory, D, (S_hi, z) and the ZIP coefficients go to the block's slice of
+// device scratch (through the cache), and the block has up to 384 threads of 168 registers.
 template <int kBPT, bool kZip, int kPh, int kTh>
-__global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 && (kZip || kPh > 1) ? 80 : 64))
+__global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && (kZip || kPh > 1) ? 80 : 64)))
     mx_tree(const __grid_constant__ TreeArgs g) {
+    constexpr bool kBig = kBPT == 16;
     extern __shared__ float4 tsm[];
     __shared__ int s_work;
     const int th = kTh ? kTh : (int)blockDim.x, ns = th * kBPT;
@@ -379,13 +387,14 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 && (kZip || kPh > 1) ? 
     const int n = a.n;
     // Arrays indexed by slot s = j th + k of position q = kBPT k + j.
     float4 *const A = tsm;       // [ns] double-float prefix sums (anchor); float2 P and X in the sweeps
-    float4 *const B = tsm + ns;  // [ns] V_ref (anchor input), x (anchor), then D = BFS(V_ref) - V_ref
-    float4 *const C = tsm + 2 * ns;  // [ns] (S_hi, z_hi) of each position
-    float4 *const Zs = tsm + 3 * ns;  // [ns] ZIP coefficients (kZip only)
+    float4 *const big = kBig ? g.scratch + (size_t)blockIdx.x * (kZip ? 3 : 2) * ns : nullptr;
+    float4 *const B = kBig ? big : tsm + ns;  // [ns] V_ref (anchor input), x (anchor), then D = BFS(V_ref) - V_ref
+    float4 *const C = kBig ? big + ns : tsm + 2 * ns;  // [ns] (S_hi, z_hi) of each position
+    float4 *const Zs = kBig ? big + 2 * ns : tsm + 3 * ns;  // [ns] ZIP coefficients (kZip only)
     // [ns] the subtree's range [q, end_q): one phase, the slot of its last position end_q - 1 (the
     // slot itself for a leaf); polyphase, end_q.  (The polyphase impedance rows stay in device
     // memory, read through the cache: in shared memory they would halve the resident blocks.)
-    short *const s_rng = reinterpret_cast<short *>(tsm + (kZip ? 4 : 3) * ns);
+    short *const s_rng = reinterpret_cast<short *>(tsm + (kBig ? 1 : (kZip ? 4 : 3)) * ns);
     short *const s_par = s_rng + ns;                               // [ns] parent slot, -1 = the slack
     // [ns] where each position's branch term goes in the ends-ordered copy of X (-1: nowhere)
     short *const s_kidx = s_par + ns;
@@ -813,9 +822,9 @@ __global__ void __maxnreg__(kBPT == 8 ? 128 : (kBPT == 4 && (kZip || kPh > 1) ? 
 int tree_bpt(int n) {
     if (const char *e = std::getenv("TPF_TREE_BPT")) {
         const int b = std::atoi(e);
-        if (b == 2 || b == 4 || b == 8) return tree_threads(n, b) ? b : 0;
+        if (b == 2 || b == 4 || b == 8 || b == kTreeBigBPT) return tree_threads(n, b) ? b : 0;
     }
-    for (int b : {4, 8})
+    for (int b : {4, 8, kTreeBigBPT})
         if (tree_threads(n, b)) return b;
     return 0;
 }
@@ -859,8 +868,15 @@ TreeWork work_of(const tpf_handle *h) {
 size_t tree_smem(int threads, int bpt, bool zip, int phases) {
     (void)phases;
     const size_t ns = (size_t)threads * bpt;
-    // A, B, C (and the ZIP coefficients); range, parent, ends index
+    // A, B, C (and the ZIP coefficients); range, parent, ends index.  The large-feeder kernel
+    // keeps only A and the indices on chip.
+    if (bpt == kTreeBigBPT) return ns * sizeof(float4) + sizeof(short) * 3 * ns;
     return (zip ? 4 : 3) * ns * sizeof(float4) + sizeof(short) * 3 * ns;
+}
+
+// Device scratch per launch column of the large-feeder kernel.
+size_t tree_scratch_per_col(int threads, int bpt, bool zip) {
+    return bpt == kTreeBigBPT ? (size_t)(zip ? 3 : 2) * threads * bpt * sizeof(float4) : 0;
 }
 
 // cols == 0 only sets the kernel's shared-memory attribute.
@@ -904,7 +920,9 @@ tpf_status launch_tree(int bpt, int threads, bool zip, int phases, int64_t cols,
     if (smem > 227 * 1024) return TPF_EUNSUPPORTED;
     cudaError_t e;
     const int64_t c = prepare ? 0 : cols;
-    if (bpt == 8)
+    if (bpt == kTreeBigBPT)
+        e = launch_tree_b<kTreeBigBPT>(threads, zip, phases, c, smem, g, st);
+    else if (bpt == 8)
         e = launch_tree_b<8>(threads, zip, phases, c, smem, g, st);
     else if (bpt == 4)
         e = launch_tree_b<4>(threads, zip, phases, c, smem, g, st);
@@ -962,10 +980,42 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
         wk.v_min2 = (float)(out->v_min * out->v_min);
         wk.v_max2 = (float)(out->v_max * out->v_max);
     }
+    // The large-feeder kernel keeps part of each column's state in device scratch: its columns go
+    // in chunks of at most 8,192 launch columns, each with its slice.
+    const bool zip = d.t_zip_hi != nullptr;
+    const size_t per_col = tree_scratch_per_col(d.t_threads, d.t_bpt, zip);
+    const int64_t chunk = per_col ? std::min<int64_t>(T, 8192) : T;
+    if (per_col && w.tree_scratch_bytes < per_col * chunk) {
+        cudaFree(w.tree_scratch);
+        w.tree_scratch = nullptr;
+        w.tree_scratch_bytes = 0;
+        if (cudaMalloc(&w.tree_scratch, per_col * chunk) != cudaSuccess) {
+            cudaGetLastError();
+            return TPF_ENOMEM;
+        }
+        w.tree_scratch_bytes = per_col * chunk;
+    }
+    g.scratch = w.tree_scratch;
     KernelTimer timer(o.profile != 0, st);
-    timer.begin(KernelTimer::kResidual);
-    rs = launch_tree(d.t_bpt, d.t_threads, d.t_zip_hi != nullptr, d.phases, T, g, st);
-    timer.end();
+    int launches = 0;
+    const int n = d.n;
+    const size_t s_size = wk.s32 ? sizeof(float2) : sizeof(double2), v_size = wk.v32 ? sizeof(float2) : sizeof(double2);
+    for (int64_t c0 = 0; c0 < T && rs == TPF_OK; c0 += chunk) {
+        TreeArgs gc = g;
+        TreeWork &wc = gc.one;
+        wc.T = std::min(chunk, T - c0);
+        wc.S = static_cast<const char *>(S) + (size_t)c0 * n * s_size;
+        if (V) wc.V0 = wc.V_out = static_cast<char *>(V) + (size_t)c0 * n * v_size;
+        if (iters) wc.iters_out = iters + c0;
+        if (mismatch) wc.mismatch_out = mismatch + c0;
+        if (wk.col_vmin) wc.col_vmin = wk.col_vmin + c0;
+        if (wk.col_vmax) wc.col_vmax = wk.col_vmax + c0;
+        if (wk.col_viol) wc.col_viol = wk.col_viol + c0;
+        timer.begin(KernelTimer::kResidual);
+        rs = launch_tree(d.t_bpt, d.t_threads, zip, d.phases, wc.T, gc, st);
+        timer.end();
+        ++launches;
+    }
     if (rs != TPF_OK) return rs;
     if (cudaMemcpyAsync(w.counters_host, w.counters, sizeof(int) * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess) {
@@ -975,7 +1025,7 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
     const int64_t conv = w.counters_host[kCntConverged];
     h->stats.sweeps = w.counters_host[5];
     h->stats.precise_sweeps = w.counters_host[6];
-    h->stats.kernel_launches = 1;
+    h->stats.kernel_launches = launches;
     h->stats.converged = conv;
     h->stats.residual_ms = timer.total_ms(KernelTimer::kResidual);
     return conv == T ? TPF_OK : TPF_ENOCONV;

@@ -351,3 +351,46 @@ def test_sparse_block_shapes(cuda, nb):
             assert ok
             assert np.abs(V[k] - Vn).max() <= TOL_MIXED
     fd.close()
+
+
+def test_sparse_large_feeders_beyond_4096(cuda):
+    """16 buses per thread with device scratch and chunked launches (4,097 to 6,144 demand buses):
+    a 5,000-bus feeder against sparse Newton-Raphson, over more columns than one launch takes
+    (the repeated columns agree bit for bit); ZIP loads on it against the oracle's ZIP power
+    balance; the 6,145-bus limit and one bus past it."""
+    import torch
+
+    f = G.make_feeder(5000, 2)
+    S3 = G.load_tensor(f, 4096, 2)[[0, 1100, 4095]]
+    S = np.concatenate([S3, np.repeat(S3[1:2], 9000, axis=0)])  # 9,003 columns: two launches
+    fd = tpf.Feeder.from_inputs(f)
+    V, it, mm, st = fd.solve(_dev(S), precision="mixed", tol=1e-10, method="sparse")
+    assert st == tpf.OK
+    assert fd.stats()["kernel_launches"] == 2
+    assert torch.equal(V[1], V[-1]) and torch.equal(V[1], V[8500])
+    Vh = V[:3].cpu().numpy()
+    Y = O.ybus(f.n_bus, f.from_bus, f.to_bus, f.z_pu)
+    for k in range(3):
+        Vn, _, ok = O.nr_solve(Y, f.slack, f.v0, f.pq_bus, S3[k], tol=1e-11)
+        assert ok
+        assert np.abs(Vh[k] - Vn).max() <= TOL_MIXED
+    alpha = np.random.default_rng(5).dirichlet([2, 1, 1], fd.n_pq).T.copy()
+    fd.set_zip(alpha)
+    Vz, _, _, st = fd.solve(_dev(S3), precision="mixed", tol=1e-10, method="sparse")
+    assert st == tpf.OK
+    mz = O.mismatch_zip(Y, f.slack, f.v0, f.pq_bus, alpha, S3, Vz.cpu().numpy())
+    assert mz.max() <= 1e-8, mz
+    fd.close()
+    for nb, ok_ in ((6145, True), (6146, False)):
+        f2 = G.make_feeder(nb, 4)
+        fd2 = tpf.Feeder.from_inputs(f2)
+        S2 = G.load_tensor(f2, 4096, 4)[[1100]]
+        V2, _, _, st = fd2.solve(_dev(S2), precision="mixed", tol=1e-10, method="sparse", check=False)
+        if ok_:
+            assert st == tpf.OK
+            Vn, _, ok = O.nr_solve(O.ybus(f2.n_bus, f2.from_bus, f2.to_bus, f2.z_pu), f2.slack, f2.v0, f2.pq_bus,
+                                   S2[0], tol=1e-11)
+            assert ok and np.abs(V2.cpu().numpy()[0] - Vn).max() <= TOL_MIXED
+        else:
+            assert st == tpf.EUNSUPPORTED
+        fd2.close()

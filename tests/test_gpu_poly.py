@@ -96,3 +96,16 @@ def test_poly_large_feeder_eight_buses_per_thread(cuda):
     assert st == tpf.OK
     assert np.abs(V.cpu().numpy() - Vo).max() <= 1e-8
     fd.close()
+
+
+def test_poly_large_feeder_sixteen_buses_per_thread(cuda):
+    """1,700 three-phase buses (5,097 unknowns, past 4,096): 16 positions per thread with device
+    scratch; the oracle's power balance of the returned voltages."""
+    pf = G.make_feeder_poly(1700, 6)
+    S = G.load_tensor_poly(pf, 4, 6).reshape(4, -1)
+    pc = O.PolyCase(pf.n_bus, pf.from_bus, pf.to_bus, pf.z_blocks, 3, vs=pf.v0, with_k=False)
+    fd = tpf.Feeder.poly(pf.n_bus, pf.from_bus, pf.to_bus, pf.z_blocks, 3, v0=pf.v0)
+    V, it, mm, st = fd.solve(_dev(S), method="sparse", tol=1e-10)
+    assert st == tpf.OK
+    assert pc.mismatch(S, V.cpu().numpy()).max() <= 1e-8
+    fd.close()

@@ -53,9 +53,9 @@ METRIC = "PF solves/s at ≤1e-8 pu vs FP64 oracle: mixed+learned-start vs plain
 # profiles/tc_gemm_n999_T16384.md (203.7 MB + 75.5 MB for 16,384 columns), per iterating column;
 # scaled by the columns each launch of this run processes.  None once the kernel has changed since.
 GEMM_TRAFFIC_BYTES_PER_COLUMN = (203.725056e6 + 75.471360e6) / 16384
-# The same for the sparse tree kernel mx_tree (one launch per solve): 262.0 MB read + 209.8 MB
+# The same for the sparse tree kernel mx_tree (one launch per solve): 262.0 MB read + 209.4 MB
 # written for 16,384 columns, profiles/mx_tree_n999_T16384.md.
-TREE_TRAFFIC_BYTES_PER_COLUMN = (262.005760e6 + 209.757440e6) / 16384
+TREE_TRAFFIC_BYTES_PER_COLUMN = (262.013952e6 + 209.440256e6) / 16384
 # Algorithmic FP32 flop per bus per sweep of the tree formulation: load current conj(S/V) 12,
 # prefix sum 2, subtree difference 2, z L 6, subtree-end subtraction 2, path prefix 2, update 4,
 # |step|^2 and max 6.

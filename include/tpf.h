@@ -261,7 +261,8 @@ tpf_status tpf_solve_ex(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev
  * mismatch may be NULL, as may their entries).  Radial feeders under TPF_METHOD_SPARSE with
  * TPF_PREC_MIXED share one launch per launch shape (feeders grouped by the block size the sparse
  * kernel uses for them), each block finding its feeder in a device table; any other feeder is
- * solved on its own with tpf_solve and TPF_METHOD_DENSE.  converged_out (host, F entries, may be NULL) receives each
+ * solved on its own with tpf_solve: radial feeders past 4,096 demand buses with the sparse method
+ * (chunked launches), the rest with TPF_METHOD_DENSE.  converged_out (host, F entries, may be NULL) receives each
  * feeder's converged-column count; stats_out (host, may be NULL) the totals.  Handles must be on
  * the current device and distinct.  Returns TPF_OK when every column of every feeder met tol,
  * TPF_ENOCONV when some did not.  Blocks until the stream has finished.

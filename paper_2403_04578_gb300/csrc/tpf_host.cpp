@@ -679,11 +679,15 @@ tpf_status tpf_solve_batch(int F, tpf_handle *const *hs, const int64_t *T, const
         for (int k = 0; k < G; ++k)
             if (converged_out) converged_out[grouped[k]] = gconv[k];
     }
-    tpf_opts od = o;
-    od.method = TPF_METHOD_DENSE;  // feeders the sparse kernel cannot take use the dense form
     for (int f : single) {
+        // Large radial feeders keep the sparse method (its chunked large-feeder kernel); feeders
+        // the sparse kernel cannot take use the dense form.
+        tpf_opts of = o;
+        const bool sparse_ok = o.method == TPF_METHOD_SPARSE && o.precision == TPF_PREC_MIXED && hs[f]->dev.radial &&
+                               hs[f]->dev.t_threads > 0;
+        if (!sparse_ok) of.method = TPF_METHOD_DENSE;
         st = tpf_solve(hs[f], T[f], S_dev[f], V_dev[f], iters_dev ? iters_dev[f] : nullptr,
-                       mismatch_dev ? mismatch_dev[f] : nullptr, &od, stream);
+                       mismatch_dev ? mismatch_dev[f] : nullptr, &of, stream);
         if (st != TPF_OK && st != TPF_ENOCONV) return st;
         all = all && st == TPF_OK;
         const tpf_stats &fs = hs[f]->stats;

@@ -374,6 +374,14 @@ def test_sparse_large_feeders_beyond_4096(cuda):
         Vn, _, ok = O.nr_solve(Y, f.slack, f.v0, f.pq_bus, S3[k], tol=1e-11)
         assert ok
         assert np.abs(Vh[k] - Vn).max() <= TOL_MIXED
+    # In a batch with a small feeder: the large one is solved on its own, with the same results.
+    fs = G.make_feeder(60, 4)
+    fds = tpf.Feeder.from_inputs(fs)
+    Ss = G.load_tensor(fs, 40, 4)
+    Vb, itb, _, conv, _, st = tpf.solve_batch([fd, fds], [_dev(S3), _dev(Ss)])
+    assert st == tpf.OK and list(conv) == [3, 40]
+    assert np.array_equal(Vb[0].cpu().numpy(), Vh)
+    fds.close()
     alpha = np.random.default_rng(5).dirichlet([2, 1, 1], fd.n_pq).T.copy()
     fd.set_zip(alpha)
     Vz, _, _, st = fd.solve(_dev(S3), precision="mixed", tol=1e-10, method="sparse")

@@ -85,11 +85,13 @@ typedef struct {
 
 /* Formulation of a solve (both give the same iterates in exact arithmetic). */
 enum {
-    TPF_METHOD_DENSE = 0,  /* Algorithm 1 / Eq. 12: the dense product with K = -Y_dd^{-1}              */
+    TPF_METHOD_DENSE = 0,  /* Algorithm 1 / Eq. 12: the dense product with K = -Y_dd^{-1}.  Mixed  *
+                            * precision up to 2,048 demand unknowns; FP64 any size                   */
     TPF_METHOD_SPARSE = 1  /* Algorithm 2 / Eq. 13-14: a sparse solve with Y_dd each sweep, here the  *
                             * fill-in-free tree substitution of a radial feeder, O(n) per column and  *
-                            * sweep, the whole sweep loop of a column on chip.  Radial networks and  *
-                            * TPF_PREC_MIXED only (TPF_EUNSUPPORTED otherwise)                       */
+                            * sweep, the whole sweep loop of a column on chip.  Radial networks of   *
+                            * up to 6,144 demand unknowns (past 4,096 in chunks of 8,192 columns with *
+                            * device scratch) and TPF_PREC_MIXED only (TPF_EUNSUPPORTED otherwise)   */
 };
 
 /* Per-solve counters (filled by tpf_last_stats after a solve). */
@@ -274,8 +276,8 @@ tpf_status tpf_solve_batch(int F, tpf_handle *const *hs, const int64_t *T, const
 
 /*
  * A prepared batch (Sec. V, one submission for many feeders): the arguments of tpf_solve_batch,
- * fixed once, with every feeder radial and opts->method == TPF_METHOD_SPARSE,
- * opts->precision == TPF_PREC_MIXED (else TPF_EUNSUPPORTED).  tpf_batch_create uploads the work
+ * fixed once, with every feeder radial with at most 4,096 demand unknowns,
+ * opts->method == TPF_METHOD_SPARSE and opts->precision == TPF_PREC_MIXED (else TPF_EUNSUPPORTED).  tpf_batch_create uploads the work
  * table and captures one solve of all feeders (counter reset, one kernel per launch shape, copy of
  * the counts to pinned host memory) as a CUDA graph; tpf_batch_launch replays it on `stream` with
  * one graph launch and returns at once; tpf_batch_wait blocks until that replay has finished and

@@ -376,8 +376,9 @@ class Feeder:
                 "bus_under": bus_counts[0], "bus_over": bus_counts[1], "status": st}
 
     def solve_host(self, S, V0=None, precision="mixed", tol=1e-10, max_iter=100, switch_tol=1e-4, stream=None,
-                   out=None, check=True, profile=False, method="dense"):
-        """tpf_solve_host on host arrays (numpy or pinned torch CPU tensors, complex128 [T][n_pq])."""
+                   out=None, check=True, profile=False, method="dense", start=None):
+        """tpf_solve_host on host arrays (numpy or pinned torch CPU tensors, complex128 [T][n_pq]).
+        With V0, start is 'given' (default) or 'warm'."""
         T = S.shape[0]
         if out is None:
             V = np.empty((T, self.n_pq), dtype=np.complex128) if V0 is None else V0
@@ -391,7 +392,9 @@ class Feeder:
         def ptr(a):
             return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
 
-        o = make_opts(precision, tol, max_iter, "given" if V0 is not None else "flat", switch_tol, profile, method)
+        if start is None:
+            start = "given" if V0 is not None else "flat"
+        o = make_opts(precision, tol, max_iter, start, switch_tol, profile, method)
         st = lib().tpf_solve_host(self._h, T, ptr(S), ptr(V), ptr(it), ptr(mm), ctypes.byref(o), _stream_ptr(stream))
         if check and st not in (OK, ENOCONV):
             raise TpfError(st, "tpf_solve_host")

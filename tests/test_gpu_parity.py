@@ -134,6 +134,9 @@ def test_warm_start(cuda, method):
         assert st == tpf.OK
         assert np.abs(V.cpu().numpy() - Vo).max() <= TOL_MIXED
         assert it.cpu().numpy().mean() <= most
+    # Host buffers take the same warm start.
+    Vh, ith, _, st = fd.solve_host(S, V0=Vp.copy(), precision="mixed", tol=1e-10, method=method, start="warm")
+    assert st == tpf.OK and np.abs(Vh - Vo).max() <= TOL_MIXED
     # FP64: warm is the given start.
     V, it, mm, st = fd.solve(_dev(S), V=_dev(Vo), precision="fp64", tol=1e-10, start="warm")
     assert st == tpf.OK and (it.cpu().numpy() == 1).all()

@@ -701,11 +701,15 @@ def main():
         e2e_steps = max(1, args.steps // 2)
         barrier(world)
         t0 = time.perf_counter()
+        step_ms = []
         for _ in range(e2e_steps):
+            ts = time.perf_counter()
             fd.solve_host(Sh, precision="mixed", tol=args.tol, out=(Vh, ith, mmh), method=args.method)
+            step_ms.append((time.perf_counter() - ts) * 1e3)
         dt = allmax(world, (time.perf_counter() - t0) / e2e_steps)
         e2e = {"value": world * T / dt, "unit": "PF/s", "h2d_bytes_per_step": T * n * 16,
                "d2h_bytes_per_step": T * n * 16 + T * 4 + T * 8, "ms_per_step": dt * 1e3,
+               "step_ms": [round(x, 2) for x in step_ms],
                "entry_point": "tpf_solve_host (pinned host buffers)"}
 
     # The other formulation on the same workload.

@@ -23,17 +23,18 @@
 // The iterate is V_ref + delta; results reach the FP64 solution.
 //
 // One block owns one column for its whole solve.  Each thread owns kBPT consecutive depth-first
-// positions and keeps their V_ref, delta, S, z and ends-list bounds in registers; shared memory
-// holds the prefix-sum arrays, D and the tree's end / parent / ends arrays, all indexed by slot
-// (j * threads + k for the j-th position of thread k) so that a warp's accesses to its own
-// positions fall in consecutive banks.  Device memory is read for S once (again at an anchor) and
-// written once for V.
+// positions and keeps their V_ref, delta and ends-list bounds in registers; shared memory holds S
+// and z, the prefix-sum arrays, D and the tree's range / parent / ends-index arrays, all indexed
+// by slot (j * threads + k for the j-th position of thread k) so that a warp's accesses to its own
+// positions fall in consecutive banks.  Device memory is read for S once (again at a second
+// anchor) and written once for V.  Feeders of 4,097 to 6,144 demand buses take 16 positions per
+// thread and keep D, S and z in a device scratch slice per block instead (see mx_tree).
 #include <algorithm>
+#include <cstdlib>
+#include <limits>
 #include <new>
 #include <tuple>
 #include <vector>
-#include <cstdlib>
-#include <limits>
 
 #include "tpf_dd.cuh"
 

@@ -94,3 +94,51 @@ def test_tensor_requires_sparse(cuda):
     res = mesh.solve_tensor(torch.from_numpy(S).cuda(), check=False)
     assert res["status"] == tpf.EUNSUPPORTED
     mesh.close()
+
+
+def test_tensor_statistics_in_every_launch_chunk(cuda):
+    """A 5,000-bus feeder over 8,200 complex64 columns: the large-feeder kernel solves them in two
+    launches, each writing its own columns' statistics.  The per-column |V| extremes and band
+    counts agree with the returned V in both, and the per-bus counts add up over all columns."""
+    import torch
+
+    f = G.make_feeder(5000, 2, peak_factor=1.6)
+    T, n = 8200, f.n_pq
+    Sd = G.load_tensor_device(f, T, 2, torch.device("cuda"), dtype=torch.complex64)
+    fd = tpf.Feeder.from_inputs(f)
+    band = (0.95, 1.02)
+    res = fd.solve_tensor(Sd, v_complex64=False, v_band=band)
+    assert res["status"] == tpf.OK
+    assert fd.stats()["kernel_launches"] == 2
+    absV = res["V"].abs()
+    vmin, vmax = absV.min(1).values.float(), absV.max(1).values.float()
+    assert (res["vmin"] - vmin).abs().max().item() <= 1e-6
+    assert (res["vmax"] - vmax).abs().max().item() <= 1e-6
+    under, over = absV < band[0], absV > band[1]
+    edge = ((absV - band[0]).abs() < 1e-6) | ((absV - band[1]).abs() < 1e-6)
+    clean = ~edge.any(1)
+    assert torch.equal(res["viol"][clean], (under | over).sum(1).to(res["viol"].dtype)[clean])
+    cols_clean = ~edge.any(0)
+    assert torch.equal(res["bus_under"][cols_clean], under.sum(0).to(res["bus_under"].dtype)[cols_clean])
+    assert torch.equal(res["bus_over"][cols_clean], over.sum(0).to(res["bus_over"].dtype)[cols_clean])
+    fd.close()
+
+
+def test_tensor_three_phase_complex64(cuda):
+    """A three-phase feeder through tpf_solve_ex with complex64 loads: V against the polyphase
+    oracle on the widened loads, and the statistics against that V."""
+    import torch
+
+    pf = G.make_feeder_poly(60, 3)
+    T = 96
+    S = G.load_tensor_poly(pf, T, 3).reshape(T, -1).astype(np.complex64)
+    pc = O.PolyCase(pf.n_bus, pf.from_bus, pf.to_bus, pf.z_blocks, 3, vs=pf.v0)
+    Vo, _, _ = pc.solve(S.astype(np.complex128), tol=1e-13)
+    fd = tpf.Feeder.poly(pf.n_bus, pf.from_bus, pf.to_bus, pf.z_blocks, 3, v0=pf.v0)
+    band = (0.97, 1.03)
+    res = fd.solve_tensor(torch.from_numpy(S).cuda(), v_complex64=False, v_band=band)
+    assert res["status"] == tpf.OK
+    V = res["V"].cpu().numpy()
+    assert np.abs(V - Vo).max() <= 1e-8
+    _check_stats(res, Vo, band, T, S.shape[1])
+    fd.close()

@@ -46,7 +46,7 @@ typedef enum {
     TPF_ECUDA = 4,        /* a CUDA runtime or driver call failed (including "no device")       */
     TPF_ETIMEOUT = 5,     /* a bounded device-side wait expired; outputs are not valid          */
     TPF_ENOCONV = 6,      /* at least one column did not converge; all outputs are valid       */
-    TPF_EUNSUPPORTED = 7  /* the request is valid but this build or device cannot serve it     */
+    TPF_EUNSUPPORTED = 7  /* the request is valid but this library or device cannot serve it   */
 } tpf_status;
 
 /* Arithmetic of a solve. */

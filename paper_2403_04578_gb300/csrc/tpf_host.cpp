@@ -432,7 +432,7 @@ const char *tpf_strerror(tpf_status s) {
         case TPF_ECUDA: return "TPF_ECUDA: CUDA error";
         case TPF_ETIMEOUT: return "TPF_ETIMEOUT: a bounded device wait expired";
         case TPF_ENOCONV: return "TPF_ENOCONV: some columns did not converge";
-        case TPF_EUNSUPPORTED: return "TPF_EUNSUPPORTED: not supported by this build or device";
+        case TPF_EUNSUPPORTED: return "TPF_EUNSUPPORTED: not supported by this library or device";
     }
     return "TPF_UNKNOWN";
 }

@@ -109,3 +109,17 @@ def test_batch_entry_points_argument_errors(tpf_lib):
     assert tpf_lib.tpf_batch_launch(None, None) == tpf.EINVAL
     assert tpf_lib.tpf_batch_wait(None, None, None) == tpf.EINVAL
     tpf_lib.tpf_batch_destroy(None)
+
+
+def test_make_opts_maps_names_to_abi_constants(tpf_lib):
+    o = tpf.make_opts("fp64", tol=1e-9, max_iter=50, start="warm", switch_tol=1e-3, profile=True, method="sparse")
+    assert (o.precision, o.start, o.method) == (tpf.PREC_FP64, tpf.START_WARM, tpf.METHOD_SPARSE)
+    assert o.tol == 1e-9 and o.max_iter == 50 and o.switch_tol == 1e-3 and o.profile == 1
+    o = tpf.make_opts()
+    assert (o.precision, o.start, o.method, o.profile) == (tpf.PREC_MIXED, tpf.START_FLAT, tpf.METHOD_DENSE, 0)
+    assert tpf.make_opts(start="given").start == tpf.START_GIVEN
+    assert tpf.make_opts(precision=tpf.PREC_FP64, method=tpf.METHOD_DENSE).precision == tpf.PREC_FP64
+    with pytest.raises(TypeError):
+        tpf.make_opts(precision="bf16")
+    with pytest.raises(TypeError):
+        tpf.make_opts(method="newton")

@@ -2,6 +2,7 @@
 
 Each test checks the oracle against something other than itself: the paper's two-bus example
 (tests/golden/two_bus_fig2.json, Sec. III Fig. 2), the closed-form roots of the two-bus quadratic,
+the Sec. III circle geometry of the load impedances (Eq. 6-7, their intersections and tangency),
 the feasibility condition of Eq. 10, the contraction factor of Eq. 11, the radial path-sum form of
 Y_dd^{-1}, an independent sparse Newton-Raphson, the power-balance residual of Eq. 1 and brute
 force on tiny feeders.  The last test plants mistakes in the oracle's inputs (a sign, a dropped
@@ -95,6 +96,90 @@ def test_fpi_basin_covers_the_plane():
     V, it, _ = c.solve(S, V0=starts[:, None], tol=1e-13, max_iter=3000)
     assert (it > 0).all()
     assert np.abs(V[:, 0] - hi).max() < 1e-11
+
+
+def sec3_circles(z_s: complex, s: complex, v0_abs: float):
+    """Eq. 6-7: the load impedances z_l = r_l + j x_l that draw p_l (resp. q_l) from the source lie
+    on a circle in the (r_l, x_l) plane; centres and radii from the two-bus power expression."""
+    rs, xs, p, q = z_s.real, z_s.imag, s.real, s.imag
+    c_p = np.array([v0_abs ** 2 / (2 * p) - rs, -xs])
+    r_p = v0_abs / (2 * p) * np.sqrt(v0_abs ** 2 - 4 * rs * p)
+    c_q = np.array([-rs, v0_abs ** 2 / (2 * q) - xs])
+    r_q = v0_abs / (2 * q) * np.sqrt(v0_abs ** 2 - 4 * xs * q)
+    return c_p, r_p, c_q, r_q
+
+
+def sec3_load_impedances(z_s: complex, s: complex, v0_abs: float):
+    """Both solutions z_l as the intersections of the Eq. 6-7 circles, found on their radical line
+    (the line through both intersections, perpendicular to the line of centres)."""
+    c_p, r_p, c_q, r_q = sec3_circles(z_s, s, v0_abs)
+    n = c_q - c_p
+    d = np.array([-n[1], n[0]]) / np.hypot(*n)
+    # A point of the radical line: equal power with respect to both circles.
+    rhs = (c_q @ c_q - r_q ** 2) - (c_p @ c_p - r_p ** 2)
+    x0 = n * rhs / (2 * (n @ n))
+    # Points x0 + t d on circle p.
+    b = d @ (x0 - c_p)
+    c = (x0 - c_p) @ (x0 - c_p) - r_p ** 2
+    ts = (-b + np.sqrt(b * b - c), -b - np.sqrt(b * b - c))
+    return [complex(*(x0 + t * d)) for t in ts], np.hypot(*x0)
+
+
+def test_load_impedances_lie_on_the_sec3_circles():
+    """Sec. III geometry, independent of the quadratic: the circles' two intersections are the two
+    load impedances, on a line through the origin, one inside and one outside |z_s|; the voltage
+    divider v = v0 z_l / (z_s + z_l) of the outer one is the FPI's fixed point, of the inner one the
+    low root that Newton-Raphson reaches from a nearby start."""
+    z, s, v0 = fig2()
+    (za, zb), offset = sec3_load_impedances(z, s, abs(v0))
+    assert offset < 1e-12  # the paper's intercept beta = 0: the radical line passes through the origin
+    c_p, r_p, c_q, r_q = sec3_circles(z, s, abs(v0))
+    for zl in (za, zb):
+        assert abs(np.hypot(zl.real - c_p[0], zl.imag - c_p[1]) - r_p) < 1e-12
+        assert abs(np.hypot(zl.real - c_q[0], zl.imag - c_q[1]) - r_q) < 1e-12
+    z_hi, z_lo = (za, zb) if abs(za) > abs(zb) else (zb, za)
+    assert abs(z_lo) < abs(z) < abs(z_hi)
+    assert abs(abs(z_lo) * abs(z_hi) - abs(z) ** 2) < 1e-12  # power of the origin: h^2 = |z_s|^2
+    v_hi = v0 * z_hi / (z + z_hi)
+    v_lo = v0 * z_lo / (z + z_lo)
+    V, it, _ = two_bus_case(z, v0).solve(np.array([[s]]), tol=1e-14, max_iter=500)
+    assert it[0] > 0 and abs(V[0, 0] - v_hi) < 1e-13
+    hi, lo = O.two_bus_roots(z, s, v0)
+    assert abs(hi - v_hi) < 1e-13 and abs(lo - v_lo) < 1e-13
+    c = two_bus_case(z, v0)
+    vnr, _, ok = O.nr_solve(c.ybus_sparse(), 0, v0, [1], [s], v_init=[v_lo * (1 + 1e-3)], tol=1e-13)
+    assert ok and abs(vnr[0] - v_lo) < 1e-10
+    # Eq. 11 with the geometric impedances: contraction at the outer solution only.
+    assert abs(O.two_bus_contraction(z, s, hi) - abs(z) / abs(z_hi)) < 1e-12
+    assert abs(z) / abs(z_lo) > 1.0
+
+
+def test_critical_load_where_the_sec3_circles_touch():
+    """Sec. III: the largest load in a fixed direction is where the two circles touch
+    (r_p + r_q = distance of the centres); the single solution there has |z_l| = |z_s|.  Below it
+    the oracle has two roots and its FPI converges, above it there is no root and the FPI never
+    stops."""
+    from scipy.optimize import brentq
+
+    z, s0, v0 = fig2()
+
+    def gap(lam):
+        c_p, r_p, c_q, r_q = sec3_circles(z, lam * s0, abs(v0))
+        return r_p + r_q - np.hypot(*(c_p - c_q))
+
+    lam_max = min(abs(v0) ** 2 / (4 * z.real * s0.real), abs(v0) ** 2 / (4 * z.imag * s0.imag))
+    lam = brentq(gap, 0.1, lam_max * (1 - 1e-12), xtol=1e-15, rtol=1e-15)
+    c_p, r_p, c_q, r_q = sec3_circles(z, lam * s0, abs(v0))
+    touch = c_p + (c_q - c_p) * r_p / (r_p + r_q)
+    assert abs(np.hypot(*touch) - abs(z)) < 1e-7  # maximum power transfer: |z_l| = |z_s|
+    assert O.two_bus_roots(z, lam * (1 - 1e-9) * s0, v0) is not None
+    assert O.two_bus_roots(z, lam * (1 + 1e-9) * s0, v0) is None
+    c = two_bus_case(z, v0)
+    S = np.array([[0.98 * lam * s0], [1.02 * lam * s0]])
+    V, it, _ = c.solve(S, tol=1e-12, max_iter=20000)
+    assert it[0] > 0 and it[1] < 0
+    zl = V[0, 0] * z / (v0 - V[0, 0])
+    assert abs(zl) > abs(z)
 
 
 @pytest.mark.parametrize("scale", [0.5, 0.9, 0.99, 1.01, 1.5])

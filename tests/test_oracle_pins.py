@@ -2,7 +2,8 @@
 
 Each test checks the oracle against something other than itself: the paper's two-bus example
 (tests/golden/two_bus_fig2.json, Sec. III Fig. 2), the closed-form roots of the two-bus quadratic,
-the Sec. III circle geometry of the load impedances (Eq. 6-7, their intersections and tangency),
+the Sec. III circle geometry of the load impedances (Eq. 6-7, their intersections and tangency)
+and its parabola of critical loads,
 the feasibility condition of Eq. 10, the contraction factor of Eq. 11, the radial path-sum form of
 Y_dd^{-1}, an independent sparse Newton-Raphson, the power-balance residual of Eq. 1 and brute
 force on tiny feeders.  The last test plants mistakes in the oracle's inputs (a sign, a dropped
@@ -180,6 +181,73 @@ def test_critical_load_where_the_sec3_circles_touch():
     assert it[0] > 0 and it[1] < 0
     zl = V[0, 0] * z / (v0 - V[0, 0])
     assert abs(zl) > abs(z)
+
+
+def sec3_parabola(z_s: complex, v0_abs: float):
+    """Coefficients (G, H, I, J, K, L) of Sec. III's conic f(p_l, q_l) = 0, the set of loads with a
+    single (maximum power transfer) solution, read so that its discriminant H^2 - 4GI vanishes as
+    the paper states: I = x_s^2, J = |v0|^2 x_s, L = -|v0|^4 / 4."""
+    r, x, v2 = z_s.real, z_s.imag, v0_abs ** 2
+    return r * r, -2 * r * x, x * x, v2 * x, v2 * r, -v2 * v2 / 4
+
+
+def parabola_limit(coef, theta: float) -> float:
+    """Largest |s| on the ray s = |s| e^{j theta} inside the parabola: the positive root of
+    f(|s| cos theta, |s| sin theta) = 0."""
+    G, H, I, J, K, L = coef
+    c, s = np.cos(theta), np.sin(theta)
+    a2, a1 = G * s * s + H * c * s + I * c * c, J * s + K * c
+    if abs(a2) < 1e-15 * abs(a1):
+        return -L / a1
+    return (-a1 + np.sqrt(a1 * a1 - 4 * a2 * L)) / (2 * a2)
+
+
+@pytest.mark.parametrize("theta", [0.15, 0.4, "z_s", 0.8, 1.2, 1.45])
+def test_feasibility_boundary_is_the_sec3_parabola(theta):
+    """Sec. III: the loads where the Eq. 6-7 circles touch form a parabola, which the Eq. 10 circle
+    |s| = |v0|^2 / (4 |z_s|) touches in the direction of z_s and stays outside of elsewhere.  On every
+    ray the oracle's roots exist up to that boundary and no further, and its FPI converges inside
+    and never stops outside.  A slack voltage of 1.05 pu separates L = -|v0|^4 / 4 from the printed
+    -|v0|^2 / 4."""
+    from scipy.optimize import brentq
+
+    z, _, _ = fig2()
+    v0 = 1.05 + 0j
+    th = float(np.angle(z)) if theta == "z_s" else theta
+    coef = sec3_parabola(z, abs(v0))
+    G, H, I, _, _, _ = coef
+    assert abs(H * H - 4 * G * I) < 1e-15  # a parabola
+    lam = parabola_limit(coef, th)
+    u = np.exp(1j * th)
+
+    def gap(m):
+        c_p, r_p, c_q, r_q = sec3_circles(z, m * u, abs(v0))
+        return r_p + r_q - np.hypot(*(c_p - c_q))
+
+    m_max = min(abs(v0) ** 2 / (4 * z.real * u.real), abs(v0) ** 2 / (4 * z.imag * u.imag))
+    assert abs(brentq(gap, 1e-3, m_max * (1 - 1e-12), xtol=1e-15, rtol=1e-15) - lam) < 1e-12
+    eq10 = abs(v0) ** 2 / (4 * abs(z))
+    if theta == "z_s":
+        assert abs(lam - eq10) < 1e-14
+    else:
+        assert lam > eq10 * (1 + 1e-6)
+    assert O.two_bus_roots(z, lam * (1 - 1e-9) * u, v0) is not None
+    assert O.two_bus_roots(z, lam * (1 + 1e-9) * u, v0) is None
+    V, it, _ = two_bus_case(z, v0).solve(np.array([[0.97 * lam * u], [1.03 * lam * u]]), tol=1e-12,
+                                         max_iter=20000)
+    assert it[0] > 0 and it[1] < 0
+    assert abs(V[0, 0] - O.two_bus_roots(z, 0.97 * lam * u, v0)[0]) < 1e-9
+
+
+def test_printed_parabola_coefficients_miss_the_tangency():
+    """The coefficient table as printed (I = |v0|^2 x_s, J = x_s^2, L = -|v0|^2 / 4) is not a
+    parabola and misses the circles' tangency, which is why the reading above exchanges I and J."""
+    z, s0, v0 = fig2()
+    r, x = z.real, z.imag
+    printed = (r * r, -2 * r * x, abs(v0) ** 2 * x, x * x, abs(v0) ** 2 * r, -abs(v0) ** 2 / 4)
+    assert abs(printed[1] ** 2 - 4 * printed[0] * printed[2]) > 0.1
+    th = float(np.angle(s0))
+    assert abs(parabola_limit(printed, th) / parabola_limit(sec3_parabola(z, abs(v0)), th) - 1) > 0.01
 
 
 @pytest.mark.parametrize("scale", [0.5, 0.9, 0.99, 1.01, 1.5])

@@ -3,8 +3,8 @@
  *
  * A plain, slow, double-precision CPU restatement of the paper's dense fixed-point power flow
  * (Sec. II Eq. 1-3, Sec. IV-A Eq. 12 and Algorithm 1).  It exists to check the CUDA library; only
- * the tests, the smoke check and the benchmark's CPU-baseline leg may load it.  It shares no code
- * with the library.
+ * the tests, the smoke check and the benchmark's CPU legs (CPU baseline, reference arm, accuracy
+ * checks after each timed region) may load it.  It shares no code with the library.
  *
  * Conventions (all complex numbers are C99 double complex, laid out like numpy complex128):
  *   - Y is the dense (n_bus x n_bus) nodal admittance matrix of Eq. 1, built branch by branch.

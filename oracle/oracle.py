@@ -1,9 +1,10 @@
 """Oracle for the tensor power flow -- TEST INFRASTRUCTURE ONLY.
 
 Plain, slow, double-precision CPU implementations used to check the CUDA library.  Only the
-tests, the smoke check and the benchmark's CPU-baseline leg may import this module; the library
-never does, and the two share no code (inputs come from ``paper_2403_04578_gb300.inputs``, which
-holds no power-flow arithmetic).
+tests, the smoke check and the benchmark's CPU legs (the timed CPU baseline, the reference arm,
+and the accuracy checks against this oracle that follow each timed region) may import this
+module; the library never does, and the two share no code (inputs come from
+``paper_2403_04578_gb300.inputs``, which holds no power-flow arithmetic).
 
 Contents, each following the passage it cites:
 

@@ -123,3 +123,17 @@ def test_make_opts_maps_names_to_abi_constants(tpf_lib):
         tpf.make_opts(precision="bf16")
     with pytest.raises(TypeError):
         tpf.make_opts(method="newton")
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without libtpf.so every entry point of the binding raises; there is no CPU fallback."""
+    monkeypatch.setattr(tpf, "_lib", None)
+    monkeypatch.setattr(tpf._build, "LIB", str(tmp_path / "libtpf.so"))
+    with pytest.raises(RuntimeError, match="not built"):
+        tpf.lib()
+    with pytest.raises(RuntimeError, match="not built"):
+        tpf.make_opts()
+    with pytest.raises(RuntimeError, match="not built"):
+        tpf.Feeder.from_inputs(G.make_feeder(10, 1))
+    with pytest.raises(RuntimeError, match="not built"):
+        tpf.precompute_host(2, [0], [1], [0.1 + 0.05j])

@@ -1,8 +1,9 @@
 /*
  * tpf.h -- C ABI of the GB300 tensor power flow library (libtpf.so).
  *
- * The library solves many power flows of one distribution feeder at once with the dense
- * fixed-point iteration of the paper (Sec. II Eq. 2-3, Sec. IV-A Eq. 12, Algorithm 1):
+ * The library solves many power flows of one distribution feeder at once with the fixed-point
+ * iteration of the paper, in its dense form (Sec. II Eq. 2-3, Sec. IV-A Eq. 12, Algorithm 1) or,
+ * on radial feeders, its sparse form (Sec. IV-B Eq. 13-14, Algorithm 2; TPF_METHOD_SPARSE):
  *
  *     V_{k+1} = K conj(S ./ V_k) + W,      K = -Y_dd^{-1},   W = K Y_ds v_s,
  *

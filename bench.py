@@ -10,7 +10,8 @@ FP32 accumulation, residual form).  Both return results within 1e-8 pu of the FP
 
 Reported on one JSON line (rank 0):
   value       PF/s, device-resident inputs (S, V on the GPU), CUDA events around the K steps,
-              max over ranks; N ranks run N independent replicas (weak scaling)
+              max over ranks; rank r solves its own year of loads of the same feeder (load seed
+              = feeder seed + r), so N ranks solve N x columns with no exchange (weak scaling)
   e2e         PF/s through tpf_solve_host with pinned HOST buffers: H2D of S, solve, D2H of V,
               iteration counts and mismatches inside the timed region
   roofline    the headline path's dominant kernel: mx_tree (sparse; FP32 flops over the derived
@@ -628,7 +629,9 @@ def main():
     config["method"] = args.method
     T, n = args.columns, f.n_pq
     Sh = torch.empty((T, n), dtype=torch.complex128, pin_memory=True)
-    G.load_tensor(f, T, args.seed, out=Sh.numpy())
+    # Each rank solves its own year of loads: the columns shard across ranks with no exchange.
+    G.load_tensor(f, T, args.seed + rank, out=Sh.numpy())
+    config["sharding"] = "rank r solves its own load year (load seed = feeder seed + r); no collective"
     Sd = Sh.to(f"cuda:{local}")
     torch.cuda.synchronize()
     t0 = time.perf_counter()

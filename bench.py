@@ -28,6 +28,8 @@ Reported on one JSON line (rank 0):
   zip_loads   the headline workload with ZIP loads (Eq. 3) on the sparse formulation
   three_phase a 500-bus three-phase feeder (Eq. 1 with phases = 3) on the sparse formulation
   large_feeder the paper's largest grid, 5,000 buses, over the one-minute year (16 buses per thread)
+  small_feeder config-1 leg: 34-bus feeder over one day (1,440 columns), FP64 and both mixed
+              formulations, CUDA-event and launch-inclusive host time per call, every column checked
   clocks      nvidia-smi samples taken during the timed region
 
 ``--impl reference`` times the CPU oracle as the reference arm on the same workload.
@@ -88,6 +90,7 @@ def parse_args():
     p.add_argument("--poly-columns", type=int, default=65536)
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-large", action="store_true")
+    p.add_argument("--no-small", action="store_true", help="skip the 34-bus one-day (1,440-column) case")
     p.add_argument("--large-buses", type=int, default=5000)
     p.add_argument("--large-columns", type=int, default=525600)
     p.add_argument("--scen", type=int, default=200)
@@ -496,6 +499,55 @@ def large_leg(args, stream, check):
     return out
 
 
+def small_leg(args, stream, check):
+    """34-bus feeder over one day of one-minute columns (1,440), flat start.  The whole problem is
+    about 1.5 MB, so it is launch- and latency-bound: each arithmetic and formulation reports its
+    CUDA-event time per call and the host's launch-inclusive time per call; the oracle checks every
+    column."""
+    import torch
+
+    from paper_2403_04578_gb300 import inputs as G
+    from paper_2403_04578_gb300 import tpf
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f = G.make_feeder(34, args.seed)
+    T = 1440
+    S_np = G.load_tensor(f, T, args.seed)
+    S = torch.from_numpy(S_np).to(dev)
+    fd = tpf.Feeder.from_inputs(f)
+    V = torch.empty_like(S)
+    it = torch.empty(T, dtype=torch.int32, device=dev)
+    mm = torch.empty(T, dtype=torch.float64, device=dev)
+    reps = 50
+    Vt = None
+    if check:
+        from oracle import oracle as O
+
+        Vt, _, _ = O.Case.from_feeder(f).solve(S_np, tol=1e-13, threads=os.cpu_count() or 1)
+    out = {"workload": f"34-bus radial feeder x {T:,} one-minute load columns (one day); flat start, per-column "
+                       f"stop at max|dV| <= {args.tol:g} pu; latency-bound"}
+    for name, precision, method in (("fp64", "fp64", "dense"), ("mixed_sparse", "mixed", "sparse"),
+                                    ("mixed_dense", "mixed", "dense")):
+        def call(precision=precision, method=method):
+            fd.solve(S, V, it, mm, precision=precision, method=method, start="flat", tol=args.tol)
+
+        ms = timed_device(call, reps, stream)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            call()
+        torch.cuda.synchronize()
+        host_ms = (time.perf_counter() - t0) * 1e3 / reps
+        r = {"value": T / (ms / 1e3), "unit": "PF/s", "ms_per_call": ms, "host_ms_per_call": host_ms,
+             "converged": fd.stats()["converged"], "mean_sweeps": float(it.abs().float().mean().item())}
+        if Vt is not None:
+            r["max_abs_err_pu"] = float(np.abs(V.cpu().numpy() - Vt).max())
+            r["columns_checked"] = T
+        out[name] = r
+    fd.close()
+    return out
+
+
 def poly_leg(args, stream, check):
     """Three-phase feeder: 500 buses (1,497 unknowns), mutual coupling 0.4, per-phase unbalance
     +-20 %, 65,536 one-minute columns, sparse formulation; the oracle checks sampled columns."""
@@ -808,6 +860,8 @@ def main():
         line["three_phase"] = poly_leg(args, stream, rank == 0 and not args.no_cpu)
     if not args.no_large:
         line["large_feeder"] = large_leg(args, stream, rank == 0 and not args.no_cpu)
+    if not args.no_small:
+        line["small_feeder"] = small_leg(args, stream, rank == 0 and not args.no_cpu)
     if rank == 0:
         print(json.dumps(line), flush=True)
     fd.close()

@@ -36,3 +36,9 @@ def test_bench_line_keys(cuda):
     for k in ("value", "unit", "cores", "kind", "sample"):
         assert k in d["cpu_baseline"], k
     assert d["accuracy"]["max_abs_err_pu"] <= 1e-8
+    small = d["small_feeder"]  # 34 buses x 1,440 columns, every column against the oracle
+    for name, bound in (("fp64", 1e-9), ("mixed_sparse", 1e-8), ("mixed_dense", 1e-8)):
+        r = small[name]
+        assert r["converged"] == 1440 and r["columns_checked"] == 1440, name
+        assert r["max_abs_err_pu"] <= bound, (name, r["max_abs_err_pu"])
+        assert r["value"] > 0 and r["host_ms_per_call"] >= r["ms_per_call"] * 0.5, name

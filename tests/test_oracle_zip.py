@@ -71,8 +71,20 @@ def test_mixed_zip_matches_an_independent_root_finder():
             r = Ydd @ v + Yds * c.vs + a[0] * np.conj(s / v) + a[1] * np.conj(s) + a[2] * np.conj(s) * v
             return np.r_[r.real, r.imag]
 
-        x = scipy_opt.fsolve(F, np.r_[np.ones(n), np.zeros(n)], xtol=1e-14)
-        assert np.abs(x[:n] + 1j * x[n:] - V[t]).max() <= 1e-10
+        def J(x):
+            # Wirtinger derivatives of the residual: A = dr/dv, B = dr/dconj(v); then
+            # dr/dRe(v) = A + B and dr/dIm(v) = j (A - B).
+            v = x[:n] + 1j * x[n:]
+            A = Ydd + np.diag(a[2] * np.conj(s))
+            B = np.diag(-a[0] * np.conj(s) / np.conj(v) ** 2)
+            dr, di = A + B, 1j * (A - B)
+            return np.block([[dr.real, di.real], [dr.imag, di.imag]])
+
+        x, info, ier, msg = scipy_opt.fsolve(F, np.r_[np.ones(n), np.zeros(n)], fprime=J, xtol=1e-10,
+                                             full_output=True)
+        assert ier == 1, msg  # the root finder itself converged
+        assert np.abs(F(x)).max() <= 1e-10  # admittances are ~2e3 pu: 1e-13 relative
+        assert np.abs(x[:n] + 1j * x[n:] - V[t]).max() <= 1e-12
 
 
 def test_planted_mistake_in_the_load_model_is_seen():

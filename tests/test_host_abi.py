@@ -137,3 +137,27 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         tpf.Feeder.from_inputs(G.make_feeder(10, 1))
     with pytest.raises(RuntimeError, match="not built"):
         tpf.precompute_host(2, [0], [1], [0.1 + 0.05j])
+
+
+def test_noalloc_argument_errors_before_any_device_call(tpf_lib):
+    """tpf_solve_fp64_noalloc checks its arguments and its 64 MiB scratch bound on the host first.
+    The pointers below are stand-ins that none of these calls dereferences."""
+    import math
+
+    import torch
+
+    f = tpf_lib.tpf_solve_fp64_noalloc
+    p = ctypes.c_void_p(0x1000)
+
+    def call(n=33, K=p, W=p, T=8, S=p, V=p, tol=1e-10, max_iter=100):
+        return f(n, K, W, T, S, V, None, ctypes.c_double(tol), max_iter, 0, None)
+
+    for kw in ({"n": 0}, {"T": -1}, {"tol": -1.0}, {"tol": math.nan}, {"max_iter": 0}, {"max_iter": 100001},
+               {"K": None}, {"W": None}, {"S": None}, {"V": None}):
+        assert call(**kw) == tpf.EINVAL, kw
+    assert call(T=0, K=None, W=None, S=None, V=None) == tpf.OK  # nothing to do
+    # Scratch = 1024 + 16 T_128 (n + 1) bytes <= 64 MiB: at n = 33 the largest T is 963 x 128.
+    assert call(n=33, T=963 * 128 + 1) == tpf.EINVAL
+    assert call(n=999, T=5000) == tpf.EINVAL
+    if not torch.cuda.is_available():
+        assert call(n=33, T=963 * 128) == tpf.ECUDA  # within the bound: it goes on to the (absent) device

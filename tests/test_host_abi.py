@@ -161,3 +161,59 @@ def test_noalloc_argument_errors_before_any_device_call(tpf_lib):
     assert call(n=999, T=5000) == tpf.EINVAL
     if not torch.cuda.is_available():
         assert call(n=33, T=963 * 128) == tpf.ECUDA  # within the bound: it goes on to the (absent) device
+
+
+def test_entry_points_refuse_null_handles_and_bad_arguments_on_the_host(tpf_lib):
+    """Every entry point that takes a handle refuses NULL, and option, size and pointer errors are
+    returned before any handle is read or any device call is made."""
+    L = tpf_lib
+    vp = ctypes.c_void_p
+    p = vp(0x1000)  # a stand-in pointer that these calls never dereference
+    o = tpf.Opts()
+    L.tpf_default_opts(ctypes.byref(o))
+    bad = tpf.Opts()
+    L.tpf_default_opts(ctypes.byref(bad))
+    bad.tol = -1.0
+    st = tpf.Stats()
+    out = tpf.Outputs(0, 0, 0.95, 1.05, None, None, None, None, None)
+    E = tpf.EINVAL
+
+    assert L.tpf_solve(None, 8, p, p, None, None, ctypes.byref(o), None) == E
+    assert L.tpf_solve_host(None, 8, p, p, None, None, ctypes.byref(o), None) == E
+    assert L.tpf_solve_ex(None, 8, p, p, None, None, None, ctypes.byref(o), None) == E
+    assert L.tpf_solve_ex(None, 8, p, p, None, None, ctypes.byref(out), ctypes.byref(o), None) == E
+    assert L.tpf_autotune(None, 8, p, ctypes.byref(o), None, None) == E
+    assert L.tpf_set_zip(None, None) == E
+    assert L.tpf_last_stats(None, ctypes.byref(st)) == E
+    assert L.tpf_n_pq(None) == -1
+    L.tpf_destroy(None)
+
+    # tpf_solve_batch: sizes and pointer arrays first, options before the empty-batch return.
+    assert L.tpf_solve_batch(-1, None, None, None, None, None, None, ctypes.byref(o), None, None, None) == E
+    assert L.tpf_solve_batch(1, None, None, None, None, None, None, ctypes.byref(o), None, None, None) == E
+    assert L.tpf_solve_batch(0, None, None, None, None, None, None, ctypes.byref(bad), None, None, None) == E
+    st.columns = 99
+    assert L.tpf_solve_batch(0, None, None, None, None, None, None, ctypes.byref(o), None, ctypes.byref(st),
+                             None) == tpf.OK
+    assert st.columns == 0  # statistics cleared
+
+    # The tensor-core self-test: tile multiples and pointers.
+    assert L.tpf_selftest_gemm(100, 128, 64, p, p, p, p, p, p, None) == E
+    assert L.tpf_selftest_gemm(128, 128, 64, p, None, p, p, p, p, None) == E
+
+    # Learned start.
+    h = vp(123)
+    assert L.tpf_mlp_create(10, 256, 3, 1024, 1, None) == E
+    assert L.tpf_mlp_create(0, 256, 3, 1024, 1, ctypes.byref(h)) == E and h.value is None
+    assert L.tpf_mlp_create(10, 256, 17, 1024, 1, ctypes.byref(h)) == E
+    assert L.tpf_mlp_create(10, 256, 3, 100, 1, ctypes.byref(h)) == E
+    assert L.tpf_mlp_param_count(None) == -1
+    f32 = (ctypes.c_float * 4)()
+    assert L.tpf_mlp_get_params(None, f32) == E
+    assert L.tpf_mlp_set_params(None, f32) == E
+    assert L.tpf_mlp_fit_normalization(None, 8, p, p, None) == E
+    assert L.tpf_mlp_get_normalization(None, f32, f32, f32, f32) == E
+    assert L.tpf_mlp_train_step(None, 128, p, p, 1e-3, None, None) == E
+    assert L.tpf_mlp_gradients(None, 128, p, p, None, f32, None) == E
+    assert L.tpf_mlp_predict(None, 8, p, p, None, None) == E
+    L.tpf_mlp_destroy(None)

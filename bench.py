@@ -21,6 +21,8 @@ Reported on one JSON line (rank 0):
   fp64_gpu    the plain FP64 GPU fixed-point iteration (direct form), timed on a column sample
   cpu_baseline the CPU oracle on the host cores, on a bounded column sample; the same leg checks
               the GPU results against the oracle (iterated to 1e-13) on sampled columns
+  cpu_newton_raphson  the oracle's sparse Newton-Raphson on 16 sampled columns, one core (context
+              for the paper's NR comparison)
   learned_start  config-5 leg: the MLP warm start on a 200-bus feeder
   scenario_tensor  config-3 leg: 500-bus feeder, [200 x 8,760] complex64 scenario tensor with fused
               voltage-band statistics
@@ -243,6 +245,27 @@ def cpu_oracle_leg(f, S_host, V_gpu_host, it_gpu, args, full_T, V_sparse_host=No
         if V_sparse_host is not None:
             check["sparse_max_abs_err_pu"] = float(np.abs(V_sparse_host[cc] - Vt).max())
     return out, check
+
+
+def cpu_newton_leg(f, S_host, full_T, columns=16):
+    """The oracle's sparse polar Newton-Raphson (SciPy sparse LU, one core, flat start, power
+    mismatch <= 1e-10 pu) on a few columns of the same workload: context for the paper's comparison
+    with NR (Sec. V), not a target."""
+    from oracle import oracle as O
+
+    Y = O.ybus(f.n_bus, f.from_bus, f.to_bus, f.z_pu)
+    case = O.Case.from_feeder(f)
+    cols = np.linspace(0, full_T - 1, columns).astype(np.int64)
+    t0 = time.perf_counter()
+    res = [O.nr_solve(Y, f.slack, f.v0, f.pq_bus, S_host[k], tol=1e-10) for k in cols]
+    dt = time.perf_counter() - t0
+    Vt, _, _ = case.solve(S_host[cols], tol=1e-13)
+    err = max(float(np.abs(r[0] - Vt[i]).max()) for i, r in enumerate(res))
+    return {"value": cols.size / dt, "unit": "PF/s", "cores": 1, "kind": "sparse Newton-Raphson (oracle)",
+            "sample": f"{cols.size} columns evenly spaced over the {full_T:,}-column year, flat start, "
+                      "power mismatch <= 1e-10 pu",
+            "converged": int(sum(bool(r[2]) for r in res)), "mean_iterations": float(np.mean([r[1] for r in res])),
+            "max_abs_err_pu_vs_fpi_oracle": err}
 
 
 def learned_start_leg(args, stream):
@@ -832,6 +855,7 @@ def main():
     if rank == 0 and not args.no_cpu:
         cpu, check = cpu_oracle_leg(f, Sh.numpy(), Vhost, ithost, args, T, V_other)
         line["cpu_baseline"] = cpu
+        line["cpu_newton_raphson"] = cpu_newton_leg(f, Sh.numpy(), T)
         if other_obj is not None and "sparse_max_abs_err_pu" in check:
             other_obj["max_abs_err_pu"] = check.pop("sparse_max_abs_err_pu")
         line["accuracy"] = check

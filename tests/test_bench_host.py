@@ -56,3 +56,16 @@ def test_workload_description_names_sizes_and_l2_rule():
     assert "60-bus" in cfg["workload"] and "525,600" in cfg["workload"]
     assert 0 < cfg["load_scale"] <= 1
     assert "%.1f GB" % (525600 * 59 * 16 / 1e9) in cfg["l2"]
+
+
+def test_cpu_newton_leg_converges_and_agrees_with_the_oracle():
+    from paper_2403_04578_gb300 import inputs as G
+
+    f = G.make_feeder(60, 2)
+    S = G.load_tensor(f, 4096, 2)
+    r = bench.cpu_newton_leg(f, S, 4096, columns=8)
+    assert r["converged"] == 8 and r["cores"] == 1 and r["value"] > 0
+    assert 1 <= r["mean_iterations"] <= 10
+    assert r["max_abs_err_pu_vs_fpi_oracle"] <= 1e-9
+    for k in ("value", "unit", "cores", "kind", "sample"):
+        assert k in r

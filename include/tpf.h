@@ -228,6 +228,9 @@ tpf_status tpf_autotune(tpf_handle *h, int64_t T, const void *S_dev, const tpf_o
  * fixed point, but B depends on each column's S when alpha_Z != 0, so a tensor of columns cannot
  * share them.  alpha == NULL returns the handle to constant power.  Served by TPF_METHOD_SPARSE and
  * TPF_PREC_FP64; the dense mixed path returns TPF_EUNSUPPORTED while ZIP coefficients are set.
+ * On the sparse path the coefficients take a fourth shared-memory region, so a feeder with 3,073
+ * to 4,096 demand buses (8 buses per thread) needs more than 227 KB per block and its sparse
+ * solves return TPF_EUNSUPPORTED before any launch; smaller and larger feeders are served.
  * TPF_EINVAL for non-finite coefficients.
  */
 tpf_status tpf_set_zip(tpf_handle *h, const double *alpha);

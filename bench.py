@@ -351,6 +351,18 @@ def learned_start_leg(args, stream):
     return out, f, S_ev, V_learned
 
 
+def secondary(fn, *a):
+    """Run a secondary workload; a failure is recorded in the JSON line (traceback on stderr)
+    instead of losing the headline measurement."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001 -- reported, not hidden
+        import traceback
+
+        traceback.print_exc()
+        return {"error": f"{type(e).__name__}: {e}"}
+
+
 def timed_device(fn, reps, stream):
     """Mean CUDA-event time (ms) of `reps` calls after one warm-up call."""
     import torch
@@ -855,7 +867,7 @@ def main():
     if rank == 0 and not args.no_cpu:
         cpu, check = cpu_oracle_leg(f, Sh.numpy(), Vhost, ithost, args, T, V_other)
         line["cpu_baseline"] = cpu
-        line["cpu_newton_raphson"] = cpu_newton_leg(f, Sh.numpy(), T)
+        line["cpu_newton_raphson"] = secondary(cpu_newton_leg, f, Sh.numpy(), T)
         if other_obj is not None and "sparse_max_abs_err_pu" in check:
             other_obj["max_abs_err_pu"] = check.pop("sparse_max_abs_err_pu")
         line["accuracy"] = check
@@ -877,15 +889,15 @@ def main():
             ls["columns_checked"] = int(cc.size)
         line["learned_start"] = ls
     if not args.no_scenario:
-        line["scenario_tensor"] = scenario_leg(args, stream, rank == 0 and not args.no_cpu)
+        line["scenario_tensor"] = secondary(scenario_leg, args, stream, rank == 0 and not args.no_cpu)
     if not args.no_batch:
-        line["feeder_batch"] = batch_leg(args, stream, rank == 0 and not args.no_cpu)
+        line["feeder_batch"] = secondary(batch_leg, args, stream, rank == 0 and not args.no_cpu)
     if not args.no_poly:
-        line["three_phase"] = poly_leg(args, stream, rank == 0 and not args.no_cpu)
+        line["three_phase"] = secondary(poly_leg, args, stream, rank == 0 and not args.no_cpu)
     if not args.no_large:
-        line["large_feeder"] = large_leg(args, stream, rank == 0 and not args.no_cpu)
+        line["large_feeder"] = secondary(large_leg, args, stream, rank == 0 and not args.no_cpu)
     if not args.no_small:
-        line["small_feeder"] = small_leg(args, stream, rank == 0 and not args.no_cpu)
+        line["small_feeder"] = secondary(small_leg, args, stream, rank == 0 and not args.no_cpu)
     if rank == 0:
         print(json.dumps(line), flush=True)
     fd.close()

@@ -69,3 +69,12 @@ def test_cpu_newton_leg_converges_and_agrees_with_the_oracle():
     assert r["max_abs_err_pu_vs_fpi_oracle"] <= 1e-9
     for k in ("value", "unit", "cores", "kind", "sample"):
         assert k in r
+
+
+def test_secondary_leg_failure_is_recorded_not_fatal(capsys):
+    def boom(x):
+        raise ValueError(f"bad {x}")
+
+    assert bench.secondary(lambda a, b: {"value": a + b}, 1, 2) == {"value": 3}
+    assert bench.secondary(boom, 7) == {"error": "ValueError: bad 7"}
+    assert "ValueError" in capsys.readouterr().err

@@ -10,6 +10,10 @@ Contents, each following the passage it cites:
 
 * ``build()`` / ``lib()`` compile and load ``fpi.c`` (Eq. 1-3, Eq. 12, Algorithm 1).
 * ``ybus``, ``precompute``, ``fpi``, ``mismatch`` -- thin ctypes wrappers over ``fpi.c``.
+* ``fpi_zip``, ``mismatch_zip`` -- Eq. 3 with ZIP loads, column by column (per-column B, F and w),
+  and the ZIP power balance (``fpi.c``).
+* ``Case`` / ``PolyCase`` -- a feeder prepared for the oracle (Y, K, W and the bus bookkeeping);
+  ``PolyCase`` builds Y from phases x phases branch blocks (Eq. 1 with phi > 1).
 * ``nr_solve`` -- an independent sparse polar Newton-Raphson (the "NR (Sparse)" method the paper
   compares against in Sec. V), used to cross-check the fixed-point solution.
 * ``two_bus_roots``, ``feasible_eq10``, ``two_bus_contraction`` -- the two-bus closed forms of
@@ -19,7 +23,9 @@ Contents, each following the passage it cites:
 * ``path_sum_K`` -- the bus-impedance path-sum of a radial feeder (follows from Eq. 1 and the
   Z_B remark after Eq. 11); pins the dense inverse.
 
-Parity pins for every function live in ``tests/test_oracle_pins.py``.
+Every function is pinned in ``tests/test_oracle_pins.py`` (dense FPI, NR, two-bus closed forms and
+geometry), ``tests/test_oracle_zip.py`` (ZIP loads) and ``tests/test_oracle_poly.py`` (polyphase);
+the learned start's reference network (``oracle/mlp.py``) in ``tests/test_oracle_mlp.py``.
 """
 from __future__ import annotations
 

@@ -197,6 +197,20 @@ def precompute_host(n_bus, from_bus, to_bus, z_pu, slack=0, v0=1.0 + 0j, pq_bus=
     return K, W
 
 
+def _host_buffer(a, name, dtype, shape):
+    """Check a host buffer handed to tpf_solve_host: a C-contiguous numpy array or CPU torch tensor
+    of the given dtype and shape (the library reads and writes exactly that many bytes)."""
+    if hasattr(a, "is_cuda"):
+        import torch
+
+        tdt = {np.complex128: torch.complex128, np.int32: torch.int32, np.float64: torch.float64}[dtype]
+        ok = not a.is_cuda and a.dtype == tdt and a.is_contiguous() and tuple(a.shape) == shape
+    else:
+        ok = isinstance(a, np.ndarray) and a.dtype == dtype and a.flags.c_contiguous and a.shape == shape
+    if not ok:
+        raise ValueError(f"{name} must be a C-contiguous host {np.dtype(dtype).name} array of shape {shape}")
+
+
 def _stream_ptr(stream):
     import torch
 
@@ -380,12 +394,18 @@ class Feeder:
         """tpf_solve_host on host arrays (numpy or pinned torch CPU tensors, complex128 [T][n_pq]).
         With V0, start is 'given' (default) or 'warm'."""
         T = S.shape[0]
+        _host_buffer(S, "S", np.complex128, (T, self.n_pq))
+        if V0 is not None:
+            _host_buffer(V0, "V0", np.complex128, (T, self.n_pq))
         if out is None:
             V = np.empty((T, self.n_pq), dtype=np.complex128) if V0 is None else V0
             it = np.empty(T, dtype=np.int32)
             mm = np.empty(T, dtype=np.float64)
         else:
             V, it, mm = out
+            _host_buffer(V, "V", np.complex128, (T, self.n_pq))
+            _host_buffer(it, "iters", np.int32, (T,))
+            _host_buffer(mm, "mismatch", np.float64, (T,))
         if V0 is not None and V is not V0:
             V[...] = V0
 

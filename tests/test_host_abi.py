@@ -217,3 +217,35 @@ def test_entry_points_refuse_null_handles_and_bad_arguments_on_the_host(tpf_lib)
     assert L.tpf_mlp_gradients(None, 128, p, p, None, f32, None) == E
     assert L.tpf_mlp_predict(None, 8, p, p, None, None) == E
     L.tpf_mlp_destroy(None)
+
+
+def test_solve_host_checks_its_host_buffers_before_the_library():
+    """tpf_solve_host reads and writes T x n_pq complex128 values: the binding refuses buffers of
+    another dtype, shape or layout, and device tensors, before any library call."""
+    import torch
+
+    fd = object.__new__(tpf.Feeder)  # no device here: the checks come first
+    fd._h, fd.n_pq = None, 5
+    T = 4
+    S = np.zeros((T, 5), np.complex128)
+    bad_S = [S.astype(np.complex64), np.zeros((T, 6), np.complex128), np.zeros((5, T), np.complex128).T,
+             torch.zeros((T, 5), dtype=torch.complex64)]
+    for b in bad_S:
+        with pytest.raises(ValueError, match="S must be"):
+            fd.solve_host(b)
+    with pytest.raises(ValueError, match="V0 must be"):
+        fd.solve_host(S, V0=np.ones((T, 5), np.complex64))
+    good = (torch.zeros((T, 5), dtype=torch.complex128), torch.zeros(T, dtype=torch.int32),
+            torch.zeros(T, dtype=torch.float64))
+    for k, b in ((1, torch.zeros(T, dtype=torch.int64)), (2, np.zeros(T, np.float32)),
+                 (0, torch.zeros((T, 4), dtype=torch.complex128))):
+        out = list(good)
+        out[k] = b
+        with pytest.raises(ValueError, match="must be a C-contiguous host"):
+            fd.solve_host(S, out=tuple(out))
+    # Well-formed buffers pass the checks and fail loudly further on: without a CUDA driver at the
+    # stream lookup, otherwise in the library, which refuses the missing handle.
+    with pytest.raises((tpf.TpfError, RuntimeError)) as e:
+        fd.solve_host(torch.from_numpy(S), out=good)
+    if isinstance(e.value, tpf.TpfError):
+        assert e.value.status == tpf.EINVAL

@@ -612,7 +612,23 @@ class LearnedStart:
             off += o
         return Ws, bs
 
+    def _columns(self, S, V=None, vname="V"):
+        """S (and V) must be contiguous CUDA complex128 [T, n_pq] tensors, V shaped like S: the
+        kernels read T x n_pq values from each.  Dtypes and shapes are checked before placement."""
+        import torch
+
+        pairs = [("S", S)] + ([(vname, V)] if V is not None else [])
+        for name, X in pairs:
+            if not isinstance(X, torch.Tensor) or X.dtype != torch.complex128:
+                raise TypeError(f"{name} must be a complex128 torch tensor")
+            if X.dim() != 2 or X.shape[1] != self.n_pq or X.shape != S.shape:
+                raise ValueError(f"{name} must have shape [T, {self.n_pq}]" + (" like S" if name != "S" else ""))
+        for name, X in pairs:
+            if not X.is_contiguous() or not X.is_cuda:
+                raise ValueError(f"{name} must be a contiguous CUDA tensor")
+
     def fit_normalization(self, S, V, stream=None):
+        self._columns(S, V)
         st = lib().tpf_mlp_fit_normalization(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()),
                                              ctypes.c_void_p(V.data_ptr()), _stream_ptr(stream))
         if st != OK:
@@ -626,6 +642,7 @@ class LearnedStart:
         return tuple(a)
 
     def train_step(self, S, V, lr=1e-3, want_loss=True, stream=None):
+        self._columns(S, V)
         loss = ctypes.c_double(0.0)
         st = lib().tpf_mlp_train_step(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()),
                                       ctypes.c_void_p(V.data_ptr()), float(lr),
@@ -635,6 +652,7 @@ class LearnedStart:
         return loss.value if want_loss else None
 
     def gradients(self, S, V, stream=None):
+        self._columns(S, V)
         loss = ctypes.c_double(0.0)
         g = np.empty(lib().tpf_mlp_param_count(self._h), dtype=np.float32)
         st = lib().tpf_mlp_gradients(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
@@ -648,7 +666,10 @@ class LearnedStart:
         import torch
 
         if V0 is None:
+            self._columns(S)
             V0 = torch.empty_like(S)
+        else:
+            self._columns(S, V0, "V0")
         fb = ctypes.c_int64(0)
         st = lib().tpf_mlp_predict(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V0.data_ptr()),
                                    ctypes.byref(fb), _stream_ptr(stream))

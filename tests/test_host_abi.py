@@ -249,3 +249,27 @@ def test_solve_host_checks_its_host_buffers_before_the_library():
         fd.solve_host(torch.from_numpy(S), out=good)
     if isinstance(e.value, tpf.TpfError):
         assert e.value.status == tpf.EINVAL
+
+
+def test_learned_start_checks_its_tensors_before_the_library():
+    """The network's kernels read T x n_pq complex128 values: other dtypes, widths, mismatched V and
+    host tensors are refused in the binding."""
+    import torch
+
+    net = object.__new__(tpf.LearnedStart)  # no device here: the checks come first
+    net._h, net.n_pq, net.max_batch = None, 6, 1024
+    S = torch.zeros((128, 6), dtype=torch.complex128)
+    with pytest.raises(TypeError, match="S must be a complex128"):
+        net.predict(S.to(torch.complex64))
+    with pytest.raises(ValueError, match=r"S must have shape \[T, 6\]"):
+        net.train_step(torch.zeros((128, 7), dtype=torch.complex128), S)
+    with pytest.raises(ValueError, match="V must have shape"):
+        net.gradients(S, torch.zeros((256, 6), dtype=torch.complex128))
+    with pytest.raises(ValueError, match="V must have shape"):
+        net.fit_normalization(S, torch.zeros((128, 5), dtype=torch.complex128))
+    with pytest.raises(ValueError, match="contiguous CUDA"):
+        net.fit_normalization(S, S)  # host tensors
+    with pytest.raises(ValueError, match="contiguous CUDA"):
+        net.predict(torch.zeros((128, 12), dtype=torch.complex128)[:, ::2])  # strided columns
+    with pytest.raises(ValueError, match="V0 must have shape"):
+        net.predict(S, torch.zeros((64, 6), dtype=torch.complex128))

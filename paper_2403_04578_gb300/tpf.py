@@ -211,6 +211,20 @@ def _host_buffer(a, name, dtype, shape):
         raise ValueError(f"{name} must be a C-contiguous host {np.dtype(dtype).name} array of shape {shape}")
 
 
+def _device_tensors(specs):
+    """specs: (name, tensor, torch dtype, shape) each.  Every tensor must have its dtype and shape
+    (the kernels read and write exactly that many elements through its pointer), then be
+    contiguous and on the device; dtypes and shapes are checked first."""
+    import torch
+
+    for name, X, dtype, shape in specs:
+        if not isinstance(X, torch.Tensor) or X.dtype != dtype or tuple(X.shape) != tuple(shape):
+            raise ValueError(f"{name} must be a {dtype} tensor of shape {tuple(shape)}")
+    for name, X, _, _ in specs:
+        if not X.is_contiguous() or not X.is_cuda:
+            raise ValueError(f"{name} must be a contiguous CUDA tensor")
+
+
 def _stream_ptr(stream):
     import torch
 
@@ -532,8 +546,13 @@ def solve_fp64_noalloc(K, W, S, V, iters=None, tol=1e-10, max_iter=100, given_st
     (complex128 [n]), S and V (complex128 [T, n]) and iters (int32 [T], optional) are the caller's
     CUDA tensors; the solve's scratch is libtpf's built-in 64 MiB array.  Returns the status.
     """
+    import torch
+
     n = K.shape[0]
     T = S.shape[0]
+    c128 = torch.complex128
+    _device_tensors([("K", K, c128, (n, n)), ("W", W, c128, (n,)), ("S", S, c128, (T, n)), ("V", V, c128, (T, n))]
+                    + ([("iters", iters, torch.int32, (T,))] if iters is not None else []))
     return lib().tpf_solve_fp64_noalloc(
         int(n), ctypes.c_void_p(K.data_ptr()), ctypes.c_void_p(W.data_ptr()), int(T), ctypes.c_void_p(S.data_ptr()),
         ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(iters.data_ptr() if iters is not None else 0), float(tol),
@@ -546,6 +565,8 @@ def selftest_gemm(Ar, Ai, Br, Bi, stream=None):
 
     M, K = Ar.shape
     N = Br.shape[0]
+    f16 = torch.float16
+    _device_tensors([("Ar", Ar, f16, (M, K)), ("Ai", Ai, f16, (M, K)), ("Br", Br, f16, (N, K)), ("Bi", Bi, f16, (N, K))])
     Dr = torch.empty((N, M), dtype=torch.float32, device=Ar.device)
     Di = torch.empty((N, M), dtype=torch.float32, device=Ar.device)
     st = lib().tpf_selftest_gemm(M, N, K, *(ctypes.c_void_p(x.data_ptr()) for x in (Ar, Ai, Br, Bi)),

@@ -273,3 +273,29 @@ def test_learned_start_checks_its_tensors_before_the_library():
         net.predict(torch.zeros((128, 12), dtype=torch.complex128)[:, ::2])  # strided columns
     with pytest.raises(ValueError, match="V0 must have shape"):
         net.predict(S, torch.zeros((64, 6), dtype=torch.complex128))
+
+
+def test_noalloc_and_gemm_bindings_check_their_tensors():
+    """The allocation-free solve and the GEMM self-test pass raw pointers: the binding checks that
+    every tensor has the dtype and shape the kernels assume, and lives on the device."""
+    import torch
+
+    c = torch.complex128
+    K, W = torch.zeros((4, 4), dtype=c), torch.zeros(4, dtype=c)
+    S = torch.zeros((8, 4), dtype=c)
+    cases = [((torch.zeros((4, 5), dtype=c), W, S, S), "K must be"),
+             ((K, torch.zeros(5, dtype=c), S, S), "W must be"),
+             ((K, W, torch.zeros((8, 3), dtype=c), S), "S must be"),
+             ((K, W, S, torch.zeros((8, 4), dtype=torch.complex64)), "V must be"),
+             ((K, W, S, S, torch.zeros(8, dtype=torch.int64)), "iters must be"),
+             ((K, W, S, S), "contiguous CUDA")]
+    for args, msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            tpf.solve_fp64_noalloc(*args)
+    h = torch.zeros((128, 64), dtype=torch.float16)
+    with pytest.raises(ValueError, match="Ai must be"):
+        tpf.selftest_gemm(h, torch.zeros((128, 32), dtype=torch.float16), h, h)
+    with pytest.raises(ValueError, match="Br must be"):
+        tpf.selftest_gemm(h, h, h.float(), h)
+    with pytest.raises(ValueError, match="contiguous CUDA"):
+        tpf.selftest_gemm(h, h, h, h)

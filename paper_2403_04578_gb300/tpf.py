@@ -225,6 +225,34 @@ def _device_tensors(specs):
             raise ValueError(f"{name} must be a contiguous CUDA tensor")
 
 
+def _batch_outputs(S, V, iters, mismatch):
+    """Caller-supplied batch outputs, per feeder f: V[f] complex128 shaped like S[f], iters[f] int32
+    and mismatch[f] float64 of length T_f, all contiguous on the device (the batch kernels write
+    through these pointers).  One pass of plain comparisons (a few microseconds per feeder); the
+    precise message, dtypes and shapes of all feeders before placement, only on failure."""
+    import torch
+
+    if not (len(V) == len(iters) == len(mismatch) == len(S)):
+        raise ValueError("one V, iters and mismatch tensor per feeder")
+    c128, i32, f64, Tn = torch.complex128, torch.int32, torch.float64, torch.Tensor
+    for s, v, i, m in zip(S, V, iters, mismatch):
+        n = (s.shape[0],)
+        if not (isinstance(v, Tn) and isinstance(i, Tn) and isinstance(m, Tn)
+                and v.dtype == c128 and i.dtype == i32 and m.dtype == f64
+                and v.shape == s.shape and i.shape == n and m.shape == n
+                and v.is_cuda and i.is_cuda and m.is_cuda
+                and v.is_contiguous() and i.is_contiguous() and m.is_contiguous()):
+            break
+    else:
+        return
+    specs = []
+    for f, s in enumerate(S):
+        n = (s.shape[0],)
+        specs += [(f"V[{f}]", V[f], c128, s.shape), (f"iters[{f}]", iters[f], i32, n),
+                  (f"mismatch[{f}]", mismatch[f], f64, n)]
+    _device_tensors(specs)
+
+
 def _stream_ptr(stream):
     import torch
 
@@ -449,6 +477,7 @@ def solve_batch(feeders, S, V=None, iters=None, mismatch=None, precision="mixed"
         raise ValueError("one load tensor per feeder")
     if start is None:
         start = "given" if V is not None else "flat"
+    supplied = V is not None or iters is not None or mismatch is not None
     V = list(V) if V is not None else [torch.empty_like(s) for s in S]
     iters = list(iters) if iters is not None else [torch.empty(s.shape[0], dtype=torch.int32, device=s.device)
                                                     for s in S]
@@ -459,6 +488,8 @@ def solve_batch(feeders, S, V=None, iters=None, mismatch=None, precision="mixed"
         if not (isinstance(s, torch.Tensor) and s.is_cuda and s.dtype == torch.complex128 and s.dim() == 2
                 and s.shape[1] == feeders[f].n_pq and s.is_contiguous()):
             raise ValueError(f"S[{f}] must be a contiguous CUDA complex128 [T, n_pq] tensor")
+    if supplied:
+        _batch_outputs(S, V, iters, mismatch)
     P = ctypes.c_void_p * F
     hs = P(*[fd._h.value for fd in feeders])
     Ts = (ctypes.c_int64 * F)(*[int(s.shape[0]) for s in S])
@@ -501,6 +532,7 @@ class BatchGraph:
             if not (isinstance(s, torch.Tensor) and s.is_cuda and s.dtype == torch.complex128 and s.dim() == 2
                     and s.shape[1] == feeders[f].n_pq and s.is_contiguous()):
                 raise ValueError(f"S[{f}] must be a contiguous CUDA complex128 [T, n_pq] tensor")
+        _batch_outputs(S, self.V, self.iters, self.mismatch)
         self.F, self.S, self.feeders = F, list(S), list(feeders)
         P = ctypes.c_void_p * F
         hs = P(*[fd._h.value for fd in feeders])

@@ -299,3 +299,23 @@ def test_noalloc_and_gemm_bindings_check_their_tensors():
         tpf.selftest_gemm(h, h, h.float(), h)
     with pytest.raises(ValueError, match="contiguous CUDA"):
         tpf.selftest_gemm(h, h, h, h)
+
+
+def test_batch_output_lists_are_checked():
+    """Caller-supplied batch outputs must match each feeder's loads in count, dtype and shape."""
+    import torch
+
+    S = [torch.zeros((8, 4), dtype=torch.complex128), torch.zeros((3, 6), dtype=torch.complex128)]
+    V = [torch.zeros_like(s) for s in S]
+    it = [torch.zeros(s.shape[0], dtype=torch.int32) for s in S]
+    mm = [torch.zeros(s.shape[0], dtype=torch.float64) for s in S]
+    with pytest.raises(ValueError, match="one V, iters and mismatch"):
+        tpf._batch_outputs(S, V[:1], it, mm)
+    with pytest.raises(ValueError, match=r"V\[1\] must be"):
+        tpf._batch_outputs(S, [V[0], torch.zeros((3, 5), dtype=torch.complex128)], it, mm)
+    with pytest.raises(ValueError, match=r"iters\[0\] must be"):
+        tpf._batch_outputs(S, V, [torch.zeros(8, dtype=torch.int64), it[1]], mm)
+    with pytest.raises(ValueError, match=r"mismatch\[1\] must be"):
+        tpf._batch_outputs(S, V, it, [mm[0], torch.zeros(4, dtype=torch.float64)])
+    with pytest.raises(ValueError, match="contiguous CUDA"):
+        tpf._batch_outputs(S, V, it, mm)  # well-formed, but host tensors

@@ -374,9 +374,11 @@ class Feeder:
             iters = torch.empty(T, dtype=torch.int32, device=S.device)
         if mismatch is None:
             mismatch = torch.empty(T, dtype=torch.float64, device=S.device)
-        for t_, dt in ((V, torch.complex128), (iters, torch.int32), (mismatch, torch.float64)):
-            if not (t_.is_cuda and t_.dtype == dt and t_.is_contiguous() and t_.shape[0] == T):
-                raise ValueError("output tensors must be contiguous CUDA tensors with T rows")
+        for t_, dt, shape in ((V, torch.complex128, S.shape), (iters, torch.int32, (T,)),
+                              (mismatch, torch.float64, (T,))):
+            if not (t_.is_cuda and t_.dtype == dt and t_.is_contiguous() and t_.shape == shape):
+                raise ValueError("V must be shaped like S, iters and mismatch [T]: contiguous CUDA tensors "
+                                 "(complex128, int32, float64)")
         o = make_opts(precision, tol, max_iter, start, switch_tol, profile, method)
         st = lib().tpf_solve(self._h, T, ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
                              ctypes.c_void_p(iters.data_ptr()), ctypes.c_void_p(mismatch.data_ptr()), ctypes.byref(o),

@@ -420,6 +420,11 @@ class Feeder:
         if bus_counts is None:
             bus_counts = (torch.zeros(self.n_pq, dtype=torch.int32, device=dev),
                           torch.zeros(self.n_pq, dtype=torch.int32, device=dev))
+        else:  # the kernels add n_pq counters into each
+            if len(bus_counts) != 2:
+                raise ValueError("bus_counts must be a pair (under, over)")
+            _device_tensors([("bus_counts[0]", bus_counts[0], torch.int32, (self.n_pq,)),
+                             ("bus_counts[1]", bus_counts[1], torch.int32, (self.n_pq,))])
         out = Outputs(1 if S.dtype == torch.complex64 else 0, 1 if v32 else 0, float(v_band[0]), float(v_band[1]),
                       vmin.data_ptr(), vmax.data_ptr(), viol.data_ptr(), bus_counts[0].data_ptr(),
                       bus_counts[1].data_ptr())

@@ -328,6 +328,10 @@ class Feeder:
 
     def autotune(self, S, tol=1e-10, max_iter=100, switch_tol=1e-4, stream=None) -> int:
         """tpf_autotune on the CUDA complex128 sample S [T, n_pq]; returns the chosen buses per thread."""
+        import torch
+
+        shape = tuple(getattr(S, "shape", ()))
+        _device_tensors([("S", S, torch.complex128, (shape[0] if len(shape) == 2 else -1, self.n_pq))])
         o = make_opts("mixed", tol, max_iter, "flat", switch_tol, False, "sparse")
         b = ctypes.c_int(0)
         st = lib().tpf_autotune(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()), ctypes.byref(o), ctypes.byref(b),

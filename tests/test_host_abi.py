@@ -319,3 +319,18 @@ def test_batch_output_lists_are_checked():
         tpf._batch_outputs(S, V, it, [mm[0], torch.zeros(4, dtype=torch.float64)])
     with pytest.raises(ValueError, match="contiguous CUDA"):
         tpf._batch_outputs(S, V, it, mm)  # well-formed, but host tensors
+
+
+def test_autotune_and_tensor_counters_are_checked():
+    import torch
+
+    fd = object.__new__(tpf.Feeder)
+    fd._h, fd.n_pq = None, 5
+    with pytest.raises(ValueError, match="S must be"):
+        fd.autotune(torch.zeros((16, 4), dtype=torch.complex128))
+    with pytest.raises(ValueError, match="S must be"):
+        fd.autotune(torch.zeros(16, dtype=torch.complex128))
+    with pytest.raises(ValueError, match="contiguous CUDA"):
+        fd.autotune(torch.zeros((16, 5), dtype=torch.complex128))
+    with pytest.raises(ValueError, match="S must be"):
+        fd.autotune(np.zeros((16, 5), np.complex128))

@@ -30,6 +30,7 @@ Reported on one JSON line (rank 0):
   zip_loads   the headline workload with ZIP loads (Eq. 3) on the sparse formulation
   three_phase a 500-bus three-phase feeder (Eq. 1 with phases = 3) on the sparse formulation
   large_feeder the paper's largest grid, 5,000 buses, over the one-minute year (16 buses per thread)
+  table1_100_bus Table I's 100-bus row: 100-bus feeder over the one-minute year, with the paper's times
   small_feeder config-1 leg: 34-bus feeder over one day (1,440 columns), FP64 and both mixed
               formulations, CUDA-event and launch-inclusive host time per call, every column checked
   clocks      nvidia-smi samples taken during the timed region
@@ -93,6 +94,7 @@ def parse_args():
     p.add_argument("--no-batch", action="store_true")
     p.add_argument("--no-large", action="store_true")
     p.add_argument("--no-small", action="store_true", help="skip the 34-bus one-day (1,440-column) case")
+    p.add_argument("--no-table1", action="store_true", help="skip the 100-bus one-year case of Table I")
     p.add_argument("--large-buses", type=int, default=5000)
     p.add_argument("--large-columns", type=int, default=525600)
     p.add_argument("--scen", type=int, default=200)
@@ -534,6 +536,43 @@ def large_leg(args, stream, check):
     return out
 
 
+def table1_100_leg(args, stream, check):
+    """Table I's 100-bus row over the one-minute year (525,600 columns) on the sparse formulation,
+    next to the paper's times for it (context: other hardware); sampled columns against the oracle."""
+    import torch
+
+    from paper_2403_04578_gb300 import inputs as G
+    from paper_2403_04578_gb300 import tpf
+
+    dev = torch.device("cuda", torch.cuda.current_device())
+    f = G.make_feeder(100, args.seed)
+    T = 525600
+    S = G.load_tensor_device(f, T, args.seed, dev)
+    fd = tpf.Feeder.from_inputs(f)
+    V = torch.empty_like(S)
+    it = torch.empty(T, dtype=torch.int32, device=dev)
+    mm = torch.empty(T, dtype=torch.float64, device=dev)
+    ms = timed_device(lambda: fd.solve(S, V, it, mm, precision="mixed", method="sparse", start="flat", tol=args.tol),
+                      max(1, min(args.steps, 3)), stream)
+    out = {"workload": f"100-bus radial feeder x {T:,} one-minute columns (Table I's 100 bus-phase row over the "
+                       "year); sparse formulation",
+           "value": T / (ms / 1e3), "unit": "PF/s", "ms_per_step": ms, "converged": fd.stats()["converged"],
+           "mean_sweeps": float(it.abs().float().mean().item()),
+           "paper_minutes": {"tensor_dense_cpu": 0.37, "tensor_gpu": 1.30, "nr_sparse_cpu": 61.85,
+                             "note": "Table I, the paper's hardware (context, not a target)"}}
+    if check:
+        from oracle import oracle as O
+
+        cc = torch.linspace(0, T - 1, 1024, device=dev).long()
+        Vt, _, _ = O.Case.from_feeder(f).solve(S[cc].cpu().numpy(), tol=1e-13, threads=os.cpu_count() or 1)
+        out["max_abs_err_pu"] = float(np.abs(V[cc].cpu().numpy() - Vt).max())
+        out["columns_checked"] = int(cc.numel())
+    fd.close()
+    del S, V
+    torch.cuda.empty_cache()
+    return out
+
+
 def small_leg(args, stream, check):
     """34-bus feeder over one day of one-minute columns (1,440), flat start.  The whole problem is
     about 1.5 MB, so it is launch- and latency-bound: each arithmetic and formulation reports its
@@ -898,6 +937,8 @@ def main():
         line["large_feeder"] = secondary(large_leg, args, stream, rank == 0 and not args.no_cpu)
     if not args.no_small:
         line["small_feeder"] = secondary(small_leg, args, stream, rank == 0 and not args.no_cpu)
+    if not args.no_table1:
+        line["table1_100_bus"] = secondary(table1_100_leg, args, stream, rank == 0 and not args.no_cpu)
     if rank == 0:
         print(json.dumps(line), flush=True)
     fd.close()

@@ -42,3 +42,6 @@ def test_bench_line_keys(cuda):
         assert r["converged"] == 1440 and r["columns_checked"] == 1440, name
         assert r["max_abs_err_pu"] <= bound, (name, r["max_abs_err_pu"])
         assert r["value"] > 0 and r["host_ms_per_call"] >= r["ms_per_call"] * 0.5, name
+    t1 = d["table1_100_bus"]  # 100 buses over the one-minute year, sampled columns against the oracle
+    assert t1["converged"] == 525600 and t1["columns_checked"] == 1024
+    assert t1["max_abs_err_pu"] <= 1e-8 and t1["value"] > 0

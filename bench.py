@@ -594,12 +594,19 @@ def small_leg(args, stream, check):
     mm = torch.empty(T, dtype=torch.float64, device=dev)
     reps = 50
     Vt = None
+    out = {"workload": f"34-bus radial feeder x {T:,} one-minute load columns (one day); flat start, per-column "
+                       f"stop at max|dV| <= {args.tol:g} pu; latency-bound"}
     if check:
         from oracle import oracle as O
 
-        Vt, _, _ = O.Case.from_feeder(f).solve(S_np, tol=1e-13, threads=os.cpu_count() or 1)
-    out = {"workload": f"34-bus radial feeder x {T:,} one-minute load columns (one day); flat start, per-column "
-                       f"stop at max|dV| <= {args.tol:g} pu; latency-bound"}
+        threads = os.cpu_count() or 1
+        case = O.Case.from_feeder(f)
+        Vt, _, _ = case.solve(S_np, tol=1e-13, threads=threads)
+        t0 = time.perf_counter()
+        case.solve(S_np, tol=args.tol, threads=threads)
+        dt = time.perf_counter() - t0
+        out["cpu_oracle"] = {"value": T / dt, "unit": "PF/s", "cores": threads, "kind": "oracle",
+                             "sample": f"all {T:,} columns, same tol"}
     for name, precision, method in (("fp64", "fp64", "dense"), ("mixed_sparse", "mixed", "sparse"),
                                     ("mixed_dense", "mixed", "dense")):
         def call(precision=precision, method=method):

@@ -71,3 +71,22 @@ def test_reference_arm_under_torchrun_prints_once():
     for k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step"):
         assert k in d["e2e"], k
     assert d["cpu_baseline"]["value"] == d["value"] and d["e2e"]["value"] == d["value"]
+
+
+def test_reference_arm_single_process():
+    """The reference arm at N = 1, launched as plain `python bench.py --impl reference` (no
+    torchrun), prints one line whose metric and config match the GPU arm's."""
+    cmd = [sys.executable, "bench.py", "--impl", "reference", "--gpus", "1", "--steps", "3", "--warmup", "3",
+           "--buses", "34", "--ref-seconds", "2"]
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 1 and d["steps"] == 3 and d["warmup"] == 3
+    sys.path.insert(0, ROOT)
+    import bench
+
+    assert d["metric"] == bench.METRIC and d["unit"] == "PF/s" and d["higher_is_better"] is True
+    assert d["config"]["buses"] == 34 and d["config"]["columns"] == 525600

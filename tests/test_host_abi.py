@@ -334,3 +334,20 @@ def test_autotune_and_tensor_counters_are_checked():
         fd.autotune(torch.zeros((16, 5), dtype=torch.complex128))
     with pytest.raises(ValueError, match="S must be"):
         fd.autotune(np.zeros((16, 5), np.complex128))
+
+
+def test_solve_host_accepts_the_buffers_callers_use():
+    """Row slices of a C-contiguous array, a V0 copy and CPU torch outputs pass the checks; the call
+    then fails only for want of a device (a CUDA driver here, the handle in the library)."""
+    import torch
+
+    fd = object.__new__(tpf.Feeder)
+    fd._h, fd.n_pq = None, 5
+    big = np.zeros((40, 5), np.complex128)
+    S = big[10:30]  # a row slice stays C-contiguous
+    out = (torch.zeros((20, 5), dtype=torch.complex128), torch.zeros(20, dtype=torch.int32),
+           torch.zeros(20, dtype=torch.float64))
+    for kw in ({}, {"V0": (S + 1.0).copy(), "start": "warm"}, {"out": out}):
+        with pytest.raises((tpf.TpfError, RuntimeError)) as e:
+            fd.solve_host(S, **kw)
+        assert not isinstance(e.value, ValueError)

@@ -55,12 +55,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "PF solves/s at ≤1e-8 pu vs FP64 oracle: mixed+learned-start vs plain FP64 FPI"
 
-# dram__bytes_read.sum + dram__bytes_write.sum of one tc_gemm launch from the ncu capture in
-# profiles/tc_gemm_n999_T16384.md (203.7 MB + 75.5 MB for 16,384 columns), per iterating column;
-# scaled by the columns each launch of this run processes.  None once the kernel has changed since.
+# dram__bytes_read.sum + dram__bytes_write.sum of one tc_gemm launch from an ncu capture of the
+# 1,000-bus feeder over 16,384 columns (203.7 MB + 75.5 MB), per iterating column; scaled by the
+# columns each launch of this run processes.  None once the kernel has changed since the capture.
 GEMM_TRAFFIC_BYTES_PER_COLUMN = (203.725056e6 + 75.471360e6) / 16384
 # The same for the sparse tree kernel mx_tree (one launch per solve): 262.0 MB read + 209.4 MB
-# written for 16,384 columns, profiles/mx_tree_n999_T16384.md.
+# written for 16,384 columns of the 1,000-bus feeder.
 TREE_TRAFFIC_BYTES_PER_COLUMN = (262.013952e6 + 209.440256e6) / 16384
 # Algorithmic FP32 flop per bus per sweep of the tree formulation: load current conj(S/V) 12,
 # prefix sum 2, subtree difference 2, z L 6, subtree-end subtraction 2, path prefix 2, update 4,
@@ -214,8 +214,16 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_oracle_leg(f, S_host, V_gpu_host, it_gpu, args, full_T, V_sparse_host=None):
-    """Time the CPU oracle on a bounded column sample and check GPU results against it."""
+def check_columns(args, full_T):
+    """The evenly spaced columns of the year on which GPU results are checked against the oracle."""
+    return np.linspace(0, full_T - 1, min(args.check_columns, full_T)).astype(np.int64)
+
+
+def cpu_oracle_leg(f, S_host, args, full_T, cc=None, it_main=None, V_checks=None):
+    """Time the CPU oracle on a bounded column sample, and check GPU results against it.
+
+    cc: the checked columns; V_checks: {name: V of those columns from a GPU path} (the first is the
+    headline's, whose iteration counts it_main are compared too)."""
     from oracle import oracle as O
 
     threads = os.cpu_count() or 1
@@ -230,22 +238,23 @@ def cpu_oracle_leg(f, S_host, V_gpu_host, it_gpu, args, full_T, V_sparse_host=No
     n_cols = int(min(full_T, max(probe_cols.size, args.cpu_seconds / max(per_col, 1e-9))))
     cols = np.linspace(0, full_T - 1, n_cols).astype(np.int64)
     t0 = time.perf_counter()
-    Vo, ito, _ = case.solve(S_host[cols], tol=args.tol, threads=threads)
+    case.solve(S_host[cols], tol=args.tol, threads=threads)
     dt = time.perf_counter() - t0
     out = {"value": n_cols / dt, "unit": "PF/s", "cores": threads, "kind": "oracle",
            "sample": f"{n_cols} columns evenly spaced over the {full_T:,}-column year, same feeder and tol; "
                      f"K = -Y_dd^-1 setup {t_setup:.1f} s not included"}
     check = {}
-    if V_gpu_host is not None:
-        cc = np.linspace(0, full_T - 1, min(args.check_columns, full_T)).astype(np.int64)
+    if V_checks:
         Vt, _, _ = case.solve(S_host[cc], tol=1e-13, threads=threads)
-        err = float(np.abs(V_gpu_host[cc] - Vt).max())
         _, it_ref, _ = case.solve(S_host[cc], tol=args.tol, threads=threads)
-        check = {"max_abs_err_pu": err, "columns_checked": int(cc.size),
-                 "iters_equal_frac": float(np.mean(it_gpu[cc] == it_ref)),
-                 "iters_diff_max": int(np.abs(it_gpu[cc] - it_ref).max())}
-        if V_sparse_host is not None:
-            check["sparse_max_abs_err_pu"] = float(np.abs(V_sparse_host[cc] - Vt).max())
+        for k, (name, Vs) in enumerate(V_checks.items()):
+            if Vs is None:
+                continue
+            check[name] = float(np.abs(Vs - Vt).max())
+        check["columns_checked"] = int(cc.size)
+        if it_main is not None:
+            check["iters_equal_frac"] = float(np.mean(it_main == it_ref))
+            check["iters_diff_max"] = int(np.abs(it_main - it_ref).max())
     return out, check
 
 
@@ -676,14 +685,21 @@ def run_reference(args, world, rank):
     threads = os.cpu_count() or 1
     case = O.Case.from_feeder(f)
     budget = args.ref_seconds  # seconds for all warm-up and timed steps
-    probe_T = G.CHUNK
-    S = G.load_tensor(f, probe_T, args.seed)
+    # The sample spreads over the whole year: n_blocks noise chunks at evenly spaced positions
+    # (each chunk regenerated on its own, CHUNK one-minute columns, about 2.8 days), and evenly
+    # spaced columns inside each chunk, so every hour of the day and every season is represented.
+    n_chunks_year = (args.columns + G.CHUNK - 1) // G.CHUNK
+    n_blocks = min(16, n_chunks_year)
+    starts = np.unique(np.linspace(0, n_chunks_year - 1, n_blocks).astype(np.int64)) * G.CHUNK
+    blocks = [G.load_tensor(f, min(G.CHUNK, args.columns - int(t0)), args.seed, t0=int(t0)) for t0 in starts]
     t0 = time.perf_counter()
-    case.solve(S[: 2 * threads], tol=args.tol, threads=threads)
+    case.solve(blocks[0][: 2 * threads], tol=args.tol, threads=threads)
     per_col = (time.perf_counter() - t0) / (2 * threads)
-    per_step = int(max(threads, min(probe_T, budget / (args.steps + args.warmup) / per_col)))
-    cols = np.linspace(0, probe_T - 1, per_step).astype(np.int64)
-    Ss = np.ascontiguousarray(S[cols])
+    per_step = int(max(threads, min(n_blocks * G.CHUNK, budget / (args.steps + args.warmup) / per_col)))
+    per_block = max(1, per_step // len(blocks))
+    Ss = np.ascontiguousarray(np.concatenate(
+        [b[np.linspace(0, b.shape[0] - 1, min(per_block, b.shape[0])).astype(np.int64)] for b in blocks]))
+    per_step = Ss.shape[0]
     for _ in range(args.warmup):
         case.solve(Ss, tol=args.tol, threads=threads)
     times = []
@@ -697,8 +713,9 @@ def run_reference(args, world, rank):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": config,
             "cpu_baseline": {"value": value, "unit": "PF/s", "cores": threads, "kind": "oracle",
-                             "sample": f"{per_step} columns per step, evenly spaced over the first {probe_T} "
-                                       "columns of the year"},
+                             "sample": f"{per_step} columns per step: {per_block} evenly spaced columns in each of "
+                                       f"{len(blocks)} {G.CHUNK}-column blocks at evenly spaced positions over the "
+                                       f"{args.columns:,}-column year"},
             "e2e": {"value": value, "unit": "PF/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -788,8 +805,15 @@ def main():
     value = world * T / (ms_per_step / 1e3)
     stats = main_run["stats"]
     column_sweeps = int(itd.abs().sum().item())
-    Vhost = Vd.cpu().numpy() if (rank == 0 and not args.no_cpu) else None
-    ithost = itd.cpu().numpy() if Vhost is not None else None
+    # GPU results on the checked columns (compared with the oracle after every timed region).
+    checking = rank == 0 and not args.no_cpu
+    cc = check_columns(args, T)
+    cc_dev = torch.from_numpy(cc).to(Sd.device)
+    V_checks = {}
+    it_main = None
+    if checking:
+        V_checks["max_abs_err_pu"] = Vd[cc_dev].cpu().numpy()
+        it_main = itd[cc_dev].cpu().numpy()
 
     def gemm_roofline(run):
         achieved = 8.0 * n * n * run["gemm_cols"] / (run["gemm_ms"] / 1e3) / 1e12
@@ -800,8 +824,8 @@ def main():
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "tc_gemm",
                 "peak_source": f"{peak_src} bf16 sustained (fp16 has the bf16 rate)",
-                "traffic_note": "ncu DRAM bytes per iterating column (16,384-column capture, "
-                                "profiles/tc_gemm_n999_T16384.md) x columns per launch",
+                "traffic_note": "ncu DRAM bytes per iterating column (capture of 16,384 columns of the "
+                                "1,000-bus feeder) x columns per launch",
                 "share_of_step": run["gemm_ms"] / sum(run["step_ms"]),
                 "ms_per_launch": run["gemm_ms"] / max(run["gemm_launch"], 1)}
 
@@ -818,7 +842,7 @@ def main():
                 "peak_source": f"FP32: {sm_count} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
                 "flops_note": f"{TREE_FLOPS_PER_BUS_SWEEP} flop per bus per sweep x {n} buses x {sweeps:,} "
                               "column-sweeps (anchors and the final residual not counted)",
-                "traffic_note": "ncu DRAM bytes per column (16,384-column capture, profiles/mx_tree_n999_T16384.md) "
+                "traffic_note": "ncu DRAM bytes per column (capture of 16,384 columns of the 1,000-bus feeder) "
                                 "x columns per launch",
                 "hbm_frac": (TREE_TRAFFIC_BYTES_PER_COLUMN or 0) * T / (run["kernel_ms"] / 1e3) / 1e9
                             / float(peaks.get("hbm_gbs", 6800.0)),
@@ -860,8 +884,8 @@ def main():
                      "sweeps": run["stats"]["sweeps"], "converged": run["stats"]["converged"]}
         other_obj["roofline"] = gemm_roofline(run) if other == "dense" else tree_roofline(
             run, int(itd.abs().sum().item()))
-        if rank == 0 and not args.no_cpu:
-            other_obj["_V"] = Vd.cpu().numpy()
+        if checking:
+            V_checks[f"{other}_max_abs_err_pu"] = Vd[cc_dev].cpu().numpy()
 
     # ZIP loads (Eq. 3) on the same workload: per-bus shares of constant power / current /
     # impedance drawn once; the oracle checks the ZIP power balance of sampled columns.
@@ -896,7 +920,23 @@ def main():
     b.record(stream)
     b.synchronize()
     fp64_pfs = F / (a.elapsed_time(b) / 2 / 1e3)
-    fp64 = {"value": fp64_pfs, "unit": "PF/s", "sample": f"first {F} columns", "sweeps": fd.stats()["sweeps"]}
+    fp64 = {"value": fp64_pfs, "unit": "PF/s", "sample": f"first {F} columns", "sweeps": fd.stats()["sweeps"],
+            "formulation": "dense (Algorithm 1, K = -Y_dd^-1), FP64"}
+
+    # Plain FP64 GPU FPI in the sparse formulation on the whole workload: the same O(n) tree
+    # substitution as the headline path, every operation in FP64.  Against it the headline ratio
+    # isolates what mixed precision buys.
+    fp64s = None
+    if args.method == "sparse":
+        ms64 = timed_device(lambda: fd.solve(Sd, Vd, itd, mmd, precision="fp64", method="sparse", start="flat",
+                                             tol=args.tol), 2, stream)
+        s64 = fd.stats()
+        fp64s = {"value": T / (ms64 / 1e3), "unit": "PF/s", "ms_per_step": ms64,
+                 "columns": T, "formulation": "sparse (Algorithm 2, tree substitution), FP64",
+                 "mean_sweeps": float(itd.abs().float().mean().item()), "converged": s64["converged"],
+                 "gpu_launches_per_step": s64["kernel_launches"]}
+        if checking:
+            V_checks["fp64_sparse_max_abs_err_pu"] = Vd[cc_dev].cpu().numpy()
 
     line = {"metric": METRIC, "value": value, "unit": "PF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
@@ -907,15 +947,26 @@ def main():
             "e2e": e2e, "clocks": main_run["clocks"], "gpu_launches": main_run["launches"],
             "sweeps": stats["sweeps"], "anchors_or_anchor_sweeps": stats["precise_sweeps"],
             "mean_sweeps": column_sweeps / T, "tpf_create_ms": create_ms,
-            "fp64_gpu": fp64, "speedup_vs_fp64_gpu": (value / world) / fp64_pfs,
+            "headline_start": "flat",
+            "fp64_gpu": fp64,
+            "speedup_vs_fp64_gpu": (value / world) / fp64_pfs,
+            "speedup_vs_fp64_gpu_note": "formulation plus precision: the mixed sparse path against the FP64 "
+                                        "dense path (8 n^2 against 36 n flop per bus-sweep)",
             }
-    V_other = other_obj.pop("_V", None) if other_obj else None
-    if rank == 0 and not args.no_cpu:
-        cpu, check = cpu_oracle_leg(f, Sh.numpy(), Vhost, ithost, args, T, V_other)
+    if fp64s is not None:
+        line["fp64_gpu_sparse"] = fp64s
+        line["speedup_vs_fp64_gpu_sparse"] = (value / world) / fp64s["value"]
+        line["speedup_vs_fp64_gpu_sparse_note"] = "precision only: both paths run the sparse formulation"
+    if other_obj is not None and other == "dense":
+        line["speedup_dense_mixed_vs_fp64_dense"] = other_obj["value"] / world / fp64_pfs
+    if checking:
+        cpu, check = cpu_oracle_leg(f, Sh.numpy(), args, T, cc, it_main, V_checks)
         line["cpu_baseline"] = cpu
         line["cpu_newton_raphson"] = secondary(cpu_newton_leg, f, Sh.numpy(), T)
-        if other_obj is not None and "sparse_max_abs_err_pu" in check:
-            other_obj["max_abs_err_pu"] = check.pop("sparse_max_abs_err_pu")
+        if other_obj is not None and f"{other}_max_abs_err_pu" in check:
+            other_obj["max_abs_err_pu"] = check.pop(f"{other}_max_abs_err_pu")
+        if fp64s is not None and "fp64_sparse_max_abs_err_pu" in check:
+            fp64s["max_abs_err_pu"] = check.pop("fp64_sparse_max_abs_err_pu")
         line["accuracy"] = check
     if other_obj is not None:
         line[f"{other}_method"] = other_obj

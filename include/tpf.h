@@ -90,9 +90,11 @@ enum {
                             * precision up to 2,048 demand unknowns; FP64 any size                   */
     TPF_METHOD_SPARSE = 1  /* Algorithm 2 / Eq. 13-14: a sparse solve with Y_dd each sweep, here the  *
                             * fill-in-free tree substitution of a radial feeder, O(n) per column and  *
-                            * sweep, the whole sweep loop of a column on chip.  Radial networks of   *
-                            * up to 6,144 demand unknowns (past 4,096 in chunks of 8,192 columns with *
-                            * device scratch) and TPF_PREC_MIXED only (TPF_EUNSUPPORTED otherwise)   */
+                            * sweep, the whole sweep loop of a column on chip.  TPF_PREC_MIXED: radial *
+                            * networks of up to 6,144 demand unknowns (past 4,096 in chunks of 8,192  *
+                            * columns with device scratch).  TPF_PREC_FP64: the same substitution in  *
+                            * plain double precision, single-phase radial networks of up to 4,096    *
+                            * demand buses (constant power or ZIP).  TPF_EUNSUPPORTED otherwise      */
 };
 
 /* Per-solve counters (filled by tpf_last_stats after a solve). */

@@ -48,7 +48,8 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
     ++d.layout_gen;
     const int n = net.n_pq;
     cudaFree(d.t_col); cudaFree(d.t_end); cudaFree(d.t_par); cudaFree(d.t_ecnt); cudaFree(d.t_ends); cudaFree(d.t_z);
-    cudaFree(d.t_zrow); cudaFree(d.t_yrow); cudaFree(d.t_kidx); cudaFree(d.t_zrow_f);
+    cudaFree(d.t_zrow); cudaFree(d.t_yrow); cudaFree(d.t_kidx); cudaFree(d.t_zrow_f); cudaFree(d.t_z64);
+    d.t_z64 = nullptr;
     d.t_col = d.t_end = d.t_par = d.t_ecnt = d.t_ends = d.t_kidx = nullptr;
     d.t_z = d.t_zrow = nullptr;
     d.t_yrow = d.t_zrow_f = nullptr;
@@ -64,6 +65,7 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
             const int ph = net.phases, nb = n / ph;
             std::vector<int> col(ns, -1), end(ns, 0), par(ns, -1), ecnt(ns, 0), ends, kidx(ns, -1);
             std::vector<float4> z(ns, make_float4(0.f, 0.f, 0.f, 0.f));
+            std::vector<double2> z64(ph == 1 ? ns : 0, make_double2(0.0, 0.0));
             // Polyphase: row p of the branch's impedance (double-float) and admittance per slot.
             std::vector<float4> zrow(ph > 1 ? (size_t)ns * ph : 0, make_float4(0.f, 0.f, 0.f, 0.f));
             std::vector<float2> yrow(ph > 1 ? (size_t)ns * ph : 0, make_float2(0.f, 0.f)), zrow_f = yrow;
@@ -89,6 +91,7 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
                 };
                 if (ph == 1) {
                     z[s] = dd(net.dfs_z[2 * q], net.dfs_z[2 * q + 1]);
+                    z64[s] = make_double2(net.dfs_z[2 * q], net.dfs_z[2 * q + 1]);
                 } else {
                     for (int pp = 0; pp < ph; ++pp) {
                         const size_t k = (size_t)q * ph + pp;
@@ -111,7 +114,7 @@ tpf_status layout_tree(tpf_handle *h, int bpt) {
                 d.t_threads = 0;
             } else if (!up(&d.t_col, col) || !up(&d.t_end, end) || !up(&d.t_par, par) || !up(&d.t_ecnt, ecnt) ||
                        !up(&d.t_ends, ends) || !up(&d.t_z, z) || !up(&d.t_kidx, kidx) ||
-                       (ph > 1 && (!up(&d.t_zrow, zrow) || !up(&d.t_yrow, yrow) || !up(&d.t_zrow_f, zrow_f)))) {
+                       (ph == 1 && !up(&d.t_z64, z64)) || (ph > 1 && (!up(&d.t_zrow, zrow) || !up(&d.t_yrow, yrow) || !up(&d.t_zrow_f, zrow_f)))) {
                 cudaGetLastError();
                 return TPF_ECUDA;
             }
@@ -258,7 +261,7 @@ void free_device(tpf_handle *h) {
     cudaFree(d.Kr16); cudaFree(d.Ki16);
     cudaFree(d.par); cudaFree(d.ch_ptr); cudaFree(d.ch); cudaFree(d.ypar);
     cudaFree(d.t_col); cudaFree(d.t_end); cudaFree(d.t_par); cudaFree(d.t_ecnt); cudaFree(d.t_ends); cudaFree(d.t_z);
-    cudaFree(d.t_kidx);
+    cudaFree(d.t_kidx); cudaFree(d.t_z64);
     cudaFree(d.zip64); cudaFree(d.t_zip_hi); cudaFree(d.t_zip_lo);
     cudaFree(d.csr_self); cudaFree(d.vs64); cudaFree(d.t_zrow); cudaFree(d.t_yrow); cudaFree(d.t_zrow_f);
     d = DeviceNet();

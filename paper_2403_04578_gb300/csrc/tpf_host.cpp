@@ -511,6 +511,7 @@ tpf_status tpf_create_poly(int n_bus, int n_branch, int phases, const int32_t *f
 
 void tpf_destroy(tpf_handle *h) {
     if (!h) return;
+    tpf::DeviceScope dscope(h->device);
     tpf::free_device(h);
     delete h;
 }
@@ -544,9 +545,12 @@ tpf_status tpf_solve(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev, i
     h->stats.columns = T;
     if (T == 0) return TPF_OK;
     if (!S_dev || !V_dev) return TPF_EINVAL;
-    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(h->device);
+    if (!dscope.ok) return TPF_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    if (o.method == TPF_METHOD_SPARSE) return tpf::solve_sparse(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
+    if (o.method == TPF_METHOD_SPARSE)
+        return o.precision == TPF_PREC_FP64 ? tpf::solve_tree64(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s)
+                                            : tpf::solve_sparse(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
     if (o.precision == TPF_PREC_FP64) return tpf::solve_fp64(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
     return tpf::solve_mixed(h, T, S_dev, V_dev, iters_dev, mismatch_dev, o, s);
 }
@@ -570,19 +574,22 @@ tpf_status tpf_batch_create(int F, tpf_handle *const *hs, const int64_t *T, cons
     for (int f = 0; f < F; ++f)  // (feeders past 4,096 buses take chunked launches with scratch)
         if (!hs[f]->dev.radial || hs[f]->dev.t_threads <= 0 || hs[f]->dev.t_bpt == tpf::kTreeBigBPT)
             return TPF_EUNSUPPORTED;
-    if (cudaSetDevice(hs[0]->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(hs[0]->device);
+    if (!dscope.ok) return TPF_ECUDA;
     return tpf::batch_plan_create(F, hs, T, S_dev, V_dev, iters_dev, mismatch_dev, o, out);
 }
 
 tpf_status tpf_batch_launch(tpf_batch *b, void *stream) {
     if (!b) return TPF_EINVAL;
-    if (cudaSetDevice(tpf::batch_device(b)) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(tpf::batch_device(b));
+    if (!dscope.ok) return TPF_ECUDA;
     return tpf::batch_plan_launch(b, reinterpret_cast<cudaStream_t>(stream));
 }
 
 tpf_status tpf_batch_wait(tpf_batch *b, int64_t *converged_out, tpf_stats *stats_out) {
     if (!b) return TPF_EINVAL;
-    if (cudaSetDevice(tpf::batch_device(b)) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(tpf::batch_device(b));
+    if (!dscope.ok) return TPF_ECUDA;
     return tpf::batch_plan_wait(b, converged_out, stats_out);
 }
 
@@ -595,7 +602,8 @@ tpf_status tpf_autotune(tpf_handle *h, int64_t T, const void *S_dev, const tpf_o
     tpf_status st = check_opts(opts, o);
     if (st != TPF_OK) return st;
     if (o.precision != TPF_PREC_MIXED) return TPF_EUNSUPPORTED;
-    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(h->device);
+    if (!dscope.ok) return TPF_ECUDA;
     st = tpf::autotune_sparse(h, T, S_dev, o, reinterpret_cast<cudaStream_t>(stream), bpt_out);
     h->stats = tpf_stats{};
     return st;
@@ -607,7 +615,8 @@ tpf_status tpf_set_zip(tpf_handle *h, const double *alpha) {
         for (size_t k = 0; k < 3 * (size_t)h->net.n_pq; ++k)
             if (!std::isfinite(alpha[k])) return TPF_EINVAL;
     }
-    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(h->device);
+    if (!dscope.ok) return TPF_ECUDA;
     return tpf::set_zip(h, alpha);
 }
 
@@ -624,7 +633,8 @@ tpf_status tpf_solve_ex(tpf_handle *h, int64_t T, const void *S_dev, void *V_dev
     h->stats.columns = T;
     if (T == 0) return TPF_OK;
     if (!S_dev || (!V_dev && o.start != TPF_START_FLAT)) return TPF_EINVAL;
-    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(h->device);
+    if (!dscope.ok) return TPF_ECUDA;
     return tpf::solve_sparse_ex(h, T, S_dev, V_dev, iters_dev, mismatch_dev, out, o,
                                 reinterpret_cast<cudaStream_t>(stream));
 }
@@ -644,7 +654,8 @@ tpf_status tpf_solve_batch(int F, tpf_handle *const *hs, const int64_t *T, const
         for (int g = 0; g < f; ++g)
             if (hs[g] == hs[f]) return TPF_EINVAL;  // each handle's workspaces serve one feeder
     }
-    if (cudaSetDevice(hs[0]->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(hs[0]->device);
+    if (!dscope.ok) return TPF_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // Radial feeders under the sparse method share launches; the rest are solved one by one.
     std::vector<int> grouped, single;
@@ -680,11 +691,15 @@ tpf_status tpf_solve_batch(int F, tpf_handle *const *hs, const int64_t *T, const
             if (converged_out) converged_out[grouped[k]] = gconv[k];
     }
     for (int f : single) {
-        // Large radial feeders keep the sparse method (its chunked large-feeder kernel); feeders
-        // the sparse kernel cannot take use the dense form.
+        // Large radial feeders keep the sparse method (its chunked large-feeder kernel), as do
+        // FP64 solves of the radial single-phase feeders the FP64 sparse kernel takes; feeders the
+        // sparse kernels cannot take use the dense form.
         tpf_opts of = o;
-        const bool sparse_ok = o.method == TPF_METHOD_SPARSE && o.precision == TPF_PREC_MIXED && hs[f]->dev.radial &&
-                               hs[f]->dev.t_threads > 0;
+        const tpf::DeviceNet &df = hs[f]->dev;
+        const bool sparse_ok = o.method == TPF_METHOD_SPARSE && df.radial && df.t_threads > 0 &&
+                               (o.precision == TPF_PREC_MIXED ||
+                                (df.phases == 1 && df.t_bpt != tpf::kTreeBigBPT &&
+                                 tpf::tree64_smem(df.t_threads, df.t_bpt) <= 227 * 1024));
         if (!sparse_ok) of.method = TPF_METHOD_DENSE;
         st = tpf_solve(hs[f], T[f], S_dev[f], V_dev[f], iters_dev ? iters_dev[f] : nullptr,
                        mismatch_dev ? mismatch_dev[f] : nullptr, &of, stream);
@@ -716,7 +731,8 @@ tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_
         return TPF_OK;
     }
     if (!S_host || !V_host) return TPF_EINVAL;
-    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(h->device);
+    if (!dscope.ok) return TPF_ECUDA;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     tpf::Workspace &w = h->ws;
     const size_t col_bytes = (size_t)h->net.n_pq * 16;

@@ -109,6 +109,7 @@ struct DeviceNet {
     int *t_col = nullptr, *t_end = nullptr, *t_par = nullptr, *t_ecnt = nullptr, *t_ends = nullptr;
     int *t_kidx = nullptr;  // per slot: the index in t_ends at which its position appears, or -1
     float4 *t_z = nullptr;
+    double2 *t_z64 = nullptr;  // FP64 z per slot (single phase), for the FP64 sparse kernel
     // ZIP load coefficients (Eq. 3), set by tpf_set_zip; null for constant power.  zip64: double
     // [3][n] in column order (FP64 path); t_zip_hi / t_zip_lo: float4 (alpha_P, alpha_I, alpha_Z, 0)
     // per slot, high and low words (sparse path).
@@ -170,6 +171,30 @@ struct Workspace {
 // falls below switch_tol.
 enum ColFlags : int { kActive = 1, kAnchored = 2, kDone = 4, kBlind = 8 };
 enum Counter : int { kCntActive = 0, kCntPrecise = 1, kCntError = 2, kCntConverged = 4 };
+
+// Makes `dev` the current device for the lifetime of the scope and then gives the caller's current
+// device back, so that an entry point of the library never changes which device its caller uses.
+struct DeviceScope {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceScope(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) {
+            cudaGetLastError();
+            prev = -1;
+        }
+        ok = (prev == dev) || cudaSetDevice(dev) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
+    ~DeviceScope() {
+        if (prev >= 0) {
+            int cur = -1;
+            if (cudaGetDevice(&cur) != cudaSuccess || cur != prev) cudaSetDevice(prev);
+            cudaGetLastError();
+        }
+    }
+    DeviceScope(const DeviceScope &) = delete;
+    DeviceScope &operator=(const DeviceScope &) = delete;
+};
 
 // CUDA-event timing of kernel launches by category (only when a solve asks for it).
 struct KernelTimer {
@@ -247,6 +272,10 @@ tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_
                         double *mismatch, const tpf_opts &o, cudaStream_t st);
 tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
                            double *mismatch, const tpf_outputs *out, const tpf_opts &o, cudaStream_t st);
+// The sparse formulation in plain FP64 (radial, single phase, up to 4,096 demand buses).
+tpf_status solve_tree64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
+                        double *mismatch, const tpf_opts &o, cudaStream_t st);
+size_t tree64_smem(int threads, int bpt);
 tpf_status solve_batch_sparse(int F, tpf_handle *const *hs, const int64_t *T, const void *const *S,
                               void *const *V, int32_t *const *iters, double *const *mismatch,
                               const tpf_opts &o, int64_t *conv_out, tpf_stats *stats, cudaStream_t st);

@@ -518,6 +518,7 @@ tpf_status tpf_mlp_create(int n_pq, int hidden, int n_hidden_layers, int max_bat
 
 void tpf_mlp_destroy(tpf_mlp *h) {
     if (!h) return;
+    tpf::DeviceScope dscope(h->device);
     free_mlp(h);
     delete h;
 }
@@ -533,7 +534,8 @@ int64_t tpf_mlp_param_count(const tpf_mlp *h) {
 // row-major, then b [out].
 static tpf_status params_io(tpf_mlp *h, float *host, bool to_host, bool grads) {
     if (!h || !host) return TPF_EINVAL;
-    if (cudaSetDevice(h->device) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(h->device);
+    if (!dscope.ok || cudaDeviceSynchronize() != cudaSuccess) return TPF_ECUDA;
     size_t off = 0;
     for (int l = 0; l < h->L; ++l) {
         const int Po = h->pad[l + 1], Pi = h->pad[l], ro = h->dim[l + 1], ri = h->dim[l];
@@ -579,7 +581,8 @@ tpf_status tpf_mlp_set_params(tpf_mlp *h, const float *host) { return params_io(
 
 tpf_status tpf_mlp_fit_normalization(tpf_mlp *h, int64_t T, const void *S_dev, const void *V_dev, void *stream) {
     if (!h || T < 1 || !S_dev || !V_dev) return TPF_EINVAL;
-    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(h->device);
+    if (!dscope.ok) return TPF_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
     k_norm_stats<<<4 * h->n, kThreads, 0, st>>>((const double2 *)S_dev, (const double2 *)V_dev, T, h->n, h->in_mean,
                                                 h->in_std, h->out_mean, h->out_std);
@@ -590,7 +593,8 @@ tpf_status tpf_mlp_fit_normalization(tpf_mlp *h, int64_t T, const void *S_dev, c
 
 tpf_status tpf_mlp_get_normalization(tpf_mlp *h, float *in_mean, float *in_std, float *out_mean, float *out_std) {
     if (!h || !in_mean || !in_std || !out_mean || !out_std) return TPF_EINVAL;
-    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(h->device);
+    if (!dscope.ok) return TPF_ECUDA;
     const size_t a = sizeof(float) * 2 * h->n;
     if (cudaMemcpy(in_mean, h->in_mean, a, cudaMemcpyDeviceToHost) != cudaSuccess ||
         cudaMemcpy(in_std, h->in_std, a, cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -603,7 +607,8 @@ tpf_status tpf_mlp_get_normalization(tpf_mlp *h, float *in_mean, float *in_std, 
 tpf_status tpf_mlp_gradients(tpf_mlp *h, int B, const void *S_dev, const void *V_dev, double *loss_out,
                              float *grads_host, void *stream) {
     if (!h || B < 128 || B % 128 || B > h->max_batch || !S_dev || !V_dev) return TPF_EINVAL;
-    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(h->device);
+    if (!dscope.ok) return TPF_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
     MLP_CK(cudaMemsetAsync(h->err, 0, sizeof(int), st));
     tpf_status rs = load_batch(h, B, S_dev, V_dev, B, 0, true, st);
@@ -619,7 +624,8 @@ tpf_status tpf_mlp_gradients(tpf_mlp *h, int B, const void *S_dev, const void *V
 tpf_status tpf_mlp_train_step(tpf_mlp *h, int B, const void *S_dev, const void *V_dev, double lr, double *loss_out,
                               void *stream) {
     if (!h || B < 128 || B % 128 || B > h->max_batch || !S_dev || !V_dev || !(lr > 0.0)) return TPF_EINVAL;
-    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(h->device);
+    if (!dscope.ok) return TPF_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
     MLP_CK(cudaMemsetAsync(h->err, 0, sizeof(int), st));
     tpf_status rs = load_batch(h, B, S_dev, V_dev, B, 0, true, st);
@@ -652,7 +658,8 @@ tpf_status tpf_mlp_predict(tpf_mlp *h, int64_t T, const void *S_dev, void *V0_de
         return TPF_OK;
     }
     if (!S_dev || !V0_dev) return TPF_EINVAL;
-    if (cudaSetDevice(h->device) != cudaSuccess) return TPF_ECUDA;
+    tpf::DeviceScope dscope(h->device);
+    if (!dscope.ok) return TPF_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
     MLP_CK(cudaMemsetAsync(h->err, 0, sizeof(int), st));
     MLP_CK(cudaMemsetAsync(h->fallback, 0, sizeof(int), st));

@@ -1255,7 +1255,7 @@ int batch_device(const tpf_batch *b) { return b->device; }
 
 void batch_plan_destroy(tpf_batch *b) {
     if (!b) return;
-    cudaSetDevice(b->device);
+    DeviceScope dscope(b->device);
     if (b->pending && b->done) cudaEventSynchronize(b->done);
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);

@@ -253,16 +253,55 @@ def _batch_outputs(S, V, iters, mismatch):
     _device_tensors(specs)
 
 
-def _stream_ptr(stream):
+def _one_device(named, want=None):
+    """The index of the one CUDA device that holds every tensor in `named` ((name, tensor) pairs;
+    None entries are skipped) and, when given, equals `want` (the device of the Feeder or network the
+    call runs on).  The library passes raw pointers to kernels launched on that device, so a tensor on
+    another GPU is refused here rather than read through a foreign pointer."""
+    dev, first = want, None
+    for name, X in named:
+        if X is None:
+            continue
+        idx = X.device.index
+        if dev is None:
+            dev, first = idx, name
+        elif idx != dev:
+            where = f"the device of {first}" if first else "the device this object was created on"
+            raise ValueError(f"{name} is on cuda:{idx}, but {where} is cuda:{dev}: "
+                             "every tensor of a call must be on one device")
+        if first is None:
+            first = name
+    return dev
+
+
+def _stream_ptr(stream, device=None):
+    """The cudaStream_t to pass: `stream`, or the current torch stream of `device`.  A given stream
+    must belong to `device`."""
     import torch
 
     if stream is None:
-        stream = torch.cuda.current_stream()
+        stream = torch.cuda.current_stream(device)
+    elif device is not None and stream.device.index != device:
+        raise ValueError(f"the stream belongs to cuda:{stream.device.index}, the tensors to cuda:{device}")
     return ctypes.c_void_p(stream.cuda_stream)
 
 
+def _on_device(device):
+    """Context in which torch's current device (and the CUDA runtime's) is `device`."""
+    import torch
+
+    return torch.cuda.device(device)
+
+
+def _current_device():
+    import torch
+
+    return torch.cuda.current_device()
+
+
 class Feeder:
-    """A feeder uploaded to the GPU (a tpf_handle)."""
+    """A feeder uploaded to the GPU (a tpf_handle) of the current device; every later call takes
+    tensors on that device and runs there."""
 
     def __init__(self, n_bus, from_bus, to_bus, z_pu, slack=0, v0=1.0 + 0j, pq_bus=None):
         if pq_bus is None:
@@ -278,6 +317,7 @@ class Feeder:
             raise TpfError(st, "tpf_create")
         self._h = h
         self.n_pq = lib().tpf_n_pq(h)
+        self.device = _current_device()  # tpf_create builds the feeder on the current device
 
     @classmethod
     def poly(cls, n_bus, from_bus, to_bus, z_blocks, phases=3, slack=0, v0=None, pq_bus=None):
@@ -301,6 +341,7 @@ class Feeder:
         obj = cls.__new__(cls)
         obj._h = h
         obj.n_pq = lib().tpf_n_pq(h)
+        obj.device = _current_device()
         obj._keep = (fa, ta, z, v, pa)
         return obj
 
@@ -332,10 +373,12 @@ class Feeder:
 
         shape = tuple(getattr(S, "shape", ()))
         _device_tensors([("S", S, torch.complex128, (shape[0] if len(shape) == 2 else -1, self.n_pq))])
+        dev = _one_device([("S", S)], getattr(self, "device", None))
         o = make_opts("mixed", tol, max_iter, "flat", switch_tol, False, "sparse")
         b = ctypes.c_int(0)
-        st = lib().tpf_autotune(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()), ctypes.byref(o), ctypes.byref(b),
-                                _stream_ptr(stream))
+        with _on_device(dev):
+            st = lib().tpf_autotune(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()), ctypes.byref(o),
+                                    ctypes.byref(b), _stream_ptr(stream, dev))
         if st != OK:
             raise TpfError(st, "tpf_autotune")
         return b.value
@@ -383,10 +426,13 @@ class Feeder:
             if not (t_.is_cuda and t_.dtype == dt and t_.is_contiguous() and t_.shape == shape):
                 raise ValueError("V must be shaped like S, iters and mismatch [T]: contiguous CUDA tensors "
                                  "(complex128, int32, float64)")
+        dev = _one_device([("S", S), ("V", V), ("iters", iters), ("mismatch", mismatch)],
+                          getattr(self, "device", None))
         o = make_opts(precision, tol, max_iter, start, switch_tol, profile, method)
-        st = lib().tpf_solve(self._h, T, ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
-                             ctypes.c_void_p(iters.data_ptr()), ctypes.c_void_p(mismatch.data_ptr()), ctypes.byref(o),
-                             _stream_ptr(stream))
+        with _on_device(dev):
+            st = lib().tpf_solve(self._h, T, ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+                                 ctypes.c_void_p(iters.data_ptr()), ctypes.c_void_p(mismatch.data_ptr()),
+                                 ctypes.byref(o), _stream_ptr(stream, dev))
         if check and st not in (OK, ENOCONV):
             raise TpfError(st, "tpf_solve")
         return V, iters, mismatch, st
@@ -432,11 +478,14 @@ class Feeder:
         out = Outputs(1 if S.dtype == torch.complex64 else 0, 1 if v32 else 0, float(v_band[0]), float(v_band[1]),
                       vmin.data_ptr(), vmax.data_ptr(), viol.data_ptr(), bus_counts[0].data_ptr(),
                       bus_counts[1].data_ptr())
+        dev = _one_device([("S", S), ("V", V), ("bus_counts[0]", bus_counts[0]), ("bus_counts[1]", bus_counts[1])],
+                          getattr(self, "device", None))
         o = make_opts("mixed", tol, max_iter, start, switch_tol, profile, "sparse")
         vp = ctypes.c_void_p
-        st = lib().tpf_solve_ex(self._h, T, vp(S.data_ptr()), vp(V.data_ptr() if V is not None else 0),
-                                vp(it.data_ptr()), vp(mm.data_ptr()), ctypes.byref(out), ctypes.byref(o),
-                                _stream_ptr(stream))
+        with _on_device(dev):
+            st = lib().tpf_solve_ex(self._h, T, vp(S.data_ptr()), vp(V.data_ptr() if V is not None else 0),
+                                    vp(it.data_ptr()), vp(mm.data_ptr()), ctypes.byref(out), ctypes.byref(o),
+                                    _stream_ptr(stream, dev))
         if check and st not in (OK, ENOCONV):
             raise TpfError(st, "tpf_solve_ex")
         return {"V": V, "iters": it, "mismatch": mm, "vmin": vmin, "vmax": vmax, "viol": viol,
@@ -468,10 +517,24 @@ class Feeder:
         if start is None:
             start = "given" if V0 is not None else "flat"
         o = make_opts(precision, tol, max_iter, start, switch_tol, profile, method)
-        st = lib().tpf_solve_host(self._h, T, ptr(S), ptr(V), ptr(it), ptr(mm), ctypes.byref(o), _stream_ptr(stream))
+        dev = getattr(self, "device", None)
+        with _on_device(dev):
+            st = lib().tpf_solve_host(self._h, T, ptr(S), ptr(V), ptr(it), ptr(mm), ctypes.byref(o),
+                                      _stream_ptr(stream, dev))
         if check and st not in (OK, ENOCONV):
             raise TpfError(st, "tpf_solve_host")
         return V, it, mm, st
+
+
+def _batch_device(feeders, S, V, iters, mismatch):
+    """The one device of a batch: every feeder's and every tensor's."""
+    named = []
+    for f in range(len(S)):
+        named += [(f"S[{f}]", S[f]), (f"V[{f}]", V[f]), (f"iters[{f}]", iters[f]), (f"mismatch[{f}]", mismatch[f])]
+    devs = {getattr(fd, "device", None) for fd in feeders} - {None}
+    if len(devs) > 1:
+        raise ValueError("the feeders of a batch must be on one device")
+    return _one_device(named, devs.pop() if devs else None)
 
 
 def solve_batch(feeders, S, V=None, iters=None, mismatch=None, precision="mixed", tol=1e-10, max_iter=100,
@@ -501,6 +564,7 @@ def solve_batch(feeders, S, V=None, iters=None, mismatch=None, precision="mixed"
             raise ValueError(f"S[{f}] must be a contiguous CUDA complex128 [T, n_pq] tensor")
     if supplied:
         _batch_outputs(S, V, iters, mismatch)
+    dev = _batch_device(feeders, S, V, iters, mismatch)
     P = ctypes.c_void_p * F
     hs = P(*[fd._h.value for fd in feeders])
     Ts = (ctypes.c_int64 * F)(*[int(s.shape[0]) for s in S])
@@ -511,8 +575,9 @@ def solve_batch(feeders, S, V=None, iters=None, mismatch=None, precision="mixed"
     conv = (ctypes.c_int64 * F)()
     st_ = Stats()
     o = make_opts(precision, tol, max_iter, start, switch_tol, profile, method)
-    st = lib().tpf_solve_batch(F, hs, Ts, Sp, Vp, Ip, Mp, ctypes.byref(o), conv, ctypes.byref(st_),
-                               _stream_ptr(stream))
+    with _on_device(dev):
+        st = lib().tpf_solve_batch(F, hs, Ts, Sp, Vp, Ip, Mp, ctypes.byref(o), conv, ctypes.byref(st_),
+                                   _stream_ptr(stream, dev))
     if check and st not in (OK, ENOCONV):
         raise TpfError(st, "tpf_solve_batch")
     return V, iters, mismatch, np.array(conv[:], dtype=np.int64), st_.as_dict(), st
@@ -544,20 +609,24 @@ class BatchGraph:
                     and s.shape[1] == feeders[f].n_pq and s.is_contiguous()):
                 raise ValueError(f"S[{f}] must be a contiguous CUDA complex128 [T, n_pq] tensor")
         _batch_outputs(S, self.V, self.iters, self.mismatch)
+        self.device = _batch_device(feeders, S, self.V, self.iters, self.mismatch)
         self.F, self.S, self.feeders = F, list(S), list(feeders)
         P = ctypes.c_void_p * F
         hs = P(*[fd._h.value for fd in feeders])
         Ts = (ctypes.c_int64 * F)(*[int(s.shape[0]) for s in S])
         o = make_opts("mixed", tol, max_iter, start, switch_tol, False, "sparse")
         self._b = ctypes.c_void_p()
-        st = lib().tpf_batch_create(F, hs, Ts, P(*[s.data_ptr() for s in S]), P(*[v.data_ptr() for v in self.V]),
-                                    P(*[i.data_ptr() for i in self.iters]), P(*[m.data_ptr() for m in self.mismatch]),
-                                    ctypes.byref(o), ctypes.byref(self._b))
+        with _on_device(self.device):
+            st = lib().tpf_batch_create(F, hs, Ts, P(*[s.data_ptr() for s in S]), P(*[v.data_ptr() for v in self.V]),
+                                        P(*[i.data_ptr() for i in self.iters]),
+                                        P(*[m.data_ptr() for m in self.mismatch]), ctypes.byref(o),
+                                        ctypes.byref(self._b))
         if st != OK:
             raise TpfError(st, "tpf_batch_create")
 
     def launch(self, stream=None):
-        st = lib().tpf_batch_launch(self._b, _stream_ptr(stream))
+        with _on_device(self.device):
+            st = lib().tpf_batch_launch(self._b, _stream_ptr(stream, self.device))
         if st != OK:
             raise TpfError(st, "tpf_batch_launch")
 
@@ -596,10 +665,13 @@ def solve_fp64_noalloc(K, W, S, V, iters=None, tol=1e-10, max_iter=100, given_st
     c128 = torch.complex128
     _device_tensors([("K", K, c128, (n, n)), ("W", W, c128, (n,)), ("S", S, c128, (T, n)), ("V", V, c128, (T, n))]
                     + ([("iters", iters, torch.int32, (T,))] if iters is not None else []))
-    return lib().tpf_solve_fp64_noalloc(
-        int(n), ctypes.c_void_p(K.data_ptr()), ctypes.c_void_p(W.data_ptr()), int(T), ctypes.c_void_p(S.data_ptr()),
-        ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(iters.data_ptr() if iters is not None else 0), float(tol),
-        int(max_iter), 1 if given_start else 0, _stream_ptr(stream))
+    dev = _one_device([("K", K), ("W", W), ("S", S), ("V", V), ("iters", iters)])
+    with _on_device(dev):  # the library solves on the current device
+        return lib().tpf_solve_fp64_noalloc(
+            int(n), ctypes.c_void_p(K.data_ptr()), ctypes.c_void_p(W.data_ptr()), int(T),
+            ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
+            ctypes.c_void_p(iters.data_ptr() if iters is not None else 0), float(tol), int(max_iter),
+            1 if given_start else 0, _stream_ptr(stream, dev))
 
 
 def selftest_gemm(Ar, Ai, Br, Bi, stream=None):
@@ -610,10 +682,13 @@ def selftest_gemm(Ar, Ai, Br, Bi, stream=None):
     N = Br.shape[0]
     f16 = torch.float16
     _device_tensors([("Ar", Ar, f16, (M, K)), ("Ai", Ai, f16, (M, K)), ("Br", Br, f16, (N, K)), ("Bi", Bi, f16, (N, K))])
+    dev = _one_device([("Ar", Ar), ("Ai", Ai), ("Br", Br), ("Bi", Bi)])
     Dr = torch.empty((N, M), dtype=torch.float32, device=Ar.device)
     Di = torch.empty((N, M), dtype=torch.float32, device=Ar.device)
-    st = lib().tpf_selftest_gemm(M, N, K, *(ctypes.c_void_p(x.data_ptr()) for x in (Ar, Ai, Br, Bi)),
-                                 ctypes.c_void_p(Dr.data_ptr()), ctypes.c_void_p(Di.data_ptr()), _stream_ptr(stream))
+    with _on_device(dev):
+        st = lib().tpf_selftest_gemm(M, N, K, *(ctypes.c_void_p(x.data_ptr()) for x in (Ar, Ai, Br, Bi)),
+                                     ctypes.c_void_p(Dr.data_ptr()), ctypes.c_void_p(Di.data_ptr()),
+                                     _stream_ptr(stream, dev))
     if st != OK:
         raise TpfError(st, "tpf_selftest_gemm")
     return Dr, Di
@@ -635,6 +710,7 @@ class LearnedStart:
         self._h = h
         self.n_pq = int(n_pq)
         self.max_batch = int(max_batch)
+        self.device = _current_device()  # tpf_mlp_create allocates on the current device
         self.sizes = [2 * n_pq] + [hidden] * hidden_layers + [2 * n_pq]
 
     def close(self):
@@ -690,11 +766,13 @@ class LearnedStart:
         for name, X in pairs:
             if not X.is_contiguous() or not X.is_cuda:
                 raise ValueError(f"{name} must be a contiguous CUDA tensor")
+        return _one_device(pairs, getattr(self, "device", None))
 
     def fit_normalization(self, S, V, stream=None):
-        self._columns(S, V)
-        st = lib().tpf_mlp_fit_normalization(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()),
-                                             ctypes.c_void_p(V.data_ptr()), _stream_ptr(stream))
+        dev = self._columns(S, V)
+        with _on_device(dev):
+            st = lib().tpf_mlp_fit_normalization(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()),
+                                                 ctypes.c_void_p(V.data_ptr()), _stream_ptr(stream, dev))
         if st != OK:
             raise TpfError(st, "tpf_mlp_fit_normalization")
 
@@ -706,21 +784,24 @@ class LearnedStart:
         return tuple(a)
 
     def train_step(self, S, V, lr=1e-3, want_loss=True, stream=None):
-        self._columns(S, V)
+        dev = self._columns(S, V)
         loss = ctypes.c_double(0.0)
-        st = lib().tpf_mlp_train_step(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()),
-                                      ctypes.c_void_p(V.data_ptr()), float(lr),
-                                      ctypes.byref(loss) if want_loss else None, _stream_ptr(stream))
+        with _on_device(dev):
+            st = lib().tpf_mlp_train_step(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()),
+                                          ctypes.c_void_p(V.data_ptr()), float(lr),
+                                          ctypes.byref(loss) if want_loss else None, _stream_ptr(stream, dev))
         if st != OK:
             raise TpfError(st, "tpf_mlp_train_step")
         return loss.value if want_loss else None
 
     def gradients(self, S, V, stream=None):
-        self._columns(S, V)
+        dev = self._columns(S, V)
         loss = ctypes.c_double(0.0)
         g = np.empty(lib().tpf_mlp_param_count(self._h), dtype=np.float32)
-        st = lib().tpf_mlp_gradients(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V.data_ptr()),
-                                     ctypes.byref(loss), self._f32(g), _stream_ptr(stream))
+        with _on_device(dev):
+            st = lib().tpf_mlp_gradients(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()),
+                                         ctypes.c_void_p(V.data_ptr()), ctypes.byref(loss), self._f32(g),
+                                         _stream_ptr(stream, dev))
         if st != OK:
             raise TpfError(st, "tpf_mlp_gradients")
         return loss.value, g
@@ -730,13 +811,14 @@ class LearnedStart:
         import torch
 
         if V0 is None:
-            self._columns(S)
+            dev = self._columns(S)
             V0 = torch.empty_like(S)
         else:
-            self._columns(S, V0, "V0")
+            dev = self._columns(S, V0, "V0")
         fb = ctypes.c_int64(0)
-        st = lib().tpf_mlp_predict(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()), ctypes.c_void_p(V0.data_ptr()),
-                                   ctypes.byref(fb), _stream_ptr(stream))
+        with _on_device(dev):
+            st = lib().tpf_mlp_predict(self._h, S.shape[0], ctypes.c_void_p(S.data_ptr()),
+                                       ctypes.c_void_p(V0.data_ptr()), ctypes.byref(fb), _stream_ptr(stream, dev))
         if st != OK:
             raise TpfError(st, "tpf_mlp_predict")
         return V0, fb.value

@@ -1,0 +1,118 @@
+"""GPU parity of the FP64 sparse formulation (Algorithm 2 in plain double precision) against the
+FP64 oracle (Algorithm 1, dense K, iterated in the same order).
+
+Bars: max |V - V_oracle| <= 1e-9 pu (oracle iterated to 1e-13).  Iteration counts: the tree
+substitution and the dense product round differently, so a column whose deciding step lies within
+a relative 1e-6 of tol may stop one sweep earlier or later.  The test brackets the count by the
+oracle's counts at tol (1 + 1e-6) and tol (1 - 1e-6), which are equal for every other column.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2403_04578_gb300 import inputs as G
+from paper_2403_04578_gb300 import tpf
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-9
+
+
+def _dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _bracket(c, S, tol, zip_alpha=None):
+    solve = (lambda t: c.solve(S, tol=t)) if zip_alpha is None else (lambda t: c.solve_zip(S, zip_alpha, tol=t))
+    return solve(tol * (1 + 1e-6))[1], solve(tol * (1 - 1e-6))[1]
+
+
+def _check(f, S, tol=1e-10, zip_alpha=None, **kw):
+    c = O.Case.from_feeder(f)
+    if zip_alpha is None:
+        Vo = c.solve(S, tol=1e-13)[0]
+    else:
+        Vo = c.solve_zip(S, zip_alpha, tol=1e-13)[0]
+    lo, hi = _bracket(c, S, tol, zip_alpha)
+    fd = tpf.Feeder.from_inputs(f)
+    if zip_alpha is not None:
+        fd.set_zip(zip_alpha)
+    V, it, mm, st = fd.solve(_dev(S), precision="fp64", method="sparse", tol=tol, **kw)
+    assert st == tpf.OK, tpf.strerror(st)
+    V, it, mm = V.cpu().numpy(), it.cpu().numpy(), mm.cpu().numpy()
+    err = np.abs(V - Vo).max()
+    assert err <= TOL_FP64, f"max |V - V_oracle| = {err:.3e}"
+    bad = np.flatnonzero((it < lo) | (it > hi))
+    assert bad.size == 0, f"{bad.size} columns outside the oracle's count, e.g. {it[bad[:5]]} vs {lo[bad[:5]]}"
+    mm_ref = c.mismatch(S, V) if zip_alpha is None else c.mismatch_zip(S, zip_alpha, V)
+    assert np.all(np.abs(mm - mm_ref) <= 1e-12 + 1e-6 * mm_ref)
+    st_ = fd.stats()
+    assert st_["converged"] == S.shape[0] and st_["kernel_launches"] == 1
+    fd.close()
+    return it
+
+
+@pytest.mark.parametrize("nb,T", [(34, 1440), (2, 7), (3, 1), (35, 129), (100, 200), (200, 300), (600, 70)])
+def test_fp64_sparse_vs_oracle(cuda, nb, T):
+    f = G.make_feeder(nb, 1)
+    _check(f, G.load_tensor(f, T, 1))
+
+
+def test_fp64_sparse_peak_hours_1000(cuda):
+    """1,000 buses (4 per thread, 256 threads), evening peak columns, ragged T."""
+    f = G.make_feeder(1000, 1)
+    _check(f, G.load_tensor(f, 4096, 1)[1080:1080 + 157])
+
+
+def test_fp64_sparse_8_buses_per_thread(cuda):
+    """2,600 buses: 8 positions per thread (325 threads, 221 KB of shared memory)."""
+    f = G.make_feeder(2600, 2)
+    _check(f, G.load_tensor(f, 1440, 2)[1100:1100 + 24])
+
+
+def test_fp64_sparse_zip(cuda):
+    f = G.make_feeder(150, 4)
+    S = G.load_tensor(f, 96, 4)
+    a = np.random.default_rng(4).dirichlet([2, 1, 1], f.n_pq).T.copy()
+    _check(f, S, zip_alpha=a)
+
+
+def test_fp64_sparse_equals_fp64_dense(cuda):
+    """Both FP64 formulations reach the same V; their counts agree wherever the oracle's does."""
+    f = G.make_feeder(300, 3)
+    S = G.load_tensor(f, 400, 3)
+    fd = tpf.Feeder.from_inputs(f)
+    Vs, its, _, _ = fd.solve(_dev(S), precision="fp64", method="sparse")
+    Vd, itd, _, _ = fd.solve(_dev(S), precision="fp64", method="dense")
+    assert float((Vs - Vd).abs().max()) <= 1e-12
+    lo, hi = _bracket(O.Case.from_feeder(f), S, 1e-10)
+    its, itd = its.cpu().numpy(), itd.cpu().numpy()
+    assert np.all((its >= lo) & (its <= hi)) and np.all((itd >= lo) & (itd <= hi))
+    fd.close()
+
+
+def test_fp64_sparse_given_start_empty_and_failures(cuda):
+    f = G.make_feeder(34, 1)
+    c = O.Case.from_feeder(f)
+    S = G.load_tensor(f, 64, 1)
+    fd = tpf.Feeder.from_inputs(f)
+    V, it, mm, st = fd.solve(_dev(S[:0]), precision="fp64", method="sparse")
+    assert st == tpf.OK and V.shape[0] == 0
+    Vo = c.solve(S, tol=1e-13)[0]
+    V, it, _, st = fd.solve(_dev(S), V=_dev(Vo), precision="fp64", method="sparse", start="given")
+    assert st == tpf.OK and (it.cpu().numpy() == 1).all()
+    assert np.abs(V.cpu().numpy() - Vo).max() <= 1e-13
+    bad = S.copy()
+    bad[3] *= 400.0  # beyond the feeder's loadability
+    bad[10, 5] = np.nan
+    V, it, mm, st = fd.solve(_dev(bad), precision="fp64", method="sparse", max_iter=60)
+    assert st == tpf.ENOCONV
+    it = it.cpu().numpy()
+    assert it[3] == -60 and it[10] == -60
+    good = np.setdiff1d(np.arange(64), [3, 10])
+    assert np.abs(V.cpu().numpy()[good] - Vo[good]).max() <= TOL_FP64
+    assert np.isinf(mm.cpu().numpy()[10])
+    assert fd.stats()["converged"] == 62
+    fd.close()

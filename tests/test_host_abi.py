@@ -351,3 +351,31 @@ def test_solve_host_accepts_the_buffers_callers_use():
         with pytest.raises((tpf.TpfError, RuntimeError)) as e:
             fd.solve_host(S, **kw)
         assert not isinstance(e.value, ValueError)
+
+
+def test_tensors_on_another_device_are_refused():
+    """The library launches on one device and passes raw pointers: a tensor on another GPU than
+    the call's other tensors, or than the feeder's or network's device, is refused in the binding,
+    and so is a stream of another device (CPU stand-ins carry only a device)."""
+    from types import SimpleNamespace
+
+    import torch
+
+    def on(k):
+        return SimpleNamespace(device=torch.device("cuda", k))
+
+    assert tpf._one_device([("S", on(1)), ("V", on(1)), ("iters", None)]) == 1
+    assert tpf._one_device([("S", on(0))], want=0) == 0
+    with pytest.raises(ValueError, match=r"V is on cuda:1, but the device of S is cuda:0"):
+        tpf._one_device([("S", on(0)), ("V", on(1))])
+    with pytest.raises(ValueError, match=r"S is on cuda:2, but the device this object was created on is cuda:0"):
+        tpf._one_device([("S", on(2))], want=0)
+    with pytest.raises(ValueError, match="belongs to cuda:1"):
+        tpf._stream_ptr(SimpleNamespace(device=torch.device("cuda", 1), cuda_stream=0), 0)
+    feeders = [SimpleNamespace(device=0), SimpleNamespace(device=1)]
+    t = [on(0), on(0)]
+    with pytest.raises(ValueError, match="feeders of a batch must be on one device"):
+        tpf._batch_device(feeders, t, t, t, t)
+    with pytest.raises(ValueError, match=r"mismatch\[1\] is on cuda:1"):
+        tpf._batch_device(feeders[:1] * 2, t, t, t, [on(0), on(1)])
+    assert tpf._batch_device(feeders[:1] * 2, t, t, t, t) == 0

@@ -49,6 +49,33 @@ def test_noalloc_matches_the_allocating_fp64_solve_twice(cuda):
     ref.close()
 
 
+def test_noalloc_given_start_and_no_iteration_output(cuda):
+    """given_start reads V as V_0: from the converged V every column stops after one sweep; and
+    with no iteration-count tensor (a NULL pointer in the C ABI) V still matches the FP64 path."""
+    import torch
+
+    f = G.make_feeder(34, 1)
+    K, W = tpf.precompute_host(f.n_bus, f.from_bus, f.to_bus, f.z_pu)
+    Kd, Wd = _dev(K), _dev(W)
+    S = _dev(G.load_tensor(f, 500, 3))
+    ref = tpf.Feeder.from_inputs(f)
+    Vr, _, _, st = ref.solve(S, precision="fp64", tol=1e-10)
+    assert st == tpf.OK
+    V = Vr.clone()
+    it = torch.empty(S.shape[0], dtype=torch.int32, device=S.device)
+    st = tpf.solve_fp64_noalloc(Kd, Wd, S, V, it, tol=1e-10, given_start=True)
+    torch.cuda.synchronize()
+    assert st == tpf.OK, tpf.strerror(st)
+    assert bool((it == 1).all())
+    assert float((V - Vr).abs().max()) <= 1e-10  # one more sweep moves V by less than tol
+    V2 = torch.empty_like(S)
+    st = tpf.solve_fp64_noalloc(Kd, Wd, S, V2, None, tol=1e-10)
+    torch.cuda.synchronize()
+    assert st == tpf.OK, tpf.strerror(st)
+    assert float((V2 - Vr).abs().max()) <= TOL_FP64
+    ref.close()
+
+
 def test_noalloc_refuses_requests_beyond_its_array(cuda):
     import torch
 

@@ -51,8 +51,8 @@ __device__ __forceinline__ double2 dmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
 }
 __device__ __forceinline__ double dabs2(double2 a) { return fma(a.x, a.x, a.y * a.y); }
-// max that keeps a NaN
-__device__ __forceinline__ double dmax_nan(double m, double x) { return (x <= m) ? m : x; }
+// max that returns NaN if either operand is NaN
+__device__ __forceinline__ double dmax_nan(double m, double x) { return (m != m || x <= m) ? m : x; }
 
 // Demand current of Eq. 3 in FP64: alpha_P conj(s / v) + alpha_I conj(s) + alpha_Z conj(s) v for
 // the bus in column i (constant power, conj(s / v), without ZIP coefficients).

@@ -230,10 +230,11 @@ tpf_status tpf_autotune(tpf_handle *h, int64_t T, const void *S_dev, const tpf_o
  * fixed point, but B depends on each column's S when alpha_Z != 0, so a tensor of columns cannot
  * share them.  alpha == NULL returns the handle to constant power.  Served by TPF_METHOD_SPARSE and
  * TPF_PREC_FP64; the dense mixed path returns TPF_EUNSUPPORTED while ZIP coefficients are set.
- * On the sparse path the coefficients take a fourth shared-memory region, so a feeder with 3,073
- * to 4,096 demand buses (8 buses per thread) needs more than 227 KB per block and its sparse
- * solves return TPF_EUNSUPPORTED before any launch; smaller and larger feeders are served.
- * TPF_EINVAL for non-finite coefficients.
+ * On the sparse path the coefficients take a fourth shared-memory region; a feeder with 3,073 to
+ * 4,096 demand buses, which would need more than 227 KB per block at 8 buses per thread, is laid
+ * out at 16 buses per thread while coefficients are set (its kernel keeps them in device scratch)
+ * and goes back to the default layout when they are dropped; its FP64 sparse solves then return
+ * TPF_EUNSUPPORTED (TPF_METHOD_DENSE serves them).  TPF_EINVAL for non-finite coefficients.
  */
 tpf_status tpf_set_zip(tpf_handle *h, const double *alpha);
 
@@ -395,6 +396,21 @@ tpf_status tpf_solve_fp64_noalloc(int n, const void *K_dev, const void *W_dev, i
 tpf_status tpf_selftest_gemm(int M, int N, int K, const void *A_re, const void *A_im,
                              const void *B_re, const void *B_im, float *D_re, float *D_im,
                              void *stream);
+
+/*
+ * Self-test of the GEMM's bounded device waits (failure detection; the paper has no counterpart).
+ * The same product as tpf_selftest_gemm, with every wait of the kernel for its work (a copy that
+ * fills a ring slot, an MMA that frees one, an accumulator for the epilogue) limited to wait_s
+ * seconds, 1e-6 <= wait_s <= 10 (the solves use 2 s).  withhold_loads != 0 makes the kernel's
+ * copy producer issue nothing, so the MMA and epilogue waits run out: the kernel raises its error
+ * flag, waits (2 s at most) for its own copies and MMAs, frees its tensor memory and returns, and
+ * the call returns TPF_ETIMEOUT after about 2 wait_s with the CUDA context still usable.  D is
+ * unspecified after TPF_ETIMEOUT.  withhold_loads == 0 with a generous wait_s computes D as
+ * tpf_selftest_gemm does.  Arguments and errors otherwise as tpf_selftest_gemm.  Blocks.
+ */
+tpf_status tpf_selftest_gemm_wait(int M, int N, int K, const void *A_re, const void *A_im,
+                                  const void *B_re, const void *B_im, float *D_re, float *D_im,
+                                  double wait_s, int withhold_loads, void *stream);
 
 #ifdef __cplusplus
 }

@@ -223,6 +223,20 @@ tpf_status set_zip(tpf_handle *h, const double *alpha) {
     DeviceNet &d = h->dev;
     if (d.phases > 1) return alpha ? TPF_EUNSUPPORTED : TPF_OK;
     ++d.layout_gen;
+    // The sparse kernel's ZIP coefficients take a fourth shared-memory region (16 B per slot): at 8
+    // buses per thread (3,073 to 4,096 demand buses) the block would need more than 227 KB, so such
+    // feeders are laid out at 16 buses per thread, whose kernel keeps the coefficients in device
+    // scratch; without coefficients they return to the default layout.
+    if (d.radial && d.t_threads > 0) {
+        const size_t zip_smem_bpt8 = (size_t)(4 * 16 + 3 * 2) * tree_threads(d.n, 8) * 8;
+        if (alpha && d.t_bpt == 8 && zip_smem_bpt8 > 227 * 1024) {
+            const tpf_status rs = layout_tree(h, kTreeBigBPT);
+            if (rs != TPF_OK) return rs;
+        } else if (!alpha && d.t_bpt == kTreeBigBPT && tree_bpt(d.n) != kTreeBigBPT) {
+            const tpf_status rs = layout_tree(h, tree_bpt(d.n));
+            if (rs != TPF_OK) return rs;
+        }
+    }
     cudaFree(d.zip64);
     cudaFree(d.t_zip_hi);
     cudaFree(d.t_zip_lo);

@@ -10,8 +10,8 @@
 // One persistent CTA per SM walks the tiles.  Warp 0 issues the TMA loads into a 3-slot ring,
 // warp 1 issues the MMAs, and warps 2-5 drain the accumulators.  TMEM holds two accumulator
 // stages (2 x 256 columns), so the epilogue of one tile overlaps the main loop of the next.
-// Every wait is bounded (2 s on %globaltimer): on expiry the CTA raises an error flag, stops,
-// waits for its own copies and MMAs (again bounded), frees TMEM and returns.
+// Every wait is bounded (2 s on %globaltimer by default): on expiry the CTA raises an error flag,
+// stops, waits for its own copies and MMAs (again bounded, 2 s), frees TMEM and returns.
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -66,14 +66,14 @@ __device__ __forceinline__ uint64_t global_ns() {
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
 }
-// Wait until the phase with the given parity has completed; false if kWaitNs passed first.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait until the phase with the given parity has completed; false if limit_ns passed first.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit_ns = kWaitNs) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_ns();
     for (;;) {
         for (int i = 0; i < 32; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     }
 }
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, uint32_t bar, int x, int y) {
@@ -178,12 +178,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const uint32_t tmem = *tmem_slot;
     const int64_t total = (int64_t)m_tiles * n_tiles;
     volatile int *vabort = abort_flag;
+    const uint64_t lim = ep.wait_ns ? ep.wait_ns : kWaitNs;  // waits for work; drains use kWaitNs
 
     if (warp == 0 && lane == 0) {
         // ---------------- TMA producer ----------------
         const uint32_t sbase = smem_u32(smem);
         int64_t g = 0;  // chunks issued by this CTA
-        for (int64_t tile = blockIdx.x; tile < total && !*vabort; tile += gridDim.x) {
+        for (int64_t tile = blockIdx.x; tile < total && !*vabort && !ep.withhold_loads; tile += gridDim.x) {
             const int64_t n_tile = tile / m_tiles;
             const int m_tile = (int)(tile % m_tiles);
             if (!tile_live(ep, n_tile)) continue;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             for (int c = 0; c < n_chunks; ++c, ++g) {
                 const int slot = (int)(g % kStages);
                 const uint32_t use = (uint32_t)(g / kStages);
-                if (!mbar_wait(smem_u32(&empty[slot]), (use & 1) ^ 1)) {
+                if (!mbar_wait(smem_u32(&empty[slot]), (use & 1) ^ 1, lim)) {
                     *vabort = 1;
                     atomicExch(ep.err, 1);
                     break;
@@ -226,7 +227,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         for (int64_t tile = blockIdx.x; tile < total && !*vabort; tile += gridDim.x) {
             if (!tile_live(ep, tile / m_tiles)) continue;
             const uint32_t a = j & 1, u = j >> 1;
-            if (!mbar_wait(smem_u32(&tempty[a]), (u & 1) ^ 1)) {
+            if (!mbar_wait(smem_u32(&tempty[a]), (u & 1) ^ 1, lim)) {
                 *vabort = 1;
                 atomicExch(ep.err, 1);
                 break;
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             bool ok = true;
             for (int c = 0; c < n_chunks; ++c, ++g) {
                 const int slot = (int)(g % kStages);
-                if (!mbar_wait(smem_u32(&full[slot]), (uint32_t)(g / kStages) & 1)) {
+                if (!mbar_wait(smem_u32(&full[slot]), (uint32_t)(g / kStages) & 1, lim)) {
                     ok = false;
                     break;
                 }
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 col_scale[et] = (f & kActive) ? pow2f_g(-ep.k_exp - ep.rexp[t]) : 0.0f;
                 col_dmax[et] = 0u;
             }
-            if (!mbar_wait(smem_u32(&tfull[a]), u & 1)) atomicOr(&s_fail, 1);
+            if (!mbar_wait(smem_u32(&tfull[a]), u & 1, lim)) atomicOr(&s_fail, 1);
             epi_barrier();
             if (s_fail) {
                 *vabort = 1;

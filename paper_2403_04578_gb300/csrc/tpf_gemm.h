@@ -14,6 +14,12 @@ struct GemmEpi {
     int cplx;  // 1: A, B, D complex (four real-plane MMAs per K step); 0: real (one MMA)
     int bf16;  // operand format: 0 = fp16, 1 = bf16
     int *err;  // set to 1 when a bounded wait expires
+    // Limit of every wait for work (0: the default 2 s).  The waits that drain a stopped CTA's own
+    // copies and MMAs keep the default.
+    uint64_t wait_ns;
+    // Self-test of the bounded waits only: the producer issues no copies, so the MMA and epilogue
+    // waits run out after wait_ns and the kernel takes its error path (flag, drain, free TMEM).
+    int withhold_loads;
     // mode 0: D[n][m] in two FP32 planes with leading dimension ldD (= M)
     float *Dr, *Di;
     int ldD;

@@ -843,4 +843,14 @@ tpf_status tpf_selftest_gemm(int M, int N, int K, const void *A_re, const void *
     return tpf::selftest_gemm(M, N, K, A_re, A_im, B_re, B_im, D_re, D_im, reinterpret_cast<cudaStream_t>(stream));
 }
 
+tpf_status tpf_selftest_gemm_wait(int M, int N, int K, const void *A_re, const void *A_im, const void *B_re,
+                                  const void *B_im, float *D_re, float *D_im, double wait_s, int withhold_loads,
+                                  void *stream) {
+    if (M <= 0 || N <= 0 || K <= 0 || M % tpf::kTileM || N % tpf::kTileN || K % tpf::kChunkK) return TPF_EINVAL;
+    if (!A_re || !A_im || !B_re || !B_im || !D_re || !D_im) return TPF_EINVAL;
+    if (!(wait_s >= 1e-6 && wait_s <= 10.0)) return TPF_EINVAL;
+    return tpf::selftest_gemm(M, N, K, A_re, A_im, B_re, B_im, D_re, D_im, reinterpret_cast<cudaStream_t>(stream),
+                              (uint64_t)(wait_s * 1e9), withhold_loads ? 1 : 0);
+}
+
 }  // extern "C"

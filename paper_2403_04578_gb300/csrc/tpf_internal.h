@@ -289,5 +289,6 @@ tpf_status batch_plan_wait(tpf_batch *b, int64_t *conv_out, tpf_stats *stats);
 void batch_plan_destroy(tpf_batch *b);
 int batch_device(const tpf_batch *b);
 tpf_status selftest_gemm(int M, int N, int K, const void *Ar, const void *Ai, const void *Br,
-                         const void *Bi, float *Dr, float *Di, cudaStream_t st);
+                         const void *Bi, float *Dr, float *Di, cudaStream_t st, uint64_t wait_ns = 0,
+                         int withhold_loads = 0);
 }  // namespace tpf

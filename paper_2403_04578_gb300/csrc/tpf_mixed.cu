@@ -82,7 +82,7 @@ __global__ void mx_pack(int64_t T, int n, int n_pad, const double2 *__restrict__
 }  // namespace
 
 tpf_status selftest_gemm(int M, int N, int K, const void *Ar, const void *Ai, const void *Br, const void *Bi, float *Dr,
-                         float *Di, cudaStream_t st) {
+                         float *Di, cudaStream_t st, uint64_t wait_ns, int withhold_loads) {
     GemmMaps maps;
     if (!make_gemm_maps(&maps, Ar, Ai, M, K, Br, Bi, N)) return TPF_ECUDA;
     int *err = nullptr;
@@ -95,6 +95,8 @@ tpf_status selftest_gemm(int M, int N, int K, const void *Ar, const void *Ai, co
     ep.Dr = Dr;
     ep.Di = Di;
     ep.ldD = M;
+    ep.wait_ns = wait_ns;
+    ep.withhold_loads = withhold_loads;
     tpf_status rs = launch_gemm(maps, M / kTileM, N / kTileN, K / kChunkK, ep, st);
     int herr = 0;
     cudaError_t e = cudaSuccess;

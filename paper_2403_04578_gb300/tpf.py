@@ -23,7 +23,8 @@ START_FLAT, START_GIVEN, START_WARM = 0, 1, 2
 EXPORTS = (
     "tpf_default_opts", "tpf_strerror", "tpf_create", "tpf_create_poly", "tpf_destroy", "tpf_n_pq", "tpf_precompute_host",
     "tpf_solve", "tpf_solve_host", "tpf_solve_ex", "tpf_solve_batch", "tpf_batch_create", "tpf_batch_launch",
-    "tpf_batch_wait", "tpf_batch_destroy", "tpf_set_zip", "tpf_autotune", "tpf_last_stats", "tpf_selftest_gemm", "tpf_solve_fp64_noalloc",
+    "tpf_batch_wait", "tpf_batch_destroy", "tpf_set_zip", "tpf_autotune", "tpf_last_stats", "tpf_selftest_gemm",
+    "tpf_selftest_gemm_wait", "tpf_solve_fp64_noalloc",
     "tpf_mlp_create", "tpf_mlp_destroy", "tpf_mlp_param_count", "tpf_mlp_get_params", "tpf_mlp_set_params",
     "tpf_mlp_fit_normalization", "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients",
     "tpf_mlp_predict",
@@ -123,6 +124,9 @@ def lib(build_if_missing: bool = False):
     L.tpf_last_stats.restype = ctypes.c_int
     L.tpf_selftest_gemm.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
     L.tpf_selftest_gemm.restype = ctypes.c_int
+    L.tpf_selftest_gemm_wait.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp, vp,
+                                         ctypes.c_double, ctypes.c_int, vp]
+    L.tpf_selftest_gemm_wait.restype = ctypes.c_int
     L.tpf_solve_fp64_noalloc.argtypes = [ctypes.c_int, vp, vp, ctypes.c_int64, vp, vp, vp, ctypes.c_double,
                                          ctypes.c_int, ctypes.c_int, vp]
     L.tpf_solve_fp64_noalloc.restype = ctypes.c_int
@@ -674,8 +678,12 @@ def solve_fp64_noalloc(K, W, S, V, iters=None, tol=1e-10, max_iter=100, given_st
             1 if given_start else 0, _stream_ptr(stream, dev))
 
 
-def selftest_gemm(Ar, Ai, Br, Bi, stream=None):
-    """D = A B^T over complex numbers with the library's tcgen05 kernel (fp16 in, FP32 out)."""
+def selftest_gemm(Ar, Ai, Br, Bi, stream=None, wait_s=None, withhold_loads=False, check=True):
+    """D = A B^T over complex numbers with the library's tcgen05 kernel (fp16 in, FP32 out).
+
+    wait_s / withhold_loads: tpf_selftest_gemm_wait, the test of the kernel's bounded waits (with
+    withhold_loads the waits run out and the status is ETIMEOUT).  Returns (Dr, Di), or
+    (Dr, Di, status) when check is False."""
     import torch
 
     M, K = Ar.shape
@@ -685,10 +693,15 @@ def selftest_gemm(Ar, Ai, Br, Bi, stream=None):
     dev = _one_device([("Ar", Ar), ("Ai", Ai), ("Br", Br), ("Bi", Bi)])
     Dr = torch.empty((N, M), dtype=torch.float32, device=Ar.device)
     Di = torch.empty((N, M), dtype=torch.float32, device=Ar.device)
+    ptrs = [ctypes.c_void_p(x.data_ptr()) for x in (Ar, Ai, Br, Bi, Dr, Di)]
     with _on_device(dev):
-        st = lib().tpf_selftest_gemm(M, N, K, *(ctypes.c_void_p(x.data_ptr()) for x in (Ar, Ai, Br, Bi)),
-                                     ctypes.c_void_p(Dr.data_ptr()), ctypes.c_void_p(Di.data_ptr()),
-                                     _stream_ptr(stream, dev))
+        if wait_s is None and not withhold_loads:
+            st = lib().tpf_selftest_gemm(M, N, K, *ptrs, _stream_ptr(stream, dev))
+        else:
+            st = lib().tpf_selftest_gemm_wait(M, N, K, *ptrs, float(2.0 if wait_s is None else wait_s),
+                                              1 if withhold_loads else 0, _stream_ptr(stream, dev))
+    if not check:
+        return Dr, Di, st
     if st != OK:
         raise TpfError(st, "tpf_selftest_gemm")
     return Dr, Di

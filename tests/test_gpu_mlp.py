@@ -3,7 +3,7 @@ and what the trained network saves the fixed-point iteration.
 
 Tolerances: the GPU runs every product in BF16 (8-bit significand) with FP32 accumulation, so its
 gradient is compared with the FP64 reference (same weights, same normalised batch) by relative L2
-error <= 3e-2 and cosine similarity >= 0.999; the loss within 2 %.
+error <= 2e-2 and cosine similarity >= 0.999; the loss within 2 %.
 """
 import numpy as np
 import pytest
@@ -76,7 +76,7 @@ def test_gradients_match_the_fp64_reference(cuda, feeder200):
     assert loss_gpu == pytest.approx(loss_ref, rel=2e-2)
     rel = np.linalg.norm(g_gpu - g_ref) / np.linalg.norm(g_ref)
     cos = float(g_gpu @ g_ref / (np.linalg.norm(g_gpu) * np.linalg.norm(g_ref)))
-    assert rel <= 3e-2, rel
+    assert rel <= 2e-2, rel
     assert cos >= 0.999, cos
     net.close()
 
@@ -109,7 +109,7 @@ def test_prediction_matches_the_fp64_reference(cuda, feeder200):
     y_ref = y_ref[:, ok]
     rel = np.linalg.norm(y_gpu - y_ref) / np.linalg.norm(y_ref)
     cos = float((y_gpu * y_ref).sum() / (np.linalg.norm(y_gpu) * np.linalg.norm(y_ref)))
-    assert rel <= 3e-2, rel
+    assert rel <= 2e-2, rel
     assert cos >= 0.999, cos
     net.close()
 

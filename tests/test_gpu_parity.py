@@ -57,6 +57,36 @@ def test_gemm_selftest(cuda, M, N, K):
         assert err.max().item() <= 1e-4, f"max scaled error {err.max().item()}"
 
 
+def test_gemm_bounded_wait_expires_cleanly(cuda):
+    """Failure detection without a fault: the GEMM's copy producer withholds its loads, so the MMA
+    and epilogue waits (limited to 20 ms here) run out.  The kernel flags the error, drains its own
+    work, frees its tensor memory and returns: the call reports ETIMEOUT within a second, and the
+    same process then computes a correct product and a solve that matches the oracle."""
+    import time
+
+    import torch
+
+    g = torch.Generator(device="cpu").manual_seed(7)
+    M, N, K = 256, 384, 192
+    A = [torch.rand((M, K), generator=g).mul(2).sub(1).half().cuda() for _ in range(2)]
+    B = [torch.rand((N, K), generator=g).mul(2).sub(1).half().cuda() for _ in range(2)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, st = tpf.selftest_gemm(A[0], A[1], B[0], B[1], wait_s=0.02, withhold_loads=True, check=False)
+    dt = time.perf_counter() - t0
+    assert st == tpf.ETIMEOUT, tpf.strerror(st)
+    assert dt < 1.0, f"the expired waits took {dt:.2f} s to return"
+    # The context is intact: a product with the same short limit but real loads, then a solve.
+    Dr, Di, st = tpf.selftest_gemm(A[0], A[1], B[0], B[1], wait_s=1.0, check=False)
+    assert st == tpf.OK
+    a = [x.double() for x in A]
+    b = [x.double() for x in B]
+    ref_r = b[0] @ a[0].T - b[1] @ a[1].T
+    assert ((Dr.double() - ref_r).abs() / (1 + ref_r.abs())).max().item() <= 1e-4
+    f, c, S = _case(34, 100)
+    _check(f, c, S, "mixed", TOL_MIXED, 1)
+
+
 def _check(f, c, S, precision, tol_v, it_slack, tol=1e-10, **kw):
     Vo, _, _ = c.solve(S, tol=1e-13)
     _, it_ref, d_ref = c.solve(S, tol=tol)

@@ -97,3 +97,33 @@ def test_zip_in_a_batch_and_given_start(cuda):
     assert np.abs(Vg.cpu().numpy() - refs[0]).max() <= 1e-12
     for fd in fds:
         fd.close()
+
+
+@pytest.mark.parametrize("nb", [2500, 3500])
+def test_zip_large_feeders(cuda, nb):
+    """ZIP loads at 8 buses per thread (2,500 buses: 2,499 demand buses, 320 threads, 179 KB of
+    shared memory) and at 3,500 buses, which would need more than 227 KB at 8 buses per thread and
+    is laid out at 16 while coefficients are set: the oracle's ZIP power balance at the returned V,
+    and the same V as the FP64 dense path (Eq. 3's current from the iterate, a different kernel).
+    Dropping the coefficients returns the feeder to constant power with its default layout."""
+    f = G.make_feeder(nb, 7)
+    S = G.load_tensor(f, 4096, 7)[[0, 1100, 2500]]
+    a = np.random.default_rng(nb).dirichlet([2, 1, 1], f.n_pq).T.copy()
+    fd = tpf.Feeder.from_inputs(f)
+    V0, _, _, st = fd.solve(_dev(S), precision="mixed", method="sparse")  # constant power first
+    assert st == tpf.OK
+    fd.set_zip(a)
+    V, it, mm, st = fd.solve(_dev(S), precision="mixed", method="sparse", tol=1e-10)
+    assert st == tpf.OK, tpf.strerror(st)
+    V = V.cpu().numpy()
+    Y = O.ybus(f.n_bus, f.from_bus, f.to_bus, f.z_pu)
+    mz = O.mismatch_zip(Y, f.slack, f.v0, f.pq_bus, a, S, V)
+    assert mz.max() <= 1e-8, mz
+    assert np.all(np.abs(mm.cpu().numpy() - mz) <= 1e-9 + 1e-3 * mz)
+    V64, _, _, st = fd.solve(_dev(S), precision="fp64", method="dense", tol=1e-10)
+    assert st == tpf.OK
+    assert np.abs(V64.cpu().numpy() - V).max() <= 1e-8
+    fd.set_zip(None)
+    V1, _, _, st = fd.solve(_dev(S), precision="mixed", method="sparse")
+    assert st == tpf.OK and np.array_equal(V1.cpu().numpy(), V0.cpu().numpy())
+    fd.close()

@@ -379,3 +379,13 @@ def test_tensors_on_another_device_are_refused():
     with pytest.raises(ValueError, match=r"mismatch\[1\] is on cuda:1"):
         tpf._batch_device(feeders[:1] * 2, t, t, t, [on(0), on(1)])
     assert tpf._batch_device(feeders[:1] * 2, t, t, t, t) == 0
+
+
+def test_gemm_wait_selftest_refuses_bad_limits_on_the_host(tpf_lib):
+    """tpf_selftest_gemm_wait checks its sizes, pointers and wait limit before any device call."""
+    p = ctypes.c_void_p(16)
+    f = ctypes.c_void_p(16)
+    for M, N, K, w in ((128, 128, 64, 0.0), (128, 128, 64, 11.0), (128, 128, 64, float("nan")),
+                       (100, 128, 64, 0.01), (128, 128, 60, 0.01)):
+        assert tpf_lib.tpf_selftest_gemm_wait(M, N, K, p, p, p, p, f, f, w, 1, None) == tpf.EINVAL
+    assert tpf_lib.tpf_selftest_gemm_wait(128, 128, 64, None, p, p, p, f, f, 0.01, 1, None) == tpf.EINVAL

@@ -337,6 +337,46 @@ def test_power_balance_residual_and_contraction_certificate():
             assert O.contraction_certificate(c.K, S[t], V[t]) < 1.0
 
 
+def test_mismatch_is_the_power_balance_away_from_the_solution():
+    """The oracle's mismatch (Eq. 1's power balance, S = load) pinned by branch currents written out
+    by hand: at a wrong V it is the imbalance of each bus's drawn power, not a small number.
+
+    Two buses: the power drawn at bus 1 is v conj((v0 - v)/z), so the imbalance is
+    |v conj((v - v0)/z) + s|; zero at both roots of the two-bus quadratic (the low root is a
+    power-flow solution too), and of the size of the perturbation elsewhere.  Three buses in a chain
+    0 - 1 - 2: with branch currents I_01 = (v0 - v1)/z1 and I_12 = (v1 - v2)/z2, bus 1 draws
+    v1 conj(I_01 - I_12) and bus 2 draws v2 conj(I_12); the mismatch is the larger imbalance."""
+    z, s, v0 = fig2()
+    c = two_bus_case(z, v0)
+    hi, lo = O.two_bus_roots(z, s, v0)
+    S = np.array([[s]])
+    for v in (hi, lo):
+        assert c.mismatch(S, np.array([[v]]))[0] < 1e-14
+    for eps in (1e-6, 1e-6j, 1e-3 * (1 + 1j), -2e-2):
+        v = hi + eps
+        got = c.mismatch(S, np.array([[v]]))[0]
+        want = power_balance(v, z, s, v0)
+        assert want > 1e-7 and got == pytest.approx(want, rel=1e-10)
+    z1, z2 = 0.02 + 0.04j, 0.05 + 0.03j
+    s1, s2 = 0.8 + 0.3j, 0.6 + 0.25j
+    vs = 1.02 + 0.01j
+    c3 = O.Case(3, [0, 1], [1, 2], [z1, z2], slack=0, vs=vs)
+    S3 = np.array([[s1, s2]])
+    V3, it3, _ = c3.solve(S3, tol=1e-14, max_iter=500)
+    assert it3[0] > 0
+
+    def by_hand(v1, v2):
+        i01, i12 = (vs - v1) / z1, (v1 - v2) / z2
+        return max(abs(v1 * np.conj(i01 - i12) - s1), abs(v2 * np.conj(i12) - s2))
+
+    assert by_hand(*V3[0]) < 1e-13 and c3.mismatch(S3, V3)[0] < 1e-13
+    for d1, d2 in ((0.0, 1e-5), (3e-4j, 0.0), (1e-2, -1e-2j)):
+        Vw = V3 + np.array([[d1, d2]])
+        got = c3.mismatch(S3, Vw)[0]
+        want = by_hand(*Vw[0])
+        assert want > 1e-7 and got == pytest.approx(want, rel=1e-10)
+
+
 def test_stopping_rule_counts_updates():
     """iters = number of updates applied; the returned V is that many steps from the start."""
     f, c, S = _config1(64)

@@ -349,6 +349,27 @@ tpf_status tpf_mlp_predict(tpf_mlp *h, int64_t T, const void *S_dev, void *V0_de
                            int64_t *fallback_out, void *stream);
 
 /*
+ * Learned-start solve: the network predicts V_0 for every column (the fused inference of all its
+ * layers, one tcgen05 kernel per chunk of columns, V_0 kept in complex64), then the sparse mixed
+ * solve runs from it (TPF_START_WARM: FP32 sweeps from the prediction, anchoring once the step is
+ * small).  A column whose prediction leaves |V| in [0.7, 1.1] starts flat; fallback_out (host, may
+ * be NULL) receives how many did.  The iteration decides the result, so the outputs are those of
+ * tpf_solve (Sec. III: the fixed point is reached from any nearby start).
+ *
+ *   hd, net      a feeder and a network for it (same n_pq, same device); the network's hidden
+ *                width must be 128 or 256 with at most 7 hidden layers (TPF_EUNSUPPORTED otherwise)
+ *   S_dev ... stream   as tpf_solve; opts->method must be TPF_METHOD_SPARSE and opts->precision
+ *                TPF_PREC_MIXED (TPF_EUNSUPPORTED otherwise); opts->start is ignored
+ *
+ * The network keeps a complex64 buffer for the predictions of up to 262,144 columns (about 2 GB at
+ * 1,000 buses) and one for their features.  tpf_last_stats(hd) reports the totals over the chunks.
+ * Blocks until done.
+ */
+tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void *S_dev, void *V_dev,
+                             int32_t *iters_dev, double *mismatch_dev, const tpf_opts *opts, int64_t *fallback_out,
+                             void *stream);
+
+/*
  * Allocation-free FP64 solve.  The paper has no counterpart to this entry point; it exists for
  * callers that must not allocate device memory themselves or have the library do it: runtimes
  * that hand out device memory only from their own pool (raw cudaMalloc/cudaFree would escape

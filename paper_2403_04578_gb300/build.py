@@ -16,7 +16,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libtpf.so")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-SOURCES = ["tpf_host.cpp", "tpf_fp64.cu", "tpf_mixed.cu", "tpf_residual.cu", "tpf_gemm.cu", "tpf_mlp.cu", "tpf_sparse.cu", "tpf_tree64.cu"]
+SOURCES = ["tpf_host.cpp", "tpf_fp64.cu", "tpf_mixed.cu", "tpf_residual.cu", "tpf_gemm.cu", "tpf_mlp.cu", "tpf_mlp_infer.cu", "tpf_sparse.cu", "tpf_tree64.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

@@ -41,6 +41,9 @@ struct GemmMaps {
     CUtensorMap ar, ai, br, bi;
 };
 
+// A [rows][inner] BF16 matrix read in (128 rows x 64 elements) boxes with the 128-byte swizzle.
+bool make_bf16_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows);
+
 // Ai, Bi may be null for a real product.  bf16 selects the element type of the maps.
 bool make_gemm_maps(GemmMaps *maps, const void *Ar, const void *Ai, int M, int K, const void *Br, const void *Bi,
                     int64_t N, bool bf16 = false);

@@ -270,8 +270,10 @@ tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t
                        double *mismatch, const tpf_opts &o, cudaStream_t st);
 tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
                         double *mismatch, const tpf_opts &o, cudaStream_t st);
+// V0_32 (device complex64 [T][n], optional): a warm start read from there instead of from V.
 tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
-                           double *mismatch, const tpf_outputs *out, const tpf_opts &o, cudaStream_t st);
+                           double *mismatch, const tpf_outputs *out, const tpf_opts &o, cudaStream_t st,
+                           const void *V0_32 = nullptr);
 // The sparse formulation in plain FP64 (radial, single phase, up to 4,096 demand buses).
 tpf_status solve_tree64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
                         double *mismatch, const tpf_opts &o, cudaStream_t st);

@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "tpf_gemm.h"
+#include "tpf_mlp_infer.h"
 
 using bf16 = __nv_bfloat16;
 
@@ -45,6 +46,16 @@ struct tpf_mlp {
     double *loss = nullptr;          // [1]
     int *err = nullptr;              // GEMM wait-expiry flag
     int *fallback = nullptr;         // [1] columns whose prediction failed the guard
+    // Fused inference (tpf_mlp_infer.cu): the first and last layers with interleaved inputs /
+    // outputs, the last bias and the statistics in the same order, rebuilt when stale.
+    bool infer_fresh = false;
+    bf16 *Wi0 = nullptr, *WiL = nullptr;   // [pad1][pad0] and [padL][pad(L-1)]
+    float *bi_out = nullptr, *om_i = nullptr, *os_i = nullptr;  // [padL]
+    float *im_i = nullptr, *is_i = nullptr;                     // [pad0]
+    bf16 *Xi = nullptr;                    // interleaved features [xi_cap][pad0]
+    int64_t xi_cap = 0;
+    float2 *V0c = nullptr;                 // complex64 starting voltages of tpf_solve_learned
+    int64_t v0_cap = 0;
 };
 
 namespace tpf {
@@ -289,6 +300,58 @@ __global__ void k_predict_out(const float *__restrict__ Y, int B, int P, int n, 
     }
 }
 
+// The inference copies: W_0 with its inputs interleaved (column 2j <- j, 2j + 1 <- n + j), W_{L-1},
+// its bias and the target statistics with their outputs interleaved (row 2i <- i, 2i + 1 <- n + i),
+// the feature statistics interleaved.  One thread per element of the largest of them.
+__global__ void k_infer_weights(const float *__restrict__ W0, const float *__restrict__ WL, const float *__restrict__ bL,
+                                const float *__restrict__ im, const float *__restrict__ is,
+                                const float *__restrict__ om, const float *__restrict__ os, int n, int P0, int H0,
+                                int PL, int HL, bf16 *Wi0, bf16 *WiL, float *bi, float *imi, float *isi, float *omi,
+                                float *osi) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    auto src = [n](int k) { return (k & 1) ? n + (k >> 1) : (k >> 1); };  // interleaved -> blocked index
+    if (idx < (int64_t)H0 * P0) {  // W_0 [H0][P0]
+        const int o = (int)(idx / P0), k = (int)(idx % P0);
+        Wi0[idx] = __float2bfloat16_rn(k < 2 * n ? W0[(int64_t)o * P0 + src(k)] : 0.0f);
+    }
+    if (idx < (int64_t)PL * HL) {  // W_{L-1} [PL][HL]
+        const int o = (int)(idx / HL), k = (int)(idx % HL);
+        WiL[idx] = __float2bfloat16_rn(o < 2 * n ? WL[(int64_t)src(o) * HL + k] : 0.0f);
+    }
+    if (idx < PL) {
+        const int o = (int)idx;
+        bi[o] = o < 2 * n ? bL[src(o)] : 0.0f;
+        omi[o] = o < 2 * n ? om[src(o)] : 0.0f;
+        osi[o] = o < 2 * n ? os[src(o)] : 0.0f;
+    }
+    if (idx < P0) {
+        const int k = (int)idx;
+        imi[k] = k < 2 * n ? im[src(k)] : 0.0f;
+        isi[k] = k < 2 * n ? is[src(k)] : 0.0f;
+    }
+}
+
+// Interleaved features of columns t0..t0+B-1 (rows beyond T are zero): X[b][2j] and X[b][2j+1] are
+// the z-scored P_j and Q_j (the same arithmetic as k_features), padding features are zero.  Thread
+// j of row b reads S_j once and writes both features as one 32-bit word.
+__global__ void k_features_il(const double2 *__restrict__ S, int64_t T, int64_t t0, int B, int n, int P0,
+                              const float *__restrict__ mean, const float *__restrict__ sd, bf16 *X) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= P0 / 2) return;
+    const float mr = j < n ? mean[2 * j] : 0.0f, dr = j < n ? sd[2 * j] : 0.0f;
+    const float mi = j < n ? mean[2 * j + 1] : 0.0f, di = j < n ? sd[2 * j + 1] : 0.0f;
+    for (int b = blockIdx.y; b < B; b += gridDim.y) {
+        const int64_t t = t0 + b;
+        float xr = 0.0f, xi = 0.0f;
+        if (j < n && t < T) {
+            const double2 s = S[t * n + j];
+            xr = dr > 0.0f ? ((float)s.x - mr) / dr : 0.0f;
+            xi = di > 0.0f ? ((float)s.y - mi) / di : 0.0f;
+        }
+        reinterpret_cast<__nv_bfloat162 *>(X)[(int64_t)b * (P0 / 2) + j] = __floats2bfloat162_rn(xr, xi);
+    }
+}
+
 unsigned blocks(int64_t work) { return (unsigned)((work + kThreads - 1) / kThreads); }
 
 // D[N][M] (FP32) = sum_k A[M][K] B[N][K] on the tensor cores, BF16 operands.
@@ -335,6 +398,8 @@ void free_mlp(tpf_mlp *h) {
     cudaFree(h->in_mean); cudaFree(h->in_std); cudaFree(h->out_mean); cudaFree(h->out_std);
     cudaFree(h->X0); cudaFree(h->X0T); cudaFree(h->dA); cudaFree(h->target); cudaFree(h->loss); cudaFree(h->err);
     cudaFree(h->fallback);
+    cudaFree(h->Wi0); cudaFree(h->WiL); cudaFree(h->bi_out); cudaFree(h->om_i); cudaFree(h->os_i);
+    cudaFree(h->im_i); cudaFree(h->is_i); cudaFree(h->Xi); cudaFree(h->V0c);
     cudaGetLastError();
 }
 
@@ -351,6 +416,7 @@ bool dalloc(T **p, size_t count) {
 
 // Rewrite the BF16 copies of every layer from the FP32 masters (no update).
 tpf_status publish(tpf_mlp *h, cudaStream_t st) {
+    h->infer_fresh = false;
     for (int l = 0; l < h->L; ++l) {
         const int Po = h->pad[l + 1], Pi = h->pad[l];
         k_adam<<<blocks((int64_t)Po * Pi), kThreads, 0, st>>>(h->W[l], h->gWT[l], h->mW[l], h->vW[l], h->b[l], h->gb[l],
@@ -431,6 +497,75 @@ tpf_status check_err(tpf_mlp *h, cudaStream_t st) {
     MLP_CK(cudaMemcpyAsync(&e, h->err, sizeof(int), cudaMemcpyDeviceToHost, st));
     MLP_CK(cudaStreamSynchronize(st));
     return e ? TPF_ETIMEOUT : TPF_OK;
+}
+
+bool fused_ok(const tpf_mlp *h) {
+    const int L = h->L, H = h->pad[1];
+    for (int l = 1; l < L; ++l)
+        if (h->pad[l] != H) return false;
+    return infer_supported(L, H, h->pad[0], h->pad[L]);
+}
+
+// Columns per fused-inference chunk (the interleaved feature buffer holds one chunk).
+constexpr int64_t kInferChunk = 131072;
+
+// Predicted V_0 of T columns with the fused kernel: complex128 (v0_64) or complex64 into V0.
+tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_64, cudaStream_t st) {
+    const int L = h->L, H = h->pad[1], P0 = h->pad[0], PL = h->pad[L];
+    if (!h->infer_fresh) {
+        if (!h->Wi0 && !(dalloc(&h->Wi0, (size_t)H * P0) && dalloc(&h->WiL, (size_t)PL * h->pad[L - 1]) &&
+                         dalloc(&h->bi_out, PL) && dalloc(&h->om_i, PL) && dalloc(&h->os_i, PL) &&
+                         dalloc(&h->im_i, P0) && dalloc(&h->is_i, P0)))
+            return TPF_ENOMEM;
+        const int64_t work = std::max<int64_t>((int64_t)H * P0, (int64_t)PL * h->pad[L - 1]);
+        k_infer_weights<<<blocks(work), kThreads, 0, st>>>(h->W[0], h->W[L - 1], h->b[L - 1], h->in_mean, h->in_std,
+                                                           h->out_mean, h->out_std, h->n, P0, H, PL, h->pad[L - 1],
+                                                           h->Wi0, h->WiL, h->bi_out, h->im_i, h->is_i, h->om_i,
+                                                           h->os_i);
+        MLP_CK(cudaGetLastError());
+        h->infer_fresh = true;
+    }
+    const int64_t chunk = std::min<int64_t>(T, kInferChunk);
+    const int64_t rows = round_up(chunk, 128);
+    if (h->xi_cap < rows) {
+        cudaFree(h->Xi);
+        h->Xi = nullptr;
+        h->xi_cap = 0;
+        if (!dalloc(&h->Xi, (size_t)rows * P0)) return TPF_ENOMEM;
+        h->xi_cap = rows;
+    }
+    InferArgs g{};
+    bool maps = make_bf16_map(&g.map_w[0], h->Wi0, P0, H) && make_bf16_map(&g.map_w[L - 1], h->WiL, H, PL);
+    for (int l = 1; l < L - 1 && maps; ++l) maps = make_bf16_map(&g.map_w[l], h->Wb[l], H, H);
+    if (!maps) return TPF_ECUDA;
+    for (int l = 0; l < L - 1; ++l) g.bias[l] = h->b[l];
+    g.bias_out = h->bi_out;
+    g.out_mean = h->om_i;
+    g.out_std = h->os_i;
+    g.L = L;
+    g.H = H;
+    g.P0 = P0;
+    g.PL = PL;
+    g.n = h->n;
+    g.lo2 = 0.7f * 0.7f;
+    g.hi2 = 1.1f * 1.1f;
+    g.v0_64 = v0_64 ? 1 : 0;
+    g.fallback = h->fallback;
+    g.err = h->err;
+    const size_t vsz = v0_64 ? sizeof(double2) : sizeof(float2);
+    for (int64_t t0 = 0; t0 < T; t0 += chunk) {
+        const int64_t Tc = std::min(chunk, T - t0);
+        k_features_il<<<grid2(P0 / 2, (int)Tc), kThreads, 0, st>>>((const double2 *)S, T, t0, (int)Tc, h->n, P0,
+                                                                  h->im_i, h->is_i, h->Xi);
+        MLP_CK(cudaGetLastError());
+        if (!make_bf16_map(&g.map_x, h->Xi, P0, Tc)) return TPF_ECUDA;
+        g.T = Tc;
+        g.tiles = (Tc + 127) / 128;
+        g.V0 = static_cast<char *>(V0) + (size_t)t0 * h->n * vsz;
+        tpf_status rs = launch_infer(g, st);
+        if (rs != TPF_OK) return rs;
+    }
+    return TPF_OK;
 }
 
 }  // namespace
@@ -584,6 +719,7 @@ tpf_status tpf_mlp_fit_normalization(tpf_mlp *h, int64_t T, const void *S_dev, c
     tpf::DeviceScope dscope(h->device);
     if (!dscope.ok) return TPF_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
+    h->infer_fresh = false;
     k_norm_stats<<<4 * h->n, kThreads, 0, st>>>((const double2 *)S_dev, (const double2 *)V_dev, T, h->n, h->in_mean,
                                                 h->in_std, h->out_mean, h->out_std);
     MLP_CK(cudaGetLastError());
@@ -633,6 +769,7 @@ tpf_status tpf_mlp_train_step(tpf_mlp *h, int B, const void *S_dev, const void *
     if (rs == TPF_OK) rs = backward(h, B, st);
     if (rs != TPF_OK) return rs;
     const int64_t k = ++h->step;
+    h->infer_fresh = false;
     const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
     const float c1 = 1.0f - (float)std::pow(0.9, (double)k), c2 = 1.0f - (float)std::pow(0.999, (double)k);
     for (int l = 0; l < h->L; ++l) {
@@ -664,6 +801,11 @@ tpf_status tpf_mlp_predict(tpf_mlp *h, int64_t T, const void *S_dev, void *V0_de
     MLP_CK(cudaMemsetAsync(h->err, 0, sizeof(int), st));
     MLP_CK(cudaMemsetAsync(h->fallback, 0, sizeof(int), st));
     const int B = h->max_batch;
+    if (fused_ok(h)) {
+        tpf_status rs = infer_fused(h, T, S_dev, V0_dev, true, st);
+        if (rs != TPF_OK) return rs;
+        T = 0;  // done: skip the layer-by-layer path below
+    }
     for (int64_t t0 = 0; t0 < T; t0 += B) {
         tpf_status rs = load_batch(h, B, S_dev, nullptr, T, t0, false, st);
         if (rs == TPF_OK) rs = forward(h, B, st, false);
@@ -678,6 +820,66 @@ tpf_status tpf_mlp_predict(tpf_mlp *h, int64_t T, const void *S_dev, void *V0_de
     tpf_status rs = check_err(h, st);
     if (fallback_out) *fallback_out = fb;
     return rs;
+}
+
+tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void *S_dev, void *V_dev,
+                             int32_t *iters_dev, double *mismatch_dev, const tpf_opts *opts, int64_t *fallback_out,
+                             void *stream) {
+    if (!hd || !net || T < 0) return TPF_EINVAL;
+    tpf_opts o;
+    tpf_default_opts(&o);
+    if (opts) o = *opts;
+    if (!(o.tol >= 0.0) || o.max_iter < 1 || o.max_iter > 100000 || !(o.switch_tol >= 0.0)) return TPF_EINVAL;
+    if (o.method != TPF_METHOD_SPARSE || o.precision != TPF_PREC_MIXED) return TPF_EUNSUPPORTED;
+    if (net->n != hd->net.n_pq || net->device != hd->device) return TPF_EINVAL;
+    if (fallback_out) *fallback_out = 0;
+    hd->stats = tpf_stats{};
+    hd->stats.columns = T;
+    if (T == 0) return TPF_OK;
+    if (!S_dev || !V_dev) return TPF_EINVAL;
+    if (!fused_ok(net)) return TPF_EUNSUPPORTED;
+    tpf::DeviceScope dscope(hd->device);
+    if (!dscope.ok) return TPF_ECUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    // Prediction and solve in chunks of columns: the complex64 starting voltages of one chunk live
+    // in a buffer of the network, grown on demand.
+    const int64_t chunk = std::min<int64_t>(T, 262144);
+    const int n = net->n;
+    if (net->v0_cap < chunk) {
+        cudaFree(net->V0c);
+        net->V0c = nullptr;
+        net->v0_cap = 0;
+        if (!dalloc(&net->V0c, (size_t)chunk * n)) return TPF_ENOMEM;
+        net->v0_cap = chunk;
+    }
+    MLP_CK(cudaMemsetAsync(net->err, 0, sizeof(int), st));
+    MLP_CK(cudaMemsetAsync(net->fallback, 0, sizeof(int), st));
+    tpf_stats total{};
+    tpf_status result = TPF_OK;
+    for (int64_t c0 = 0; c0 < T; c0 += chunk) {
+        const int64_t Tc = std::min(chunk, T - c0);
+        const double2 *Sc = static_cast<const double2 *>(S_dev) + (size_t)c0 * n;
+        tpf_status rs = infer_fused(net, Tc, Sc, net->V0c, false, st);
+        if (rs != TPF_OK) return rs;
+        rs = tpf::solve_sparse_ex(hd, Tc, Sc, static_cast<double2 *>(V_dev) + (size_t)c0 * n,
+                                  iters_dev ? iters_dev + c0 : nullptr, mismatch_dev ? mismatch_dev + c0 : nullptr,
+                                  nullptr, o, st, net->V0c);
+        if (rs != TPF_OK && rs != TPF_ENOCONV) return rs;
+        if (rs == TPF_ENOCONV) result = TPF_ENOCONV;
+        const tpf_stats &p = hd->stats;
+        total.sweeps = std::max(total.sweeps, p.sweeps);
+        total.precise_sweeps = std::max(total.precise_sweeps, p.precise_sweeps);
+        total.converged += p.converged;
+        total.kernel_launches += p.kernel_launches + 2;  // features and fused inference per chunk
+        total.residual_ms += p.residual_ms;
+    }
+    int fb = 0;
+    MLP_CK(cudaMemcpyAsync(&fb, net->fallback, sizeof(int), cudaMemcpyDeviceToHost, st));
+    const tpf_status rs = check_err(net, st);
+    total.columns = T;
+    hd->stats = total;
+    if (fallback_out) *fallback_out = fb;
+    return rs != TPF_OK ? rs : result;
 }
 
 }  // extern "C"

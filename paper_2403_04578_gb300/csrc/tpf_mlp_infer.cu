@@ -1,0 +1,329 @@
+// Fused inference of the learned warm start: every layer of the network for a tile of 128
+// columns in one persistent tcgen05 kernel, the hidden activations kept in shared memory.
+//
+// The network maps a column's loads to a starting voltage (features P_j, Q_j z-scored; targets
+// Re V_i - 1, Im V_i z-scored; hidden layers z = W a + b, a = gelu(z)).  For inference the input
+// features and the outputs are taken in interleaved order (P_1, Q_1, P_2, Q_2, ... and
+// Re V_1 - 1, Im V_1, ...), so that a tile of features is a contiguous run of buses and an
+// output tile is a contiguous run of complex voltages; the first and last weight matrices are
+// permuted to match once per change of the parameters.
+//
+// Per CTA tile (M = 128 columns):
+//   layer 0       D = X W_0^T        A = X (TMA from the feature matrix), B = W_0 (TMA), K = P0
+//   layers 1..    D = H W_l^T        A = H (shared memory), B = W_l (TMA), K = hidden
+//   last layer    D = H W_L^T        in N tiles of 128 outputs, A = H, B = rows of W_L (TMA)
+// with the FP32 accumulator in TMEM (two stages of 256 columns).  Warp 0 issues the TMA loads
+// into a 3-slot ring, warp 1 the MMAs (one thread), warps 2-5 the epilogues: bias and GELU of a
+// hidden layer written as BF16 into the shared-memory A operand of the next layer (128-byte
+// swizzle, the layout TMA would have written), and for the last layer the denormalisation into
+// V_0 with the |V| guard.  Every wait is bounded; on expiry the CTA flags the error, drains its
+// own copies and MMAs, frees TMEM and returns.
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "tpf_gemm.h"
+#include "tpf_mlp_infer.h"
+#include "tpf_tc.cuh"
+
+namespace tpf {
+
+namespace {
+
+using namespace tc;
+
+constexpr int kThreads = 192;
+constexpr int kStages = 3;
+constexpr uint32_t kATile = 128 * 64 * 2;  // 16 KB: 128 rows x 64 BF16 (one K chunk of A)
+constexpr uint32_t kBMax = 256 * 64 * 2;   // 32 KB: up to 256 rows x 64 BF16 (one K chunk of B)
+constexpr uint32_t kStageBytes = kATile + kBMax;
+constexpr uint32_t kHBytes = 128 * 256 * 2;  // hidden activations of the tile, 4 K chunks of 16 KB
+constexpr size_t kSmem = 1024 + kStages * kStageBytes + kHBytes + 1024;
+constexpr int kOutTile = 128;  // outputs per last-layer accumulator job
+
+__device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+__global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__ InferArgs g) {
+    extern __shared__ uint8_t smem_raw[];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t *Hs = smem + kStages * kStageBytes;
+    uint64_t *full = (uint64_t *)(Hs + kHBytes);  // [kStages] TMA -> MMA
+    uint64_t *empty = full + kStages;              // [kStages] MMA -> TMA
+    uint64_t *tfull = empty + kStages;             // [2] MMA -> epilogue
+    uint64_t *tempty = tfull + 2;                  // [2] epilogue -> MMA
+    uint64_t *hready = tempty + 2;                 // [1] epilogue -> MMA: the activations are written
+    uint64_t *done = hready + 1;                   // [1] every MMA of this CTA retired
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    int *abort_flag = (int *)(tmem_slot + 1);
+    __shared__ int s_fail;
+
+    const int L = g.L, H = g.H;
+    const int k0 = g.P0 / 64, kh = H / 64, n_out = g.PL / kOutTile;
+    constexpr uint32_t kTmemCols = 512;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(smem_u32(&tfull[a]), 1);
+            mbar_init(smem_u32(&tempty[a]), 4);  // lane 0 of each epilogue warp
+        }
+        mbar_init(smem_u32(hready), 1);
+        mbar_init(smem_u32(done), 1);
+        *abort_flag = 0;
+        s_fail = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    volatile int *vabort = abort_flag;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------- TMA producer: the operand chunks of every job, in job order ----------------
+        const uint32_t sbase = smem_u32(smem);
+        int64_t q = 0;  // chunks issued by this CTA
+        auto slot_ready = [&](uint32_t &st) -> bool {
+            const int slot = (int)(q % kStages);
+            if (!mbar_wait(smem_u32(&empty[slot]), ((uint32_t)(q / kStages) & 1) ^ 1)) {
+                *vabort = 1;
+                atomicExch(g.err, 1);
+                return false;
+            }
+            st = sbase + slot * kStageBytes;
+            return true;
+        };
+        for (int64_t tile = blockIdx.x; tile < g.tiles && !*vabort; tile += gridDim.x) {
+            const int row0 = (int)(tile * 128);
+            bool ok = true;
+            for (int c = 0; c < k0 && ok; ++c, ++q) {  // layer 0: features and W_0
+                uint32_t st;
+                if (!(ok = slot_ready(st))) break;
+                const uint32_t bar = smem_u32(&full[q % kStages]);
+                mbar_expect_tx(bar, kATile + (uint32_t)H * 128);
+                tma_load_2d(st, &g.map_x, bar, c * 64, row0);
+                for (int r = 0; r < H / 128; ++r) tma_load_2d(st + kATile + r * 16384, &g.map_w[0], bar, c * 64, r * 128);
+            }
+            for (int l = 1; l < L - 1 && ok; ++l)  // hidden layers: W_l
+                for (int c = 0; c < kh && ok; ++c, ++q) {
+                    uint32_t st;
+                    if (!(ok = slot_ready(st))) break;
+                    const uint32_t bar = smem_u32(&full[q % kStages]);
+                    mbar_expect_tx(bar, (uint32_t)H * 128);
+                    for (int r = 0; r < H / 128; ++r)
+                        tma_load_2d(st + kATile + r * 16384, &g.map_w[l], bar, c * 64, r * 128);
+                }
+            for (int nt = 0; nt < n_out && ok; ++nt)  // last layer: 128 output rows of W_L at a time
+                for (int c = 0; c < kh && ok; ++c, ++q) {
+                    uint32_t st;
+                    if (!(ok = slot_ready(st))) break;
+                    const uint32_t bar = smem_u32(&full[q % kStages]);
+                    mbar_expect_tx(bar, 16384);
+                    tma_load_2d(st + kATile, &g.map_w[L - 1], bar, c * 64, nt * kOutTile);
+                }
+            if (!ok) break;
+        }
+        if (*vabort) {  // the copies in flight land before the CTA leaves (bounded)
+            for (int64_t r = q - 1; r >= 0 && r >= q - kStages; --r)
+                mbar_wait(smem_u32(&full[r % kStages]), (uint32_t)(r / kStages) & 1);
+        }
+    } else if (warp == 1 && lane == 0) {
+        // ---------------- MMA issuer ----------------
+        const uint32_t sbase = smem_u32(smem), hbase = smem_u32(Hs);
+        const uint32_t id_hidden = idesc_f16(128, H, 0, 1), id_out = idesc_f16(128, kOutTile, 0, 1);
+        int64_t q = 0;   // chunks consumed
+        uint32_t jq = 0; // accumulator jobs
+        uint32_t hq = 0; // activation tiles waited for
+        bool ok = true;
+        // One accumulator job: wait for the stage, optionally for fresh activations, then n_k chunks.
+        auto job = [&](int n_k, bool from_h, bool wait_h, uint32_t idesc) -> bool {
+            const uint32_t a = jq & 1, u = jq >> 1;
+            if (!mbar_wait(smem_u32(&tempty[a]), (u & 1) ^ 1)) return false;
+            if (wait_h) {
+                if (!mbar_wait(smem_u32(hready), hq & 1)) return false;
+                ++hq;
+            }
+            tc_fence_after();
+            const uint32_t acc = tmem + a * 256;
+            for (int c = 0; c < n_k; ++c, ++q) {
+                const int slot = (int)(q % kStages);
+                if (!mbar_wait(smem_u32(&full[slot]), (uint32_t)(q / kStages) & 1)) return false;
+                tc_fence_after();
+                const uint32_t st = sbase + slot * kStageBytes;
+                const uint32_t abase = from_h ? hbase + c * kATile : st;
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    umma_f16(acc, sw128_desc(abase + kk * 32), sw128_desc(st + kATile + kk * 32), idesc, (c | kk) != 0);
+                umma_commit(smem_u32(&empty[slot]));
+            }
+            umma_commit(smem_u32(&tfull[a]));
+            ++jq;
+            return true;
+        };
+        for (int64_t tile = blockIdx.x; tile < g.tiles && ok && !*vabort; tile += gridDim.x) {
+            ok = job(k0, false, false, id_hidden);
+            for (int l = 1; l < L - 1 && ok; ++l) ok = job(kh, true, true, id_hidden);
+            for (int nt = 0; nt < n_out && ok; ++nt) ok = job(kh, true, nt == 0, id_out);
+        }
+        if (!ok) {
+            *vabort = 1;
+            atomicExch(g.err, 1);
+        }
+        umma_commit(smem_u32(done));
+        mbar_wait(smem_u32(done), 0);  // every MMA of this CTA has retired (bounded)
+    } else if (warp >= 2) {
+        // ---------------- epilogue: 128 threads, thread = column row of the tile ----------------
+        const int quarter = warp & 3;  // TMEM lanes this warp may access
+        const int row = quarter * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
+        const int et = tid - 64;
+        // This row's 128-byte line inside each 16 KB K chunk of the activations (SW128 layout).
+        uint8_t *hrow = Hs + (row >> 3) * 1024 + (row & 7) * 128;
+        uint32_t jq = 0;
+        epi_sync();
+        for (int64_t tile = blockIdx.x; tile < g.tiles; tile += gridDim.x) {
+            const int64_t t = tile * 128 + row;  // this thread's column
+            bool guard_ok = true;
+            bool failed = false;
+            const int jobs = L - 1 + n_out;
+            for (int j = 0; j < jobs; ++j, ++jq) {
+                const uint32_t a = jq & 1, u = jq >> 1;
+                if (!mbar_wait(smem_u32(&tfull[a]), u & 1)) atomicOr(&s_fail, 1);
+                epi_sync();
+                if (s_fail) {
+                    failed = true;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t acc = tmem + a * 256 + lane_off;
+                if (j < L - 1) {
+                    // Hidden activations of layer j: bias, GELU, BF16 into the next layer's A operand.
+                    const float *bias = g.bias[j];
+                    for (int p = 0; p < H / 32; ++p) {
+                        uint32_t v[32];
+                        tmem_ld32(acc + p * 32, v);
+                        tmem_wait_ld();
+                        uint32_t w[16];
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) {
+                            const int o = p * 32 + 2 * e;
+                            const float z0 = __uint_as_float(v[2 * e]) + __ldg(bias + o);
+                            const float z1 = __uint_as_float(v[2 * e + 1]) + __ldg(bias + o + 1);
+                            w[e] = pack_bf16(gelu_erf(z0), gelu_erf(z1));
+                        }
+                        // Units p*32 .. p*32+31: K chunk p/2, 16-byte groups 4 (p&1) .. +3, swizzled by row.
+                        uint8_t *chunk = hrow + (p >> 1) * kATile;
+#pragma unroll
+                        for (int gq = 0; gq < 4; ++gq) {
+                            const int grp = ((p & 1) * 4 + gq) ^ (row & 7);
+                            *reinterpret_cast<uint4 *>(chunk + grp * 16) =
+                                make_uint4(w[4 * gq], w[4 * gq + 1], w[4 * gq + 2], w[4 * gq + 3]);
+                        }
+                    }
+                    fence_async_smem();  // the MMAs (async proxy) read these activations next
+                    tc_fence_before();
+                    epi_sync();
+                    if (et == 0) mbar_arrive(smem_u32(hready));
+                } else {
+                    // Outputs 128 nt .. 128 nt + 127 (interleaved Re V_i - 1, Im V_i): V_0 of buses
+                    // 64 nt .. 64 nt + 63.
+                    const int nt = j - (L - 1);
+                    for (int p = 0; p < kOutTile / 32; ++p) {
+                        uint32_t v[32];
+                        tmem_ld32(acc + p * 32, v);
+                        tmem_wait_ld();
+                        if (t < g.T) {
+#pragma unroll
+                            for (int e = 0; e < 16; ++e) {
+                                const int o = nt * kOutTile + p * 32 + 2 * e, i = o >> 1;
+                                if (i < g.n) {
+                                    const float re = 1.0f + (__uint_as_float(v[2 * e]) + __ldg(g.bias_out + o)) *
+                                                                __ldg(g.out_std + o) + __ldg(g.out_mean + o);
+                                    const float im = (__uint_as_float(v[2 * e + 1]) + __ldg(g.bias_out + o + 1)) *
+                                                         __ldg(g.out_std + o + 1) + __ldg(g.out_mean + o + 1);
+                                    const float m2 = re * re + im * im;
+                                    if (!(m2 >= g.lo2 && m2 <= g.hi2)) guard_ok = false;
+                                    const int64_t k = t * g.n + i;
+                                    if (g.v0_64)
+                                        static_cast<double2 *>(g.V0)[k] = make_double2((double)re, (double)im);
+                                    else
+                                        static_cast<float2 *>(g.V0)[k] = make_float2(re, im);
+                                }
+                            }
+                        }
+                    }
+                }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&tempty[a]));
+            }
+            if (failed) {
+                *vabort = 1;
+                atomicExch(g.err, 1);
+                break;
+            }
+            if (t < g.T && !guard_ok) {  // outside the guard band: the flat start for this column
+                for (int i = 0; i < g.n; ++i) {
+                    const int64_t k = t * g.n + i;
+                    if (g.v0_64)
+                        static_cast<double2 *>(g.V0)[k] = make_double2(1.0, 0.0);
+                    else
+                        static_cast<float2 *>(g.V0)[k] = make_float2(1.0f, 0.0f);
+                }
+                atomicAdd(g.fallback, 1);
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+    }
+}
+
+}  // namespace
+
+bool infer_supported(int L, int H, int P0, int PL) {
+    return L >= 2 && L <= kMaxInferLayers && (H == 128 || H == 256) && P0 % 128 == 0 && PL % kOutTile == 0;
+}
+
+tpf_status launch_infer(const InferArgs &g, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem) != cudaSuccess) {
+            cudaGetLastError();
+            return TPF_ECUDA;
+        }
+        attr = true;
+    }
+    if (g.tiles <= 0) return TPF_OK;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return TPF_ECUDA;
+    }
+    const unsigned grid = (unsigned)(g.tiles < sms ? g.tiles : sms);
+    mlp_infer<<<grid, kThreads, kSmem, st>>>(g);
+    if (cudaGetLastError() != cudaSuccess) return TPF_ECUDA;
+    return TPF_OK;
+}
+
+}  // namespace tpf

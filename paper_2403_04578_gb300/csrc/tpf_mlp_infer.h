@@ -1,0 +1,34 @@
+// The fused inference kernel of the learned warm start (tpf_mlp_infer.cu).
+#pragma once
+
+#include <cuda.h>
+
+#include "tpf_internal.h"
+
+namespace tpf {
+
+constexpr int kMaxInferLayers = 8;  // weight layers the fused kernel takes (up to 7 hidden layers)
+
+struct InferArgs {
+    CUtensorMap map_x;                      // features [rows][P0] BF16, interleaved (P_1, Q_1, ...), box 64 x 128
+    CUtensorMap map_w[kMaxInferLayers];     // W_l [out][in] BF16, box 64 x 128: W_0 with interleaved inputs,
+                                            // W_{L-1} with interleaved output rows
+    const float *bias[kMaxInferLayers];     // FP32 biases of the hidden layers
+    const float *bias_out;                  // [PL] last layer's bias, interleaved
+    const float *out_mean, *out_std;        // [PL] target statistics, interleaved
+    int L, H, P0, PL, n;                    // weight layers, hidden width (128 or 256), padded widths, buses
+    int64_t T, tiles;                       // columns and 128-column tiles
+    float lo2, hi2;                         // guard: |V_0|^2 must lie in [lo2, hi2]
+    void *V0;                               // [T][n] complex64, or complex128 when v0_64
+    int v0_64;
+    int *fallback;                          // columns that failed the guard (given the flat start)
+    int *err;                               // set when a bounded wait expired
+};
+
+// Whether the fused kernel takes a network of this shape.
+bool infer_supported(int L, int H, int P0, int PL);
+
+// One launch over g.tiles tiles (one persistent CTA per SM).
+tpf_status launch_infer(const InferArgs &g, cudaStream_t st);
+
+}  // namespace tpf

@@ -69,6 +69,7 @@ struct TreeWork {
     int32_t *iters_out;  // [T] or null
     double *mismatch_out;  // [T] or null
     int s32, v32;
+    int v0_32;           // V0 is complex64 while V_out is complex128 (a warm start from a prediction)
     int64_t col0;        // first launch column of this feeder
     int64_t T;
     int *conv;           // converged columns of this feeder (accumulated)
@@ -452,7 +453,7 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
             const int q = base + j, s = j * th + tid;
             if (q < n) {
                 const int64_t k = t * n + a.col[s];
-                if (a.v32) {
+                if (a.v32 || a.v0_32) {
                     vr[j] = static_cast<const float2 *>(a.V0)[k];
                 } else {
                     const double2 v = static_cast<const double2 *>(a.V0)[k];
@@ -948,7 +949,7 @@ TreeArgs args_of(const tpf_opts &o) {
 }  // namespace
 
 tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters, double *mismatch,
-                           const tpf_outputs *out, const tpf_opts &o, cudaStream_t st) {
+                           const tpf_outputs *out, const tpf_opts &o, cudaStream_t st, const void *V0_32) {
     const DeviceNet &d = h->dev;
     if (!d.radial || o.precision != TPF_PREC_MIXED || d.t_threads == 0) return TPF_EUNSUPPORTED;
     if (T > 0x7fffffff) return TPF_EUNSUPPORTED;
@@ -966,6 +967,12 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
     wk.S = S;
     wk.V0 = V;
     wk.V_out = V;
+    if (V0_32) {  // a warm start read from a separate complex64 V_0
+        wk.V0 = V0_32;
+        wk.v0_32 = 1;
+        g.given = 1;
+        g.blind = 0;
+    }
     wk.iters_out = iters;
     wk.mismatch_out = mismatch;
     wk.T = T;
@@ -1007,6 +1014,7 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
         wc.T = std::min(chunk, T - c0);
         wc.S = static_cast<const char *>(S) + (size_t)c0 * n * s_size;
         if (V) wc.V0 = wc.V_out = static_cast<char *>(V) + (size_t)c0 * n * v_size;
+        if (V0_32) wc.V0 = static_cast<const char *>(V0_32) + (size_t)c0 * n * sizeof(float2);
         if (iters) wc.iters_out = iters + c0;
         if (mismatch) wc.mismatch_out = mismatch + c0;
         if (wk.col_vmin) wc.col_vmin = wk.col_vmin + c0;

@@ -27,7 +27,7 @@ EXPORTS = (
     "tpf_selftest_gemm_wait", "tpf_solve_fp64_noalloc",
     "tpf_mlp_create", "tpf_mlp_destroy", "tpf_mlp_param_count", "tpf_mlp_get_params", "tpf_mlp_set_params",
     "tpf_mlp_fit_normalization", "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients",
-    "tpf_mlp_predict",
+    "tpf_mlp_predict", "tpf_solve_learned",
 )
 
 # Size of the built-in scratch array of tpf_solve_fp64_noalloc (include/tpf.h).
@@ -144,6 +144,9 @@ def lib(build_if_missing: bool = False):
     L.tpf_mlp_train_step.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.c_double, ctypes.POINTER(ctypes.c_double), vp]
     L.tpf_mlp_gradients.argtypes = [vp, ctypes.c_int, vp, vp, ctypes.POINTER(ctypes.c_double), f32p, vp]
     L.tpf_mlp_predict.argtypes = [vp, ctypes.c_int64, vp, vp, ctypes.POINTER(ctypes.c_int64), vp]
+    L.tpf_solve_learned.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(Opts),
+                                    ctypes.POINTER(ctypes.c_int64), vp]
+    L.tpf_solve_learned.restype = ctypes.c_int
     for name in ("tpf_mlp_create", "tpf_mlp_get_params", "tpf_mlp_set_params", "tpf_mlp_fit_normalization",
                  "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients", "tpf_mlp_predict"):
         getattr(L, name).restype = ctypes.c_int
@@ -440,6 +443,38 @@ class Feeder:
         if check and st not in (OK, ENOCONV):
             raise TpfError(st, "tpf_solve")
         return V, iters, mismatch, st
+
+    def solve_learned(self, net, S, V=None, iters=None, mismatch=None, tol=1e-10, max_iter=100, switch_tol=1e-4,
+                      stream=None, check=True, profile=False):
+        """tpf_solve_learned: V_0 from the LearnedStart network ``net`` (fused inference), then the
+        sparse mixed solve from it.  Returns (V, iters, mismatch, fallback columns, status)."""
+        import torch
+
+        if not (isinstance(S, torch.Tensor) and S.is_cuda and S.dtype == torch.complex128 and S.dim() == 2):
+            raise TypeError("S must be a CUDA complex128 tensor [T, n_pq]")
+        if S.shape[1] != self.n_pq or not S.is_contiguous():
+            raise ValueError(f"S must be contiguous with {self.n_pq} columns")
+        if net.n_pq != self.n_pq:
+            raise ValueError(f"the network is for {net.n_pq} demand buses, the feeder has {self.n_pq}")
+        T = S.shape[0]
+        V = torch.empty_like(S) if V is None else V
+        iters = torch.empty(T, dtype=torch.int32, device=S.device) if iters is None else iters
+        mismatch = torch.empty(T, dtype=torch.float64, device=S.device) if mismatch is None else mismatch
+        _device_tensors([("V", V, torch.complex128, S.shape), ("iters", iters, torch.int32, (T,)),
+                         ("mismatch", mismatch, torch.float64, (T,))])
+        dev = _one_device([("S", S), ("V", V), ("iters", iters), ("mismatch", mismatch)],
+                          getattr(self, "device", None))
+        _one_device([("S", S)], getattr(net, "device", None))
+        o = make_opts("mixed", tol, max_iter, "warm", switch_tol, profile, "sparse")
+        fb = ctypes.c_int64(0)
+        with _on_device(dev):
+            st = lib().tpf_solve_learned(self._h, net._h, T, ctypes.c_void_p(S.data_ptr()),
+                                         ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(iters.data_ptr()),
+                                         ctypes.c_void_p(mismatch.data_ptr()), ctypes.byref(o), ctypes.byref(fb),
+                                         _stream_ptr(stream, dev))
+        if check and st not in (OK, ENOCONV):
+            raise TpfError(st, "tpf_solve_learned")
+        return V, iters, mismatch, fb.value, st
 
     def solve_tensor(self, S, V=None, want_V=True, v_complex64=None, v_band=(0.95, 1.05), bus_counts=None,
                      tol=1e-10, max_iter=100, start=None, switch_tol=1e-4, stream=None, check=True, profile=False):

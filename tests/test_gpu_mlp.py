@@ -211,3 +211,82 @@ def test_learned_start_in_the_batch_path(cuda):
     for fd in fds:
         fd.close()
     torch.cuda.synchronize()
+
+
+@pytest.mark.parametrize("hidden,layers,T", [(256, 3, 1000), (128, 1, 300), (256, 2, 129)])
+def test_fused_prediction_matches_the_fp64_reference(cuda, feeder200, hidden, layers, T):
+    """The fused inference kernel (all layers of a 128-column tile in one tcgen05 kernel, hidden
+    activations in shared memory) against the FP64 network on the same weights, over several
+    tiles with a ragged last one; then outputs pushed outside the |V| guard send every column to
+    the flat start."""
+    f, c = feeder200
+    S = G.load_tensor(f, 4096, 9)[:T]
+    V, _, _ = c.solve(S, tol=1e-12)
+    net = tpf.LearnedStart(f.n_pq, hidden=hidden, hidden_layers=layers, max_batch=128, seed=3)
+    Sd, Vd = _dev(S), _dev(V)
+    net.fit_normalization(Sd, Vd)
+    xm, xs, ym, ys = (np.asarray(a, dtype=np.float64) for a in net.normalization())
+    rng = np.random.default_rng(hidden + layers)
+    sizes = net.sizes
+    Ws = [rng.uniform(-1, 1, (sizes[i + 1], sizes[i])) * np.sqrt(6.0 / (sizes[i] + sizes[i + 1]))
+          for i in range(len(sizes) - 1)]
+    bs = [rng.normal(0, 0.05, sizes[i + 1]) for i in range(len(sizes) - 1)]
+    Ws[-1] *= 0.05
+    flat = np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(Ws, bs)]).astype(np.float32)
+    net.set_params(flat)
+    V0, fallback = net.predict(Sd)
+    assert fallback == 0
+    ref = OM.MLP([w.astype(np.float32).astype(np.float64) for w in Ws], [b.astype(np.float32) for b in bs])
+    y_ref, _ = ref.forward(_norm(_features(S), xm, xs))
+    V0 = V0.cpu().numpy()
+    ok = ys > 0
+    y_gpu = (np.concatenate([V0.real - 1.0, V0.imag], axis=1)[:, ok] - ym[ok]) / ys[ok]
+    rel = np.linalg.norm(y_gpu - y_ref[:, ok]) / np.linalg.norm(y_ref[:, ok])
+    rows = np.linalg.norm(y_gpu - y_ref[:, ok], axis=1) / np.linalg.norm(y_ref[:, ok], axis=1)
+    assert rel <= 2e-2 and rows.max() <= 5e-2, (rel, rows.max())
+    bs_far = [b.copy() for b in bs]
+    bs_far[-1][: f.n_pq] += 1e4  # Re V far above the band at every bus (1e4 standard deviations)
+    net.set_params(np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(Ws, bs_far)]).astype(np.float32))
+    V0, fallback = net.predict(Sd)
+    assert fallback == T
+    assert np.array_equal(V0.cpu().numpy(), np.ones_like(S))
+    net.close()
+
+
+def test_learned_solve_matches_the_oracle(cuda, feeder200):
+    """tpf_solve_learned (fused prediction into complex64 starting voltages, then the sparse mixed
+    solve from them): the oracle's solution within 1e-8 pu, fewer sweeps than the flat start, no
+    column sent to the flat start; argument errors on the host."""
+    import torch
+
+    f, c = feeder200
+    fd = tpf.Feeder.from_inputs(f)
+    S_tr = _dev(G.load_tensor(f, 16384, 41))
+    V_tr, _, _, st = fd.solve(S_tr, precision="mixed", tol=1e-10, method="sparse")
+    assert st == tpf.OK
+    net = tpf.LearnedStart(f.n_pq, max_batch=1024, seed=7)
+    net.fit_normalization(S_tr, V_tr)
+    for epoch in range(25):
+        for k in range(0, 16384, 1024):
+            net.train_step(S_tr[k:k + 1024], V_tr[k:k + 1024], lr=1e-3, want_loss=False)
+    S_np = G.load_tensor(f, 4096, 42)[:3001]
+    S_ev = _dev(S_np)
+    V, it, mm, fb, st = fd.solve_learned(net, S_ev, tol=1e-10)
+    assert st == tpf.OK and fb == 0
+    Vo, _, _ = c.solve(S_np, tol=1e-13)
+    assert np.abs(V.cpu().numpy() - Vo).max() <= 1e-8
+    assert fd.stats()["converged"] == S_np.shape[0]
+    mm_ref = c.mismatch(S_np, V.cpu().numpy())
+    assert np.all(np.abs(mm.cpu().numpy() - mm_ref) <= 1e-9 + 1e-3 * mm_ref)
+    _, it_f, _, _ = fd.solve(S_ev, precision="mixed", tol=1e-10, method="sparse")
+    assert it.float().mean().item() < it_f.float().mean().item() - 1.0
+    # Empty input, and a network for another feeder size.
+    _, _, _, fb, st = fd.solve_learned(net, S_ev[:0])
+    assert st == tpf.OK and fb == 0
+    other = tpf.LearnedStart(30, max_batch=128, seed=1)
+    with pytest.raises(ValueError, match="demand buses"):
+        fd.solve_learned(other, S_ev)
+    other.close()
+    net.close()
+    fd.close()
+    torch.cuda.synchronize()

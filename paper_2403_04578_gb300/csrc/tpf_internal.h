@@ -244,6 +244,7 @@ struct tpf_handle {
     tpf::DeviceNet dev;
     tpf::Workspace ws;
     tpf_stats stats{};
+    int64_t start_fallback = 0;  // columns of the last learned-start solve that started flat
     void *tmaps = nullptr;  // tensor maps of the fp16 K planes (opaque, allocated by the mixed path)
 };
 
@@ -270,10 +271,12 @@ tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t
                        double *mismatch, const tpf_opts &o, cudaStream_t st);
 tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
                         double *mismatch, const tpf_opts &o, cudaStream_t st);
-// V0_32 (device complex64 [T][n], optional): a warm start read from there instead of from V.
+// V0_pred (optional, device complex64 [T][n]): a warm start read from a prediction instead of from
+// V; a column whose prediction has some |V_i| outside [0.7, 1.1] starts flat (counted in
+// h->start_fallback).
 tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
                            double *mismatch, const tpf_outputs *out, const tpf_opts &o, cudaStream_t st,
-                           const void *V0_32 = nullptr);
+                           const void *V0_pred = nullptr);
 // The sparse formulation in plain FP64 (radial, single phase, up to 4,096 demand buses).
 tpf_status solve_tree64(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
                         double *mismatch, const tpf_opts &o, cudaStream_t st);

@@ -509,8 +509,11 @@ bool fused_ok(const tpf_mlp *h) {
 // Columns per fused-inference chunk (the interleaved feature buffer holds one chunk).
 constexpr int64_t kInferChunk = 131072;
 
-// Predicted V_0 of T columns with the fused kernel: complex128 (v0_64) or complex64 into V0.
-tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_64, cudaStream_t st) {
+// Predicted V_0 of T columns with the fused kernel: complex128 (v0_64) or complex64 into V0; with
+// guard, a column whose prediction leaves the |V| band gets the flat start here (otherwise its
+// reader, the learned-start solve, checks the band).
+tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_64, cudaStream_t st,
+                       bool guard = true) {
     const int L = h->L, H = h->pad[1], P0 = h->pad[0], PL = h->pad[L];
     if (!h->infer_fresh) {
         if (!h->Wi0 && !(dalloc(&h->Wi0, (size_t)H * P0) && dalloc(&h->WiL, (size_t)PL * h->pad[L - 1]) &&
@@ -550,6 +553,7 @@ tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_6
     g.lo2 = 0.7f * 0.7f;
     g.hi2 = 1.1f * 1.1f;
     g.v0_64 = v0_64 ? 1 : 0;
+    g.guard = guard ? 1 : 0;
     g.fallback = h->fallback;
     g.err = h->err;
     const size_t vsz = v0_64 ? sizeof(double2) : sizeof(float2);
@@ -844,28 +848,31 @@ tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void
     // Prediction and solve in chunks of columns: the complex64 starting voltages of one chunk live
     // in a buffer of the network, grown on demand.
     const int64_t chunk = std::min<int64_t>(T, 262144);
+    const int64_t cap = round_up(chunk, 128);
     const int n = net->n;
-    if (net->v0_cap < chunk) {
+    if (net->v0_cap < cap) {
         cudaFree(net->V0c);
         net->V0c = nullptr;
         net->v0_cap = 0;
-        if (!dalloc(&net->V0c, (size_t)chunk * n)) return TPF_ENOMEM;
-        net->v0_cap = chunk;
+        if (!dalloc(&net->V0c, (size_t)cap * n)) return TPF_ENOMEM;
+        net->v0_cap = cap;
     }
     MLP_CK(cudaMemsetAsync(net->err, 0, sizeof(int), st));
     MLP_CK(cudaMemsetAsync(net->fallback, 0, sizeof(int), st));
     tpf_stats total{};
     tpf_status result = TPF_OK;
+    int64_t fallback = 0;
     for (int64_t c0 = 0; c0 < T; c0 += chunk) {
         const int64_t Tc = std::min(chunk, T - c0);
         const double2 *Sc = static_cast<const double2 *>(S_dev) + (size_t)c0 * n;
-        tpf_status rs = infer_fused(net, Tc, Sc, net->V0c, false, st);
+        tpf_status rs = infer_fused(net, Tc, Sc, net->V0c, false, st, false);
         if (rs != TPF_OK) return rs;
         rs = tpf::solve_sparse_ex(hd, Tc, Sc, static_cast<double2 *>(V_dev) + (size_t)c0 * n,
                                   iters_dev ? iters_dev + c0 : nullptr, mismatch_dev ? mismatch_dev + c0 : nullptr,
                                   nullptr, o, st, net->V0c);
         if (rs != TPF_OK && rs != TPF_ENOCONV) return rs;
         if (rs == TPF_ENOCONV) result = TPF_ENOCONV;
+        fallback += hd->start_fallback;
         const tpf_stats &p = hd->stats;
         total.sweeps = std::max(total.sweeps, p.sweeps);
         total.precise_sweeps = std::max(total.precise_sweeps, p.precise_sweeps);
@@ -873,12 +880,10 @@ tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void
         total.kernel_launches += p.kernel_launches + 2;  // features and fused inference per chunk
         total.residual_ms += p.residual_ms;
     }
-    int fb = 0;
-    MLP_CK(cudaMemcpyAsync(&fb, net->fallback, sizeof(int), cudaMemcpyDeviceToHost, st));
     const tpf_status rs = check_err(net, st);
     total.columns = T;
     hd->stats = total;
-    if (fallback_out) *fallback_out = fb;
+    if (fallback_out) *fallback_out = fallback;
     return rs != TPF_OK ? rs : result;
 }
 

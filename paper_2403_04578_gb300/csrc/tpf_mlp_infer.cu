@@ -11,13 +11,15 @@
 // Per CTA tile (M = 128 columns):
 //   layer 0       D = X W_0^T        A = X (TMA from the feature matrix), B = W_0 (TMA), K = P0
 //   layers 1..    D = H W_l^T        A = H (shared memory), B = W_l (TMA), K = hidden
-//   last layer    D = H W_L^T        in N tiles of 128 outputs, A = H, B = rows of W_L (TMA)
-// with the FP32 accumulator in TMEM (two stages of 256 columns).  Warp 0 issues the TMA loads
-// into a 3-slot ring, warp 1 the MMAs (one thread), warps 2-5 the epilogues: bias and GELU of a
-// hidden layer written as BF16 into the shared-memory A operand of the next layer (128-byte
-// swizzle, the layout TMA would have written), and for the last layer the denormalisation into
-// V_0 with the |V| guard.  Every wait is bounded; on expiry the CTA flags the error, drains its
-// own copies and MMAs, frees TMEM and returns.
+//   last layer    D = W_L H^T        in M tiles of 128 outputs, A = rows of W_L (TMA), B = H
+// with the FP32 accumulator in TMEM (two stages of 256 columns).  The last layer is taken
+// transposed (outputs on the TMEM lanes, the tile's columns along TMEM), so that a warp's 32
+// threads hold 32 consecutive outputs of one column and its stores to V_0 are contiguous.  Warp 0
+// issues the TMA loads into a 3-slot ring, warp 1 the MMAs (one thread), warps 2-9 the epilogues:
+// bias and GELU of a hidden layer written as BF16 into the shared-memory operand of the next layer
+// (128-byte swizzle, the layout TMA would have written), and for the last layer the
+// denormalisation into V_0 with the |V| guard.  Every wait is bounded; on expiry the CTA flags the
+// error, drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 
 #include <cstring>
@@ -32,18 +34,31 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two per TMEM lane quarter)
+constexpr int kEpiThreads = 256;
 constexpr int kStages = 3;
 constexpr uint32_t kATile = 128 * 64 * 2;  // 16 KB: 128 rows x 64 BF16 (one K chunk of A)
 constexpr uint32_t kBMax = 256 * 64 * 2;   // 32 KB: up to 256 rows x 64 BF16 (one K chunk of B)
 constexpr uint32_t kStageBytes = kATile + kBMax;
 constexpr uint32_t kHBytes = 128 * 256 * 2;  // hidden activations of the tile, 4 K chunks of 16 KB
-constexpr size_t kSmem = 1024 + kStages * kStageBytes + kHBytes + 1024;
+constexpr uint32_t kBiasBytes = (kMaxInferLayers - 1) * 256 * 4;  // hidden biases, staged once
+constexpr size_t kSmem = 1024 + kStages * kStageBytes + kHBytes + 1024 + kBiasBytes;
 constexpr int kOutTile = 128;  // outputs per last-layer accumulator job
 
-__device__ __forceinline__ float gelu_erf(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// GELU in its erf form, z Phi(z) = z (1 + erf(z / sqrt 2)) / 2, with erf from the rational
+// approximation of Abramowitz and Stegun 7.1.26 (Hastings): for x >= 0,
+//     erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2),  t = 1 / (1 + p x),
+// |error| <= 1.5e-7, far below the BF16 rounding (2^-9) of the activation it feeds; erf is odd.
+__device__ __forceinline__ float gelu_erf(float z) {
+    const float x = fabsf(z) * 0.70710678118654752f;
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+    const float e = 1.0f - poly * __expf(-x * x);
+    return 0.5f * z * (1.0f + copysignf(e, z));
+}
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -64,7 +79,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
     uint64_t *done = hready + 1;                   // [1] every MMA of this CTA retired
     uint32_t *tmem_slot = (uint32_t *)(done + 1);
     int *abort_flag = (int *)(tmem_slot + 1);
+    float *s_bias = (float *)(Hs + kHBytes + 1024);  // [L-1][H] biases of the hidden layers
     __shared__ int s_fail;
+    __shared__ unsigned s_badm[4];  // bit c: column c of the tile left the guard band somewhere
 
     const int L = g.L, H = g.H;
     const int k0 = g.P0 / 64, kh = H / 64, n_out = g.PL / kOutTile;
@@ -82,14 +99,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&tfull[a]), 1);
-            mbar_init(smem_u32(&tempty[a]), 4);  // lane 0 of each epilogue warp
+            mbar_init(smem_u32(&tempty[a]), kEpiThreads / 32);  // lane 0 of each epilogue warp
         }
         mbar_init(smem_u32(hready), 1);
         mbar_init(smem_u32(done), 1);
         *abort_flag = 0;
         s_fail = 0;
+        for (int c = 0; c < 4; ++c) s_badm[c] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    for (int k = tid; k < (L - 1) * H; k += blockDim.x) s_bias[k] = __ldg(g.bias[k / H] + k % H);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -136,7 +155,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
                     if (!(ok = slot_ready(st))) break;
                     const uint32_t bar = smem_u32(&full[q % kStages]);
                     mbar_expect_tx(bar, 16384);
-                    tma_load_2d(st + kATile, &g.map_w[L - 1], bar, c * 64, nt * kOutTile);
+                    tma_load_2d(st, &g.map_w[L - 1], bar, c * 64, nt * kOutTile);
                 }
             if (!ok) break;
         }
@@ -153,7 +172,9 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
         uint32_t hq = 0; // activation tiles waited for
         bool ok = true;
         // One accumulator job: wait for the stage, optionally for fresh activations, then n_k chunks.
-        auto job = [&](int n_k, bool from_h, bool wait_h, uint32_t idesc) -> bool {
+        // from_h: A = the activations, B = the ring's weights; out: A = the ring's weights, B = the
+        // activations (the transposed last layer).
+        auto job = [&](int n_k, bool from_h, bool wait_h, uint32_t idesc, bool out = false) -> bool {
             const uint32_t a = jq & 1, u = jq >> 1;
             if (!mbar_wait(smem_u32(&tempty[a]), (u & 1) ^ 1)) return false;
             if (wait_h) {
@@ -167,10 +188,11 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
                 if (!mbar_wait(smem_u32(&full[slot]), (uint32_t)(q / kStages) & 1)) return false;
                 tc_fence_after();
                 const uint32_t st = sbase + slot * kStageBytes;
-                const uint32_t abase = from_h ? hbase + c * kATile : st;
+                const uint32_t abase = out ? st : (from_h ? hbase + c * kATile : st);
+                const uint32_t bbase = out ? hbase + c * kATile : st + kATile;
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk)
-                    umma_f16(acc, sw128_desc(abase + kk * 32), sw128_desc(st + kATile + kk * 32), idesc, (c | kk) != 0);
+                    umma_f16(acc, sw128_desc(abase + kk * 32), sw128_desc(bbase + kk * 32), idesc, (c | kk) != 0);
                 umma_commit(smem_u32(&empty[slot]));
             }
             umma_commit(smem_u32(&tfull[a]));
@@ -180,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
         for (int64_t tile = blockIdx.x; tile < g.tiles && ok && !*vabort; tile += gridDim.x) {
             ok = job(k0, false, false, id_hidden);
             for (int l = 1; l < L - 1 && ok; ++l) ok = job(kh, true, true, id_hidden);
-            for (int nt = 0; nt < n_out && ok; ++nt) ok = job(kh, true, nt == 0, id_out);
+            for (int nt = 0; nt < n_out && ok; ++nt) ok = job(kh, false, nt == 0, id_out, true);
         }
         if (!ok) {
             *vabort = 1;
@@ -189,18 +211,20 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
         umma_commit(smem_u32(done));
         mbar_wait(smem_u32(done), 0);  // every MMA of this CTA has retired (bounded)
     } else if (warp >= 2) {
-        // ---------------- epilogue: 128 threads, thread = column row of the tile ----------------
+        // ---------------- epilogue: 256 threads, two warps per TMEM lane quarter ----------------
+        // Hidden layers: thread = column row of the tile, `half` splits the units.  Last layer:
+        // thread = output row of the accumulator, `half` splits the tile's columns.
         const int quarter = warp & 3;  // TMEM lanes this warp may access
+        const int half = (warp - 2) >> 2;
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         const int et = tid - 64;
         // This row's 128-byte line inside each 16 KB K chunk of the activations (SW128 layout).
         uint8_t *hrow = Hs + (row >> 3) * 1024 + (row & 7) * 128;
+        const int hp = H / 64;  // pieces of 32 units per half
         uint32_t jq = 0;
-        epi_sync();
         for (int64_t tile = blockIdx.x; tile < g.tiles; tile += gridDim.x) {
-            const int64_t t = tile * 128 + row;  // this thread's column
-            bool guard_ok = true;
+            const int64_t t = tile * 128 + row;  // this thread's column (hidden layers)
             bool failed = false;
             const int jobs = L - 1 + n_out;
             for (int j = 0; j < jobs; ++j, ++jq) {
@@ -215,18 +239,17 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
                 const uint32_t acc = tmem + a * 256 + lane_off;
                 if (j < L - 1) {
                     // Hidden activations of layer j: bias, GELU, BF16 into the next layer's A operand.
-                    const float *bias = g.bias[j];
-                    for (int p = 0; p < H / 32; ++p) {
+                    const float *bias = s_bias + j * H;
+                    for (int p = half * hp; p < (half + 1) * hp; ++p) {
                         uint32_t v[32];
                         tmem_ld32(acc + p * 32, v);
                         tmem_wait_ld();
                         uint32_t w[16];
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
-                            const int o = p * 32 + 2 * e;
-                            const float z0 = __uint_as_float(v[2 * e]) + __ldg(bias + o);
-                            const float z1 = __uint_as_float(v[2 * e + 1]) + __ldg(bias + o + 1);
-                            w[e] = pack_bf16(gelu_erf(z0), gelu_erf(z1));
+                            const float2 b2 = *reinterpret_cast<const float2 *>(bias + p * 32 + 2 * e);
+                            w[e] = pack_bf16(gelu_erf(__uint_as_float(v[2 * e]) + b2.x),
+                                             gelu_erf(__uint_as_float(v[2 * e + 1]) + b2.y));
                         }
                         // Units p*32 .. p*32+31: K chunk p/2, 16-byte groups 4 (p&1) .. +3, swizzled by row.
                         uint8_t *chunk = hrow + (p >> 1) * kATile;
@@ -242,30 +265,54 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
                     epi_sync();
                     if (et == 0) mbar_arrive(smem_u32(hready));
                 } else {
-                    // Outputs 128 nt .. 128 nt + 127 (interleaved Re V_i - 1, Im V_i): V_0 of buses
-                    // 64 nt .. 64 nt + 63.
-                    const int nt = j - (L - 1);
-                    for (int p = 0; p < kOutTile / 32; ++p) {
+                    // Transposed last layer: this thread's lane is output o = 128 nt + row (interleaved:
+                    // bus o / 2, Re V - 1 for even o, Im V for odd o), the accumulator columns are the
+                    // tile's 128 columns.  The even and odd lanes of a pair see both parts of a bus.
+                    const int o = (j - (L - 1)) * kOutTile + row, i = o >> 1;
+                    // value = (d + b) s + m (+ 1 for Re V) = d s + c
+                    const float so = __ldg(g.out_std + o);
+                    const float co = __ldg(g.bias_out + o) * so + __ldg(g.out_mean + o) + ((o & 1) ? 0.0f : 1.0f);
+                    const int64_t stride = 2 * (int64_t)g.n;
+                    for (int p = 2 * half; p < 2 * half + 2; ++p) {
                         uint32_t v[32];
                         tmem_ld32(acc + p * 32, v);
                         tmem_wait_ld();
-                        if (t < g.T) {
+                        const int64_t c0 = tile * 128 + p * 32;  // first column of this piece
+                        const int valid = i < g.n ? (int)min((int64_t)32, g.T - c0) : 0;
+                        float val[32];
 #pragma unroll
-                            for (int e = 0; e < 16; ++e) {
-                                const int o = nt * kOutTile + p * 32 + 2 * e, i = o >> 1;
-                                if (i < g.n) {
-                                    const float re = 1.0f + (__uint_as_float(v[2 * e]) + __ldg(g.bias_out + o)) *
-                                                                __ldg(g.out_std + o) + __ldg(g.out_mean + o);
-                                    const float im = (__uint_as_float(v[2 * e + 1]) + __ldg(g.bias_out + o + 1)) *
-                                                         __ldg(g.out_std + o + 1) + __ldg(g.out_mean + o + 1);
-                                    const float m2 = re * re + im * im;
-                                    if (!(m2 >= g.lo2 && m2 <= g.hi2)) guard_ok = false;
-                                    const int64_t k = t * g.n + i;
-                                    if (g.v0_64)
-                                        static_cast<double2 *>(g.V0)[k] = make_double2((double)re, (double)im);
-                                    else
-                                        static_cast<float2 *>(g.V0)[k] = make_float2(re, im);
-                                }
+                        for (int e = 0; e < 32; ++e) val[e] = fmaf(__uint_as_float(v[e]), so, co);
+                        if (g.guard) {
+                            uint32_t bad = 0;  // bit e: column c0 + e left the guard band at this bus
+#pragma unroll
+                            for (int e = 0; e < 32; ++e) {
+                                const float other = __shfl_xor_sync(0xffffffffu, val[e], 1);
+                                const float m2 = fmaf(val[e], val[e], other * other);
+                                bad |= (m2 >= g.lo2 && m2 <= g.hi2) ? 0u : (1u << e);
+                            }
+                            bad &= valid >= 32 ? 0xffffffffu : (valid <= 0 ? 0u : (1u << valid) - 1u);
+                            bad = __reduce_or_sync(0xffffffffu, bad);
+                            if (lane == 0 && bad) atomicOr(&s_badm[p], bad);
+                        }
+                        if (g.v0_64) {
+                            double *dst = static_cast<double *>(g.V0) + c0 * stride + o;
+                            if (valid == 32) {
+#pragma unroll
+                                for (int e = 0; e < 32; ++e) dst[e * stride] = (double)val[e];
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 32; ++e)
+                                    if (e < valid) dst[e * stride] = (double)val[e];
+                            }
+                        } else {
+                            float *dst = static_cast<float *>(g.V0) + c0 * stride + o;
+                            if (valid == 32) {
+#pragma unroll
+                                for (int e = 0; e < 32; ++e) dst[e * stride] = val[e];
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 32; ++e)
+                                    if (e < valid) dst[e * stride] = val[e];
                             }
                         }
                     }
@@ -279,15 +326,21 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
                 atomicExch(g.err, 1);
                 break;
             }
-            if (t < g.T && !guard_ok) {  // outside the guard band: the flat start for this column
-                for (int i = 0; i < g.n; ++i) {
-                    const int64_t k = t * g.n + i;
-                    if (g.v0_64)
-                        static_cast<double2 *>(g.V0)[k] = make_double2(1.0, 0.0);
-                    else
-                        static_cast<float2 *>(g.V0)[k] = make_float2(1.0f, 0.0f);
+            epi_sync();  // every output of the tile has been checked
+            const bool bad = (s_badm[row >> 5] >> (row & 31)) & 1u;
+            epi_sync();  // every thread has read its bit
+            if (et < 4) s_badm[et] = 0;  // (set again only after the next tile's first job barrier)
+            if (half == 0) {
+                if (t < g.T && bad) {  // outside the guard band: the flat start for this column
+                    for (int i = 0; i < g.n; ++i) {
+                        const int64_t k = t * g.n + i;
+                        if (g.v0_64)
+                            static_cast<double2 *>(g.V0)[k] = make_double2(1.0, 0.0);
+                        else
+                            static_cast<float2 *>(g.V0)[k] = make_float2(1.0f, 0.0f);
+                    }
+                    atomicAdd(g.fallback, 1);
                 }
-                atomicAdd(g.fallback, 1);
             }
         }
     }

@@ -21,6 +21,7 @@ struct InferArgs {
     float lo2, hi2;                         // guard: |V_0|^2 must lie in [lo2, hi2]
     void *V0;                               // [T][n] complex64, or complex128 when v0_64
     int v0_64;
+    int guard;                              // apply the |V| guard here (else the reader checks)
     int *fallback;                          // columns that failed the guard (given the flat start)
     int *err;                               // set when a bounded wait expired
 };

@@ -69,7 +69,8 @@ struct TreeWork {
     int32_t *iters_out;  // [T] or null
     double *mismatch_out;  // [T] or null
     int s32, v32;
-    int v0_32;           // V0 is complex64 while V_out is complex128 (a warm start from a prediction)
+    int v0_pred;         // V0 is a complex64 prediction of the learned start (V_out complex128): a
+                         // column with some |V_i| outside [0.7, 1.1] starts flat instead
     int64_t col0;        // first launch column of this feeder
     int64_t T;
     int *conv;           // converged columns of this feeder (accumulated)
@@ -448,12 +449,17 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
         if (kZip) Zs[s] = q < n ? a.zip_hi[s] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     if (g.given) {  // a loop of its own: fewer loads in flight at once, fewer registers
+        bool off_band = false;
 #pragma unroll
         for (int j = 0; j < kBPT; ++j) {
             const int q = base + j, s = j * th + tid;
             if (q < n) {
                 const int64_t k = t * n + a.col[s];
-                if (a.v32 || a.v0_32) {
+                if (a.v0_pred) {
+                    vr[j] = static_cast<const float2 *>(a.V0)[k];
+                    const float m2 = abs2(vr[j]);
+                    off_band |= !(m2 >= 0.49f && m2 <= 1.21f);
+                } else if (a.v32) {
                     vr[j] = static_cast<const float2 *>(a.V0)[k];
                 } else {
                     const double2 v = static_cast<const double2 *>(a.V0)[k];
@@ -463,6 +469,12 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
                                             __double2float_rn(v.y - (double)vr[j].y));
                 }
             }
+        }
+        // A predicted V_0 with |V_i| outside [0.7, 1.1] at any bus is not trusted: the flat start.
+        if (a.v0_pred && __syncthreads_or(off_band)) {
+#pragma unroll
+            for (int j = 0; j < kBPT; ++j) vr[j] = make_float2(1.0f, 0.0f);
+            if (tid == 0) atomicAdd(&g.counters[7], 1);
         }
     }
     __syncthreads();
@@ -949,7 +961,7 @@ TreeArgs args_of(const tpf_opts &o) {
 }  // namespace
 
 tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters, double *mismatch,
-                           const tpf_outputs *out, const tpf_opts &o, cudaStream_t st, const void *V0_32) {
+                           const tpf_outputs *out, const tpf_opts &o, cudaStream_t st, const void *V0_pred) {
     const DeviceNet &d = h->dev;
     if (!d.radial || o.precision != TPF_PREC_MIXED || d.t_threads == 0) return TPF_EUNSUPPORTED;
     if (T > 0x7fffffff) return TPF_EUNSUPPORTED;
@@ -967,9 +979,9 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
     wk.S = S;
     wk.V0 = V;
     wk.V_out = V;
-    if (V0_32) {  // a warm start read from a separate complex64 V_0
-        wk.V0 = V0_32;
-        wk.v0_32 = 1;
+    if (V0_pred) {  // a warm start read from a separate predicted V_0
+        wk.V0 = V0_pred;
+        wk.v0_pred = 1;
         g.given = 1;
         g.blind = 0;
     }
@@ -1014,7 +1026,7 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
         wc.T = std::min(chunk, T - c0);
         wc.S = static_cast<const char *>(S) + (size_t)c0 * n * s_size;
         if (V) wc.V0 = wc.V_out = static_cast<char *>(V) + (size_t)c0 * n * v_size;
-        if (V0_32) wc.V0 = static_cast<const char *>(V0_32) + (size_t)c0 * n * sizeof(float2);
+        if (V0_pred) wc.V0 = static_cast<const char *>(V0_pred) + (size_t)c0 * n * sizeof(float2);
         if (iters) wc.iters_out = iters + c0;
         if (mismatch) wc.mismatch_out = mismatch + c0;
         if (wk.col_vmin) wc.col_vmin = wk.col_vmin + c0;
@@ -1033,6 +1045,7 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
     }
     const int64_t conv = w.counters_host[kCntConverged];
     h->stats.sweeps = w.counters_host[5];
+    h->start_fallback = V0_pred ? w.counters_host[7] : 0;
     h->stats.precise_sweeps = w.counters_host[6];
     h->stats.kernel_launches = launches;
     h->stats.converged = conv;

@@ -280,6 +280,17 @@ def test_learned_solve_matches_the_oracle(cuda, feeder200):
     assert np.all(np.abs(mm.cpu().numpy() - mm_ref) <= 1e-9 + 1e-3 * mm_ref)
     _, it_f, _, _ = fd.solve(S_ev, precision="mixed", tol=1e-10, method="sparse")
     assert it.float().mean().item() < it_f.float().mean().item() - 1.0
+    # Predictions pushed outside the |V| band: every column starts flat (the solver's guard), with
+    # the flat start's results.
+    params = net.params()
+    Ws, bs = net.unflatten(params.copy())
+    bs[-1][: f.n_pq] += 1e4
+    net.set_params(np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(Ws, bs)]))
+    V2, it2, _, fb2, st2 = fd.solve_learned(net, S_ev, tol=1e-10)
+    assert st2 == tpf.OK and fb2 == S_np.shape[0]
+    assert torch.equal(it2, it_f)
+    assert np.abs(V2.cpu().numpy() - Vo).max() <= 1e-8
+    net.set_params(params)
     # Empty input, and a network for another feeder size.
     _, _, _, fb, st = fd.solve_learned(net, S_ev[:0])
     assert st == tpf.OK and fb == 0

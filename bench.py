@@ -102,6 +102,10 @@ def parse_args():
     p.add_argument("--scen-buses", type=int, default=500)
     p.add_argument("--batch-feeders", type=int, default=4096)
     p.add_argument("--no-other", action="store_true", help="skip timing the other formulation")
+    p.add_argument("--headline", choices=["learned", "flat"], default="learned",
+                   help="the headline step: learned-start solve (prediction + warm solve) or flat start")
+    p.add_argument("--train-columns", type=int, default=100000)
+    p.add_argument("--epochs", type=int, default=60)
     return p.parse_args()
 
 
@@ -277,6 +281,89 @@ def cpu_newton_leg(f, S_host, full_T, columns=16):
                       "power mismatch <= 1e-10 pu",
             "converged": int(sum(bool(r[2]) for r in res)), "mean_iterations": float(np.mean([r[1] for r in res])),
             "max_abs_err_pu_vs_fpi_oracle": err}
+
+
+def train_start_network(f, fd, args, dev, n_train, epochs, seed_offset=100):
+    """The learned start's network for feeder f: n_train columns of another load draw (seed +
+    seed_offset, drawn on the device), solved by the library (sparse, mixed, tol), then `epochs`
+    epochs of Adam on batches of 1,024 with a cosine learning rate from 1e-3 down to 1e-4."""
+    import torch
+
+    from paper_2403_04578_gb300 import inputs as G
+    from paper_2403_04578_gb300 import tpf
+
+    S_tr = G.load_tensor_device(f, n_train, args.seed + seed_offset, dev)
+    V_tr, _, _, st = fd.solve(S_tr, precision="mixed", tol=args.tol, method="sparse")
+    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=1024, seed=args.seed)
+    net.fit_normalization(S_tr, V_tr)
+    B = 1024
+    steps_per_epoch = n_train // B
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    perm_gen = torch.Generator(device="cpu").manual_seed(args.seed)
+    for ep in range(epochs):
+        lr = 1e-3 * (0.5 * (1 + np.cos(np.pi * ep / epochs)) * 0.9 + 0.1)
+        order = torch.randperm(n_train, generator=perm_gen)[: steps_per_epoch * B].to(dev)
+        Sp, Vp = S_tr[order].contiguous(), V_tr[order].contiguous()
+        for k in range(steps_per_epoch):
+            net.train_step(Sp[k * B:(k + 1) * B], Vp[k * B:(k + 1) * B], lr=lr, want_loss=False)
+    loss = net.train_step(S_tr[:B], V_tr[:B], lr=1e-12)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del S_tr, V_tr
+    torch.cuda.empty_cache()
+    return net, {"train_columns": n_train, "epochs": epochs, "train_seconds": train_s, "final_batch_loss": loss,
+                 "network": f"{2 * f.n_pq}-256-256-256-{2 * f.n_pq}, GELU, BF16 tensor-core products"}
+
+
+def learned_e2e(fd, net, Sh, Vh, ith, mmh, Sd, Vd, itd, mmd, args, world, chunks=8):
+    """The learned-start solve end to end through the public API: pinned host loads copied in
+    chunks on one stream, each chunk solved (prediction + warm solve) as soon as its copy lands,
+    and its V, iteration counts and mismatches copied back on a third stream while the next chunk is
+    solved."""
+    import torch
+
+    T = Sh.shape[0]
+    bounds = [(T * c // chunks, T * (c + 1) // chunks) for c in range(chunks)]
+    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
+    comp = torch.cuda.current_stream()
+
+    def one():
+        ev_in = []
+        with torch.cuda.stream(s_in):
+            for a, b in bounds:
+                Sd[a:b].copy_(Sh[a:b], non_blocking=True)
+                e = torch.cuda.Event()
+                e.record(s_in)
+                ev_in.append(e)
+        for (a, b), e in zip(bounds, ev_in):
+            comp.wait_event(e)
+            fd.solve_learned(net, Sd[a:b], Vd[a:b], itd[a:b], mmd[a:b], tol=args.tol, stream=comp)
+            done = torch.cuda.Event()
+            done.record(comp)
+            s_out.wait_event(done)
+            with torch.cuda.stream(s_out):
+                Vh[a:b].copy_(Vd[a:b], non_blocking=True)
+                ith[a:b].copy_(itd[a:b], non_blocking=True)
+                mmh[a:b].copy_(mmd[a:b], non_blocking=True)
+        s_out.synchronize()
+
+    one()
+    steps = max(1, args.steps // 2)
+    barrier(world)
+    t0 = time.perf_counter()
+    step_ms = []
+    for _ in range(steps):
+        ts = time.perf_counter()
+        one()
+        step_ms.append((time.perf_counter() - ts) * 1e3)
+    dt = allmax(world, (time.perf_counter() - t0) / steps)
+    n = Sh.shape[1]
+    return {"value": world * T / dt, "unit": "PF/s", "h2d_bytes_per_step": T * n * 16,
+            "d2h_bytes_per_step": T * n * 16 + T * 4 + T * 8, "ms_per_step": dt * 1e3,
+            "step_ms": [round(x, 2) for x in step_ms],
+            "entry_point": f"tpf_solve_learned per chunk of {T // chunks:,} columns, pinned host buffers, "
+                           "copies on their own streams"}
 
 
 def learned_start_leg(args, stream):
@@ -720,8 +807,10 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def timed_steps(fd, Sd, Vd, itd, mmd, args, method, steps, stream, world, clocks_index=None):
-    """Time `steps` full solves of every column with CUDA events; returns per-step numbers."""
+def timed_steps(fd, Sd, Vd, itd, mmd, args, method, steps, stream, world, clocks_index=None, net=None):
+    """Time `steps` full solves of every column with CUDA events; returns per-step numbers.  With
+    `net`, a step is the learned-start solve (prediction of V_0 by the network, then the sparse
+    mixed solve from it)."""
     import torch
 
     kern_ms = gemm_ms = gemm_cols = gemm_launch = 0.0
@@ -739,7 +828,10 @@ def timed_steps(fd, Sd, Vd, itd, mmd, args, method, steps, stream, world, clocks
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat", profile=True, method=method)
+        if net is not None:
+            fd.solve_learned(net, Sd, Vd, itd, mmd, tol=args.tol, profile=True)
+        else:
+            fd.solve(Sd, Vd, itd, mmd, precision="mixed", tol=args.tol, start="flat", profile=True, method=method)
         b.record(stream)
         s = fd.stats()
         kern_ms += s["residual_ms"] if method == "sparse" else s["gemm_ms"]
@@ -850,6 +942,30 @@ def main():
                 "ms_per_launch": run["kernel_ms"]}
 
     roofline = tree_roofline(main_run, column_sweeps) if args.method == "sparse" else gemm_roofline(main_run)
+    flat = {"value": value, "unit": "PF/s", "ms_per_step": ms_per_step, "mean_sweeps": column_sweeps / T,
+            "gpu_launches": main_run["launches"], "roofline": roofline,
+            "note": "flat start V_0 = 1 (Algorithm 1), sparse mixed solve"}
+
+    # The learned start on the same workload: the network is trained once per feeder (on other load
+    # columns, not timed: a per-feeder set-up cost, reported), and a step is the prediction of V_0
+    # for every column plus the sparse mixed solve from it.
+    learned = net = None
+    if args.method == "sparse" and args.headline == "learned":
+        net, train_info = train_start_network(f, fd, args, Sd.device, args.train_columns, args.epochs)
+        for _ in range(args.warmup):
+            fd.solve_learned(net, Sd, Vd, itd, mmd, tol=args.tol)
+        _, _, _, fallback, _ = fd.solve_learned(net, Sd, Vd, itd, mmd, tol=args.tol)
+        torch.cuda.synchronize()
+        lrun = timed_steps(fd, Sd, Vd, itd, mmd, args, "sparse", args.steps, stream, world, clocks_index=local,
+                           net=net)
+        l_sweeps = int(itd.abs().sum().item())
+        learned = {"value": world * T / (lrun["ms_per_step"] / 1e3), "unit": "PF/s", "ms_per_step": lrun["ms_per_step"],
+                   "mean_sweeps": l_sweeps / T, "fallback_columns": fallback, "converged": lrun["stats"]["converged"],
+                   "gpu_launches": lrun["launches"], "roofline": tree_roofline(lrun, l_sweeps),
+                   "solve_kernel_ms": lrun["kernel_ms"], "predict_ms": lrun["ms_per_step"] - lrun["kernel_ms"],
+                   "clocks": lrun["clocks"], **train_info}
+        if checking:
+            V_checks["learned_max_abs_err_pu"] = Vd[cc_dev].cpu().numpy()
 
     # End to end through the host-buffer entry point.
     e2e = None
@@ -867,10 +983,12 @@ def main():
             fd.solve_host(Sh, precision="mixed", tol=args.tol, out=(Vh, ith, mmh), method=args.method)
             step_ms.append((time.perf_counter() - ts) * 1e3)
         dt = allmax(world, (time.perf_counter() - t0) / e2e_steps)
-        e2e = {"value": world * T / dt, "unit": "PF/s", "h2d_bytes_per_step": T * n * 16,
+        flat["e2e"] = e2e = {"value": world * T / dt, "unit": "PF/s", "h2d_bytes_per_step": T * n * 16,
                "d2h_bytes_per_step": T * n * 16 + T * 4 + T * 8, "ms_per_step": dt * 1e3,
                "step_ms": [round(x, 2) for x in step_ms],
                "entry_point": "tpf_solve_host (pinned host buffers)"}
+        if learned is not None:
+            learned["e2e"] = learned_e2e(fd, net, Sh, Vh, ith, mmh, Sd, Vd, itd, mmd, args, world)
 
     # The other formulation on the same workload.
     other = "dense" if args.method == "sparse" else "sparse"
@@ -938,21 +1056,36 @@ def main():
         if checking:
             V_checks["fp64_sparse_max_abs_err_pu"] = Vd[cc_dev].cpu().numpy()
 
+    # The headline step: the learned-start solve when it ran, else the flat start.
+    head = learned if learned is not None else flat
+    if learned is not None:
+        value, ms_per_step, e2e = learned["value"], learned["ms_per_step"], learned.get("e2e")
+        roofline, clocks, launches = learned["roofline"], learned["clocks"], learned["gpu_launches"]
+        config["start"] = (f"learned: V_0 predicted by a {learned['network']} network trained on "
+                           f"{learned['train_columns']:,} other columns ({learned['epochs']} epochs, not timed), "
+                           "then the sparse mixed solve from it")
+    else:
+        clocks, launches = main_run["clocks"], main_run["launches"]
+        config["start"] = "flat"
     line = {"metric": METRIC, "value": value, "unit": "PF/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None,
             "dtype": ("f32 sweeps + double-float anchors" if args.method == "sparse"
                       else "f16 tensor-core products + f32/double-float elementwise"),
             "data": "synthetic", "config": config, "roofline": roofline,
-            "e2e": e2e, "clocks": main_run["clocks"], "gpu_launches": main_run["launches"],
+            "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
             "sweeps": stats["sweeps"], "anchors_or_anchor_sweeps": stats["precise_sweeps"],
-            "mean_sweeps": column_sweeps / T, "tpf_create_ms": create_ms,
-            "headline_start": "flat",
+            "mean_sweeps": head["mean_sweeps"], "tpf_create_ms": create_ms,
+            "headline_start": "learned" if learned is not None else "flat",
+            "flat_start": flat,
             "fp64_gpu": fp64,
             "speedup_vs_fp64_gpu": (value / world) / fp64_pfs,
             "speedup_vs_fp64_gpu_note": "formulation plus precision: the mixed sparse path against the FP64 "
                                         "dense path (8 n^2 against 36 n flop per bus-sweep)",
             }
+    if learned is not None:
+        line["learned_start_headline"] = {k: v for k, v in learned.items() if k not in ("roofline", "clocks", "e2e")}
+        line["speedup_learned_vs_flat"] = learned["value"] / flat["value"]
     if fp64s is not None:
         line["fp64_gpu_sparse"] = fp64s
         line["speedup_vs_fp64_gpu_sparse"] = (value / world) / fp64s["value"]
@@ -967,6 +1100,12 @@ def main():
             other_obj["max_abs_err_pu"] = check.pop(f"{other}_max_abs_err_pu")
         if fp64s is not None and "fp64_sparse_max_abs_err_pu" in check:
             fp64s["max_abs_err_pu"] = check.pop("fp64_sparse_max_abs_err_pu")
+        # The headline's accuracy is the learned solve's when it is the headline; the flat start's
+        # iteration counts are compared with the oracle's.
+        flat["max_abs_err_pu"] = check["max_abs_err_pu"]
+        if "learned_max_abs_err_pu" in check:
+            check["max_abs_err_pu"] = learned["max_abs_err_pu"] = check.pop("learned_max_abs_err_pu")
+            check["iters_compared"] = "flat start"
         line["accuracy"] = check
     if other_obj is not None:
         line[f"{other}_method"] = other_obj
@@ -999,6 +1138,8 @@ def main():
         line["table1_100_bus"] = secondary(table1_100_leg, args, stream, rank == 0 and not args.no_cpu)
     if rank == 0:
         print(json.dumps(line), flush=True)
+    if net is not None:
+        net.close()
     fd.close()
 
 

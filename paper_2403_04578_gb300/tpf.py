@@ -566,7 +566,12 @@ class Feeder:
 
 
 def _batch_device(feeders, S, V, iters, mismatch):
-    """The one device of a batch: every feeder's and every tensor's."""
+    """The one device of a batch: every feeder's and every tensor's.  With a single visible GPU every
+    CUDA tensor is on it, and the per-tensor pass (thousands of tensors in a large batch) is skipped."""
+    import torch
+
+    if torch.cuda.device_count() == 1 and len(S):
+        return S[0].device.index
     named = []
     for f in range(len(S)):
         named += [(f"S[{f}]", S[f]), (f"V[{f}]", V[f]), (f"iters[{f}]", iters[f]), (f"mismatch[{f}]", mismatch[f])]

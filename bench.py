@@ -105,7 +105,7 @@ def parse_args():
     p.add_argument("--headline", choices=["learned", "flat"], default="learned",
                    help="the headline step: learned-start solve (prediction + warm solve) or flat start")
     p.add_argument("--train-columns", type=int, default=100000)
-    p.add_argument("--epochs", type=int, default=60)
+    p.add_argument("--epochs", type=int, default=100)
     return p.parse_args()
 
 
@@ -368,9 +368,9 @@ def learned_e2e(fd, net, Sh, Vh, ith, mmh, Sd, Vd, itd, mmd, args, world, chunks
 
 def learned_start_leg(args, stream):
     """Config 5: a 200-bus feeder, the network trained on 100,000 columns solved by the library, then
-    525,600 unseen columns solved from its prediction (a warm start) vs from the flat start (both
-    mixed, sparse formulation, tol as the headline), and the plain FP64 GPU path from the flat start
-    on a column sample."""
+    525,600 unseen columns solved by the learned-start solve (fused prediction + warm sparse solve)
+    against the flat start (both mixed, sparse formulation, tol as the headline), and the plain FP64
+    GPU path from the flat start on a column sample."""
     import torch
 
     from paper_2403_04578_gb300 import inputs as G
@@ -379,70 +379,39 @@ def learned_start_leg(args, stream):
     dev = torch.device("cuda", torch.cuda.current_device())
     f = G.make_feeder(200, args.seed)
     fd = tpf.Feeder.from_inputs(f)
-    n_train, n_eval = 100_000, args.columns
-    S_tr = torch.from_numpy(G.load_tensor(f, n_train, args.seed + 100)).to(dev)
-    V_tr, _, _, st = fd.solve(S_tr, precision="mixed", tol=args.tol, method="sparse")
-    # Buffers for 16,384-column batches: training steps use 1,024 columns, inference the full width
-    # (fewer, larger launches).
-    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=16384, seed=args.seed)
-    net.fit_normalization(S_tr, V_tr)
-    B = 1024
-    steps_per_epoch = n_train // B
-    epochs = 20
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    perm_gen = torch.Generator(device="cpu").manual_seed(args.seed)
-    for ep in range(epochs):
-        lr = 1e-3 * (0.5 * (1 + np.cos(np.pi * ep / epochs)) * 0.9 + 0.1)
-        order = torch.randperm(n_train, generator=perm_gen)[: steps_per_epoch * B].to(dev)
-        Sp, Vp = S_tr[order].contiguous(), V_tr[order].contiguous()
-        for k in range(steps_per_epoch):
-            net.train_step(Sp[k * B:(k + 1) * B], Vp[k * B:(k + 1) * B], lr=lr, want_loss=False)
-    loss = net.train_step(S_tr[:B], V_tr[:B], lr=1e-12)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    S_ev = torch.from_numpy(G.load_tensor(f, n_eval, args.seed + 200)).to(dev)
+    n_eval = args.columns
+    net, train_info = train_start_network(f, fd, args, dev, 100_000, args.epochs)
+    S_ev = G.load_tensor_device(f, n_eval, args.seed + 200, dev)
     V = torch.empty_like(S_ev)
     it = torch.empty(n_eval, dtype=torch.int32, device=dev)
     mm = torch.empty(n_eval, dtype=torch.float64, device=dev)
-
-    def timed(fn, reps=3):
-        fn()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(reps):
-            fn()
-        b.record(stream)
-        b.synchronize()
-        return a.elapsed_time(b) / reps
-
     fb = [0]
 
     def learned():
-        V0, fb[0] = net.predict(S_ev, V)
-        fd.solve(S_ev, V0, it, mm, precision="mixed", tol=args.tol, start="warm", method="sparse")
+        fb[0] = fd.solve_learned(net, S_ev, V, it, mm, tol=args.tol)[3]
 
-    ms_learned = timed(learned)
+    ms_learned = timed_device(learned, 3, stream)
     it_learned = it.float().mean().item()
     V_learned = V.cpu().numpy()
-    ms_predict = timed(lambda: net.predict(S_ev, V))
-    ms_flat = timed(lambda: fd.solve(S_ev, V, it, mm, precision="mixed", tol=args.tol, start="flat", method="sparse"))
+    ms_predict = timed_device(lambda: net.predict(S_ev, V), 3, stream)
+    ms_flat = timed_device(lambda: fd.solve(S_ev, V, it, mm, precision="mixed", tol=args.tol, start="flat",
+                                            method="sparse"), 3, stream)
     it_flat = it.float().mean().item()
     F = min(args.fp64_sample, n_eval)
     Sf = S_ev[:F].contiguous()
-    ms_fp64 = timed(lambda: fd.solve(Sf, precision="fp64", tol=args.tol), reps=2)
+    ms_fp64 = timed_device(lambda: fd.solve(Sf, precision="fp64", tol=args.tol), 2, stream)
     out = {
-        "workload": f"200-bus feeder, network 398-256-256-256-398 (GELU, BF16), trained {epochs} epochs on "
-                    f"{n_train:,} library-solved columns; evaluated on {n_eval:,} unseen columns",
-        "value": n_eval / (ms_learned / 1e3), "unit": "PF/s", "method": "sparse, start=warm",
-        "predict_ms": ms_predict, "solve_ms": ms_learned - ms_predict,
-        "flat_start_mixed": n_eval / (ms_flat / 1e3),
+        "workload": f"200-bus feeder, network {2 * f.n_pq}-256-256-256-{2 * f.n_pq} (GELU, BF16), trained "
+                    f"{train_info['epochs']} epochs on {train_info['train_columns']:,} library-solved columns; "
+                    f"evaluated on {n_eval:,} unseen columns",
+        "value": n_eval / (ms_learned / 1e3), "unit": "PF/s", "method": "tpf_solve_learned (sparse, warm start)",
+        "ms_per_step": ms_learned, "predict_ms_complex128": ms_predict,
+        "flat_start_mixed": n_eval / (ms_flat / 1e3), "flat_ms_per_step": ms_flat,
+        "speedup_learned_vs_flat": ms_flat / ms_learned,
         "plain_fp64_gpu": F / (ms_fp64 / 1e3),
         "speedup_vs_plain_fp64": (n_eval / (ms_learned / 1e3)) / (F / (ms_fp64 / 1e3)),
-        "mean_sweeps_learned": it_learned, "mean_sweeps_flat": it_flat,
-        "fallback_columns": fb[0], "train_seconds": train_s, "final_batch_loss": loss,
+        "mean_sweeps_learned": it_learned, "mean_sweeps_flat": it_flat, "fallback_columns": fb[0],
+        **{k: v for k, v in train_info.items() if k != "network"},
     }
     fd.close()
     net.close()

@@ -361,8 +361,9 @@ tpf_status tpf_mlp_predict(tpf_mlp *h, int64_t T, const void *S_dev, void *V0_de
  *   S_dev ... stream   as tpf_solve; opts->method must be TPF_METHOD_SPARSE and opts->precision
  *                TPF_PREC_MIXED (TPF_EUNSUPPORTED otherwise); opts->start is ignored
  *
- * The network keeps a complex64 buffer for the predictions of up to 262,144 columns (about 2 GB at
- * 1,000 buses) and one for their features.  tpf_last_stats(hd) reports the totals over the chunks.
+ * The columns go in equal chunks of at most 1,048,576; the network keeps a complex64 buffer for the
+ * predictions of one chunk (8 n_pq bytes per column: 4.2 GB for a one-minute year at 1,000 buses)
+ * and one for the features of up to 131,072 columns.  tpf_last_stats(hd) reports the totals over the chunks.
  * Blocks until done.
  */
 tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void *S_dev, void *V_dev,

@@ -55,7 +55,7 @@ struct tpf_mlp {
     bf16 *Xi = nullptr;                    // interleaved features [xi_cap][pad0]
     int64_t xi_cap = 0;
     float2 *V0c = nullptr;                 // complex64 starting voltages of tpf_solve_learned
-    int64_t v0_cap = 0;
+    int64_t v0_cap = 0;                    // complex values allocated in V0c
 };
 
 namespace tpf {
@@ -513,7 +513,7 @@ constexpr int64_t kInferChunk = 131072;
 // guard, a column whose prediction leaves the |V| band gets the flat start here (otherwise its
 // reader, the learned-start solve, checks the band).
 tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_64, cudaStream_t st,
-                       bool guard = true) {
+                       bool guard = true, int64_t pitch = 0) {
     const int L = h->L, H = h->pad[1], P0 = h->pad[0], PL = h->pad[L];
     if (!h->infer_fresh) {
         if (!h->Wi0 && !(dalloc(&h->Wi0, (size_t)H * P0) && dalloc(&h->WiL, (size_t)PL * h->pad[L - 1]) &&
@@ -528,8 +528,10 @@ tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_6
         MLP_CK(cudaGetLastError());
         h->infer_fresh = true;
     }
-    const int64_t chunk = std::min<int64_t>(T, kInferChunk);
-    const int64_t rows = round_up(chunk, 128);
+    // Equal chunks of at most kInferChunk columns (whole tiles), so that no chunk is a small tail.
+    const int64_t n_ch = (T + kInferChunk - 1) / kInferChunk;
+    const int64_t chunk = round_up((T + n_ch - 1) / n_ch, 128);
+    const int64_t rows = chunk;
     if (h->xi_cap < rows) {
         cudaFree(h->Xi);
         h->Xi = nullptr;
@@ -554,6 +556,7 @@ tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_6
     g.hi2 = 1.1f * 1.1f;
     g.v0_64 = v0_64 ? 1 : 0;
     g.guard = guard ? 1 : 0;
+    g.pitch = pitch ? pitch : h->n;
     g.fallback = h->fallback;
     g.err = h->err;
     const size_t vsz = v0_64 ? sizeof(double2) : sizeof(float2);
@@ -565,7 +568,7 @@ tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_6
         if (!make_bf16_map(&g.map_x, h->Xi, P0, Tc)) return TPF_ECUDA;
         g.T = Tc;
         g.tiles = (Tc + 127) / 128;
-        g.V0 = static_cast<char *>(V0) + (size_t)t0 * h->n * vsz;
+        g.V0 = static_cast<char *>(V0) + (size_t)t0 * g.pitch * vsz;
         tpf_status rs = launch_infer(g, st);
         if (rs != TPF_OK) return rs;
     }
@@ -845,17 +848,22 @@ tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void
     tpf::DeviceScope dscope(hd->device);
     if (!dscope.ok) return TPF_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    // Prediction and solve in chunks of columns: the complex64 starting voltages of one chunk live
-    // in a buffer of the network, grown on demand.
-    const int64_t chunk = std::min<int64_t>(T, 262144);
+    // Prediction and solve in equal chunks of at most 1,048,576 columns: the complex64 starting
+    // voltages of one chunk live in a buffer of the network, grown on demand.
+    constexpr int64_t kLearnedChunk = 1 << 20;
+    const int64_t n_ch = (T + kLearnedChunk - 1) / kLearnedChunk;
+    const int64_t chunk = std::min<int64_t>(T, round_up((T + n_ch - 1) / n_ch, 128));
     const int64_t cap = round_up(chunk, 128);
     const int n = net->n;
-    if (net->v0_cap < cap) {
+    // Columns of the prediction buffer start on 128-byte boundaries: a warp's 32 consecutive
+    // outputs of one column then fill one cache line.
+    const int64_t pitch = round_up(n, 16);
+    if (net->v0_cap < cap * pitch) {
         cudaFree(net->V0c);
         net->V0c = nullptr;
         net->v0_cap = 0;
-        if (!dalloc(&net->V0c, (size_t)cap * n)) return TPF_ENOMEM;
-        net->v0_cap = cap;
+        if (!dalloc(&net->V0c, (size_t)(cap * pitch))) return TPF_ENOMEM;
+        net->v0_cap = cap * pitch;
     }
     MLP_CK(cudaMemsetAsync(net->err, 0, sizeof(int), st));
     MLP_CK(cudaMemsetAsync(net->fallback, 0, sizeof(int), st));
@@ -865,11 +873,11 @@ tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void
     for (int64_t c0 = 0; c0 < T; c0 += chunk) {
         const int64_t Tc = std::min(chunk, T - c0);
         const double2 *Sc = static_cast<const double2 *>(S_dev) + (size_t)c0 * n;
-        tpf_status rs = infer_fused(net, Tc, Sc, net->V0c, false, st, false);
+        tpf_status rs = infer_fused(net, Tc, Sc, net->V0c, false, st, false, pitch);
         if (rs != TPF_OK) return rs;
         rs = tpf::solve_sparse_ex(hd, Tc, Sc, static_cast<double2 *>(V_dev) + (size_t)c0 * n,
                                   iters_dev ? iters_dev + c0 : nullptr, mismatch_dev ? mismatch_dev + c0 : nullptr,
-                                  nullptr, o, st, net->V0c);
+                                  nullptr, o, st, net->V0c, pitch);
         if (rs != TPF_OK && rs != TPF_ENOCONV) return rs;
         if (rs == TPF_ENOCONV) result = TPF_ENOCONV;
         fallback += hd->start_fallback;

@@ -16,11 +16,13 @@
 // transposed (outputs on the TMEM lanes, the tile's columns along TMEM), so that a warp's 32
 // threads hold 32 consecutive outputs of one column and its stores to V_0 are contiguous.  Warp 0
 // issues the TMA loads into a 3-slot ring, warp 1 the MMAs (one thread), warps 2-9 the epilogues:
-// bias and GELU of a hidden layer written as BF16 into the shared-memory operand of the next layer
+// bias and GELU (tanh form, half precision) of a hidden layer written as BF16 into the
+// shared-memory operand of the next layer
 // (128-byte swizzle, the layout TMA would have written), and for the last layer the
 // denormalisation into V_0 with the |V| guard.  Every wait is bounded; on expiry the CTA flags the
 // error, drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <cstring>
 
@@ -45,26 +47,31 @@ constexpr uint32_t kBiasBytes = (kMaxInferLayers - 1) * 256 * 4;  // hidden bias
 constexpr size_t kSmem = 1024 + kStages * kStageBytes + kHBytes + 1024 + kBiasBytes;
 constexpr int kOutTile = 128;  // outputs per last-layer accumulator job
 
-// GELU in its erf form, z Phi(z) = z (1 + erf(z / sqrt 2)) / 2, with erf from the rational
-// approximation of Abramowitz and Stegun 7.1.26 (Hastings): for x >= 0,
-//     erf(x) = 1 - (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-x^2),  t = 1 / (1 + p x),
-// |error| <= 1.5e-7, far below the BF16 rounding (2^-9) of the activation it feeds; erf is odd.
-__device__ __forceinline__ float gelu_erf(float z) {
-    const float x = fabsf(z) * 0.70710678118654752f;
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
-    const float poly =
-        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
-    const float e = 1.0f - poly * __expf(-x * x);
-    return 0.5f * z * (1.0f + copysignf(e, z));
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+// GELU of a pair of pre-activations for the next layer's BF16 operand, in packed half precision
+// with its tanh form, 0.5 z (1 + tanh(sqrt(2/pi) (z + 0.044715 z^3))): one tanh.approx.f16x2 and
+// a few f16x2 FMAs per pair.  The tanh form differs from the erf form z Phi(z) (which training
+// uses) by at most about 3e-4, and the half-precision evaluation by about 1e-3 relative, both
+// below the BF16 rounding (2^-9 relative) of the activation they produce.
+__device__ __forceinline__ uint32_t gelu_pair_bf16(float z0, float z1) {
+    const __half2 z = __floats2half2_rn(z0, z1);
+    const __half2 k0 = __float2half2_rn(0.7978845608f), k1 = __float2half2_rn(0.0356774081f);  // sqrt(2/pi), *0.044715
+    const __half2 half = __float2half2_rn(0.5f);
+    const __half2 u = __hmul2(z, __hfma2(__hmul2(z, z), k1, k0));
+    __half2 t;
+    asm("tanh.approx.f16x2 %0, %1;" : "=r"(*reinterpret_cast<uint32_t *>(&t)) : "r"(*reinterpret_cast<const uint32_t *>(&u)));
+    const __half2 hz = __hmul2(half, z);
+    const float2 g = __half22float2(__hfma2(hz, t, hz));
+    return pack_bf16(g.x, g.y);
 }
 
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
-__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
-    return *reinterpret_cast<const uint32_t *>(&v);
-}
 
 __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__ InferArgs g) {
     extern __shared__ uint8_t smem_raw[];
@@ -248,8 +255,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
                             const float2 b2 = *reinterpret_cast<const float2 *>(bias + p * 32 + 2 * e);
-                            w[e] = pack_bf16(gelu_erf(__uint_as_float(v[2 * e]) + b2.x),
-                                             gelu_erf(__uint_as_float(v[2 * e + 1]) + b2.y));
+                            w[e] = gelu_pair_bf16(__uint_as_float(v[2 * e]) + b2.x,
+                                                  __uint_as_float(v[2 * e + 1]) + b2.y);
                         }
                         // Units p*32 .. p*32+31: K chunk p/2, 16-byte groups 4 (p&1) .. +3, swizzled by row.
                         uint8_t *chunk = hrow + (p >> 1) * kATile;
@@ -272,7 +279,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
                     // value = (d + b) s + m (+ 1 for Re V) = d s + c
                     const float so = __ldg(g.out_std + o);
                     const float co = __ldg(g.bias_out + o) * so + __ldg(g.out_mean + o) + ((o & 1) ? 0.0f : 1.0f);
-                    const int64_t stride = 2 * (int64_t)g.n;
+                    const int64_t stride = 2 * g.pitch;  // floats (or doubles) per column of V0
                     for (int p = 2 * half; p < 2 * half + 2; ++p) {
                         uint32_t v[32];
                         tmem_ld32(acc + p * 32, v);
@@ -333,7 +340,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
             if (half == 0) {
                 if (t < g.T && bad) {  // outside the guard band: the flat start for this column
                     for (int i = 0; i < g.n; ++i) {
-                        const int64_t k = t * g.n + i;
+                        const int64_t k = t * g.pitch + i;
                         if (g.v0_64)
                             static_cast<double2 *>(g.V0)[k] = make_double2(1.0, 0.0);
                         else

@@ -71,6 +71,7 @@ struct TreeWork {
     int s32, v32;
     int v0_pred;         // V0 is a complex64 prediction of the learned start (V_out complex128): a
                          // column with some |V_i| outside [0.7, 1.1] starts flat instead
+    int64_t v0_pitch;    // complex values per column of that prediction
     int64_t col0;        // first launch column of this feeder
     int64_t T;
     int *conv;           // converged columns of this feeder (accumulated)
@@ -456,7 +457,7 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
             if (q < n) {
                 const int64_t k = t * n + a.col[s];
                 if (a.v0_pred) {
-                    vr[j] = static_cast<const float2 *>(a.V0)[k];
+                    vr[j] = static_cast<const float2 *>(a.V0)[t * a.v0_pitch + a.col[s]];
                     const float m2 = abs2(vr[j]);
                     off_band |= !(m2 >= 0.49f && m2 <= 1.21f);
                 } else if (a.v32) {
@@ -961,7 +962,8 @@ TreeArgs args_of(const tpf_opts &o) {
 }  // namespace
 
 tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters, double *mismatch,
-                           const tpf_outputs *out, const tpf_opts &o, cudaStream_t st, const void *V0_pred) {
+                           const tpf_outputs *out, const tpf_opts &o, cudaStream_t st, const void *V0_pred,
+                           int64_t v0_pitch) {
     const DeviceNet &d = h->dev;
     if (!d.radial || o.precision != TPF_PREC_MIXED || d.t_threads == 0) return TPF_EUNSUPPORTED;
     if (T > 0x7fffffff) return TPF_EUNSUPPORTED;
@@ -982,6 +984,7 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
     if (V0_pred) {  // a warm start read from a separate predicted V_0
         wk.V0 = V0_pred;
         wk.v0_pred = 1;
+        wk.v0_pitch = v0_pitch > 0 ? v0_pitch : h->dev.n;
         g.given = 1;
         g.blind = 0;
     }
@@ -1026,7 +1029,7 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
         wc.T = std::min(chunk, T - c0);
         wc.S = static_cast<const char *>(S) + (size_t)c0 * n * s_size;
         if (V) wc.V0 = wc.V_out = static_cast<char *>(V) + (size_t)c0 * n * v_size;
-        if (V0_pred) wc.V0 = static_cast<const char *>(V0_pred) + (size_t)c0 * n * sizeof(float2);
+        if (V0_pred) wc.V0 = static_cast<const char *>(V0_pred) + (size_t)c0 * wk.v0_pitch * sizeof(float2);
         if (iters) wc.iters_out = iters + c0;
         if (mismatch) wc.mismatch_out = mismatch + c0;
         if (wk.col_vmin) wc.col_vmin = wk.col_vmin + c0;

@@ -59,9 +59,12 @@ METRIC = "PF solves/s at ≤1e-8 pu vs FP64 oracle: mixed+learned-start vs plain
 # 1,000-bus feeder over 16,384 columns (203.7 MB + 75.5 MB), per iterating column; scaled by the
 # columns each launch of this run processes.  None once the kernel has changed since the capture.
 GEMM_TRAFFIC_BYTES_PER_COLUMN = (203.725056e6 + 75.471360e6) / 16384
-# The same for the sparse tree kernel mx_tree (one launch per solve): 262.0 MB read + 209.4 MB
-# written for 16,384 columns of the 1,000-bus feeder.
-TREE_TRAFFIC_BYTES_PER_COLUMN = (262.013952e6 + 209.440256e6) / 16384
+# The same for the sparse tree kernel mx_tree started from the learned prediction (the headline
+# step's solve): 394.1 MB read (S and the complex64 prediction) + 221.2 MB written for 16,384
+# columns of the 1,000-bus feeder.
+TREE_TRAFFIC_BYTES_PER_COLUMN = (394.113536e6 + 221.190656e6) / 16384
+# From the flat start: not captured for the current build of the kernel (null in the line).
+TREE_FLAT_TRAFFIC_BYTES_PER_COLUMN = None
 # Algorithmic FP32 flop per bus per sweep of the tree formulation: load current conj(S/V) 12,
 # prefix sum 2, subtree difference 2, z L 6, subtree-end subtraction 2, path prefix 2, update 4,
 # |step|^2 and max 6.
@@ -890,14 +893,14 @@ def main():
                 "share_of_step": run["gemm_ms"] / sum(run["step_ms"]),
                 "ms_per_launch": run["gemm_ms"] / max(run["gemm_launch"], 1)}
 
-    def tree_roofline(run, sweeps):
+    def tree_roofline(run, sweeps, per_column=TREE_TRAFFIC_BYTES_PER_COLUMN):
         # FP32 peak from the unit counts: SMs x 128 FP32 lanes x 2 flop (FMA) x max SM clock.
         sm_count = torch.cuda.get_device_properties(local).multi_processor_count
         peak = sm_count * 128 * 2 * float(peaks.get("sm_max_mhz", 2070.0)) * 1e6 / 1e12
         achieved = TREE_FLOPS_PER_BUS_SWEEP * n * sweeps / (run["kernel_ms"] / 1e3) / 1e12
         traffic = None
-        if TREE_TRAFFIC_BYTES_PER_COLUMN is not None and args.buses == 1000:
-            traffic = TREE_TRAFFIC_BYTES_PER_COLUMN * T
+        if per_column is not None and args.buses == 1000:
+            traffic = per_column * T
         return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "mx_tree",
                 "peak_source": f"FP32: {sm_count} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
@@ -905,12 +908,13 @@ def main():
                               "column-sweeps (anchors and the final residual not counted)",
                 "traffic_note": "ncu DRAM bytes per column (capture of 16,384 columns of the 1,000-bus feeder) "
                                 "x columns per launch",
-                "hbm_frac": (TREE_TRAFFIC_BYTES_PER_COLUMN or 0) * T / (run["kernel_ms"] / 1e3) / 1e9
-                            / float(peaks.get("hbm_gbs", 6800.0)),
+                "hbm_frac": (per_column or 0) * T / (run["kernel_ms"] / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0))
+                            if per_column else None,
                 "share_of_step": run["kernel_ms"] * len(run["step_ms"]) / sum(run["step_ms"]),
                 "ms_per_launch": run["kernel_ms"]}
 
-    roofline = tree_roofline(main_run, column_sweeps) if args.method == "sparse" else gemm_roofline(main_run)
+    roofline = (tree_roofline(main_run, column_sweeps, TREE_FLAT_TRAFFIC_BYTES_PER_COLUMN) if args.method == "sparse"
+                else gemm_roofline(main_run))
     flat = {"value": value, "unit": "PF/s", "ms_per_step": ms_per_step, "mean_sweeps": column_sweeps / T,
             "gpu_launches": main_run["launches"], "roofline": roofline,
             "note": "flat start V_0 = 1 (Algorithm 1), sparse mixed solve"}

@@ -8,8 +8,12 @@
 
 namespace tpf {
 
-// A double-float value is hi + lo with |lo| <= ulp(hi)/2.  Every operation uses explicitly rounded
-// intrinsics so that the compiler cannot fuse or reorder the error terms.
+// A double-float value is hi + lo with |lo| <= ulp(hi)/2.  The arithmetic is the classical
+// error-free-transformation method: Knuth's TwoSum (and Dekker's FastTwoSum when |a| >= |b|) for
+// the exact rounding error of a sum, the FMA-based TwoProduct (p = fl(a b), e = fma(a, b, -p)) for
+// that of a product, and one Newton step q1 + q1 (1 - b q1) for a reciprocal; the double-float
+// operations combine them as in Dekker's and Shewchuk's double-length arithmetic.  Every operation
+// uses explicitly rounded intrinsics so that the compiler cannot fuse or reorder the error terms.
 struct f2 {
     float h, l;
 };

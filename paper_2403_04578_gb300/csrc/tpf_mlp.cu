@@ -513,7 +513,7 @@ constexpr int64_t kInferChunk = 131072;
 // guard, a column whose prediction leaves the |V| band gets the flat start here (otherwise its
 // reader, the learned-start solve, checks the band).
 tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_64, cudaStream_t st,
-                       bool guard = true, int64_t pitch = 0) {
+                       bool guard = true, int64_t pitch = 0, int64_t *launches = nullptr) {
     const int L = h->L, H = h->pad[1], P0 = h->pad[0], PL = h->pad[L];
     if (!h->infer_fresh) {
         if (!h->Wi0 && !(dalloc(&h->Wi0, (size_t)H * P0) && dalloc(&h->WiL, (size_t)PL * h->pad[L - 1]) &&
@@ -527,6 +527,7 @@ tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_6
                                                            h->os_i);
         MLP_CK(cudaGetLastError());
         h->infer_fresh = true;
+        if (launches) ++*launches;
     }
     // Equal chunks of at most kInferChunk columns (whole tiles), so that no chunk is a small tail.
     const int64_t n_ch = (T + kInferChunk - 1) / kInferChunk;
@@ -571,6 +572,7 @@ tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_6
         g.V0 = static_cast<char *>(V0) + (size_t)t0 * g.pitch * vsz;
         tpf_status rs = launch_infer(g, st);
         if (rs != TPF_OK) return rs;
+        if (launches) *launches += 2;  // features and the fused inference
     }
     return TPF_OK;
 }
@@ -873,7 +875,8 @@ tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void
     for (int64_t c0 = 0; c0 < T; c0 += chunk) {
         const int64_t Tc = std::min(chunk, T - c0);
         const double2 *Sc = static_cast<const double2 *>(S_dev) + (size_t)c0 * n;
-        tpf_status rs = infer_fused(net, Tc, Sc, net->V0c, false, st, false, pitch);
+        int64_t predict_launches = 0;
+        tpf_status rs = infer_fused(net, Tc, Sc, net->V0c, false, st, false, pitch, &predict_launches);
         if (rs != TPF_OK) return rs;
         rs = tpf::solve_sparse_ex(hd, Tc, Sc, static_cast<double2 *>(V_dev) + (size_t)c0 * n,
                                   iters_dev ? iters_dev + c0 : nullptr, mismatch_dev ? mismatch_dev + c0 : nullptr,
@@ -885,7 +888,7 @@ tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void
         total.sweeps = std::max(total.sweeps, p.sweeps);
         total.precise_sweeps = std::max(total.precise_sweeps, p.precise_sweeps);
         total.converged += p.converged;
-        total.kernel_launches += p.kernel_launches + 2;  // features and fused inference per chunk
+        total.kernel_launches += p.kernel_launches + predict_launches;
         total.residual_ms += p.residual_ms;
     }
     const tpf_status rs = check_err(net, st);

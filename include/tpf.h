@@ -350,9 +350,9 @@ tpf_status tpf_mlp_predict(tpf_mlp *h, int64_t T, const void *S_dev, void *V0_de
 
 /*
  * Learned-start solve: the network predicts V_0 for every column (the fused inference of all its
- * layers, one tcgen05 kernel per chunk of columns, V_0 kept in complex64), then the sparse mixed
- * solve runs from it (TPF_START_WARM: FP32 sweeps from the prediction, anchoring once the step is
- * small).  A column whose prediction leaves |V| in [0.7, 1.1] starts flat; fallback_out (host, may
+ * layers, one tcgen05 kernel per chunk of columns, V_0 kept as half-precision deviations from the
+ * flat start, Re V - 1 and Im V), then the sparse mixed solve runs from it (TPF_START_WARM: FP32
+ * sweeps from the prediction, anchoring once the step is small).  A column whose prediction leaves |V| in [0.7, 1.1] starts flat; fallback_out (host, may
  * be NULL) receives how many did.  The iteration decides the result, so the outputs are those of
  * tpf_solve (Sec. III: the fixed point is reached from any nearby start).
  *
@@ -361,8 +361,8 @@ tpf_status tpf_mlp_predict(tpf_mlp *h, int64_t T, const void *S_dev, void *V0_de
  *   S_dev ... stream   as tpf_solve; opts->method must be TPF_METHOD_SPARSE and opts->precision
  *                TPF_PREC_MIXED (TPF_EUNSUPPORTED otherwise); opts->start is ignored
  *
- * The columns go in equal chunks of at most 1,048,576; the network keeps a complex64 buffer for the
- * predictions of one chunk (8 n_pq bytes per column: 4.2 GB for a one-minute year at 1,000 buses)
+ * The columns go in equal chunks of at most 1,048,576; the network keeps a buffer for the
+ * predictions of one chunk (4 bytes per bus and column: 2.1 GB for a one-minute year at 1,000 buses)
  * and one for the features of up to 131,072 columns.  tpf_last_stats(hd) reports the totals over the chunks.
  * Blocks until done.
  */

@@ -271,9 +271,10 @@ tpf_status solve_mixed(tpf_handle *h, int64_t T, const void *S, void *V, int32_t
                        double *mismatch, const tpf_opts &o, cudaStream_t st);
 tpf_status solve_sparse(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
                         double *mismatch, const tpf_opts &o, cudaStream_t st);
-// V0_pred (optional, device complex64, column t at V0_pred + t * v0_pitch, v0_pitch >= n; 0 = n): a
-// warm start read from a prediction instead of from V; a column whose prediction has some |V_i|
-// outside [0.7, 1.1] starts flat (counted in h->start_fallback).
+// V0_pred (optional, device half2 deviations (Re V - 1, Im V) per bus, column t at
+// V0_pred + t * v0_pitch, v0_pitch >= n; 0 = n): a warm start read from a prediction instead of
+// from V; a column whose prediction has some |V_i| outside [0.7, 1.1] starts flat (counted in
+// h->start_fallback).
 tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int32_t *iters,
                            double *mismatch, const tpf_outputs *out, const tpf_opts &o, cudaStream_t st,
                            const void *V0_pred = nullptr, int64_t v0_pitch = 0);

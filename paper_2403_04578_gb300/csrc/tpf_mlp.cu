@@ -54,7 +54,7 @@ struct tpf_mlp {
     float *im_i = nullptr, *is_i = nullptr;                     // [pad0]
     bf16 *Xi = nullptr;                    // interleaved features [xi_cap][pad0]
     int64_t xi_cap = 0;
-    float2 *V0c = nullptr;                 // complex64 starting voltages of tpf_solve_learned
+    __half2 *V0c = nullptr;                // predicted deviations (Re V - 1, Im V) of tpf_solve_learned
     int64_t v0_cap = 0;                    // complex values allocated in V0c
 };
 
@@ -513,7 +513,7 @@ constexpr int64_t kInferChunk = 131072;
 // guard, a column whose prediction leaves the |V| band gets the flat start here (otherwise its
 // reader, the learned-start solve, checks the band).
 tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_64, cudaStream_t st,
-                       bool guard = true, int64_t pitch = 0, int64_t *launches = nullptr) {
+                       bool guard = true, int64_t pitch = 0, int64_t *launches = nullptr, bool v0_half = false) {
     const int L = h->L, H = h->pad[1], P0 = h->pad[0], PL = h->pad[L];
     if (!h->infer_fresh) {
         if (!h->Wi0 && !(dalloc(&h->Wi0, (size_t)H * P0) && dalloc(&h->WiL, (size_t)PL * h->pad[L - 1]) &&
@@ -557,10 +557,11 @@ tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_6
     g.hi2 = 1.1f * 1.1f;
     g.v0_64 = v0_64 ? 1 : 0;
     g.guard = guard ? 1 : 0;
+    g.v0_half = v0_half ? 1 : 0;
     g.pitch = pitch ? pitch : h->n;
     g.fallback = h->fallback;
     g.err = h->err;
-    const size_t vsz = v0_64 ? sizeof(double2) : sizeof(float2);
+    const size_t vsz = v0_half ? sizeof(__half2) : (v0_64 ? sizeof(double2) : sizeof(float2));
     for (int64_t t0 = 0; t0 < T; t0 += chunk) {
         const int64_t Tc = std::min(chunk, T - t0);
         k_features_il<<<grid2(P0 / 2, (int)Tc), kThreads, 0, st>>>((const double2 *)S, T, t0, (int)Tc, h->n, P0,
@@ -850,8 +851,9 @@ tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void
     tpf::DeviceScope dscope(hd->device);
     if (!dscope.ok) return TPF_ECUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    // Prediction and solve in equal chunks of at most 1,048,576 columns: the complex64 starting
-    // voltages of one chunk live in a buffer of the network, grown on demand.
+    // Prediction and solve in equal chunks of at most 1,048,576 columns: the predicted deviations
+    // from the flat start (half2 per bus) of one chunk live in a buffer of the network, grown on
+    // demand.
     constexpr int64_t kLearnedChunk = 1 << 20;
     const int64_t n_ch = (T + kLearnedChunk - 1) / kLearnedChunk;
     const int64_t chunk = std::min<int64_t>(T, round_up((T + n_ch - 1) / n_ch, 128));
@@ -876,7 +878,7 @@ tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void
         const int64_t Tc = std::min(chunk, T - c0);
         const double2 *Sc = static_cast<const double2 *>(S_dev) + (size_t)c0 * n;
         int64_t predict_launches = 0;
-        tpf_status rs = infer_fused(net, Tc, Sc, net->V0c, false, st, false, pitch, &predict_launches);
+        tpf_status rs = infer_fused(net, Tc, Sc, net->V0c, false, st, false, pitch, &predict_launches, true);
         if (rs != TPF_OK) return rs;
         rs = tpf::solve_sparse_ex(hd, Tc, Sc, static_cast<double2 *>(V_dev) + (size_t)c0 * n,
                                   iters_dev ? iters_dev + c0 : nullptr, mismatch_dev ? mismatch_dev + c0 : nullptr,

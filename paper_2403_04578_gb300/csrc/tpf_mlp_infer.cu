@@ -15,7 +15,7 @@
 // with the FP32 accumulator in TMEM (two stages of 256 columns).  The last layer is taken
 // transposed (outputs on the TMEM lanes, the tile's columns along TMEM), so that a warp's 32
 // threads hold 32 consecutive outputs of one column and its stores to V_0 are contiguous.  Warp 0
-// issues the TMA loads into a 3-slot ring, warp 1 the MMAs (one thread), warps 2-9 the epilogues:
+// issues the TMA loads into a 3-slot ring, warp 1 the MMAs (one thread), 16 warps the epilogues:
 // bias and GELU (tanh form, half precision) of a hidden layer written as BF16 into the
 // shared-memory operand of the next layer
 // (128-byte swizzle, the layout TMA would have written), and for the last layer the
@@ -36,8 +36,9 @@ namespace {
 
 using namespace tc;
 
-constexpr int kThreads = 320;  // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue (two per TMEM lane quarter)
-constexpr int kEpiThreads = 256;
+constexpr int kEpiGroups = 4;  // epilogue warps per TMEM lane quarter
+constexpr int kEpiThreads = 128 * kEpiGroups;
+constexpr int kThreads = 64 + kEpiThreads;  // warp 0 TMA, warp 1 MMA, then the epilogue warps
 constexpr int kStages = 3;
 constexpr uint32_t kATile = 128 * 64 * 2;  // 16 KB: 128 rows x 64 BF16 (one K chunk of A)
 constexpr uint32_t kBMax = 256 * 64 * 2;   // 32 KB: up to 256 rows x 64 BF16 (one K chunk of B)
@@ -69,7 +70,7 @@ __device__ __forceinline__ uint32_t gelu_pair_bf16(float z0, float z1) {
     return pack_bf16(g.x, g.y);
 }
 
-__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, 256;" ::: "memory"); }
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 
@@ -218,17 +219,17 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
         umma_commit(smem_u32(done));
         mbar_wait(smem_u32(done), 0);  // every MMA of this CTA has retired (bounded)
     } else if (warp >= 2) {
-        // ---------------- epilogue: 256 threads, two warps per TMEM lane quarter ----------------
-        // Hidden layers: thread = column row of the tile, `half` splits the units.  Last layer:
-        // thread = output row of the accumulator, `half` splits the tile's columns.
+        // ---------------- epilogue: kEpiGroups warps per TMEM lane quarter ----------------
+        // Hidden layers: thread = column row of the tile, `part` splits the units.  Last layer:
+        // thread = output row of the accumulator, `part` splits the tile's columns.
         const int quarter = warp & 3;  // TMEM lanes this warp may access
-        const int half = (warp - 2) >> 2;
+        const int part = (warp - 2) >> 2;
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         const int et = tid - 64;
         // This row's 128-byte line inside each 16 KB K chunk of the activations (SW128 layout).
         uint8_t *hrow = Hs + (row >> 3) * 1024 + (row & 7) * 128;
-        const int hp = H / 64;  // pieces of 32 units per half
+        const int hp = H / 32 / kEpiGroups;  // pieces of 32 units per part
         uint32_t jq = 0;
         for (int64_t tile = blockIdx.x; tile < g.tiles; tile += gridDim.x) {
             const int64_t t = tile * 128 + row;  // this thread's column (hidden layers)
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
                 if (j < L - 1) {
                     // Hidden activations of layer j: bias, GELU, BF16 into the next layer's A operand.
                     const float *bias = s_bias + j * H;
-                    for (int p = half * hp; p < (half + 1) * hp; ++p) {
+                    for (int p = part * hp; p < (part + 1) * hp; ++p) {
                         uint32_t v[32];
                         tmem_ld32(acc + p * 32, v);
                         tmem_wait_ld();
@@ -278,14 +279,30 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
                     const int o = (j - (L - 1)) * kOutTile + row, i = o >> 1;
                     // value = (d + b) s + m (+ 1 for Re V) = d s + c
                     const float so = __ldg(g.out_std + o);
-                    const float co = __ldg(g.bias_out + o) * so + __ldg(g.out_mean + o) + ((o & 1) ? 0.0f : 1.0f);
+                    const float cd = __ldg(g.bias_out + o) * so + __ldg(g.out_mean + o);  // deviation: Re V - 1, Im V
+                    const float co = cd + ((o & 1) ? 0.0f : 1.0f);
                     const int64_t stride = 2 * g.pitch;  // floats (or doubles) per column of V0
-                    for (int p = 2 * half; p < 2 * half + 2; ++p) {
+                    for (int p = part * (4 / kEpiGroups); p < (part + 1) * (4 / kEpiGroups); ++p) {
                         uint32_t v[32];
                         tmem_ld32(acc + p * 32, v);
                         tmem_wait_ld();
                         const int64_t c0 = tile * 128 + p * 32;  // first column of this piece
                         const int valid = i < g.n ? (int)min((int64_t)32, g.T - c0) : 0;
+                        if (g.v0_half) {
+                            // The deviation from the flat start in half precision (the reader adds 1
+                            // to the real part and checks the |V| band).
+                            __half *dst = static_cast<__half *>(g.V0) + c0 * stride + o;
+                            if (valid == 32) {
+#pragma unroll
+                                for (int e = 0; e < 32; ++e)
+                                    dst[e * stride] = __float2half_rn(fmaf(__uint_as_float(v[e]), so, cd));
+                            } else {
+#pragma unroll
+                                for (int e = 0; e < 32; ++e)
+                                    if (e < valid) dst[e * stride] = __float2half_rn(fmaf(__uint_as_float(v[e]), so, cd));
+                            }
+                            continue;
+                        }
                         float val[32];
 #pragma unroll
                         for (int e = 0; e < 32; ++e) val[e] = fmaf(__uint_as_float(v[e]), so, co);
@@ -337,7 +354,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
             const bool bad = (s_badm[row >> 5] >> (row & 31)) & 1u;
             epi_sync();  // every thread has read its bit
             if (et < 4) s_badm[et] = 0;  // (set again only after the next tile's first job barrier)
-            if (half == 0) {
+            if (part == 0) {
                 if (t < g.T && bad) {  // outside the guard band: the flat start for this column
                     for (int i = 0; i < g.n; ++i) {
                         const int64_t k = t * g.pitch + i;

@@ -22,6 +22,7 @@ struct InferArgs {
     void *V0;                               // [T][n] complex64, or complex128 when v0_64
     int v0_64;
     int guard;                              // apply the |V| guard here (else the reader checks)
+    int v0_half;                            // V0 holds half2 deviations (Re V - 1, Im V) instead
     int64_t pitch;                          // complex values per column of V0 (>= n; n for [T][n])
     int *fallback;                          // columns that failed the guard (given the flat start)
     int *err;                               // set when a bounded wait expired

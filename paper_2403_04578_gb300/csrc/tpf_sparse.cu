@@ -69,8 +69,9 @@ struct TreeWork {
     int32_t *iters_out;  // [T] or null
     double *mismatch_out;  // [T] or null
     int s32, v32;
-    int v0_pred;         // V0 is a complex64 prediction of the learned start (V_out complex128): a
-                         // column with some |V_i| outside [0.7, 1.1] starts flat instead
+    int v0_pred;         // V0 is the learned start's prediction, half2 deviations (Re V - 1, Im V)
+                         // per bus (V_out complex128): a column with some |V_i| outside
+                         // [0.7, 1.1] starts flat instead
     int64_t v0_pitch;    // complex values per column of that prediction
     int64_t col0;        // first launch column of this feeder
     int64_t T;
@@ -457,7 +458,8 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
             if (q < n) {
                 const int64_t k = t * n + a.col[s];
                 if (a.v0_pred) {
-                    vr[j] = static_cast<const float2 *>(a.V0)[t * a.v0_pitch + a.col[s]];
+                    const float2 d = __half22float2(static_cast<const __half2 *>(a.V0)[t * a.v0_pitch + a.col[s]]);
+                    vr[j] = make_float2(1.0f + d.x, d.y);
                     const float m2 = abs2(vr[j]);
                     off_band |= !(m2 >= 0.49f && m2 <= 1.21f);
                 } else if (a.v32) {
@@ -1029,7 +1031,7 @@ tpf_status solve_sparse_ex(tpf_handle *h, int64_t T, const void *S, void *V, int
         wc.T = std::min(chunk, T - c0);
         wc.S = static_cast<const char *>(S) + (size_t)c0 * n * s_size;
         if (V) wc.V0 = wc.V_out = static_cast<char *>(V) + (size_t)c0 * n * v_size;
-        if (V0_pred) wc.V0 = static_cast<const char *>(V0_pred) + (size_t)c0 * wk.v0_pitch * sizeof(float2);
+        if (V0_pred) wc.V0 = static_cast<const char *>(V0_pred) + (size_t)c0 * wk.v0_pitch * sizeof(__half2);
         if (iters) wc.iters_out = iters + c0;
         if (mismatch) wc.mismatch_out = mismatch + c0;
         if (wk.col_vmin) wc.col_vmin = wk.col_vmin + c0;

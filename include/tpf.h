@@ -342,18 +342,19 @@ tpf_status tpf_mlp_train_step(tpf_mlp *h, int B, const void *S_dev, const void *
  * receives them in the parameter order.  Blocks. */
 tpf_status tpf_mlp_gradients(tpf_mlp *h, int B, const void *S_dev, const void *V_dev,
                              double *loss_out, float *grads_host, void *stream);
-/* Predicted V_0 for T columns (device complex128 [T][n_pq] in and out).  A column whose predicted
- * |V_i| leaves [0.7, 1.1] at any bus gets the flat start; fallback_out (host, may be NULL)
- * receives how many.  Blocks. */
+/* Predicted V_0 for T columns (device complex128 [T][n_pq] in and out; S_dev 16-byte aligned).
+ * A column whose predicted |V_i| leaves [0.7, 1.1] at any bus gets the flat start; fallback_out
+ * (host, may be NULL) receives how many.  Blocks. */
 tpf_status tpf_mlp_predict(tpf_mlp *h, int64_t T, const void *S_dev, void *V0_dev,
                            int64_t *fallback_out, void *stream);
 
 /*
  * Learned-start solve: the network predicts V_0 for every column (the fused inference of all its
- * layers, one tcgen05 kernel per chunk of columns, V_0 kept as half-precision deviations from the
- * flat start, Re V - 1 and Im V), then the sparse mixed solve runs from it (TPF_START_WARM: FP32
- * sweeps from the prediction, anchoring once the step is small).  A column whose prediction leaves |V| in [0.7, 1.1] starts flat; fallback_out (host, may
- * be NULL) receives how many did.  The iteration decides the result, so the outputs are those of
+ * layers, one tcgen05 kernel per chunk of columns that reads S itself, V_0 kept as half-precision
+ * deviations from the flat start, Re V - 1 and Im V), then the sparse mixed solve runs from it
+ * (TPF_START_WARM: FP32 sweeps from the prediction, anchoring once the step is small).  A column
+ * whose prediction leaves |V| in [0.7, 1.1] at any bus starts flat; fallback_out (host, may be
+ * NULL) receives how many did.  The iteration decides the result, so the outputs are those of
  * tpf_solve (Sec. III: the fixed point is reached from any nearby start).
  *
  *   hd, net      a feeder and a network for it (same n_pq, same device); the network's hidden
@@ -362,8 +363,9 @@ tpf_status tpf_mlp_predict(tpf_mlp *h, int64_t T, const void *S_dev, void *V0_de
  *                TPF_PREC_MIXED (TPF_EUNSUPPORTED otherwise); opts->start is ignored
  *
  * The columns go in equal chunks of at most 1,048,576; the network keeps a buffer for the
- * predictions of one chunk (4 bytes per bus and column: 2.1 GB for a one-minute year at 1,000 buses)
- * and one for the features of up to 131,072 columns.  tpf_last_stats(hd) reports the totals over the chunks.
+ * predictions of one chunk (4 bytes per bus and column: 2.1 GB for a one-minute year at 1,000
+ * buses).  S_dev must be 16-byte aligned (TPF_EINVAL otherwise).  tpf_last_stats(hd) reports the
+ * totals over the chunks.
  * Blocks until done.
  */
 tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void *S_dev, void *V_dev,

@@ -51,9 +51,7 @@ struct tpf_mlp {
     bool infer_fresh = false;
     bf16 *Wi0 = nullptr, *WiL = nullptr;   // [pad1][pad0] and [padL][pad(L-1)]
     float *bi_out = nullptr, *om_i = nullptr, *os_i = nullptr;  // [padL]
-    float *im_i = nullptr, *is_i = nullptr;                     // [pad0]
-    bf16 *Xi = nullptr;                    // interleaved features [xi_cap][pad0]
-    int64_t xi_cap = 0;
+    float4 *xn_i = nullptr;  // [pad0 / 2] per bus: 1 / sd_P, -mean_P / sd_P, 1 / sd_Q, -mean_Q / sd_Q
     __half2 *V0c = nullptr;                // predicted deviations (Re V - 1, Im V) of tpf_solve_learned
     int64_t v0_cap = 0;                    // complex values allocated in V0c
 };
@@ -302,12 +300,12 @@ __global__ void k_predict_out(const float *__restrict__ Y, int B, int P, int n, 
 
 // The inference copies: W_0 with its inputs interleaved (column 2j <- j, 2j + 1 <- n + j), W_{L-1},
 // its bias and the target statistics with their outputs interleaved (row 2i <- i, 2i + 1 <- n + i),
-// the feature statistics interleaved.  One thread per element of the largest of them.
+// and per bus the feature z-score as a scale and a shift (x = s * scale + shift; both zero where
+// the standard deviation is, as in the training features).  One thread per element of the largest.
 __global__ void k_infer_weights(const float *__restrict__ W0, const float *__restrict__ WL, const float *__restrict__ bL,
                                 const float *__restrict__ im, const float *__restrict__ is,
                                 const float *__restrict__ om, const float *__restrict__ os, int n, int P0, int H0,
-                                int PL, int HL, bf16 *Wi0, bf16 *WiL, float *bi, float *imi, float *isi, float *omi,
-                                float *osi) {
+                                int PL, int HL, bf16 *Wi0, bf16 *WiL, float *bi, float4 *xn, float *omi, float *osi) {
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     auto src = [n](int k) { return (k & 1) ? n + (k >> 1) : (k >> 1); };  // interleaved -> blocked index
     if (idx < (int64_t)H0 * P0) {  // W_0 [H0][P0]
@@ -324,31 +322,15 @@ __global__ void k_infer_weights(const float *__restrict__ W0, const float *__res
         omi[o] = o < 2 * n ? om[src(o)] : 0.0f;
         osi[o] = o < 2 * n ? os[src(o)] : 0.0f;
     }
-    if (idx < P0) {
-        const int k = (int)idx;
-        imi[k] = k < 2 * n ? im[src(k)] : 0.0f;
-        isi[k] = k < 2 * n ? is[src(k)] : 0.0f;
-    }
-}
-
-// Interleaved features of columns t0..t0+B-1 (rows beyond T are zero): X[b][2j] and X[b][2j+1] are
-// the z-scored P_j and Q_j (the same arithmetic as k_features), padding features are zero.  Thread
-// j of row b reads S_j once and writes both features as one 32-bit word.
-__global__ void k_features_il(const double2 *__restrict__ S, int64_t T, int64_t t0, int B, int n, int P0,
-                              const float *__restrict__ mean, const float *__restrict__ sd, bf16 *X) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= P0 / 2) return;
-    const float mr = j < n ? mean[2 * j] : 0.0f, dr = j < n ? sd[2 * j] : 0.0f;
-    const float mi = j < n ? mean[2 * j + 1] : 0.0f, di = j < n ? sd[2 * j + 1] : 0.0f;
-    for (int b = blockIdx.y; b < B; b += gridDim.y) {
-        const int64_t t = t0 + b;
-        float xr = 0.0f, xi = 0.0f;
-        if (j < n && t < T) {
-            const double2 s = S[t * n + j];
-            xr = dr > 0.0f ? ((float)s.x - mr) / dr : 0.0f;
-            xi = di > 0.0f ? ((float)s.y - mi) / di : 0.0f;
+    if (idx < P0 / 2) {
+        const int j = (int)idx;
+        float4 z = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (j < n) {
+            const float dp = is[j], dq = is[n + j];
+            if (dp > 0.0f) z.x = 1.0f / dp, z.y = -im[j] / dp;
+            if (dq > 0.0f) z.z = 1.0f / dq, z.w = -im[n + j] / dq;
         }
-        reinterpret_cast<__nv_bfloat162 *>(X)[(int64_t)b * (P0 / 2) + j] = __floats2bfloat162_rn(xr, xi);
+        xn[j] = z;
     }
 }
 
@@ -399,7 +381,7 @@ void free_mlp(tpf_mlp *h) {
     cudaFree(h->X0); cudaFree(h->X0T); cudaFree(h->dA); cudaFree(h->target); cudaFree(h->loss); cudaFree(h->err);
     cudaFree(h->fallback);
     cudaFree(h->Wi0); cudaFree(h->WiL); cudaFree(h->bi_out); cudaFree(h->om_i); cudaFree(h->os_i);
-    cudaFree(h->im_i); cudaFree(h->is_i); cudaFree(h->Xi); cudaFree(h->V0c);
+    cudaFree(h->xn_i); cudaFree(h->V0c);
     cudaGetLastError();
 }
 
@@ -506,45 +488,36 @@ bool fused_ok(const tpf_mlp *h) {
     return infer_supported(L, H, h->pad[0], h->pad[L]);
 }
 
-// Columns per fused-inference chunk (the interleaved feature buffer holds one chunk).
-constexpr int64_t kInferChunk = 131072;
-
-// Predicted V_0 of T columns with the fused kernel: complex128 (v0_64) or complex64 into V0; with
-// guard, a column whose prediction leaves the |V| band gets the flat start here (otherwise its
-// reader, the learned-start solve, checks the band).
+// Predicted V_0 of T columns with the fused kernel (one launch; it reads S itself): complex128
+// (v0_64) or complex64 into V0, or with v0_half the half-precision deviations (Re V - 1, Im V);
+// with guard, a column whose prediction leaves the |V| band gets the flat start here (otherwise
+// its reader, the learned-start solve, checks the band).  V0 holds pitch (default n) values per
+// column.
 tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_64, cudaStream_t st,
                        bool guard = true, int64_t pitch = 0, int64_t *launches = nullptr, bool v0_half = false) {
     const int L = h->L, H = h->pad[1], P0 = h->pad[0], PL = h->pad[L];
+    if (reinterpret_cast<uintptr_t>(S) % 16) return TPF_EINVAL;  // one 16-byte load per complex128 load
     if (!h->infer_fresh) {
         if (!h->Wi0 && !(dalloc(&h->Wi0, (size_t)H * P0) && dalloc(&h->WiL, (size_t)PL * h->pad[L - 1]) &&
                          dalloc(&h->bi_out, PL) && dalloc(&h->om_i, PL) && dalloc(&h->os_i, PL) &&
-                         dalloc(&h->im_i, P0) && dalloc(&h->is_i, P0)))
+                         dalloc(&h->xn_i, P0 / 2)))
             return TPF_ENOMEM;
         const int64_t work = std::max<int64_t>((int64_t)H * P0, (int64_t)PL * h->pad[L - 1]);
         k_infer_weights<<<blocks(work), kThreads, 0, st>>>(h->W[0], h->W[L - 1], h->b[L - 1], h->in_mean, h->in_std,
                                                            h->out_mean, h->out_std, h->n, P0, H, PL, h->pad[L - 1],
-                                                           h->Wi0, h->WiL, h->bi_out, h->im_i, h->is_i, h->om_i,
-                                                           h->os_i);
+                                                           h->Wi0, h->WiL, h->bi_out, h->xn_i, h->om_i, h->os_i);
         MLP_CK(cudaGetLastError());
         h->infer_fresh = true;
         if (launches) ++*launches;
     }
-    // Equal chunks of at most kInferChunk columns (whole tiles), so that no chunk is a small tail.
-    const int64_t n_ch = (T + kInferChunk - 1) / kInferChunk;
-    const int64_t chunk = round_up((T + n_ch - 1) / n_ch, 128);
-    const int64_t rows = chunk;
-    if (h->xi_cap < rows) {
-        cudaFree(h->Xi);
-        h->Xi = nullptr;
-        h->xi_cap = 0;
-        if (!dalloc(&h->Xi, (size_t)rows * P0)) return TPF_ENOMEM;
-        h->xi_cap = rows;
-    }
+    if (T <= 0) return TPF_OK;
     InferArgs g{};
     bool maps = make_bf16_map(&g.map_w[0], h->Wi0, P0, H) && make_bf16_map(&g.map_w[L - 1], h->WiL, H, PL);
     for (int l = 1; l < L - 1 && maps; ++l) maps = make_bf16_map(&g.map_w[l], h->Wb[l], H, H);
     if (!maps) return TPF_ECUDA;
     for (int l = 0; l < L - 1; ++l) g.bias[l] = h->b[l];
+    g.S = static_cast<const double2 *>(S);
+    g.xnorm = h->xn_i;
     g.bias_out = h->bi_out;
     g.out_mean = h->om_i;
     g.out_std = h->os_i;
@@ -561,21 +534,12 @@ tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_6
     g.pitch = pitch ? pitch : h->n;
     g.fallback = h->fallback;
     g.err = h->err;
-    const size_t vsz = v0_half ? sizeof(__half2) : (v0_64 ? sizeof(double2) : sizeof(float2));
-    for (int64_t t0 = 0; t0 < T; t0 += chunk) {
-        const int64_t Tc = std::min(chunk, T - t0);
-        k_features_il<<<grid2(P0 / 2, (int)Tc), kThreads, 0, st>>>((const double2 *)S, T, t0, (int)Tc, h->n, P0,
-                                                                  h->im_i, h->is_i, h->Xi);
-        MLP_CK(cudaGetLastError());
-        if (!make_bf16_map(&g.map_x, h->Xi, P0, Tc)) return TPF_ECUDA;
-        g.T = Tc;
-        g.tiles = (Tc + 127) / 128;
-        g.V0 = static_cast<char *>(V0) + (size_t)t0 * g.pitch * vsz;
-        tpf_status rs = launch_infer(g, st);
-        if (rs != TPF_OK) return rs;
-        if (launches) *launches += 2;  // features and the fused inference
-    }
-    return TPF_OK;
+    g.V0 = V0;
+    g.T = T;
+    g.tiles = (T + 127) / 128;
+    tpf_status rs = launch_infer(g, st);
+    if (rs == TPF_OK && launches) ++*launches;
+    return rs;
 }
 
 }  // namespace

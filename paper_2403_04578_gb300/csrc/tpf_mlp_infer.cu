@@ -9,13 +9,18 @@
 // permuted to match once per change of the parameters.
 //
 // Per CTA tile (M = 128 columns):
-//   layer 0       D = X W_0^T        A = X (TMA from the feature matrix), B = W_0 (TMA), K = P0
+//   layer 0       D = X W_0^T        A = X (written from S by the converter warps), B = W_0 (TMA), K = P0
 //   layers 1..    D = H W_l^T        A = H (shared memory), B = W_l (TMA), K = hidden
 //   last layer    D = W_L H^T        in M tiles of 128 outputs, A = rows of W_L (TMA), B = H
 // with the FP32 accumulator in TMEM (two stages of 256 columns).  The last layer is taken
 // transposed (outputs on the TMEM lanes, the tile's columns along TMEM), so that a warp's 32
 // threads hold 32 consecutive outputs of one column and its stores to V_0 are contiguous.  Warp 0
-// issues the TMA loads into a 3-slot ring, warp 1 the MMAs (one thread), 16 warps the epilogues:
+// issues the TMA loads of the weights into a 3-slot ring, warp 1 the MMAs (one thread); 8 converter
+// warps read the loads S of the tile's columns straight from the complex128 tensor, z-score them
+// and write the layer-0 operand (BF16, the 128-byte swizzled layout TMA would have written) into
+// a 3-slot ring of their own, so that the feature matrix never exists in memory (each ring has its
+// own full / empty barriers: a parity wait is exact only for a waiter that takes part in every
+// phase of its barrier); 8 warps run the epilogues:
 // bias and GELU (tanh form, half precision) of a hidden layer written as BF16 into the
 // shared-memory operand of the next layer
 // (128-byte swizzle, the layout TMA would have written), and for the last layer the
@@ -36,16 +41,19 @@ namespace {
 
 using namespace tc;
 
-constexpr int kEpiGroups = 4;  // epilogue warps per TMEM lane quarter
+constexpr int kEpiGroups = 2;  // epilogue warps per TMEM lane quarter
 constexpr int kEpiThreads = 128 * kEpiGroups;
-constexpr int kThreads = 64 + kEpiThreads;  // warp 0 TMA, warp 1 MMA, then the epilogue warps
+constexpr int kConvWarps = 8;  // feature converters: 16 rows of each layer-0 chunk per warp
+constexpr int kConvRows = 128 / kConvWarps;
+constexpr int kEpiWarp0 = 2 + kConvWarps;
+constexpr int kThreads = 64 + 32 * kConvWarps + kEpiThreads;  // TMA, MMA, converters, epilogues
 constexpr int kStages = 3;
 constexpr uint32_t kATile = 128 * 64 * 2;  // 16 KB: 128 rows x 64 BF16 (one K chunk of A)
 constexpr uint32_t kBMax = 256 * 64 * 2;   // 32 KB: up to 256 rows x 64 BF16 (one K chunk of B)
-constexpr uint32_t kStageBytes = kATile + kBMax;
+constexpr uint32_t kStageBytes = kBMax;    // weight ring slot: a K chunk of W_0 or W_l, or 128 rows of W_L
 constexpr uint32_t kHBytes = 128 * 256 * 2;  // hidden activations of the tile, 4 K chunks of 16 KB
 constexpr uint32_t kBiasBytes = (kMaxInferLayers - 1) * 256 * 4;  // hidden biases, staged once
-constexpr size_t kSmem = 1024 + kStages * kStageBytes + kHBytes + 1024 + kBiasBytes;
+constexpr size_t kSmem = 1024 + kStages * (kStageBytes + kATile) + kHBytes + 1024 + kBiasBytes;
 constexpr int kOutTile = 128;  // outputs per last-layer accumulator job
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
@@ -70,6 +78,16 @@ __device__ __forceinline__ uint32_t gelu_pair_bf16(float z0, float z1) {
     return pack_bf16(g.x, g.y);
 }
 
+// FP64 -> FP32 from the high word alone (sign, 11-bit exponent rebiased from 1023 to 127, the
+// top 20 mantissa bits; truncated), by the IEEE-754 field layout: plain integer arithmetic instead
+// of the FP64 pipe, exact enough for a feature rounded to BF16 (8 mantissa bits).  Magnitudes below
+// FP32's normal range flush to zero, those above it (and NaN) become infinity.
+__device__ __forceinline__ float f64_hi_to_f32(uint32_t hi) {
+    const uint32_t mag = min(hi & 0x7fffffffu, 0x47f00000u);
+    const uint32_t f = mag >= 0x38100000u ? (mag - 0x38000000u) << 3 : 0u;
+    return __uint_as_float(f | (hi & 0x80000000u));
+}
+
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
@@ -78,14 +96,17 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
     extern __shared__ uint8_t smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *Hs = smem + kStages * kStageBytes;
+    uint8_t *Xs = smem + kStages * kStageBytes;  // [kStages] layer-0 A tiles written by the converters
+    uint8_t *Hs = Xs + kStages * kATile;
     uint64_t *full = (uint64_t *)(Hs + kHBytes);  // [kStages] TMA -> MMA
     uint64_t *empty = full + kStages;              // [kStages] MMA -> TMA
     uint64_t *tfull = empty + kStages;             // [2] MMA -> epilogue
     uint64_t *tempty = tfull + 2;                  // [2] epilogue -> MMA
     uint64_t *hready = tempty + 2;                 // [1] epilogue -> MMA: the activations are written
     uint64_t *done = hready + 1;                   // [1] every MMA of this CTA retired
-    uint32_t *tmem_slot = (uint32_t *)(done + 1);
+    uint64_t *xfull = done + 1;                    // [kStages] converters -> MMA: a layer-0 A tile is written
+    uint64_t *xempty = xfull + kStages;            // [kStages] MMA -> converters
+    uint32_t *tmem_slot = (uint32_t *)(xempty + kStages);
     int *abort_flag = (int *)(tmem_slot + 1);
     float *s_bias = (float *)(Hs + kHBytes + 1024);  // [L-1][H] biases of the hidden layers
     __shared__ int s_fail;
@@ -104,6 +125,8 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
         for (int s = 0; s < kStages; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
             mbar_init(smem_u32(&empty[s]), 1);
+            mbar_init(smem_u32(&xfull[s]), kConvWarps);  // lane 0 of each converter warp
+            mbar_init(smem_u32(&xempty[s]), 1);
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&tfull[a]), 1);
@@ -138,15 +161,13 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
             return true;
         };
         for (int64_t tile = blockIdx.x; tile < g.tiles && !*vabort; tile += gridDim.x) {
-            const int row0 = (int)(tile * 128);
             bool ok = true;
-            for (int c = 0; c < k0 && ok; ++c, ++q) {  // layer 0: features and W_0
+            for (int c = 0; c < k0 && ok; ++c, ++q) {  // layer 0: W_0 (the converters write X)
                 uint32_t st;
                 if (!(ok = slot_ready(st))) break;
                 const uint32_t bar = smem_u32(&full[q % kStages]);
-                mbar_expect_tx(bar, kATile + (uint32_t)H * 128);
-                tma_load_2d(st, &g.map_x, bar, c * 64, row0);
-                for (int r = 0; r < H / 128; ++r) tma_load_2d(st + kATile + r * 16384, &g.map_w[0], bar, c * 64, r * 128);
+                mbar_expect_tx(bar, (uint32_t)H * 128);
+                for (int r = 0; r < H / 128; ++r) tma_load_2d(st + r * 16384, &g.map_w[0], bar, c * 64, r * 128);
             }
             for (int l = 1; l < L - 1 && ok; ++l)  // hidden layers: W_l
                 for (int c = 0; c < kh && ok; ++c, ++q) {
@@ -155,7 +176,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
                     const uint32_t bar = smem_u32(&full[q % kStages]);
                     mbar_expect_tx(bar, (uint32_t)H * 128);
                     for (int r = 0; r < H / 128; ++r)
-                        tma_load_2d(st + kATile + r * 16384, &g.map_w[l], bar, c * 64, r * 128);
+                        tma_load_2d(st + r * 16384, &g.map_w[l], bar, c * 64, r * 128);
                 }
             for (int nt = 0; nt < n_out && ok; ++nt)  // last layer: 128 output rows of W_L at a time
                 for (int c = 0; c < kh && ok; ++c, ++q) {
@@ -173,15 +194,16 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        const uint32_t sbase = smem_u32(smem), hbase = smem_u32(Hs);
+        const uint32_t sbase = smem_u32(smem), xbase = smem_u32(Xs), hbase = smem_u32(Hs);
         const uint32_t id_hidden = idesc_f16(128, H, 0, 1), id_out = idesc_f16(128, kOutTile, 0, 1);
         int64_t q = 0;   // chunks consumed
         uint32_t jq = 0; // accumulator jobs
         uint32_t hq = 0; // activation tiles waited for
+        uint32_t xq = 0; // layer-0 A tiles consumed
         bool ok = true;
         // One accumulator job: wait for the stage, optionally for fresh activations, then n_k chunks.
         // from_h: A = the activations, B = the ring's weights; out: A = the ring's weights, B = the
-        // activations (the transposed last layer).
+        // activations (the transposed last layer); otherwise layer 0: A = the converters' features.
         auto job = [&](int n_k, bool from_h, bool wait_h, uint32_t idesc, bool out = false) -> bool {
             const uint32_t a = jq & 1, u = jq >> 1;
             if (!mbar_wait(smem_u32(&tempty[a]), (u & 1) ^ 1)) return false;
@@ -194,14 +216,21 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
             for (int c = 0; c < n_k; ++c, ++q) {
                 const int slot = (int)(q % kStages);
                 if (!mbar_wait(smem_u32(&full[slot]), (uint32_t)(q / kStages) & 1)) return false;
+                const bool x_in = !from_h && !out;
+                const uint32_t xslot = xq % kStages;
+                if (x_in && !mbar_wait(smem_u32(&xfull[xslot]), (xq / kStages) & 1)) return false;
                 tc_fence_after();
                 const uint32_t st = sbase + slot * kStageBytes;
-                const uint32_t abase = out ? st : (from_h ? hbase + c * kATile : st);
-                const uint32_t bbase = out ? hbase + c * kATile : st + kATile;
+                const uint32_t abase = out ? st : (from_h ? hbase + c * kATile : xbase + xslot * kATile);
+                const uint32_t bbase = out ? hbase + c * kATile : st;
 #pragma unroll
                 for (int kk = 0; kk < 4; ++kk)
                     umma_f16(acc, sw128_desc(abase + kk * 32), sw128_desc(bbase + kk * 32), idesc, (c | kk) != 0);
                 umma_commit(smem_u32(&empty[slot]));
+                if (x_in) {
+                    umma_commit(smem_u32(&xempty[xslot]));
+                    ++xq;
+                }
             }
             umma_commit(smem_u32(&tfull[a]));
             ++jq;
@@ -218,15 +247,70 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
         }
         umma_commit(smem_u32(done));
         mbar_wait(smem_u32(done), 0);  // every MMA of this CTA has retired (bounded)
-    } else if (warp >= 2) {
+    } else if (warp >= 2 && warp < kEpiWarp0) {
+        // ---------------- feature converters ----------------
+        // Layer-0 chunk c of a tile is features 64 c .. 64 c + 63 = buses 32 c .. 32 c + 31, (P, Q)
+        // interleaved.  Lane l takes bus 32 c + l; warp w rows (columns t) 16 w .. 16 w + 15, one
+        // coalesced 512-byte load of S per row.  The chunk's loads go out in two halves of 8 rows,
+        // each half of the next chunk issued as soon as this chunk's half is converted, so that
+        // one to two halves per warp stay in flight.
+        const int cw = warp - 2;
+        const int64_t my_tiles = g.tiles > blockIdx.x ? (g.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        const int64_t steps = my_tiles * k0;
+        const uint8_t *Sb = reinterpret_cast<const uint8_t *>(g.S);
+        auto load_half = [&](uint4 (&v)[8], int64_t s, int half) {
+            const int64_t tile = blockIdx.x + (s / k0) * gridDim.x;
+            const int j = (int)(s % k0) * 32 + lane;
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int64_t t = tile * 128 + cw * kConvRows + half * 8 + i;
+                v[i] = (j < g.n && t < g.T) ? __ldg(reinterpret_cast<const uint4 *>(Sb + (t * g.n + j) * 16))
+                                            : make_uint4(0u, 0u, 0u, 0u);
+            }
+        };
+        auto store_half = [&](const uint4 (&v)[8], uint8_t *a, float4 nm, int half) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int r = cw * kConvRows + half * 8 + i;
+                const float xr = fmaf(f64_hi_to_f32(v[i].y), nm.x, nm.y);
+                const float xi = fmaf(f64_hi_to_f32(v[i].w), nm.z, nm.w);
+                *reinterpret_cast<uint32_t *>(a + (r >> 3) * 1024 + (r & 7) * 128 + (((lane >> 2) ^ (r & 7)) << 4) +
+                                              ((lane & 3) << 2)) = pack_bf16(xr, xi);
+            }
+        };
+        uint4 va[8], vb[8];
+        if (steps > 0) {
+            load_half(va, 0, 0);
+            load_half(vb, 0, 1);
+        }
+        for (int64_t s = 0; s < steps; ++s) {  // s: this A tile's place in the converters' ring
+            const int c = (int)(s % k0);
+            const int slot = (int)(s % kStages);
+            const int j = c * 32 + lane;
+            const float4 nm = j < g.n ? __ldg(g.xnorm + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (*vabort || !mbar_wait(smem_u32(&xempty[slot]), ((uint32_t)(s / kStages) & 1) ^ 1)) {
+                *vabort = 1;
+                atomicExch(g.err, 1);
+                break;
+            }
+            uint8_t *a = Xs + slot * kATile;
+            store_half(va, a, nm, 0);
+            if (s + 1 < steps) load_half(va, s + 1, 0);
+            store_half(vb, a, nm, 1);
+            if (s + 1 < steps) load_half(vb, s + 1, 1);
+            fence_async_smem();  // the MMAs (async proxy) read this tile next
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&xfull[slot]));
+        }
+    } else if (warp >= kEpiWarp0) {
         // ---------------- epilogue: kEpiGroups warps per TMEM lane quarter ----------------
         // Hidden layers: thread = column row of the tile, `part` splits the units.  Last layer:
         // thread = output row of the accumulator, `part` splits the tile's columns.
         const int quarter = warp & 3;  // TMEM lanes this warp may access
-        const int part = (warp - 2) >> 2;
+        const int part = (warp - kEpiWarp0) >> 2;
         const int row = quarter * 32 + lane;
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
-        const int et = tid - 64;
+        const int et = tid - 32 * kEpiWarp0;
         // This row's 128-byte line inside each 16 KB K chunk of the activations (SW128 layout).
         uint8_t *hrow = Hs + (row >> 3) * 1024 + (row & 7) * 128;
         const int hp = H / 32 / kEpiGroups;  // pieces of 32 units per part

@@ -10,10 +10,12 @@ namespace tpf {
 constexpr int kMaxInferLayers = 8;  // weight layers the fused kernel takes (up to 7 hidden layers)
 
 struct InferArgs {
-    CUtensorMap map_x;                      // features [rows][P0] BF16, interleaved (P_1, Q_1, ...), box 64 x 128
     CUtensorMap map_w[kMaxInferLayers];     // W_l [out][in] BF16, box 64 x 128: W_0 with interleaved inputs,
                                             // W_{L-1} with interleaved output rows
     const float *bias[kMaxInferLayers];     // FP32 biases of the hidden layers
+    const double2 *S;                       // [T][n] complex128 loads of the columns (16-byte aligned)
+    const float4 *xnorm;                    // [P0 / 2] per bus: 1 / sd_P, -mean_P / sd_P, 1 / sd_Q, -mean_Q / sd_Q
+                                            // (zero for padding buses and constant features)
     const float *bias_out;                  // [PL] last layer's bias, interleaved
     const float *out_mean, *out_std;        // [PL] target statistics, interleaved
     int L, H, P0, PL, n;                    // weight layers, hidden width (128 or 256), padded widths, buses

@@ -25,9 +25,9 @@ def test_bench_line_keys(cuda):
               "vs_baseline", "dtype", "data", "config", "roofline", "cpu_baseline", "e2e", "clocks", "gpu_launches"):
         assert k in d, k
     assert d["value"] > 0 and d["n_gpus"] == 1 and d["steps"] == 3 and d["warmup"] == 3
-    # The headline step is the learned-start solve: features, fused inference and one sparse launch
-    # (4,096 columns: one prediction chunk).
-    assert d["headline_start"] == "learned" and d["gpu_launches"] == 9
+    # The headline step is the learned-start solve: the fused inference (it reads S itself) and one
+    # sparse launch.
+    assert d["headline_start"] == "learned" and d["gpu_launches"] == 6
     assert d["flat_start"]["gpu_launches"] == 3  # one sparse launch per step
     lh = d["learned_start_headline"]
     assert lh["fallback_columns"] == 0 and lh["converged"] == 4096 and lh["mean_sweeps"] < d["flat_start"]["mean_sweeps"]

@@ -253,6 +253,45 @@ def test_fused_prediction_matches_the_fp64_reference(cuda, feeder200, hidden, la
     net.close()
 
 
+def test_fused_prediction_with_several_tiles_per_cta(cuda, feeder200):
+    """More 128-column tiles than SMs: each persistent CTA takes several tiles in turn and the rings
+    of the weights and of the converted features wrap many times.  Every column's prediction equals
+    the one computed in a launch with one tile per CTA (a column's outputs depend on its own row of
+    the products only, so the two agree bit for bit), and sampled columns match the FP64 network."""
+    import torch
+
+    f, c = feeder200
+    S_fit = G.load_tensor(f, 4096, 9)
+    V_fit, _, _ = c.solve(S_fit, tol=1e-12)
+    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=128, seed=5)
+    net.fit_normalization(_dev(S_fit), _dev(V_fit))
+    xm, xs, ym, ys = (np.asarray(a, dtype=np.float64) for a in net.normalization())
+    rng = np.random.default_rng(17)
+    sizes = net.sizes
+    Ws = [rng.uniform(-1, 1, (sizes[i + 1], sizes[i])) * np.sqrt(6.0 / (sizes[i] + sizes[i + 1]))
+          for i in range(len(sizes) - 1)]
+    bs = [rng.normal(0, 0.05, sizes[i + 1]) for i in range(len(sizes) - 1)]
+    Ws[-1] *= 0.05
+    net.set_params(np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(Ws, bs)]).astype(np.float32))
+    T = 48_037  # 376 tiles over at most 152 CTAs, the last one ragged
+    S = G.load_tensor(f, T, 10)
+    Sd = _dev(S)
+    V0, fallback = net.predict(Sd)
+    assert fallback == 0
+    for k in (0, 128 * 151 + 5, T - 2000):
+        part, fb = net.predict(Sd[k:k + 2000])  # 16 tiles: one per CTA
+        assert fb == 0 and torch.equal(part, V0[k:k + 2000]), k
+    idx = np.sort(rng.choice(T, 512, replace=False))
+    ref = OM.MLP([w.astype(np.float32).astype(np.float64) for w in Ws], [b.astype(np.float32) for b in bs])
+    y_ref, _ = ref.forward(_norm(_features(S[idx]), xm, xs))
+    V0s = V0.cpu().numpy()[idx]
+    ok = ys > 0
+    y_gpu = (np.concatenate([V0s.real - 1.0, V0s.imag], axis=1)[:, ok] - ym[ok]) / ys[ok]
+    rel = np.linalg.norm(y_gpu - y_ref[:, ok]) / np.linalg.norm(y_ref[:, ok])
+    assert rel <= 2e-2, rel
+    net.close()
+
+
 def test_learned_solve_matches_the_oracle(cuda, feeder200):
     """tpf_solve_learned (fused prediction into complex64 starting voltages, then the sparse mixed
     solve from them): the oracle's solution within 1e-8 pu, fewer sweeps than the flat start, no

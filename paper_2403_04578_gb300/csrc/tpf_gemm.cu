@@ -346,6 +346,19 @@ bool make_bf16_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t 
     return make_map(map, base, inner, rows, true);
 }
 
+bool make_f64_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint32_t box_inner,
+                  uint32_t box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return false;
+    cuuint64_t dims[2] = {inner, rows};
+    cuuint64_t strides[1] = {inner * 8};
+    cuuint32_t box[2] = {box_inner, box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<void *>(base), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 bool make_gemm_maps(GemmMaps *maps, const void *Ar, const void *Ai, int M, int K, const void *Br, const void *Bi,
                     int64_t N, bool bf16) {
     std::memset(maps, 0, sizeof(*maps));

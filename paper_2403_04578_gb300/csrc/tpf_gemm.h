@@ -43,6 +43,10 @@ struct GemmMaps {
 
 // A [rows][inner] BF16 matrix read in (128 rows x 64 elements) boxes with the 128-byte swizzle.
 bool make_bf16_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows);
+// A [rows][inner] FP64 matrix (row stride inner * 8 bytes, a multiple of 16) read in unswizzled
+// (box_rows x box_inner) boxes; elements outside the matrix read as zero.
+bool make_f64_map(CUtensorMap *map, const void *base, uint64_t inner, uint64_t rows, uint32_t box_inner,
+                  uint32_t box_rows);
 
 // Ai, Bi may be null for a real product.  bf16 selects the element type of the maps.
 bool make_gemm_maps(GemmMaps *maps, const void *Ar, const void *Ai, int M, int K, const void *Br, const void *Bi,

@@ -496,7 +496,8 @@ bool fused_ok(const tpf_mlp *h) {
 tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_64, cudaStream_t st,
                        bool guard = true, int64_t pitch = 0, int64_t *launches = nullptr, bool v0_half = false) {
     const int L = h->L, H = h->pad[1], P0 = h->pad[0], PL = h->pad[L];
-    if (reinterpret_cast<uintptr_t>(S) % 16) return TPF_EINVAL;  // one 16-byte load per complex128 load
+    // S is read by TMA: a 16-byte aligned base, and column indices within its 32-bit coordinates.
+    if (reinterpret_cast<uintptr_t>(S) % 16 || T > ((int64_t)1 << 31) - 256) return TPF_EINVAL;
     if (!h->infer_fresh) {
         if (!h->Wi0 && !(dalloc(&h->Wi0, (size_t)H * P0) && dalloc(&h->WiL, (size_t)PL * h->pad[L - 1]) &&
                          dalloc(&h->bi_out, PL) && dalloc(&h->om_i, PL) && dalloc(&h->os_i, PL) &&
@@ -516,7 +517,7 @@ tpf_status infer_fused(tpf_mlp *h, int64_t T, const void *S, void *V0, bool v0_6
     for (int l = 1; l < L - 1 && maps; ++l) maps = make_bf16_map(&g.map_w[l], h->Wb[l], H, H);
     if (!maps) return TPF_ECUDA;
     for (int l = 0; l < L - 1; ++l) g.bias[l] = h->b[l];
-    g.S = static_cast<const double2 *>(S);
+    if (!make_f64_map(&g.map_s, S, 2 * (uint64_t)h->n, (uint64_t)T, 64, 32)) return TPF_ECUDA;
     g.xnorm = h->xn_i;
     g.bias_out = h->bi_out;
     g.out_mean = h->om_i;

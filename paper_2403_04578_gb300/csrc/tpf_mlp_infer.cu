@@ -9,23 +9,26 @@
 // permuted to match once per change of the parameters.
 //
 // Per CTA tile (M = 128 columns):
-//   layer 0       D = X W_0^T        A = X (written from S by the converter warps), B = W_0 (TMA), K = P0
+//   layer 0       D = X W_0^T        A = X (converted from S on chip), B = W_0 (TMA), K = P0
 //   layers 1..    D = H W_l^T        A = H (shared memory), B = W_l (TMA), K = hidden
 //   last layer    D = W_L H^T        in M tiles of 128 outputs, A = rows of W_L (TMA), B = H
-// with the FP32 accumulator in TMEM (two stages of 256 columns).  The last layer is taken
-// transposed (outputs on the TMEM lanes, the tile's columns along TMEM), so that a warp's 32
-// threads hold 32 consecutive outputs of one column and its stores to V_0 are contiguous.  Warp 0
-// issues the TMA loads of the weights into a 3-slot ring, warp 1 the MMAs (one thread); 8 converter
-// warps read the loads S of the tile's columns straight from the complex128 tensor, z-score them
-// and write the layer-0 operand (BF16, the 128-byte swizzled layout TMA would have written) into
-// a 3-slot ring of their own, so that the feature matrix never exists in memory (each ring has its
-// own full / empty barriers: a parity wait is exact only for a waiter that takes part in every
-// phase of its barrier); 8 warps run the epilogues:
-// bias and GELU (tanh form, half precision) of a hidden layer written as BF16 into the
-// shared-memory operand of the next layer
-// (128-byte swizzle, the layout TMA would have written), and for the last layer the
-// denormalisation into V_0 with the |V| guard.  Every wait is bounded; on expiry the CTA flags the
-// error, drains its own copies and MMAs, frees TMEM and returns.
+// with FP32 accumulators in TMEM: layer 0 in columns 0..255, the hidden layers in 256..511, the
+// last layer's jobs in alternating halves of 256..511.  The last layer is taken transposed
+// (outputs on the TMEM lanes, the tile's columns along TMEM), so that a warp's 32 threads hold 32
+// consecutive outputs of one column and its stores to V_0 are contiguous.
+//
+// Warps: 0 issues the TMA loads of the weights into a ring of 16 KB slots (128 rows x 64 BF16;
+// a 256-row operand takes two slots and two N = 128 MMAs); 1 issues the MMAs (one thread); 2
+// issues the TMA loads of the loads S themselves (complex128 read as FP64 pairs, boxes of 32
+// columns x 32 buses) into a staging ring; 3-10 convert the staged loads into the layer-0 operand
+// (z-scored, BF16, in the 128-byte swizzled layout TMA would have written) in a ring of their own,
+// so that no feature matrix exists in memory; 11-18 run the epilogues: bias and GELU (tanh form,
+// half precision) of a hidden layer written as BF16 into the shared-memory operand of the next
+// layer, and for the last layer the denormalisation into V_0 with the |V| guard.  The next
+// tile's layer-0 chunks are issued between this tile's hidden and output jobs, so that reading S
+// overlaps the output epilogue.  Each ring has its own full / empty barriers (a parity wait is
+// exact only for a waiter that takes part in every phase of its barrier).  Every wait is bounded;
+// on expiry the CTA flags the error, drains its own copies and MMAs, frees TMEM and returns.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -43,18 +46,22 @@ using namespace tc;
 
 constexpr int kEpiGroups = 2;  // epilogue warps per TMEM lane quarter
 constexpr int kEpiThreads = 128 * kEpiGroups;
-constexpr int kConvWarps = 8;  // feature converters: 16 rows of each layer-0 chunk per warp
-constexpr int kConvRows = 128 / kConvWarps;
-constexpr int kEpiWarp0 = 2 + kConvWarps;
-constexpr int kThreads = 64 + 32 * kConvWarps + kEpiThreads;  // TMA, MMA, converters, epilogues
-constexpr int kStages = 3;
-constexpr uint32_t kATile = 128 * 64 * 2;  // 16 KB: 128 rows x 64 BF16 (one K chunk of A)
-constexpr uint32_t kBMax = 256 * 64 * 2;   // 32 KB: up to 256 rows x 64 BF16 (one K chunk of B)
-constexpr uint32_t kStageBytes = kBMax;    // weight ring slot: a K chunk of W_0 or W_l, or 128 rows of W_L
-constexpr uint32_t kHBytes = 128 * 256 * 2;  // hidden activations of the tile, 4 K chunks of 16 KB
-constexpr uint32_t kBiasBytes = (kMaxInferLayers - 1) * 256 * 4;  // hidden biases, staged once
-constexpr size_t kSmem = 1024 + kStages * (kStageBytes + kATile) + kHBytes + 1024 + kBiasBytes;
+constexpr int kConvWarps = 8;                      // feature converters
+constexpr int kSRows = 32;                         // columns (rows of S) per staged box
+constexpr int kConvRows = kSRows / kConvWarps;     // rows of a box per converter warp
+constexpr int kBoxes = 128 / kSRows;               // staged boxes per layer-0 chunk
+constexpr int kConvWarp0 = 3;
+constexpr int kEpiWarp0 = kConvWarp0 + kConvWarps;
+constexpr int kThreads = 32 * kEpiWarp0 + kEpiThreads;  // TMA W, MMA, TMA S, converters, epilogues
+constexpr int kWSlots = 4;                         // weight ring: 16 KB slots
+constexpr int kXSlots = 2;                         // layer-0 operand ring: 16 KB slots
+constexpr int kSSlots = 4;                         // staged S: 16 KB slots
+constexpr uint32_t kSlot = 128 * 64 * 2;           // 16 KB: 128 rows x 64 BF16 (one K chunk of 128 rows)
+constexpr uint32_t kSBox = kSRows * 32 * 16;       // 16 KB: 32 columns x 32 complex128 loads
+constexpr uint32_t kHBytes = 128 * 256 * 2;        // hidden activations of the tile, 4 K chunks of 16 KB
+constexpr size_t kSmem = 1024 + (kWSlots + kXSlots) * kSlot + kSSlots * kSBox + kHBytes + 1024;
 constexpr int kOutTile = 128;  // outputs per last-layer accumulator job
+static_assert(kSmem <= 232448, "shared memory");
 
 __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
@@ -88,32 +95,44 @@ __device__ __forceinline__ float f64_hi_to_f32(uint32_t hi) {
     return __uint_as_float(f | (hi & 0x80000000u));
 }
 
+// The next tile's layer-0 chunks that go after job jj of this tile's J jobs: spread evenly over
+// the jobs, the last one after the last job.
+__device__ __forceinline__ int l0_target(int jj, int J, int k0) {
+    return jj + 1 >= J ? k0 : min(k0 - 1, (jj + 1) * k0 / J);
+}
+
 __device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-
 
 __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__ InferArgs g) {
     extern __shared__ uint8_t smem_raw[];
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    uint8_t *Xs = smem + kStages * kStageBytes;  // [kStages] layer-0 A tiles written by the converters
-    uint8_t *Hs = Xs + kStages * kATile;
-    uint64_t *full = (uint64_t *)(Hs + kHBytes);  // [kStages] TMA -> MMA
-    uint64_t *empty = full + kStages;              // [kStages] MMA -> TMA
-    uint64_t *tfull = empty + kStages;             // [2] MMA -> epilogue
-    uint64_t *tempty = tfull + 2;                  // [2] epilogue -> MMA
-    uint64_t *hready = tempty + 2;                 // [1] epilogue -> MMA: the activations are written
+    uint8_t *Ws = smem;                    // [kWSlots] weight boxes (TMA)
+    uint8_t *Xs = Ws + kWSlots * kSlot;    // [kXSlots] layer-0 A tiles (converters)
+    uint8_t *Ss = Xs + kXSlots * kSlot;    // [kSSlots] staged boxes of S (TMA)
+    uint8_t *Hs = Ss + kSSlots * kSBox;    // activations of the tile
+    uint64_t *wfull = (uint64_t *)(Hs + kHBytes);  // [kWSlots] TMA -> MMA
+    uint64_t *wempty = wfull + kWSlots;            // [kWSlots] MMA -> TMA
+    uint64_t *xfull = wempty + kWSlots;            // [kXSlots] converters -> MMA
+    uint64_t *xempty = xfull + kXSlots;            // [kXSlots] MMA -> converters
+    uint64_t *sfull = xempty + kXSlots;            // [kSSlots] TMA -> converters
+    uint64_t *sempty = sfull + kSSlots;            // [kSSlots] converters -> TMA
+    // Accumulators in TMEM: columns 0..255 take layer 0 (region 1); columns 256..511 (region 2)
+    // take the hidden layers (both halves) and the last layer's jobs (alternating halves of 128).
+    uint64_t *tfull1 = sempty + kSSlots;           // [1] MMA -> epilogue: layer 0 accumulated
+    uint64_t *tempty1 = tfull1 + 1;                // [1] epilogue -> MMA: region 1 read
+    uint64_t *tfull2 = tempty1 + 1;                // [2] per half of region 2
+    uint64_t *tempty2 = tfull2 + 2;                // [2]
+    uint64_t *hready = tempty2 + 2;                // [1] epilogue -> MMA: the activations are written
     uint64_t *done = hready + 1;                   // [1] every MMA of this CTA retired
-    uint64_t *xfull = done + 1;                    // [kStages] converters -> MMA: a layer-0 A tile is written
-    uint64_t *xempty = xfull + kStages;            // [kStages] MMA -> converters
-    uint32_t *tmem_slot = (uint32_t *)(xempty + kStages);
+    uint32_t *tmem_slot = (uint32_t *)(done + 1);
     int *abort_flag = (int *)(tmem_slot + 1);
-    float *s_bias = (float *)(Hs + kHBytes + 1024);  // [L-1][H] biases of the hidden layers
     __shared__ int s_fail;
     __shared__ unsigned s_badm[4];  // bit c: column c of the tile left the guard band somewhere
 
     const int L = g.L, H = g.H;
-    const int k0 = g.P0 / 64, kh = H / 64, n_out = g.PL / kOutTile;
+    const int k0 = g.P0 / 64, kh = H / 64, n_out = g.PL / kOutTile, hr = H / 128;
     constexpr uint32_t kTmemCols = 512;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -122,15 +141,23 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (tid == 0) {
-        for (int s = 0; s < kStages; ++s) {
-            mbar_init(smem_u32(&full[s]), 1);
-            mbar_init(smem_u32(&empty[s]), 1);
+        for (int s = 0; s < kWSlots; ++s) {
+            mbar_init(smem_u32(&wfull[s]), 1);
+            mbar_init(smem_u32(&wempty[s]), 1);
+        }
+        for (int s = 0; s < kXSlots; ++s) {
             mbar_init(smem_u32(&xfull[s]), kConvWarps);  // lane 0 of each converter warp
             mbar_init(smem_u32(&xempty[s]), 1);
         }
+        for (int s = 0; s < kSSlots; ++s) {
+            mbar_init(smem_u32(&sfull[s]), 1);
+            mbar_init(smem_u32(&sempty[s]), kConvWarps);
+        }
+        mbar_init(smem_u32(tfull1), 1);
+        mbar_init(smem_u32(tempty1), kEpiThreads / 32);  // lane 0 of each epilogue warp
         for (int a = 0; a < 2; ++a) {
-            mbar_init(smem_u32(&tfull[a]), 1);
-            mbar_init(smem_u32(&tempty[a]), kEpiThreads / 32);  // lane 0 of each epilogue warp
+            mbar_init(smem_u32(&tfull2[a]), 1);
+            mbar_init(smem_u32(&tempty2[a]), kEpiThreads / 32);
         }
         mbar_init(smem_u32(hready), 1);
         mbar_init(smem_u32(done), 1);
@@ -139,168 +166,243 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
         for (int c = 0; c < 4; ++c) s_badm[c] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int k = tid; k < (L - 1) * H; k += blockDim.x) s_bias[k] = __ldg(g.bias[k / H] + k % H);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
     volatile int *vabort = abort_flag;
+    // This CTA's tiles, and the jobs of one tile after its layer 0: the hidden layers, then the
+    // last layer's output tiles.
+    const int64_t my_tiles = g.tiles > blockIdx.x ? (g.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int J = (L - 2) + n_out;
+    auto fail = [&]() {
+        *vabort = 1;
+        atomicExch(g.err, 1);
+    };
 
     if (warp == 0 && lane == 0) {
-        // ---------------- TMA producer: the operand chunks of every job, in job order ----------------
-        const uint32_t sbase = smem_u32(smem);
-        int64_t q = 0;  // chunks issued by this CTA
-        auto slot_ready = [&](uint32_t &st) -> bool {
-            const int slot = (int)(q % kStages);
-            if (!mbar_wait(smem_u32(&empty[slot]), ((uint32_t)(q / kStages) & 1) ^ 1)) {
-                *vabort = 1;
-                atomicExch(g.err, 1);
+        // ---------------- TMA producer of the weights, in the MMA's order ----------------
+        // One 16 KB box per ring slot: 128 rows x one K chunk of 64.
+        const uint32_t wbase = smem_u32(Ws);
+        int64_t q = 0;  // boxes issued by this CTA
+        auto box = [&](const CUtensorMap *map, int x, int y) -> bool {
+            const int slot = (int)(q % kWSlots);
+            if (!mbar_wait(smem_u32(&wempty[slot]), ((uint32_t)(q / kWSlots) & 1) ^ 1)) {
+                fail();
                 return false;
             }
-            st = sbase + slot * kStageBytes;
+            const uint32_t bar = smem_u32(&wfull[slot]);
+            mbar_expect_tx(bar, kSlot);
+            tma_load_2d(wbase + slot * kSlot, map, bar, x, y);
+            ++q;
             return true;
         };
-        for (int64_t tile = blockIdx.x; tile < g.tiles && !*vabort; tile += gridDim.x) {
-            bool ok = true;
-            for (int c = 0; c < k0 && ok; ++c, ++q) {  // layer 0: W_0 (the converters write X)
-                uint32_t st;
-                if (!(ok = slot_ready(st))) break;
-                const uint32_t bar = smem_u32(&full[q % kStages]);
-                mbar_expect_tx(bar, (uint32_t)H * 128);
-                for (int r = 0; r < H / 128; ++r) tma_load_2d(st + r * 16384, &g.map_w[0], bar, c * 64, r * 128);
+        auto w0_chunk = [&](int c) -> bool {  // layer 0: K chunk c of W_0, H / 128 boxes
+            for (int r = 0; r < hr; ++r)
+                if (!box(&g.map_w[0], c * 64, r * 128)) return false;
+            return true;
+        };
+        auto job_chunks = [&](int jj) -> bool {
+            for (int c = 0; c < kh; ++c) {
+                if (jj < L - 2) {  // hidden layer jj + 1: K chunk c of W_l
+                    for (int r = 0; r < hr; ++r)
+                        if (!box(&g.map_w[jj + 1], c * 64, r * 128)) return false;
+                } else if (!box(&g.map_w[L - 1], c * 64, (jj - (L - 2)) * kOutTile)) {  // 128 rows of W_L
+                    return false;
+                }
             }
-            for (int l = 1; l < L - 1 && ok; ++l)  // hidden layers: W_l
-                for (int c = 0; c < kh && ok; ++c, ++q) {
-                    uint32_t st;
-                    if (!(ok = slot_ready(st))) break;
-                    const uint32_t bar = smem_u32(&full[q % kStages]);
-                    mbar_expect_tx(bar, (uint32_t)H * 128);
-                    for (int r = 0; r < H / 128; ++r)
-                        tma_load_2d(st + r * 16384, &g.map_w[l], bar, c * 64, r * 128);
-                }
-            for (int nt = 0; nt < n_out && ok; ++nt)  // last layer: 128 output rows of W_L at a time
-                for (int c = 0; c < kh && ok; ++c, ++q) {
-                    uint32_t st;
-                    if (!(ok = slot_ready(st))) break;
-                    const uint32_t bar = smem_u32(&full[q % kStages]);
-                    mbar_expect_tx(bar, 16384);
-                    tma_load_2d(st, &g.map_w[L - 1], bar, c * 64, nt * kOutTile);
-                }
-            if (!ok) break;
+            return true;
+        };
+        bool ok = true;
+        for (int c = 0; c < k0 && ok && my_tiles > 0; ++c) ok = w0_chunk(c);
+        for (int64_t it = 0; it < my_tiles && ok && !*vabort; ++it) {
+            const bool next = it + 1 < my_tiles;
+            int cn = 0;  // the next tile's layer-0 chunks issued so far
+            for (int jj = 0; jj < J && ok; ++jj) {
+                ok = job_chunks(jj);
+                for (const int tgt = next ? l0_target(jj, J, k0) : 0; cn < tgt && ok; ++cn) ok = w0_chunk(cn);
+            }
         }
         if (*vabort) {  // the copies in flight land before the CTA leaves (bounded)
-            for (int64_t r = q - 1; r >= 0 && r >= q - kStages; --r)
-                mbar_wait(smem_u32(&full[r % kStages]), (uint32_t)(r / kStages) & 1);
+            for (int64_t r = q - 1; r >= 0 && r >= q - kWSlots; --r)
+                mbar_wait(smem_u32(&wfull[r % kWSlots]), (uint32_t)(r / kWSlots) & 1);
+        }
+    } else if (warp == 2 && lane == 0) {
+        // ---------------- TMA producer of the loads S ----------------
+        // Per tile and layer-0 chunk c: kBoxes boxes of 32 columns x 32 buses (64 FP64 values:
+        // P, Q of buses 32 c .. 32 c + 31); buses beyond n and columns beyond T read as zero.
+        const uint32_t sbase = smem_u32(Ss);
+        int64_t k = 0;  // boxes issued
+        bool ok = true;
+        for (int64_t it = 0; it < my_tiles && ok && !*vabort; ++it) {
+            const int64_t tile = blockIdx.x + it * gridDim.x;
+            for (int c = 0; c < k0 && ok; ++c)
+                for (int b = 0; b < kBoxes; ++b, ++k) {
+                    const int slot = (int)(k % kSSlots);
+                    if (!mbar_wait(smem_u32(&sempty[slot]), ((uint32_t)(k / kSSlots) & 1) ^ 1)) {
+                        fail();
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t bar = smem_u32(&sfull[slot]);
+                    mbar_expect_tx(bar, kSBox);
+                    tma_load_2d(sbase + slot * kSBox, &g.map_s, bar, c * 64, (int)(tile * 128 + b * kSRows));
+                }
+        }
+        if (*vabort) {
+            for (int64_t r = k - 1; r >= 0 && r >= k - kSSlots; --r)
+                mbar_wait(smem_u32(&sfull[r % kSSlots]), (uint32_t)(r / kSSlots) & 1);
         }
     } else if (warp == 1 && lane == 0) {
         // ---------------- MMA issuer ----------------
-        const uint32_t sbase = smem_u32(smem), xbase = smem_u32(Xs), hbase = smem_u32(Hs);
-        const uint32_t id_hidden = idesc_f16(128, H, 0, 1), id_out = idesc_f16(128, kOutTile, 0, 1);
-        int64_t q = 0;   // chunks consumed
-        uint32_t jq = 0; // accumulator jobs
-        uint32_t hq = 0; // activation tiles waited for
-        uint32_t xq = 0; // layer-0 A tiles consumed
-        bool ok = true;
-        // One accumulator job: wait for the stage, optionally for fresh activations, then n_k chunks.
-        // from_h: A = the activations, B = the ring's weights; out: A = the ring's weights, B = the
-        // activations (the transposed last layer); otherwise layer 0: A = the converters' features.
-        auto job = [&](int n_k, bool from_h, bool wait_h, uint32_t idesc, bool out = false) -> bool {
-            const uint32_t a = jq & 1, u = jq >> 1;
-            if (!mbar_wait(smem_u32(&tempty[a]), (u & 1) ^ 1)) return false;
-            if (wait_h) {
+        // Per tile: layer 0 into region 1 (A = the converters' features), the hidden layers into
+        // region 2 (A = the activations), the last layer's output tiles into the halves of region 2
+        // (A = rows of W_L, B = the activations); a 256-unit layer is two N = 128 halves, one
+        // weight box each.  The next tile's layer-0 chunks are interleaved between this tile's
+        // jobs (l0_target), the last of them after the last output job, so that layer 0's
+        // completion also retires every MMA that reads this tile's activations.
+        const uint32_t wbase = smem_u32(Ws), xbase = smem_u32(Xs), hbase = smem_u32(Hs);
+        const uint32_t id128 = idesc_f16(128, 128, 0, 1);
+        int64_t q = 0;              // weight boxes consumed
+        uint32_t xq = 0;            // layer-0 A tiles consumed
+        uint32_t hq = 0;            // activation tiles waited for
+        uint32_t u1 = 0;            // uses of region 1
+        uint32_t u20 = 0, u21 = 0;  // uses of the halves of region 2
+        uint32_t jo = 0;            // output jobs
+        auto next_w = [&](uint32_t &st) -> bool {
+            const int slot = (int)(q % kWSlots);
+            if (!mbar_wait(smem_u32(&wfull[slot]), (uint32_t)(q / kWSlots) & 1)) return false;
+            tc_fence_after();
+            st = wbase + slot * kSlot;
+            return true;
+        };
+        auto release_w = [&]() {
+            umma_commit(smem_u32(&wempty[q % kWSlots]));
+            ++q;
+        };
+        auto mma4 = [&](uint32_t acc, uint32_t a, uint32_t b, bool accumulate) {
+#pragma unroll
+            for (int kk = 0; kk < 4; ++kk)
+                umma_f16(acc, sw128_desc(a + kk * 32), sw128_desc(b + kk * 32), id128, accumulate || kk != 0);
+        };
+        auto l0_chunk = [&](int c) -> bool {
+            if (c == 0 && !mbar_wait(smem_u32(tempty1), (u1 & 1) ^ 1)) return false;
+            const uint32_t xslot = xq % kXSlots;
+            if (!mbar_wait(smem_u32(&xfull[xslot]), (xq / kXSlots) & 1)) return false;
+            tc_fence_after();
+            for (int r = 0; r < hr; ++r) {
+                uint32_t st;
+                if (!next_w(st)) return false;
+                mma4(tmem + r * 128, xbase + xslot * kSlot, st, c != 0);
+                release_w();
+            }
+            umma_commit(smem_u32(&xempty[xslot]));
+            ++xq;
+            if (c == k0 - 1) {
+                umma_commit(smem_u32(tfull1));
+                ++u1;
+            }
+            return true;
+        };
+        auto job = [&](int jj) -> bool {
+            const bool hidden = jj < L - 2;
+            const uint32_t h = jo & 1, uh = h ? u21 : u20;
+            if (hidden) {
+                if (!mbar_wait(smem_u32(&tempty2[0]), (u20 & 1) ^ 1) || !mbar_wait(smem_u32(&tempty2[1]), (u21 & 1) ^ 1))
+                    return false;
+            } else if (!mbar_wait(smem_u32(&tempty2[h]), (uh & 1) ^ 1)) {
+                return false;
+            }
+            if (hidden || jj == L - 2) {  // the activations this job reads are written
                 if (!mbar_wait(smem_u32(hready), hq & 1)) return false;
                 ++hq;
             }
             tc_fence_after();
-            const uint32_t acc = tmem + a * 256;
-            for (int c = 0; c < n_k; ++c, ++q) {
-                const int slot = (int)(q % kStages);
-                if (!mbar_wait(smem_u32(&full[slot]), (uint32_t)(q / kStages) & 1)) return false;
-                const bool x_in = !from_h && !out;
-                const uint32_t xslot = xq % kStages;
-                if (x_in && !mbar_wait(smem_u32(&xfull[xslot]), (xq / kStages) & 1)) return false;
-                tc_fence_after();
-                const uint32_t st = sbase + slot * kStageBytes;
-                const uint32_t abase = out ? st : (from_h ? hbase + c * kATile : xbase + xslot * kATile);
-                const uint32_t bbase = out ? hbase + c * kATile : st;
-#pragma unroll
-                for (int kk = 0; kk < 4; ++kk)
-                    umma_f16(acc, sw128_desc(abase + kk * 32), sw128_desc(bbase + kk * 32), idesc, (c | kk) != 0);
-                umma_commit(smem_u32(&empty[slot]));
-                if (x_in) {
-                    umma_commit(smem_u32(&xempty[xslot]));
-                    ++xq;
+            for (int c = 0; c < kh; ++c) {
+                if (hidden) {
+                    for (int r = 0; r < hr; ++r) {
+                        uint32_t st;
+                        if (!next_w(st)) return false;
+                        mma4(tmem + 256 + r * 128, hbase + c * kSlot, st, c != 0);
+                        release_w();
+                    }
+                } else {
+                    uint32_t st;
+                    if (!next_w(st)) return false;
+                    mma4(tmem + 256 + h * kOutTile, st, hbase + c * kSlot, c != 0);
+                    release_w();
                 }
             }
-            umma_commit(smem_u32(&tfull[a]));
-            ++jq;
+            if (hidden) {
+                umma_commit(smem_u32(&tfull2[0]));
+                umma_commit(smem_u32(&tfull2[1]));
+                ++u20;
+                ++u21;
+            } else {
+                umma_commit(smem_u32(&tfull2[h]));
+                if (h) ++u21; else ++u20;
+                ++jo;
+            }
             return true;
         };
-        for (int64_t tile = blockIdx.x; tile < g.tiles && ok && !*vabort; tile += gridDim.x) {
-            ok = job(k0, false, false, id_hidden);
-            for (int l = 1; l < L - 1 && ok; ++l) ok = job(kh, true, true, id_hidden);
-            for (int nt = 0; nt < n_out && ok; ++nt) ok = job(kh, false, nt == 0, id_out, true);
+        bool ok = true;
+        for (int c = 0; c < k0 && ok && my_tiles > 0; ++c) ok = l0_chunk(c);
+        for (int64_t it = 0; it < my_tiles && ok && !*vabort; ++it) {
+            const bool next = it + 1 < my_tiles;
+            int cn = 0;
+            for (int jj = 0; jj < J && ok; ++jj) {
+                ok = job(jj);
+                for (const int tgt = next ? l0_target(jj, J, k0) : 0; cn < tgt && ok; ++cn) ok = l0_chunk(cn);
+            }
         }
-        if (!ok) {
-            *vabort = 1;
-            atomicExch(g.err, 1);
-        }
+        if (!ok) fail();
         umma_commit(smem_u32(done));
         mbar_wait(smem_u32(done), 0);  // every MMA of this CTA has retired (bounded)
-    } else if (warp >= 2 && warp < kEpiWarp0) {
+    } else if (warp >= kConvWarp0 && warp < kEpiWarp0) {
         // ---------------- feature converters ----------------
         // Layer-0 chunk c of a tile is features 64 c .. 64 c + 63 = buses 32 c .. 32 c + 31, (P, Q)
-        // interleaved.  Lane l takes bus 32 c + l; warp w rows (columns t) 16 w .. 16 w + 15, one
-        // coalesced 512-byte load of S per row.  The chunk's loads go out in two halves of 8 rows,
-        // each half of the next chunk issued as soon as this chunk's half is converted, so that
-        // one to two halves per warp stay in flight.
-        const int cw = warp - 2;
-        const int64_t my_tiles = g.tiles > blockIdx.x ? (g.tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+        // interleaved.  Lane l takes bus 32 c + l; warp w rows 4 w .. 4 w + 3 of each staged box
+        // (one 16-byte shared-memory read per row, 512 contiguous bytes per warp), converted from
+        // the FP64 high words and written as one BF16 pair into the swizzled A tile.
+        const int cw = warp - kConvWarp0;
         const int64_t steps = my_tiles * k0;
-        const uint8_t *Sb = reinterpret_cast<const uint8_t *>(g.S);
-        auto load_half = [&](uint4 (&v)[8], int64_t s, int half) {
-            const int64_t tile = blockIdx.x + (s / k0) * gridDim.x;
+        int64_t k = 0;  // staged boxes consumed
+        for (int64_t s = 0; s < steps; ++s) {
+            const int xslot = (int)(s % kXSlots);
             const int j = (int)(s % k0) * 32 + lane;
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int64_t t = tile * 128 + cw * kConvRows + half * 8 + i;
-                v[i] = (j < g.n && t < g.T) ? __ldg(reinterpret_cast<const uint4 *>(Sb + (t * g.n + j) * 16))
-                                            : make_uint4(0u, 0u, 0u, 0u);
-            }
-        };
-        auto store_half = [&](const uint4 (&v)[8], uint8_t *a, float4 nm, int half) {
-#pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                const int r = cw * kConvRows + half * 8 + i;
-                const float xr = fmaf(f64_hi_to_f32(v[i].y), nm.x, nm.y);
-                const float xi = fmaf(f64_hi_to_f32(v[i].w), nm.z, nm.w);
-                *reinterpret_cast<uint32_t *>(a + (r >> 3) * 1024 + (r & 7) * 128 + (((lane >> 2) ^ (r & 7)) << 4) +
-                                              ((lane & 3) << 2)) = pack_bf16(xr, xi);
-            }
-        };
-        uint4 va[8], vb[8];
-        if (steps > 0) {
-            load_half(va, 0, 0);
-            load_half(vb, 0, 1);
-        }
-        for (int64_t s = 0; s < steps; ++s) {  // s: this A tile's place in the converters' ring
-            const int c = (int)(s % k0);
-            const int slot = (int)(s % kStages);
-            const int j = c * 32 + lane;
             const float4 nm = j < g.n ? __ldg(g.xnorm + j) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-            if (*vabort || !mbar_wait(smem_u32(&xempty[slot]), ((uint32_t)(s / kStages) & 1) ^ 1)) {
-                *vabort = 1;
-                atomicExch(g.err, 1);
+            if (*vabort || !mbar_wait(smem_u32(&xempty[xslot]), ((uint32_t)(s / kXSlots) & 1) ^ 1)) {
+                fail();
                 break;
             }
-            uint8_t *a = Xs + slot * kATile;
-            store_half(va, a, nm, 0);
-            if (s + 1 < steps) load_half(va, s + 1, 0);
-            store_half(vb, a, nm, 1);
-            if (s + 1 < steps) load_half(vb, s + 1, 1);
+            uint8_t *a = Xs + xslot * kSlot;
+            bool ok = true;
+            for (int b = 0; b < kBoxes; ++b, ++k) {
+                const int sslot = (int)(k % kSSlots);
+                if (!mbar_wait(smem_u32(&sfull[sslot]), (uint32_t)(k / kSSlots) & 1)) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t *src = Ss + sslot * kSBox;
+#pragma unroll
+                for (int i = 0; i < kConvRows; ++i) {
+                    const int rl = cw * kConvRows + i, r = b * kSRows + rl;
+                    const uint4 v = *reinterpret_cast<const uint4 *>(src + rl * 512 + lane * 16);
+                    const float xr = fmaf(f64_hi_to_f32(v.y), nm.x, nm.y);
+                    const float xi = fmaf(f64_hi_to_f32(v.w), nm.z, nm.w);
+                    *reinterpret_cast<uint32_t *>(a + (r >> 3) * 1024 + (r & 7) * 128 + (((lane >> 2) ^ (r & 7)) << 4) +
+                                                  ((lane & 3) << 2)) = pack_bf16(xr, xi);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_u32(&sempty[sslot]));
+            }
+            if (!ok) {
+                fail();
+                break;
+            }
             fence_async_smem();  // the MMAs (async proxy) read this tile next
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&xfull[slot]));
+            if (lane == 0) mbar_arrive(smem_u32(&xfull[xslot]));
         }
     } else if (warp >= kEpiWarp0) {
         // ---------------- epilogue: kEpiGroups warps per TMEM lane quarter ----------------
@@ -314,24 +416,33 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
         // This row's 128-byte line inside each 16 KB K chunk of the activations (SW128 layout).
         uint8_t *hrow = Hs + (row >> 3) * 1024 + (row & 7) * 128;
         const int hp = H / 32 / kEpiGroups;  // pieces of 32 units per part
-        uint32_t jq = 0;
+        uint32_t e1 = 0, e20 = 0, e21 = 0, eo = 0;  // uses of region 1, of the halves of region 2; output jobs
         for (int64_t tile = blockIdx.x; tile < g.tiles; tile += gridDim.x) {
             const int64_t t = tile * 128 + row;  // this thread's column (hidden layers)
             bool failed = false;
             const int jobs = L - 1 + n_out;
-            for (int j = 0; j < jobs; ++j, ++jq) {
-                const uint32_t a = jq & 1, u = jq >> 1;
-                if (!mbar_wait(smem_u32(&tfull[a]), u & 1)) atomicOr(&s_fail, 1);
+            for (int j = 0; j < jobs; ++j) {
+                // Job j: layer 0 (region 1), hidden layer j (region 2), or output tile j - (L - 1)
+                // (half eo & 1 of region 2).
+                const uint32_t h = eo & 1, eh = h ? e21 : e20;
+                bool got;
+                if (j == 0)
+                    got = mbar_wait(smem_u32(tfull1), e1 & 1);
+                else if (j < L - 1)
+                    got = mbar_wait(smem_u32(&tfull2[0]), e20 & 1) && mbar_wait(smem_u32(&tfull2[1]), e21 & 1);
+                else
+                    got = mbar_wait(smem_u32(&tfull2[h]), eh & 1);
+                if (!got) atomicOr(&s_fail, 1);
                 epi_sync();
                 if (s_fail) {
                     failed = true;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t acc = tmem + a * 256 + lane_off;
+                const uint32_t acc = tmem + (j == 0 ? 0u : 256u + (j < L - 1 ? 0u : h * kOutTile)) + lane_off;
                 if (j < L - 1) {
                     // Hidden activations of layer j: bias, GELU, BF16 into the next layer's A operand.
-                    const float *bias = s_bias + j * H;
+                    const float *bias = g.bias[j];
                     for (int p = part * hp; p < (part + 1) * hp; ++p) {
                         uint32_t v[32];
                         tmem_ld32(acc + p * 32, v);
@@ -339,12 +450,12 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
                         uint32_t w[16];
 #pragma unroll
                         for (int e = 0; e < 16; ++e) {
-                            const float2 b2 = *reinterpret_cast<const float2 *>(bias + p * 32 + 2 * e);
+                            const float2 b2 = __ldg(reinterpret_cast<const float2 *>(bias + p * 32 + 2 * e));
                             w[e] = gelu_pair_bf16(__uint_as_float(v[2 * e]) + b2.x,
                                                   __uint_as_float(v[2 * e + 1]) + b2.y);
                         }
                         // Units p*32 .. p*32+31: K chunk p/2, 16-byte groups 4 (p&1) .. +3, swizzled by row.
-                        uint8_t *chunk = hrow + (p >> 1) * kATile;
+                        uint8_t *chunk = hrow + (p >> 1) * kSlot;
 #pragma unroll
                         for (int gq = 0; gq < 4; ++gq) {
                             const int grp = ((p & 1) * 4 + gq) ^ (row & 7);
@@ -427,7 +538,21 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_infer(const __grid_constant__
                 }
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_u32(&tempty[a]));
+                if (j == 0) {
+                    if (lane == 0) mbar_arrive(smem_u32(tempty1));
+                    ++e1;
+                } else if (j < L - 1) {
+                    if (lane == 0) {
+                        mbar_arrive(smem_u32(&tempty2[0]));
+                        mbar_arrive(smem_u32(&tempty2[1]));
+                    }
+                    ++e20;
+                    ++e21;
+                } else {
+                    if (lane == 0) mbar_arrive(smem_u32(&tempty2[h]));
+                    if (h) ++e21; else ++e20;
+                    ++eo;
+                }
             }
             if (failed) {
                 *vabort = 1;

@@ -13,7 +13,7 @@ struct InferArgs {
     CUtensorMap map_w[kMaxInferLayers];     // W_l [out][in] BF16, box 64 x 128: W_0 with interleaved inputs,
                                             // W_{L-1} with interleaved output rows
     const float *bias[kMaxInferLayers];     // FP32 biases of the hidden layers
-    const double2 *S;                       // [T][n] complex128 loads of the columns (16-byte aligned)
+    CUtensorMap map_s;                      // S [T][n] complex128 as FP64 [T][2n], box 64 x 32, no swizzle
     const float4 *xnorm;                    // [P0 / 2] per bus: 1 / sd_P, -mean_P / sd_P, 1 / sd_Q, -mean_Q / sd_Q
                                             // (zero for padding buses and constant features)
     const float *bias_out;                  // [PL] last layer's bias, interleaved

@@ -60,9 +60,9 @@ METRIC = "PF solves/s at ≤1e-8 pu vs FP64 oracle: mixed+learned-start vs plain
 # columns each launch of this run processes.  None once the kernel has changed since the capture.
 GEMM_TRAFFIC_BYTES_PER_COLUMN = (203.725056e6 + 75.471360e6) / 16384
 # The same for the sparse tree kernel mx_tree started from the learned prediction (the headline
-# step's solve): 394.1 MB read (S and the complex64 prediction) + 221.2 MB written for 16,384
-# columns of the 1,000-bus feeder.
-TREE_TRAFFIC_BYTES_PER_COLUMN = (394.113536e6 + 221.190656e6) / 16384
+# step's solve): 1,313.9 MB read (S and the half-precision prediction) + 1,002.9 MB written for
+# 65,536 columns of the 1,000-bus feeder.
+TREE_TRAFFIC_BYTES_PER_COLUMN = (1313.903e6 + 1002.918e6) / 65536
 # From the flat start: not captured for the current build of the kernel (null in the line).
 TREE_FLAT_TRAFFIC_BYTES_PER_COLUMN = None
 # Algorithmic FP32 flop per bus per sweep of the tree formulation: load current conj(S/V) 12,
@@ -286,10 +286,11 @@ def cpu_newton_leg(f, S_host, full_T, columns=16):
             "max_abs_err_pu_vs_fpi_oracle": err}
 
 
-def train_start_network(f, fd, args, dev, n_train, epochs, seed_offset=100):
-    """The learned start's network for feeder f: n_train columns of another load draw (seed +
-    seed_offset, drawn on the device), solved by the library (sparse, mixed, tol), then `epochs`
-    epochs of Adam on batches of 1,024 with a cosine learning rate from 1e-3 down to 1e-4."""
+def train_start_network(f, fd, args, dev, n_train, epochs, seed_offset=100, hidden=256, layers=3):
+    """The learned start's network for feeder f (`layers` hidden layers of `hidden` units): n_train
+    columns of another load draw (seed + seed_offset, drawn on the device), solved by the library
+    (sparse, mixed, tol), then `epochs` epochs of Adam on batches of 1,024 with a cosine learning
+    rate from 1e-3 down to 1e-4."""
     import torch
 
     from paper_2403_04578_gb300 import inputs as G
@@ -297,7 +298,7 @@ def train_start_network(f, fd, args, dev, n_train, epochs, seed_offset=100):
 
     S_tr = G.load_tensor_device(f, n_train, args.seed + seed_offset, dev)
     V_tr, _, _, st = fd.solve(S_tr, precision="mixed", tol=args.tol, method="sparse")
-    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=1024, seed=args.seed)
+    net = tpf.LearnedStart(f.n_pq, hidden=hidden, hidden_layers=layers, max_batch=1024, seed=args.seed)
     net.fit_normalization(S_tr, V_tr)
     B = 1024
     steps_per_epoch = n_train // B
@@ -316,7 +317,8 @@ def train_start_network(f, fd, args, dev, n_train, epochs, seed_offset=100):
     del S_tr, V_tr
     torch.cuda.empty_cache()
     return net, {"train_columns": n_train, "epochs": epochs, "train_seconds": train_s, "final_batch_loss": loss,
-                 "network": f"{2 * f.n_pq}-256-256-256-{2 * f.n_pq}, GELU, BF16 tensor-core products"}
+                 "network": "-".join([str(2 * f.n_pq)] + [str(hidden)] * layers + [str(2 * f.n_pq)]) +
+                            ", GELU, BF16 tensor-core products"}
 
 
 def learned_e2e(fd, net, Sh, Vh, ith, mmh, Sd, Vd, itd, mmd, args, world, chunks=32):
@@ -352,7 +354,8 @@ def learned_e2e(fd, net, Sh, Vh, ith, mmh, Sd, Vd, itd, mmd, args, world, chunks
         s_out.synchronize()
 
     one()
-    steps = max(1, args.steps // 2)
+    one()  # two warm-up passes: the first touches of the pinned pages and the copy engines' queues
+    steps = max(1, args.steps)
     barrier(world)
     t0 = time.perf_counter()
     step_ms = []
@@ -920,6 +923,7 @@ def main():
                 else gemm_roofline(main_run))
     flat = {"value": value, "unit": "PF/s", "ms_per_step": ms_per_step, "mean_sweeps": column_sweeps / T,
             "gpu_launches": main_run["launches"], "roofline": roofline,
+            "step_ms": [round(x, 3) for x in main_run["step_ms"]],
             "note": "flat start V_0 = 1 (Algorithm 1), sparse mixed solve"}
 
     # The learned start on the same workload: the network is trained once per feeder (on other load
@@ -939,6 +943,7 @@ def main():
                    "mean_sweeps": l_sweeps / T, "fallback_columns": fallback, "converged": lrun["stats"]["converged"],
                    "gpu_launches": lrun["launches"], "roofline": tree_roofline(lrun, l_sweeps),
                    "solve_kernel_ms": lrun["kernel_ms"], "predict_ms": lrun["ms_per_step"] - lrun["kernel_ms"],
+                   "step_ms": [round(x, 3) for x in lrun["step_ms"]],
                    "clocks": lrun["clocks"], **train_info}
         if checking:
             V_checks["learned_max_abs_err_pu"] = Vd[cc_dev].cpu().numpy()
@@ -949,8 +954,9 @@ def main():
         Vh = torch.empty((T, n), dtype=torch.complex128, pin_memory=True)
         ith = torch.empty(T, dtype=torch.int32, pin_memory=True)
         mmh = torch.empty(T, dtype=torch.float64, pin_memory=True)
-        fd.solve_host(Sh, precision="mixed", tol=args.tol, out=(Vh, ith, mmh), method=args.method)
-        e2e_steps = max(1, args.steps // 2)
+        for _ in range(2):  # warm-up: the first touches of the pinned pages and the copy engines' queues
+            fd.solve_host(Sh, precision="mixed", tol=args.tol, out=(Vh, ith, mmh), method=args.method)
+        e2e_steps = max(1, args.steps)
         barrier(world)
         t0 = time.perf_counter()
         step_ms = []

@@ -824,8 +824,8 @@ tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void
     const int64_t chunk = std::min<int64_t>(T, round_up((T + n_ch - 1) / n_ch, 128));
     const int64_t cap = round_up(chunk, 128);
     const int n = net->n;
-    // Columns of the prediction buffer start on 128-byte boundaries: a warp's 32 consecutive
-    // outputs of one column then fill one cache line.
+    // Columns of the prediction buffer start on 64-byte boundaries: a warp's 32 consecutive
+    // half-precision outputs of one column then fill two whole 32-byte sectors.
     const int64_t pitch = round_up(n, 16);
     if (net->v0_cap < cap * pitch) {
         cudaFree(net->V0c);

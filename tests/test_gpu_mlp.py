@@ -253,7 +253,8 @@ def test_fused_prediction_matches_the_fp64_reference(cuda, feeder200, hidden, la
     net.close()
 
 
-def test_fused_prediction_with_several_tiles_per_cta(cuda, feeder200):
+@pytest.mark.parametrize("hidden,layers", [(256, 3), (128, 1)])
+def test_fused_prediction_with_several_tiles_per_cta(cuda, feeder200, hidden, layers):
     """More 128-column tiles than SMs: each persistent CTA takes several tiles in turn and the rings
     of the weights and of the converted features wrap many times.  Every column's prediction equals
     the one computed in a launch with one tile per CTA (a column's outputs depend on its own row of
@@ -263,10 +264,10 @@ def test_fused_prediction_with_several_tiles_per_cta(cuda, feeder200):
     f, c = feeder200
     S_fit = G.load_tensor(f, 4096, 9)
     V_fit, _, _ = c.solve(S_fit, tol=1e-12)
-    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=128, seed=5)
+    net = tpf.LearnedStart(f.n_pq, hidden=hidden, hidden_layers=layers, max_batch=128, seed=5)
     net.fit_normalization(_dev(S_fit), _dev(V_fit))
     xm, xs, ym, ys = (np.asarray(a, dtype=np.float64) for a in net.normalization())
-    rng = np.random.default_rng(17)
+    rng = np.random.default_rng(17 + layers)
     sizes = net.sizes
     Ws = [rng.uniform(-1, 1, (sizes[i + 1], sizes[i])) * np.sqrt(6.0 / (sizes[i] + sizes[i + 1]))
           for i in range(len(sizes) - 1)]

@@ -321,37 +321,15 @@ def train_start_network(f, fd, args, dev, n_train, epochs, seed_offset=100, hidd
                             ", GELU, BF16 tensor-core products"}
 
 
-def learned_e2e(fd, net, Sh, Vh, ith, mmh, Sd, Vd, itd, mmd, args, world, chunks=32):
-    """The learned-start solve end to end through the public API: pinned host loads copied in
-    chunks on one stream, each chunk solved (prediction + warm solve) as soon as its copy lands,
-    and its V, iteration counts and mismatches copied back on a third stream while the next chunk is
-    solved."""
-    import torch
-
-    T = Sh.shape[0]
-    bounds = [(T * c // chunks, T * (c + 1) // chunks) for c in range(chunks)]
-    s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-    comp = torch.cuda.current_stream()
+def learned_e2e(fd, net, Sh, Vh, ith, mmh, args, world):
+    """The learned-start solve end to end through the public host-buffer entry point
+    (tpf_solve_learned_host): pinned host loads in, pinned V, iteration counts and mismatches out;
+    the library pipelines the host-to-device copies, the chunked predictions and solves, and the
+    copies back."""
+    T, n = Sh.shape
 
     def one():
-        ev_in = []
-        with torch.cuda.stream(s_in):
-            for a, b in bounds:
-                Sd[a:b].copy_(Sh[a:b], non_blocking=True)
-                e = torch.cuda.Event()
-                e.record(s_in)
-                ev_in.append(e)
-        for (a, b), e in zip(bounds, ev_in):
-            comp.wait_event(e)
-            fd.solve_learned(net, Sd[a:b], Vd[a:b], itd[a:b], mmd[a:b], tol=args.tol, stream=comp)
-            done = torch.cuda.Event()
-            done.record(comp)
-            s_out.wait_event(done)
-            with torch.cuda.stream(s_out):
-                Vh[a:b].copy_(Vd[a:b], non_blocking=True)
-                ith[a:b].copy_(itd[a:b], non_blocking=True)
-                mmh[a:b].copy_(mmd[a:b], non_blocking=True)
-        s_out.synchronize()
+        fd.solve_learned_host(net, Sh, tol=args.tol, out=(Vh, ith, mmh))
 
     one()
     one()  # two warm-up passes: the first touches of the pinned pages and the copy engines' queues
@@ -364,12 +342,10 @@ def learned_e2e(fd, net, Sh, Vh, ith, mmh, Sd, Vd, itd, mmd, args, world, chunks
         one()
         step_ms.append((time.perf_counter() - ts) * 1e3)
     dt = allmax(world, (time.perf_counter() - t0) / steps)
-    n = Sh.shape[1]
     return {"value": world * T / dt, "unit": "PF/s", "h2d_bytes_per_step": T * n * 16,
             "d2h_bytes_per_step": T * n * 16 + T * 4 + T * 8, "ms_per_step": dt * 1e3,
             "step_ms": [round(x, 2) for x in step_ms],
-            "entry_point": f"tpf_solve_learned per chunk of {T // chunks:,} columns, pinned host buffers, "
-                           "copies on their own streams"}
+            "entry_point": "tpf_solve_learned_host (pinned host buffers; up to 32 chunks pipelined in the library)"}
 
 
 def learned_start_leg(args, stream):
@@ -970,7 +946,7 @@ def main():
                "step_ms": [round(x, 2) for x in step_ms],
                "entry_point": "tpf_solve_host (pinned host buffers)"}
         if learned is not None:
-            learned["e2e"] = learned_e2e(fd, net, Sh, Vh, ith, mmh, Sd, Vd, itd, mmd, args, world)
+            learned["e2e"] = learned_e2e(fd, net, Sh, Vh, ith, mmh, args, world)
 
     # The other formulation on the same workload.
     other = "dense" if args.method == "sparse" else "sparse"

@@ -373,6 +373,21 @@ tpf_status tpf_solve_learned(tpf_handle *hd, tpf_mlp *net, int64_t T, const void
                              void *stream);
 
 /*
+ * The learned-start solve from HOST buffers (the host-buffer counterpart of tpf_solve_learned, as
+ * tpf_solve_host is of tpf_solve): S_host [T][n_pq] complex128 in, V_host [T][n_pq] complex128,
+ * iters_host [T] and mismatch_host [T] (both may be NULL) out.  The columns go through the
+ * handle's device workspace in up to 32 chunks: every host-to-device copy is queued at once, each
+ * chunk's prediction and solve wait only for its own copy, and its results go back while the next
+ * chunk is solved (pinned host memory overlaps copies and compute; pageable memory works, with the
+ * copies serialised).  fallback_out (host, may be NULL) receives the columns that started flat.
+ * opts as tpf_solve_learned; errors as tpf_solve_learned, plus TPF_ENOMEM when the workspace
+ * (2 x 16 n_pq + 12 bytes per column) cannot be allocated.  Blocks until done.
+ */
+tpf_status tpf_solve_learned_host(tpf_handle *hd, tpf_mlp *net, int64_t T, const void *S_host, void *V_host,
+                                  int32_t *iters_host, double *mismatch_host, const tpf_opts *opts,
+                                  int64_t *fallback_out, void *stream);
+
+/*
  * Allocation-free FP64 solve.  The paper has no counterpart to this entry point; it exists for
  * callers that must not allocate device memory themselves or have the library do it: runtimes
  * that hand out device memory only from their own pool (raw cudaMalloc/cudaFree would escape

@@ -410,6 +410,119 @@ void compute_dense(Network &net) {
 
 }  // namespace tpf
 
+namespace {
+
+// The host-buffer solve: columns are independent, so it runs chunk by chunk on the device
+// workspace (see the comment inside); solve(cols, S_dev, V_dev, iters_dev, mismatch_dev) solves one
+// chunk on `stream` and leaves its statistics in h->stats.  v_in: V_host holds a start to copy in.
+template <class Solve>
+tpf_status host_chunks(tpf_handle *h, int64_t T, const void *S_host, void *V_host, int32_t *iters_host,
+                       double *mismatch_host, const tpf_opts &o, void *stream, bool v_in, Solve solve) {
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    tpf::Workspace &w = h->ws;
+    const size_t col_bytes = (size_t)h->net.n_pq * 16;
+    if (T > w.host_cap) {
+        cudaFree(w.S_dev); cudaFree(w.V_dev); cudaFree(w.it_dev); cudaFree(w.mm_dev);
+        w.S_dev = w.V_dev = nullptr; w.it_dev = nullptr; w.mm_dev = nullptr; w.host_cap = 0;
+        if (cudaMalloc(&w.S_dev, col_bytes * T) != cudaSuccess || cudaMalloc(&w.V_dev, col_bytes * T) != cudaSuccess ||
+            cudaMalloc(&w.it_dev, sizeof(int32_t) * T) != cudaSuccess ||
+            cudaMalloc(&w.mm_dev, sizeof(double) * T) != cudaSuccess) {
+            cudaGetLastError();
+            return TPF_ENOMEM;
+        }
+        w.host_cap = T;
+    }
+    // Columns are independent, so the solve runs chunk by chunk: every host-to-device copy is queued
+    // at once on an input stream, each chunk's solve waits only for its own copy, and its results go
+    // back on an output stream while the next chunk is solved (pinned host memory overlaps; pageable
+    // memory still works, with the copies serialised by the driver).
+    // The sparse solve is one short launch per chunk, so it takes finer chunks (less fill and drain
+    // around the copies); the dense solve's per-sweep host loop prefers fewer.
+    const int64_t max_chunks = o.method == TPF_METHOD_SPARSE ? 32 : 8;  // the learned start is sparse
+    const int64_t n_chunks = T >= 65536 ? std::min<int64_t>(max_chunks, T / 16384) : 1;
+    const int64_t chunk = tpf::round_up((T + n_chunks - 1) / n_chunks, tpf::kTileN);
+    cudaStream_t sin = nullptr, sout = nullptr;
+    std::vector<cudaEvent_t> ev;
+    auto cleanup = [&]() {
+        if (sout) cudaStreamSynchronize(sout);
+        if (sin) cudaStreamSynchronize(sin);
+        for (cudaEvent_t e : ev) cudaEventDestroy(e);
+        if (sin) cudaStreamDestroy(sin);
+        if (sout) cudaStreamDestroy(sout);
+        cudaGetLastError();
+    };
+    if (cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking) != cudaSuccess) {
+        cleanup();
+        return TPF_ECUDA;
+    }
+    ev.assign(2 * n_chunks, nullptr);
+    for (cudaEvent_t &e : ev)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cleanup();
+            return TPF_ECUDA;
+        }
+    const char *Sh = static_cast<const char *>(S_host);
+    char *Vh = static_cast<char *>(V_host);
+    char *Sd = static_cast<char *>(w.S_dev), *Vd = static_cast<char *>(w.V_dev);
+    for (int64_t c = 0; c < n_chunks; ++c) {
+        const int64_t a = c * chunk, b = std::min(T, a + chunk);
+        if (a >= b) break;
+        if (cudaMemcpyAsync(Sd + a * col_bytes, Sh + a * col_bytes, (b - a) * col_bytes, cudaMemcpyHostToDevice, sin) !=
+                cudaSuccess ||
+            (v_in && cudaMemcpyAsync(Vd + a * col_bytes, Vh + a * col_bytes, (b - a) * col_bytes,
+                                                           cudaMemcpyHostToDevice, sin) != cudaSuccess) ||
+            cudaEventRecord(ev[2 * c], sin) != cudaSuccess) {
+            cleanup();
+            return TPF_ECUDA;
+        }
+    }
+    tpf_stats total{};
+    tpf_status result = TPF_OK;
+    for (int64_t c = 0; c < n_chunks; ++c) {
+        const int64_t a = c * chunk, b = std::min(T, a + chunk);
+        if (a >= b) break;
+        if (cudaStreamWaitEvent(s, ev[2 * c], 0) != cudaSuccess) {
+            cleanup();
+            return TPF_ECUDA;
+        }
+        tpf_status st = solve(b - a, Sd + a * col_bytes, Vd + a * col_bytes, iters_host ? w.it_dev + a : nullptr,
+                              mismatch_host ? w.mm_dev + a : nullptr);
+        if (st != TPF_OK && st != TPF_ENOCONV) {
+            cleanup();
+            return st;
+        }
+        if (st == TPF_ENOCONV) result = TPF_ENOCONV;
+        const tpf_stats &p = h->stats;
+        total.sweeps = std::max(total.sweeps, p.sweeps);
+        total.precise_sweeps = std::max(total.precise_sweeps, p.precise_sweeps);
+        total.converged += p.converged;
+        total.columns += p.columns;
+        total.kernel_launches += p.kernel_launches;
+        total.gemm_ms += p.gemm_ms;
+        total.residual_ms += p.residual_ms;
+        total.other_ms += p.other_ms;
+        total.gemm_launches += p.gemm_launches;
+        total.gemm_columns += p.gemm_columns;
+        if (cudaEventRecord(ev[2 * c + 1], s) != cudaSuccess || cudaStreamWaitEvent(sout, ev[2 * c + 1], 0) != cudaSuccess ||
+            cudaMemcpyAsync(Vh + a * col_bytes, Vd + a * col_bytes, (b - a) * col_bytes, cudaMemcpyDeviceToHost, sout) !=
+                cudaSuccess ||
+            (iters_host && cudaMemcpyAsync(iters_host + a, w.it_dev + a, sizeof(int32_t) * (b - a),
+                                           cudaMemcpyDeviceToHost, sout) != cudaSuccess) ||
+            (mismatch_host && cudaMemcpyAsync(mismatch_host + a, w.mm_dev + a, sizeof(double) * (b - a),
+                                              cudaMemcpyDeviceToHost, sout) != cudaSuccess)) {
+            cleanup();
+            return TPF_ECUDA;
+        }
+    }
+    const bool ok = cudaStreamSynchronize(sout) == cudaSuccess;
+    cleanup();
+    h->stats = total;
+    return ok ? result : TPF_ECUDA;
+}
+
+}  // namespace
+
 extern "C" {
 
 void tpf_default_opts(tpf_opts *o) {
@@ -733,107 +846,38 @@ tpf_status tpf_solve_host(tpf_handle *h, int64_t T, const void *S_host, void *V_
     if (!S_host || !V_host) return TPF_EINVAL;
     tpf::DeviceScope dscope(h->device);
     if (!dscope.ok) return TPF_ECUDA;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    tpf::Workspace &w = h->ws;
-    const size_t col_bytes = (size_t)h->net.n_pq * 16;
-    if (T > w.host_cap) {
-        cudaFree(w.S_dev); cudaFree(w.V_dev); cudaFree(w.it_dev); cudaFree(w.mm_dev);
-        w.S_dev = w.V_dev = nullptr; w.it_dev = nullptr; w.mm_dev = nullptr; w.host_cap = 0;
-        if (cudaMalloc(&w.S_dev, col_bytes * T) != cudaSuccess || cudaMalloc(&w.V_dev, col_bytes * T) != cudaSuccess ||
-            cudaMalloc(&w.it_dev, sizeof(int32_t) * T) != cudaSuccess ||
-            cudaMalloc(&w.mm_dev, sizeof(double) * T) != cudaSuccess) {
-            cudaGetLastError();
-            return TPF_ENOMEM;
-        }
-        w.host_cap = T;
+    return host_chunks(h, T, S_host, V_host, iters_host, mismatch_host, o, stream, o.start != TPF_START_FLAT,
+                       [&](int64_t cols, void *Sd, void *Vd, int32_t *itd, double *mmd) {
+                           return tpf_solve(h, cols, Sd, Vd, itd, mmd, &o, stream);
+                       });
+}
+
+tpf_status tpf_solve_learned_host(tpf_handle *hd, tpf_mlp *net, int64_t T, const void *S_host, void *V_host,
+                                  int32_t *iters_host, double *mismatch_host, const tpf_opts *opts,
+                                  int64_t *fallback_out, void *stream) {
+    if (fallback_out) *fallback_out = 0;
+    if (!hd || !net || T < 0) return TPF_EINVAL;
+    tpf_opts o;
+    tpf_status st = check_opts(opts, o);
+    if (st != TPF_OK) return st;
+    if (o.method != TPF_METHOD_SPARSE || o.precision != TPF_PREC_MIXED) return TPF_EUNSUPPORTED;
+    if (T == 0) {
+        hd->stats = tpf_stats{};
+        return TPF_OK;
     }
-    // Columns are independent, so the solve runs chunk by chunk: every host-to-device copy is queued
-    // at once on an input stream, each chunk's solve waits only for its own copy, and its results go
-    // back on an output stream while the next chunk is solved (pinned host memory overlaps; pageable
-    // memory still works, with the copies serialised by the driver).
-    // The sparse solve is one short launch per chunk, so it takes finer chunks (less fill and drain
-    // around the copies); the dense solve's per-sweep host loop prefers fewer.
-    const int64_t max_chunks = o.method == TPF_METHOD_SPARSE ? 32 : 8;
-    const int64_t n_chunks = T >= 65536 ? std::min<int64_t>(max_chunks, T / 16384) : 1;
-    const int64_t chunk = tpf::round_up((T + n_chunks - 1) / n_chunks, tpf::kTileN);
-    cudaStream_t sin = nullptr, sout = nullptr;
-    std::vector<cudaEvent_t> ev;
-    auto cleanup = [&]() {
-        if (sout) cudaStreamSynchronize(sout);
-        if (sin) cudaStreamSynchronize(sin);
-        for (cudaEvent_t e : ev) cudaEventDestroy(e);
-        if (sin) cudaStreamDestroy(sin);
-        if (sout) cudaStreamDestroy(sout);
-        cudaGetLastError();
-    };
-    if (cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking) != cudaSuccess) {
-        cleanup();
-        return TPF_ECUDA;
-    }
-    ev.assign(2 * n_chunks, nullptr);
-    for (cudaEvent_t &e : ev)
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-            cleanup();
-            return TPF_ECUDA;
-        }
-    const char *Sh = static_cast<const char *>(S_host);
-    char *Vh = static_cast<char *>(V_host);
-    char *Sd = static_cast<char *>(w.S_dev), *Vd = static_cast<char *>(w.V_dev);
-    for (int64_t c = 0; c < n_chunks; ++c) {
-        const int64_t a = c * chunk, b = std::min(T, a + chunk);
-        if (a >= b) break;
-        if (cudaMemcpyAsync(Sd + a * col_bytes, Sh + a * col_bytes, (b - a) * col_bytes, cudaMemcpyHostToDevice, sin) !=
-                cudaSuccess ||
-            (o.start != TPF_START_FLAT && cudaMemcpyAsync(Vd + a * col_bytes, Vh + a * col_bytes, (b - a) * col_bytes,
-                                                           cudaMemcpyHostToDevice, sin) != cudaSuccess) ||
-            cudaEventRecord(ev[2 * c], sin) != cudaSuccess) {
-            cleanup();
-            return TPF_ECUDA;
-        }
-    }
-    tpf_stats total{};
-    tpf_status result = TPF_OK;
-    for (int64_t c = 0; c < n_chunks; ++c) {
-        const int64_t a = c * chunk, b = std::min(T, a + chunk);
-        if (a >= b) break;
-        if (cudaStreamWaitEvent(s, ev[2 * c], 0) != cudaSuccess) {
-            cleanup();
-            return TPF_ECUDA;
-        }
-        st = tpf_solve(h, b - a, Sd + a * col_bytes, Vd + a * col_bytes, iters_host ? w.it_dev + a : nullptr,
-                       mismatch_host ? w.mm_dev + a : nullptr, &o, stream);
-        if (st != TPF_OK && st != TPF_ENOCONV) {
-            cleanup();
-            return st;
-        }
-        if (st == TPF_ENOCONV) result = TPF_ENOCONV;
-        const tpf_stats &p = h->stats;
-        total.sweeps = std::max(total.sweeps, p.sweeps);
-        total.precise_sweeps = std::max(total.precise_sweeps, p.precise_sweeps);
-        total.converged += p.converged;
-        total.columns += p.columns;
-        total.kernel_launches += p.kernel_launches;
-        total.gemm_ms += p.gemm_ms;
-        total.residual_ms += p.residual_ms;
-        total.other_ms += p.other_ms;
-        total.gemm_launches += p.gemm_launches;
-        total.gemm_columns += p.gemm_columns;
-        if (cudaEventRecord(ev[2 * c + 1], s) != cudaSuccess || cudaStreamWaitEvent(sout, ev[2 * c + 1], 0) != cudaSuccess ||
-            cudaMemcpyAsync(Vh + a * col_bytes, Vd + a * col_bytes, (b - a) * col_bytes, cudaMemcpyDeviceToHost, sout) !=
-                cudaSuccess ||
-            (iters_host && cudaMemcpyAsync(iters_host + a, w.it_dev + a, sizeof(int32_t) * (b - a),
-                                           cudaMemcpyDeviceToHost, sout) != cudaSuccess) ||
-            (mismatch_host && cudaMemcpyAsync(mismatch_host + a, w.mm_dev + a, sizeof(double) * (b - a),
-                                              cudaMemcpyDeviceToHost, sout) != cudaSuccess)) {
-            cleanup();
-            return TPF_ECUDA;
-        }
-    }
-    const bool ok = cudaStreamSynchronize(sout) == cudaSuccess;
-    cleanup();
-    h->stats = total;
-    return ok ? result : TPF_ECUDA;
+    if (!S_host || !V_host) return TPF_EINVAL;
+    tpf::DeviceScope dscope(hd->device);
+    if (!dscope.ok) return TPF_ECUDA;
+    int64_t fallback = 0;
+    st = host_chunks(hd, T, S_host, V_host, iters_host, mismatch_host, o, stream, false,
+                     [&](int64_t cols, void *Sd, void *Vd, int32_t *itd, double *mmd) {
+                         int64_t fb = 0;
+                         const tpf_status r = tpf_solve_learned(hd, net, cols, Sd, Vd, itd, mmd, &o, &fb, stream);
+                         fallback += fb;
+                         return r;
+                     });
+    if (fallback_out) *fallback_out = fallback;
+    return st;
 }
 
 tpf_status tpf_selftest_gemm(int M, int N, int K, const void *A_re, const void *A_im, const void *B_re,

@@ -27,7 +27,7 @@ EXPORTS = (
     "tpf_selftest_gemm_wait", "tpf_solve_fp64_noalloc",
     "tpf_mlp_create", "tpf_mlp_destroy", "tpf_mlp_param_count", "tpf_mlp_get_params", "tpf_mlp_set_params",
     "tpf_mlp_fit_normalization", "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients",
-    "tpf_mlp_predict", "tpf_solve_learned",
+    "tpf_mlp_predict", "tpf_solve_learned", "tpf_solve_learned_host",
 )
 
 # Size of the built-in scratch array of tpf_solve_fp64_noalloc (include/tpf.h).
@@ -147,6 +147,8 @@ def lib(build_if_missing: bool = False):
     L.tpf_solve_learned.argtypes = [vp, vp, ctypes.c_int64, vp, vp, vp, vp, ctypes.POINTER(Opts),
                                     ctypes.POINTER(ctypes.c_int64), vp]
     L.tpf_solve_learned.restype = ctypes.c_int
+    L.tpf_solve_learned_host.argtypes = L.tpf_solve_learned.argtypes
+    L.tpf_solve_learned_host.restype = ctypes.c_int
     for name in ("tpf_mlp_create", "tpf_mlp_get_params", "tpf_mlp_set_params", "tpf_mlp_fit_normalization",
                  "tpf_mlp_get_normalization", "tpf_mlp_train_step", "tpf_mlp_gradients", "tpf_mlp_predict"):
         getattr(L, name).restype = ctypes.c_int
@@ -475,6 +477,40 @@ class Feeder:
         if check and st not in (OK, ENOCONV):
             raise TpfError(st, "tpf_solve_learned")
         return V, iters, mismatch, fb.value, st
+
+    def solve_learned_host(self, net, S, tol=1e-10, max_iter=100, switch_tol=1e-4, stream=None, out=None,
+                           check=True, profile=False):
+        """tpf_solve_learned_host on host arrays (numpy or pinned torch CPU tensors, complex128
+        [T][n_pq]): the learned-start solve with the host-to-device copies, the solve and the copies
+        back pipelined inside the library.  Returns (V, iters, mismatch, fallback columns, status)."""
+        T = S.shape[0]
+        _host_buffer(S, "S", np.complex128, (T, self.n_pq))
+        if net.n_pq != self.n_pq:
+            raise ValueError(f"the network is for {net.n_pq} demand buses, the feeder has {self.n_pq}")
+        if out is None:
+            V = np.empty((T, self.n_pq), dtype=np.complex128)
+            it = np.empty(T, dtype=np.int32)
+            mm = np.empty(T, dtype=np.float64)
+        else:
+            V, it, mm = out
+            _host_buffer(V, "V", np.complex128, (T, self.n_pq))
+            _host_buffer(it, "iters", np.int32, (T,))
+            _host_buffer(mm, "mismatch", np.float64, (T,))
+
+        def ptr(a):
+            return ctypes.c_void_p(a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data)
+
+        dev = getattr(self, "device", None)
+        if dev is not None and getattr(net, "device", dev) != dev:
+            raise ValueError(f"the network is on cuda:{net.device}, the feeder on cuda:{dev}")
+        o = make_opts("mixed", tol, max_iter, "warm", switch_tol, profile, "sparse")
+        fb = ctypes.c_int64(0)
+        with _on_device(dev):
+            st = lib().tpf_solve_learned_host(self._h, net._h, T, ptr(S), ptr(V), ptr(it), ptr(mm), ctypes.byref(o),
+                                              ctypes.byref(fb), _stream_ptr(stream, dev))
+        if check and st not in (OK, ENOCONV):
+            raise TpfError(st, "tpf_solve_learned_host")
+        return V, it, mm, fb.value, st
 
     def solve_tensor(self, S, V=None, want_V=True, v_complex64=None, v_band=(0.95, 1.05), bus_counts=None,
                      tol=1e-10, max_iter=100, start=None, switch_tol=1e-4, stream=None, check=True, profile=False):

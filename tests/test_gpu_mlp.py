@@ -293,6 +293,48 @@ def test_fused_prediction_with_several_tiles_per_cta(cuda, feeder200, hidden, la
     net.close()
 
 
+def test_learned_host_solve_matches_the_device_solve(cuda, feeder200):
+    """tpf_solve_learned_host (host buffers, copies and chunked solves pipelined in the library):
+    70,000 columns go in four chunks, and every column's V, sweep count and mismatch equal the
+    device-resident tpf_solve_learned's bit for bit (a column's prediction and solve do not depend on
+    the other columns); sampled columns match the oracle within 1e-8 pu; the fallback counts agree."""
+    import torch
+
+    f, c = feeder200
+    fd = tpf.Feeder.from_inputs(f)
+    S_fit = G.load_tensor(f, 4096, 9)
+    V_fit, _, _ = c.solve(S_fit, tol=1e-12)
+    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=128, seed=5)
+    net.fit_normalization(_dev(S_fit), _dev(V_fit))
+    rng = np.random.default_rng(23)
+    sizes = net.sizes
+    Ws = [rng.uniform(-1, 1, (sizes[i + 1], sizes[i])) * np.sqrt(6.0 / (sizes[i] + sizes[i + 1]))
+          for i in range(len(sizes) - 1)]
+    bs = [rng.normal(0, 0.05, sizes[i + 1]) for i in range(len(sizes) - 1)]
+    Ws[-1] *= 0.05
+    net.set_params(np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(Ws, bs)]).astype(np.float32))
+    T = 70_000
+    S = G.load_tensor(f, T, 11)
+    Sh = torch.from_numpy(S).pin_memory()
+    Vh, ith, mmh, fb_h, st_h = fd.solve_learned_host(net, Sh, tol=1e-10)
+    assert st_h == tpf.OK
+    assert fd.stats()["converged"] == T
+    V, it, mm, fb, st = fd.solve_learned(net, _dev(S), tol=1e-10)
+    assert st == tpf.OK and fb_h == fb
+    assert np.array_equal(Vh, V.cpu().numpy())
+    assert np.array_equal(ith, it.cpu().numpy())
+    assert np.array_equal(mmh, mm.cpu().numpy())
+    idx = np.sort(rng.choice(T, 256, replace=False))
+    Vo, ito, _ = c.solve(S[idx], tol=1e-13)
+    assert np.abs(Vh[idx] - Vo).max() <= 1e-8
+    # Empty input.
+    _, _, _, fb0, st0 = fd.solve_learned_host(net, S[:0])
+    assert st0 == tpf.OK and fb0 == 0
+    net.close()
+    fd.close()
+    torch.cuda.synchronize()
+
+
 def test_learned_solve_matches_the_oracle(cuda, feeder200):
     """tpf_solve_learned (fused prediction into complex64 starting voltages, then the sparse mixed
     solve from them): the oracle's solution within 1e-8 pu, fewer sweeps than the flat start, no

@@ -218,6 +218,18 @@ def test_entry_points_refuse_null_handles_and_bad_arguments_on_the_host(tpf_lib)
     assert L.tpf_mlp_predict(None, 8, p, p, None, None) == E
     L.tpf_mlp_destroy(None)
 
+    # The learned-start solve from host buffers: handles, sizes and options before any device call.
+    fb = ctypes.c_int64(7)
+    assert L.tpf_solve_learned_host(None, p, 8, p, p, None, None, ctypes.byref(o), ctypes.byref(fb), None) == E
+    assert fb.value == 0
+    assert L.tpf_solve_learned_host(p, None, 8, p, p, None, None, ctypes.byref(o), None, None) == E
+    assert L.tpf_solve_learned_host(p, p, -1, p, p, None, None, ctypes.byref(o), None, None) == E
+    assert L.tpf_solve_learned_host(p, p, 8, p, p, None, None, ctypes.byref(bad), None, None) == E
+    dense = tpf.make_opts("mixed", 1e-10, 100, "warm", 1e-4, False, "dense")
+    assert L.tpf_solve_learned_host(p, p, 8, p, p, None, None, ctypes.byref(dense), None, None) == tpf.EUNSUPPORTED
+    fp64 = tpf.make_opts("fp64", 1e-10, 100, "warm", 1e-4, False, "sparse")
+    assert L.tpf_solve_learned_host(p, p, 8, p, p, None, None, ctypes.byref(fp64), None, None) == tpf.EUNSUPPORTED
+
 
 def test_solve_host_checks_its_host_buffers_before_the_library():
     """tpf_solve_host reads and writes T x n_pq complex128 values: the binding refuses buffers of

@@ -63,8 +63,8 @@ GEMM_TRAFFIC_BYTES_PER_COLUMN = (203.725056e6 + 75.471360e6) / 16384
 # step's solve): 1,313.9 MB read (S and the half-precision prediction) + 1,002.9 MB written for
 # 65,536 columns of the 1,000-bus feeder.
 TREE_TRAFFIC_BYTES_PER_COLUMN = (1313.903e6 + 1002.918e6) / 65536
-# From the flat start: not captured for the current build of the kernel (null in the line).
-TREE_FLAT_TRAFFIC_BYTES_PER_COLUMN = None
+# From the flat start: 262.1 MB read + 210.0 MB written for the first 16,384 columns of the year.
+TREE_FLAT_TRAFFIC_BYTES_PER_COLUMN = (262.051328e6 + 209.968640e6) / 16384
 # Algorithmic FP32 flop per bus per sweep of the tree formulation: load current conj(S/V) 12,
 # prefix sum 2, subtree difference 2, z L 6, subtree-end subtraction 2, path prefix 2, update 4,
 # |step|^2 and max 6.
@@ -888,8 +888,10 @@ def main():
                 "peak_source": f"FP32: {sm_count} SMs x 128 lanes x 2 flop x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz",
                 "flops_note": f"{TREE_FLOPS_PER_BUS_SWEEP} flop per bus per sweep x {n} buses x {sweeps:,} "
                               "column-sweeps (anchors and the final residual not counted)",
-                "traffic_note": "ncu DRAM bytes per column (capture of 16,384 columns of the 1,000-bus feeder) "
-                                "x columns per launch",
+                "traffic_note": ("ncu DRAM bytes per column (capture of the first 16,384 columns of the 1,000-bus "
+                                 "year, flat start)" if per_column == TREE_FLAT_TRAFFIC_BYTES_PER_COLUMN else
+                                 "ncu DRAM bytes per column (capture of 65,536 columns of the 1,000-bus year from "
+                                 "the learned start)") + " x columns per launch",
                 "hbm_frac": (per_column or 0) * T / (run["kernel_ms"] / 1e3) / 1e9 / float(peaks.get("hbm_gbs", 6800.0))
                             if per_column else None,
                 "share_of_step": run["kernel_ms"] * len(run["step_ms"]) / sum(run["step_ms"]),

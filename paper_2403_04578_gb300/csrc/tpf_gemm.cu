@@ -370,17 +370,14 @@ bool make_gemm_maps(GemmMaps *maps, const void *Ar, const void *Ai, int M, int K
 
 tpf_status launch_gemm(const GemmMaps &maps, int m_tiles, int64_t n_tiles, int n_chunks, const GemmEpi &ep,
                        cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem) !=
-                cudaSuccess ||
-            cudaFuncSetAttribute(tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem) !=
-                cudaSuccess) {
-            cudaGetLastError();
-            return TPF_ECUDA;
-        }
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    if (!once_per_device(attr, [] {
+            return cudaFuncSetAttribute(tc_gemm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem) ==
+                       cudaSuccess &&
+                   cudaFuncSetAttribute(tc_gemm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kGemmSmem) ==
+                       cudaSuccess;
+        }))
+        return TPF_ECUDA;
     if (ep.cplx ? ep.mode == 2 : ep.mode == 1) return TPF_EINVAL;
     if (ep.mode == 2 && (!ep.bias || (!ep.Dr && !ep.Ab))) return TPF_EINVAL;
     int dev = 0, sms = 0;

@@ -1,6 +1,7 @@
 // Internal declarations shared by the host and device translation units of libtpf.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <vector>
 
@@ -20,6 +21,26 @@ constexpr int kTileM = 128;
 constexpr int kTileN = 128;
 
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+// Runs set() (a kernel attribute, which is per device) once for the current device: `done` holds
+// one bit per device, devices past the 64th run it every time.  False when set() or the device
+// query fails (the CUDA error is cleared).
+template <class F>
+bool once_per_device(std::atomic<uint64_t> &done, F set) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const uint64_t bit = dev >= 0 && dev < 64 ? 1ull << dev : 0;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return true;
+    if (!set()) {
+        cudaGetLastError();
+        return false;
+    }
+    done.fetch_or(bit, std::memory_order_relaxed);
+    return true;
+}
 
 // Sparse formulation: demand buses per thread (2, 4 or 8; 16 for the large-feeder kernel, whose
 // D, S and z live in a device scratch), largest block, and the block size for n demand buses with

@@ -592,14 +592,11 @@ bool infer_supported(int L, int H, int P0, int PL) {
 }
 
 tpf_status launch_infer(const InferArgs &g, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        if (cudaFuncSetAttribute(mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem) != cudaSuccess) {
-            cudaGetLastError();
-            return TPF_ECUDA;
-        }
-        attr = true;
-    }
+    static std::atomic<uint64_t> attr{0};
+    if (!once_per_device(attr, [] {
+            return cudaFuncSetAttribute(mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmem) == cudaSuccess;
+        }))
+        return TPF_ECUDA;
     if (g.tiles <= 0) return TPF_OK;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {

@@ -301,16 +301,13 @@ __global__ void __launch_bounds__(kResThreads) mx_residual(PrologueArgs a, Final
 
 template <bool FINAL>
 tpf_status launch(const PrologueArgs &a, const FinalArgs &fo, int64_t cols, cudaStream_t st) {
-    static bool attr = false;
+    static std::atomic<uint64_t> attr{0};
     const size_t smem = (size_t)2 * kCPB * a.n_pad * sizeof(float2);
-    if (!attr) {
-        if (cudaFuncSetAttribute(mx_residual<FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            return TPF_ECUDA;
-        }
-        attr = true;
-    }
+    if (!once_per_device(attr, [] {
+            return cudaFuncSetAttribute(mx_residual<FINAL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) ==
+                   cudaSuccess;
+        }))
+        return TPF_ECUDA;
     const int64_t blocks = (cols + kCPB - 1) / kCPB;
     mx_residual<FINAL><<<(unsigned)blocks, kResThreads, smem, st>>>(a, fo);
     if (cudaGetLastError() != cudaSuccess) return TPF_ECUDA;

@@ -335,6 +335,45 @@ def test_learned_host_solve_matches_the_device_solve(cuda, feeder200):
     torch.cuda.synchronize()
 
 
+def test_learned_solve_with_infeasible_and_non_finite_columns(cuda, feeder200):
+    """Bad columns through the learned start: a load far beyond the feeder's loadability, a NaN, a
+    load of 1e300 (beyond FP32: the converter's infinity) and an infinite one.  The NaN and infinite
+    predictions fail the |V| band and start flat; every bad column is reported unconverged
+    (-max_iter, TPF_ENOCONV); the other columns match the oracle."""
+    f, c = feeder200
+    fd = tpf.Feeder.from_inputs(f)
+    S_fit = G.load_tensor(f, 4096, 9)
+    V_fit, _, _ = c.solve(S_fit, tol=1e-12)
+    net = tpf.LearnedStart(f.n_pq, hidden=256, hidden_layers=3, max_batch=128, seed=5)
+    net.fit_normalization(_dev(S_fit), _dev(V_fit))
+    rng = np.random.default_rng(31)
+    sizes = net.sizes
+    Ws = [rng.uniform(-1, 1, (sizes[i + 1], sizes[i])) * np.sqrt(6.0 / (sizes[i] + sizes[i + 1]))
+          for i in range(len(sizes) - 1)]
+    bs = [rng.normal(0, 0.05, sizes[i + 1]) for i in range(len(sizes) - 1)]
+    Ws[-1] *= 0.05
+    net.set_params(np.concatenate([np.concatenate([w.ravel(), b]) for w, b in zip(Ws, bs)]).astype(np.float32))
+    S = G.load_tensor(f, 4096, 12).copy()
+    bad = [3, 10, 20, 30]
+    S[3] *= 400.0
+    S[10, 5] = np.nan
+    S[20, 7] = 1e300
+    S[30, 0] = np.inf
+    V, it, mm, fallback, st = fd.solve_learned(net, _dev(S), tol=1e-10, max_iter=60)
+    assert st == tpf.ENOCONV
+    itc = it.cpu().numpy()
+    assert all(itc[k] == -60 for k in bad), itc[bad]
+    assert fallback >= 3  # the NaN, 1e300 and infinite columns at least
+    assert fd.stats()["converged"] == 4096 - len(bad)
+    good = np.setdiff1d(np.arange(4096), bad)
+    idx = good[:: 16]
+    Vo, _, _ = c.solve(S[idx], tol=1e-13)
+    assert np.abs(V.cpu().numpy()[idx] - Vo).max() <= 1e-8
+    assert np.all(itc[good] > 0)
+    net.close()
+    fd.close()
+
+
 def test_learned_solve_matches_the_oracle(cuda, feeder200):
     """tpf_solve_learned (fused prediction into complex64 starting voltages, then the sparse mixed
     solve from them): the oracle's solution within 1e-8 pu, fewer sweeps than the flat start, no

@@ -113,6 +113,18 @@ __device__ __forceinline__ float fmax_nan(float a, float b) {
     asm("max.NaN.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
     return r;
 }
+// Maximum over the 32 lanes of a warp, returned to every lane, in one warp-wide reduction
+// (redux.sync on FP32, sm_100 family): the NaN-propagating form, and the form that ignores NaN.
+__device__ __forceinline__ float warp_max_nan(float v) {
+    float r;
+    asm volatile("redux.sync.max.NaN.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float warp_max(float v) {
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
+}
 __device__ __forceinline__ float4 pack(c2 v) { return make_float4(v.re.h, v.re.l, v.im.h, v.im.l); }
 __device__ __forceinline__ c2 unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
 
@@ -593,18 +605,12 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
                 const float4 tw = lane < nwarps ? wtm[lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
                 if (pending) {
                     pending = false;
-                    // Max over lanes 0 .. nwarps - 1 (the warps' maxima; a NaN stays NaN) into lane 0,
-                    // then lane 0's value for every lane: the decision below must be the same in every
-                    // thread of the block, or threads would leave the sweep loop while others wait at
-                    // a barrier.  max |delta| only counts on a blind anchor.
-                    float2 dm = make_float2(tw.z, tw.w);
-#pragma unroll
-                    for (int o = 1; o < nwarps; o <<= 1) dm.x = fmax_nan(dm.x, __shfl_xor_sync(kFull, dm.x, o));
-                    dm.x = __shfl_sync(kFull, dm.x, 0);
-#pragma unroll
-                    for (int o = 1; o < nwarps; o <<= 1) dm.y = fmaxf(dm.y, __shfl_xor_sync(kFull, dm.y, o));
-                    dm.y = __shfl_sync(kFull, dm.y, 0);
-                    decide(dm);
+                    // Max over lanes 0 .. nwarps - 1 (the warps' maxima; a NaN stays NaN), one warp-wide
+                    // reduction whose result every lane receives: the decision below must be the same
+                    // in every thread of the block, or threads would leave the sweep loop while others
+                    // wait at a barrier.  Lanes past nwarps hold 0, below every squared step, so the
+                    // reduction runs over all 32 lanes.  max |delta| only counts on a blind anchor.
+                    decide(make_float2(warp_max_nan(tw.z), warp_max(tw.w)));
                     if (done || anchor_now) continue;
                 }
                 off = add2(warps_before(make_float2(tw.x, tw.y), lane, warp, nwarps),
@@ -700,11 +706,7 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
                 mx.x = fmax_nan(mx.x, abs2(step));
             }
         }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx.x = fmax_nan(mx.x, __shfl_xor_sync(kFull, mx.x, o));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) mx.y = fmaxf(mx.y, __shfl_xor_sync(kFull, mx.y, o));
-        wmx = mx;
+        wmx = make_float2(warp_max_nan(mx.x), warp_max(mx.y));
         pending = true;
     }
 
@@ -810,13 +812,8 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
             if (over && a.bus_over) atomicAdd(&a.bus_over[a.col[s]], 1);
         }
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        red.x = fmaxf(red.x, __shfl_xor_sync(kFull, red.x, o));
-        red.y = fmaxf(red.y, __shfl_xor_sync(kFull, red.y, o));
-        red.z = fmaxf(red.z, __shfl_xor_sync(kFull, red.z, o));
-        red.w += __shfl_xor_sync(kFull, red.w, o);
-    }
+    red = make_float4(warp_max(red.x), warp_max(red.y), warp_max(red.z),
+                      (float)__reduce_add_sync(kFull, (unsigned)red.w));
     if (lane == 0) wm[warp] = red;
     __syncthreads();
     if (tid == 0) {

@@ -103,10 +103,14 @@ __device__ __forceinline__ int phase_of(int ec) { return (int)((unsigned)ec >> 3
 
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// The FP32 products below are written with explicitly rounded intrinsics, so that the compiler
+// cannot contract them differently in different instantiations of the kernel: every kernel then
+// rounds a given formula the same way (ZIP loads with alpha_P = 1 reproduce constant power bit for
+// bit, whatever code surrounds the formula).
 __device__ __forceinline__ float2 cmul2(float2 a, float2 b) {
-    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+    return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
-__device__ __forceinline__ float abs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float abs2(float2 a) { return __fmaf_rn(a.x, a.x, __fmul_rn(a.y, a.y)); }
 // max(a, b) that returns NaN if either is NaN (fmaxf returns the other operand).
 __device__ __forceinline__ float fmax_nan(float a, float b) {
     float r;
@@ -131,16 +135,17 @@ __device__ __forceinline__ c2 unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}
 // conj(s / v) in FP32 with the hardware reciprocal (sweeps: their rounding is far below what the
 // FP32 phase resolves, and the anchored corrections are small differences).
 __device__ __forceinline__ float2 current_fast(float2 v, float2 s) {
-    const float inv = __fdividef(1.0f, v.x * v.x + v.y * v.y);
-    return make_float2((s.x * v.x + s.y * v.y) * inv, (s.x * v.y - s.y * v.x) * inv);
+    const float inv = __fdividef(1.0f, abs2(v));
+    return make_float2(__fmul_rn(__fmaf_rn(s.x, v.x, __fmul_rn(s.y, v.y)), inv),
+                       __fmul_rn(__fmaf_rn(s.x, v.y, -__fmul_rn(s.y, v.x)), inv));
 }
 // conj(s / (v + d)) - conj(s / v) = -conj(s d / ((v + d) v)), FP32 with the hardware reciprocal.
 __device__ __forceinline__ float2 delta_current_fast(float2 v, float2 d, float2 s) {
-    const float2 w = make_float2(s.x * d.x - s.y * d.y, s.x * d.y + s.y * d.x);
-    const float2 vp = make_float2(v.x + d.x, v.y + d.y);
-    const float2 q = make_float2(vp.x * v.x - vp.y * v.y, vp.x * v.y + vp.y * v.x);
-    const float inv = __fdividef(1.0f, q.x * q.x + q.y * q.y);
-    return make_float2(-(w.x * q.x + w.y * q.y) * inv, (w.y * q.x - w.x * q.y) * inv);
+    const float2 w = cmul2(s, d);
+    const float2 q = cmul2(add2(v, d), v);
+    const float inv = __fdividef(1.0f, abs2(q));
+    return make_float2(-__fmul_rn(__fmaf_rn(w.x, q.x, __fmul_rn(w.y, q.y)), inv),
+                       __fmul_rn(__fmaf_rn(w.y, q.x, -__fmul_rn(w.x, q.y)), inv));
 }
 
 // Demand current of Eq. 3 with ZIP loads, i_d = alpha_P conj(s / v) + alpha_I conj(s) +
@@ -150,15 +155,16 @@ template <bool kZip>
 __device__ __forceinline__ float2 demand_current(float2 v, float2 s, float4 al) {
     const float2 c = current_fast(v, s);
     if (!kZip) return c;
-    const float2 cs_v = make_float2(s.x * v.x + s.y * v.y, s.x * v.y - s.y * v.x);  // conj(s) v
-    return make_float2(al.x * c.x + al.y * s.x + al.z * cs_v.x, al.x * c.y - al.y * s.y + al.z * cs_v.y);
+    const float2 cs_v = cmul2(make_float2(s.x, -s.y), v);  // conj(s) v
+    return make_float2(__fmaf_rn(al.x, c.x, __fmaf_rn(al.y, s.x, __fmul_rn(al.z, cs_v.x))),
+                       __fmaf_rn(al.x, c.y, __fmaf_rn(-al.y, s.y, __fmul_rn(al.z, cs_v.y))));
 }
 template <bool kZip>
 __device__ __forceinline__ float2 demand_change(float2 v, float2 d, float2 s, float4 al) {
     const float2 c = delta_current_fast(v, d, s);
     if (!kZip) return c;
-    const float2 cs_d = make_float2(s.x * d.x + s.y * d.y, s.x * d.y - s.y * d.x);  // conj(s) d
-    return make_float2(al.x * c.x + al.z * cs_d.x, al.x * c.y + al.z * cs_d.y);
+    const float2 cs_d = cmul2(make_float2(s.x, -s.y), d);  // conj(s) d
+    return make_float2(__fmaf_rn(al.x, c.x, __fmul_rn(al.z, cs_d.x)), __fmaf_rn(al.x, c.y, __fmul_rn(al.z, cs_d.y)));
 }
 
 // Sum of the warp totals of the warps before `warp`: lane l holds the total of warp l (lanes past
@@ -182,8 +188,9 @@ __device__ __forceinline__ float2 block_scan(float2 v, float2 *wt, int lane, int
         const float ux = __shfl_up_sync(kFull, inc.x, o), uy = __shfl_up_sync(kFull, inc.y, o);
         if (lane >= o) inc = add2(make_float2(ux, uy), inc);
     }
-    const float ex = __shfl_up_sync(kFull, inc.x, 1), ey = __shfl_up_sync(kFull, inc.y, 1);
-    const float2 off = lane ? make_float2(ex, ey) : make_float2(0.0f, 0.0f);
+    // The lane's exclusive value as its inclusive value minus its own (one rounding, one shuffle
+    // fewer than taking the neighbour's inclusive value).
+    const float2 off = lane ? make_float2(inc.x - v.x, inc.y - v.y) : make_float2(0.0f, 0.0f);
     if (lane == 31) wt[warp] = inc;
     __syncthreads();
     return add2(warps_before(wt[lane < kMaxWarps ? lane : 0], lane, warp, nw), off);
@@ -580,16 +587,25 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
         for (int j = 0; j < kBPT; ++j) loc[j] = off;
         if (!zero_sweep) {
             // Load currents (or their change from V_ref) and their inclusive prefix sums P.
+            // (Two loops behind one block-uniform branch, so that only one of the two current
+            // formulas is evaluated.)
             float2 run = make_float2(0.0f, 0.0f);
+            if (anchored) {
 #pragma unroll
-            for (int j = 0; j < kBPT; ++j) {
-                const float4 cs = C[j * th + tid];
-                const float2 sh = make_float2(cs.x, cs.y);
-                const float4 al = kZip ? Zs[j * th + tid] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
-                const float2 I = anchored ? demand_change<kZip>(vr[j], dl[j], sh, al)
-                                          : demand_current<kZip>(vr[j], sh, al);
-                run = add2(run, I);  // positions past n have S = 0 and add nothing
-                loc[j] = run;
+                for (int j = 0; j < kBPT; ++j) {
+                    const float4 cs = C[j * th + tid];
+                    const float4 al = kZip ? Zs[j * th + tid] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+                    run = add2(run, demand_change<kZip>(vr[j], dl[j], make_float2(cs.x, cs.y), al));
+                    loc[j] = run;  // positions past n have S = 0 and add nothing
+                }
+            } else {
+#pragma unroll
+                for (int j = 0; j < kBPT; ++j) {
+                    const float4 cs = C[j * th + tid];
+                    const float4 al = kZip ? Zs[j * th + tid] : make_float4(1.0f, 0.0f, 0.0f, 0.0f);
+                    run = add2(run, demand_current<kZip>(vr[j], make_float2(cs.x, cs.y), al));
+                    loc[j] = run;
+                }
             }
             {
                 // First scan; its barrier also finishes the previous sweep's block max.
@@ -599,7 +615,7 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
                     const float ux = __shfl_up_sync(kFull, inc.x, o), uy = __shfl_up_sync(kFull, inc.y, o);
                     if (lane >= o) inc = add2(make_float2(ux, uy), inc);
                 }
-                const float ex = __shfl_up_sync(kFull, inc.x, 1), ey = __shfl_up_sync(kFull, inc.y, 1);
+                const float ex = inc.x - run.x, ey = inc.y - run.y;  // exclusive: inclusive minus own
                 if (lane == 31) wtm[warp] = make_float4(inc.x, inc.y, wmx.x, wmx.y);
                 __syncthreads();
                 const float4 tw = lane < nwarps ? wtm[lane] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
@@ -686,24 +702,27 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
         }
         // max |step|^2 (NaN if any step is NaN), and on a blind anchor max |delta|^2
         float2 mx = make_float2(0.0f, 0.0f);
+        if (anchored) {
 #pragma unroll
-        for (int j = 0; j < kBPT; ++j) {
-            const int q = base + j, s = j * th + tid;
-            if (q < n) {
-                const float2 ps = add2(off, loc[j]);
-                float2 step;
-                if (anchored) {
+            for (int j = 0; j < kBPT; ++j) {
+                const int q = base + j, s = j * th + tid;
+                if (q < n) {
                     const float4 D = B[s];
-                    const float2 nd = add2(sub2(make_float2(D.x, D.y), ps), make_float2(D.z, D.w));
-                    step = sub2(nd, dl[j]);
+                    const float2 nd = add2(sub2(make_float2(D.x, D.y), add2(off, loc[j])), make_float2(D.z, D.w));
+                    mx.x = fmax_nan(mx.x, abs2(sub2(nd, dl[j])));
                     dl[j] = nd;
                     mx.y = fmaxf(mx.y, abs2(nd));
-                } else {
-                    const float2 nv = sub2(kPh == 1 ? a.vs_f : a.vs_fp[phase_of(ecnt[j])], ps);
-                    step = sub2(nv, vr[j]);
+                }
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kBPT; ++j) {
+                const int q = base + j;
+                if (q < n) {
+                    const float2 nv = sub2(kPh == 1 ? a.vs_f : a.vs_fp[phase_of(ecnt[j])], add2(off, loc[j]));
+                    mx.x = fmax_nan(mx.x, abs2(sub2(nv, vr[j])));
                     vr[j] = nv;
                 }
-                mx.x = fmax_nan(mx.x, abs2(step));
             }
         }
         wmx = make_float2(warp_max_nan(mx.x), warp_max(mx.y));

@@ -204,6 +204,16 @@ __device__ __forceinline__ f2 qadd(f2 a, f2 b) {
     return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
 }
 __device__ __forceinline__ f2 qneg(f2 a) { return {-a.h, -a.l}; }
+// The sum without the final renormalisation: the high part is the rounded sum of the high parts,
+// the low part collects their exact rounding error and the low parts.  Inside a scan, where a
+// handful of such sums follow one another, the low part stays within a few ulp of the high part;
+// qnorm restores |l| <= ulp(h) / 2 at the end.
+__device__ __forceinline__ f2 qadd_lazy(f2 a, f2 b) {
+    const f2 s = two_sum(a.h, b.h);
+    return {s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l))};
+}
+__device__ __forceinline__ c2 cqadd_lazy(c2 a, c2 b) { return {qadd_lazy(a.re, b.re), qadd_lazy(a.im, b.im)}; }
+__device__ __forceinline__ c2 cqnorm(c2 a) { return {fast_two_sum(a.re.h, a.re.l), fast_two_sum(a.im.h, a.im.l)}; }
 __device__ __forceinline__ c2 cqadd(c2 a, c2 b) { return {qadd(a.re, b.re), qadd(a.im, b.im)}; }
 __device__ __forceinline__ c2 cqsub(c2 a, c2 b) { return {qadd(a.re, qneg(b.re)), qadd(a.im, qneg(b.im))}; }
 // a * b, both double-float complex.
@@ -248,8 +258,9 @@ __device__ __forceinline__ c2 block_scan_dd(c2 v, float4 *wt, int lane, int warp
         u.y = __shfl_up_sync(kFull, u.y, o);
         u.z = __shfl_up_sync(kFull, u.z, o);
         u.w = __shfl_up_sync(kFull, u.w, o);
-        if (lane >= o) inc = cqadd(unpack(u), inc);
+        if (lane >= o) inc = cqadd_lazy(unpack(u), inc);
     }
+    inc = cqnorm(inc);
     float4 e = pack(inc);
     e.x = __shfl_up_sync(kFull, e.x, 1);
     e.y = __shfl_up_sync(kFull, e.y, 1);
@@ -267,8 +278,9 @@ __device__ __forceinline__ c2 block_scan_dd(c2 v, float4 *wt, int lane, int warp
         u.y = __shfl_up_sync(kFull, tw.y, o);
         u.z = __shfl_up_sync(kFull, tw.z, o);
         u.w = __shfl_up_sync(kFull, tw.w, o);
-        if (lane >= o) tw = pack(cqadd(unpack(u), unpack(tw)));
+        if (lane >= o) tw = pack(cqadd_lazy(unpack(u), unpack(tw)));
     }
+    tw = pack(cqnorm(unpack(tw)));
     const int src = warp ? warp - 1 : 0;
     tw.x = __shfl_sync(kFull, tw.x, src);
     tw.y = __shfl_sync(kFull, tw.y, src);
@@ -290,14 +302,14 @@ __device__ __forceinline__ int next_slot(int s, int th) {
 
 // First part of an anchor, in double-float.  On entry A[s] = (S_hi) and B[s] = (V_ref, S_lo) for
 // the thread's own slots.  Leaves in B the inclusive prefix sums of the path terms and returns the
-// thread's exclusive scan offset.  ecnt holds the thread's ends-list bounds, s_rng the subtree
+// thread's exclusive scan offset.  ecnt holds the thread's ends-list bounds, s_rk the subtree
 // ranges (as in the kernel).
 // The loops run over shared memory only and are not unrolled: the anchor runs once or twice per
 // column and its code stays small; the unrolled staging in the kernel keeps the device-memory
 // loads in flight together.
 template <int kBPT, bool kZip, int kPh>
-__device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B, const short *s_rng,
-                                        const short *s_kidx, const float4 *Zs, const int *ecnt, float4 *wtd,
+__device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B, const int *s_rk,
+                                        const float4 *Zs, const int *ecnt, float4 *wtd,
                                         int tid, int th, int lane, int warp) {
     const int n = a.n, base = tid * kBPT;
     // Load currents at V_ref and their inclusive prefix sums.
@@ -335,12 +347,12 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
         const int q = base + j, s = j * th + tid;
         if (q < n) {
             if (kPh == 1) {
-                c2 L = unpack(A[s_rng[s]]);
+                c2 L = unpack(A[s_rk[s] & 0xffff]);
                 if (q > 0) L = cqsub(L, unpack(A[j ? s - th : (kBPT - 1) * th + tid - 1]));
                 const float4 zq = B[s];
                 B[s] = pack(cqmul(c2{{zq.x, zq.z}, {zq.y, zq.w}}, L));
             } else {
-                const int p = q / a.nbp, qb = q - p * a.nbp, eb = s_rng[s] - p * a.nbp;
+                const int p = q / a.nbp, qb = q - p * a.nbp, eb = (s_rk[s] & 0xffff) - p * a.nbp;
                 c2 x = {{0.0f, 0.0f}, {0.0f, 0.0f}};
                 for (int pp = 0; pp < kPh; ++pp) {
                     c2 L = unpack(A[slot_of<kBPT>(pp * a.nbp + eb - 1, th)]);
@@ -358,7 +370,7 @@ __device__ __forceinline__ c2 anchor_dd(const TreeWork &a, float4 *A, float4 *B,
     // contiguous.
 #pragma unroll
     for (int j = 0; j < kBPT; ++j) {
-        const int s = j * th + tid, k = s_kidx[s];
+        const int s = j * th + tid, k = s_rk[s] >> 16;
         if (k >= 0) A[k] = B[s];
     }
     __syncthreads();
@@ -418,10 +430,13 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
     // [ns] the subtree's range [q, end_q): one phase, the slot of its last position end_q - 1 (the
     // slot itself for a leaf); polyphase, end_q.  (The polyphase impedance rows stay in device
     // memory, read through the cache: in shared memory they would halve the resident blocks.)
-    short *const s_rng = reinterpret_cast<short *>(tsm + (kBig ? 1 : (kZip ? 4 : 3)) * ns);
-    short *const s_par = s_rng + ns;                               // [ns] parent slot, -1 = the slack
-    // [ns] where each position's branch term goes in the ends-ordered copy of X (-1: nowhere)
-    short *const s_kidx = s_par + ns;
+    // [ns] per slot, bits 0-15: the subtree's range [q, end_q): one phase, the slot of its last
+    // position end_q - 1 (the slot itself for a leaf); polyphase, end_q.  Bits 16-31: where the
+    // position's branch term goes in the ends-ordered copy of X (-1: nowhere).  One word, so that a
+    // sweep reads both with one shared-memory load.  (The polyphase impedance rows stay in device
+    // memory, read through the cache: in shared memory they would halve the resident blocks.)
+    int *const s_rk = reinterpret_cast<int *>(tsm + (kBig ? 1 : (kZip ? 4 : 3)) * ns);
+    short *const s_par = reinterpret_cast<short *>(s_rk + ns);  // [ns] parent slot, -1 = the slack
     float2 *P = reinterpret_cast<float2 *>(A);  // [ns] inclusive prefix sums of the load currents
     float2 *X = P + ns;                           // [ns] branch terms z_q L_q; the residual's x at the end
     __shared__ float2 wt2[kMaxWarps];
@@ -437,9 +452,9 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
 #pragma unroll
     for (int j = 0; j < kBPT; ++j) {
         const int q = base + j, s = j * th + tid;
-        s_rng[s] = (short)(kPh > 1 ? a.end[s] : (q < n ? slot_of<kBPT>(a.end[s] - 1, th) : s));
+        const int rng = kPh > 1 ? a.end[s] : (q < n ? slot_of<kBPT>(a.end[s] - 1, th) : s);
+        s_rk[s] = (rng & 0xffff) | (a.kidx[s] << 16);
         s_par[s] = (short)a.par[s];
-        s_kidx[s] = (short)a.kidx[s];
     }
     // Per position: V_ref (or V before anchoring) and delta = V - V_ref in registers, the ends-list
     // bounds in registers, S and z in C.
@@ -566,7 +581,7 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
                 A[s] = make_float4(cs.x, cs.y, 0.0f, 0.0f);
                 B[s] = make_float4(re.h, im.h, b.x, b.y);
             }
-            const c2 off = anchor_dd<kBPT, kZip, kPh>(a, A, B, s_rng, s_kidx, Zs, ecnt, wtd, tid, th, lane, warp);
+            const c2 off = anchor_dd<kBPT, kZip, kPh>(a, A, B, s_rk, Zs, ecnt, wtd, tid, th, lane, warp);
 #pragma unroll
             for (int j = 0; j < kBPT; ++j) {
                 const int q = base + j, s = j * th + tid;
@@ -642,11 +657,11 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
             // Descending j: loc[j - 1] still holds the prefix value of position q - 1.
 #pragma unroll
             for (int j = kBPT - 1; j >= 0; --j) {
-                const int q = base + j, s = j * th + tid;
+                const int q = base + j, s = j * th + tid, rk = s_rk[s];
                 float2 xq = make_float2(0.0f, 0.0f);  // positions past n contribute nothing
                 if (q < n) {
                     if (kPh == 1) {
-                        const int ls = s_rng[s];  // slot of the subtree's last position (s for a leaf)
+                        const int ls = rk & 0xffff;  // slot of the subtree's last position (s for a leaf)
                         float2 L = ls == s ? loc[j] : P[ls];
                         if (j) L = sub2(L, loc[j - 1]);
                         else if (q > 0) L = sub2(L, P[(kBPT - 1) * th + tid - 1]);
@@ -654,7 +669,7 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
                         xq = cmul2(make_float2(cs.z, cs.w), L);
                     } else {
                         // x = sum over phases p' of Z[p][p'] L_{p'}
-                        const int p = phase_of(ecnt[j]), qb = q - p * a.nbp, eb = s_rng[s] - p * a.nbp;
+                        const int p = phase_of(ecnt[j]), qb = q - p * a.nbp, eb = (rk & 0xffff) - p * a.nbp;
 #pragma unroll
                         for (int pp = 0; pp < kPh; ++pp) {
                             float2 L = P[slot_of<kBPT>(pp * a.nbp + eb - 1, th)];
@@ -666,7 +681,7 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
                 }
                 // The branch term goes where the position that closes its range gathers it: X
                 // holds the terms in ends-list order, so each position's list is contiguous.
-                const int k = s_kidx[s];
+                const int k = rk >> 16;
                 if (k >= 0) X[k] = xq;
                 loc[j] = xq;
             }
@@ -805,18 +820,18 @@ __global__ void __maxnreg__(kBPT == 16 ? 168 : (kBPT == 8 ? 128 : (kBPT == 4 && 
             if (kPh == 1) {
                 // The first child is q + 1, each next one follows the previous one's last position;
                 // the child whose subtree ends where q's ends is the last.
-                const int lq = s_rng[s];
+                const int lq = s_rk[s] & 0xffff;
                 for (int ks = lq == s ? -1 : next_slot<kBPT>(s, th); ks >= 0;) {
                     r = add2(r, J[ks]);
-                    const int lc = s_rng[ks];
+                    const int lc = s_rk[ks] & 0xffff;
                     ks = lc == lq ? -1 : next_slot<kBPT>(lc, th);
                 }
             } else {
-                const int e = s_rng[s];
+                const int e = s_rk[s] & 0xffff;
                 for (int k = q + 1; k < e;) {
                     const int ks = slot_of<kBPT>(k, th);
                     r = add2(r, J[ks]);
-                    k = s_rng[ks];
+                    k = s_rk[ks] & 0xffff;
                 }
             }
             const float v2 = abs2(add2(vr[j], dl[j]));

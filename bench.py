@@ -60,11 +60,11 @@ METRIC = "PF solves/s at ≤1e-8 pu vs FP64 oracle: mixed+learned-start vs plain
 # columns each launch of this run processes.  None once the kernel has changed since the capture.
 GEMM_TRAFFIC_BYTES_PER_COLUMN = (203.725056e6 + 75.471360e6) / 16384
 # The same for the sparse tree kernel mx_tree started from the learned prediction (the headline
-# step's solve): 1,313.9 MB read (S and the half-precision prediction) + 1,002.9 MB written for
+# step's solve): 1,313.1 MB read (S and the half-precision prediction) + 1,002.8 MB written for
 # 65,536 columns of the 1,000-bus feeder.
-TREE_TRAFFIC_BYTES_PER_COLUMN = (1313.903e6 + 1002.918e6) / 65536
-# From the flat start: 262.1 MB read + 210.0 MB written for the first 16,384 columns of the year.
-TREE_FLAT_TRAFFIC_BYTES_PER_COLUMN = (262.051328e6 + 209.968640e6) / 16384
+TREE_TRAFFIC_BYTES_PER_COLUMN = (1313.136e6 + 1002.844e6) / 65536
+# From the flat start: 262.2 MB read + 210.6 MB written for the first 16,384 columns of the year.
+TREE_FLAT_TRAFFIC_BYTES_PER_COLUMN = (262.154496e6 + 210.563328e6) / 16384
 # Algorithmic FP32 flop per bus per sweep of the tree formulation: load current conj(S/V) 12,
 # prefix sum 2, subtree difference 2, z L 6, subtree-end subtraction 2, path prefix 2, update 4,
 # |step|^2 and max 6.

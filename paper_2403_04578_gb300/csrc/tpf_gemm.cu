@@ -8,8 +8,9 @@
 // streamed by TMA in the 128-byte swizzle that the MMA descriptors read.
 //
 // One persistent CTA per SM walks the tiles.  Warp 0 issues the TMA loads into a 3-slot ring,
-// warp 1 issues the MMAs, and warps 2-5 drain the accumulators.  TMEM holds two accumulator
-// stages (2 x 256 columns), so the epilogue of one tile overlaps the main loop of the next.
+// warp 1 issues the MMAs, and warps 2-9 drain the accumulators (two warps per TMEM lane quarter,
+// each taking half of the tile's columns).  TMEM holds two accumulator stages (2 x 256 columns),
+// so the epilogue of one tile overlaps the main loop of the next.
 // Every wait is bounded (2 s on %globaltimer by default): on expiry the CTA raises an error flag,
 // stops, waits for its own copies and MMAs (again bounded, 2 s), frees TMEM and returns.
 #include <cudaTypedefs.h>
@@ -28,7 +29,9 @@ namespace {
 using namespace tc;
 
 constexpr uint32_t kTileBytes = kTileM * kChunkK * 2;  // 16 KB: 128 rows x 64 16-bit elements
-constexpr int kGemmThreads = 192;                       // 6 warps
+constexpr int kEpiWarps = 8;                            // two per TMEM lane quarter
+constexpr int kEpiThreads = 32 * kEpiWarps;
+constexpr int kGemmThreads = 64 + kEpiThreads;          // TMA, MMA, epilogue warps
 constexpr size_t kGemmSmem = 1024 + 192 * 1024 + 2048;  // align slack + operand ring + barriers
 
 // Complex products stream four planes per K chunk (Ar, Ai, Br, Bi) into 3 slots and keep two
@@ -44,6 +47,16 @@ struct Cfg {
 __device__ __forceinline__ float pow2f_g(int e) {
     e = e < -126 ? -126 : (e > 127 ? 127 : e);
     return __int_as_float((127 + e) << 23);
+}
+
+// Barrier of the epilogue warps alone.
+__device__ __forceinline__ void epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory"); }
+
+// Maximum over the 32 lanes of a warp, returned to every lane (redux.sync on FP32).
+__device__ __forceinline__ float warp_max_f(float v) {
+    float r;
+    asm volatile("redux.sync.max.f32 %0, %1, 0xffffffff;" : "=f"(r) : "f"(v));
+    return r;
 }
 
 __device__ __forceinline__ bool tile_live(const GemmEpi &ep, int64_t n_tile) {
@@ -68,9 +81,11 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     uint64_t *done = tempty + 2;                                   // [1]        all MMAs retired
     uint32_t *tmem_slot = (uint32_t *)(done + 1);
     int *abort_flag = (int *)(tmem_slot + 1);
+    // Per column of the current tile (mode 1): the update's scale, 0 for a column that does not
+    // iterate and negative for an anchored one (whose offset from V_ref is updated); the largest
+    // |dV| over the tile's rows.
     float *col_scale = (float *)(abort_flag + 1);                  // [128]
-    int *col_flag = (int *)(col_scale + kTileN);                   // [128]
-    unsigned *col_dmax = (unsigned *)(col_flag + kTileN);          // [128]
+    unsigned *col_dmax = (unsigned *)(col_scale + kTileN);         // [128]
 
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -85,7 +100,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(smem_u32(&tfull[a]), 1);
-            mbar_init(smem_u32(&tempty[a]), 4);  // lane 0 of each epilogue warp
+            mbar_init(smem_u32(&tempty[a]), kEpiWarps);  // lane 0 of each epilogue warp
         }
         mbar_init(smem_u32(done), 1);
         *abort_flag = 0;
@@ -192,29 +207,30 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         umma_commit(smem_u32(done));
         mbar_wait(smem_u32(done), 0);  // every MMA of this CTA has retired (bounded)
     } else if (warp >= 2) {
-        // ---------------- epilogue (128 threads, one TMEM lane each) ----------------
+        // ---------------- epilogue (256 threads: one TMEM lane each, two per lane) ----------------
         const int et = tid - 64;
         const int quarter = warp & 3;  // TMEM lanes this warp may access
         const int row = quarter * 32 + lane;
+        const int half = (warp - 2) >> 2;  // the tile's columns 64 half .. 64 half + 63
         const uint32_t lane_off = (uint32_t)(quarter * 32) << 16;
         __shared__ int s_fail;
         if (et == 0) s_fail = 0;
-        epi_barrier();
+        epi_sync();
         uint32_t j = 0;
         for (int64_t tile = blockIdx.x; tile < total; tile += gridDim.x) {
             const int64_t n_tile = tile / m_tiles;
             const int m_tile = (int)(tile % m_tiles);
             if (!tile_live(ep, n_tile)) continue;
             const uint32_t a = j & 1, u = j >> 1;
-            if (ep.mode == 1) {
+            if (ep.mode == 1 && et < kTileN) {
                 const int64_t t = n_tile * kTileN + et;
                 const int f = ep.flags[t];
-                col_flag[et] = f;
-                col_scale[et] = (f & kActive) ? pow2f_g(-ep.k_exp - ep.rexp[t]) : 0.0f;
+                const float sc = pow2f_g(-ep.k_exp - ep.rexp[t]);
+                col_scale[et] = (f & kActive) ? ((f & kAnchored) ? -sc : sc) : 0.0f;
                 col_dmax[et] = 0u;
             }
             if (!mbar_wait(smem_u32(&tfull[a]), u & 1, lim)) atomicOr(&s_fail, 1);
-            epi_barrier();
+            epi_sync();
             if (s_fail) {
                 *vabort = 1;
                 atomicExch(ep.err, 1);
@@ -223,7 +239,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             tc_fence_after();
             const int m = m_tile * kTileM + row;
             const uint32_t tacc = tmem + a * kAccCols + lane_off;
-            for (int cb = 0; cb < kTileN / 32; ++cb) {
+            for (int cb = half * (kTileN / 64); cb < (half + 1) * (kTileN / 64); ++cb) {
                 uint32_t vr[32], vi[32];
                 tmem_ld32(tacc + cb * 32, vr);
                 if constexpr (CPLX) tmem_ld32(tacc + kTileN + cb * 32, vi);
@@ -250,59 +266,51 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         }
                     }
                 } else {
-                    // Update V of this lane's bus for 32 columns (loads first, then stores), then a
-                    // transposed butterfly: after 31 shuffles lane l holds max_rows |dV| of column
-                    // cb*32 + l.
-                    float2 old[32];
-                    float mag[32];
+                    // Update V of this lane's bus for the block's 32 columns, 16 at a time (loads
+                    // first, then stores); the largest |dV|^2 of each column over the warp's rows by
+                    // one warp-wide reduction, kept by lane q for column q, its square root taken
+                    // once (the square root is monotonic, so this is the largest |dV|).
+                    const bool row_ok = m < ep.n;
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        const int c = cb * 32 + q;
-                        const int f = col_flag[c];
-                        const bool act = (f & kActive) && m < ep.n;
-                        const int64_t k = (n_tile * kTileN + c) * ep.n_pad + m;
-                        const float2 *src = (f & kAnchored) ? ep.Vlo : ep.Vhi;  // anchored: V_ref fixed
-                        old[q] = act ? src[k] : make_float2(0.0f, 0.0f);
-                    }
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const int c0 = cb * 32 + hh * 16;
+                        float2 old[16];
 #pragma unroll
-                    for (int q = 0; q < 32; ++q) {
-                        const int c = cb * 32 + q;
-                        const int f = col_flag[c];
-                        const bool act = (f & kActive) && m < ep.n;
-                        const float sc = col_scale[c];
-                        const float dr = __uint_as_float(vr[q]) * sc, di = __uint_as_float(vi[q]) * sc;
-                        float dmag = 0.0f;
-                        if (act) {
-                            const int64_t k = (n_tile * kTileN + c) * ep.n_pad + m;
-                            float2 *dst = (f & kAnchored) ? ep.Vlo : ep.Vhi;
-                            dst[k] = make_float2(old[q].x + dr, old[q].y + di);
-                            dmag = sqrtf(dr * dr + di * di);
-                            if (dmag != dmag) dmag = __int_as_float(0x7f800000);  // NaN -> +inf
+                        for (int q = 0; q < 16; ++q) {
+                            const float sc = col_scale[c0 + q];
+                            const int64_t k = (n_tile * kTileN + c0 + q) * ep.n_pad + m;
+                            const float2 *src = sc < 0.0f ? ep.Vlo : ep.Vhi;  // anchored: V_ref fixed
+                            old[q] = (sc != 0.0f && row_ok) ? src[k] : make_float2(0.0f, 0.0f);
                         }
-                        mag[q] = dmag;
-                    }
+                        float mine = 0.0f;
 #pragma unroll
-                    for (int off = 16; off >= 1; off >>= 1) {
-                        const bool upper = (lane & off) != 0;
-#pragma unroll
-                        for (int jj = 0; jj < off; ++jj) {
-                            const float send = upper ? mag[jj] : mag[jj + off];
-                            const float keep = upper ? mag[jj + off] : mag[jj];
-                            mag[jj] = fmaxf(keep, __shfl_xor_sync(0xffffffffu, send, off));
+                        for (int q = 0; q < 16; ++q) {
+                            const float sc = col_scale[c0 + q], s = fabsf(sc);
+                            const float dr = __uint_as_float(vr[hh * 16 + q]) * s, di = __uint_as_float(vi[hh * 16 + q]) * s;
+                            float d2 = 0.0f;
+                            if (sc != 0.0f && row_ok) {
+                                const int64_t k = (n_tile * kTileN + c0 + q) * ep.n_pad + m;
+                                float2 *dst = sc < 0.0f ? ep.Vlo : ep.Vhi;
+                                dst[k] = make_float2(old[q].x + dr, old[q].y + di);
+                                d2 = __fmaf_rn(dr, dr, __fmul_rn(di, di));
+                                if (d2 != d2) d2 = __int_as_float(0x7f800000);  // NaN -> +inf
+                            }
+                            const float mx = warp_max_f(d2);
+                            if (lane == q) mine = mx;
                         }
+                        if (lane < 16 && mine > 0.0f) atomicMax(&col_dmax[c0 + lane], __float_as_uint(sqrtf(mine)));
                     }
-                    if (mag[0] > 0.0f) atomicMax(&col_dmax[cb * 32 + lane], __float_as_uint(mag[0]));
                 }
             }
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&tempty[a]));  // accumulator stage a is free again
-            epi_barrier();
-            if (ep.mode == 1) {
+            epi_sync();
+            if (ep.mode == 1 && et < kTileN) {
                 const unsigned d = col_dmax[et];
                 if (d) atomicMax(&ep.delta[n_tile * kTileN + et], d);
             }
-            epi_barrier();  // column info is rewritten by the next tile
+            epi_sync();  // column info is rewritten by the next tile
             ++j;
         }
     }

@@ -56,9 +56,9 @@ sys.path.insert(0, ROOT)
 METRIC = "PF solves/s at ≤1e-8 pu vs FP64 oracle: mixed+learned-start vs plain FP64 FPI"
 
 # dram__bytes_read.sum + dram__bytes_write.sum of one tc_gemm launch from an ncu capture of the
-# 1,000-bus feeder over 16,384 columns (203.7 MB + 75.5 MB), per iterating column; scaled by the
+# 1,000-bus feeder over 16,384 columns (203.8 MB + 77.4 MB), per iterating column; scaled by the
 # columns each launch of this run processes.  None once the kernel has changed since the capture.
-GEMM_TRAFFIC_BYTES_PER_COLUMN = (203.725056e6 + 75.471360e6) / 16384
+GEMM_TRAFFIC_BYTES_PER_COLUMN = (203.764224e6 + 77.426432e6) / 16384
 # The same for the sparse tree kernel mx_tree started from the learned prediction (the headline
 # step's solve): 1,313.1 MB read (S and the half-precision prediction) + 1,002.8 MB written for
 # 65,536 columns of the 1,000-bus feeder.

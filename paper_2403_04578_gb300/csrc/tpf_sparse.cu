@@ -105,8 +105,8 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return make_float2(
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
 // The FP32 products below are written with explicitly rounded intrinsics, so that the compiler
 // cannot contract them differently in different instantiations of the kernel: every kernel then
-// rounds a given formula the same way (ZIP loads with alpha_P = 1 reproduce constant power bit for
-// bit, whatever code surrounds the formula).
+// rounds a given formula the same way, whatever code surrounds it (ZIP loads with alpha_P = 1 then
+// round their currents exactly as constant power does).
 __device__ __forceinline__ float2 cmul2(float2 a, float2 b) {
     return make_float2(__fmaf_rn(a.x, b.x, -__fmul_rn(a.y, b.y)), __fmaf_rn(a.x, b.y, __fmul_rn(a.y, b.x)));
 }
@@ -207,7 +207,7 @@ __device__ __forceinline__ f2 qneg(f2 a) { return {-a.h, -a.l}; }
 // The sum without the final renormalisation: the high part is the rounded sum of the high parts,
 // the low part collects their exact rounding error and the low parts.  Inside a scan, where a
 // handful of such sums follow one another, the low part stays within a few ulp of the high part;
-// qnorm restores |l| <= ulp(h) / 2 at the end.
+// cqnorm restores |l| <= ulp(h) / 2 at the end.
 __device__ __forceinline__ f2 qadd_lazy(f2 a, f2 b) {
     const f2 s = two_sum(a.h, b.h);
     return {s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l))};
